@@ -1,0 +1,244 @@
+/*
+ * vup.h -- C ABI of libvup.so, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of Vectorized Uncertainty Propagation (VUP) and
+ * Input Probability Sensitivity Analysis (IPSA), arXiv 1908.11246.
+ *
+ * The calls follow the paper's statement of the problem:
+ *   1. a uniform grid of midpoints over the input domain (Sec. 3, composite
+ *      midpoint rule; Algorithm "VUP - Single probability", first step);
+ *   2. the model evaluated once on that grid, and the model matrix built
+ *      from it (Eq. 5 and Eq. MUP: a one-hot matrix that sorts every grid
+ *      point into its output bin);
+ *   3. K input densities pushed through that single model matrix at once
+ *      (Eq. VUP), giving per-density output histograms (Eq. 4) and moments;
+ *   4. IPSA sensitivities of those moments to each density's location and
+ *      width (Sec. 5.2).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Grid: ndim in {1,2,3} axes; axis d has n[d] midpoints
+ *   x_{d,a} = lo[d] + (a + 1/2) (hi[d] - lo[d]) / n[d].  The flat index is
+ *   row-major with axis 0 slowest.  N = prod n[d].
+ * - Densities are products over axes of one-dimensional densities
+ *   (Gaussian as in Eq. gaussh, uniform, truncated normal), evaluated at the
+ *   midpoints and normalised over the grid, i.e. hard-truncated at the domain
+ *   boundary and renormalised (Sec. 5.3).
+ * - Output bins: B equal-width bins over [min y, max y], half-open, the last
+ *   closed: bin = min(floor((y - ymin) / (ymax - ymin) * B), B - 1), all in
+ *   IEEE double with correctly rounded operations (Eq. 4).
+ * - Moments: raw[k][j-1] = sum_i W[k,i] y_i^j and central[k][0] = mean,
+ *   central[k][j-1] = E[(y - mean)^j] (j = 2..J), J = n_moments <= 4.
+ * - Pointers documented as "device" must point to memory of the current CUDA
+ *   device; "host" pointers are read during the call and not retained.
+ *   The caller owns every buffer it passes; the grid owns its internals.
+ * - Every call returns a vup_status.  Argument errors are detected on the
+ *   host before any work is queued and leave all outputs untouched.
+ *   Conditions detected on the device (a density with no grid point in its
+ *   support, a bounded device-side wait that expired) are recorded in the
+ *   grid's device status word and returned by vup_sync().  No call exits,
+ *   aborts or traps.
+ * - Stream-ordered calls enqueue work on `stream` and return without
+ *   synchronising.  A grid must not be used from two streams concurrently.
+ */
+#ifndef VUP_H
+#define VUP_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *vup_stream_t; /* == cudaStream_t; NULL = legacy default stream */
+
+typedef struct vup_grid_s *vup_grid;
+
+typedef enum {
+    VUP_OK = 0,
+    VUP_ERR_INVALID_ARG = 1,   /* bad shape, null required pointer, out-of-range value */
+    VUP_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    VUP_ERR_OOM = 3,           /* device allocation failed */
+    VUP_ERR_STATE = 4,         /* grid has no model outputs yet (call vup_eval_model first) */
+    VUP_ERR_EMPTY_SUPPORT = 5, /* some density holds no grid point in its support */
+    VUP_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired; results are invalid */
+    VUP_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+} vup_status;
+
+typedef enum { VUP_GAUSS = 0, VUP_UNIFORM = 1, VUP_TRUNCNORM = 2 } vup_density_kind;
+
+typedef enum {
+    VUP_FP64 = 0,   /* 1-D grids only: every step in double precision            */
+    VUP_FP32 = 1,   /* plain FP32 CUDA-core contraction, FP64 final reduction     */
+    VUP_BF16X3 = 2  /* tcgen05 tensor cores, 3 split BF16 products, FP32 accumulate */
+} vup_precision;
+
+/* Built-in models (model_id of vup_eval_model).  theta is a host array. */
+typedef enum {
+    VUP_MODEL_SIN_QUAD_1D = 1,     /* y = t0 sin x + t1 x^2                         (1 axis) */
+    VUP_MODEL_SIN_SIN2_2D = 2,     /* y = t0 sin x1 + t1 sin^2 x2    (Sec. 4.1)     (2 axes) */
+    VUP_MODEL_MIXED_3D = 3,        /* y = sin x1 + t0 sin^2 x2 + t1 x3^4 sin x1     (3 axes) */
+    VUP_MODEL_OSCILLATOR_2D = 4,   /* y = exp(-x2 x1 t0) cos(x1 sqrt(1 - x2^2) t0)  (2 axes) */
+    VUP_MODEL_IPSA_EXAMPLE_2D = 5, /* y = x1^2 + 5 sin(3 x1) + x2    (Sec. 5.3)     (2 axes) */
+    VUP_MODEL_POLY = 6             /* y = t0 + sum_d (t[1+2d] x_d + t[2+2d] x_d^2)  (1-3 axes) */
+} vup_model_id;
+
+/*
+ * Densities, structure of arrays with element [k * ndim + d].  All pointers
+ * are device pointers owned by the caller and must stay valid until the
+ * queued work has run.
+ *   kind  : uint8 vup_density_kind per (k, d)
+ *   mu    : Gaussian / truncated-normal mean; uniform centre
+ *   sigma : Gaussian / truncated-normal standard deviation (> 0);
+ *           uniform full width (> 0), support |x - mu| <= sigma / 2
+ *   lo,hi : truncated-normal absolute bounds (support lo <= x <= hi);
+ *           may be NULL when no axis is truncated normal
+ */
+typedef struct {
+    int64_t K;
+    int32_t ndim;
+    const uint8_t *kind;
+    const double *mu;
+    const double *sigma;
+    const double *lo;
+    const double *hi;
+} vup_densities;
+
+/* Limits of this build. */
+#define VUP_MAX_BINS 8192
+#define VUP_MAX_MOMENTS 4
+#define VUP_MAX_AXIS_POINTS 32767
+
+/*
+ * Create a grid (Sec. 3 uniform midpoint grid).  n, lo, hi: host arrays of
+ * length ndim; 1 <= n[d] <= VUP_MAX_AXIS_POINTS, lo[d] < hi[d], finite.
+ * Allocates device memory synchronously on the current device.
+ * *out receives the handle; release it with vup_grid_destroy.
+ */
+vup_status vup_grid_create(int ndim, const int64_t *n, const double *lo, const double *hi,
+                           vup_grid *out);
+
+/* Free every device allocation the grid owns (synchronises the device). */
+vup_status vup_grid_destroy(vup_grid g);
+
+/*
+ * Evaluate a built-in model on the grid and build the model matrix (Sec. 2
+ * model function; Algorithm "VUP - Single probability" steps 1-2 and the
+ * sparse model-matrix construction; Eq. MUP):
+ *   y_i = M(x_i; theta) in FP64, [min y, max y], per-point bin ids,
+ *   a stable counting sort of the grid points by bin (the CSR form of the
+ *   one-hot model matrix), and the power tables (y / s)^j, j = 1..n_moments,
+ *   with s = max(|min y|, |max y|).
+ * theta: host array of n_theta doubles (n_theta <= 8).
+ * 1 <= n_bins <= VUP_MAX_BINS, 1 <= n_moments <= VUP_MAX_MOMENTS.
+ * Model values must be finite.
+ */
+vup_status vup_eval_model(vup_grid g, int model_id, const double *theta, int n_theta,
+                          int n_bins, int n_moments, vup_stream_t stream);
+
+/*
+ * Same as vup_eval_model but with model values supplied by the caller:
+ * y_dev is a device array of N finite doubles in flat grid order (a user
+ * model evaluated elsewhere).  It is copied; the caller keeps ownership.
+ */
+vup_status vup_set_outputs(vup_grid g, const double *y_dev, int n_bins, int n_moments,
+                           vup_stream_t stream);
+
+/*
+ * Push K densities through the grid's model matrix at once (Eq. VUP):
+ *   moments_raw     [K][J] double, device, or NULL
+ *   moments_central [K][J] double, device, or NULL
+ *   hist            [K][B] float,  device, or NULL   (Eq. 4 output probabilities)
+ * J and B are the values given to vup_eval_model.  precision selects the
+ * contraction: VUP_FP64 requires ndim == 1; 1-D grids run in FP64 whatever
+ * is requested; VUP_BF16X3 needs ndim >= 2.  W[k, i] is generated on the
+ * fly and never stored.  The first call with a larger K than before
+ * allocates per-K scratch (not capturable in a CUDA graph); later calls with
+ * K no larger allocate nothing.
+ */
+vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_precision precision,
+                         double *moments_raw, double *moments_central, float *hist,
+                         vup_stream_t stream);
+
+/*
+ * Supplied-weights variant (Eq. VUP with the input probability matrix given
+ * explicitly, as the paper materialises it): W is a device [K][N] float
+ * array of per-grid-point weights (used as given, not renormalised).
+ *   moments_raw [K][J] double (device, or NULL), hist [K][B] float (device, or NULL).
+ */
+vup_status vup_propagate_weights(vup_grid g, int64_t K, const float *W, double *moments_raw,
+                                 float *hist, vup_stream_t stream);
+
+/*
+ * IPSA sensitivities (Sec. 5.2): derivatives of the raw moments M_j with
+ * respect to each density's mu and sigma on every axis, for ndim == 2 grids
+ * (and ndim == 1).  Gaussian and truncated-normal axes are differentiated
+ * with their truncation bounds held fixed; uniform axes return 0.
+ * W is recomputed, never stored.
+ *   grad_moments NULL : full Jacobian, dmu/dsigma are [K][ndim][J] float
+ *   grad_moments [K][J] double (device): vector-Jacobian product,
+ *                        dmu/dsigma are [K][ndim] float,
+ *                        dmu[k][d] = sum_j grad[k][j] dM_j/dmu_{k,d}
+ * precision: VUP_FP32 or VUP_BF16X3 (VUP_FP64 for ndim == 1).
+ */
+vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, vup_precision precision,
+                                const double *grad_moments, float *dmu, float *dsigma,
+                                vup_stream_t stream);
+
+/*
+ * Batched uneven propagation: n_inst independent instances (grid g[i] with
+ * densities d[i]) in one persistent launch per stage.  g, d, moments_raw and
+ * hist are host arrays of length n_inst; moments_raw[i] / hist[i] are device
+ * pointers (or NULL) shaped as in vup_propagate.  All grids must have ndim == 2
+ * and the same n_moments.  Work tiles are ordered longest-first.
+ */
+vup_status vup_propagate_batched(int n_inst, const vup_grid *g, const vup_densities *d,
+                                 vup_precision precision, double *const *moments_raw,
+                                 float *const *hist, vup_stream_t stream);
+
+/*
+ * Wait for the grid's queued work on `stream` and return (and clear) the
+ * first condition recorded on the device: VUP_OK, VUP_ERR_EMPTY_SUPPORT or
+ * VUP_ERR_TIMEOUT.
+ */
+vup_status vup_sync(vup_grid g, vup_stream_t stream);
+
+/* Grid facts after vup_eval_model / vup_set_outputs (host copies). */
+typedef struct {
+    int32_t ndim;
+    int64_t n[3];
+    int64_t N;
+    int32_t n_bins;
+    int32_t n_moments;
+    double ymin, ymax, yscale;
+    int32_t have_model;
+} vup_grid_info_t;
+vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info);
+
+/* Copy one of the grid's arrays into a caller device buffer (for checks).
+ * which: 0 = y (double[N]), 1 = bin ids (int32[N]), 2 = sorted order
+ * (int32[N], flat index of the t-th point in bin order), 3 = bin offsets
+ * (int32[B+1]).  nbytes must equal the array's size. */
+vup_status vup_grid_copy(vup_grid g, int which, void *dst_dev, size_t nbytes,
+                         vup_stream_t stream);
+
+/*
+ * Per-kernel timing for measurement: while enabled, every kernel the library
+ * launches is bracketed by CUDA events recorded on its launching stream.
+ * vup_profile(1) clears the record and enables it, vup_profile(0) disables it.
+ * vup_profile_read synchronises the device and writes a NUL-terminated JSON
+ * object {"kernel": [launches, total_ms], ...} into buf (cap bytes).
+ */
+vup_status vup_profile(int enable);
+vup_status vup_profile_read(char *buf, size_t cap);
+
+/* Static description of a status code. */
+const char *vup_status_string(vup_status s);
+
+/* Library version string. */
+const char *vup_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VUP_H */

@@ -1,0 +1,503 @@
+// C ABI of libvup: argument checking, grid lifetime, scratch management and
+// the order in which the hot-path kernels are queued.
+#include "vup_internal.cuh"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+static thread_local char g_last_err[512];
+
+void vup_set_last_cuda_error(cudaError_t e, const char *expr, const char *file, int line) {
+    snprintf(g_last_err, sizeof(g_last_err), "%s: %s (%s:%d)", cudaGetErrorName(e), expr, file, line);
+}
+
+vup_status devbuf_reserve(DevBuf &b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return VUP_OK;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes < 256 ? 256 : bytes);
+    if (e != cudaSuccess) {
+        vup_set_last_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+        cudaGetLastError();
+        return VUP_ERR_OOM;
+    }
+    b.p = p;
+    b.bytes = bytes;
+    return VUP_OK;
+}
+
+void devbuf_free(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// ---- per-kernel timing registry -------------------------------------------
+namespace {
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+    int launches;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_recs;
+std::vector<cudaEvent_t> g_prof_pool;
+
+cudaEvent_t prof_event() {
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+ProfScope::ProfScope(const char *n, cudaStream_t s, int l) : name(n), stream(s), launches(l), slot(-1) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfRec r{n, prof_event(), prof_event(), l};
+    cudaEventRecord(r.a, s);
+    g_prof_recs.push_back(r);
+    slot = (int)g_prof_recs.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (slot < (int)g_prof_recs.size()) cudaEventRecord(g_prof_recs[slot].b, stream);
+}
+
+extern "C" vup_status vup_profile(int enable) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (enable) {
+        for (auto &r : g_prof_recs) {
+            g_prof_pool.push_back(r.a);
+            g_prof_pool.push_back(r.b);
+        }
+        g_prof_recs.clear();
+    }
+    g_prof_on = enable != 0;
+    return VUP_OK;
+}
+
+extern "C" vup_status vup_profile_read(char *buf, size_t cap) {
+    if (!buf || cap < 3) return VUP_ERR_INVALID_ARG;
+    VUP_CHECK_CUDA(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::map<std::string, std::pair<long, double>> agg;
+    for (auto &r : g_prof_recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        auto &e = agg[r.name];
+        e.first += r.launches;
+        e.second += ms;
+    }
+    std::string out = "{";
+    bool first = true;
+    for (auto &kv : agg) {
+        char tmp[256];
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": [%ld, %.6f]", first ? "" : ", ", kv.first.c_str(), kv.second.first,
+                 kv.second.second);
+        out += tmp;
+        first = false;
+    }
+    out += "}";
+    if (out.size() + 1 > cap) return VUP_ERR_INVALID_ARG;
+    memcpy(buf, out.c_str(), out.size() + 1);
+    return VUP_OK;
+}
+
+int vup_num_sms() {
+    int dev = 0, n = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+int vup_hist_chunks_for(int64_t N);
+
+extern "C" const char *vup_status_string(vup_status s) {
+    switch (s) {
+    case VUP_OK: return "VUP_OK";
+    case VUP_ERR_INVALID_ARG: return "VUP_ERR_INVALID_ARG: invalid argument";
+    case VUP_ERR_CUDA: return "VUP_ERR_CUDA: a CUDA call failed";
+    case VUP_ERR_OOM: return "VUP_ERR_OOM: device allocation failed";
+    case VUP_ERR_STATE: return "VUP_ERR_STATE: grid has no model outputs (call vup_eval_model)";
+    case VUP_ERR_EMPTY_SUPPORT: return "VUP_ERR_EMPTY_SUPPORT: a density holds no grid point";
+    case VUP_ERR_TIMEOUT: return "VUP_ERR_TIMEOUT: a bounded device wait expired";
+    case VUP_ERR_UNSUPPORTED: return "VUP_ERR_UNSUPPORTED: not implemented for these arguments";
+    }
+    return "unknown vup_status";
+}
+
+extern "C" const char *vup_version(void) { return "vup-gb300 0.1 (sm_103a)"; }
+
+extern "C" const char *vup_last_error_detail(void) { return g_last_err; }
+
+static void free_grid(vup_grid g) {
+    cudaFree(g->y);
+    cudaFree(g->ext);
+    cudaFree(g->bins);
+    cudaFree(g->perm);
+    cudaFree(g->offsets);
+    cudaFree(g->hpt);
+    cudaFree(g->run_start);
+    cudaFree(g->run_rest);
+    cudaFree(g->run_bin);
+    cudaFree(g->n_runs);
+    cudaFree(g->flags_scan);
+    cudaFree(g->chunk_pt);
+    cudaFree(g->chunk_run);
+    cudaFree(g->chunk_bin);
+    cudaFree(g->ydev_scale);
+    cudaFree(g->dstatus);
+    for (int o = 0; o < 2; ++o) {
+        cudaFree(g->zs[o]);
+        cudaFree(g->zt_hi[o]);
+        cudaFree(g->zt_lo[o]);
+    }
+    devbuf_free(g->sort_counts);
+    devbuf_free(g->scan_tmp);
+    devbuf_free(g->dconst);
+    devbuf_free(g->dstats);
+    devbuf_free(g->ftab);
+    devbuf_free(g->atab_hi);
+    devbuf_free(g->atab_lo);
+    devbuf_free(g->partials);
+    devbuf_free(g->hist_part);
+    devbuf_free(g->ipsa_part);
+    delete g;
+}
+
+extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *lo, const double *hi,
+                                      vup_grid *out) {
+    if (!out || !n || !lo || !hi || ndim < 1 || ndim > 3) return VUP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int64_t N = 1;
+    for (int d = 0; d < ndim; ++d) {
+        if (n[d] < 1 || n[d] > VUP_MAX_AXIS_POINTS) return VUP_ERR_INVALID_ARG;
+        if (!isfinite(lo[d]) || !isfinite(hi[d]) || !(lo[d] < hi[d])) return VUP_ERR_INVALID_ARG;
+        N *= n[d];
+    }
+    if (N >= ((int64_t)1 << 31) - 1) return VUP_ERR_INVALID_ARG;
+    vup_grid g = new vup_grid_s();
+    cudaGetDevice(&g->device);
+    g->ndim = ndim;
+    g->N = N;
+    for (int d = 0; d < ndim; ++d) {
+        g->n[d] = n[d];
+        g->lo[d] = lo[d];
+        g->hi[d] = hi[d];
+    }
+    // orientation 0: reduce over the last axis; orientation 1: over axis 0 (2-D)
+    for (int o = 0; o < 2; ++o) {
+        Orient &ori = g->orient[o];
+        ori.red_axis0 = o == 0 ? ndim - 1 : 0;
+        ori.R = g->n[ori.red_axis0];
+        ori.R_pad = ceil_div64(ori.R, 64) * 64;
+        ori.Q = N / ori.R;
+        ori.NC = ori.Q * 4;
+        ori.n_rest_axes = 0;
+        ori.rest_axes[0] = ori.rest_axes[1] = -1;
+        for (int d = 0; d < ndim; ++d)
+            if (d != ori.red_axis0 && ori.n_rest_axes < 2) ori.rest_axes[ori.n_rest_axes++] = d;
+    }
+    g->n_chunks = vup_hist_chunks_for(N);
+    const int C = g->n_chunks;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes) \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
+    ALLOC(g->y, sizeof(double) * N);
+    ALLOC(g->ext, sizeof(unsigned long long) * 2);
+    ALLOC(g->bins, sizeof(int32_t) * N);
+    ALLOC(g->perm, sizeof(int32_t) * N);
+    ALLOC(g->hpt, sizeof(uint32_t) * (N + 4));
+    ALLOC(g->run_start, sizeof(int32_t) * (N + 1));
+    ALLOC(g->run_rest, sizeof(int32_t) * N);
+    ALLOC(g->run_bin, sizeof(int32_t) * N);
+    ALLOC(g->n_runs, sizeof(int32_t));
+    ALLOC(g->flags_scan, sizeof(int32_t) * N);
+    ALLOC(g->chunk_pt, sizeof(int32_t) * (C + 1));
+    ALLOC(g->chunk_run, sizeof(int32_t) * (C + 1));
+    ALLOC(g->chunk_bin, sizeof(int32_t) * 2 * C);
+    ALLOC(g->ydev_scale, sizeof(double));
+    ALLOC(g->dstatus, sizeof(int));
+#undef ALLOC
+    if (e == cudaSuccess) e = cudaMemset(g->dstatus, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        vup_set_last_cuda_error(e, "vup_grid_create", __FILE__, __LINE__);
+        cudaGetLastError();
+        free_grid(g);
+        return e == cudaErrorMemoryAllocation ? VUP_ERR_OOM : VUP_ERR_CUDA;
+    }
+    *out = g;
+    return VUP_OK;
+}
+
+extern "C" vup_status vup_grid_destroy(vup_grid g) {
+    if (!g) return VUP_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    free_grid(g);
+    return VUP_OK;
+}
+
+static vup_status model_ready(vup_grid g, int n_bins, int n_moments) {
+    if (n_bins < 1 || n_bins > VUP_MAX_BINS || n_moments < 1 || n_moments > VUP_MAX_MOMENTS)
+        return VUP_ERR_INVALID_ARG;
+    if (g->B_cap < n_bins) {
+        cudaFree(g->offsets);
+        g->offsets = nullptr;
+        VUP_CHECK_CUDA(cudaMalloc(&g->offsets, sizeof(int32_t) * (n_bins + 1)));
+        g->B_cap = n_bins;
+    }
+    g->B = n_bins;
+    g->J = n_moments;
+    return VUP_OK;
+}
+
+static vup_status finish_model(vup_grid g, cudaStream_t s) {
+    vup_status st = vup_launch_grid_finish(g, s);
+    if (st != VUP_OK) return st;
+    if (g->ndim >= 2) {
+        st = vup_build_tables(g, 0, 0, s);
+        if (st != VUP_OK) return st;
+        st = vup_build_tables(g, 0, 1, s);
+        if (st != VUP_OK) return st;
+    }
+    g->have_model = 1;
+    return VUP_OK;
+}
+
+static bool model_ndim_ok(int model_id, int ndim) {
+    switch (model_id) {
+    case VUP_MODEL_SIN_QUAD_1D: return ndim == 1;
+    case VUP_MODEL_SIN_SIN2_2D:
+    case VUP_MODEL_OSCILLATOR_2D:
+    case VUP_MODEL_IPSA_EXAMPLE_2D: return ndim == 2;
+    case VUP_MODEL_MIXED_3D: return ndim == 3;
+    case VUP_MODEL_POLY: return ndim >= 1 && ndim <= 3;
+    default: return false;
+    }
+}
+
+extern "C" vup_status vup_eval_model(vup_grid g, int model_id, const double *theta, int n_theta, int n_bins,
+                                     int n_moments, vup_stream_t stream) {
+    if (!g || n_theta < 0 || n_theta > 8 || (n_theta > 0 && !theta)) return VUP_ERR_INVALID_ARG;
+    if (!model_ndim_ok(model_id, g->ndim)) return VUP_ERR_INVALID_ARG;
+    double th[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < n_theta; ++q) {
+        if (!isfinite(theta[q])) return VUP_ERR_INVALID_ARG;
+        th[q] = theta[q];
+    }
+    vup_status st = model_ready(g, n_bins, n_moments);
+    if (st != VUP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->have_model = 0;
+    st = vup_launch_model_eval(g, model_id, th, s);
+    if (st != VUP_OK) return st;
+    return finish_model(g, s);
+}
+
+extern "C" vup_status vup_set_outputs(vup_grid g, const double *y_dev, int n_bins, int n_moments,
+                                      vup_stream_t stream) {
+    if (!g || !y_dev) return VUP_ERR_INVALID_ARG;
+    vup_status st = model_ready(g, n_bins, n_moments);
+    if (st != VUP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->have_model = 0;
+    VUP_CHECK_CUDA(cudaMemcpyAsync(g->y, y_dev, sizeof(double) * g->N, cudaMemcpyDeviceToDevice, s));
+    return finish_model(g, s);
+}
+
+static vup_status check_dens(vup_grid g, const vup_densities *d) {
+    if (!d || d->K < 1 || d->K > (int64_t)1 << 26 || d->ndim != g->ndim) return VUP_ERR_INVALID_ARG;
+    if (!d->kind || !d->mu || !d->sigma) return VUP_ERR_INVALID_ARG;
+    if ((d->lo == nullptr) != (d->hi == nullptr)) return VUP_ERR_INVALID_ARG;
+    return VUP_OK;
+}
+
+// Per-K scratch: density constants, factor tables, split A tables, partials.
+static vup_status reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa) {
+    const int64_t K_pad = ceil_div64(K, 128) * 128;
+    const int nd = g->ndim;
+    vup_status st;
+    if ((st = devbuf_reserve(g->dconst, sizeof(DensConst) * K_pad * nd)) != VUP_OK) return st;
+    if ((st = devbuf_reserve(g->dstats, sizeof(DensStats) * K_pad * nd)) != VUP_OK) return st;
+    if ((st = devbuf_reserve(g->ftab, sizeof(float) * K_pad * vup_ftab_floats(g))) != VUP_OK) return st;
+    if (nd >= 2) {
+        const int64_t nct = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles(g->orient[0]));
+        if ((st = devbuf_reserve(g->partials, sizeof(float) * 4 * K_pad * nct)) != VUP_OK) return st;
+        if ((st = devbuf_reserve(g->hist_part, sizeof(float) * 2 * K_pad * g->n_chunks)) != VUP_OK) return st;
+        if (bf16) {
+            size_t a = (size_t)K_pad * g->orient[0].R_pad + (ipsa ? (size_t)K_pad * g->orient[1].R_pad : 0);
+            if ((st = devbuf_reserve(g->atab_hi, sizeof(__nv_bfloat16) * a)) != VUP_OK) return st;
+            if ((st = devbuf_reserve(g->atab_lo, sizeof(__nv_bfloat16) * a)) != VUP_OK) return st;
+        }
+        if (ipsa) {
+            int64_t n0 = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles(g->orient[0]));
+            int64_t n1 = std::max(vup_simt_col_tiles(g->orient[1]), vup_tc_col_tiles(g->orient[1]));
+            if ((st = devbuf_reserve(g->ipsa_part, sizeof(float) * 4 * 3 * K_pad * (n0 + n1))) != VUP_OK)
+                return st;
+        }
+    }
+    g->K_cap = std::max(g->K_cap, K);
+    return VUP_OK;
+}
+
+extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_precision precision,
+                                    double *moments_raw, double *moments_central, float *hist,
+                                    vup_stream_t stream) {
+    if (!g) return VUP_ERR_INVALID_ARG;
+    vup_status st = check_dens(g, d);
+    if (st != VUP_OK) return st;
+    if (precision != VUP_FP64 && precision != VUP_FP32 && precision != VUP_BF16X3) return VUP_ERR_INVALID_ARG;
+    if (!g->have_model) return VUP_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t K = d->K;
+    if (g->ndim == 1) {
+        if (precision == VUP_BF16X3) return VUP_ERR_UNSUPPORTED;
+        return vup_propagate_1d(g, d, moments_raw, moments_central, hist, s);
+    }
+    if (precision == VUP_FP64) return VUP_ERR_UNSUPPORTED;
+    const bool bf16 = precision == VUP_BF16X3;
+    const bool want_m = moments_raw || moments_central;
+    if ((st = reserve_k(g, K, bf16, false)) != VUP_OK) return st;
+    if ((st = vup_density_prep(g, d, (bf16 && want_m) ? 1 : 0, s)) != VUP_OK) return st;
+    if (want_m) {
+        int64_t nct;
+        if (bf16) {
+            if ((st = vup_moments_tc(g, K, 0, 1, (float *)g->partials.p, s)) != VUP_OK) return st;
+            nct = vup_tc_col_tiles(g->orient[0]);
+        } else {
+            if ((st = vup_moments_simt(g, K, 0, 1, (float *)g->partials.p, s)) != VUP_OK) return st;
+            nct = vup_simt_col_tiles(g->orient[0]);
+        }
+        if ((st = vup_moments_finish(g, K, (int)nct, moments_raw, moments_central, s)) != VUP_OK) return st;
+    }
+    if (hist) {
+        if ((st = vup_hist_fused(g, K, hist, s)) != VUP_OK) return st;
+    }
+    return VUP_OK;
+}
+
+extern "C" vup_status vup_propagate_weights(vup_grid g, int64_t K, const float *W, double *moments_raw,
+                                            float *hist, vup_stream_t stream) {
+    if (!g || !W || K < 1 || K > (int64_t)1 << 26) return VUP_ERR_INVALID_ARG;
+    if (!g->have_model) return VUP_ERR_STATE;
+    return vup_weights_path(g, K, W, moments_raw, hist, (cudaStream_t)stream);
+}
+
+extern "C" vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, vup_precision precision,
+                                           const double *grad_moments, float *dmu, float *dsigma,
+                                           vup_stream_t stream) {
+    if (!g || !dmu || !dsigma) return VUP_ERR_INVALID_ARG;
+    vup_status st = check_dens(g, d);
+    if (st != VUP_OK) return st;
+    if (precision != VUP_FP64 && precision != VUP_FP32 && precision != VUP_BF16X3) return VUP_ERR_INVALID_ARG;
+    if (!g->have_model) return VUP_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->ndim == 1) {
+        if (precision == VUP_BF16X3) return VUP_ERR_UNSUPPORTED;
+        return vup_ipsa_1d(g, d, grad_moments, dmu, dsigma, s);
+    }
+    if (g->ndim != 2 || precision == VUP_FP64) return VUP_ERR_UNSUPPORTED;
+    const int64_t K = d->K;
+    const bool bf16 = precision == VUP_BF16X3;
+    if ((st = reserve_k(g, K, bf16, true)) != VUP_OK) return st;
+    if ((st = vup_build_tables(g, 1, bf16 ? 1 : 0, s)) != VUP_OK) return st;
+    if ((st = vup_density_prep(g, d, bf16 ? 3 : 0, s)) != VUP_OK) return st;
+    const int64_t K_pad = ceil_div64(K, 128) * 128;
+    float *p0 = (float *)g->ipsa_part.p;
+    int64_t n0, n1;
+    if (bf16) {
+        n0 = vup_tc_col_tiles(g->orient[0]);
+        n1 = vup_tc_col_tiles(g->orient[1]);
+    } else {
+        n0 = vup_simt_col_tiles(g->orient[0]);
+        n1 = vup_simt_col_tiles(g->orient[1]);
+    }
+    float *p1 = p0 + (size_t)3 * n0 * K_pad * 4;
+    for (int o = 0; o < 2; ++o) {
+        float *p = o == 0 ? p0 : p1;
+        st = bf16 ? vup_moments_tc(g, K, o, 3, p, s) : vup_moments_simt(g, K, o, 3, p, s);
+        if (st != VUP_OK) return st;
+    }
+    return vup_ipsa_finish(g, K, (int)n0, (int)n1, grad_moments, dmu, dsigma, s);
+}
+
+extern "C" vup_status vup_sync(vup_grid g, vup_stream_t stream) {
+    if (!g) return VUP_ERR_INVALID_ARG;
+    VUP_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int code = 0;
+    VUP_CHECK_CUDA(cudaMemcpy(&code, g->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code) VUP_CHECK_CUDA(cudaMemset(g->dstatus, 0, sizeof(int)));
+    switch (code) {
+    case 0: return VUP_OK;
+    case VUP_DSTAT_EMPTY: return VUP_ERR_EMPTY_SUPPORT;
+    case VUP_DSTAT_TIMEOUT: return VUP_ERR_TIMEOUT;
+    default: return VUP_ERR_INVALID_ARG;
+    }
+}
+
+extern "C" vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info) {
+    if (!g || !info) return VUP_ERR_INVALID_ARG;
+    memset(info, 0, sizeof(*info));
+    info->ndim = g->ndim;
+    for (int d = 0; d < 3; ++d) info->n[d] = d < g->ndim ? g->n[d] : 1;
+    info->N = g->N;
+    info->n_bins = g->B;
+    info->n_moments = g->J;
+    info->have_model = g->have_model;
+    if (g->have_model) {
+        unsigned long long k[2];
+        double sc = 1.0;
+        VUP_CHECK_CUDA(cudaDeviceSynchronize());
+        VUP_CHECK_CUDA(cudaMemcpy(k, g->ext, sizeof(k), cudaMemcpyDeviceToHost));
+        VUP_CHECK_CUDA(cudaMemcpy(&sc, g->ydev_scale, sizeof(double), cudaMemcpyDeviceToHost));
+        auto inv = [](unsigned long long key) {
+            unsigned long long u = (key >> 63) ? (key & 0x7fffffffffffffffull) : ~key;
+            double v;
+            memcpy(&v, &u, sizeof(v));
+            return v;
+        };
+        info->ymin = inv(k[0]);
+        info->ymax = inv(k[1]);
+        info->yscale = sc;
+    }
+    return VUP_OK;
+}
+
+extern "C" vup_status vup_grid_copy(vup_grid g, int which, void *dst_dev, size_t nbytes, vup_stream_t stream) {
+    if (!g || !dst_dev) return VUP_ERR_INVALID_ARG;
+    if (!g->have_model) return VUP_ERR_STATE;
+    const void *src = nullptr;
+    size_t need = 0;
+    switch (which) {
+    case 0: src = g->y; need = sizeof(double) * g->N; break;
+    case 1: src = g->bins; need = sizeof(int32_t) * g->N; break;
+    case 2: src = g->perm; need = sizeof(int32_t) * g->N; break;
+    case 3: src = g->offsets; need = sizeof(int32_t) * (g->B + 1); break;
+    default: return VUP_ERR_INVALID_ARG;
+    }
+    if (nbytes != need) return VUP_ERR_INVALID_ARG;
+    VUP_CHECK_CUDA(cudaMemcpyAsync(dst_dev, src, need, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return VUP_OK;
+}

@@ -1,0 +1,181 @@
+// Density preparation: the input pdfs evaluated on the grid and normalised
+// (Algorithm "VUP - Single probability": evaluate the input pdf at the grid
+// points and normalise; Sec. 5.3: hard truncation at the domain boundary and
+// renormalisation; Eq. gaussh Gaussian measurement uncertainty).
+//
+// Product densities factor over axes, so W[k, i] = prod_d g_d(k, a_d) / Z_d(k)
+// with Z_d = sum_a g_d(k, a).  This kernel writes the per-axis factor tables
+// g_d[a][k] (K x sum_d n_d floats -- never the K x N weights) and the FP64
+// normalisation statistics.  The contraction and histogram kernels form W on
+// the fly as products of these factors.
+#include "vup_internal.cuh"
+
+#include <math.h>
+
+#include <algorithm>
+
+namespace {
+
+struct DensIn {
+    const uint8_t *kind;
+    const double *mu, *sigma, *lo, *hi;
+};
+
+// Neumaier-compensated FP32 accumulator.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float t = s + v;
+        if (fabsf(s) >= fabsf(v)) c += (s - t) + v; else c += (v - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Per-axis density value at midpoint a (unnormalised), and u = ((a - n) - f) r.
+// Gaussian values are divided by their value at the midpoint nearest the mean
+// (a constant per (k, d) that the normalisation removes), so that very narrow
+// densities do not underflow in FP32.
+__device__ __forceinline__ float dens_value(int kind, int64_t a, double nk, float f, float r, float u0sq,
+                                            double xa, double mu, double sigma, double tlo, double thi,
+                                            float &u) {
+    if (kind == VUP_UNIFORM) {
+        u = 0.f;
+        double half = __dmul_rn(0.5, sigma);
+        double dx = fabs(__dsub_rn(xa, mu));
+        return dx <= half ? 1.f : 0.f;
+    }
+    float t = (float)((double)a - nk) - f;
+    u = t * r;
+    if (kind == VUP_TRUNCNORM && !(tlo <= xa && xa <= thi)) return 0.f;
+    return expf(-0.5f * ((u - sqrtf(u0sq)) * (u + sqrtf(u0sq))));
+}
+
+__global__ void k_density_prep(DensIn in, int64_t K, int64_t K_pad, int ndim, int64_t n0, int64_t n1,
+                               int64_t n2, double lo0, double lo1, double lo2, double h0, double h1,
+                               double h2, DensConst *__restrict__ dconst, DensStats *__restrict__ dstats,
+                               float *__restrict__ ftab, int *__restrict__ dstatus) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int d = blockIdx.y;
+    if (k >= K_pad) return;
+    const int64_t nd = d == 0 ? n0 : (d == 1 ? n1 : n2);
+    const double lo = d == 0 ? lo0 : (d == 1 ? lo1 : lo2);
+    const double h = d == 0 ? h0 : (d == 1 ? h1 : h2);
+    int64_t off = 0;
+    if (d >= 1) off += n0 * K_pad;
+    if (d >= 2) off += n1 * K_pad;
+    float *tab = ftab + off;
+    if (k >= K) {
+        for (int64_t a = 0; a < nd; ++a) tab[a * K_pad + k] = 0.f;
+        return;
+    }
+    const int64_t p = k * ndim + d;
+    const int kind = in.kind[p];
+    const double mu = in.mu[p], sigma = in.sigma[p];
+    const double tlo = in.lo ? in.lo[p] : 0.0, thi = in.hi ? in.hi[p] : 0.0;
+    // index coordinate of the mean: (mu - lo) / h - 1/2 = nk + f
+    const double c = (mu - lo) / h - 0.5;
+    const double nk = floor(c);
+    const float f = (float)(c - nk);
+    const float r = (float)(h / sigma);
+    // squared index-space distance from the mean to its nearest midpoint
+    double anear = floor(c + 0.5);
+    anear = fmin(fmax(anear, 0.0), (double)(nd - 1));
+    float t0 = (float)(anear - nk) - f;
+    float u0 = t0 * r;
+    float u0sq = kind == VUP_UNIFORM ? 0.f : u0 * u0;
+    if (!(u0sq < 1e30f)) u0sq = 0.f;
+    KSum S0, S1, S2;
+    for (int64_t a = 0; a < nd; ++a) {
+        double xa = 0.0;
+        if (kind != VUP_GAUSS) xa = __dadd_rn(lo, __dmul_rn((double)a + 0.5, h));
+        float u;
+        float g = dens_value(kind, a, nk, f, r, u0sq, xa, mu, sigma, tlo, thi, u);
+        tab[a * K_pad + k] = g;
+        S0.add(g);
+        S1.add(g * u);
+        S2.add(g * u * u);
+    }
+    DensConst dc;
+    dc.n = (int32_t)fmax(fmin(nk, 2147483647.0), -2147483647.0);
+    dc.f = f;
+    dc.r = r;
+    dc.kind = kind;
+    dconst[p] = dc;
+    const double Z = S0.value();
+    DensStats ds;
+    ds.invZ = Z > 0.0 ? 1.0 / Z : 0.0;
+    ds.Eu = Z > 0.0 ? S1.value() / Z : 0.0;
+    ds.Eu2 = Z > 0.0 ? S2.value() / Z : 0.0;
+    ds.inv_sigma = 1.0 / sigma;
+    dstats[p] = ds;
+    if (!(Z > 0.0)) atomicCAS(dstatus, 0, VUP_DSTAT_EMPTY);
+}
+
+// A-operand table of the tensor-core contraction: rows k, reduction index a
+// contiguous (K-major), each FP32 factor split into BF16 hi + lo.
+__global__ void k_split_transpose(const float *__restrict__ tab, int64_t nd, int64_t K_pad,
+                                  int64_t R_pad, __nv_bfloat16 *__restrict__ hi,
+                                  __nv_bfloat16 *__restrict__ lo) {
+    __shared__ float t[32][33];
+    const int64_t a0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        int64_t a = a0 + y, k = k0 + threadIdx.x;
+        t[y][threadIdx.x] = (a < nd && k < K_pad) ? tab[a * K_pad + k] : 0.f;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        int64_t k = k0 + y, a = a0 + threadIdx.x;
+        if (k < K_pad && a < R_pad) {
+            float v = t[threadIdx.x][y];
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            float rem = v - __bfloat162float(h);
+            hi[k * R_pad + a] = h;
+            lo[k * R_pad + a] = __float2bfloat16_rn(rem);
+        }
+    }
+}
+
+}  // namespace
+
+size_t vup_ftab_floats(const vup_grid g) {
+    size_t s = 0;
+    for (int d = 0; d < g->ndim; ++d) s += (size_t)g->n[d];
+    return s;
+}
+
+// need_bf16_orient_mask: bit o set -> build the split BF16 A table for the
+// reduction axis of orientation o.
+vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_orient_mask, cudaStream_t s) {
+    const int64_t K = d->K;
+    const int64_t K_pad = ceil_div64(K, 128) * 128;
+    DensIn in{d->kind, d->mu, d->sigma, d->lo, d->hi};
+    double h[3];
+    for (int q = 0; q < 3; ++q) h[q] = (g->hi[q] - g->lo[q]) / (double)g->n[q];
+    dim3 grd((unsigned)ceil_div64(K_pad, 128), (unsigned)g->ndim);
+    VUP_PROF("density_prep", s, 1 + __builtin_popcount(need_bf16_orient_mask));
+    k_density_prep<<<grd, 128, 0, s>>>(in, K, K_pad, g->ndim, g->n[0], g->n[1], g->n[2], g->lo[0], g->lo[1],
+                                       g->lo[2], h[0], h[1], h[2], (DensConst *)g->dconst.p,
+                                       (DensStats *)g->dstats.p, (float *)g->ftab.p, g->dstatus);
+    VUP_CHECK_LAUNCH();
+    for (int o = 0; o < 2; ++o) {
+        if (!(need_bf16_orient_mask & (1 << o))) continue;
+        const Orient &ori = g->orient[o];
+        const int dred = ori.red_axis0;
+        int64_t off = 0;
+        for (int q = 0; q < dred; ++q) off += g->n[q] * K_pad;
+        __nv_bfloat16 *hi = (__nv_bfloat16 *)g->atab_hi.p + (size_t)o * K_pad * ori.R_pad * 0;
+        __nv_bfloat16 *lo = (__nv_bfloat16 *)g->atab_lo.p;
+        if (o == 1) {
+            // orientation-1 tables live after the orientation-0 tables
+            const size_t o0 = (size_t)K_pad * g->orient[0].R_pad;
+            hi = (__nv_bfloat16 *)g->atab_hi.p + o0;
+            lo = (__nv_bfloat16 *)g->atab_lo.p + o0;
+        }
+        dim3 tg((unsigned)ceil_div64(ori.R_pad, 32), (unsigned)ceil_div64(K_pad, 32));
+        k_split_transpose<<<tg, dim3(32, 8), 0, s>>>((const float *)g->ftab.p + off, g->n[dred], K_pad, ori.R_pad,
+                                                     hi, lo);
+        VUP_CHECK_LAUNCH();
+    }
+    return VUP_OK;
+}

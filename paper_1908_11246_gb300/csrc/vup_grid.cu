@@ -1,0 +1,585 @@
+// Grid-side steps of the VUP hot path, run once per (grid, model):
+//   midpoint coordinates and model evaluation in FP64 (Sec. 2 model function,
+//   Sec. 3 composite midpoint rule), the exact output range, per-point bin ids
+//   (Eq. 4), a stable counting sort of the grid points by bin -- the CSR form
+//   of the one-hot model matrix of Eq. MUP -- the run/chunk structure the
+//   segmented histogram kernel walks, and the power tables (y/s)^j.
+#include "vup_internal.cuh"
+
+#include <math.h>
+
+#include <algorithm>
+
+namespace {
+
+constexpr int kSortTile = 2048;      // points per warp in the counting sort
+constexpr int kSortWarps = 4;        // warps per CTA in the counting sort
+constexpr uint32_t kRunEnd = 0x80000000u;
+
+struct Theta {
+    double t[8];
+};
+
+// Midpoint x_a = lo + (a + 1/2) h, with the product and sum rounded once each
+// (no fused multiply-add), exactly as the FP64 oracle computes it.
+__device__ __forceinline__ double grid_x(double lo, double h, int64_t a) {
+    double t = (double)a + 0.5;
+    return __dadd_rn(lo, __dmul_rn(t, h));
+}
+
+__device__ __forceinline__ double model_value(int model, const Theta &th, const double *x, int ndim) {
+    switch (model) {
+    case VUP_MODEL_SIN_QUAD_1D: {
+        double s = sin(x[0]);
+        double q = __dmul_rn(x[0], x[0]);
+        return __dadd_rn(__dmul_rn(th.t[0], s), __dmul_rn(th.t[1], q));
+    }
+    case VUP_MODEL_SIN_SIN2_2D: {
+        double s1 = sin(x[0]);
+        double s2 = sin(x[1]);
+        double q = __dmul_rn(s2, s2);
+        return __dadd_rn(__dmul_rn(th.t[0], s1), __dmul_rn(th.t[1], q));
+    }
+    case VUP_MODEL_MIXED_3D: {
+        double s1 = sin(x[0]);
+        double s2 = sin(x[1]);
+        double q = __dmul_rn(s2, s2);
+        double x2 = __dmul_rn(x[2], x[2]);
+        double x4 = __dmul_rn(x2, x2);
+        double b = __dmul_rn(th.t[0], q);
+        double c = __dmul_rn(th.t[1], x4);
+        double c2 = __dmul_rn(c, s1);
+        double r = __dadd_rn(s1, b);
+        return __dadd_rn(r, c2);
+    }
+    case VUP_MODEL_OSCILLATOR_2D: {
+        double w = x[0], z = x[1], T = th.t[0];
+        double zw = __dmul_rn(z, w);
+        double e = exp(-__dmul_rn(zw, T));
+        double om = __dsub_rn(1.0, __dmul_rn(z, z));
+        double wd = __dmul_rn(w, sqrt(om));
+        double c = cos(__dmul_rn(wd, T));
+        return __dmul_rn(e, c);
+    }
+    case VUP_MODEL_IPSA_EXAMPLE_2D: {
+        double q = __dmul_rn(x[0], x[0]);
+        double t = __dmul_rn(3.0, x[0]);
+        double s = __dmul_rn(5.0, sin(t));
+        double r = __dadd_rn(q, s);
+        return __dadd_rn(r, x[1]);
+    }
+    case VUP_MODEL_POLY: {
+        double r = th.t[0];
+        for (int d = 0; d < ndim; ++d) {
+            double a = __dmul_rn(th.t[1 + 2 * d], x[d]);
+            double q = __dmul_rn(x[d], x[d]);
+            double b = __dmul_rn(th.t[2 + 2 * d], q);
+            r = __dadd_rn(r, a);
+            r = __dadd_rn(r, b);
+        }
+        return r;
+    }
+    default:
+        return __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+struct GridGeom {
+    int ndim;
+    int64_t n[3];
+    double lo[3];
+    double h[3];
+};
+
+__global__ void k_model_eval(double *__restrict__ y, int64_t N, GridGeom G, int model, Theta th) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t rem = i;
+        double x[3];
+        for (int d = G.ndim - 1; d >= 0; --d) {
+            int64_t a = rem % G.n[d];
+            rem /= G.n[d];
+            x[d] = grid_x(G.lo[d], G.h[d], a);
+        }
+        y[i] = model_value(model, th, x, G.ndim);
+    }
+}
+
+// Order-preserving map of a double to an unsigned key (for exact atomic min/max).
+__device__ __forceinline__ unsigned long long dkey(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+    unsigned long long u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)u);
+}
+
+__global__ void k_minmax(const double *__restrict__ y, int64_t N, unsigned long long *ext) {
+    unsigned long long mn = ~0ull, mx = 0ull;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long k = dkey(y[i]);
+        mn = k < mn ? k : mn;
+        mx = k > mx ? k : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
+        unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+        mn = a < mn ? a : mn;
+        mx = b > mx ? b : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&ext[0], mn);
+        atomicMax(&ext[1], mx);
+    }
+}
+
+// Output range and the power-table scale s = max(|ymin|, |ymax|) (1 if 0).
+__device__ __forceinline__ void read_range(const unsigned long long *ext, double &ymin, double &ymax) {
+    ymin = dkey_inv(ext[0]);
+    ymax = dkey_inv(ext[1]);
+}
+
+__global__ void k_scale(const unsigned long long *ext, double *s_out) {
+    double ymin, ymax;
+    read_range(ext, ymin, ymax);
+    double s = fmax(fabs(ymin), fabs(ymax));
+    s_out[0] = s > 0.0 ? s : 1.0;
+}
+
+// Eq. 4 bins: t = (y - ymin) / (ymax - ymin), bin = min(floor(t B), B - 1),
+// every operation correctly rounded and unfused, as in the FP64 oracle.
+// Also counts points per (bin, warp tile) for the stable counting sort.
+__global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
+                             const unsigned long long *ext, int32_t *__restrict__ bins,
+                             int32_t *__restrict__ counts, int64_t n_tiles) {
+    extern __shared__ int32_t s_cnt[];  // [kSortWarps][B]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *cnt = s_cnt + warp * B;
+    for (int b = lane; b < B; b += 32) cnt[b] = 0;
+    __syncwarp();
+    const int64_t tile = (int64_t)blockIdx.x * kSortWarps + warp;
+    double ymin, ymax;
+    read_range(ext, ymin, ymax);
+    const double range = __dsub_rn(ymax, ymin);
+    if (tile < n_tiles) {
+        const int64_t i0 = tile * kSortTile;
+        const int64_t i1 = min(N, i0 + kSortTile);
+        for (int64_t i = i0 + lane; i < i1; i += 32) {
+            int32_t b = 0;
+            if (range > 0.0) {
+                double t = __ddiv_rn(__dsub_rn(y[i], ymin), range);
+                double f = floor(__dmul_rn(t, (double)B));
+                b = (int32_t)f;
+                b = b > B - 1 ? B - 1 : b;
+                b = b < 0 ? 0 : b;
+            }
+            bins[i] = b;
+            atomicAdd(&cnt[b], 1);
+        }
+        __syncwarp();
+        for (int b = lane; b < B; b += 32) counts[(int64_t)b * n_tiles + tile] = cnt[b];
+    }
+}
+
+// Stable scatter: each warp walks its tile in order, 32 points at a time;
+// equal bins inside a step are ranked by lane with __match_any_sync.
+__global__ void k_sort_scatter(const int32_t *__restrict__ bins, int64_t N, int B,
+                               const int32_t *__restrict__ starts, int64_t n_tiles,
+                               int32_t *__restrict__ perm) {
+    extern __shared__ int32_t s_cnt[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *cnt = s_cnt + warp * B;
+    const int64_t tile = (int64_t)blockIdx.x * kSortWarps + warp;
+    if (tile >= n_tiles) return;
+    for (int b = lane; b < B; b += 32) cnt[b] = starts[(int64_t)b * n_tiles + tile];
+    __syncwarp();
+    const int64_t i0 = tile * kSortTile;
+    const int64_t i1 = min(N, i0 + kSortTile);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t base = i0; base < i1; base += 32) {
+        const int64_t i = base + lane;
+        const bool v = i < i1;
+        const unsigned act = __ballot_sync(0xffffffffu, v);
+        int32_t b = v ? bins[i] : -1;
+        unsigned peers = __match_any_sync(0xffffffffu, b);
+        peers &= act;
+        int32_t pos = 0;
+        if (v) {
+            pos = cnt[b] + __popc(peers & lt);
+            perm[pos] = (int32_t)i;
+        }
+        __syncwarp();
+        if (v && (peers & lt) == 0) cnt[b] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+// ---- exclusive scan of int32 (three-phase, deterministic) ----------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *s_warp, int32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    int32_t warp_off = warp > 0 ? s_warp[warp - 1] : 0;
+    total = s_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_off + x - v;
+}
+
+__global__ void k_scan_blocks(const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t L,
+                              int32_t *__restrict__ block_sums) {
+    __shared__ int32_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int32_t tsum = 0;
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = base + j < L ? in[base + j] : 0;
+        tsum += v[j];
+    }
+    int32_t total;
+    int32_t off = block_excl_scan(tsum, s_warp, total);
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < L) out[base + j] = off;
+        off += v[j];
+    }
+    if (threadIdx.x == 0 && block_sums) block_sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(int32_t *__restrict__ out, int64_t L, const int32_t *__restrict__ block_off) {
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    const int32_t add = block_off[blockIdx.x];
+    for (int j = threadIdx.x; j < kScanBlock; j += blockDim.x)
+        if (base + j < L) out[base + j] += add;
+}
+
+// ---- runs and chunks for the segmented histogram --------------------------
+// A run is a maximal stretch of sorted points sharing the output bin and every
+// axis index but the last one.  hpt[t] packs the last-axis index of the t-th
+// sorted point (bits 0..15) and a run-end flag (bit 31).
+__global__ void k_run_flags(const int32_t *__restrict__ perm, const int32_t *__restrict__ bins,
+                            int64_t N, int64_t n_last, int32_t *__restrict__ flags) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int32_t f = 1;
+        if (t > 0) {
+            int32_t i = perm[t], ip = perm[t - 1];
+            f = (bins[i] != bins[ip]) || (i / n_last != ip / n_last);
+        }
+        flags[t] = f;
+    }
+}
+
+__global__ void k_run_build(const int32_t *__restrict__ perm, const int32_t *__restrict__ bins,
+                            int64_t N, int64_t n_last, const int32_t *__restrict__ flags,
+                            const int32_t *__restrict__ excl, int32_t *__restrict__ run_start,
+                            int32_t *__restrict__ run_rest, int32_t *__restrict__ run_bin,
+                            uint32_t *__restrict__ hpt, int32_t *__restrict__ n_runs) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = perm[t];
+        const int32_t rid = excl[t] + flags[t] - 1;
+        if (flags[t]) {
+            run_start[rid] = (int32_t)t;
+            run_rest[rid] = (int32_t)(i / n_last);
+            run_bin[rid] = bins[i];
+        }
+        const bool last = (t == N - 1) || flags[t + 1];
+        hpt[t] = (uint32_t)(i % n_last) | (last ? kRunEnd : 0u);
+        if (t == N - 1) {
+            n_runs[0] = rid + 1;
+            run_start[rid + 1] = (int32_t)N;
+        }
+    }
+}
+
+// Chunk c starts at the first run whose first point is >= c N / C.
+__global__ void k_chunks(const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_bin,
+                         const int32_t *__restrict__ n_runs_p, int64_t N, int C,
+                         int32_t *__restrict__ chunk_pt, int32_t *__restrict__ chunk_run) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > C) return;
+    const int32_t n_runs = n_runs_p[0];
+    int32_t r;
+    if (c == C) {
+        r = n_runs;
+    } else {
+        const int64_t target = (N * (int64_t)c) / C;
+        int32_t lo = 0, hi = n_runs;  // first r in [0, n_runs] with run_start[r] >= target
+        while (lo < hi) {
+            int32_t mid = (lo + hi) >> 1;
+            if (run_start[mid] >= target) hi = mid; else lo = mid + 1;
+        }
+        r = lo;
+    }
+    chunk_run[c] = r;
+    chunk_pt[c] = run_start[r];
+}
+
+__global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
+
+__global__ void k_chunk_bins(const int32_t *__restrict__ chunk_run, const int32_t *__restrict__ run_bin,
+                             int C, int32_t *__restrict__ chunk_bin) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const int32_t r0 = chunk_run[c], r1 = chunk_run[c + 1];
+    chunk_bin[2 * c] = r1 > r0 ? run_bin[r0] : -1;
+    chunk_bin[2 * c + 1] = r1 > r0 ? run_bin[r1 - 1] : -1;
+}
+
+// ---- power tables -----------------------------------------------------------
+// y viewed as a matrix Y[P][S] (flat i = p S + s).  Element (p, s) yields
+// z = y / s_scale and its powers z^j, j = 1..4 (FP64, then rounded).
+// mode 0: out[(p*4 + j) * ld + s]      (rows (p, j), cols s)
+// mode 1: out[s * ld + p*4 + j]        (rows s, cols (p, j))
+// mode 2: out[(s*4 + j) * ld + p]      (rows (s, j), cols p)
+// mode 3: out[p * ld + s*4 + j]        (rows p, cols (s, j))
+// A 32 x 32 (p, s) tile goes through shared memory so that both the read of y
+// and the write of the table are coalesced whatever the mode.
+template <typename T>
+struct Store;
+template <>
+struct Store<float> {
+    static __device__ __forceinline__ void put(float *o, float * /*o2*/, int64_t idx, double v) {
+        o[idx] = (float)v;
+    }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ void put(__nv_bfloat16 *o, __nv_bfloat16 *o2, int64_t idx, double v) {
+        __nv_bfloat16 h = __double2bfloat16(v);
+        double r = v - (double)__bfloat162float(h);
+        o[idx] = h;
+        o2[idx] = __double2bfloat16(r);
+    }
+};
+
+template <typename T>
+__global__ void k_power_table(const double *__restrict__ y, int64_t P, int64_t S,
+                              const double *__restrict__ sc, int mode, int64_t ld,
+                              T *__restrict__ out, T *__restrict__ out2) {
+    __shared__ double tile[32][33];
+    const int64_t p0 = (int64_t)blockIdx.y * 32, s0 = (int64_t)blockIdx.x * 32;
+    const double scale = sc[0];
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int64_t p = p0 + r, s = s0 + threadIdx.x;
+        double z = 0.0;
+        if (p < P && s < S) z = __ddiv_rn(y[p * S + s], scale);
+        tile[r][threadIdx.x] = z;
+    }
+    __syncthreads();
+    // 32 x 32 x 4 values; thread t handles values linear in the output order
+    const int tid = threadIdx.y * 32 + threadIdx.x, nthr = 32 * blockDim.y;
+    for (int e = tid; e < 32 * 32 * 4; e += nthr) {
+        int a, b, j;  // a = fast output coordinate within the tile
+        int lp, ls;
+        int64_t idx;
+        switch (mode) {
+        case 0: {  // rows (p, j), cols s : fast = s
+            ls = e & 31; j = (e >> 5) & 3; lp = e >> 7;
+            idx = ((p0 + lp) * 4 + j) * ld + (s0 + ls);
+            break;
+        }
+        case 1: {  // rows s, cols (p, j) : fast = (p, j)
+            j = e & 3; lp = (e >> 2) & 31; ls = e >> 7;
+            idx = (s0 + ls) * ld + (p0 + lp) * 4 + j;
+            break;
+        }
+        case 2: {  // rows (s, j), cols p : fast = p
+            lp = e & 31; j = (e >> 5) & 3; ls = e >> 7;
+            idx = ((s0 + ls) * 4 + j) * ld + (p0 + lp);
+            break;
+        }
+        default: {  // rows p, cols (s, j) : fast = (s, j)
+            j = e & 3; ls = (e >> 2) & 31; lp = e >> 7;
+            idx = (p0 + lp) * ld + (s0 + ls) * 4 + j;
+            break;
+        }
+        }
+        (void)a; (void)b;
+        if (p0 + lp >= P || s0 + ls >= S) continue;
+        double z = tile[lp][ls];
+        double v = z;
+        for (int q = 0; q < j; ++q) v = v * z;
+        Store<T>::put(out, out2, idx, v);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+// Exclusive scan of L int32 values; `scratch` holds the per-level block sums
+// (scan_scratch_ints(L) entries).
+static int64_t scan_scratch_ints(int64_t L) {
+    int64_t total = 0;
+    for (int64_t nb = ceil_div64(L, kScanBlock); nb > 1; nb = ceil_div64(nb, kScanBlock))
+        total += 2 * nb + 64;
+    return total + 64;
+}
+
+static vup_status scan_exclusive(const int32_t *in, int32_t *out, int64_t L, int32_t *scratch,
+                                 cudaStream_t s) {
+    const int64_t nb = ceil_div64(L, kScanBlock);
+    if (nb <= 1) {
+        k_scan_blocks<<<1, kScanThreads, 0, s>>>(in, out, L, nullptr);
+        VUP_CHECK_LAUNCH();
+        return VUP_OK;
+    }
+    int32_t *sums = scratch;
+    int32_t *sums_scan = scratch + nb + 32;
+    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, L, sums);
+    VUP_CHECK_LAUNCH();
+    vup_status st = scan_exclusive(sums, sums_scan, nb, scratch + 2 * nb + 64, s);
+    if (st != VUP_OK) return st;
+    k_scan_add<<<(unsigned)nb, 256, 0, s>>>(out, L, sums_scan);
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}
+
+static GridGeom geom_of(vup_grid g) {
+    GridGeom G;
+    G.ndim = g->ndim;
+    for (int d = 0; d < 3; ++d) {
+        G.n[d] = g->n[d];
+        G.lo[d] = g->lo[d];
+        G.h[d] = (g->hi[d] - g->lo[d]) / (double)g->n[d];
+    }
+    return G;
+}
+
+vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta, cudaStream_t s) {
+    Theta th;
+    for (int q = 0; q < 8; ++q) th.t[q] = theta[q];
+    GridGeom G = geom_of(g);
+    int blocks = (int)std::min<int64_t>(ceil_div64(g->N, 256), (int64_t)vup_num_sms() * 16);
+    VUP_PROF("model_eval", s, 1);
+    k_model_eval<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th);
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}
+
+int vup_hist_chunks_for(int64_t N);
+
+vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
+    const int64_t N = g->N;
+    const int B = g->B;
+    // range, bins, sort (+2 scans of up to 3 launches), runs, chunks
+    VUP_PROF("range_bins_sort_runs", s, g->ndim >= 2 ? 16 : 8);
+    // exact range of y
+    VUP_CHECK_CUDA(cudaMemsetAsync(g->ext, 0xff, sizeof(unsigned long long), s));
+    VUP_CHECK_CUDA(cudaMemsetAsync(g->ext + 1, 0x00, sizeof(unsigned long long), s));
+    int blocks = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
+    k_minmax<<<blocks, 256, 0, s>>>(g->y, N, g->ext);
+    VUP_CHECK_LAUNCH();
+    k_scale<<<1, 1, 0, s>>>(g->ext, g->ydev_scale);
+    VUP_CHECK_LAUNCH();
+
+    // bins + stable counting sort
+    const int64_t n_tiles = ceil_div64(N, kSortTile);
+    const int64_t L = (int64_t)B * n_tiles;
+    vup_status st = devbuf_reserve(g->sort_counts,
+                                   sizeof(int32_t) * (size_t)std::max<int64_t>(2 * L + 8, N + 8));
+    if (st != VUP_OK) return st;
+    st = devbuf_reserve(g->scan_tmp, sizeof(int32_t) * (size_t)scan_scratch_ints(std::max<int64_t>(L, N)));
+    if (st != VUP_OK) return st;
+    int32_t *scratch = (int32_t *)g->scan_tmp.p;
+    int32_t *counts = (int32_t *)g->sort_counts.p;
+    int32_t *starts = counts + L + 4;
+    const size_t smem = sizeof(int32_t) * (size_t)B * kSortWarps;
+    const unsigned sblocks = (unsigned)ceil_div64(n_tiles, kSortWarps);
+    if (smem > 48 * 1024) {
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_bins_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    k_bins_count<<<sblocks, 32 * kSortWarps, smem, s>>>(g->y, N, B, g->ext, g->bins, counts, n_tiles);
+    VUP_CHECK_LAUNCH();
+    st = scan_exclusive(counts, starts, L, scratch, s);
+    if (st != VUP_OK) return st;
+    k_sort_scatter<<<sblocks, 32 * kSortWarps, smem, s>>>(g->bins, N, B, starts, n_tiles, g->perm);
+    VUP_CHECK_LAUNCH();
+    // offsets[b] = starts[b * n_tiles], offsets[B] = N
+    VUP_CHECK_CUDA(cudaMemcpy2DAsync(g->offsets, sizeof(int32_t), starts, sizeof(int32_t) * n_tiles,
+                                     sizeof(int32_t), B, cudaMemcpyDeviceToDevice, s));
+    k_set_i32<<<1, 1, 0, s>>>(g->offsets + B, (int32_t)N);
+    VUP_CHECK_LAUNCH();
+
+    // runs and chunks (2-D and 3-D grids; 1-D uses bins directly)
+    if (g->ndim >= 2) {
+        const int64_t n_last = g->n[g->ndim - 1];
+        int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
+        k_run_flags<<<rb, 256, 0, s>>>(g->perm, g->bins, N, n_last, g->flags_scan);
+        VUP_CHECK_LAUNCH();
+        // the sort counts are dead once the offsets are copied: reuse them
+        int32_t *excl = (int32_t *)g->sort_counts.p;
+        st = scan_exclusive(g->flags_scan, excl, N, scratch, s);
+        if (st != VUP_OK) return st;
+        k_run_build<<<rb, 256, 0, s>>>(g->perm, g->bins, N, n_last, g->flags_scan, excl, g->run_start,
+                                       g->run_rest, g->run_bin, g->hpt, g->n_runs);
+        VUP_CHECK_LAUNCH();
+        const int C = g->n_chunks;
+        k_chunks<<<(C + 1 + 127) / 128, 128, 0, s>>>(g->run_start, g->run_bin, g->n_runs, N, C,
+                                                      g->chunk_pt, g->chunk_run);
+        VUP_CHECK_LAUNCH();
+        k_chunk_bins<<<(C + 127) / 128, 128, 0, s>>>(g->chunk_run, g->run_bin, C, g->chunk_bin);
+        VUP_CHECK_LAUNCH();
+    }
+    g->have_tab[0][0] = g->have_tab[0][1] = g->have_tab[1][0] = g->have_tab[1][1] = 0;
+    return VUP_OK;
+}
+
+// Build (lazily) the power tables of orientation `orient` in FP32 (SIMT
+// layout [R][NC]) or split BF16 (tensor layout [NC][R_pad]).
+vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
+    if (g->have_tab[orient][bf16]) return VUP_OK;
+    const Orient &o = g->orient[orient];
+    // View y as [P][S]: orientation 0 -> P = rest (Q), S = red (R);
+    // orientation 1 (2-D) -> P = axis 0 = red, S = axis 1 = rest.
+    const int64_t P = orient == 0 ? o.Q : o.R;
+    const int64_t S = orient == 0 ? o.R : o.Q;
+    dim3 blk(32, 8), grd((unsigned)ceil_div64(S, 32), (unsigned)ceil_div64(P, 32));
+    VUP_PROF(bf16 ? "power_table_bf16" : "power_table_fp32", s, 1);
+    if (!bf16) {
+        const int64_t ld = ceil_div64(o.NC, 128) * 128;
+        const size_t bytes = sizeof(float) * (size_t)ld * (size_t)o.R;
+        if (!g->zs[orient]) VUP_CHECK_CUDA(cudaMalloc(&g->zs[orient], bytes));
+        VUP_CHECK_CUDA(cudaMemsetAsync(g->zs[orient], 0, bytes, s));
+        // SIMT wants [r][q*4+j]: orientation 0 -> rows s (mode 1); 1 -> rows p (mode 3)
+        k_power_table<float><<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, orient == 0 ? 1 : 3, ld,
+                                                 g->zs[orient], nullptr);
+        VUP_CHECK_LAUNCH();
+    } else {
+        const int64_t ld = o.R_pad;
+        const int64_t rows = ceil_div64(o.NC, 256) * 256;
+        const size_t bytes = sizeof(__nv_bfloat16) * (size_t)ld * (size_t)rows;
+        if (!g->zt_hi[orient]) {
+            VUP_CHECK_CUDA(cudaMalloc(&g->zt_hi[orient], bytes));
+            VUP_CHECK_CUDA(cudaMalloc(&g->zt_lo[orient], bytes));
+        }
+        VUP_CHECK_CUDA(cudaMemsetAsync(g->zt_hi[orient], 0, bytes, s));
+        VUP_CHECK_CUDA(cudaMemsetAsync(g->zt_lo[orient], 0, bytes, s));
+        // tensor wants [q*4+j][r]: orientation 0 -> rows (p, j) (mode 0); 1 -> rows (s, j) (mode 2)
+        k_power_table<__nv_bfloat16><<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, orient == 0 ? 0 : 2, ld,
+                                                         g->zt_hi[orient], g->zt_lo[orient]);
+        VUP_CHECK_LAUNCH();
+    }
+    g->have_tab[orient][bf16] = 1;
+    return VUP_OK;
+}

@@ -1,0 +1,162 @@
+// Internal declarations shared by the libvup CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "vup.h"
+
+#define VUP_CHECK_CUDA(expr)                                                  \
+    do {                                                                      \
+        cudaError_t _e = (expr);                                              \
+        if (_e != cudaSuccess) {                                              \
+            vup_set_last_cuda_error(_e, #expr, __FILE__, __LINE__);           \
+            return _e == cudaErrorMemoryAllocation ? VUP_ERR_OOM : VUP_ERR_CUDA; \
+        }                                                                     \
+    } while (0)
+
+#define VUP_CHECK_LAUNCH() VUP_CHECK_CUDA(cudaGetLastError())
+
+void vup_set_last_cuda_error(cudaError_t e, const char *expr, const char *file, int line);
+
+// Device status word codes (grid->dstatus[0]); the first non-zero code wins.
+enum { VUP_DSTAT_OK = 0, VUP_DSTAT_EMPTY = 5, VUP_DSTAT_TIMEOUT = 6 };
+
+// Per-(k, axis) density constants written by the density-prep kernel.
+//   Gaussian / truncated normal, index space: the midpoint index of mu is
+//   c = (mu - lo) / h - 1/2 = n + f with integer n and f in [0, 1); the
+//   density at midpoint a is exp(-((a - n) - f)^2 r^2 / 2) with r = h / sigma.
+struct DensConst {
+    int32_t n;      // integer part of the mean's index coordinate
+    float f;        // fractional part
+    float r;        // h / sigma
+    int32_t kind;   // vup_density_kind
+};
+
+// Per-(k, axis) normalisation statistics (FP64).
+struct DensStats {
+    double invZ;    // 1 / sum_a g(a)
+    double Eu;      // sum_a g u / sum_a g,   u = ((a - n) - f) r
+    double Eu2;     // sum_a g u^2 / sum_a g
+    double inv_sigma;
+};
+
+// Capacity-tracked device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+vup_status devbuf_reserve(DevBuf &b, size_t bytes);
+void devbuf_free(DevBuf &b);
+
+// Layout of the contraction for one orientation of a grid.
+//   red  : the reduction axes (flat index r), contiguous in y
+//   rest : the remaining axes (flat index q), columns c = q * J + j
+struct Orient {
+    int red_axis0;      // first reduction axis
+    int64_t R;          // reduction length
+    int64_t R_pad;      // padded to a multiple of 64
+    int64_t Q;          // number of rest points
+    int64_t NC;         // Q * J
+    int rest_axes[2];   // rest axes (up to 2), -1 if unused
+    int n_rest_axes;
+};
+
+struct vup_grid_s {
+    int device = 0;
+    int ndim = 0;
+    int64_t n[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    int64_t N = 0;
+
+    // model outputs
+    int have_model = 0;
+    int B = 0, J = 0;
+    double host_ext[3] = {0, 0, 1};  // ymin, ymax, s (filled lazily by vup_grid_info)
+
+    double *y = nullptr;           // [N]
+    unsigned long long *ext = nullptr;  // [2] ordered-bits min / max of y
+    int32_t *bins = nullptr;       // [N]
+    int32_t *perm = nullptr;       // [N] sorted position -> flat index
+    int32_t *offsets = nullptr;    // [B_cap + 1]
+    int32_t B_cap = 0;
+
+    // counting-sort scratch
+    DevBuf sort_counts, scan_tmp;
+
+    // histogram point stream (sorted order), runs and chunks
+    uint32_t *hpt = nullptr;       // [N] packed per-point word
+    int32_t *run_start = nullptr;  // [N + 1]
+    int32_t *run_rest = nullptr;   // [N]
+    int32_t *run_bin = nullptr;    // [N]
+    int32_t *n_runs = nullptr;     // [1] device
+    int32_t *flags_scan = nullptr; // [N] scratch
+    int32_t n_chunks = 0;
+    int32_t *chunk_pt = nullptr;   // [n_chunks + 1] chunk start (point index)
+    int32_t *chunk_run = nullptr;  // [n_chunks + 1] chunk start (run index)
+    int32_t *chunk_bin = nullptr;  // [n_chunks * 2] first / last bin of each chunk
+
+    // power tables; orientation 0 = reduce over the last axis,
+    // orientation 1 = reduce over axis 0 (2-D only, for the IPSA adjoint)
+    Orient orient[2];
+    int have_tab[2][2] = {{0, 0}, {0, 0}};  // [orient][0: fp32, 1: bf16]
+    float *zs[2] = {nullptr, nullptr};          // SIMT layout [R][NC]
+    __nv_bfloat16 *zt_hi[2] = {nullptr, nullptr};  // tensor layout [NC][R_pad]
+    __nv_bfloat16 *zt_lo[2] = {nullptr, nullptr};
+    double *ydev_scale = nullptr;  // [1] s on device
+
+    // per-K scratch (density constants, factor tables, partials)
+    int64_t K_cap = 0;
+    DevBuf dconst, dstats, ftab, atab_hi, atab_lo, partials, hist_part, ipsa_part;
+
+    int *dstatus = nullptr;        // [1] device status word
+};
+
+// ---- kernels / launchers implemented in the .cu files -------------------
+vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta,
+                                 cudaStream_t s);
+vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s);  // range, bins, sort, runs, tables
+vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s);
+
+vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_orient_mask,
+                            cudaStream_t s);
+vup_status vup_moments_simt(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s);
+vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s);
+vup_status vup_moments_finish(vup_grid g, int64_t K, int n_col_tiles, double *raw,
+                              double *central, cudaStream_t s);
+vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s);
+vup_status vup_propagate_1d(vup_grid g, const vup_densities *d, double *raw, double *central,
+                            float *hist, cudaStream_t s);
+vup_status vup_ipsa_1d(vup_grid g, const vup_densities *d, const double *grad, float *dmu,
+                       float *dsg, cudaStream_t s);
+vup_status vup_ipsa_finish(vup_grid g, int64_t K, int n_tiles0, int n_tiles1,
+                           const double *grad, float *dmu, float *dsg, cudaStream_t s);
+vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, float *hist,
+                            cudaStream_t s);
+
+int vup_num_sms();
+
+// Per-kernel timing scope (active only while vup_profile(1) is in effect):
+// records a CUDA event pair on `s` around the launches made in its lifetime.
+struct ProfScope {
+    ProfScope(const char *name, cudaStream_t s, int launches = 1);
+    ~ProfScope();
+    const char *name;
+    cudaStream_t stream;
+    int launches;
+    int slot;
+};
+#define VUP_PROF_CAT2(a, b) a##b
+#define VUP_PROF_CAT(a, b) VUP_PROF_CAT2(a, b)
+#define VUP_PROF(name, s, n) ProfScope VUP_PROF_CAT(_vup_prof_, __LINE__)(name, s, n)
+
+// Column-tile counts used by the contraction kernels (for the finish step).
+int64_t vup_simt_col_tiles(const Orient &o);
+int64_t vup_tc_col_tiles(const Orient &o);
+
+// Scratch sizes per K row.
+size_t vup_ftab_floats(const vup_grid g);   // sum_d n[d] floats per k
+
+static inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -1,0 +1,316 @@
+// Moment contraction on CUDA cores in FP32 (the plain FP32 GPU path), and the
+// FP64 epilogues shared with the tensor-core path.
+//
+// For a tensor-product grid with product densities the moments factor:
+//   M[k, j] = sum_q g_rest(k, q) sum_r g_red(k, r) Z_j[q, r] / (Z_rest Z_red)
+// where r runs over the reduction axis (contiguous in y) and q over the rest.
+// The inner sum is a GEMM  T[k, (q, j)] = sum_r A[k, r] B[r, (q, j)]  with
+// A = g_red (K x R) and B = the power table (R x 4Q); the epilogue contracts
+// T with g_rest on the fly.  W itself (K x N) never exists.  Output moments
+// of Eq. VUP's output probability matrix (Fig. 4c expectation fields).
+#include "vup_internal.cuh"
+
+#include <math.h>
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 16;
+
+struct EpiArgs {
+    const float *g_rest0;   // factor table of the first rest axis  [n][K_pad]
+    const float *g_rest1;   // second rest axis (3-D) or nullptr
+    int64_t n_rest1;        // size of the second rest axis (1 if none)
+    int64_t Q;              // number of rest points
+    const DensConst *dconst;  // for IPSA weights of the rest axis
+    int ndim;
+    int rest_axis;          // axis index of the (single) rest axis for IPSA
+};
+
+template <int NOUT>
+__global__ void __launch_bounds__(256, NOUT == 1 ? 2 : 1)
+k_moments_simt(const float *__restrict__ A, const float *__restrict__ Zt, int64_t R, int64_t K_pad,
+               int64_t ldz, EpiArgs ep, int64_t n_ct, float *__restrict__ part) {
+    __shared__ __align__(16) float As[2][BK][BM];
+    __shared__ __align__(16) float Bs[2][BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t ct = blockIdx.x;         // column tile
+    const int64_t k0 = (int64_t)blockIdx.y * BM;
+    const int64_t c0 = ct * BN;
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    float4 ra[2], rb[2];
+    auto load_regs = [&](int64_t r0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = tid + h * 256;
+            const int row = e >> 5, c4 = e & 31;
+            const int64_t r = r0 + row;
+            if (r < R) {
+                ra[h] = *reinterpret_cast<const float4 *>(A + r * K_pad + k0 + c4 * 4);
+                rb[h] = *reinterpret_cast<const float4 *>(Zt + r * ldz + c0 + c4 * 4);
+            } else {
+                ra[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+                rb[h] = ra[h];
+            }
+        }
+    };
+    auto store_smem = [&](int buf) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = tid + h * 256;
+            const int row = e >> 5, c4 = e & 31;
+            *reinterpret_cast<float4 *>(&As[buf][row][c4 * 4]) = ra[h];
+            *reinterpret_cast<float4 *>(&Bs[buf][row][c4 * 4]) = rb[h];
+        }
+    };
+
+    const int64_t n_rt = (R + BK - 1) / BK;
+    load_regs(0);
+    store_smem(0);
+    __syncthreads();
+    for (int64_t rt = 0; rt < n_rt; ++rt) {
+        const int buf = rt & 1;
+        if (rt + 1 < n_rt) load_regs((rt + 1) * BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[8], b[8];
+            *reinterpret_cast<float4 *>(&a[0]) = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+            *reinterpret_cast<float4 *>(&a[4]) = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+            *reinterpret_cast<float4 *>(&b[0]) = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+            *reinterpret_cast<float4 *>(&b[4]) = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (rt + 1 < n_rt) {
+            store_smem(buf ^ 1);
+        }
+        __syncthreads();
+    }
+
+    // epilogue: contract with the rest-axis factors (and IPSA weights)
+    float out[NOUT][8][4];
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) out[o][i][j] = 0.f;
+#pragma unroll
+    for (int gq = 0; gq < 2; ++gq) {
+        const int64_t q = c0 / 4 + gq * 16 + tx;
+        const bool qok = q < ep.Q;
+        int64_t qa = q, qb = 0;
+        if (ep.g_rest1) {
+            qa = q / ep.n_rest1;
+            qb = q - qa * ep.n_rest1;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t k = k0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+            float e = 0.f;
+            if (qok) {
+                e = ep.g_rest0[qa * K_pad + k];
+                if (ep.g_rest1) e *= ep.g_rest1[qb * K_pad + k];
+            }
+            float w[NOUT];
+            w[0] = e;
+            if (NOUT == 3) {
+                const DensConst dc = ep.dconst[k * ep.ndim + ep.rest_axis];
+                const float t = (float)(q - dc.n) - dc.f;
+                const float u = t * dc.r;
+                w[NOUT == 3 ? 1 : 0] = e * u;
+                w[NOUT == 3 ? 2 : 0] = e * u * u;
+            }
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) out[o][i][j] = fmaf(w[o], acc[i][gq * 4 + j], out[o][i][j]);
+        }
+    }
+    // reduce over the 16 column threads of a half-warp
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float v = out[o][i][j];
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                out[o][i][j] = v;
+            }
+    if (tx == 0) {
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t k = k0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+                *reinterpret_cast<float4 *>(part + (((int64_t)o * n_ct + ct) * K_pad + k) * 4) =
+                    make_float4(out[o][i][0], out[o][i][1], out[o][i][2], out[o][i][3]);
+            }
+    }
+}
+
+// Sum the per-column-tile partials in FP64, undo the normalisation and the
+// power-table scale, and form central moments about the mean.
+__global__ void k_moments_finish(const float *__restrict__ part, int64_t n_ct, int64_t K, int64_t K_pad, int J,
+                                 const DensStats *__restrict__ ds, int ndim, const double *__restrict__ scale,
+                                 double *__restrict__ raw, double *__restrict__ central) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double mz[4] = {0, 0, 0, 0};
+    for (int64_t t = 0; t < n_ct; ++t) {
+        const float4 v = *reinterpret_cast<const float4 *>(part + (t * K_pad + k) * 4);
+        mz[0] += v.x; mz[1] += v.y; mz[2] += v.z; mz[3] += v.w;
+    }
+    double invZ = 1.0;
+    for (int d = 0; d < ndim; ++d) invZ *= ds[k * ndim + d].invZ;
+    const double s = scale[0];
+    double M[4];
+    double sp = s;
+    for (int j = 0; j < 4; ++j) {
+        M[j] = mz[j] * invZ * sp;
+        sp *= s;
+    }
+    if (raw)
+        for (int j = 0; j < J; ++j) raw[k * J + j] = M[j];
+    if (central) {
+        const double m = M[0];
+        double c[4];
+        c[0] = m;
+        c[1] = M[1] - m * m;
+        c[2] = M[2] - 3.0 * m * M[1] + 2.0 * m * m * m;
+        c[3] = M[3] - 4.0 * m * M[2] + 6.0 * m * m * M[1] - 3.0 * m * m * m * m;
+        for (int j = 0; j < J; ++j) central[k * J + j] = c[j];
+    }
+}
+
+// IPSA combine.  With u_d = (x_d - mu_d) / sigma_d and W = g / sum g,
+//   dM_j/dmu_d    = s^j / sigma_d (sum_i W u_d z^j   - E_d[u]   Mz_j)
+//   dM_j/dsigma_d = s^j / sigma_d (sum_i W u_d^2 z^j - E_d[u^2] Mz_j)
+// part0 holds orientation 0 (rest = axis 0): [w, w u_0, w u_0^2] partials,
+// part1 orientation 1 (rest = axis 1, 2-D only).
+__global__ void k_ipsa_finish(const float *__restrict__ part0, int64_t nct0, const float *__restrict__ part1,
+                              int64_t nct1, int64_t K, int64_t K_pad, int J, const DensStats *__restrict__ ds,
+                              const DensConst *__restrict__ dc, int ndim, const double *__restrict__ scale,
+                              const double *__restrict__ grad, float *__restrict__ dmu,
+                              float *__restrict__ dsg) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double invZ = 1.0;
+    for (int d = 0; d < ndim; ++d) invZ *= ds[k * ndim + d].invZ;
+    const double s = scale[0];
+    double S[2][3][4];
+    for (int o = 0; o < 2; ++o)
+        for (int w = 0; w < 3; ++w)
+            for (int j = 0; j < 4; ++j) S[o][w][j] = 0.0;
+    for (int o = 0; o < ndim; ++o) {
+        const float *part = o == 0 ? part0 : part1;
+        const int64_t nct = o == 0 ? nct0 : nct1;
+        for (int w = 0; w < 3; ++w)
+            for (int64_t t = 0; t < nct; ++t) {
+                const float4 v = *reinterpret_cast<const float4 *>(part + ((w * nct + t) * K_pad + k) * 4);
+                S[o][w][0] += v.x; S[o][w][1] += v.y; S[o][w][2] += v.z; S[o][w][3] += v.w;
+            }
+    }
+    for (int d = 0; d < ndim; ++d) {
+        const DensStats st = ds[k * ndim + d];
+        const bool diff = dc[k * ndim + d].kind != VUP_UNIFORM;
+        double gm = 0.0, gs = 0.0;
+        double sp = s;
+        for (int j = 0; j < J; ++j) {
+            const double Mz = S[0][0][j] * invZ;
+            const double Su = S[d][1][j] * invZ;
+            const double Su2 = S[d][2][j] * invZ;
+            double dm = diff ? sp * st.inv_sigma * (Su - st.Eu * Mz) : 0.0;
+            double dsd = diff ? sp * st.inv_sigma * (Su2 - st.Eu2 * Mz) : 0.0;
+            sp *= s;
+            if (grad) {
+                gm += grad[k * J + j] * dm;
+                gs += grad[k * J + j] * dsd;
+            } else {
+                dmu[(k * ndim + d) * J + j] = (float)dm;
+                dsg[(k * ndim + d) * J + j] = (float)dsd;
+            }
+        }
+        if (grad) {
+            dmu[k * ndim + d] = (float)gm;
+            dsg[k * ndim + d] = (float)gs;
+        }
+    }
+}
+
+}  // namespace
+
+int64_t vup_simt_col_tiles(const Orient &o) { return ceil_div64(o.NC, BN); }
+
+static EpiArgs epi_for(vup_grid g, int orient, int64_t K_pad) {
+    const Orient &o = g->orient[orient];
+    EpiArgs ep{};
+    auto tab = [&](int axis) {
+        int64_t off = 0;
+        for (int q = 0; q < axis; ++q) off += g->n[q] * K_pad;
+        return (const float *)g->ftab.p + off;
+    };
+    ep.g_rest0 = tab(o.rest_axes[0]);
+    ep.g_rest1 = o.n_rest_axes > 1 ? tab(o.rest_axes[1]) : nullptr;
+    ep.n_rest1 = o.n_rest_axes > 1 ? g->n[o.rest_axes[1]] : 1;
+    ep.Q = o.Q;
+    ep.dconst = (const DensConst *)g->dconst.p;
+    ep.ndim = g->ndim;
+    ep.rest_axis = o.rest_axes[0];
+    return ep;
+}
+
+vup_status vup_moments_simt(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s) {
+    const Orient &o = g->orient[orient];
+    const int64_t K_pad = ceil_div64(K, 128) * 128;
+    int64_t off = 0;
+    for (int q = 0; q < o.red_axis0; ++q) off += g->n[q] * K_pad;
+    const float *A = (const float *)g->ftab.p + off;
+    const int64_t n_ct = vup_simt_col_tiles(o);
+    const int64_t ldz = ceil_div64(o.NC, 128) * 128;
+    EpiArgs ep = epi_for(g, orient, K_pad);
+    dim3 grd((unsigned)n_ct, (unsigned)(K_pad / BM));
+    VUP_PROF(n_out == 1 ? "moments_fp32_simt" : "ipsa_fp32_simt", s, 1);
+    if (n_out == 1)
+        k_moments_simt<1><<<grd, 256, 0, s>>>(A, g->zs[orient], o.R, K_pad, ldz, ep, n_ct, part);
+    else
+        k_moments_simt<3><<<grd, 256, 0, s>>>(A, g->zs[orient], o.R, K_pad, ldz, ep, n_ct, part);
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}
+
+vup_status vup_moments_finish(vup_grid g, int64_t K, int n_col_tiles, double *raw, double *central,
+                              cudaStream_t s) {
+    const int64_t K_pad = ceil_div64(K, 128) * 128;
+    VUP_PROF("moments_finish_fp64", s, 1);
+    k_moments_finish<<<(unsigned)ceil_div64(K, 128), 128, 0, s>>>(
+        (const float *)g->partials.p, n_col_tiles, K, K_pad, g->J, (const DensStats *)g->dstats.p, g->ndim,
+        g->ydev_scale, raw, central);
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}
+
+vup_status vup_ipsa_finish(vup_grid g, int64_t K, int n_tiles0, int n_tiles1, const double *grad, float *dmu,
+                           float *dsg, cudaStream_t s) {
+    const int64_t K_pad = ceil_div64(K, 128) * 128;
+    const float *p0 = (const float *)g->ipsa_part.p;
+    const float *p1 = p0 + (size_t)3 * n_tiles0 * K_pad * 4;
+    VUP_PROF("ipsa_finish_fp64", s, 1);
+    k_ipsa_finish<<<(unsigned)ceil_div64(K, 128), 128, 0, s>>>(
+        p0, n_tiles0, p1, n_tiles1, K, K_pad, g->J, (const DensStats *)g->dstats.p,
+        (const DensConst *)g->dconst.p, g->ndim, g->ydev_scale, grad, dmu, dsg);
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}

@@ -1,0 +1,169 @@
+// Supplied-weights VUP: the input probability matrix is given explicitly
+// (N x K in the paper's Eq. VUP, stored here row-major as W[K][N]) and is
+// streamed once from HBM.  Every grid point's weight is multiplied into the
+// moment sums and added into its output bin (the one-hot model matrix of
+// Eq. MUP applied to each column).  The kernel is bound by the W read:
+// 4 bytes per distribution-point.
+#include "vup_internal.cuh"
+
+#include <algorithm>
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int RB>
+__global__ void __launch_bounds__(kThreads) k_weights(const float *__restrict__ W, int64_t K, int64_t N,
+                                                      const float *__restrict__ z32,
+                                                      const int32_t *__restrict__ bins, int B, int64_t n_split,
+                                                      double *__restrict__ mpart, float *__restrict__ hpart) {
+    extern __shared__ float sh[];  // [RB][B]
+    __shared__ double red[RB][4][kThreads / 32];
+    const int64_t split = blockIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.y * RB;
+    for (int e = threadIdx.x; e < RB * B; e += blockDim.x) sh[e] = 0.f;
+    __syncthreads();
+    // column range of this split, in float4 units (rows of W are 16-byte
+    // aligned only when N is a multiple of 4; otherwise every column goes
+    // through the scalar loop below)
+    const int64_t n4 = (N % 4 == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0) ? N / 4 : 0;
+    const int64_t per = (n4 + n_split - 1) / n_split;
+    const int64_t c0 = split * per, c1 = min(n4, c0 + per);
+    float m[RB][4];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m[r][j] = 0.f;
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        const float4 z = *reinterpret_cast<const float4 *>(z32 + c * 4);
+        const int4 b = *reinterpret_cast<const int4 *>(bins + c * 4);
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+        const int bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            if (k0 + r >= K) break;
+            const float4 w = __ldcs(reinterpret_cast<const float4 *>(W + (k0 + r) * N) + c);
+            const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float p = zz[q];
+                float t = ww[q] * p;
+                m[r][0] += t;
+                t *= p; m[r][1] += t;
+                t *= p; m[r][2] += t;
+                t *= p; m[r][3] += t;
+                atomicAdd(&sh[r * B + bb[q]], ww[q]);
+            }
+        }
+    }
+    // columns not covered by the float4 loop, split evenly
+    {
+        const int64_t rem = N - n4 * 4;
+        const int64_t per1 = (rem + n_split - 1) / n_split;
+        const int64_t i0 = n4 * 4 + split * per1, i1 = min(N, i0 + per1);
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const float p = z32[i];
+            const int bq = bins[i];
+            for (int r = 0; r < RB; ++r) {
+                if (k0 + r >= K) break;
+                const float w = W[(k0 + r) * N + i];
+                float t = w * p;
+                m[r][0] += t;
+                t *= p; m[r][1] += t;
+                t *= p; m[r][2] += t;
+                t *= p; m[r][3] += t;
+                atomicAdd(&sh[r * B + bq], w);
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            double v = m[r][j];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[r][j][warp] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < RB * 4) {
+        const int r = threadIdx.x >> 2, j = threadIdx.x & 3;
+        double v = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) v += red[r][j][w];
+        if (k0 + r < K) mpart[(split * K + k0 + r) * 4 + j] = v;
+    }
+    for (int e = threadIdx.x; e < RB * B; e += blockDim.x) {
+        const int r = e / B, b = e - r * B;
+        if (k0 + r < K) hpart[(split * K + k0 + r) * B + b] = sh[e];
+    }
+}
+
+__global__ void k_weights_finish(const double *__restrict__ mpart, const float *__restrict__ hpart,
+                                 int64_t n_split, int64_t K, int B, int J, const double *__restrict__ scale,
+                                 double *__restrict__ raw, float *__restrict__ hist) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (hist && e < K * B) {
+        float s = 0.f;
+        for (int64_t q = 0; q < n_split; ++q) s += hpart[q * K * B + e];
+        hist[e] = s;
+    }
+    if (raw && e < K * J) {
+        const int64_t k = e / J;
+        const int j = (int)(e - k * J);
+        double s = 0.0;
+        for (int64_t q = 0; q < n_split; ++q) s += mpart[(q * K + k) * 4 + j];
+        double sp = scale[0];
+        for (int q = 0; q < j; ++q) sp *= scale[0];
+        raw[e] = s * sp;
+    }
+}
+
+__global__ void k_z32(const double *__restrict__ y, int64_t N, const double *__restrict__ scale,
+                      float *__restrict__ z32) {
+    const double s = scale[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        z32[i] = (float)(y[i] / s);
+}
+
+}  // namespace
+
+static DevBuf g_wz32, g_wmpart, g_whpart;  // process-wide scratch of this path
+
+vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, float *hist, cudaStream_t s) {
+    const int64_t N = g->N;
+    const int B = g->B;
+    vup_status st;
+    if ((st = devbuf_reserve(g_wz32, sizeof(float) * (N + 4))) != VUP_OK) return st;
+    k_z32<<<(unsigned)std::min<int64_t>(ceil_div64(N, 256), 4096), 256, 0, s>>>(g->y, N, g->ydev_scale,
+                                                                                (float *)g_wz32.p);
+    VUP_CHECK_LAUNCH();
+    const int RB = B <= 3072 ? 8 : (B <= 6144 ? 4 : 2);
+    const int64_t rows = ceil_div64(K, RB);
+    int64_t n_split = std::max<int64_t>(1, (int64_t)vup_num_sms() * 8 / std::max<int64_t>(rows, 1));
+    n_split = std::min<int64_t>(n_split, std::max<int64_t>(1, N / 4096));
+    if ((st = devbuf_reserve(g_wmpart, sizeof(double) * 4 * K * n_split)) != VUP_OK) return st;
+    if ((st = devbuf_reserve(g_whpart, sizeof(float) * (size_t)B * K * n_split)) != VUP_OK) return st;
+    const size_t smem = sizeof(float) * (size_t)RB * B;
+    dim3 grd((unsigned)n_split, (unsigned)rows);
+    VUP_PROF("weights_stream", s, 3);
+    if (RB == 8) {
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_weights<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        k_weights<8><<<grd, kThreads, smem, s>>>(W, K, N, (const float *)g_wz32.p, g->bins, B, n_split,
+                                                 (double *)g_wmpart.p, (float *)g_whpart.p);
+    } else if (RB == 4) {
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_weights<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        k_weights<4><<<grd, kThreads, smem, s>>>(W, K, N, (const float *)g_wz32.p, g->bins, B, n_split,
+                                                 (double *)g_wmpart.p, (float *)g_whpart.p);
+    } else {
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_weights<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        k_weights<2><<<grd, kThreads, smem, s>>>(W, K, N, (const float *)g_wz32.p, g->bins, B, n_split,
+                                                 (double *)g_wmpart.p, (float *)g_whpart.p);
+    }
+    VUP_CHECK_LAUNCH();
+    const int64_t tot = std::max<int64_t>(K * B, K * g->J);
+    k_weights_finish<<<(unsigned)ceil_div64(tot, 256), 256, 0, s>>>((const double *)g_wmpart.p,
+                                                                    (const float *)g_whpart.p, n_split, K, B,
+                                                                    g->J, g->ydev_scale, raw, hist);
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}
