@@ -32,23 +32,57 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// Error-free FP32 transformations (Knuth two-sum, FMA two-product).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Constants of one (k, d) Gaussian factor in index space, as FP32 pairs.
+struct GaussArg {
+    double nk;       // integer part of the mean's index coordinate
+    float fh, fl;    // fractional part f = fh + fl
+    float rh, rl;    // r = h / sigma = rh + rl
+    float qh, ql;    // u0^2 = qh + ql (u at the midpoint nearest the mean)
+};
+
 // Per-axis density value at midpoint a (unnormalised), and u = ((a - n) - f) r.
-// Gaussian values are divided by their value at the midpoint nearest the mean
-// (a constant per (k, d) that the normalisation removes), so that very narrow
-// densities do not underflow in FP32.
-__device__ __forceinline__ float dens_value(int kind, int64_t a, double nk, float f, float r, float u0sq,
-                                            double xa, double mu, double sigma, double tlo, double thi,
-                                            float &u) {
+// The exponent 0.5 (u^2 - u0^2) is carried as an FP32 pair (error ~2^-44
+// relative) and exp is split, exp(-(eh + el)) = expf(-eh) (1 - el), so the
+// factor keeps FP32 relative accuracy even far in the tails, where the
+// exponent is large and a plain FP32 argument would lose ~e * 2^-24.
+// Dividing by the value at the midpoint nearest the mean (u0) is a constant
+// per (k, d) that the normalisation removes; it keeps narrow densities from
+// underflowing.
+__device__ __forceinline__ float dens_value(int kind, int64_t a, const GaussArg &ga, double xa, double mu,
+                                            double sigma, double tlo, double thi, float &u) {
     if (kind == VUP_UNIFORM) {
         u = 0.f;
         double half = __dmul_rn(0.5, sigma);
         double dx = fabs(__dsub_rn(xa, mu));
         return dx <= half ? 1.f : 0.f;
     }
-    float t = (float)((double)a - nk) - f;
-    u = t * r;
+    // t = (a - n) - f exactly as a pair
+    const float A = (float)((double)a - ga.nk);
+    float th, tl;
+    two_sum(A, -ga.fh, th, tl);
+    tl -= ga.fl;
+    // u = t r
+    const float uh = th * ga.rh;
+    const float ul = fmaf(th, ga.rh, -uh) + (th * ga.rl + tl * ga.rh);
+    u = uh + ul;
     if (kind == VUP_TRUNCNORM && !(tlo <= xa && xa <= thi)) return 0.f;
-    return expf(-0.5f * ((u - sqrtf(u0sq)) * (u + sqrtf(u0sq))));
+    // u^2 - u0^2
+    const float sh = uh * uh;
+    const float sl = fmaf(uh, uh, -sh) + 2.f * uh * ul;
+    float dh, dl;
+    two_sum(sh, -ga.qh, dh, dl);
+    dl += sl - ga.ql;
+    const float eh0 = 0.5f * dh, el0 = 0.5f * dl;
+    const float eh = eh0 + el0;
+    const float el = el0 - (eh - eh0);
+    return expf(-eh) * (1.f - el);
 }
 
 __global__ void k_density_prep(DensIn in, int64_t K, int64_t K_pad, int ndim, int64_t n0, int64_t n1,
@@ -76,21 +110,30 @@ __global__ void k_density_prep(DensIn in, int64_t K, int64_t K_pad, int ndim, in
     // index coordinate of the mean: (mu - lo) / h - 1/2 = nk + f
     const double c = (mu - lo) / h - 0.5;
     const double nk = floor(c);
-    const float f = (float)(c - nk);
-    const float r = (float)(h / sigma);
+    const double fd = c - nk;
+    const double rd = h / sigma;
+    const float f = (float)fd;
+    const float r = (float)rd;
+    GaussArg ga;
+    ga.nk = nk;
+    ga.fh = f;
+    ga.fl = (float)(fd - (double)f);
+    ga.rh = r;
+    ga.rl = (float)(rd - (double)r);
     // squared index-space distance from the mean to its nearest midpoint
     double anear = floor(c + 0.5);
     anear = fmin(fmax(anear, 0.0), (double)(nd - 1));
-    float t0 = (float)(anear - nk) - f;
-    float u0 = t0 * r;
-    float u0sq = kind == VUP_UNIFORM ? 0.f : u0 * u0;
-    if (!(u0sq < 1e30f)) u0sq = 0.f;
+    const double u0 = ((anear - nk) - fd) * rd;
+    double u0sq = kind == VUP_UNIFORM ? 0.0 : u0 * u0;
+    if (!(u0sq < 1e30)) u0sq = 0.0;
+    ga.qh = (float)u0sq;
+    ga.ql = (float)(u0sq - (double)ga.qh);
     KSum S0, S1, S2;
     for (int64_t a = 0; a < nd; ++a) {
         double xa = 0.0;
         if (kind != VUP_GAUSS) xa = __dadd_rn(lo, __dmul_rn((double)a + 0.5, h));
         float u;
-        float g = dens_value(kind, a, nk, f, r, u0sq, xa, mu, sigma, tlo, thi, u);
+        float g = dens_value(kind, a, ga, xa, mu, sigma, tlo, thi, u);
         tab[a * K_pad + k] = g;
         S0.add(g);
         S1.add(g * u);

@@ -19,11 +19,10 @@ namespace {
 
 constexpr int kHistWarps = 16;
 constexpr int kKT = 32;              // densities per k-tile (one per lane)
-constexpr uint32_t kRunEnd = 0x80000000u;
 
 struct HistArgs {
     const uint32_t *hpt;
-    const int32_t *run_rest, *run_bin;
+    const int32_t *run_start, *run_rest, *run_bin;
     const int32_t *chunk_pt, *chunk_run, *chunk_bin;
     const int32_t *offsets;
     const float *g_last;      // factor table of the last axis  [n_last][K_pad]
@@ -38,6 +37,8 @@ struct HistArgs {
     float *hist;              // [K][B]
     float *part;              // [C][2][K_pad]
 };
+
+constexpr int kPF = 16;              // runs whose rest-axis factor is prefetched ahead
 
 template <bool kSmem>
 __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist(HistArgs A) {
@@ -67,10 +68,16 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist(HistArgs A) {
     const int32_t r0 = A.chunk_run[c], r1 = A.chunk_run[c + 1];
     const int32_t first_bin = A.chunk_bin[2 * c];
 
-    int32_t r = r0;
-    int32_t cur_bin = A.run_bin[r0];
-    float acc = 0.f, bacc = 0.f;
-
+    // rest-axis factor of run r for this lane's density
+    auto wrest = [&](int32_t r) -> float {
+        if (r >= r1) return 0.f;
+        const int32_t rest = A.run_rest[r];
+        if (A.ndim == 3) {
+            const int64_t a0 = rest / A.n1, a1 = rest - a0 * A.n1;
+            return A.g0[a0 * A.K_pad + k] * A.g1[a1 * A.K_pad + k];
+        }
+        return A.g0[(int64_t)rest * A.K_pad + k];
+    };
     auto flush_bin = [&](int32_t b, float v) {
         const float val = v * invZ;
         const bool shared = A.offsets[b] < p0 || A.offsets[b + 1] > p1;
@@ -81,59 +88,48 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist(HistArgs A) {
             A.hist[k * A.B + b] = val;
         }
     };
-    auto end_run = [&]() {
-        const int32_t rest = A.run_rest[r];
-        float wr;
-        if (A.ndim == 3) {
-            const int64_t a0 = rest / A.n1, a1 = rest - a0 * A.n1;
-            wr = A.g0[a0 * A.K_pad + k] * A.g1[a1 * A.K_pad + k];
-        } else {
-            wr = A.g0[(int64_t)rest * A.K_pad + k];
-        }
-        bacc = fmaf(wr, acc, bacc);
-        acc = 0.f;
-        ++r;
-        const int32_t nb = r < r1 ? A.run_bin[r] : -1;
-        if (nb != cur_bin) {
-            flush_bin(cur_bin, bacc);
-            bacc = 0.f;
-            cur_bin = nb;
+
+    int32_t cur_bin = A.run_bin[r0];
+    float bacc = 0.f;
+    float wa[kPF], wb[kPF];
+#pragma unroll
+    for (int u = 0; u < kPF; ++u) wa[u] = wrest(r0 + u);
+
+    // one block of kPF runs: sum the last-axis factors of each run's points,
+    // scale by the run's rest factor, flush at bin changes
+    auto do_block = [&](int32_t rb, const float (&w)[kPF]) {
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) {
+            const int32_t r = rb + u;
+            if (r >= r1) break;
+            const int32_t s0 = A.run_start[r], s1 = A.run_start[r + 1];
+            float acc = 0.f;
+            int32_t p = s0;
+            for (; p + 2 <= s1; p += 2) {
+                const uint32_t u0 = A.hpt[p], u1 = A.hpt[p + 1];
+                const float v0 = wl[(int64_t)(u0 & 0xffffu) * wstride];
+                const float v1 = wl[(int64_t)(u1 & 0xffffu) * wstride];
+                acc += v0;
+                acc += v1;
+            }
+            if (p < s1) acc += wl[(int64_t)(A.hpt[p] & 0xffffu) * wstride];
+            bacc = fmaf(w[u], acc, bacc);
+            const int32_t nb = r + 1 < r1 ? A.run_bin[r + 1] : -1;
+            if (nb != cur_bin) {
+                flush_bin(cur_bin, bacc);
+                bacc = 0.f;
+                cur_bin = nb;
+            }
         }
     };
-
-    int32_t p = p0;
-    // head: scalar until 4-aligned
-    for (; p < p1 && (p & 3); ++p) {
-        const uint32_t u = A.hpt[p];
-        acc += wl[(int64_t)(u & 0xffffu) * wstride];
-        if (u & kRunEnd) end_run();
-    }
-    for (; p + 4 <= p1; p += 4) {
-        const uint4 u = *reinterpret_cast<const uint4 *>(A.hpt + p);
-        const float v0 = wl[(int64_t)(u.x & 0xffffu) * wstride];
-        const float v1 = wl[(int64_t)(u.y & 0xffffu) * wstride];
-        const float v2 = wl[(int64_t)(u.z & 0xffffu) * wstride];
-        const float v3 = wl[(int64_t)(u.w & 0xffffu) * wstride];
-        if (((u.x | u.y | u.z | u.w) & kRunEnd) == 0) {
-            acc += v0;
-            acc += v1;
-            acc += v2;
-            acc += v3;
-        } else {
-            acc += v0;
-            if (u.x & kRunEnd) end_run();
-            acc += v1;
-            if (u.y & kRunEnd) end_run();
-            acc += v2;
-            if (u.z & kRunEnd) end_run();
-            acc += v3;
-            if (u.w & kRunEnd) end_run();
-        }
-    }
-    for (; p < p1; ++p) {
-        const uint32_t u = A.hpt[p];
-        acc += wl[(int64_t)(u & 0xffffu) * wstride];
-        if (u & kRunEnd) end_run();
+    for (int32_t rb = r0; rb < r1; rb += 2 * kPF) {
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) wb[u] = wrest(rb + kPF + u);
+        do_block(rb, wa);
+        if (rb + kPF >= r1) break;
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) wa[u] = wrest(rb + 2 * kPF + u);
+        do_block(rb + kPF, wb);
     }
 }
 
@@ -182,6 +178,7 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
     const int64_t K_pad = ceil_div64(K, 128) * 128;
     HistArgs A{};
     A.hpt = g->hpt;
+    A.run_start = g->run_start;
     A.run_rest = g->run_rest;
     A.run_bin = g->run_bin;
     A.chunk_pt = g->chunk_pt;

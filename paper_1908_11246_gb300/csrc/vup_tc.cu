@@ -1,6 +1,396 @@
-// Tensor-core (tcgen05) moment contraction -- placeholder until the kernel lands.
+// Moment contraction on the 5th-generation tensor cores (tcgen05 + TMEM).
+//
+//   T[k, (q, j)] = sum_r g_red(k, r) (y_(q,r) / s)^(j+1)        (GEMM, Eq. VUP
+//   M[k, j]     += sum_q g_rest(k, q) T[k, (q, j)]               as moments)
+//
+// BF16x3: every FP32 operand is split into bf16 hi + lo and the product is
+// formed as hi*hi + hi*lo + lo*hi with FP32 accumulation in TMEM (the lo*lo
+// term, ~2^-16 relative, is dropped).  Operand tiles are staged by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) into a 2-stage shared-memory ring;
+// one thread issues tcgen05.mma; the accumulator is double-buffered in TMEM
+// (2 x 256 columns) so that the epilogue of one tile overlaps the main loop
+// of the next.  The epilogue reads TMEM with tcgen05.ld, multiplies by the
+// rest-axis density factors generated from the factor tables, reduces over
+// the tile's q values and writes FP32 partials that an FP64 kernel sums.
+//
+// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer,
+// warps 2..5 = epilogue (one TMEM lane quadrant each).  Persistent CTAs walk
+// the (row tile, column tile) list with a static stride.  Every mbarrier wait
+// is bounded; on expiry the kernel records VUP_DSTAT_TIMEOUT, drains what it
+// issued and returns.
 #include "vup_internal.cuh"
 
-int64_t vup_tc_col_tiles(const Orient &o) { return ceil_div64(o.NC, 256); }
+#include <cuda.h>
 
-vup_status vup_moments_tc(vup_grid, int64_t, int, int, float *, cudaStream_t) { return VUP_ERR_UNSUPPORTED; }
+#include <algorithm>
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int STAGES = 2;
+constexpr int A_BYTES = BM * BK * 2;            // 16 KB per bf16 plane
+constexpr int B_BYTES = BN * BK * 2;            // 32 KB per bf16 plane
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int TMEM_COLS = 512;                  // 2 accumulators of BN fp32 columns
+constexpr int kThreads = 192;
+constexpr uint32_t kSpinLimit = 1u << 26;       // bounded waits (~seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: returns false (and raises the abort flag) on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int *dstatus) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (i > 64) __nanosleep(32);
+    }
+    *abort_flag = 1;
+    atomicCAS(dstatus, 0, VUP_DSTAT_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart (SBO), version 1 (sm_100+).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3fff);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;               // descriptor version
+    d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcEpi {
+    const float *g_rest0;      // [n_rest0][K_pad]
+    const float *g_rest1;      // 3-D second rest axis or nullptr
+    int64_t n_rest1;
+    int64_t Q;                 // rest points
+    const DensConst *dconst;   // IPSA weights (rest axis)
+    int ndim, rest_axis;
+};
+
+template <int NOUT>
+__global__ void __launch_bounds__(kThreads, 1)
+k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+             const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int n_m, int n_n,
+             int n_kb, int64_t K_pad, TcEpi ep, float *__restrict__ part, int *__restrict__ dstatus) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(drain + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = n_m * n_n;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                const int m = t / n_n, n = t - m * n_n;
+                for (int kb = 0; kb < n_kb; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, dstatus)) { ok = false; break; }
+                    uint8_t *st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(st, &tmAh, &full[s], kb * BK, m * BM);
+                    tma_load_2d(st + A_BYTES, &tmAl, &full[s], kb * BK, m * BM);
+                    tma_load_2d(st + 2 * A_BYTES, &tmBh, &full[s], kb * BK, n * BN);
+                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmBl, &full[s], kb * BK, n * BN);
+                }
+            }
+            // drain: every issued stage must land before shared memory is released
+            if (!ok) {
+                for (uint32_t j = (it > (uint32_t)STAGES ? it - STAGES : 0); j < it; ++j) {
+                    for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(&full[j % STAGES], (j / STAGES) & 1); ++i) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t it = 0, tile_it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tile_it) {
+                const int b = tile_it & 1;
+                if (!mbar_wait(&tempty[b], ((tile_it >> 1) & 1) ^ 1, abort_flag, dstatus)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t dcol = tmem_base + (uint32_t)(b * BN);
+                for (int kb = 0; kb < n_kb; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, dstatus)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t a_lo = a_hi + A_BYTES;
+                    const uint32_t b_hi = a_hi + 2 * A_BYTES;
+                    const uint32_t b_lo = b_hi + B_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t off = kk * 32;  // 16 bf16 along K inside the swizzle atom
+                        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+                        umma_bf16(dcol, sw128_desc(a_lo + off), sw128_desc(b_hi + off), acc0);
+                        umma_bf16(dcol, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
+                        umma_bf16(dcol, sw128_desc(a_hi + off), sw128_desc(b_hi + off), 1u);
+                    }
+                    umma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                umma_commit(&tfull[b]);
+            }
+            // all MMAs issued by this thread complete before TMEM is released
+            umma_commit(drain);
+            for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(drain, 0); ++i) {
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        uint32_t tile_it = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tile_it) {
+            const int m = t / n_n, n = t - m * n_n;
+            const int b = tile_it & 1;
+            if (!mbar_wait(&tfull[b], (tile_it >> 1) & 1, abort_flag, dstatus)) break;
+            tc_fence_after();
+            const int64_t k = (int64_t)m * BM + row;
+            float out[NOUT][4];
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) out[o][j] = 0.f;
+            DensConst dc{};
+            if (NOUT == 3) dc = ep.dconst[k * ep.ndim + ep.rest_axis];
+            const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN);
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                float v[32];
+                tmem_ld32(tbase + ch * 32, v);
+                const int64_t q0 = (int64_t)n * (BN / 4) + ch * 8;
+                float e[8];
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq) {
+                    const int64_t q = q0 + qq;
+                    float w = 0.f;
+                    if (q < ep.Q) {
+                        if (ep.g_rest1) {
+                            const int64_t qa = q / ep.n_rest1, qb = q - qa * ep.n_rest1;
+                            w = ep.g_rest0[qa * K_pad + k] * ep.g_rest1[qb * K_pad + k];
+                        } else {
+                            w = ep.g_rest0[q * K_pad + k];
+                        }
+                    }
+                    e[qq] = w;
+                }
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq) {
+                    float w[NOUT];
+                    w[0] = e[qq];
+                    if (NOUT == 3) {
+                        const float tt = (float)(q0 + qq - dc.n) - dc.f;
+                        const float u = tt * dc.r;
+                        w[NOUT == 3 ? 1 : 0] = e[qq] * u;
+                        w[NOUT == 3 ? 2 : 0] = e[qq] * u * u;
+                    }
+#pragma unroll
+                    for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) out[o][j] = fmaf(w[o], v[qq * 4 + j], out[o][j]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o)
+                *reinterpret_cast<float4 *>(part + (((int64_t)o * n_n + n) * K_pad + k) * 4) =
+                    make_float4(out[o][0], out[o][1], out[o][2], out[o][3]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---- host side: tensor maps -------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 2-D bf16 map over a row-major [rows][ld] array, box [box_rows][64].
+bool make_map(CUtensorMap *m, const void *base, int64_t ld, int64_t rows, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int64_t vup_tc_col_tiles(const Orient &o) { return ceil_div64(o.NC, BN); }
+
+vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s) {
+    const Orient &o = g->orient[orient];
+    const int64_t K_pad = ceil_div64(K, 128) * 128;
+    const int64_t nn = vup_tc_col_tiles(o);
+    const int64_t rows_b = ceil_div64(o.NC, 256) * 256;
+    const __nv_bfloat16 *ah = (const __nv_bfloat16 *)g->atab_hi.p, *al = (const __nv_bfloat16 *)g->atab_lo.p;
+    if (orient == 1) {
+        const size_t o0 = (size_t)K_pad * g->orient[0].R_pad;
+        ah += o0;
+        al += o0;
+    }
+    CUtensorMap mAh, mAl, mBh, mBl;
+    if (!make_map(&mAh, ah, o.R_pad, K_pad, BM) || !make_map(&mAl, al, o.R_pad, K_pad, BM) ||
+        !make_map(&mBh, g->zt_hi[orient], o.R_pad, rows_b, BN) || !make_map(&mBl, g->zt_lo[orient], o.R_pad, rows_b, BN))
+        return VUP_ERR_CUDA;
+    TcEpi ep{};
+    auto tab = [&](int axis) {
+        int64_t off = 0;
+        for (int q = 0; q < axis; ++q) off += g->n[q] * K_pad;
+        return (const float *)g->ftab.p + off;
+    };
+    ep.g_rest0 = tab(o.rest_axes[0]);
+    ep.g_rest1 = o.n_rest_axes > 1 ? tab(o.rest_axes[1]) : nullptr;
+    ep.n_rest1 = o.n_rest_axes > 1 ? g->n[o.rest_axes[1]] : 1;
+    ep.Q = o.Q;
+    ep.dconst = (const DensConst *)g->dconst.p;
+    ep.ndim = g->ndim;
+    ep.rest_axis = o.rest_axes[0];
+    const int n_m = (int)(K_pad / BM), n_n = (int)nn, n_kb = (int)(o.R_pad / BK);
+    const int n_tiles = n_m * n_n;
+    const int grid = std::min(n_tiles, vup_num_sms());
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+    VUP_PROF(n_out == 1 ? "moments_bf16x3_tc" : "ipsa_bf16x3_tc", s, 1);
+    if (n_out == 1) {
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_moments_tc<1><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, g->dstatus);
+    } else {
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_moments_tc<3><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, g->dstatus);
+    }
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}

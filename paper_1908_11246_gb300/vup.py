@@ -248,9 +248,10 @@ class Grid:
         import torch
         K = dev_dens["mu"].shape[0]
         dev = dev_dens["mu"].device
-        raw = torch.empty((K, self.n_moments), dtype=torch.float64, device=dev) if moments else None
-        cen = torch.empty((K, self.n_moments), dtype=torch.float64, device=dev) if central else None
-        hs = torch.empty((K, self.n_bins), dtype=torch.float32, device=dev) if hist else None
+        J, B = self.n_moments or 1, self.n_bins or 1   # before eval_model the library reports VUP_ERR_STATE
+        raw = torch.empty((K, J), dtype=torch.float64, device=dev) if moments else None
+        cen = torch.empty((K, J), dtype=torch.float64, device=dev) if central else None
+        hs = torch.empty((K, B), dtype=torch.float32, device=dev) if hist else None
         d = make_densities(dev_dens)
         vup_propagate(self.h, d, PRECISIONS[precision], raw, cen, hs, stream)
         return raw, cen, hs

@@ -54,7 +54,10 @@ GRID_CASES = [
 def test_model_bins_and_sorted_order(prob):
     """y within libm ulp bounds (bit-exact for polynomial models); bins,
     sorted order and bin offsets bit-exact away from edge ties."""
-    g, *_ = gpu_run(prob, "fp32", moments=False, central=False, hist=False)
+    vup = vupmod()
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.eval_model(prob.model_id, prob.theta, prob.n_bins, prob.n_moments)
+    g.sync()
     y_g = g.array("y").cpu().numpy()
     b_g = g.array("bins").cpu().numpy()
     p_g = g.array("perm").cpu().numpy()
@@ -108,6 +111,33 @@ def test_propagate_random_ragged_shapes(seed):
     _parity(prob, "fp32")
 
 
+def test_bf16x3_single_tile():
+    """One 128 x 256 tensor-core tile, one 64-wide k-block."""
+    prob = I.Problem("tile1", (64, 64), (-2.0, -1.0), (2.0, 1.5), I.MODEL_SIN_SIN2_2D, (1.0, 3.0),
+                     I.random_densities(np.random.default_rng(5), 128, (-2.0, -1.0), (2.0, 1.5),
+                                        sig=(0.1, 0.8), width=(0.3, 1.0)), 32)
+    _parity(prob, "bf16x3")
+
+
+@pytest.mark.parametrize("name", ["c2", "c3", "c4"])
+def test_propagate_small_configs_bf16x3(name):
+    _parity(I.config(name, "small"), "bf16x3")
+
+
+@pytest.mark.parametrize("seed", [211, 212, 213, 214])
+def test_propagate_random_ragged_shapes_bf16x3(seed):
+    prob = I.random_problem(seed, ndim=2 + seed % 2)
+    _parity(prob, "bf16x3")
+
+
+@pytest.mark.parametrize("name", ["c2", "c3"])
+def test_propagate_full_size_sampled_rows_bf16x3(name):
+    prob = I.config(name)
+    rows = np.random.default_rng(8).choice(prob.K, size=24, replace=False)
+    rows = np.concatenate([[0, prob.K - 1], rows])
+    _parity(prob, "bf16x3", rows=rows)
+
+
 def test_propagate_c1_full_fp64_all_rows():
     _parity(I.config("c1"), "fp64")
 
@@ -146,7 +176,7 @@ def _ipsa_gate(g_gpu, g_or, scale, tol):
     return float(err.max())
 
 
-@pytest.mark.parametrize("precision", ["fp32"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 def test_ipsa_matches_oracle_and_fd(precision):
     vup = vupmod()
     import torch
