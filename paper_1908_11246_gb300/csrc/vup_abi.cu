@@ -158,15 +158,23 @@ static void free_grid(vup_grid g) {
     cudaFree(g->bins);
     cudaFree(g->perm);
     cudaFree(g->offsets);
-    cudaFree(g->hpt);
-    cudaFree(g->run_start);
-    cudaFree(g->run_rest);
-    cudaFree(g->run_bin);
-    cudaFree(g->n_runs);
+    for (int l = 0; l < 2; ++l) {
+        auto &L = g->hl[l];
+        if (l == 1) {
+            cudaFree(L.keys);
+            cudaFree(L.perm);
+        }
+        cudaFree(L.hpt);
+        cudaFree(L.run_start);
+        cudaFree(L.run_rest);
+        cudaFree(L.run_bin);
+        cudaFree(L.n_runs);
+        cudaFree(L.chunk_pt);
+        cudaFree(L.chunk_run);
+        cudaFree(L.chunk_bin);
+    }
+    cudaFree(g->hist_sel);
     cudaFree(g->flags_scan);
-    cudaFree(g->chunk_pt);
-    cudaFree(g->chunk_run);
-    cudaFree(g->chunk_bin);
     cudaFree(g->ydev_scale);
     cudaFree(g->dstatus);
     for (int o = 0; o < 2; ++o) {
@@ -229,19 +237,33 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
     ALLOC(g->ext, sizeof(unsigned long long) * 2);
     ALLOC(g->bins, sizeof(int32_t) * N);
     ALLOC(g->perm, sizeof(int32_t) * N);
-    ALLOC(g->hpt, sizeof(uint32_t) * (N + 4));
-    ALLOC(g->run_start, sizeof(int32_t) * (N + 1));
-    ALLOC(g->run_rest, sizeof(int32_t) * N);
-    ALLOC(g->run_bin, sizeof(int32_t) * N);
-    ALLOC(g->n_runs, sizeof(int32_t));
+    g->n_layouts = ndim == 2 ? 2 : 1;
+    for (int l = 0; l < g->n_layouts; ++l) {
+        auto &L = g->hl[l];
+        L.last_axis = l == 0 ? ndim - 1 : 0;
+        L.n_last = g->n[L.last_axis];
+        if (l == 1) {
+            ALLOC(L.keys, sizeof(int32_t) * N);
+            ALLOC(L.perm, sizeof(int32_t) * N);
+        }
+        ALLOC(L.hpt, sizeof(uint32_t) * (N + 512));  // tail slack for whole staged windows
+        ALLOC(L.run_start, sizeof(int32_t) * (N + 1));
+        ALLOC(L.run_rest, sizeof(int32_t) * N);
+        ALLOC(L.run_bin, sizeof(int32_t) * N);
+        ALLOC(L.n_runs, sizeof(int32_t));
+        ALLOC(L.chunk_pt, sizeof(int32_t) * (C + 1));
+        ALLOC(L.chunk_run, sizeof(int32_t) * (C + 1));
+        ALLOC(L.chunk_bin, sizeof(int32_t) * 2 * C);
+    }
+    g->hl[0].keys = g->bins;
+    g->hl[0].perm = g->perm;
+    ALLOC(g->hist_sel, sizeof(int32_t));
     ALLOC(g->flags_scan, sizeof(int32_t) * N);
-    ALLOC(g->chunk_pt, sizeof(int32_t) * (C + 1));
-    ALLOC(g->chunk_run, sizeof(int32_t) * (C + 1));
-    ALLOC(g->chunk_bin, sizeof(int32_t) * 2 * C);
     ALLOC(g->ydev_scale, sizeof(double));
     ALLOC(g->dstatus, sizeof(int));
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMemset(g->dstatus, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(g->hist_sel, 0, sizeof(int32_t));
     if (e != cudaSuccess) {
         vup_set_last_cuda_error(e, "vup_grid_create", __FILE__, __LINE__);
         cudaGetLastError();

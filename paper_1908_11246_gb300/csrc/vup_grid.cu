@@ -14,7 +14,11 @@ namespace {
 
 constexpr int kSortTile = 2048;      // points per warp in the counting sort
 constexpr int kSortWarps = 4;        // warps per CTA in the counting sort
-constexpr uint32_t kRunEnd = 0x80000000u;
+// Packed sorted-point word: last-axis index << 7 (the byte offset of its row in
+// a 32-float shared-memory tile), run-end flag (bit 30), bin-end flag (bit 31).
+constexpr int kPtShift = 7;
+constexpr uint32_t kRunEnd = 1u << 30;
+constexpr uint32_t kBinEnd = 1u << 31;
 
 struct Theta {
     double t[8];
@@ -183,6 +187,44 @@ __global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
     }
 }
 
+// Points per (bin, warp tile) of an already binned key array.
+__global__ void k_count(const int32_t *__restrict__ keys, int64_t N, int B, int32_t *__restrict__ counts,
+                        int64_t n_tiles) {
+    extern __shared__ int32_t s_cnt[];  // [kSortWarps][B]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *cnt = s_cnt + warp * B;
+    for (int b = lane; b < B; b += 32) cnt[b] = 0;
+    __syncwarp();
+    const int64_t tile = (int64_t)blockIdx.x * kSortWarps + warp;
+    if (tile < n_tiles) {
+        const int64_t i0 = tile * kSortTile;
+        const int64_t i1 = min(N, i0 + kSortTile);
+        for (int64_t i = i0 + lane; i < i1; i += 32) atomicAdd(&cnt[keys[i]], 1);
+        __syncwarp();
+        for (int b = lane; b < B; b += 32) counts[(int64_t)b * n_tiles + tile] = cnt[b];
+    }
+}
+
+// out[a1 * n0 + a0] = in[a0 * n1 + a1]
+__global__ void k_transpose_i32(const int32_t *__restrict__ in, int64_t n0, int64_t n1, int32_t *__restrict__ out) {
+    __shared__ int32_t t[32][33];
+    const int64_t a0b = (int64_t)blockIdx.y * 32, a1b = (int64_t)blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int64_t a0 = a0b + y, a1 = a1b + threadIdx.x;
+        if (a0 < n0 && a1 < n1) t[y][threadIdx.x] = in[a0 * n1 + a1];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int64_t a1 = a1b + y, a0 = a0b + threadIdx.x;
+        if (a0 < n0 && a1 < n1) out[a1 * n0 + a0] = t[threadIdx.x][y];
+    }
+}
+
+// The histogram walks the layout with fewer runs (less per-run work).
+__global__ void k_pick_layout(const int32_t *n_runs0, const int32_t *n_runs1, int32_t *sel) {
+    sel[0] = (n_runs1 && n_runs1[0] < n_runs0[0]) ? 1 : 0;
+}
+
 // Stable scatter: each warp walks its tile in order, 32 points at a time;
 // equal bins inside a step are ranked by lane with __match_any_sync.
 __global__ void k_sort_scatter(const int32_t *__restrict__ bins, int64_t N, int B,
@@ -274,7 +316,7 @@ __global__ void k_scan_add(int32_t *__restrict__ out, int64_t L, const int32_t *
 // ---- runs and chunks for the segmented histogram --------------------------
 // A run is a maximal stretch of sorted points sharing the output bin and every
 // axis index but the last one.  hpt[t] packs the last-axis index of the t-th
-// sorted point (bits 0..15) and a run-end flag (bit 31).
+// sorted point and the run-end / bin-end flags (layout above).
 __global__ void k_run_flags(const int32_t *__restrict__ perm, const int32_t *__restrict__ bins,
                             int64_t N, int64_t n_last, int32_t *__restrict__ flags) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
@@ -303,11 +345,41 @@ __global__ void k_run_build(const int32_t *__restrict__ perm, const int32_t *__r
             run_bin[rid] = bins[i];
         }
         const bool last = (t == N - 1) || flags[t + 1];
-        hpt[t] = (uint32_t)(i % n_last) | (last ? kRunEnd : 0u);
+        const bool bin_last = (t == N - 1) || bins[perm[t + 1]] != bins[i];
+        hpt[t] = ((uint32_t)(i % n_last) << kPtShift) | (last ? kRunEnd : 0u) | (bin_last ? kBinEnd : 0u);
         if (t == N - 1) {
             n_runs[0] = rid + 1;
             run_start[rid + 1] = (int32_t)N;
         }
+    }
+}
+
+// The run-end word of run r also carries the rest-axis index of run r + 4
+// (the histogram kernel loads that run's factor four runs ahead): for 2-D
+// grids the 15-bit index sits in bits 0..6 and 22..29; for 3-D grids a0
+// (7 bits) in bits 0..6 and a1 (8 bits) in bits 22..29.  Zero past the end.
+constexpr int kRunAhead = 4;
+__global__ void k_run_encode(const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_rest,
+                             const int32_t *__restrict__ n_runs_p, int ndim, int64_t n1,
+                             uint32_t *__restrict__ hpt) {
+    const int32_t n_runs = n_runs_p[0];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_runs;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ra = r + kRunAhead;
+        uint32_t code = 0;
+        if (ra < n_runs) {
+            const int32_t rest = run_rest[ra];
+            uint32_t lo7, hi8;
+            if (ndim == 3) {
+                lo7 = (uint32_t)(rest / n1);
+                hi8 = (uint32_t)(rest % n1);
+            } else {
+                lo7 = (uint32_t)rest & 0x7fu;
+                hi8 = (uint32_t)rest >> 7;
+            }
+            code = (lo7 & 0x7fu) | ((hi8 & 0xffu) << 22);
+        }
+        hpt[run_start[r + 1] - 1] |= code;
     }
 }
 
@@ -482,7 +554,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     const int64_t N = g->N;
     const int B = g->B;
     // range, bins, sort (+2 scans of up to 3 launches), runs, chunks
-    VUP_PROF("range_bins_sort_runs", s, g->ndim >= 2 ? 16 : 8);
+    VUP_PROF("range_bins_sort_runs", s, g->ndim == 2 ? 32 : (g->ndim == 3 ? 18 : 9));
     // exact range of y
     VUP_CHECK_CUDA(cudaMemsetAsync(g->ext, 0xff, sizeof(unsigned long long), s));
     VUP_CHECK_CUDA(cudaMemsetAsync(g->ext + 1, 0x00, sizeof(unsigned long long), s));
@@ -492,7 +564,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     k_scale<<<1, 1, 0, s>>>(g->ext, g->ydev_scale);
     VUP_CHECK_LAUNCH();
 
-    // bins + stable counting sort
+    // bins + stable counting sort (natural order), offsets
     const int64_t n_tiles = ceil_div64(N, kSortTile);
     const int64_t L = (int64_t)B * n_tiles;
     vup_status st = devbuf_reserve(g->sort_counts,
@@ -507,40 +579,58 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     const unsigned sblocks = (unsigned)ceil_div64(n_tiles, kSortWarps);
     if (smem > 48 * 1024) {
         VUP_CHECK_CUDA(cudaFuncSetAttribute(k_bins_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         VUP_CHECK_CUDA(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    k_bins_count<<<sblocks, 32 * kSortWarps, smem, s>>>(g->y, N, B, g->ext, g->bins, counts, n_tiles);
-    VUP_CHECK_LAUNCH();
-    st = scan_exclusive(counts, starts, L, scratch, s);
-    if (st != VUP_OK) return st;
-    k_sort_scatter<<<sblocks, 32 * kSortWarps, smem, s>>>(g->bins, N, B, starts, n_tiles, g->perm);
-    VUP_CHECK_LAUNCH();
-    // offsets[b] = starts[b * n_tiles], offsets[B] = N
-    VUP_CHECK_CUDA(cudaMemcpy2DAsync(g->offsets, sizeof(int32_t), starts, sizeof(int32_t) * n_tiles,
-                                     sizeof(int32_t), B, cudaMemcpyDeviceToDevice, s));
-    k_set_i32<<<1, 1, 0, s>>>(g->offsets + B, (int32_t)N);
-    VUP_CHECK_LAUNCH();
-
-    // runs and chunks (2-D and 3-D grids; 1-D uses bins directly)
-    if (g->ndim >= 2) {
-        const int64_t n_last = g->n[g->ndim - 1];
-        int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
-        k_run_flags<<<rb, 256, 0, s>>>(g->perm, g->bins, N, n_last, g->flags_scan);
+    for (int l = 0; l < g->n_layouts; ++l) {
+        auto &HL = g->hl[l];
+        if (l == 0) {
+            k_bins_count<<<sblocks, 32 * kSortWarps, smem, s>>>(g->y, N, B, g->ext, g->bins, counts, n_tiles);
+            VUP_CHECK_LAUNCH();
+        } else {
+            // layout 1 (2-D): keys in transposed order, j = a1 * n0 + a0
+            dim3 tg((unsigned)ceil_div64(g->n[1], 32), (unsigned)ceil_div64(g->n[0], 32));
+            k_transpose_i32<<<tg, dim3(32, 8), 0, s>>>(g->bins, g->n[0], g->n[1], HL.keys);
+            VUP_CHECK_LAUNCH();
+            k_count<<<sblocks, 32 * kSortWarps, smem, s>>>(HL.keys, N, B, counts, n_tiles);
+            VUP_CHECK_LAUNCH();
+        }
+        st = scan_exclusive(counts, starts, L, scratch, s);
+        if (st != VUP_OK) return st;
+        k_sort_scatter<<<sblocks, 32 * kSortWarps, smem, s>>>(HL.keys, N, B, starts, n_tiles, HL.perm);
         VUP_CHECK_LAUNCH();
-        // the sort counts are dead once the offsets are copied: reuse them
+        if (l == 0) {
+            // offsets[b] = starts[b * n_tiles], offsets[B] = N (identical for every layout)
+            VUP_CHECK_CUDA(cudaMemcpy2DAsync(g->offsets, sizeof(int32_t), starts, sizeof(int32_t) * n_tiles,
+                                             sizeof(int32_t), B, cudaMemcpyDeviceToDevice, s));
+            k_set_i32<<<1, 1, 0, s>>>(g->offsets + B, (int32_t)N);
+            VUP_CHECK_LAUNCH();
+        }
+        if (g->ndim < 2) break;
+        // runs and chunks
+        const int64_t n_last = HL.n_last;
+        int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
+        k_run_flags<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, n_last, g->flags_scan);
+        VUP_CHECK_LAUNCH();
+        // the sort counts are dead once this layout's scatter (and the offsets copy) ran
         int32_t *excl = (int32_t *)g->sort_counts.p;
         st = scan_exclusive(g->flags_scan, excl, N, scratch, s);
         if (st != VUP_OK) return st;
-        k_run_build<<<rb, 256, 0, s>>>(g->perm, g->bins, N, n_last, g->flags_scan, excl, g->run_start,
-                                       g->run_rest, g->run_bin, g->hpt, g->n_runs);
+        k_run_build<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, n_last, g->flags_scan, excl, HL.run_start,
+                                       HL.run_rest, HL.run_bin, HL.hpt, HL.n_runs);
+        VUP_CHECK_LAUNCH();
+        k_run_encode<<<rb, 256, 0, s>>>(HL.run_start, HL.run_rest, HL.n_runs, g->ndim,
+                                        g->ndim == 3 ? g->n[1] : 1, HL.hpt);
         VUP_CHECK_LAUNCH();
         const int C = g->n_chunks;
-        k_chunks<<<(C + 1 + 127) / 128, 128, 0, s>>>(g->run_start, g->run_bin, g->n_runs, N, C,
-                                                      g->chunk_pt, g->chunk_run);
+        k_chunks<<<(C + 1 + 127) / 128, 128, 0, s>>>(HL.run_start, HL.run_bin, HL.n_runs, N, C, HL.chunk_pt,
+                                                      HL.chunk_run);
         VUP_CHECK_LAUNCH();
-        k_chunk_bins<<<(C + 127) / 128, 128, 0, s>>>(g->chunk_run, g->run_bin, C, g->chunk_bin);
+        k_chunk_bins<<<(C + 127) / 128, 128, 0, s>>>(HL.chunk_run, HL.run_bin, C, HL.chunk_bin);
         VUP_CHECK_LAUNCH();
     }
+    k_pick_layout<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->n_layouts > 1 ? g->hl[1].n_runs : nullptr, g->hist_sel);
+    VUP_CHECK_LAUNCH();
     g->have_tab[0][0] = g->have_tab[0][1] = g->have_tab[1][0] = g->have_tab[1][1] = 0;
     return VUP_OK;
 }

@@ -86,17 +86,28 @@ struct vup_grid_s {
     // counting-sort scratch
     DevBuf sort_counts, scan_tmp;
 
-    // histogram point stream (sorted order), runs and chunks
-    uint32_t *hpt = nullptr;       // [N] packed per-point word
-    int32_t *run_start = nullptr;  // [N + 1]
-    int32_t *run_rest = nullptr;   // [N]
-    int32_t *run_bin = nullptr;    // [N]
-    int32_t *n_runs = nullptr;     // [1] device
+    // histogram point streams.  Layout 0 gathers the last axis per point and
+    // forms runs over the other axes; on 2-D grids layout 1 swaps the roles
+    // (points ordered by (bin, a1, a0)).  The device picks the layout with
+    // fewer runs (hist_sel) after both are built.
+    struct HistLayout {
+        int last_axis = -1;            // axis gathered per point
+        int64_t n_last = 0;
+        int32_t *keys = nullptr;       // bin of the layout's flat index (layout 1: transposed bins)
+        int32_t *perm = nullptr;       // [N] sorted position -> layout flat index
+        uint32_t *hpt = nullptr;       // [N + 512] packed per-point word
+        int32_t *run_start = nullptr;  // [N + 1]
+        int32_t *run_rest = nullptr;   // [N]
+        int32_t *run_bin = nullptr;    // [N]
+        int32_t *n_runs = nullptr;     // [1] device
+        int32_t *chunk_pt = nullptr;   // [n_chunks + 1] chunk start (point index)
+        int32_t *chunk_run = nullptr;  // [n_chunks + 1] chunk start (run index)
+        int32_t *chunk_bin = nullptr;  // [n_chunks * 2] first / last bin of each chunk
+    } hl[2];
+    int n_layouts = 1;
+    int32_t *hist_sel = nullptr;   // [1] device: chosen layout
     int32_t *flags_scan = nullptr; // [N] scratch
     int32_t n_chunks = 0;
-    int32_t *chunk_pt = nullptr;   // [n_chunks + 1] chunk start (point index)
-    int32_t *chunk_run = nullptr;  // [n_chunks + 1] chunk start (run index)
-    int32_t *chunk_bin = nullptr;  // [n_chunks * 2] first / last bin of each chunk
 
     // power tables; orientation 0 = reduce over the last axis,
     // orientation 1 = reduce over axis 0 (2-D only, for the IPSA adjoint)
