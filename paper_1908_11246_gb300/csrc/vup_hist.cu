@@ -205,14 +205,22 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, in
         asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(wsl + (u & kOffMask)));
         return v;
     };
+    // words without flags carry nothing but the row byte offset (run codes sit
+    // on run-end words only), so the common path needs no masking
+    auto gather_raw = [&](uint32_t u) -> float {
+        float v;
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(wsl + u));
+        return v;
+    };
     auto group = [&](const uint4 v) {
-        const float a0 = gather(v.x), a1 = gather(v.y), a2 = gather(v.z), a3 = gather(v.w);
         if (((v.x | v.y | v.z | v.w) & kFlags) == 0) {
+            const float a0 = gather_raw(v.x), a1 = gather_raw(v.y), a2 = gather_raw(v.z), a3 = gather_raw(v.w);
             acc += a0;
             acc += a1;
             acc += a2;
             acc += a3;
         } else {
+            const float a0 = gather(v.x), a1 = gather(v.y), a2 = gather(v.z), a3 = gather(v.w);
             acc += a0;
             if (v.x & kFlags) run_end(v.x);
             acc += a1;
@@ -249,6 +257,7 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, in
             const int pa = lo & ~3;
             group(masked(*reinterpret_cast<const uint4 *>(wv + pa), pa, lo, hi));
         }
+#pragma unroll 2
         for (int pa = ga; pa < gb; pa += 4) group(*reinterpret_cast<const uint4 *>(wv + pa));
         if ((hi & 3) && gb >= ga) group(masked(*reinterpret_cast<const uint4 *>(wv + gb), gb, lo, hi));
         __syncwarp();
