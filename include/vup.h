@@ -170,6 +170,26 @@ vup_status vup_propagate_weights(vup_grid g, int64_t K, const float *W, double *
                                  float *hist, vup_stream_t stream);
 
 /*
+ * vup_propagate_weights without any device allocation.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc once they are
+ * running -- hosts with a fixed device-memory budget, allocators that forbid
+ * growth after start-up, or code embedded in a runtime that owns the device
+ * heap.  Inputs and outputs are exactly those of vup_propagate_weights (the
+ * caller still owns W and the outputs; the grid is created beforehand).
+ * Scratch: one device array of VUP_STATIC_SCRATCH_BYTES compiled into the
+ * library; every GPU that loads libvup holds it until the process exits.
+ * Each call needs K * (32 + 4 * n_bins) bytes of it at least; larger requests
+ * return VUP_ERR_INVALID_ARG before any work is queued.
+ * The first call on a device resolves the array's device address (set-up);
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents (nothing in it needs clearing): two
+ * calls whose work overlaps on the GPU race, so serialise them (one stream).
+ */
+#define VUP_STATIC_SCRATCH_BYTES (16u << 20)
+vup_status vup_propagate_weights_noalloc(vup_grid g, int64_t K, const float *W, double *moments_raw,
+                                         float *hist, vup_stream_t stream);
+
+/*
  * IPSA sensitivities (Sec. 5.2): derivatives of the raw moments M_j with
  * respect to each density's mu and sigma on every axis, for ndim == 2 grids
  * (and ndim == 1).  Gaussian and truncated-normal axes are differentiated

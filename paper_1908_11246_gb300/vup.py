@@ -25,7 +25,7 @@ PRECISIONS = {"fp64": VUP_FP64, "fp32": VUP_FP32, "bf16x3": VUP_BF16X3}
 # exported symbols declared in include/vup.h
 ABI_SYMBOLS = [
     "vup_grid_create", "vup_grid_destroy", "vup_eval_model", "vup_set_outputs", "vup_propagate",
-    "vup_propagate_weights", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_sync",
+    "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_sync",
     "vup_grid_info", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
     "vup_profile_read",
 ]
@@ -65,6 +65,7 @@ def lib():
         l.vup_set_outputs.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         l.vup_propagate.argtypes = [vp, C.POINTER(vup_densities), C.c_int, vp, vp, vp, vp]
         l.vup_propagate_weights.argtypes = [vp, i64, vp, vp, vp, vp]
+        l.vup_propagate_weights_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
         l.vup_ipsa_sensitivity.argtypes = [vp, C.POINTER(vup_densities), C.c_int, vp, vp, vp, vp]
         l.vup_propagate_batched.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vup_densities), C.c_int,
                                             C.POINTER(vp), C.POINTER(vp), vp]
@@ -153,6 +154,12 @@ def vup_propagate(h, dens, precision, moments_raw=None, moments_central=None, hi
 def vup_propagate_weights(h, W, moments_raw=None, hist=None, stream=None):
     _check(lib().vup_propagate_weights(h, int(W.shape[0]), _ptr(W), _ptr(moments_raw), _ptr(hist),
                                        _stream(stream)), "vup_propagate_weights")
+
+
+def vup_propagate_weights_noalloc(h, W, moments_raw=None, hist=None, stream=None):
+    """Same as vup_propagate_weights, with the library's fixed device scratch array."""
+    _check(lib().vup_propagate_weights_noalloc(h, int(W.shape[0]), _ptr(W), _ptr(moments_raw), _ptr(hist),
+                                               _stream(stream)), "vup_propagate_weights_noalloc")
 
 
 def vup_ipsa_sensitivity(h, dens, precision, dmu, dsigma, grad_moments=None, stream=None):
