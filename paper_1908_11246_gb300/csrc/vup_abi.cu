@@ -133,6 +133,7 @@ int vup_num_sms() {
 }
 
 int vup_hist_chunks_for(int64_t N);
+int vup_hist_parts_for(int64_t n_last, int n_bins);
 
 extern "C" const char *vup_status_string(vup_status s) {
     switch (s) {
@@ -160,10 +161,10 @@ static void free_grid(vup_grid g) {
     cudaFree(g->offsets);
     for (int l = 0; l < 2; ++l) {
         auto &L = g->hl[l];
-        if (l == 1) {
-            cudaFree(L.keys);
-            cudaFree(L.perm);
-        }
+        if (L.perm != g->perm) cudaFree(L.perm);
+        cudaFree(L.binsT);
+        cudaFree(L.keys_own);
+        cudaFree(L.koff);
         cudaFree(L.hpt);
         cudaFree(L.run_start);
         cudaFree(L.run_rest);
@@ -191,6 +192,7 @@ static void free_grid(vup_grid g) {
     devbuf_free(g->atab_lo);
     devbuf_free(g->partials);
     devbuf_free(g->hist_part);
+    devbuf_free(g->hist_direct);
     devbuf_free(g->ipsa_part);
     delete g;
 }
@@ -242,21 +244,20 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
         auto &L = g->hl[l];
         L.last_axis = l == 0 ? ndim - 1 : 0;
         L.n_last = g->n[L.last_axis];
-        if (l == 1) {
-            ALLOC(L.keys, sizeof(int32_t) * N);
-            ALLOC(L.perm, sizeof(int32_t) * N);
-        }
+        const int p_max = vup_hist_parts_for(L.n_last, 1);
+        if (l == 1) ALLOC(L.binsT, sizeof(int32_t) * N);
+        if (ndim >= 2) ALLOC(L.perm, sizeof(int32_t) * N);
+        if (l == 1 || p_max > 1) ALLOC(L.keys_own, sizeof(int32_t) * N);
         ALLOC(L.hpt, sizeof(uint32_t) * (N + 512));  // tail slack for whole staged windows
         ALLOC(L.run_start, sizeof(int32_t) * (N + 1));
         ALLOC(L.run_rest, sizeof(int32_t) * N);
         ALLOC(L.run_bin, sizeof(int32_t) * N);
         ALLOC(L.n_runs, sizeof(int32_t));
-        ALLOC(L.chunk_pt, sizeof(int32_t) * (C + 1));
-        ALLOC(L.chunk_run, sizeof(int32_t) * (C + 1));
-        ALLOC(L.chunk_bin, sizeof(int32_t) * 2 * C);
+        ALLOC(L.chunk_pt, sizeof(int32_t) * (p_max * C + 1));
+        ALLOC(L.chunk_run, sizeof(int32_t) * (p_max * C + 1));
+        ALLOC(L.chunk_bin, sizeof(int32_t) * 2 * p_max * C);
     }
-    g->hl[0].keys = g->bins;
-    g->hl[0].perm = g->perm;
+    if (ndim == 1) g->hl[0].perm = g->perm;
     ALLOC(g->hist_sel, sizeof(int32_t));
     ALLOC(g->flags_scan, sizeof(int32_t) * N);
     ALLOC(g->ydev_scale, sizeof(double));
@@ -367,7 +368,11 @@ static vup_status reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa) {
     if (nd >= 2) {
         const int64_t nct = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles(g->orient[0]));
         if ((st = devbuf_reserve(g->partials, sizeof(float) * 4 * K_pad * nct)) != VUP_OK) return st;
-        if ((st = devbuf_reserve(g->hist_part, sizeof(float) * 2 * K_pad * g->n_chunks)) != VUP_OK) return st;
+        if ((st = devbuf_reserve(g->hist_part, sizeof(float) * 2 * K_pad * g->n_chunks * g->hist_P)) != VUP_OK)
+            return st;
+        if (g->hist_P > 1 &&
+            (st = devbuf_reserve(g->hist_direct, sizeof(float) * (size_t)g->hist_P * K * g->B)) != VUP_OK)
+            return st;
         if (bf16) {
             size_t a = (size_t)K_pad * g->orient[0].R_pad + (ipsa ? (size_t)K_pad * g->orient[1].R_pad : 0);
             if ((st = devbuf_reserve(g->atab_hi, sizeof(__nv_bfloat16) * a)) != VUP_OK) return st;
@@ -515,7 +520,13 @@ extern "C" vup_status vup_grid_copy(vup_grid g, int which, void *dst_dev, size_t
     switch (which) {
     case 0: src = g->y; need = sizeof(double) * g->N; break;
     case 1: src = g->bins; need = sizeof(int32_t) * g->N; break;
-    case 2: src = g->perm; need = sizeof(int32_t) * g->N; break;
+    case 2: {
+        vup_status st = vup_natural_sort(g, (cudaStream_t)stream);
+        if (st != VUP_OK) return st;
+        src = g->perm;
+        need = sizeof(int32_t) * g->N;
+        break;
+    }
     case 3: src = g->offsets; need = sizeof(int32_t) * (g->B + 1); break;
     default: return VUP_ERR_INVALID_ARG;
     }

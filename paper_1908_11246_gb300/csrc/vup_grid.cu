@@ -14,9 +14,10 @@ namespace {
 
 constexpr int kSortTile = 2048;      // points per warp in the counting sort
 constexpr int kSortWarps = 4;        // warps per CTA in the counting sort
-// Packed sorted-point word: last-axis index << 7 (the byte offset of its row in
-// a 32-float shared-memory tile), run-end flag (bit 30), bin-end flag (bit 31).
-constexpr int kPtShift = 7;
+// Packed sorted-point word: the gathered-axis row inside its part << 8 (the
+// byte offset of its row in a 64-float shared-memory tile), run-end flag
+// (bit 30), key-end flag (bit 31).
+constexpr int kRowShift = 8;
 constexpr uint32_t kRunEnd = 1u << 30;
 constexpr uint32_t kBinEnd = 1u << 31;
 
@@ -155,15 +156,16 @@ __global__ void k_scale(const unsigned long long *ext, double *s_out) {
 // Eq. 4 bins: t = (y - ymin) / (ymax - ymin), bin = min(floor(t B), B - 1),
 // every operation correctly rounded and unfused, as in the FP64 oracle.
 // Also counts points per (bin, warp tile) for the stable counting sort.
+// The CTA has blockDim.x / 32 warps, each owning one tile of kSortTile points.
 __global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
                              const unsigned long long *ext, int32_t *__restrict__ bins,
                              int32_t *__restrict__ counts, int64_t n_tiles) {
-    extern __shared__ int32_t s_cnt[];  // [kSortWarps][B]
+    extern __shared__ int32_t s_cnt[];  // [warps][B]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t *cnt = s_cnt + warp * B;
     for (int b = lane; b < B; b += 32) cnt[b] = 0;
     __syncwarp();
-    const int64_t tile = (int64_t)blockIdx.x * kSortWarps + warp;
+    const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     double ymin, ymax;
     read_range(ext, ymin, ymax);
     const double range = __dsub_rn(ymax, ymin);
@@ -187,21 +189,21 @@ __global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
     }
 }
 
-// Points per (bin, warp tile) of an already binned key array.
-__global__ void k_count(const int32_t *__restrict__ keys, int64_t N, int B, int32_t *__restrict__ counts,
+// Points per (key, warp tile) of a key array with key < Bk.
+__global__ void k_count(const int32_t *__restrict__ keys, int64_t N, int Bk, int32_t *__restrict__ counts,
                         int64_t n_tiles) {
-    extern __shared__ int32_t s_cnt[];  // [kSortWarps][B]
+    extern __shared__ int32_t s_cnt[];  // [warps][Bk]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int32_t *cnt = s_cnt + warp * B;
-    for (int b = lane; b < B; b += 32) cnt[b] = 0;
+    int32_t *cnt = s_cnt + warp * Bk;
+    for (int b = lane; b < Bk; b += 32) cnt[b] = 0;
     __syncwarp();
-    const int64_t tile = (int64_t)blockIdx.x * kSortWarps + warp;
+    const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (tile < n_tiles) {
         const int64_t i0 = tile * kSortTile;
         const int64_t i1 = min(N, i0 + kSortTile);
         for (int64_t i = i0 + lane; i < i1; i += 32) atomicAdd(&cnt[keys[i]], 1);
         __syncwarp();
-        for (int b = lane; b < B; b += 32) counts[(int64_t)b * n_tiles + tile] = cnt[b];
+        for (int b = lane; b < Bk; b += 32) counts[(int64_t)b * n_tiles + tile] = cnt[b];
     }
 }
 
@@ -209,15 +211,37 @@ __global__ void k_count(const int32_t *__restrict__ keys, int64_t N, int B, int3
 __global__ void k_transpose_i32(const int32_t *__restrict__ in, int64_t n0, int64_t n1, int32_t *__restrict__ out) {
     __shared__ int32_t t[32][33];
     const int64_t a0b = (int64_t)blockIdx.y * 32, a1b = (int64_t)blockIdx.x * 32;
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int64_t a0 = a0b + y, a1 = a1b + threadIdx.x;
-        if (a0 < n0 && a1 < n1) t[y][threadIdx.x] = in[a0 * n1 + a1];
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int64_t a0 = a0b + yy, a1 = a1b + threadIdx.x;
+        if (a0 < n0 && a1 < n1) t[yy][threadIdx.x] = in[a0 * n1 + a1];
     }
     __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int64_t a1 = a1b + y, a0 = a0b + threadIdx.x;
-        if (a0 < n0 && a1 < n1) out[a1 * n0 + a0] = t[threadIdx.x][y];
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int64_t a1 = a1b + yy, a0 = a0b + threadIdx.x;
+        if (a0 < n0 && a1 < n1) out[a1 * n0 + a0] = t[threadIdx.x][yy];
     }
+}
+
+// Sort key of a layout: the part of the gathered axis first, then the bin.
+__global__ void k_make_keys(const int32_t *__restrict__ bins, int64_t N, int64_t n_last, int64_t part_rows, int B,
+                            int32_t *__restrict__ keys) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
+        keys[j] = (int32_t)((j % n_last) / part_rows) * B + bins[j];
+}
+
+// Bin offsets of the model matrix from a layout's key offsets:
+// offsets[b] = sum over parts of the points of that part in bins below b.
+__global__ void k_natural_offsets(const int32_t *__restrict__ koff, int P, int B, int64_t N,
+                                  int32_t *__restrict__ offsets) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > B) return;
+    if (b == B) {
+        offsets[B] = (int32_t)N;
+        return;
+    }
+    int32_t s = 0;
+    for (int p = 0; p < P; ++p) s += koff[p * B + b] - koff[p * B];
+    offsets[b] = s;
 }
 
 // The histogram walks the layout with fewer runs (less per-run work).
@@ -226,16 +250,16 @@ __global__ void k_pick_layout(const int32_t *n_runs0, const int32_t *n_runs1, in
 }
 
 // Stable scatter: each warp walks its tile in order, 32 points at a time;
-// equal bins inside a step are ranked by lane with __match_any_sync.
-__global__ void k_sort_scatter(const int32_t *__restrict__ bins, int64_t N, int B,
+// equal keys inside a step are ranked by lane with __match_any_sync.
+__global__ void k_sort_scatter(const int32_t *__restrict__ keys, int64_t N, int Bk,
                                const int32_t *__restrict__ starts, int64_t n_tiles,
                                int32_t *__restrict__ perm) {
     extern __shared__ int32_t s_cnt[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int32_t *cnt = s_cnt + warp * B;
-    const int64_t tile = (int64_t)blockIdx.x * kSortWarps + warp;
+    int32_t *cnt = s_cnt + warp * Bk;
+    const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (tile >= n_tiles) return;
-    for (int b = lane; b < B; b += 32) cnt[b] = starts[(int64_t)b * n_tiles + tile];
+    for (int b = lane; b < Bk; b += 32) cnt[b] = starts[(int64_t)b * n_tiles + tile];
     __syncwarp();
     const int64_t i0 = tile * kSortTile;
     const int64_t i1 = min(N, i0 + kSortTile);
@@ -244,7 +268,7 @@ __global__ void k_sort_scatter(const int32_t *__restrict__ bins, int64_t N, int 
         const int64_t i = base + lane;
         const bool v = i < i1;
         const unsigned act = __ballot_sync(0xffffffffu, v);
-        int32_t b = v ? bins[i] : -1;
+        int32_t b = v ? keys[i] : -1;
         unsigned peers = __match_any_sync(0xffffffffu, b);
         peers &= act;
         int32_t pos = 0;
@@ -314,27 +338,30 @@ __global__ void k_scan_add(int32_t *__restrict__ out, int64_t L, const int32_t *
 }
 
 // ---- runs and chunks for the segmented histogram --------------------------
-// A run is a maximal stretch of sorted points sharing the output bin and every
-// axis index but the last one.  hpt[t] packs the last-axis index of the t-th
-// sorted point and the run-end / bin-end flags (layout above).
-__global__ void k_run_flags(const int32_t *__restrict__ perm, const int32_t *__restrict__ bins,
+// A run is a maximal stretch of sorted points sharing the sort key (part and
+// bin) and every axis index but the gathered one.  hpt[t] packs the t-th
+// sorted point's row inside its part of the gathered axis (<< shift; the
+// row's byte offset in a shared-memory tile of 2^shift-byte rows) and the
+// run-end / key-end flags (bits 30, 31).
+__global__ void k_run_flags(const int32_t *__restrict__ perm, const int32_t *__restrict__ keys,
                             int64_t N, int64_t n_last, int32_t *__restrict__ flags) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
          t += (int64_t)gridDim.x * blockDim.x) {
         int32_t f = 1;
         if (t > 0) {
             int32_t i = perm[t], ip = perm[t - 1];
-            f = (bins[i] != bins[ip]) || (i / n_last != ip / n_last);
+            f = (keys[i] != keys[ip]) || (i / n_last != ip / n_last);
         }
         flags[t] = f;
     }
 }
 
-__global__ void k_run_build(const int32_t *__restrict__ perm, const int32_t *__restrict__ bins,
-                            int64_t N, int64_t n_last, const int32_t *__restrict__ flags,
-                            const int32_t *__restrict__ excl, int32_t *__restrict__ run_start,
-                            int32_t *__restrict__ run_rest, int32_t *__restrict__ run_bin,
-                            uint32_t *__restrict__ hpt, int32_t *__restrict__ n_runs) {
+__global__ void k_run_build(const int32_t *__restrict__ perm, const int32_t *__restrict__ keys,
+                            int64_t N, int64_t n_last, int64_t part_rows, int shift,
+                            const int32_t *__restrict__ flags, const int32_t *__restrict__ excl,
+                            int32_t *__restrict__ run_start, int32_t *__restrict__ run_rest,
+                            int32_t *__restrict__ run_bin, uint32_t *__restrict__ hpt,
+                            int32_t *__restrict__ n_runs) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = perm[t];
@@ -342,11 +369,13 @@ __global__ void k_run_build(const int32_t *__restrict__ perm, const int32_t *__r
         if (flags[t]) {
             run_start[rid] = (int32_t)t;
             run_rest[rid] = (int32_t)(i / n_last);
-            run_bin[rid] = bins[i];
+            run_bin[rid] = keys[i];
         }
         const bool last = (t == N - 1) || flags[t + 1];
-        const bool bin_last = (t == N - 1) || bins[perm[t + 1]] != bins[i];
-        hpt[t] = ((uint32_t)(i % n_last) << kPtShift) | (last ? kRunEnd : 0u) | (bin_last ? kBinEnd : 0u);
+        const bool key_last = (t == N - 1) || keys[perm[t + 1]] != keys[i];
+        const int64_t a = i % n_last;
+        const uint32_t row = (uint32_t)(a - (a / part_rows) * part_rows);
+        hpt[t] = (row << shift) | (last ? kRunEnd : 0u) | (key_last ? kBinEnd : 0u);
         if (t == N - 1) {
             n_runs[0] = rid + 1;
             run_start[rid + 1] = (int32_t)N;
@@ -355,52 +384,58 @@ __global__ void k_run_build(const int32_t *__restrict__ perm, const int32_t *__r
 }
 
 // The run-end word of run r also carries the rest-axis index of run r + 4
-// (the histogram kernel loads that run's factor four runs ahead): for 2-D
-// grids the 15-bit index sits in bits 0..6 and 22..29; for 3-D grids a0
-// (7 bits) in bits 0..6 and a1 (8 bits) in bits 22..29.  Zero past the end.
+// (the histogram kernel loads that run's factor four runs ahead) in the 15
+// bits beside the row field: `shift` low bits (0 .. shift-1) and 15 - shift
+// high bits (shift + 15 .. 29).  2-D grids split the rest index itself; 3-D
+// grids put a0 in the low field and a1 in the high field.  Zero past the end.
 constexpr int kRunAhead = 4;
 __global__ void k_run_encode(const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_rest,
-                             const int32_t *__restrict__ n_runs_p, int ndim, int64_t n1,
+                             const int32_t *__restrict__ n_runs_p, int ndim, int64_t n1, int shift,
                              uint32_t *__restrict__ hpt) {
     const int32_t n_runs = n_runs_p[0];
+    const uint32_t lo_mask = (1u << shift) - 1u;
+    const uint32_t hi_mask = (1u << (15 - shift)) - 1u;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_runs;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ra = r + kRunAhead;
         uint32_t code = 0;
         if (ra < n_runs) {
             const int32_t rest = run_rest[ra];
-            uint32_t lo7, hi8;
+            uint32_t lo, hi;
             if (ndim == 3) {
-                lo7 = (uint32_t)(rest / n1);
-                hi8 = (uint32_t)(rest % n1);
+                lo = (uint32_t)(rest / n1);
+                hi = (uint32_t)(rest % n1);
             } else {
-                lo7 = (uint32_t)rest & 0x7fu;
-                hi8 = (uint32_t)rest >> 7;
+                lo = (uint32_t)rest & lo_mask;
+                hi = (uint32_t)rest >> shift;
             }
-            code = (lo7 & 0x7fu) | ((hi8 & 0xffu) << 22);
+            code = (lo & lo_mask) | ((hi & hi_mask) << (shift + 15));
         }
         hpt[run_start[r + 1] - 1] |= code;
     }
 }
 
-// Chunk c starts at the first run whose first point is >= c N / C.
-__global__ void k_chunks(const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_bin,
-                         const int32_t *__restrict__ n_runs_p, int64_t N, int C,
+// Chunks, C per part: chunk c of part p starts at the first run whose first
+// point is >= lo_p + (hi_p - lo_p) c / C, [lo_p, hi_p) being the part's points.
+__global__ void k_chunks(const int32_t *__restrict__ run_start, const int32_t *__restrict__ n_runs_p,
+                         const int32_t *__restrict__ koff, int B, int P, int C,
                          int32_t *__restrict__ chunk_pt, int32_t *__restrict__ chunk_run) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > C) return;
+    if (c > P * C) return;
     const int32_t n_runs = n_runs_p[0];
     int32_t r;
-    if (c == C) {
+    if (c == P * C) {
         r = n_runs;
     } else {
-        const int64_t target = (N * (int64_t)c) / C;
-        int32_t lo = 0, hi = n_runs;  // first r in [0, n_runs] with run_start[r] >= target
-        while (lo < hi) {
-            int32_t mid = (lo + hi) >> 1;
-            if (run_start[mid] >= target) hi = mid; else lo = mid + 1;
+        const int p = c / C, cc = c - p * C;
+        const int64_t lo = koff[p * B], hi = koff[(p + 1) * B];
+        const int64_t target = lo + ((hi - lo) * (int64_t)cc) / C;
+        int32_t a = 0, b = n_runs;  // first r in [0, n_runs] with run_start[r] >= target
+        while (a < b) {
+            int32_t mid = (a + b) >> 1;
+            if (run_start[mid] >= target) b = mid; else a = mid + 1;
         }
-        r = lo;
+        r = a;
     }
     chunk_run[c] = r;
     chunk_pt[c] = run_start[r];
@@ -549,12 +584,60 @@ vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta, 
 }
 
 int vup_hist_chunks_for(int64_t N);
+int vup_hist_parts_for(int64_t n_last, int n_bins);
+
+// Warps per CTA of the counting-sort kernels for a key space of Bk keys (the
+// per-warp counters of Bk ints must fit 128 KB of shared memory).
+static int sort_warps(int Bk) { return std::max(1, std::min(kSortWarps, 32768 / std::max(Bk, 1))); }
+
+// Stable counting sort of `keys` (values < Bk) into perm; key offsets to koff
+// (Bk + 1 entries) when koff is not null.  `counts` must hold 2 Bk n_tiles + 8.
+static vup_status counting_sort(vup_grid g, const int32_t *keys, int Bk, int32_t *perm, int32_t *koff,
+                                int32_t *counts, int32_t *scratch, bool counts_ready, cudaStream_t s) {
+    const int64_t N = g->N;
+    const int64_t n_tiles = ceil_div64(N, kSortTile);
+    const int64_t L = (int64_t)Bk * n_tiles;
+    int32_t *starts = counts + L + 4;
+    const int nw = sort_warps(Bk);
+    const size_t smem = sizeof(int32_t) * (size_t)Bk * nw;
+    const unsigned blocks = (unsigned)ceil_div64(n_tiles, nw);
+    if (smem > 48 * 1024) {
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    if (!counts_ready) {
+        k_count<<<blocks, 32 * nw, smem, s>>>(keys, N, Bk, counts, n_tiles);
+        VUP_CHECK_LAUNCH();
+    }
+    vup_status st = scan_exclusive(counts, starts, L, scratch, s);
+    if (st != VUP_OK) return st;
+    k_sort_scatter<<<blocks, 32 * nw, smem, s>>>(keys, N, Bk, starts, n_tiles, perm);
+    VUP_CHECK_LAUNCH();
+    if (koff) {
+        // koff[b] = starts[b * n_tiles], koff[Bk] = N
+        VUP_CHECK_CUDA(cudaMemcpy2DAsync(koff, sizeof(int32_t), starts, sizeof(int32_t) * n_tiles, sizeof(int32_t),
+                                         Bk, cudaMemcpyDeviceToDevice, s));
+        k_set_i32<<<1, 1, 0, s>>>(koff + Bk, (int32_t)N);
+        VUP_CHECK_LAUNCH();
+    }
+    return VUP_OK;
+}
+
+// The CSR form of the one-hot model matrix (points stably sorted by bin) for
+// grids whose histogram runs on a layout stream; built when first asked for.
+vup_status vup_natural_sort(vup_grid g, cudaStream_t s) {
+    if (g->natural_valid) return VUP_OK;
+    int32_t *scratch = (int32_t *)g->scan_tmp.p;
+    vup_status st = counting_sort(g, g->bins, g->B, g->perm, nullptr, (int32_t *)g->sort_counts.p, scratch, false, s);
+    if (st != VUP_OK) return st;
+    g->natural_valid = 1;
+    return VUP_OK;
+}
 
 vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     const int64_t N = g->N;
     const int B = g->B;
-    // range, bins, sort (+2 scans of up to 3 launches), runs, chunks
-    VUP_PROF("range_bins_sort_runs", s, g->ndim == 2 ? 32 : (g->ndim == 3 ? 18 : 9));
+    VUP_PROF("range_bins_sort_runs", s, g->ndim == 2 ? 36 : 20);
     // exact range of y
     VUP_CHECK_CUDA(cudaMemsetAsync(g->ext, 0xff, sizeof(unsigned long long), s));
     VUP_CHECK_CUDA(cudaMemsetAsync(g->ext + 1, 0x00, sizeof(unsigned long long), s));
@@ -564,73 +647,95 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     k_scale<<<1, 1, 0, s>>>(g->ext, g->ydev_scale);
     VUP_CHECK_LAUNCH();
 
-    // bins + stable counting sort (natural order), offsets
+    // parts of each layout's gathered axis for this bin count
+    int Bk_max = B;
+    g->hist_P = 1;
+    if (g->ndim >= 2) {
+        for (int l = 0; l < g->n_layouts; ++l) {
+            auto &HL = g->hl[l];
+            HL.P = vup_hist_parts_for(HL.n_last, B);
+            HL.part_rows = ceil_div64(HL.n_last, HL.P);
+            Bk_max = std::max(Bk_max, HL.P * B);
+            g->hist_P = std::max(g->hist_P, HL.P);
+            if (HL.koff_cap < HL.P * B + 1) {
+                cudaFree(HL.koff);
+                HL.koff = nullptr;
+                VUP_CHECK_CUDA(cudaMalloc(&HL.koff, sizeof(int32_t) * (HL.P * B + 1)));
+                HL.koff_cap = HL.P * B + 1;
+            }
+        }
+    }
     const int64_t n_tiles = ceil_div64(N, kSortTile);
-    const int64_t L = (int64_t)B * n_tiles;
-    vup_status st = devbuf_reserve(g->sort_counts,
-                                   sizeof(int32_t) * (size_t)std::max<int64_t>(2 * L + 8, N + 8));
+    const int64_t Lmax = (int64_t)Bk_max * n_tiles;
+    vup_status st = devbuf_reserve(g->sort_counts, sizeof(int32_t) * (size_t)std::max<int64_t>(2 * Lmax + 8, N + 8));
     if (st != VUP_OK) return st;
-    st = devbuf_reserve(g->scan_tmp, sizeof(int32_t) * (size_t)scan_scratch_ints(std::max<int64_t>(L, N)));
+    st = devbuf_reserve(g->scan_tmp, sizeof(int32_t) * (size_t)scan_scratch_ints(std::max<int64_t>(Lmax, N)));
     if (st != VUP_OK) return st;
     int32_t *scratch = (int32_t *)g->scan_tmp.p;
     int32_t *counts = (int32_t *)g->sort_counts.p;
-    int32_t *starts = counts + L + 4;
-    const size_t smem = sizeof(int32_t) * (size_t)B * kSortWarps;
-    const unsigned sblocks = (unsigned)ceil_div64(n_tiles, kSortWarps);
-    if (smem > 48 * 1024) {
-        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_bins_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+
+    // bins (Eq. 4), counted per tile for the sort by bin
+    {
+        const int nw = sort_warps(B);
+        const size_t smem = sizeof(int32_t) * (size_t)B * nw;
+        if (smem > 48 * 1024)
+            VUP_CHECK_CUDA(cudaFuncSetAttribute(k_bins_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_bins_count<<<(unsigned)ceil_div64(n_tiles, nw), 32 * nw, smem, s>>>(g->y, N, B, g->ext, g->bins, counts,
+                                                                              n_tiles);
+        VUP_CHECK_LAUNCH();
     }
-    for (int l = 0; l < g->n_layouts; ++l) {
-        auto &HL = g->hl[l];
-        if (l == 0) {
-            k_bins_count<<<sblocks, 32 * kSortWarps, smem, s>>>(g->y, N, B, g->ext, g->bins, counts, n_tiles);
-            VUP_CHECK_LAUNCH();
-        } else {
-            // layout 1 (2-D): keys in transposed order, j = a1 * n0 + a0
-            dim3 tg((unsigned)ceil_div64(g->n[1], 32), (unsigned)ceil_div64(g->n[0], 32));
-            k_transpose_i32<<<tg, dim3(32, 8), 0, s>>>(g->bins, g->n[0], g->n[1], HL.keys);
-            VUP_CHECK_LAUNCH();
-            k_count<<<sblocks, 32 * kSortWarps, smem, s>>>(HL.keys, N, B, counts, n_tiles);
-            VUP_CHECK_LAUNCH();
-        }
-        st = scan_exclusive(counts, starts, L, scratch, s);
+    g->natural_valid = 0;
+    if (g->ndim == 1) {
+        // the 1-D path walks the model matrix in CSR form directly
+        st = counting_sort(g, g->bins, B, g->perm, g->offsets, counts, scratch, true, s);
         if (st != VUP_OK) return st;
-        k_sort_scatter<<<sblocks, 32 * kSortWarps, smem, s>>>(HL.keys, N, B, starts, n_tiles, HL.perm);
-        VUP_CHECK_LAUNCH();
-        if (l == 0) {
-            // offsets[b] = starts[b * n_tiles], offsets[B] = N (identical for every layout)
-            VUP_CHECK_CUDA(cudaMemcpy2DAsync(g->offsets, sizeof(int32_t), starts, sizeof(int32_t) * n_tiles,
-                                             sizeof(int32_t), B, cudaMemcpyDeviceToDevice, s));
-            k_set_i32<<<1, 1, 0, s>>>(g->offsets + B, (int32_t)N);
-            VUP_CHECK_LAUNCH();
-        }
-        if (g->ndim < 2) break;
-        // runs and chunks
-        const int64_t n_last = HL.n_last;
-        int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
-        k_run_flags<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, n_last, g->flags_scan);
-        VUP_CHECK_LAUNCH();
-        // the sort counts are dead once this layout's scatter (and the offsets copy) ran
-        int32_t *excl = (int32_t *)g->sort_counts.p;
-        st = scan_exclusive(g->flags_scan, excl, N, scratch, s);
-        if (st != VUP_OK) return st;
-        k_run_build<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, n_last, g->flags_scan, excl, HL.run_start,
-                                       HL.run_rest, HL.run_bin, HL.hpt, HL.n_runs);
-        VUP_CHECK_LAUNCH();
-        k_run_encode<<<rb, 256, 0, s>>>(HL.run_start, HL.run_rest, HL.n_runs, g->ndim,
-                                        g->ndim == 3 ? g->n[1] : 1, HL.hpt);
-        VUP_CHECK_LAUNCH();
+        g->natural_valid = 1;
+    } else {
         const int C = g->n_chunks;
-        k_chunks<<<(C + 1 + 127) / 128, 128, 0, s>>>(HL.run_start, HL.run_bin, HL.n_runs, N, C, HL.chunk_pt,
-                                                      HL.chunk_run);
+        for (int l = 0; l < g->n_layouts; ++l) {
+            auto &HL = g->hl[l];
+            const int32_t *src = g->bins;
+            if (l == 1) {  // transposed order, j = a1 * n0 + a0
+                dim3 tg((unsigned)ceil_div64(g->n[1], 32), (unsigned)ceil_div64(g->n[0], 32));
+                k_transpose_i32<<<tg, dim3(32, 8), 0, s>>>(g->bins, g->n[0], g->n[1], HL.binsT);
+                VUP_CHECK_LAUNCH();
+                src = HL.binsT;
+            }
+            HL.keys = const_cast<int32_t *>(src);
+            if (HL.P > 1) {
+                k_make_keys<<<blocks, 256, 0, s>>>(src, N, HL.n_last, HL.part_rows, B, HL.keys_own);
+                VUP_CHECK_LAUNCH();
+                HL.keys = HL.keys_own;
+            }
+            const int Bk = HL.P * B;
+            st = counting_sort(g, HL.keys, Bk, HL.perm, HL.koff, counts, scratch, false, s);
+            if (st != VUP_OK) return st;
+            // runs and chunks
+            const int64_t n_last = HL.n_last;
+            int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
+            k_run_flags<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, n_last, g->flags_scan);
+            VUP_CHECK_LAUNCH();
+            int32_t *excl = counts;  // the sort counts are dead once the scatter ran
+            st = scan_exclusive(g->flags_scan, excl, N, scratch, s);
+            if (st != VUP_OK) return st;
+            k_run_build<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, n_last, HL.part_rows, kRowShift, g->flags_scan, excl,
+                                           HL.run_start, HL.run_rest, HL.run_bin, HL.hpt, HL.n_runs);
+            VUP_CHECK_LAUNCH();
+            k_run_encode<<<rb, 256, 0, s>>>(HL.run_start, HL.run_rest, HL.n_runs, g->ndim, g->ndim == 3 ? g->n[1] : 1,
+                                            kRowShift, HL.hpt);
+            VUP_CHECK_LAUNCH();
+            const int PC = HL.P * C;
+            k_chunks<<<(PC + 1 + 127) / 128, 128, 0, s>>>(HL.run_start, HL.n_runs, HL.koff, B, HL.P, C, HL.chunk_pt,
+                                                           HL.chunk_run);
+            VUP_CHECK_LAUNCH();
+            k_chunk_bins<<<(PC + 127) / 128, 128, 0, s>>>(HL.chunk_run, HL.run_bin, PC, HL.chunk_bin);
+            VUP_CHECK_LAUNCH();
+        }
+        k_natural_offsets<<<(B + 1 + 127) / 128, 128, 0, s>>>(g->hl[0].koff, g->hl[0].P, B, N, g->offsets);
         VUP_CHECK_LAUNCH();
-        k_chunk_bins<<<(C + 127) / 128, 128, 0, s>>>(HL.chunk_run, HL.run_bin, C, HL.chunk_bin);
+        k_pick_layout<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->n_layouts > 1 ? g->hl[1].n_runs : nullptr, g->hist_sel);
         VUP_CHECK_LAUNCH();
     }
-    k_pick_layout<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->n_layouts > 1 ? g->hl[1].n_runs : nullptr, g->hist_sel);
-    VUP_CHECK_LAUNCH();
     g->have_tab[0][0] = g->have_tab[0][1] = g->have_tab[1][0] = g->have_tab[1][1] = 0;
     return VUP_OK;
 }

@@ -3,19 +3,23 @@
 // bin b.  The one-hot model matrix of Eq. MUP is applied as a segmented
 // reduction over the grid points pre-sorted by bin ("sort and sum").
 //
-// Layout: lanes of a warp are 32 densities k; every lane walks the same
-// sorted point stream, so control flow is uniform and the factor gathers hit
-// 32 consecutive shared-memory words (conflict-free).  Points are grouped in
-// runs that share the bin and every axis index but the gathered ("last")
-// one: inside a run only the last-axis factor is gathered, from a shared-
-// memory tile; the product with the other axes' factors is applied once per
-// run.  Those factors are loaded four runs ahead: the run-end word of run r
-// carries the rest index of run r + 4.  The point stream is staged into
-// shared memory with bulk asynchronous copies (cp.async.bulk + mbarrier) and
-// read four points per broadcast load.  Each warp owns a chunk of runs; bins
-// cut by chunk boundaries are written as partials and summed by a
-// deterministic fix-up kernel.  On 2-D grids two layouts exist (either axis
-// gathered); the device uses the one with fewer runs.
+// Layout: a warp serves 64 densities, two per lane; every lane walks the same
+// sorted point stream, so control flow is uniform and one 8-byte gather per
+// lane (64 consecutive shared-memory words per warp, conflict-free) yields two
+// distribution-points.  Points are grouped in runs that share the sort key
+// and every axis index but the gathered one: inside a run only the gathered
+// axis' factor is read, from a shared-memory tile; the product with the other
+// axes' factors is applied once per run.  Those factors are loaded four runs
+// ahead: the run-end word of run r carries the rest index of run r + 4.  The
+// point stream is staged into shared memory with bulk asynchronous copies
+// (cp.async.bulk + mbarrier) and read four points per broadcast load.
+//
+// The gathered axis is cut into P parts so that one part's 64-density tile
+// fits in shared memory; the stream is sorted by (part, bin) and every part
+// is chunked separately.  Each warp owns a chunk; bins cut by chunk
+// boundaries are written as partials, and a reduction kernel sums partials
+// and parts in a fixed order (deterministic).  On 2-D grids two layouts exist
+// (either axis gathered); the device uses the one with fewer runs.
 #include "vup_internal.cuh"
 
 #include <algorithm>
@@ -23,9 +27,10 @@
 namespace {
 
 constexpr int kHistWarps = 32;
-constexpr int kKT = 32;                      // densities per k-tile (one per lane)
+constexpr int kKT = 64;                      // densities per k-tile (two per lane)
 constexpr int kWin = 128;                    // sorted-point words per staging buffer
-constexpr uint32_t kOffMask = 0x7fffu << 7;  // gathered-axis row byte offset (index << 7)
+constexpr int kMaxPartRows = 704;            // gathered-axis rows per shared-memory tile
+constexpr uint32_t kOffMask = 0x7fffu << 8;  // row byte offset in a 256-byte-row tile
 constexpr uint32_t kRunEnd = 1u << 30, kBinEnd = 1u << 31;
 constexpr uint32_t kFlags = kRunEnd | kBinEnd;
 constexpr uint32_t kSpin = 1u << 26;
@@ -35,23 +40,25 @@ struct LayoutArgs {
     const uint32_t *hpt;
     const int32_t *run_start, *run_rest, *run_bin;
     const int32_t *chunk_pt, *chunk_run, *chunk_bin;
-    const float *g_last;  // factor table of the gathered axis  [n_last][K_pad]
-    const float *g0, *g1; // rest-axis factor tables (g1 only for 3-D)
-    int64_t n_last;
-    int64_t n1;           // size of the second rest axis (3-D)
+    const int32_t *koff;   // key offsets [P * B + 1]
+    const float *g_last;   // factor table of the gathered axis  [n_last][K_pad]
+    const float *g0, *g1;  // rest-axis factor tables (g1 only for 3-D)
+    int64_t n_last, part_rows;
+    int64_t n1;            // size of the second rest axis (3-D)
+    int P;
 };
 
 struct HistArgs {
     LayoutArgs L0, L1;
     const int32_t *sel;   // device: chosen layout
-    const int32_t *offsets;
     const DensStats *ds;
     int ndim;
     int64_t K, K_pad;
     int B;
-    int C;                // chunks per k-tile
+    int C;                // chunks per part
     float *hist;          // [K][B]
-    float *part;          // [C][2][K_pad]
+    float *part;          // [P * C][2][K_pad]
+    float *direct;        // [P][K][B] (P > 1)
     int *dstatus;
 };
 
@@ -91,50 +98,84 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
-// Shared memory of k_hist_smem: the gathered-axis factor tile [n_last + 1][32]
-// (the extra row is zero; foreign points of a chunk's first and last group
-// point at it), per warp 2 staging buffers of kWin point words, 2 mbarriers
-// per warp.
-__host__ __device__ inline size_t hist_tile_bytes(int64_t n_last) { return (size_t)((n_last + 1) * 128); }
+// Shared memory of k_hist_smem: the part's gathered-axis factor tile
+// [rows + 1][64] (the extra row is zero; foreign points of a chunk's first
+// and last group point at it), per warp 2 staging buffers of kWin point
+// words, 2 mbarriers per warp.
+__host__ __device__ inline size_t hist_tile_bytes(int64_t rows) { return (size_t)((rows + 1) * kKT * 4); }
 __host__ __device__ inline size_t hist_warp_bytes() { return (size_t)2 * kWin * 4; }
-__host__ __device__ inline size_t hist_smem_bytes(int64_t n_last) {
-    return hist_tile_bytes(n_last) + kHistWarps * hist_warp_bytes() + kHistWarps * 2 * sizeof(uint64_t);
+__host__ __device__ inline size_t hist_smem_bytes(int64_t rows) {
+    return hist_tile_bytes(rows) + kHistWarps * hist_warp_bytes() + kHistWarps * 2 * sizeof(uint64_t);
+}
+
+// Store the finished sums of key `key` for this lane's two densities.
+struct Flusher {
+    const HistArgs &A;
+    const LayoutArgs &H;
+    int c, p;
+    int32_t p0, p1, first_key;
+    int64_t k;
+    float2 invZ;
+    __device__ __forceinline__ void operator()(int32_t key, float2 v) const {
+        const float2 val = make_float2(v.x * invZ.x, v.y * invZ.y);
+        const bool shared = H.koff[key] < p0 || H.koff[key + 1] > p1;
+        if (shared) {
+            const int side = (key == first_key) ? 0 : 1;
+            *reinterpret_cast<float2 *>(A.part + ((int64_t)c * 2 + side) * A.K_pad + k) = val;
+        } else {
+            const int b = key - p * A.B;
+            float *out = H.P > 1 ? A.direct + (int64_t)p * A.K * A.B : A.hist;
+            if (k < A.K) out[k * A.B + b] = val.x;
+            if (k + 1 < A.K) out[(k + 1) * A.B + b] = val.y;
+        }
+    }
+};
+
+__device__ __forceinline__ float2 load_inv_z(const HistArgs &A, int64_t k) {
+    float2 r = make_float2(0.f, 0.f);
+    for (int q = 0; q < 2; ++q) {
+        if (k + q < A.K) {
+            double z = 1.0;
+            for (int d = 0; d < A.ndim; ++d) z *= A.ds[(k + q) * A.ndim + d].invZ;
+            if (q == 0) r.x = (float)z; else r.y = (float)z;
+        }
+    }
+    return r;
 }
 
 template <int NF>
-__global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, int64_t n_tile_rows) {
+__global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, int64_t tile_rows, int G) {
     extern __shared__ __align__(128) uint8_t sm[];
     const LayoutArgs H = pick(A);
+    const int p = blockIdx.x / G, cg = blockIdx.x - p * G;
+    if (p >= H.P) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k0 = (int64_t)blockIdx.y * kKT;
-    const int64_t k = k0 + lane;
+    const int64_t k = k0 + 2 * lane;
     float *ws = reinterpret_cast<float *>(sm);
-    const size_t tb = hist_tile_bytes(n_tile_rows);
+    const size_t tb = hist_tile_bytes(tile_rows);
     uint32_t *win = reinterpret_cast<uint32_t *>(sm + tb + (size_t)warp * hist_warp_bytes());
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + tb + kHistWarps * hist_warp_bytes()) + 2 * warp;
 
-    // gathered-axis factor tile of this k-tile (16-byte asynchronous copies) + zero row
-    for (int64_t e = threadIdx.x; e < H.n_last * 8; e += blockDim.x) {
-        const int64_t a = e >> 3, c = e & 7;
-        cp_async16(ws + a * 32 + c * 4, H.g_last + a * A.K_pad + k0 + c * 4);
+    // this part's rows of the gathered-axis factor table (16-byte asynchronous
+    // copies) + a zero row
+    const int64_t row0 = (int64_t)p * H.part_rows;
+    const int64_t nrows = min(H.part_rows, H.n_last - row0);
+    for (int64_t e = threadIdx.x; e < nrows * 16; e += blockDim.x) {
+        const int64_t a = e >> 4, cc = e & 15;
+        cp_async16(ws + a * kKT + cc * 4, H.g_last + (row0 + a) * A.K_pad + k0 + cc * 4);
     }
     cp_async_commit();
-    if (threadIdx.x < 32) ws[H.n_last * 32 + threadIdx.x] = 0.f;
+    if (threadIdx.x < kKT) ws[nrows * kKT + threadIdx.x] = 0.f;
     cp_async_wait_all();
     __syncthreads();
 
-    const int c = blockIdx.x * kHistWarps + warp;
-    if (c >= A.C) return;
+    const int c = p * A.C + cg * kHistWarps + warp;
+    if (cg * kHistWarps + warp >= A.C) return;
     const int32_t p0 = H.chunk_pt[c], p1 = H.chunk_pt[c + 1];
     if (p0 >= p1) return;
     const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
-    const int32_t first_bin = H.chunk_bin[2 * c];
-    float invZ = 0.f;
-    if (k < A.K) {
-        double z = 1.0;
-        for (int d = 0; d < A.ndim; ++d) z *= A.ds[k * A.ndim + d].invZ;
-        invZ = (float)z;
-    }
+    const Flusher flush{A, H, c, p, p0, p1, H.chunk_bin[2 * c], k, load_inv_z(A, k)};
 
     // staging of the sorted point stream: buffer b holds window wi (wi & 1 == b)
     const int32_t wb0 = p0 & ~(kWin - 1);
@@ -147,52 +188,46 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, in
     }
     __syncwarp();
 
-    // rest-axis factors of runs r .. r + 3, rotated through registers
+    // rest-axis factors (two densities) of runs r .. r + 3, rotated through registers
     const float *g0k = H.g0 + k;
     const float *g1k = NF == 2 ? H.g1 + k : nullptr;
     const int64_t K_pad = A.K_pad;
-    auto rest_factor = [&](int32_t r) -> float {
-        if (r >= r1) return 0.f;
+    auto ld2 = [](const float *q) { return *reinterpret_cast<const float2 *>(q); };
+    auto rest_factor = [&](int32_t r) -> float2 {
+        if (r >= r1) return make_float2(0.f, 0.f);
         const int32_t rest = H.run_rest[r];
         if (NF == 2) {
             const int32_t a0 = rest / (int32_t)H.n1, a1 = rest - a0 * (int32_t)H.n1;
-            return g0k[a0 * K_pad] * g1k[a1 * K_pad];
+            const float2 u = ld2(g0k + a0 * K_pad), w = ld2(g1k + a1 * K_pad);
+            return make_float2(u.x * w.x, u.y * w.y);
         }
-        return g0k[rest * K_pad];
+        return ld2(g0k + rest * K_pad);
     };
-    float f0 = rest_factor(r0), f1 = rest_factor(r0 + 1), f2 = rest_factor(r0 + 2), f3 = rest_factor(r0 + 3);
+    float2 f0 = rest_factor(r0), f1 = rest_factor(r0 + 1), f2 = rest_factor(r0 + 2), f3 = rest_factor(r0 + 3);
     // factor of run r + 4, decoded from run r's end word (the load stays in flight)
-    auto coded_factor = [&](uint32_t u) -> float {
+    auto coded_factor = [&](uint32_t u) -> float2 {
         if (NF == 2) {
-            const uint32_t a0 = u & 0x7fu, a1 = (u >> 22) & 0xffu;
-            return g0k[(int64_t)a0 * K_pad] * g1k[(int64_t)a1 * K_pad];
+            const uint32_t a0 = u & 0xffu, a1 = (u >> 23) & 0x7fu;
+            const float2 x = ld2(g0k + (int64_t)a0 * K_pad), w = ld2(g1k + (int64_t)a1 * K_pad);
+            return make_float2(x.x * w.x, x.y * w.y);
         }
-        const uint32_t idx = (u & 0x7fu) | ((u >> 15) & 0x7f80u);
-        return g0k[(int64_t)idx * K_pad];
+        const uint32_t idx = (u & 0xffu) | ((u >> 15) & 0x7f00u);
+        return ld2(g0k + (int64_t)idx * K_pad);
     };
 
-    int32_t r = r0, cur_bin = H.run_bin[r0];
-    float acc = 0.f, bacc = 0.f;
-    const uint32_t wsl = smem_u32(ws) + lane * 4;
-    const uint32_t null_word = (uint32_t)H.n_last << 7;  // zero row, no flags
+    int32_t r = r0, cur_key = H.run_bin[r0];
+    float2 acc = make_float2(0.f, 0.f), bacc = make_float2(0.f, 0.f);
+    const uint32_t wsl = smem_u32(ws) + lane * 8;
+    const uint32_t null_word = (uint32_t)nrows << 8;  // zero row, no flags
 
-    auto flush_bin = [&](int32_t b, float v) {
-        const float val = v * invZ;
-        const bool shared = A.offsets[b] < p0 || A.offsets[b + 1] > p1;
-        if (shared) {
-            const int side = (b == first_bin) ? 0 : 1;
-            A.part[((int64_t)c * 2 + side) * A.K_pad + k] = val;
-        } else if (k < A.K) {
-            A.hist[k * A.B + b] = val;
-        }
-    };
     auto run_end = [&](uint32_t u) {
-        bacc = fmaf(f0, acc, bacc);
-        acc = 0.f;
+        bacc.x = fmaf(f0.x, acc.x, bacc.x);
+        bacc.y = fmaf(f0.y, acc.y, bacc.y);
+        acc = make_float2(0.f, 0.f);
         if (u & kBinEnd) {
-            flush_bin(cur_bin, bacc);
-            bacc = 0.f;
-            cur_bin = r + 1 < r1 ? H.run_bin[r + 1] : -1;
+            flush(cur_key, bacc);
+            bacc = make_float2(0.f, 0.f);
+            cur_key = r + 1 < r1 ? H.run_bin[r + 1] : -1;
         }
         ++r;
         f0 = f1;
@@ -200,34 +235,39 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, in
         f2 = f3;
         f3 = coded_factor(u);
     };
-    auto gather = [&](uint32_t u) -> float {
-        float v;
-        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(wsl + (u & kOffMask)));
+    auto gather = [&](uint32_t addr) -> float2 {
+        float2 v;
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
         return v;
     };
     // words without flags carry nothing but the row byte offset (run codes sit
     // on run-end words only), so the common path needs no masking
-    auto gather_raw = [&](uint32_t u) -> float {
-        float v;
-        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(wsl + u));
-        return v;
-    };
     auto group = [&](const uint4 v) {
         if (((v.x | v.y | v.z | v.w) & kFlags) == 0) {
-            const float a0 = gather_raw(v.x), a1 = gather_raw(v.y), a2 = gather_raw(v.z), a3 = gather_raw(v.w);
-            acc += a0;
-            acc += a1;
-            acc += a2;
-            acc += a3;
+            const float2 a0 = gather(wsl + v.x), a1 = gather(wsl + v.y), a2 = gather(wsl + v.z),
+                         a3 = gather(wsl + v.w);
+            acc.x += a0.x;
+            acc.y += a0.y;
+            acc.x += a1.x;
+            acc.y += a1.y;
+            acc.x += a2.x;
+            acc.y += a2.y;
+            acc.x += a3.x;
+            acc.y += a3.y;
         } else {
-            const float a0 = gather(v.x), a1 = gather(v.y), a2 = gather(v.z), a3 = gather(v.w);
-            acc += a0;
+            const float2 a0 = gather(wsl + (v.x & kOffMask)), a1 = gather(wsl + (v.y & kOffMask)),
+                         a2 = gather(wsl + (v.z & kOffMask)), a3 = gather(wsl + (v.w & kOffMask));
+            acc.x += a0.x;
+            acc.y += a0.y;
             if (v.x & kFlags) run_end(v.x);
-            acc += a1;
+            acc.x += a1.x;
+            acc.y += a1.y;
             if (v.y & kFlags) run_end(v.y);
-            acc += a2;
+            acc.x += a2.x;
+            acc.y += a2.y;
             if (v.z & kFlags) run_end(v.z);
-            acc += a3;
+            acc.x += a3.x;
+            acc.y += a3.y;
             if (v.w & kFlags) run_end(v.w);
         }
     };
@@ -266,74 +306,65 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, in
             bulk_copy(win + b * kWin, H.hpt + wbase + 2 * kWin, kWin * 4, &mbar[b]);
         }
     }
-    if (cur_bin >= 0) flush_bin(cur_bin, bacc);
+    if (cur_key >= 0) flush(cur_key, bacc);
 }
 
-// Fallback for gathered axes too long for the shared-memory tile (or 3-D
-// rest indices beyond the run-end encoding): factors are gathered from global
-// memory (L1-cached), rest-axis factors prefetched in register blocks.
-__global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_global(HistArgs A) {
+// Fallback when a part's tile does not fit shared memory (or 3-D rest indices
+// exceed the run-end encoding): factors are gathered from global memory
+// (L1-cached), rest-axis factors prefetched in register blocks.
+__global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_global(HistArgs A, int G) {
     const LayoutArgs H = pick(A);
+    const int p = blockIdx.x / G, cg = blockIdx.x - p * G;
+    if (p >= H.P) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t k0 = (int64_t)blockIdx.y * kKT;
-    const int64_t k = k0 + lane;
-    const float *wl = H.g_last + k;
-    float invZ = 0.f;
-    if (k < A.K) {
-        double z = 1.0;
-        for (int d = 0; d < A.ndim; ++d) z *= A.ds[k * A.ndim + d].invZ;
-        invZ = (float)z;
-    }
-    const int c = blockIdx.x * kHistWarps + warp;
-    if (c >= A.C) return;
+    const int64_t k = (int64_t)blockIdx.y * kKT + 2 * lane;
+    const int c = p * A.C + cg * kHistWarps + warp;
+    if (cg * kHistWarps + warp >= A.C) return;
     const int32_t p0 = H.chunk_pt[c], p1 = H.chunk_pt[c + 1];
     if (p0 >= p1) return;
     const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
-    const int32_t first_bin = H.chunk_bin[2 * c];
-    auto wrest = [&](int32_t r) -> float {
-        if (r >= r1) return 0.f;
+    const Flusher flush{A, H, c, p, p0, p1, H.chunk_bin[2 * c], k, load_inv_z(A, k)};
+    const float *wl = H.g_last + (int64_t)p * H.part_rows * A.K_pad + k;
+    auto ld2 = [](const float *q) { return *reinterpret_cast<const float2 *>(q); };
+    auto wrest = [&](int32_t r) -> float2 {
+        if (r >= r1) return make_float2(0.f, 0.f);
         const int32_t rest = H.run_rest[r];
         if (A.ndim == 3) {
             const int64_t a0 = rest / H.n1, a1 = rest - a0 * H.n1;
-            return H.g0[a0 * A.K_pad + k] * H.g1[a1 * A.K_pad + k];
+            const float2 u = ld2(H.g0 + a0 * A.K_pad + k), w = ld2(H.g1 + a1 * A.K_pad + k);
+            return make_float2(u.x * w.x, u.y * w.y);
         }
-        return H.g0[(int64_t)rest * A.K_pad + k];
+        return ld2(H.g0 + (int64_t)rest * A.K_pad + k);
     };
-    auto flush_bin = [&](int32_t b, float v) {
-        const float val = v * invZ;
-        const bool shared = A.offsets[b] < p0 || A.offsets[b + 1] > p1;
-        if (shared) {
-            const int side = (b == first_bin) ? 0 : 1;
-            A.part[((int64_t)c * 2 + side) * A.K_pad + k] = val;
-        } else if (k < A.K) {
-            A.hist[k * A.B + b] = val;
-        }
-    };
-    int32_t cur_bin = H.run_bin[r0];
-    float bacc = 0.f;
+    int32_t cur_key = H.run_bin[r0];
+    float2 bacc = make_float2(0.f, 0.f);
     for (int32_t rb = r0; rb < r1; rb += kPF) {
-        float w[kPF];
+        float2 w[kPF];
 #pragma unroll
         for (int u = 0; u < kPF; ++u) w[u] = wrest(rb + u);
         for (int u = 0; u < kPF; ++u) {
             const int32_t r = rb + u;
             if (r >= r1) break;
-            float acc = 0.f;
-            for (int32_t p = H.run_start[r]; p < H.run_start[r + 1]; ++p)
-                acc += wl[(int64_t)((H.hpt[p] & kOffMask) >> 7) * A.K_pad];
-            bacc = fmaf(w[u], acc, bacc);
-            const int32_t nb = r + 1 < r1 ? H.run_bin[r + 1] : -1;
-            if (nb != cur_bin) {
-                flush_bin(cur_bin, bacc);
-                bacc = 0.f;
-                cur_bin = nb;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int32_t q = H.run_start[r]; q < H.run_start[r + 1]; ++q) {
+                const float2 v = ld2(wl + (int64_t)((H.hpt[q] & kOffMask) >> 8) * A.K_pad);
+                acc.x += v.x;
+                acc.y += v.y;
+            }
+            bacc.x = fmaf(w[u].x, acc.x, bacc.x);
+            bacc.y = fmaf(w[u].y, acc.y, bacc.y);
+            const int32_t nk = r + 1 < r1 ? H.run_bin[r + 1] : -1;
+            if (nk != cur_key) {
+                flush(cur_key, bacc);
+                bacc = make_float2(0.f, 0.f);
+                cur_key = nk;
             }
         }
     }
 }
 
-__device__ __forceinline__ int chunk_of(const int32_t *chunk_pt, int C, int32_t p) {
-    int lo = 0, hi = C;  // last c with chunk_pt[c] <= p
+__device__ __forceinline__ int chunk_of(const int32_t *chunk_pt, int n, int32_t p) {
+    int lo = 0, hi = n;  // last c in [0, n) with chunk_pt[c] <= p
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (chunk_pt[mid] <= p) lo = mid; else hi = mid - 1;
@@ -341,27 +372,38 @@ __device__ __forceinline__ int chunk_of(const int32_t *chunk_pt, int C, int32_t 
     return lo;
 }
 
-// Bins cut by chunk boundaries: sum the partials of every chunk overlapping
-// the bin (in chunk order); empty bins are zero.
-__global__ void k_hist_fixup(HistArgs A) {
+// Finish H[k, b]: for every part, the key (part, b) is either empty, written
+// directly by the single chunk that holds it, or cut by chunk boundaries and
+// summed from the partials of the chunks overlapping it (in chunk order);
+// parts are added in order.  With one part, directly written bins are final.
+__global__ void k_hist_finish(HistArgs A) {
     const LayoutArgs H = pick(A);
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (k >= A.K) return;
-    const int32_t o0 = A.offsets[b], o1 = A.offsets[b + 1];
-    if (o0 == o1) {
-        A.hist[k * A.B + b] = 0.f;
-        return;
+    const int n_chunks = H.P * A.C;
+    float total = 0.f;
+    bool touched = H.P > 1;
+    for (int p = 0; p < H.P; ++p) {
+        const int32_t key = p * A.B + b;
+        const int32_t o0 = H.koff[key], o1 = H.koff[key + 1];
+        if (o0 == o1) continue;
+        const int c0 = chunk_of(H.chunk_pt, n_chunks, o0), c1 = chunk_of(H.chunk_pt, n_chunks, o1 - 1);
+        if (c0 == c1) {
+            if (H.P > 1) total += A.direct[((int64_t)p * A.K + k) * A.B + b];
+            continue;
+        }
+        touched = true;
+        float s = 0.f;
+        for (int c = c0; c <= c1; ++c) {
+            if (H.chunk_pt[c] >= H.chunk_pt[c + 1]) continue;
+            const int side = H.chunk_bin[2 * c] == key ? 0 : 1;
+            s += A.part[((int64_t)c * 2 + side) * A.K_pad + k];
+        }
+        total += s;
     }
-    const int c0 = chunk_of(H.chunk_pt, A.C, o0), c1 = chunk_of(H.chunk_pt, A.C, o1 - 1);
-    if (c0 == c1) return;  // written directly by its chunk
-    float s = 0.f;
-    for (int c = c0; c <= c1; ++c) {
-        if (H.chunk_pt[c] >= H.chunk_pt[c + 1]) continue;
-        const int side = H.chunk_bin[2 * c] == b ? 0 : 1;
-        s += A.part[((int64_t)c * 2 + side) * A.K_pad + k];
-    }
-    A.hist[k * A.B + b] = s;
+    if (H.P == 1 && H.koff[b] == H.koff[b + 1]) touched = true;  // empty bin: zero
+    if (touched) A.hist[k * A.B + b] = total;
 }
 
 }  // namespace
@@ -370,6 +412,14 @@ int vup_hist_chunks_for(int64_t N) {
     int64_t S = N / ((int64_t)kHistWarps * 16384);
     S = std::max<int64_t>(1, std::min<int64_t>(16, S));
     return (int)(S * kHistWarps);
+}
+
+// Parts of a gathered axis of n_last rows (one 64-density tile each) for a
+// bin count; one part when the (part, bin) key space would exceed the sort.
+int vup_hist_parts_for(int64_t n_last, int n_bins) {
+    int P = (int)ceil_div64(n_last, kMaxPartRows);
+    if ((int64_t)P * n_bins > 32768) P = 1;
+    return P;
 }
 
 vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
@@ -382,6 +432,7 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
     };
     HistArgs A{};
     int64_t rows = 0;
+    int P_max = 1;
     for (int l = 0; l < 2; ++l) {
         const auto &HL = g->hl[l < g->n_layouts ? l : 0];
         LayoutArgs &La = l == 0 ? A.L0 : A.L1;
@@ -392,6 +443,7 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
         La.chunk_pt = HL.chunk_pt;
         La.chunk_run = HL.chunk_run;
         La.chunk_bin = HL.chunk_bin;
+        La.koff = HL.koff;
         La.g_last = tab(HL.last_axis);
         if (nd == 3) {
             La.g0 = tab(0);
@@ -403,10 +455,12 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
             La.n1 = 1;
         }
         La.n_last = HL.n_last;
-        rows = std::max(rows, HL.n_last);
+        La.part_rows = HL.part_rows;
+        La.P = HL.P;
+        rows = std::max(rows, HL.part_rows);
+        P_max = std::max(P_max, HL.P);
     }
     A.sel = g->hist_sel;
-    A.offsets = g->offsets;
     A.ds = (const DensStats *)g->dstats.p;
     A.ndim = nd;
     A.K = K;
@@ -415,29 +469,31 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
     A.C = g->n_chunks;
     A.hist = hist;
     A.part = (float *)g->hist_part.p;
+    A.direct = (float *)g->hist_direct.p;
     A.dstatus = g->dstatus;
     const size_t smem = hist_smem_bytes(rows);
-    // run-end words encode the rest index in 15 bits (3-D: a0 < 128, a1 < 256)
-    const bool coded = nd == 2 || (g->n[0] <= 128 && g->n[1] <= 256);
-    dim3 grd((unsigned)(A.C / kHistWarps), (unsigned)ceil_div64(K, kKT));
+    // run-end words encode the rest index in 15 bits (3-D: a0 < 256, a1 < 128)
+    const bool coded = nd == 2 || (g->n[0] <= 256 && g->n[1] <= 128);
+    const int G = A.C / kHistWarps;
+    dim3 grd((unsigned)(P_max * G), (unsigned)ceil_div64(K, kKT));
     {
         VUP_PROF("hist_segmented", s, 1);
         if (smem <= 220 * 1024 && coded) {
             if (nd == 3) {
                 VUP_CHECK_CUDA(cudaFuncSetAttribute(k_hist_smem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_hist_smem<2><<<grd, kHistWarps * 32, smem, s>>>(A, rows);
+                k_hist_smem<2><<<grd, kHistWarps * 32, smem, s>>>(A, rows, G);
             } else {
                 VUP_CHECK_CUDA(cudaFuncSetAttribute(k_hist_smem<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_hist_smem<1><<<grd, kHistWarps * 32, smem, s>>>(A, rows);
+                k_hist_smem<1><<<grd, kHistWarps * 32, smem, s>>>(A, rows, G);
             }
         } else {
-            k_hist_global<<<grd, kHistWarps * 32, 0, s>>>(A);
+            k_hist_global<<<grd, kHistWarps * 32, 0, s>>>(A, G);
         }
         VUP_CHECK_LAUNCH();
     }
     VUP_PROF("hist_fixup", s, 1);
     dim3 fg((unsigned)ceil_div64(K, 128), (unsigned)g->B);
-    k_hist_fixup<<<fg, 128, 0, s>>>(A);
+    k_hist_finish<<<fg, 128, 0, s>>>(A);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }

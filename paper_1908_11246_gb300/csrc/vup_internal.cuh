@@ -82,6 +82,7 @@ struct vup_grid_s {
     int32_t *perm = nullptr;       // [N] sorted position -> flat index
     int32_t *offsets = nullptr;    // [B_cap + 1]
     int32_t B_cap = 0;
+    int natural_valid = 0;         // perm holds the stable sort by bin
 
     // counting-sort scratch
     DevBuf sort_counts, scan_tmp;
@@ -93,17 +94,24 @@ struct vup_grid_s {
     struct HistLayout {
         int last_axis = -1;            // axis gathered per point
         int64_t n_last = 0;
-        int32_t *keys = nullptr;       // bin of the layout's flat index (layout 1: transposed bins)
+        int P = 1;                     // parts of the gathered axis (shared-memory tiles)
+        int64_t part_rows = 0;         // gathered-axis rows per part
+        int32_t *binsT = nullptr;      // layout 1: bins in transposed order
+        int32_t *keys = nullptr;       // sort key of the layout's flat index: part * B + bin
+        int32_t *keys_own = nullptr;   // [N] key storage when keys != bins
+        int32_t *koff = nullptr;       // [P * B + 1] key offsets in the sorted stream
+        int32_t koff_cap = 0;
         int32_t *perm = nullptr;       // [N] sorted position -> layout flat index
         uint32_t *hpt = nullptr;       // [N + 512] packed per-point word
         int32_t *run_start = nullptr;  // [N + 1]
         int32_t *run_rest = nullptr;   // [N]
         int32_t *run_bin = nullptr;    // [N]
         int32_t *n_runs = nullptr;     // [1] device
-        int32_t *chunk_pt = nullptr;   // [n_chunks + 1] chunk start (point index)
-        int32_t *chunk_run = nullptr;  // [n_chunks + 1] chunk start (run index)
-        int32_t *chunk_bin = nullptr;  // [n_chunks * 2] first / last bin of each chunk
+        int32_t *chunk_pt = nullptr;   // [P * n_chunks + 1] chunk start (point index)
+        int32_t *chunk_run = nullptr;  // [P * n_chunks + 1] chunk start (run index)
+        int32_t *chunk_bin = nullptr;  // [P * n_chunks * 2] first / last key of each chunk
     } hl[2];
+    int hist_P = 1;                // max parts over layouts (scratch sizing)
     int n_layouts = 1;
     int32_t *hist_sel = nullptr;   // [1] device: chosen layout
     int32_t *flags_scan = nullptr; // [N] scratch
@@ -120,7 +128,7 @@ struct vup_grid_s {
 
     // per-K scratch (density constants, factor tables, partials)
     int64_t K_cap = 0;
-    DevBuf dconst, dstats, ftab, atab_hi, atab_lo, partials, hist_part, ipsa_part;
+    DevBuf dconst, dstats, ftab, atab_hi, atab_lo, partials, hist_part, hist_direct, ipsa_part;
 
     int *dstatus = nullptr;        // [1] device status word
 };
@@ -130,6 +138,7 @@ vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta,
                                  cudaStream_t s);
 vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s);  // range, bins, sort, runs, tables
 vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s);
+vup_status vup_natural_sort(vup_grid g, cudaStream_t s);
 
 vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_orient_mask,
                             cudaStream_t s);
