@@ -207,14 +207,44 @@ vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, vup_precisio
 
 /*
  * Batched uneven propagation: n_inst independent instances (grid g[i] with
- * densities d[i]) in one persistent launch per stage.  g, d, moments_raw and
- * hist are host arrays of length n_inst; moments_raw[i] / hist[i] are device
- * pointers (or NULL) shaped as in vup_propagate.  All grids must have ndim == 2
- * and the same n_moments.  Work tiles are ordered longest-first.
+ * densities d[i]), the many-small-problems form of the Sec. 4 pipeline.  Every
+ * stage runs as one launch over the work items of all instances, longest
+ * items first (density preparation, the moment contraction, the FP64 finish,
+ * the segmented histogram and its finish).
+ *   g, d, moments_raw, hist : host arrays of length n_inst; moments_raw[i]
+ *       ([K_i][J_i] double) and hist[i] ([K_i][B_i] float) are device
+ *       pointers or NULL, laid out as in vup_propagate; moments_raw or hist
+ *       may itself be NULL (no instance wants that output).
+ *   precision : VUP_FP32 or VUP_BF16X3 (VUP_FP64: VUP_ERR_UNSUPPORTED).
+ * Every grid must be 2-D with a model (VUP_ERR_STATE otherwise) and each
+ * gathered-axis part of its histogram layout must fit one shared-memory tile
+ * (704 rows; VUP_ERR_UNSUPPORTED otherwise).
+ * The first call for a batch (same grids, densities, output pointers and
+ * sizes) builds the work lists, chooses the contraction tile width for the
+ * batch's shape (VUP_BF16X3: times tile-width caps 256, 128 and 64 once per
+ * shape, replaying the whole batch; the choice is remembered for the process
+ * and appended to the file named by the environment variable VUP_TUNE_CACHE,
+ * if set, as one JSON object per line) and captures the launches into a CUDA
+ * graph; later calls replay that graph on `stream`.  The first call is
+ * synchronous and allocates; later calls allocate nothing and may be captured
+ * into a caller's graph (their stage kernels are then captured directly; a
+ * first call made while `stream` is capturing returns VUP_ERR_STATE).  Up to 8 batches are remembered.  Device conditions are
+ * recorded per grid (VUP_ERR_EMPTY_SUPPORT) and, for an expired wait in the
+ * contraction, in g[0]; read them with vup_sync.
  */
 vup_status vup_propagate_batched(int n_inst, const vup_grid *g, const vup_densities *d,
                                  vup_precision precision, double *const *moments_raw,
                                  float *const *hist, vup_stream_t stream);
+
+/*
+ * What the calling thread's most recent vup_propagate_batched did:
+ *   bn_cap  : tile-width cap of the contraction (256 / 128 / 64; 0 for FP32)
+ *   source  : 0 replayed a remembered graph, 1 built a graph with a remembered
+ *             tile-width choice, 2 built one after timing the candidates,
+ *             -1 no call yet
+ *   tune_ms : device time spent timing candidates in that call (0 if none)
+ */
+vup_status vup_batched_report(int *bn_cap, int *source, double *tune_ms);
 
 /*
  * Wait for the grid's queued work on `stream` and return (and clear) the

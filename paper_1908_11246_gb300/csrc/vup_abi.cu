@@ -69,6 +69,8 @@ cudaEvent_t prof_event() {
 
 ProfScope::ProfScope(const char *n, cudaStream_t s, int l) : name(n), stream(s), launches(l), slot(-1) {
     if (!g_prof_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfRec r{n, prof_event(), prof_event(), l};
     cudaEventRecord(r.a, s);
@@ -81,6 +83,8 @@ ProfScope::~ProfScope() {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (slot < (int)g_prof_recs.size()) cudaEventRecord(g_prof_recs[slot].b, stream);
 }
+
+bool vup_profiling() { return g_prof_on; }
 
 extern "C" vup_status vup_profile(int enable) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -187,6 +191,7 @@ static void free_grid(vup_grid g) {
     devbuf_free(g->scan_tmp);
     devbuf_free(g->dconst);
     devbuf_free(g->dstats);
+    devbuf_free(g->dpart);
     devbuf_free(g->ftab);
     devbuf_free(g->atab_hi);
     devbuf_free(g->atab_lo);
@@ -306,6 +311,7 @@ static vup_status finish_model(vup_grid g, cudaStream_t s) {
         if (st != VUP_OK) return st;
     }
     g->have_model = 1;
+    ++g->model_gen;
     return VUP_OK;
 }
 
@@ -350,7 +356,7 @@ extern "C" vup_status vup_set_outputs(vup_grid g, const double *y_dev, int n_bin
     return finish_model(g, s);
 }
 
-static vup_status check_dens(vup_grid g, const vup_densities *d) {
+vup_status vup_check_dens(vup_grid g, const vup_densities *d) {
     if (!d || d->K < 1 || d->K > (int64_t)1 << 26 || d->ndim != g->ndim) return VUP_ERR_INVALID_ARG;
     if (!d->kind || !d->mu || !d->sigma) return VUP_ERR_INVALID_ARG;
     if ((d->lo == nullptr) != (d->hi == nullptr)) return VUP_ERR_INVALID_ARG;
@@ -358,7 +364,7 @@ static vup_status check_dens(vup_grid g, const vup_densities *d) {
 }
 
 // Per-K scratch: density constants, factor tables, split A tables, partials.
-static vup_status reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa) {
+vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa) {
     const int64_t K_pad = ceil_div64(K, 128) * 128;
     const int nd = g->ndim;
     vup_status st;
@@ -393,7 +399,7 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
                                     double *moments_raw, double *moments_central, float *hist,
                                     vup_stream_t stream) {
     if (!g) return VUP_ERR_INVALID_ARG;
-    vup_status st = check_dens(g, d);
+    vup_status st = vup_check_dens(g, d);
     if (st != VUP_OK) return st;
     if (precision != VUP_FP64 && precision != VUP_FP32 && precision != VUP_BF16X3) return VUP_ERR_INVALID_ARG;
     if (!g->have_model) return VUP_ERR_STATE;
@@ -406,7 +412,7 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
     if (precision == VUP_FP64) return VUP_ERR_UNSUPPORTED;
     const bool bf16 = precision == VUP_BF16X3;
     const bool want_m = moments_raw || moments_central;
-    if ((st = reserve_k(g, K, bf16, false)) != VUP_OK) return st;
+    if ((st = vup_reserve_k(g, K, bf16, false)) != VUP_OK) return st;
     if ((st = vup_density_prep(g, d, (bf16 && want_m) ? 1 : 0, s)) != VUP_OK) return st;
     if (want_m) {
         int64_t nct;
@@ -436,7 +442,7 @@ extern "C" vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, v
                                            const double *grad_moments, float *dmu, float *dsigma,
                                            vup_stream_t stream) {
     if (!g || !dmu || !dsigma) return VUP_ERR_INVALID_ARG;
-    vup_status st = check_dens(g, d);
+    vup_status st = vup_check_dens(g, d);
     if (st != VUP_OK) return st;
     if (precision != VUP_FP64 && precision != VUP_FP32 && precision != VUP_BF16X3) return VUP_ERR_INVALID_ARG;
     if (!g->have_model) return VUP_ERR_STATE;
@@ -448,7 +454,7 @@ extern "C" vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, v
     if (g->ndim != 2 || precision == VUP_FP64) return VUP_ERR_UNSUPPORTED;
     const int64_t K = d->K;
     const bool bf16 = precision == VUP_BF16X3;
-    if ((st = reserve_k(g, K, bf16, true)) != VUP_OK) return st;
+    if ((st = vup_reserve_k(g, K, bf16, true)) != VUP_OK) return st;
     if ((st = vup_build_tables(g, 1, bf16 ? 1 : 0, s)) != VUP_OK) return st;
     if ((st = vup_density_prep(g, d, bf16 ? 3 : 0, s)) != VUP_OK) return st;
     const int64_t K_pad = ceil_div64(K, 128) * 128;

@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 namespace {
 
@@ -85,22 +86,44 @@ __device__ __forceinline__ float dens_value(int kind, int64_t a, const GaussArg 
     return expf(-eh) * (1.f - el);
 }
 
-__global__ void k_density_prep(DensIn in, int64_t K, int64_t K_pad, int ndim, int64_t n0, int64_t n1,
-                               int64_t n2, double lo0, double lo1, double lo2, double h0, double h1,
-                               double h2, DensConst *__restrict__ dconst, DensStats *__restrict__ dstats,
-                               float *__restrict__ ftab, int *__restrict__ dstatus) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int d = blockIdx.y;
-    if (k >= K_pad) return;
-    const int64_t nd = d == 0 ? n0 : (d == 1 ? n1 : n2);
-    const double lo = d == 0 ? lo0 : (d == 1 ? lo1 : lo2);
-    const double h = d == 0 ? h0 : (d == 1 ? h1 : h2);
+// Everything one density-prep launch needs for one grid (one instance).
+struct DensJob {
+    DensIn in;
+    int64_t K, K_pad;
+    int ndim;
+    int64_t n[3];
+    double lo[3], h[3];
+    int S;  // segments per axis
+    DensConst *dconst;
+    double *dpart;
+    float *ftab;
+    DensStats *dstats;
+    int *dstatus;
+    // split BF16 A table of the orientation-0 reduction axis (tensor-core path)
+    const float *red_tab;
+    int64_t nd_red, R_pad;
+    __nv_bfloat16 *ahi, *alo;
+};
+
+// Density factors of densities kb*128 .. kb*128+127 on axis d, segment z of
+// that axis: the factor table entries and partial compensated sums.
+__device__ __forceinline__ void density_prep_body(const DensJob &J, int64_t kb, int d, int z) {
+    const int64_t k = kb * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= J.K_pad) return;
+    const int64_t K = J.K, K_pad = J.K_pad;
+    const int ndim = J.ndim, S = J.S;
+    const DensIn &in = J.in;
+    const int64_t nd = J.n[d];
+    // this thread's segment of the axis
+    const int64_t seg = (nd + S - 1) / S;
+    const int64_t a_begin = z * seg, a_end = a_begin + seg < nd ? a_begin + seg : nd;
+    const double lo = J.lo[d];
+    const double h = J.h[d];
     int64_t off = 0;
-    if (d >= 1) off += n0 * K_pad;
-    if (d >= 2) off += n1 * K_pad;
-    float *tab = ftab + off;
+    for (int q = 0; q < d; ++q) off += J.n[q] * K_pad;
+    float *tab = J.ftab + off;
     if (k >= K) {
-        for (int64_t a = 0; a < nd; ++a) tab[a * K_pad + k] = 0.f;
+        for (int64_t a = a_begin; a < a_end; ++a) tab[a * K_pad + k] = 0.f;
         return;
     }
     const int64_t p = k * ndim + d;
@@ -129,7 +152,7 @@ __global__ void k_density_prep(DensIn in, int64_t K, int64_t K_pad, int ndim, in
     ga.qh = (float)u0sq;
     ga.ql = (float)(u0sq - (double)ga.qh);
     KSum S0, S1, S2;
-    for (int64_t a = 0; a < nd; ++a) {
+    for (int64_t a = a_begin; a < a_end; ++a) {
         double xa = 0.0;
         if (kind != VUP_GAUSS) xa = __dadd_rn(lo, __dmul_rn((double)a + 0.5, h));
         float u;
@@ -139,29 +162,51 @@ __global__ void k_density_prep(DensIn in, int64_t K, int64_t K_pad, int ndim, in
         S1.add(g * u);
         S2.add(g * u * u);
     }
-    DensConst dc;
-    dc.n = (int32_t)fmax(fmin(nk, 2147483647.0), -2147483647.0);
-    dc.f = f;
-    dc.r = r;
-    dc.kind = kind;
-    dconst[p] = dc;
-    const double Z = S0.value();
+    if (z == 0) {
+        DensConst dc;
+        dc.n = (int32_t)fmax(fmin(nk, 2147483647.0), -2147483647.0);
+        dc.f = f;
+        dc.r = r;
+        dc.kind = kind;
+        J.dconst[p] = dc;
+    }
+    double *q = J.dpart + (((int64_t)d * S + z) * K_pad + k) * 3;
+    q[0] = S0.value();
+    q[1] = S1.value();
+    q[2] = S2.value();
+}
+
+
+// Normalisation statistics from the per-segment compensated sums (segments
+// added in order, FP64): Z = sum g, E[u] and E[u^2] under g / Z.
+__device__ __forceinline__ void density_finish_body(const DensJob &J, int64_t kb, int d) {
+    const int64_t k = kb * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= J.K) return;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int z = 0; z < J.S; ++z) {
+        const double *q = J.dpart + (((int64_t)d * J.S + z) * J.K_pad + k) * 3;
+        s0 += q[0];
+        s1 += q[1];
+        s2 += q[2];
+    }
+    const int64_t p = k * J.ndim + d;
     DensStats ds;
-    ds.invZ = Z > 0.0 ? 1.0 / Z : 0.0;
-    ds.Eu = Z > 0.0 ? S1.value() / Z : 0.0;
-    ds.Eu2 = Z > 0.0 ? S2.value() / Z : 0.0;
-    ds.inv_sigma = 1.0 / sigma;
-    dstats[p] = ds;
-    if (!(Z > 0.0)) atomicCAS(dstatus, 0, VUP_DSTAT_EMPTY);
+    ds.invZ = s0 > 0.0 ? 1.0 / s0 : 0.0;
+    ds.Eu = s0 > 0.0 ? s1 / s0 : 0.0;
+    ds.Eu2 = s0 > 0.0 ? s2 / s0 : 0.0;
+    ds.inv_sigma = 1.0 / J.in.sigma[p];
+    J.dstats[p] = ds;
+    if (!(s0 > 0.0)) atomicCAS(J.dstatus, 0, VUP_DSTAT_EMPTY);
 }
 
 // A-operand table of the tensor-core contraction: rows k, reduction index a
-// contiguous (K-major), each FP32 factor split into BF16 hi + lo.
-__global__ void k_split_transpose(const float *__restrict__ tab, int64_t nd, int64_t K_pad,
-                                  int64_t R_pad, __nv_bfloat16 *__restrict__ hi,
-                                  __nv_bfloat16 *__restrict__ lo) {
+// contiguous (K-major), each FP32 factor split into BF16 hi + lo.  Block
+// (bx, by) transposes the 32 x 32 tile at a = 32 bx, k = 32 by.
+__device__ __forceinline__ void split_transpose_body(const float *__restrict__ tab, int64_t nd, int64_t K_pad,
+                                                     int64_t R_pad, __nv_bfloat16 *__restrict__ hi,
+                                                     __nv_bfloat16 *__restrict__ lo, int64_t bx, int64_t by) {
     __shared__ float t[32][33];
-    const int64_t a0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+    const int64_t a0 = bx * 32, k0 = by * 32;
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
         int64_t a = a0 + y, k = k0 + threadIdx.x;
         t[y][threadIdx.x] = (a < nd && k < K_pad) ? tab[a * K_pad + k] : 0.f;
@@ -177,6 +222,64 @@ __global__ void k_split_transpose(const float *__restrict__ tab, int64_t nd, int
             lo[k * R_pad + a] = __float2bfloat16_rn(rem);
         }
     }
+    __syncthreads();
+}
+
+__global__ void k_density_prep(DensJob J) { density_prep_body(J, blockIdx.x, blockIdx.y, blockIdx.z); }
+__global__ void k_density_finish(DensJob J) { density_finish_body(J, blockIdx.x, blockIdx.y); }
+__global__ void k_split_transpose(const float *__restrict__ tab, int64_t nd, int64_t K_pad, int64_t R_pad,
+                                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+    split_transpose_body(tab, nd, K_pad, R_pad, hi, lo, blockIdx.x, blockIdx.y);
+}
+
+// Batched forms: one launch for the blocks of every instance; items[b] =
+// (instance, block coordinates) of block b.
+__global__ void k_density_prep_batched(const DensJob *__restrict__ jobs, const int4 *__restrict__ items) {
+    const int4 it = items[blockIdx.x];
+    density_prep_body(jobs[it.x], it.y, it.z, it.w);
+}
+__global__ void k_density_finish_batched(const DensJob *__restrict__ jobs, const int4 *__restrict__ items) {
+    const int4 it = items[blockIdx.x];
+    density_finish_body(jobs[it.x], it.y, it.z);
+}
+__global__ void k_split_transpose_batched(const DensJob *__restrict__ jobs, const int4 *__restrict__ items) {
+    const int4 it = items[blockIdx.x];
+    const DensJob &J = jobs[it.x];
+    split_transpose_body(J.red_tab, J.nd_red, J.K_pad, J.R_pad, J.ahi, J.alo, it.y, it.z);
+}
+
+int density_segments(vup_grid g) {
+    int64_t nmax = 1;
+    for (int q = 0; q < g->ndim; ++q) nmax = std::max(nmax, g->n[q]);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(16, nmax / 128));
+}
+
+DensJob make_job(vup_grid g, const vup_densities *d) {
+    DensJob J{};
+    J.in = DensIn{d->kind, d->mu, d->sigma, d->lo, d->hi};
+    J.K = d->K;
+    J.K_pad = ceil_div64(d->K, 128) * 128;
+    J.ndim = g->ndim;
+    for (int q = 0; q < 3; ++q) {
+        J.n[q] = g->n[q];
+        J.lo[q] = g->lo[q];
+        J.h[q] = (g->hi[q] - g->lo[q]) / (double)g->n[q];
+    }
+    J.S = density_segments(g);
+    J.dconst = (DensConst *)g->dconst.p;
+    J.dpart = (double *)g->dpart.p;
+    J.ftab = (float *)g->ftab.p;
+    J.dstats = (DensStats *)g->dstats.p;
+    J.dstatus = g->dstatus;
+    const Orient &o = g->orient[0];
+    int64_t off = 0;
+    for (int q = 0; q < o.red_axis0; ++q) off += g->n[q] * J.K_pad;
+    J.red_tab = (const float *)g->ftab.p + off;
+    J.nd_red = g->n[o.red_axis0];
+    J.R_pad = o.R_pad;
+    J.ahi = (__nv_bfloat16 *)g->atab_hi.p;
+    J.alo = (__nv_bfloat16 *)g->atab_lo.p;
+    return J;
 }
 
 }  // namespace
@@ -187,19 +290,24 @@ size_t vup_ftab_floats(const vup_grid g) {
     return s;
 }
 
+vup_status vup_density_reserve(vup_grid g, int64_t K) {
+    const int64_t K_pad = ceil_div64(K, 128) * 128;
+    return devbuf_reserve(g->dpart, sizeof(double) * 3 * (size_t)density_segments(g) * g->ndim * K_pad);
+}
+
 // need_bf16_orient_mask: bit o set -> build the split BF16 A table for the
 // reduction axis of orientation o.
 vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_orient_mask, cudaStream_t s) {
-    const int64_t K = d->K;
-    const int64_t K_pad = ceil_div64(K, 128) * 128;
-    DensIn in{d->kind, d->mu, d->sigma, d->lo, d->hi};
-    double h[3];
-    for (int q = 0; q < 3; ++q) h[q] = (g->hi[q] - g->lo[q]) / (double)g->n[q];
-    dim3 grd((unsigned)ceil_div64(K_pad, 128), (unsigned)g->ndim);
-    VUP_PROF("density_prep", s, 1 + __builtin_popcount(need_bf16_orient_mask));
-    k_density_prep<<<grd, 128, 0, s>>>(in, K, K_pad, g->ndim, g->n[0], g->n[1], g->n[2], g->lo[0], g->lo[1],
-                                       g->lo[2], h[0], h[1], h[2], (DensConst *)g->dconst.p,
-                                       (DensStats *)g->dstats.p, (float *)g->ftab.p, g->dstatus);
+    vup_status st = vup_density_reserve(g, d->K);
+    if (st != VUP_OK) return st;
+    const DensJob J = make_job(g, d);
+    const int64_t K_pad = J.K_pad;
+    dim3 grd((unsigned)ceil_div64(K_pad, 128), (unsigned)g->ndim, (unsigned)J.S);
+    VUP_PROF("density_prep", s, 2 + __builtin_popcount(need_bf16_orient_mask));
+    k_density_prep<<<grd, 128, 0, s>>>(J);
+    VUP_CHECK_LAUNCH();
+    dim3 fgrd((unsigned)ceil_div64(d->K, 128), (unsigned)g->ndim);
+    k_density_finish<<<fgrd, 128, 0, s>>>(J);
     VUP_CHECK_LAUNCH();
     for (int o = 0; o < 2; ++o) {
         if (!(need_bf16_orient_mask & (1 << o))) continue;
@@ -207,18 +315,88 @@ vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_or
         const int dred = ori.red_axis0;
         int64_t off = 0;
         for (int q = 0; q < dred; ++q) off += g->n[q] * K_pad;
-        __nv_bfloat16 *hi = (__nv_bfloat16 *)g->atab_hi.p + (size_t)o * K_pad * ori.R_pad * 0;
+        __nv_bfloat16 *hi = (__nv_bfloat16 *)g->atab_hi.p;
         __nv_bfloat16 *lo = (__nv_bfloat16 *)g->atab_lo.p;
         if (o == 1) {
             // orientation-1 tables live after the orientation-0 tables
             const size_t o0 = (size_t)K_pad * g->orient[0].R_pad;
-            hi = (__nv_bfloat16 *)g->atab_hi.p + o0;
-            lo = (__nv_bfloat16 *)g->atab_lo.p + o0;
+            hi += o0;
+            lo += o0;
         }
         dim3 tg((unsigned)ceil_div64(ori.R_pad, 32), (unsigned)ceil_div64(K_pad, 32));
         k_split_transpose<<<tg, dim3(32, 8), 0, s>>>((const float *)g->ftab.p + off, g->n[dred], K_pad, ori.R_pad,
                                                      hi, lo);
         VUP_CHECK_LAUNCH();
     }
+    return VUP_OK;
+}
+
+// Batched density preparation for n instances (one launch per stage).  The
+// job and item tables are built on the host and uploaded into `plan`
+// (device memory owned by the caller); returns the device pointers' layout
+// via the launch.  Scratch of every grid must already be reserved for its K.
+struct DensPlan {
+    DevBuf jobs, items;
+    int n_prep = 0, n_fin = 0, n_split = 0;
+};
+
+vup_status vup_density_plan(int n, const vup_grid *gs, const vup_densities *ds, bool bf16, void **plan_out) {
+    DensPlan *P = new DensPlan();
+    std::vector<DensJob> jobs(n);
+    std::vector<int4> prep, fin, split;
+    for (int i = 0; i < n; ++i) {
+        jobs[i] = make_job(gs[i], &ds[i]);
+        const DensJob &J = jobs[i];
+        const int64_t nkb_pad = ceil_div64(J.K_pad, 128), nkb = ceil_div64(J.K, 128);
+        for (int d = 0; d < J.ndim; ++d)
+            for (int z = 0; z < J.S; ++z)
+                for (int64_t kb = 0; kb < nkb_pad; ++kb) prep.push_back(make_int4(i, (int)kb, d, z));
+        for (int d = 0; d < J.ndim; ++d)
+            for (int64_t kb = 0; kb < nkb; ++kb) fin.push_back(make_int4(i, (int)kb, d, 0));
+        if (bf16)
+            for (int64_t by = 0; by < ceil_div64(J.K_pad, 32); ++by)
+                for (int64_t bx = 0; bx < ceil_div64(J.R_pad, 32); ++bx)
+                    split.push_back(make_int4(i, (int)bx, (int)by, 0));
+    }
+    P->n_prep = (int)prep.size();
+    P->n_fin = (int)fin.size();
+    P->n_split = (int)split.size();
+    std::vector<int4> all;
+    all.insert(all.end(), prep.begin(), prep.end());
+    all.insert(all.end(), fin.begin(), fin.end());
+    all.insert(all.end(), split.begin(), split.end());
+    vup_status st;
+    if ((st = devbuf_reserve(P->jobs, sizeof(DensJob) * n)) != VUP_OK ||
+        (st = devbuf_reserve(P->items, sizeof(int4) * all.size())) != VUP_OK) {
+        devbuf_free(P->jobs);
+        devbuf_free(P->items);
+        delete P;
+        return st;
+    }
+    VUP_CHECK_CUDA(cudaMemcpy(P->jobs.p, jobs.data(), sizeof(DensJob) * n, cudaMemcpyHostToDevice));
+    VUP_CHECK_CUDA(cudaMemcpy(P->items.p, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice));
+    *plan_out = P;
+    return VUP_OK;
+}
+
+void vup_density_plan_free(void *plan) {
+    DensPlan *P = (DensPlan *)plan;
+    if (!P) return;
+    devbuf_free(P->jobs);
+    devbuf_free(P->items);
+    delete P;
+}
+
+vup_status vup_density_batched(void *plan, cudaStream_t s) {
+    const DensPlan *P = (const DensPlan *)plan;
+    const DensJob *jobs = (const DensJob *)P->jobs.p;
+    const int4 *items = (const int4 *)P->items.p;
+    VUP_PROF("density_prep_batched", s, P->n_split ? 3 : 2);
+    if (P->n_prep) k_density_prep_batched<<<P->n_prep, 128, 0, s>>>(jobs, items);
+    VUP_CHECK_LAUNCH();
+    if (P->n_fin) k_density_finish_batched<<<P->n_fin, 128, 0, s>>>(jobs, items + P->n_prep);
+    VUP_CHECK_LAUNCH();
+    if (P->n_split) k_split_transpose_batched<<<P->n_split, dim3(32, 8), 0, s>>>(jobs, items + P->n_prep + P->n_fin);
+    VUP_CHECK_LAUNCH();
     return VUP_OK;
 }

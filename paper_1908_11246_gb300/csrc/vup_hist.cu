@@ -23,6 +23,7 @@
 #include "vup_internal.cuh"
 
 #include <algorithm>
+#include <vector>
 
 namespace {
 
@@ -143,14 +144,14 @@ __device__ __forceinline__ float2 load_inv_z(const HistArgs &A, int64_t k) {
     return r;
 }
 
+// One work item: part p, chunk group cg (kHistWarps chunks, one per warp) and
+// the 64 densities from k0 of layout H.  Called by every thread of the CTA;
+// `wseq` counts the staging windows this warp has consumed so far (it keeps
+// the per-warp mbarrier phases consistent across items).
 template <int NF>
-__global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, int64_t tile_rows, int G) {
-    extern __shared__ __align__(128) uint8_t sm[];
-    const LayoutArgs H = pick(A);
-    const int p = blockIdx.x / G, cg = blockIdx.x - p * G;
-    if (p >= H.P) return;
+__device__ __forceinline__ void hist_item(const HistArgs &A, const LayoutArgs &H, int p, int cg, int64_t k0,
+                                          uint8_t *sm, int64_t tile_rows, uint32_t &wseq, volatile int *abort) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t k0 = (int64_t)blockIdx.y * kKT;
     const int64_t k = k0 + 2 * lane;
     float *ws = reinterpret_cast<float *>(sm);
     const size_t tb = hist_tile_bytes(tile_rows);
@@ -158,7 +159,9 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, in
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + tb + kHistWarps * hist_warp_bytes()) + 2 * warp;
 
     // this part's rows of the gathered-axis factor table (16-byte asynchronous
-    // copies) + a zero row
+    // copies) + a zero row; the previous item's readers are done first
+    __syncthreads();
+    if (*abort) return;  // a wait of an earlier item expired (uniform: read after the barrier)
     const int64_t row0 = (int64_t)p * H.part_rows;
     const int64_t nrows = min(H.part_rows, H.n_last - row0);
     for (int64_t e = threadIdx.x; e < nrows * 16; e += blockDim.x) {
@@ -177,14 +180,14 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, in
     const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
     const Flusher flush{A, H, c, p, p0, p1, H.chunk_bin[2 * c], k, load_inv_z(A, k)};
 
-    // staging of the sorted point stream: buffer b holds window wi (wi & 1 == b)
+    // staging of the sorted point stream: window i of this item lands in
+    // buffer (wseq + i) & 1
     const int32_t wb0 = p0 & ~(kWin - 1);
     if (lane == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        bulk_copy(win, H.hpt + wb0, kWin * 4, &mbar[0]);
-        if (wb0 + kWin < p1) bulk_copy(win + kWin, H.hpt + wb0 + kWin, kWin * 4, &mbar[1]);
+        const int b0 = wseq & 1;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier items' reads of both buffers
+        bulk_copy(win + b0 * kWin, H.hpt + wb0, kWin * 4, &mbar[b0]);
+        if (wb0 + kWin < p1) bulk_copy(win + (b0 ^ 1) * kWin, H.hpt + wb0 + kWin, kWin * 4, &mbar[b0 ^ 1]);
     }
     __syncwarp();
 
@@ -280,11 +283,11 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, in
         return v;
     };
 
-    int wi = 0;
-    for (int32_t wbase = wb0; wbase < p1; wbase += kWin, ++wi) {
-        const int b = wi & 1;
-        for (uint32_t i = 0; !mbar_try_wait(&mbar[b], (wi >> 1) & 1); ++i) {
-            if (i > kSpin) {  // a staged copy never landed: record and stop
+    for (int32_t wbase = wb0; wbase < p1; wbase += kWin, ++wseq) {
+        const int b = wseq & 1;
+        for (uint32_t i = 0; !mbar_try_wait(&mbar[b], (wseq >> 1) & 1); ++i) {
+            if (i > kSpin || *abort) {  // a staged copy never landed: record and stop
+                *abort = 1;
                 atomicCAS(A.dstatus, 0, VUP_DSTAT_TIMEOUT);
                 return;
             }
@@ -307,6 +310,57 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, in
         }
     }
     if (cur_key >= 0) flush(cur_key, bacc);
+}
+
+__device__ __forceinline__ uint64_t *hist_mbar(uint8_t *sm, int64_t tile_rows) {
+    return reinterpret_cast<uint64_t *>(sm + hist_tile_bytes(tile_rows) + kHistWarps * hist_warp_bytes()) +
+           2 * (threadIdx.x >> 5);
+}
+__device__ __forceinline__ void hist_init_mbar(uint8_t *sm, int64_t tile_rows) {
+    if ((threadIdx.x & 31) == 0) {
+        uint64_t *mbar = hist_mbar(sm, tile_rows);
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+}
+
+template <int NF>
+__global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, int64_t tile_rows, int G) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    const LayoutArgs H = pick(A);
+    const int p = blockIdx.x / G, cg = blockIdx.x - p * G;
+    if (p >= H.P) return;
+    __shared__ int abort;
+    if (threadIdx.x == 0) abort = 0;
+    hist_init_mbar(sm, tile_rows);
+    uint32_t wseq = 0;
+    hist_item<NF>(A, H, p, cg, (int64_t)blockIdx.y * kKT, sm, tile_rows, wseq, &abort);
+}
+
+// Batched form: one persistent launch over the work items of many instances
+// (each with its own grid, densities and outputs), longest items first.
+struct HistItem {
+    int32_t inst, p, cg, kt;
+};
+
+template <int NF>
+__global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_batched(const HistArgs *__restrict__ insts,
+                                                                     const HistItem *__restrict__ items,
+                                                                     int n_items, int64_t tile_rows) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    __shared__ int abort;
+    if (threadIdx.x == 0) abort = 0;
+    hist_init_mbar(sm, tile_rows);
+    uint32_t wseq = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const HistItem w = items[it];
+        const HistArgs A = insts[w.inst];
+        const LayoutArgs H = pick(A);
+        if (w.p >= H.P) continue;  // uniform: every thread reads the same item
+        hist_item<NF>(A, H, w.p, w.cg, (int64_t)w.kt * kKT, sm, tile_rows, wseq, &abort);
+    }
 }
 
 // Fallback when a part's tile does not fit shared memory (or 3-D rest indices
@@ -376,11 +430,9 @@ __device__ __forceinline__ int chunk_of(const int32_t *chunk_pt, int n, int32_t 
 // directly by the single chunk that holds it, or cut by chunk boundaries and
 // summed from the partials of the chunks overlapping it (in chunk order);
 // parts are added in order.  With one part, directly written bins are final.
-__global__ void k_hist_finish(HistArgs A) {
-    const LayoutArgs H = pick(A);
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int b = blockIdx.y;
-    if (k >= A.K) return;
+__device__ __forceinline__ void hist_finish_body(const HistArgs &A, const LayoutArgs &H, int64_t kb, int b) {
+    const int64_t k = kb * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= A.K || b >= A.B) return;
     const int n_chunks = H.P * A.C;
     float total = 0.f;
     bool touched = H.P > 1;
@@ -406,6 +458,19 @@ __global__ void k_hist_finish(HistArgs A) {
     if (touched) A.hist[k * A.B + b] = total;
 }
 
+__global__ void k_hist_finish(HistArgs A) {
+    const LayoutArgs H = pick(A);
+    hist_finish_body(A, H, blockIdx.x, blockIdx.y);
+}
+
+// Batched finish: items[i] = (instance, density block, first of 8 bins).
+__global__ void k_hist_finish_batched(const HistArgs *__restrict__ insts, const int4 *__restrict__ items) {
+    const int4 it = items[blockIdx.x];
+    const HistArgs A = insts[it.x];
+    const LayoutArgs H = pick(A);
+    for (int b = it.z; b < it.z + 8; ++b) hist_finish_body(A, H, it.y, b);
+}
+
 }  // namespace
 
 int vup_hist_chunks_for(int64_t N) {
@@ -422,7 +487,9 @@ int vup_hist_parts_for(int64_t n_last, int n_bins) {
     return P;
 }
 
-vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
+// Arguments of the histogram kernels for one grid; `rows` receives the
+// largest shared-memory tile (rows of one part of a gathered axis).
+static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows, int &P_max) {
     const int64_t K_pad = ceil_div64(K, 128) * 128;
     const int nd = g->ndim;
     auto tab = [&](int axis) {
@@ -431,8 +498,8 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
         return (const float *)g->ftab.p + off;
     };
     HistArgs A{};
-    int64_t rows = 0;
-    int P_max = 1;
+    rows = 0;
+    P_max = 1;
     for (int l = 0; l < 2; ++l) {
         const auto &HL = g->hl[l < g->n_layouts ? l : 0];
         LayoutArgs &La = l == 0 ? A.L0 : A.L1;
@@ -471,6 +538,14 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
     A.part = (float *)g->hist_part.p;
     A.direct = (float *)g->hist_direct.p;
     A.dstatus = g->dstatus;
+    return A;
+}
+
+vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
+    const int nd = g->ndim;
+    int64_t rows;
+    int P_max;
+    const HistArgs A = hist_args_for(g, K, hist, rows, P_max);
     const size_t smem = hist_smem_bytes(rows);
     // run-end words encode the rest index in 15 bits (3-D: a0 < 256, a1 < 128)
     const bool coded = nd == 2 || (g->n[0] <= 256 && g->n[1] <= 128);
@@ -494,6 +569,95 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
     VUP_PROF("hist_fixup", s, 1);
     dim3 fg((unsigned)ceil_div64(K, 128), (unsigned)g->B);
     k_hist_finish<<<fg, 128, 0, s>>>(A);
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}
+
+// A 2-D grid whose every part fits the shared-memory tile.
+bool vup_hist_batchable(vup_grid g) {
+    if (g->ndim != 2) return false;
+    for (int l = 0; l < g->n_layouts; ++l)
+        if (hist_smem_bytes(g->hl[l].part_rows) > 220 * 1024) return false;
+    return true;
+}
+
+// Batched histograms of n 2-D instances: one persistent launch over every
+// instance's (part, chunk group, density tile) items, longest first, and one
+// finishing launch.
+struct HistPlan {
+    DevBuf args, items, fitems;
+    int n_items = 0, n_fitems = 0;
+    int64_t rows = 0;
+};
+
+vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *const *hists, void **out) {
+    std::vector<HistArgs> args(n);
+    std::vector<std::pair<int64_t, HistItem>> work;
+    std::vector<int4> fin;
+    int64_t rows_max = 0;
+    for (int i = 0; i < n; ++i) {
+        int64_t rows;
+        int P_max;
+        args[i] = hist_args_for(gs[i], Ks[i], hists[i], rows, P_max);
+        if (!hists[i]) continue;
+        rows_max = std::max(rows_max, rows);
+        const int G = args[i].C / kHistWarps;
+        const int64_t nkt = ceil_div64(Ks[i], kKT);
+        // cost of one item: points per chunk x densities per tile
+        const int64_t cost = gs[i]->N / std::max<int64_t>(1, (int64_t)P_max * args[i].C);
+        for (int p = 0; p < P_max; ++p)
+            for (int cg = 0; cg < G; ++cg)
+                for (int64_t kt = 0; kt < nkt; ++kt) work.push_back({cost, HistItem{i, p, cg, (int32_t)kt}});
+        for (int64_t kb = 0; kb < ceil_div64(Ks[i], 128); ++kb)
+            for (int b0 = 0; b0 < gs[i]->B; b0 += 8) fin.push_back(make_int4(i, (int)kb, b0, 0));
+    }
+    std::stable_sort(work.begin(), work.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<HistItem> items(work.size());
+    for (size_t q = 0; q < work.size(); ++q) items[q] = work[q].second;
+    HistPlan *P = new HistPlan();
+    P->n_items = (int)items.size();
+    P->n_fitems = (int)fin.size();
+    P->rows = rows_max;
+    vup_status st;
+    if ((st = devbuf_reserve(P->args, sizeof(HistArgs) * n)) != VUP_OK ||
+        (st = devbuf_reserve(P->items, sizeof(HistItem) * std::max<size_t>(1, items.size()))) != VUP_OK ||
+        (st = devbuf_reserve(P->fitems, sizeof(int4) * std::max<size_t>(1, fin.size()))) != VUP_OK) {
+        devbuf_free(P->args);
+        devbuf_free(P->items);
+        devbuf_free(P->fitems);
+        delete P;
+        return st;
+    }
+    VUP_CHECK_CUDA(cudaMemcpy(P->args.p, args.data(), sizeof(HistArgs) * n, cudaMemcpyHostToDevice));
+    VUP_CHECK_CUDA(cudaMemcpy(P->items.p, items.data(), sizeof(HistItem) * items.size(), cudaMemcpyHostToDevice));
+    VUP_CHECK_CUDA(cudaMemcpy(P->fitems.p, fin.data(), sizeof(int4) * fin.size(), cudaMemcpyHostToDevice));
+    // the largest tile any plan may use, so that graphs of earlier plans stay launchable
+    VUP_CHECK_CUDA(
+        cudaFuncSetAttribute(k_hist_batched<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    *out = P;
+    return VUP_OK;
+}
+
+void vup_hist_plan_free(void *plan) {
+    HistPlan *P = (HistPlan *)plan;
+    if (!P) return;
+    devbuf_free(P->args);
+    devbuf_free(P->items);
+    devbuf_free(P->fitems);
+    delete P;
+}
+
+vup_status vup_hist_batched(void *plan, cudaStream_t s) {
+    const HistPlan *P = (const HistPlan *)plan;
+    if (P->n_items == 0) return VUP_OK;
+    const size_t smem = hist_smem_bytes(P->rows);
+    if (smem > 220 * 1024) return VUP_ERR_UNSUPPORTED;
+    VUP_PROF("hist_segmented_batched", s, 2);
+    const int grid = std::max(1, std::min(P->n_items, vup_num_sms()));
+    k_hist_batched<1><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p, (const HistItem *)P->items.p,
+                                                          P->n_items, P->rows);
+    VUP_CHECK_LAUNCH();
+    k_hist_finish_batched<<<P->n_fitems, 128, 0, s>>>((const HistArgs *)P->args.p, (const int4 *)P->fitems.p);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }

@@ -73,6 +73,7 @@ struct vup_grid_s {
 
     // model outputs
     int have_model = 0;
+    uint64_t model_gen = 0;        // bumped whenever the model (and its tables) are rebuilt
     int B = 0, J = 0;
     double host_ext[3] = {0, 0, 1};  // ymin, ymax, s (filled lazily by vup_grid_info)
 
@@ -128,7 +129,7 @@ struct vup_grid_s {
 
     // per-K scratch (density constants, factor tables, partials)
     int64_t K_cap = 0;
-    DevBuf dconst, dstats, ftab, atab_hi, atab_lo, partials, hist_part, hist_direct, ipsa_part;
+    DevBuf dconst, dstats, dpart, ftab, atab_hi, atab_lo, partials, hist_part, hist_direct, ipsa_part;
 
     int *dstatus = nullptr;        // [1] device status word
 };
@@ -157,6 +158,35 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
                             cudaStream_t s);
 
 int vup_num_sms();
+bool vup_profiling();
+vup_status vup_check_dens(vup_grid g, const vup_densities *d);
+vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa);
+
+// Batched stages over many 2-D instances.  Each *_plan builds host-side work
+// lists and uploads them into device memory it owns (synchronous; never call
+// during stream capture); each *_batched launch is stream-ordered and
+// capturable; *_plan_free releases a plan.
+vup_status vup_density_reserve(vup_grid g, int64_t K);
+vup_status vup_density_plan(int n, const vup_grid *gs, const vup_densities *ds, bool bf16, void **plan);
+vup_status vup_density_batched(void *plan, cudaStream_t s);
+void vup_density_plan_free(void *plan);
+int64_t vup_tc_col_tiles_bn(const Orient &o, int bn);
+int vup_tc_bn_for(const Orient &o, int bn_cap);
+vup_status vup_tc_plan(int n, const vup_grid *gs, const int64_t *Ks, const int *bns, float *const *parts,
+                       void **plan);
+vup_status vup_tc_batched(void *plan, int *dstatus, cudaStream_t s);
+void vup_tc_plan_free(void *plan);
+vup_status vup_simt_plan(int n, const vup_grid *gs, const int64_t *Ks, float *const *parts, void **plan);
+vup_status vup_simt_batched(void *plan, cudaStream_t s);
+void vup_simt_plan_free(void *plan);
+vup_status vup_finish_plan(int n, const vup_grid *gs, const int64_t *Ks, const int64_t *n_cts,
+                           float *const *parts, double *const *raws, double *const *centrals, void **plan);
+vup_status vup_finish_batched(void *plan, cudaStream_t s);
+void vup_finish_plan_free(void *plan);
+bool vup_hist_batchable(vup_grid g);
+vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *const *hists, void **plan);
+vup_status vup_hist_batched(void *plan, cudaStream_t s);
+void vup_hist_plan_free(void *plan);
 
 // Per-kernel timing scope (active only while vup_profile(1) is in effect):
 // records a CUDA event pair on `s` around the launches made in its lifetime.

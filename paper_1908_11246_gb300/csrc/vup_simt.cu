@@ -12,6 +12,9 @@
 
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 16;
@@ -26,16 +29,25 @@ struct EpiArgs {
     int rest_axis;          // axis index of the (single) rest axis for IPSA
 };
 
+// One 128 x 128 output tile: column tile ct, row (density) tile rt.
+struct SimtJob {
+    const float *A;
+    const float *Zt;
+    int64_t R, K_pad, ldz;
+    EpiArgs ep;
+    int64_t n_ct;
+    float *part;
+};
+
 template <int NOUT>
-__global__ void __launch_bounds__(256, NOUT == 1 ? 2 : 1)
-k_moments_simt(const float *__restrict__ A, const float *__restrict__ Zt, int64_t R, int64_t K_pad,
-               int64_t ldz, EpiArgs ep, int64_t n_ct, float *__restrict__ part) {
+__device__ __forceinline__ void simt_tile(const float *__restrict__ A, const float *__restrict__ Zt, int64_t R,
+                                          int64_t K_pad, int64_t ldz, const EpiArgs &ep, int64_t n_ct,
+                                          float *__restrict__ part, int64_t ct, int64_t row_tile) {
     __shared__ __align__(16) float As[2][BK][BM];
     __shared__ __align__(16) float Bs[2][BK][BN];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int64_t ct = blockIdx.x;         // column tile
-    const int64_t k0 = (int64_t)blockIdx.y * BM;
+    const int64_t k0 = row_tile * BM;
     const int64_t c0 = ct * BN;
 
     float acc[8][8];
@@ -161,12 +173,43 @@ k_moments_simt(const float *__restrict__ A, const float *__restrict__ Zt, int64_
     }
 }
 
+template <int NOUT>
+__global__ void __launch_bounds__(256, NOUT == 1 ? 2 : 1)
+k_moments_simt(const float *__restrict__ A, const float *__restrict__ Zt, int64_t R, int64_t K_pad,
+               int64_t ldz, EpiArgs ep, int64_t n_ct, float *__restrict__ part) {
+    simt_tile<NOUT>(A, Zt, R, K_pad, ldz, ep, n_ct, part, blockIdx.x, blockIdx.y);
+}
+
+// Batched form: one persistent launch over the tiles of many instances,
+// longest reductions first (items[t] = (instance, column tile, row tile)).
+__global__ void __launch_bounds__(256, 2)
+k_moments_simt_batched(const SimtJob *__restrict__ jobs, const int4 *__restrict__ items, int n_items) {
+    for (int t = blockIdx.x; t < n_items; t += gridDim.x) {
+        const int4 it = items[t];
+        const SimtJob J = jobs[it.x];
+        simt_tile<1>(J.A, J.Zt, J.R, J.K_pad, J.ldz, J.ep, J.n_ct, J.part, it.y, it.z);
+        __syncthreads();
+    }
+}
+
 // Sum the per-column-tile partials in FP64, undo the normalisation and the
 // power-table scale, and form central moments about the mean.
-__global__ void k_moments_finish(const float *__restrict__ part, int64_t n_ct, int64_t K, int64_t K_pad, int J,
-                                 const DensStats *__restrict__ ds, int ndim, const double *__restrict__ scale,
-                                 double *__restrict__ raw, double *__restrict__ central) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+struct FinishJob {
+    const float *part;
+    int64_t n_ct, K, K_pad;
+    int J;
+    const DensStats *ds;
+    int ndim;
+    const double *scale;
+    double *raw, *central;
+};
+
+__device__ __forceinline__ void moments_finish_body(const float *__restrict__ part, int64_t n_ct, int64_t K,
+                                                    int64_t K_pad, int J, const DensStats *__restrict__ ds,
+                                                    int ndim, const double *__restrict__ scale,
+                                                    double *__restrict__ raw, double *__restrict__ central,
+                                                    int64_t kb) {
+    const int64_t k = kb * (int64_t)blockDim.x + threadIdx.x;
     if (k >= K) return;
     double mz[4] = {0, 0, 0, 0};
     for (int64_t t = 0; t < n_ct; ++t) {
@@ -193,6 +236,18 @@ __global__ void k_moments_finish(const float *__restrict__ part, int64_t n_ct, i
         c[3] = M[3] - 4.0 * m * M[2] + 6.0 * m * m * M[1] - 3.0 * m * m * m * m;
         for (int j = 0; j < J; ++j) central[k * J + j] = c[j];
     }
+}
+
+__global__ void k_moments_finish(const float *__restrict__ part, int64_t n_ct, int64_t K, int64_t K_pad, int J,
+                                 const DensStats *__restrict__ ds, int ndim, const double *__restrict__ scale,
+                                 double *__restrict__ raw, double *__restrict__ central) {
+    moments_finish_body(part, n_ct, K, K_pad, J, ds, ndim, scale, raw, central, blockIdx.x);
+}
+
+__global__ void k_moments_finish_batched(const FinishJob *__restrict__ jobs, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];
+    const FinishJob F = jobs[it.x];
+    moments_finish_body(F.part, F.n_ct, F.K, F.K_pad, F.J, F.ds, F.ndim, F.scale, F.raw, F.central, it.y);
 }
 
 // IPSA combine.  With u_d = (x_d - mu_d) / sigma_d and W = g / sum g,
@@ -311,6 +366,133 @@ vup_status vup_ipsa_finish(vup_grid g, int64_t K, int n_tiles0, int n_tiles1, co
     k_ipsa_finish<<<(unsigned)ceil_div64(K, 128), 128, 0, s>>>(
         p0, n_tiles0, p1, n_tiles1, K, K_pad, g->J, (const DensStats *)g->dstats.p,
         (const DensConst *)g->dconst.p, g->ndim, g->ydev_scale, grad, dmu, dsg);
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}
+
+// Batched FP32 contraction over n 2-D instances (orientation 0): instance i
+// writes its partials [n_ct][K_pad][4] to parts[i]; tiles of the longest
+// reductions first.
+struct SimtPlan {
+    DevBuf jobs, items;
+    int n_items = 0;
+};
+
+vup_status vup_simt_plan(int n, const vup_grid *gs, const int64_t *Ks, float *const *parts, void **out) {
+    std::vector<SimtJob> jobs(n);
+    std::vector<std::pair<int64_t, int4>> work;
+    for (int i = 0; i < n; ++i) {
+        vup_grid g = gs[i];
+        const Orient &o = g->orient[0];
+        const int64_t K_pad = ceil_div64(Ks[i], 128) * 128;
+        int64_t off = 0;
+        for (int q = 0; q < o.red_axis0; ++q) off += g->n[q] * K_pad;
+        SimtJob &J = jobs[i];
+        J.A = (const float *)g->ftab.p + off;
+        J.Zt = g->zs[0];
+        J.R = o.R;
+        J.K_pad = K_pad;
+        J.ldz = ceil_div64(o.NC, 128) * 128;
+        J.ep = epi_for(g, 0, K_pad);
+        J.n_ct = vup_simt_col_tiles(o);
+        J.part = parts[i];
+        for (int64_t rt = 0; rt < K_pad / BM; ++rt)
+            for (int64_t ct = 0; ct < J.n_ct; ++ct) work.push_back({o.R, make_int4(i, (int)ct, (int)rt, 0)});
+    }
+    std::stable_sort(work.begin(), work.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<int4> items(work.size());
+    for (size_t q = 0; q < work.size(); ++q) items[q] = work[q].second;
+    SimtPlan *P = new SimtPlan();
+    P->n_items = (int)items.size();
+    vup_status st;
+    if ((st = devbuf_reserve(P->jobs, sizeof(SimtJob) * n)) != VUP_OK ||
+        (st = devbuf_reserve(P->items, sizeof(int4) * std::max<size_t>(1, items.size()))) != VUP_OK) {
+        devbuf_free(P->jobs);
+        devbuf_free(P->items);
+        delete P;
+        return st;
+    }
+    VUP_CHECK_CUDA(cudaMemcpy(P->jobs.p, jobs.data(), sizeof(SimtJob) * n, cudaMemcpyHostToDevice));
+    VUP_CHECK_CUDA(cudaMemcpy(P->items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    *out = P;
+    return VUP_OK;
+}
+
+void vup_simt_plan_free(void *plan) {
+    SimtPlan *P = (SimtPlan *)plan;
+    if (!P) return;
+    devbuf_free(P->jobs);
+    devbuf_free(P->items);
+    delete P;
+}
+
+vup_status vup_simt_batched(void *plan, cudaStream_t s) {
+    const SimtPlan *P = (const SimtPlan *)plan;
+    if (P->n_items == 0) return VUP_OK;
+    const int grid = std::min(P->n_items, 2 * vup_num_sms());
+    VUP_PROF("moments_fp32_simt_batched", s, 1);
+    k_moments_simt_batched<<<grid, 256, 0, s>>>((const SimtJob *)P->jobs.p, (const int4 *)P->items.p, P->n_items);
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}
+
+// Batched FP64 finish: instance i sums n_cts[i] column-tile partials from
+// parts[i] into raws[i] / centrals[i] (either may be null).
+struct FinishPlan {
+    DevBuf jobs, items;
+    int n_items = 0;
+};
+
+vup_status vup_finish_plan(int n, const vup_grid *gs, const int64_t *Ks, const int64_t *n_cts,
+                           float *const *parts, double *const *raws, double *const *centrals, void **out) {
+    std::vector<FinishJob> jobs(n);
+    std::vector<int2> items;
+    for (int i = 0; i < n; ++i) {
+        vup_grid g = gs[i];
+        FinishJob &F = jobs[i];
+        F.part = parts[i];
+        F.n_ct = n_cts[i];
+        F.K = Ks[i];
+        F.K_pad = ceil_div64(Ks[i], 128) * 128;
+        F.J = g->J;
+        F.ds = (const DensStats *)g->dstats.p;
+        F.ndim = g->ndim;
+        F.scale = g->ydev_scale;
+        F.raw = raws ? raws[i] : nullptr;
+        F.central = centrals ? centrals[i] : nullptr;
+        if (!F.raw && !F.central) continue;
+        for (int64_t kb = 0; kb < ceil_div64(Ks[i], 128); ++kb) items.push_back(make_int2(i, (int)kb));
+    }
+    FinishPlan *P = new FinishPlan();
+    P->n_items = (int)items.size();
+    vup_status st;
+    if ((st = devbuf_reserve(P->jobs, sizeof(FinishJob) * n)) != VUP_OK ||
+        (st = devbuf_reserve(P->items, sizeof(int2) * std::max<size_t>(1, items.size()))) != VUP_OK) {
+        devbuf_free(P->jobs);
+        devbuf_free(P->items);
+        delete P;
+        return st;
+    }
+    VUP_CHECK_CUDA(cudaMemcpy(P->jobs.p, jobs.data(), sizeof(FinishJob) * n, cudaMemcpyHostToDevice));
+    if (!items.empty())
+        VUP_CHECK_CUDA(cudaMemcpy(P->items.p, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+    *out = P;
+    return VUP_OK;
+}
+
+void vup_finish_plan_free(void *plan) {
+    FinishPlan *P = (FinishPlan *)plan;
+    if (!P) return;
+    devbuf_free(P->jobs);
+    devbuf_free(P->items);
+    delete P;
+}
+
+vup_status vup_finish_batched(void *plan, cudaStream_t s) {
+    const FinishPlan *P = (const FinishPlan *)plan;
+    if (P->n_items == 0) return VUP_OK;
+    VUP_PROF("moments_finish_fp64_batched", s, 1);
+    k_moments_finish_batched<<<P->n_items, 128, 0, s>>>((const FinishJob *)P->jobs.p, (const int2 *)P->items.p);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }

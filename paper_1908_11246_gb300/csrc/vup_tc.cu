@@ -23,6 +23,8 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 namespace {
 
@@ -94,16 +96,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major,
+// M = 128, N = bn (a multiple of 16 up to 256).
+__host__ __device__ constexpr uint32_t idesc_for(int bn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
@@ -138,11 +143,30 @@ struct TcEpi {
     int ndim, rest_axis;
 };
 
-template <int NOUT>
+// Batched instance descriptor (device memory, 128-byte aligned): the four
+// operand tensor maps of one instance, its column-tile width bn (64, 128 or
+// 256; the B maps' box is bn rows) and its epilogue parameters.
+struct alignas(128) TcInst {
+    CUtensorMap maps[4];  // A hi, A lo, B hi, B lo
+    TcEpi ep;
+    int64_t K_pad;
+    float *part;
+    int n_n, n_kb, bn;
+};
+struct TcTile {
+    int32_t inst, m, n, pad;
+};
+
+// kBatched == false: one instance, tensor maps as kernel parameters, tiles
+// t -> (m, n) = (t / n_n, t % n_n).  kBatched == true: tiles come from a work
+// list over many instances and each tile's maps and epilogue parameters from
+// its instance descriptor.
+template <int NOUT, bool kBatched>
 __global__ void __launch_bounds__(kThreads, 1)
 k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int n_m, int n_n,
-             int n_kb, int64_t K_pad, TcEpi ep, float *__restrict__ part, int *__restrict__ dstatus) {
+             int n_kb, int64_t K_pad, TcEpi ep, float *__restrict__ part, const TcInst *__restrict__ insts,
+             const TcTile *__restrict__ tiles, int n_tiles_batched, int *__restrict__ dstatus) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
@@ -154,7 +178,24 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = n_m * n_n;
+    const int n_tiles = kBatched ? n_tiles_batched : n_m * n_n;
+    // tile t -> (instance, row tile, column tile, k-blocks, tile width)
+    auto tile_at = [&](int t, int &m, int &n, int &nkb, int &bn, const TcInst *&in) {
+        if (kBatched) {
+            const TcTile tt = tiles[t];
+            in = insts + tt.inst;
+            m = tt.m;
+            n = tt.n;
+            nkb = in->n_kb;
+            bn = in->bn;
+        } else {
+            in = nullptr;
+            m = t / n_n;
+            n = t - m * n_n;
+            nkb = n_kb;
+            bn = BN;
+        }
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -186,16 +227,22 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
             uint32_t it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                const int m = t / n_n, n = t - m * n_n;
-                for (int kb = 0; kb < n_kb; ++kb, ++it) {
+                int m, n, nkb, bn;
+                const TcInst *in;
+                tile_at(t, m, n, nkb, bn, in);
+                const CUtensorMap *mAh = kBatched ? &in->maps[0] : &tmAh;
+                const CUtensorMap *mAl = kBatched ? &in->maps[1] : &tmAl;
+                const CUtensorMap *mBh = kBatched ? &in->maps[2] : &tmBh;
+                const CUtensorMap *mBl = kBatched ? &in->maps[3] : &tmBl;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % STAGES;
                     if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, dstatus)) { ok = false; break; }
                     uint8_t *st = smem + s * STAGE_BYTES;
-                    mbar_expect_tx(&full[s], STAGE_BYTES);
-                    tma_load_2d(st, &tmAh, &full[s], kb * BK, m * BM);
-                    tma_load_2d(st + A_BYTES, &tmAl, &full[s], kb * BK, m * BM);
-                    tma_load_2d(st + 2 * A_BYTES, &tmBh, &full[s], kb * BK, n * BN);
-                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmBl, &full[s], kb * BK, n * BN);
+                    mbar_expect_tx(&full[s], 2 * A_BYTES + 4 * bn * BK);
+                    tma_load_2d(st, mAh, &full[s], kb * BK, m * BM);
+                    tma_load_2d(st + A_BYTES, mAl, &full[s], kb * BK, m * BM);
+                    tma_load_2d(st + 2 * A_BYTES, mBh, &full[s], kb * BK, n * bn);
+                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, mBl, &full[s], kb * BK, n * bn);
                 }
             }
             // drain: every issued stage must land before shared memory is released
@@ -212,11 +259,15 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
             uint32_t it = 0, tile_it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tile_it) {
+                int m_, n_, nkb, bn;
+                const TcInst *in_;
+                tile_at(t, m_, n_, nkb, bn, in_);
+                const uint32_t idesc = idesc_for(bn);
                 const int b = tile_it & 1;
                 if (!mbar_wait(&tempty[b], ((tile_it >> 1) & 1) ^ 1, abort_flag, dstatus)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dcol = tmem_base + (uint32_t)(b * BN);
-                for (int kb = 0; kb < n_kb; ++kb, ++it) {
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % STAGES;
                     if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, dstatus)) { ok = false; break; }
                     tc_fence_after();
@@ -228,9 +279,9 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t off = kk * 32;  // 16 bf16 along K inside the swizzle atom
                         const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-                        umma_bf16(dcol, sw128_desc(a_lo + off), sw128_desc(b_hi + off), acc0);
-                        umma_bf16(dcol, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
-                        umma_bf16(dcol, sw128_desc(a_hi + off), sw128_desc(b_hi + off), 1u);
+                        umma_bf16(dcol, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, acc0);
+                        umma_bf16(dcol, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+                        umma_bf16(dcol, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, 1u);
                     }
                     umma_commit(&empty[s]);
                 }
@@ -248,7 +299,13 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
         const int row = quad * 32 + lane;
         uint32_t tile_it = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tile_it) {
-            const int m = t / n_n, n = t - m * n_n;
+            int m, n, nkb, bn;
+            const TcInst *in;
+            tile_at(t, m, n, nkb, bn, in);
+            const TcEpi &E = kBatched ? in->ep : ep;
+            const int64_t Kp = kBatched ? in->K_pad : K_pad;
+            const int nn = kBatched ? in->n_n : n_n;
+            float *const P = kBatched ? in->part : part;
             const int b = tile_it & 1;
             if (!mbar_wait(&tfull[b], (tile_it >> 1) & 1, abort_flag, dstatus)) break;
             tc_fence_after();
@@ -259,24 +316,24 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
 #pragma unroll
                 for (int j = 0; j < 4; ++j) out[o][j] = 0.f;
             DensConst dc{};
-            if (NOUT == 3) dc = ep.dconst[k * ep.ndim + ep.rest_axis];
+            if (NOUT == 3) dc = E.dconst[k * E.ndim + E.rest_axis];
             const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN);
 #pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ++ch) {
+            for (int ch = 0; ch < bn / 32; ++ch) {
                 float v[32];
                 tmem_ld32(tbase + ch * 32, v);
-                const int64_t q0 = (int64_t)n * (BN / 4) + ch * 8;
+                const int64_t q0 = (int64_t)n * (bn / 4) + ch * 8;
                 float e[8];
 #pragma unroll
                 for (int qq = 0; qq < 8; ++qq) {
                     const int64_t q = q0 + qq;
                     float w = 0.f;
-                    if (q < ep.Q) {
-                        if (ep.g_rest1) {
-                            const int64_t qa = q / ep.n_rest1, qb = q - qa * ep.n_rest1;
-                            w = ep.g_rest0[qa * K_pad + k] * ep.g_rest1[qb * K_pad + k];
+                    if (q < E.Q) {
+                        if (E.g_rest1) {
+                            const int64_t qa = q / E.n_rest1, qb = q - qa * E.n_rest1;
+                            w = E.g_rest0[qa * Kp + k] * E.g_rest1[qb * Kp + k];
                         } else {
-                            w = ep.g_rest0[q * K_pad + k];
+                            w = E.g_rest0[q * Kp + k];
                         }
                     }
                     e[qq] = w;
@@ -302,7 +359,7 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
             if (lane == 0) mbar_arrive(&tempty[b]);
 #pragma unroll
             for (int o = 0; o < NOUT; ++o)
-                *reinterpret_cast<float4 *>(part + (((int64_t)o * n_n + n) * K_pad + k) * 4) =
+                *reinterpret_cast<float4 *>(P + (((int64_t)o * nn + n) * Kp + k) * 4) =
                     make_float4(out[o][0], out[o][1], out[o][2], out[o][3]);
         }
     }
@@ -385,12 +442,117 @@ vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *p
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
     VUP_PROF(n_out == 1 ? "moments_bf16x3_tc" : "ipsa_bf16x3_tc", s, 1);
     if (n_out == 1) {
-        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_moments_tc<1><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, g->dstatus);
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_moments_tc<1, false><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, nullptr,
+                                                            nullptr, 0, g->dstatus);
     } else {
-        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_moments_tc<3><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, g->dstatus);
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_moments_tc<3, false><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, nullptr,
+                                                            nullptr, 0, g->dstatus);
     }
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}
+
+// Column tiles of an orientation at tile width bn.
+int64_t vup_tc_col_tiles_bn(const Orient &o, int bn) { return ceil_div64(o.NC, bn); }
+
+// Tile width of one instance: the smallest of 64 / 128 / 256 that covers the
+// instance's columns, capped at bn_cap (narrower tiles waste less padding on
+// small instances and give the persistent kernel finer work to balance).
+int vup_tc_bn_for(const Orient &o, int bn_cap) {
+    int bn = 64;
+    while (bn < BN && bn < bn_cap && bn < o.NC) bn *= 2;
+    return bn;
+}
+
+// Batched raw-moment contraction over n 2-D instances: instance i writes its
+// partials [n_n][K_pad][4] to parts[i].  The tile list holds every instance's
+// (row tile, column tile) pairs, longest reductions first.
+struct TcPlan {
+    DevBuf insts, tiles;
+    int n_tiles = 0;
+};
+
+vup_status vup_tc_plan(int n, const vup_grid *gs, const int64_t *Ks, const int *bns, float *const *parts,
+                       void **out) {
+    std::vector<TcInst> insts(n);
+    std::vector<std::pair<int64_t, TcTile>> work;
+    for (int i = 0; i < n; ++i) {
+        vup_grid g = gs[i];
+        const Orient &o = g->orient[0];
+        const int bn = bns[i];
+        const int64_t K_pad = ceil_div64(Ks[i], 128) * 128;
+        const int64_t rows_b = ceil_div64(o.NC, 256) * 256;
+        TcInst &I = insts[i];
+        memset(&I, 0, sizeof(I));
+        if (!make_map(&I.maps[0], g->atab_hi.p, o.R_pad, K_pad, BM) ||
+            !make_map(&I.maps[1], g->atab_lo.p, o.R_pad, K_pad, BM) ||
+            !make_map(&I.maps[2], g->zt_hi[0], o.R_pad, rows_b, bn) ||
+            !make_map(&I.maps[3], g->zt_lo[0], o.R_pad, rows_b, bn))
+            return VUP_ERR_CUDA;
+        auto tab = [&](int axis) {
+            int64_t off = 0;
+            for (int q = 0; q < axis; ++q) off += g->n[q] * K_pad;
+            return (const float *)g->ftab.p + off;
+        };
+        I.ep.g_rest0 = tab(o.rest_axes[0]);
+        I.ep.g_rest1 = nullptr;
+        I.ep.n_rest1 = 1;
+        I.ep.Q = o.Q;
+        I.ep.dconst = (const DensConst *)g->dconst.p;
+        I.ep.ndim = g->ndim;
+        I.ep.rest_axis = o.rest_axes[0];
+        I.K_pad = K_pad;
+        I.part = parts[i];
+        I.n_n = (int)vup_tc_col_tiles_bn(o, bn);
+        I.n_kb = (int)(o.R_pad / BK);
+        I.bn = bn;
+        const int64_t cost = (int64_t)(I.n_kb + 2) * bn;
+        for (int m = 0; m < (int)(K_pad / BM); ++m)
+            for (int c = 0; c < I.n_n; ++c) work.push_back({cost, TcTile{i, m, c, 0}});
+    }
+    std::stable_sort(work.begin(), work.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<TcTile> tiles(work.size());
+    for (size_t q = 0; q < work.size(); ++q) tiles[q] = work[q].second;
+    TcPlan *P = new TcPlan();
+    P->n_tiles = (int)tiles.size();
+    vup_status st;
+    if ((st = devbuf_reserve(P->insts, sizeof(TcInst) * n)) != VUP_OK ||
+        (st = devbuf_reserve(P->tiles, sizeof(TcTile) * std::max<size_t>(1, tiles.size()))) != VUP_OK) {
+        devbuf_free(P->insts);
+        devbuf_free(P->tiles);
+        delete P;
+        return st;
+    }
+    VUP_CHECK_CUDA(cudaMemcpy(P->insts.p, insts.data(), sizeof(TcInst) * n, cudaMemcpyHostToDevice));
+    VUP_CHECK_CUDA(cudaMemcpy(P->tiles.p, tiles.data(), sizeof(TcTile) * tiles.size(), cudaMemcpyHostToDevice));
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+    VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    *out = P;
+    return VUP_OK;
+}
+
+void vup_tc_plan_free(void *plan) {
+    TcPlan *P = (TcPlan *)plan;
+    if (!P) return;
+    devbuf_free(P->insts);
+    devbuf_free(P->tiles);
+    delete P;
+}
+
+vup_status vup_tc_batched(void *plan, int *dstatus, cudaStream_t s) {
+    const TcPlan *P = (const TcPlan *)plan;
+    if (P->n_tiles == 0) return VUP_OK;
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+    const int grid = std::min(P->n_tiles, vup_num_sms());
+    VUP_PROF("moments_bf16x3_tc_batched", s, 1);
+    CUtensorMap dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    TcEpi ep{};
+    k_moments_tc<1, true><<<grid, kThreads, smem, s>>>(dummy, dummy, dummy, dummy, 0, 0, 0, 0, ep, nullptr,
+                                                       (const TcInst *)P->insts.p, (const TcTile *)P->tiles.p,
+                                                       P->n_tiles, dstatus);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }

@@ -25,7 +25,7 @@ PRECISIONS = {"fp64": VUP_FP64, "fp32": VUP_FP32, "bf16x3": VUP_BF16X3}
 # exported symbols declared in include/vup.h
 ABI_SYMBOLS = [
     "vup_grid_create", "vup_grid_destroy", "vup_eval_model", "vup_set_outputs", "vup_propagate",
-    "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_sync",
+    "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_batched_report", "vup_sync",
     "vup_grid_info", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
     "vup_profile_read",
 ]
@@ -69,6 +69,7 @@ def lib():
         l.vup_ipsa_sensitivity.argtypes = [vp, C.POINTER(vup_densities), C.c_int, vp, vp, vp, vp]
         l.vup_propagate_batched.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vup_densities), C.c_int,
                                             C.POINTER(vp), C.POINTER(vp), vp]
+        l.vup_batched_report.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
         l.vup_sync.argtypes = [vp, vp]
         l.vup_grid_info.argtypes = [vp, C.POINTER(vup_grid_info_t)]
         l.vup_grid_copy.argtypes = [vp, C.c_int, vp, C.c_size_t, vp]
@@ -175,6 +176,36 @@ def vup_propagate_batched(handles, dens_list, precision, raws, hists, stream=Non
     hh = (C.c_void_p * n)(*[None if x is None else x.data_ptr() for x in hists])
     _check(lib().vup_propagate_batched(n, hs, ds, int(precision), rs, hh, _stream(stream)),
            "vup_propagate_batched")
+
+
+def vup_batched_report():
+    cap, src, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(lib().vup_batched_report(C.byref(cap), C.byref(src), C.byref(ms)), "vup_batched_report")
+    return {"bn_cap": cap.value, "source": src.value, "tune_ms": ms.value}
+
+
+def batched_outputs(grids, dev_dens_list, moments=True, hist=True):
+    """Per-instance output tensors (raw moments [K][J], histograms [K][B])."""
+    import torch
+    raws, hists = [], []
+    for g, dd in zip(grids, dev_dens_list):
+        K = dd["mu"].shape[0]
+        dev = dd["mu"].device
+        raws.append(torch.empty((K, g.n_moments or 1), dtype=torch.float64, device=dev) if moments else None)
+        hists.append(torch.empty((K, g.n_bins or 1), dtype=torch.float32, device=dev) if hist else None)
+    return raws, hists
+
+
+def propagate_batched(grids, dev_dens_list, precision="bf16x3", moments=True, hist=True, out=None,
+                      stream=None):
+    """Propagate many (grid, densities) instances in one batched call; returns
+    per-instance lists of raw moments and histograms (``out`` reuses a pair of
+    lists from ``batched_outputs``, which lets later calls replay the batch's
+    graph)."""
+    raws, hists = out if out is not None else batched_outputs(grids, dev_dens_list, moments, hist)
+    ds = [make_densities(dd) for dd in dev_dens_list]
+    vup_propagate_batched([g.h for g in grids], ds, PRECISIONS[precision], raws, hists, stream)
+    return raws, hists
 
 
 def vup_sync(h, stream=None):
