@@ -117,31 +117,52 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    prob = I.config(args.config)
     from oracle import oracle as O
     threads = os.cpu_count() or 1
-    y = O.eval_model(prob.model_id, prob.theta, prob.n, prob.lo, prob.hi)
-    b, _, _ = O.bins(y, prob.n_bins)
     rows_per_step = threads
     rng = np.random.default_rng(0)
+    if args.config == "c5":
+        # one instance per step (drawn from the batch), `threads` of its distributions
+        probs = I.oscillator_batch(5, n_inst=512)
+        cache = {}
 
-    def step():
-        rows = rng.choice(prob.K, size=rows_per_step, replace=False)
-        O.propagate(prob.n, prob.lo, prob.hi, y, b, prob.n_bins, prob.n_moments, prob.dens, rows=rows,
-                    threads=threads)
+        def step():
+            i = int(rng.integers(len(probs)))
+            p = probs[i]
+            if i not in cache:
+                y = O.eval_model(p.model_id, p.theta, p.n, p.lo, p.hi)
+                cache[i] = (y, O.bins(y, p.n_bins)[0])
+            y, b = cache[i]
+            rows = rng.choice(p.K, size=min(rows_per_step, p.K), replace=False)
+            O.propagate(p.n, p.lo, p.hi, y, b, p.n_bins, p.n_moments, p.dens, rows=rows, threads=threads)
+            return len(rows) * p.N
+        prob = None
+    else:
+        prob = I.config("c2" if args.config == "weights" else args.config)
+        if args.k or args.config == "weights":
+            prob.dens = prob.dens.take(range(min(args.k or 1024, prob.K)))
+        y = O.eval_model(prob.model_id, prob.theta, prob.n, prob.lo, prob.hi)
+        b, _, _ = O.bins(y, prob.n_bins)
+
+        def step():
+            rows = rng.choice(prob.K, size=min(rows_per_step, prob.K), replace=False)
+            O.propagate(prob.n, prob.lo, prob.hi, y, b, prob.n_bins, prob.n_moments, prob.dens, rows=rows,
+                        threads=threads)
+            return len(rows) * prob.N
 
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
+    units = 0
     for _ in range(args.steps):
-        step()
+        units += step()
     dt = time.perf_counter() - t0
-    value = args.steps * rows_per_step * prob.N / dt
+    value = units / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "K": prob.K, "N": prob.N, "bins": prob.n_bins,
+            "config": {"workload": WORKLOADS[args.config], "precision": "fp64 (oracle)",
                        "step": f"{rows_per_step} sampled distributions x all grid points"},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": threads,
                              "sample": f"{rows_per_step} distributions per step"},
@@ -150,30 +171,215 @@ def run_reference(args):
     return 0
 
 
-def roofline_for(name, ms, launches, prob, pk, clk_mhz):
+def traffic_for(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` recorded from an ncu
+    capture (dram__bytes_read.sum + dram__bytes_write.sum) in the kernel's
+    summary under profiles/, or None."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_launch:"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except (ValueError, IndexError):
+                return None
+    return None
+
+
+def roofline_for(name, ms, launches, KN, pk, clk_mhz, workload):
     """Algorithmic work of one launch of `name` divided by its event-timed duration."""
-    KN = prob.K * prob.N
     per = ms / max(launches, 1) * 1e-3
     sms = 152
-    if name.startswith("moments_bf16"):
-        a = 24.0 * KN / per / 1e12   # 3 BF16 products x 2J flops per dist-point
+    tr = traffic_for(name, workload)
+    if name.startswith("moments_bf16") or name.startswith("ipsa_bf16"):
+        fl = 24.0 if name.startswith("moments") else 72.0
+        a = fl * KN / launches / per / 1e12
         return {"bound": "tensor", "achieved": a, "peak": pk["bf16_sus"], "unit": "TFLOP/s",
-                "frac": a / pk["bf16_sus"], "traffic": None,
-                "note": f"24 tensor flops/dist-point (BF16x3, J=4), peak = sustained bf16 ({pk['source']})"}
-    if name.startswith("moments_fp32"):
+                "frac": a / pk["bf16_sus"], "traffic": tr,
+                "note": f"{fl:g} tensor flops/dist-point (BF16x3, J=4) per launch; peak = sustained bf16, "
+                        f"of {pk['source']}"}
+    if name.startswith("moments_fp32") or name.startswith("ipsa_fp32"):
+        fl = 8.0 if name.startswith("moments") else 24.0
         peak = sms * 128 * 2 * clk_mhz * 1e6 / 1e12
-        a = 8.0 * KN / per / 1e12
+        a = fl * KN / launches / per / 1e12
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-                "traffic": None, "note": "8 FP32 flops/dist-point; peak = 152 SM x 128 FMA x 2 x median SM clock"}
-    if name.startswith("hist"):
+                "traffic": tr, "note": f"{fl:g} FP32 flops/dist-point; peak = 152 SM x 128 FMA x 2 x median SM clock"}
+    if name.startswith("hist_seg"):
         peak = sms * 128 * clk_mhz * 1e6 / 1e9
-        a = 4.0 * KN / per / 1e9
-        return {"bound": "alu", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": None,
+        a = 4.0 * KN / launches / per / 1e9
+        return {"bound": "alu", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": tr,
                 "note": "one 4-byte shared-memory factor gather per dist-point; peak = 152 SM x 128 B/clk "
                         "shared-memory bandwidth x median SM clock"}
-    a = 4.0 * KN / per / 1e9
+    a = 4.0 * KN / launches / per / 1e9
     return {"bound": "hbm", "achieved": a, "peak": pk["hbm"], "unit": "GB/s", "frac": a / pk["hbm"],
-            "traffic": None}
+            "traffic": tr, "note": f"4 B/dist-point; peak = measured copy bandwidth, of {pk['source']}"}
+
+
+WORKLOADS = {
+    "c2": WORKLOAD,
+    "c3": ("c3: 3-D VUP, y = sin x1 + 7 sin^2 x2 + 0.1 x3^4 sin x1 on a 128^3 midpoint grid over [-pi,pi]^3, "
+           "K=32768 (each axis Gaussian, uniform or truncated normal), 4 moments + 512-bin histograms"),
+    "c4": ("c4: config-2 model on a 2048x2048 grid, K=65536 product Gaussians (256x256 lattice), "
+           "4 moments + 256-bin histograms, then the IPSA adjoint (vector-Jacobian product w.r.t. mu, sigma)"),
+    "c5": ("c5: 512 damped-oscillator instances, square grids of side log-uniform in [32,1024], "
+           "K log-uniform in [64,8192], 4 moments + 128-bin histograms, one batched call per step "
+           "(grids and model outputs built once)"),
+    "weights": ("weights: supplied dense W (FP32 [K][N] in HBM), config-2 grid and model, K=1024, "
+                "4 moments + 256-bin histograms"),
+}
+
+
+class SingleGrid:
+    """c2 / c3 / c4: one grid; a step evaluates the model (values, range, bins,
+    sort, power tables) and propagates all K densities (plus the adjoint for c4)."""
+
+    def __init__(self, name, k, prec, vup, torch):
+        self.vup, self.torch = vup, torch
+        prob = I.config(name)
+        if k:
+            prob.dens = prob.dens.take(range(min(k, prob.K)))
+        self.prob = prob
+        self.ipsa = name == "c4"
+        self.prec = prec
+        self.g = vup.Grid(prob.n, prob.lo, prob.hi)
+        self.dev = vup.densities_to_device(prob.dens)
+        self.ds = vup.make_densities(self.dev)
+        K, J, B = prob.K, prob.n_moments, prob.n_bins
+        dv = "cuda"
+        self.raw = torch.empty((K, J), dtype=torch.float64, device=dv)
+        self.cen = torch.empty((K, J), dtype=torch.float64, device=dv)
+        self.hist = torch.empty((K, B), dtype=torch.float32, device=dv)
+        if self.ipsa:
+            self.grad = torch.ones((K, J), dtype=torch.float64, device=dv)
+            self.dmu = torch.empty((K, 2), dtype=torch.float32, device=dv)
+            self.dsg = torch.empty((K, 2), dtype=torch.float32, device=dv)
+        self.units = K * prob.N
+        self.K = K
+
+    def step(self, stream):
+        v, p = self.vup, self.prob
+        v.vup_eval_model(self.g.h, p.model_id, p.theta, p.n_bins, p.n_moments, stream)
+        v.vup_propagate(self.g.h, self.ds, self.prec, self.raw, self.cen, self.hist, stream)
+        if self.ipsa:
+            v.vup_ipsa_sensitivity(self.g.h, self.ds, self.prec, self.dmu, self.dsg, self.grad, stream)
+
+    def sync(self):
+        self.g.sync()
+
+    def e2e(self):
+        """Host buffers: inputs copied in, every output copied back, each step."""
+        torch = self.torch
+        host = {k: v.cpu().pin_memory() for k, v in self.dev.items()}
+        outs = [self.raw, self.cen, self.hist] + ([self.dmu, self.dsg] if self.ipsa else [])
+        outs_h = [torch.empty_like(x, device="cpu").pin_memory() for x in outs]
+        bi = sum(v.numel() * v.element_size() for v in host.values())
+        bo = sum(x.numel() * x.element_size() for x in outs_h)
+
+        def run(stream):
+            for k, v in host.items():
+                self.dev[k].copy_(v, non_blocking=True)
+            self.step(stream)
+            for h, d in zip(outs_h, outs):
+                h.copy_(d, non_blocking=True)
+        return run, bi, bo
+
+
+class Batched:
+    """c5: many uneven instances, one batched call (graph replay) per step."""
+
+    def __init__(self, prec, vup, torch):
+        self.vup, self.torch = vup, torch
+        self.probs = I.oscillator_batch(5, n_inst=512)
+        self.grids, self.dev = [], []
+        for p in self.probs:
+            g = vup.Grid(p.n, p.lo, p.hi)
+            g.eval_model(p.model_id, p.theta, p.n_bins, p.n_moments)
+            self.grids.append(g)
+            self.dev.append(vup.densities_to_device(p.dens))
+        self.prec = prec
+        self.out = vup.batched_outputs(self.grids, self.dev)
+        self.units = sum(p.K * p.N for p in self.probs)
+        self.K = sum(p.K for p in self.probs)
+        self.call = vup.BatchedArgs([g.h for g in self.grids], [vup.make_densities(d) for d in self.dev],
+                                    self.out[0], self.out[1])
+
+    def step(self, stream):
+        self.call(self.prec, stream)
+
+    def sync(self):
+        for g in self.grids:
+            g.sync()
+
+    def e2e(self):
+        torch = self.torch
+        host = [{k: v.cpu().pin_memory() for k, v in d.items()} for d in self.dev]
+        outs = self.out[0] + self.out[1]
+        outs_h = [torch.empty_like(x, device="cpu").pin_memory() for x in outs]
+        bi = sum(v.numel() * v.element_size() for h in host for v in h.values())
+        bo = sum(x.numel() * x.element_size() for x in outs_h)
+
+        def run(stream):
+            for h, d in zip(host, self.dev):
+                for k, v in h.items():
+                    d[k].copy_(v, non_blocking=True)
+            self.step(stream)
+            for h, d in zip(outs_h, outs):
+                h.copy_(d, non_blocking=True)
+        return run, bi, bo
+
+
+class Weights:
+    """Supplied-W path: dense W [K][N] FP32 resident in HBM, moments + histograms."""
+
+    def __init__(self, k, vup, torch):
+        self.vup, self.torch = vup, torch
+        prob = I.config("c2")
+        prob.dens = prob.dens.take(range(k or 1024))
+        self.prob = prob
+        self.g = vup.Grid(prob.n, prob.lo, prob.hi)
+        self.g.eval_model(prob.model_id, prob.theta, prob.n_bins, prob.n_moments)
+        K, (n0, n1) = prob.K, prob.n
+        # input generation (not the measured path): normalised product Gaussians
+        x0 = torch.linspace(prob.lo[0], prob.hi[0], n0 + 1, dtype=torch.float64, device="cuda")
+        x1 = torch.linspace(prob.lo[1], prob.hi[1], n1 + 1, dtype=torch.float64, device="cuda")
+        x0, x1 = 0.5 * (x0[1:] + x0[:-1]), 0.5 * (x1[1:] + x1[:-1])
+        mu = torch.as_tensor(prob.dens.mu, device="cuda")
+        sg = torch.as_tensor(prob.dens.sigma, device="cuda")
+        w0 = torch.exp(-0.5 * ((x0[None, :] - mu[:, :1]) / sg[:, :1]) ** 2)
+        w1 = torch.exp(-0.5 * ((x1[None, :] - mu[:, 1:]) / sg[:, 1:]) ** 2)
+        w0 = w0 / w0.sum(1, keepdim=True)
+        w1 = w1 / w1.sum(1, keepdim=True)
+        self.W = torch.empty((K, n0 * n1), dtype=torch.float32, device="cuda")
+        for k0 in range(0, K, 64):
+            blk = (w0[k0:k0 + 64, :, None] * w1[k0:k0 + 64, None, :]).reshape(-1, n0 * n1)
+            self.W[k0:k0 + 64] = blk.float()
+        del w0, w1
+        self.raw = torch.empty((K, prob.n_moments), dtype=torch.float64, device="cuda")
+        self.hist = torch.empty((K, prob.n_bins), dtype=torch.float32, device="cuda")
+        self.units = K * prob.N
+        self.K = K
+
+    def step(self, stream):
+        self.vup.vup_propagate_weights(self.g.h, self.W, self.raw, self.hist, stream)
+
+    def sync(self):
+        self.g.sync()
+
+    def e2e(self):
+        torch = self.torch
+        Wh = self.W.cpu().pin_memory()
+        outs = [self.raw, self.hist]
+        outs_h = [torch.empty_like(x, device="cpu").pin_memory() for x in outs]
+        bi = Wh.numel() * Wh.element_size()
+        bo = sum(x.numel() * x.element_size() for x in outs_h)
+
+        def run(stream):
+            self.W.copy_(Wh, non_blocking=True)
+            self.step(stream)
+            for h, d in zip(outs_h, outs):
+                h.copy_(d, non_blocking=True)
+        return run, bi, bo
 
 
 def main():
@@ -183,7 +389,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32"])
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--k", type=int, default=0, help="use the first K densities of the workload (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -204,25 +411,19 @@ def main():
     B.build()
     from paper_1908_11246_gb300 import vup
 
-    prob = I.config(args.config)
     pk = peaks()
     prec = vup.PRECISIONS[args.precision]
-    g = vup.Grid(prob.n, prob.lo, prob.hi)
-    dev = vup.densities_to_device(prob.dens)
-    dstruct = vup.make_densities(dev)
-    K, J, Bn = prob.K, prob.n_moments, prob.n_bins
-    raw = torch.empty((K, J), dtype=torch.float64, device="cuda")
-    cen = torch.empty((K, J), dtype=torch.float64, device="cuda")
-    hist = torch.empty((K, Bn), dtype=torch.float32, device="cuda")
+    if args.config == "c5":
+        work = Batched(prec, vup, torch)
+    elif args.config == "weights":
+        work = Weights(args.k, vup, torch)
+    else:
+        work = SingleGrid(args.config, args.k, prec, vup, torch)
     stream = torch.cuda.current_stream()
 
-    def step():
-        vup.vup_eval_model(g.h, prob.model_id, prob.theta, Bn, J, stream)
-        vup.vup_propagate(g.h, dstruct, prec, raw, cen, hist, stream)
-
     for _ in range(max(3, args.warmup)):
-        step()
-    g.sync()
+        work.step(stream)
+    work.sync()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
     clocks = Clocks(local)
@@ -230,58 +431,55 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    vup.vup_profile(True)
+    # the batched path replays one CUDA graph per step; its per-stage times
+    # come from a separate pass below (profiling makes it launch stage by stage)
+    profile_live = args.config != "c5"
+    if profile_live:
+        vup.vup_profile(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for s in range(args.steps):
         flush.zero_()
         ev[s][0].record(stream)
-        step()
+        work.step(stream)
         ev[s][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    vup.vup_profile(False)
     clk = clocks.stop()
+    if not profile_live:
+        vup.vup_profile(True)
+        for s in range(args.steps):
+            flush.zero_()
+            work.step(stream)
+        torch.cuda.synchronize()
+    vup.vup_profile(False)
     prof = vup.vup_profile_read()
-    g.sync()
+    work.sync()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     t_ms = float(t.item())
     ms_step = t_ms / args.steps
-    value = world * K * prob.N / (ms_step * 1e-3)
+    value = world * work.units / (ms_step * 1e-3)
 
     # end-to-end through the public API with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
-        host = {k: v.cpu().pin_memory() for k, v in dev.items()}
-        raw_h = torch.empty_like(raw, device="cpu").pin_memory()
-        cen_h = torch.empty_like(cen, device="cpu").pin_memory()
-        hist_h = torch.empty_like(hist, device="cpu").pin_memory()
-        bi = sum(v.numel() * v.element_size() for v in host.values())
-        bo = sum(x.numel() * x.element_size() for x in (raw_h, cen_h, hist_h))
+        run, bi, bo = work.e2e()
         n_e2e = max(3, args.steps // 2)
-
-        def e2e_step():
-            for k, v in host.items():
-                dev[k].copy_(v, non_blocking=True)
-            step()
-            raw_h.copy_(raw, non_blocking=True)
-            cen_h.copy_(cen, non_blocking=True)
-            hist_h.copy_(hist, non_blocking=True)
-
-        e2e_step()
+        run(stream)
         torch.cuda.synchronize()
         tot = 0.0
         for _ in range(n_e2e):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            e2e_step()
+            run(stream)
             torch.cuda.synchronize()
             tot += time.perf_counter() - t0
-        e2e = {"value": world * K * prob.N / (tot / n_e2e), "unit": UNIT, "h2d_bytes_per_step": bi,
+        work.sync()
+        e2e = {"value": world * work.units / (tot / n_e2e), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": 1e3 * tot / n_e2e}
 
     if rank != 0:
@@ -291,27 +489,49 @@ def main():
 
     clk_mhz = clk["sm_mhz"] if clk else pk["sm_max"]
     per_step = {k: {"launches": v[0] / args.steps, "ms_per_step": v[1] / args.steps} for k, v in prof.items()}
+    wl = args.config + (f"_k{work.K}" if args.k else "")
     dominant = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
-    roof = roofline_for(dominant, prof[dominant][1], prof[dominant][0], prob, pk, clk_mhz) if dominant else None
+    KN = work.units * args.steps
+    roof = roofline_for(dominant, prof[dominant][1], prof[dominant][0], KN, pk, clk_mhz, wl) if dominant else None
     if roof:
         roof["kernel"] = dominant
-    kern_roof = {k: roofline_for(k, v[1], v[0], prob, pk, clk_mhz)
-                 for k, v in prof.items() if k.startswith(("moments_bf16", "moments_fp32", "hist_seg"))}
+    kern_roof = {k: roofline_for(k, v[1], v[0], KN, pk, clk_mhz, wl)
+                 for k, v in prof.items()
+                 if k.startswith(("moments_bf16", "moments_fp32", "ipsa_bf16", "ipsa_fp32", "hist_seg", "weights"))}
+    stage = {"model_eval_bins_sort_tables": 0.0, "moments": 0.0, "histogram": 0.0, "ipsa": 0.0, "other": 0.0}
+    for k, v in per_step.items():
+        if k.startswith(("model_eval", "range_bins", "power_table")):
+            stage["model_eval_bins_sort_tables"] += v["ms_per_step"]
+        elif k.startswith(("moments", "density_prep")):
+            stage["moments"] += v["ms_per_step"]
+        elif k.startswith("hist"):
+            stage["histogram"] += v["ms_per_step"]
+        elif k.startswith("ipsa"):
+            stage["ipsa"] += v["ms_per_step"]
+        else:
+            stage["other"] += v["ms_per_step"]
+    cfg = {"workload": WORKLOADS[args.config], "dist_points_per_step": work.units, "K": work.K,
+           "precision": args.precision, "parallelism": f"replicas x{world} (no collective)",
+           "l2": "flushed before every timed step (256 MB write, outside the step events)"}
+    if args.k:
+        cfg["k_subset"] = work.K
+    if hasattr(work, "prob"):
+        cfg.update({"N": work.prob.N, "bins": work.prob.n_bins, "moments": work.prob.n_moments})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16x3" else "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "K": K, "N": prob.N, "bins": Bn, "moments": J,
-                   "precision": args.precision, "parallelism": f"replicas x{world} (K-sharded, no collective)",
-                   "l2": "flushed before every timed step (256 MB write, outside the step events)"},
+        "config": cfg,
         "roofline": roof,
-        "kernels": {"per_step": per_step, "roofline": kern_roof},
+        "kernels": {"per_step": per_step, "stage_ms_per_step": stage, "roofline": kern_roof,
+                    "timing": "CUDA events per kernel group inside the timed region" if profile_live
+                    else "per-stage CUDA events from a second pass of the same steps (stage by stage)"},
         "gpu_launches": int(sum(v[0] for v in prof.values())),
         "clocks": clk,
         "e2e": e2e,
     }
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(prob)
+    if world == 1 and not args.no_cpu_baseline and hasattr(work, "prob") and args.config != "weights":
+        line["cpu_baseline"] = cpu_baseline(work.prob)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

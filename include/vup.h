@@ -253,6 +253,16 @@ vup_status vup_batched_report(int *bn_cap, int *source, double *tune_ms);
  */
 vup_status vup_sync(vup_grid g, vup_stream_t stream);
 
+/*
+ * Self-test of the bounded device-side waits: launches one CTA that waits on
+ * an mbarrier nothing arrives at, polling `polls` times about 1 us apart
+ * (1 <= polls <= 2^20, else VUP_ERR_INVALID_ARG), then records the expiry in
+ * the grid's device status word and exits.  The next vup_sync(g) returns
+ * VUP_ERR_TIMEOUT; the context stays usable.  This is the path every wait of
+ * the contraction and histogram kernels takes on expiry.
+ */
+vup_status vup_selftest_wait(vup_grid g, uint32_t polls, vup_stream_t stream);
+
 /* Grid facts after vup_eval_model / vup_set_outputs (host copies). */
 typedef struct {
     int32_t ndim;

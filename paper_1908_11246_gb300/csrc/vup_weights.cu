@@ -23,6 +23,11 @@ __global__ void __launch_bounds__(kThreads) k_weights(const float *__restrict__ 
     const int64_t k0 = (int64_t)blockIdx.y * RB;
     for (int e = threadIdx.x; e < RB * B; e += blockDim.x) sh[e] = 0.f;
     __syncthreads();
+    // rows past K re-read row K-1 and are never stored, so that every row's
+    // load is unconditional and all RB loads of a column are in flight at once
+    const float *wrow[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) wrow[r] = W + min(k0 + r, K - 1) * N;
     // column range of this split, in float4 units (rows of W are 16-byte
     // aligned only when N is a multiple of 4; otherwise every column goes
     // through the scalar loop below)
@@ -34,19 +39,21 @@ __global__ void __launch_bounds__(kThreads) k_weights(const float *__restrict__ 
     for (int r = 0; r < RB; ++r)
 #pragma unroll
         for (int j = 0; j < 4; ++j) m[r][j] = 0.f;
+#pragma unroll 2
     for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        float4 w[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) w[r] = __ldcs(reinterpret_cast<const float4 *>(wrow[r]) + c);
         const float4 z = *reinterpret_cast<const float4 *>(z32 + c * 4);
         const int4 b = *reinterpret_cast<const int4 *>(bins + c * 4);
         const float zz[4] = {z.x, z.y, z.z, z.w};
         const int bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
-            if (k0 + r >= K) break;
-            const float4 w = __ldcs(reinterpret_cast<const float4 *>(W + (k0 + r) * N) + c);
-            const float ww[4] = {w.x, w.y, w.z, w.w};
+            const float ww[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                float p = zz[q];
+                const float p = zz[q];
                 float t = ww[q] * p;
                 m[r][0] += t;
                 t *= p; m[r][1] += t;
@@ -65,8 +72,7 @@ __global__ void __launch_bounds__(kThreads) k_weights(const float *__restrict__ 
             const float p = z32[i];
             const int bq = bins[i];
             for (int r = 0; r < RB; ++r) {
-                if (k0 + r >= K) break;
-                const float w = W[(k0 + r) * N + i];
+                const float w = wrow[r][i];
                 float t = w * p;
                 m[r][0] += t;
                 t *= p; m[r][1] += t;

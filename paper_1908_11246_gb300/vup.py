@@ -25,7 +25,7 @@ PRECISIONS = {"fp64": VUP_FP64, "fp32": VUP_FP32, "bf16x3": VUP_BF16X3}
 # exported symbols declared in include/vup.h
 ABI_SYMBOLS = [
     "vup_grid_create", "vup_grid_destroy", "vup_eval_model", "vup_set_outputs", "vup_propagate",
-    "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_batched_report", "vup_sync",
+    "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_batched_report", "vup_sync", "vup_selftest_wait",
     "vup_grid_info", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
     "vup_profile_read",
 ]
@@ -71,6 +71,7 @@ def lib():
                                             C.POINTER(vp), C.POINTER(vp), vp]
         l.vup_batched_report.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
         l.vup_sync.argtypes = [vp, vp]
+        l.vup_selftest_wait.argtypes = [vp, C.c_uint32, vp]
         l.vup_grid_info.argtypes = [vp, C.POINTER(vup_grid_info_t)]
         l.vup_grid_copy.argtypes = [vp, C.c_int, vp, C.c_size_t, vp]
         l.vup_profile.argtypes = [C.c_int]
@@ -168,14 +169,23 @@ def vup_ipsa_sensitivity(h, dens, precision, dmu, dsigma, grad_moments=None, str
                                       _ptr(dsigma), _stream(stream)), "vup_ipsa_sensitivity")
 
 
+class BatchedArgs:
+    """The host arrays of one vup_propagate_batched call, marshalled once."""
+
+    def __init__(self, handles, dens_list, raws, hists):
+        n = self.n = len(handles)
+        self.hs = (C.c_void_p * n)(*[h.value for h in handles])
+        self.ds = (vup_densities * n)(*dens_list)
+        self.rs = (C.c_void_p * n)(*[None if r is None else r.data_ptr() for r in raws])
+        self.hh = (C.c_void_p * n)(*[None if x is None else x.data_ptr() for x in hists])
+
+    def __call__(self, precision, stream=None):
+        _check(lib().vup_propagate_batched(self.n, self.hs, self.ds, int(precision), self.rs, self.hh,
+                                           _stream(stream)), "vup_propagate_batched")
+
+
 def vup_propagate_batched(handles, dens_list, precision, raws, hists, stream=None):
-    n = len(handles)
-    hs = (C.c_void_p * n)(*[h.value for h in handles])
-    ds = (vup_densities * n)(*dens_list)
-    rs = (C.c_void_p * n)(*[None if r is None else r.data_ptr() for r in raws])
-    hh = (C.c_void_p * n)(*[None if x is None else x.data_ptr() for x in hists])
-    _check(lib().vup_propagate_batched(n, hs, ds, int(precision), rs, hh, _stream(stream)),
-           "vup_propagate_batched")
+    BatchedArgs(handles, dens_list, raws, hists)(precision, stream)
 
 
 def vup_batched_report():
@@ -206,6 +216,10 @@ def propagate_batched(grids, dev_dens_list, precision="bf16x3", moments=True, hi
     ds = [make_densities(dd) for dd in dev_dens_list]
     vup_propagate_batched([g.h for g in grids], ds, PRECISIONS[precision], raws, hists, stream)
     return raws, hists
+
+
+def vup_selftest_wait(h, polls, stream=None):
+    _check(lib().vup_selftest_wait(h, int(polls), _stream(stream)), "vup_selftest_wait")
 
 
 def vup_sync(h, stream=None):

@@ -281,6 +281,29 @@ def test_empty_support_reported_by_sync():
     g.sync()  # the condition is cleared once reported
 
 
+def test_expired_device_wait_reported_by_sync_and_context_survives():
+    """A bounded wait that runs out (an mbarrier nothing arrives at) is
+    reported as VUP_ERR_TIMEOUT by vup_sync; the next propagation is exact."""
+    vup = vupmod()
+    prob = I.config("c2", "small")
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.eval_model(prob.model_id, prob.theta, prob.n_bins, prob.n_moments)
+    g.sync()
+    vup.vup_selftest_wait(g.h, 2000)
+    with pytest.raises(vup.VUPError) as e:
+        g.sync()
+    assert e.value.status == vup.VUP_ERR_TIMEOUT
+    g.sync()  # cleared once reported
+    with pytest.raises(vup.VUPError) as e:
+        vup.vup_selftest_wait(g.h, 0)
+    assert e.value.status == vup.VUP_ERR_INVALID_ARG
+    dd = vup.densities_to_device(prob.dens.take(range(64)))
+    raw, _, hs = g.propagate(dd, "fp32", central=False)
+    g.sync()
+    np.testing.assert_allclose(hs.sum(dim=1).cpu().numpy(), 1.0, atol=1e-6)
+    assert np.isfinite(raw.cpu().numpy()).all()
+
+
 def test_state_and_argument_errors():
     vup = vupmod()
     import torch
