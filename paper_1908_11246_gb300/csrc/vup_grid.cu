@@ -17,7 +17,8 @@ constexpr int kSortWarps = 4;        // warps per CTA in the counting sort
 // Packed sorted-point word: the gathered-axis row inside its part << 8 (the
 // byte offset of its row in a 64-float shared-memory tile), run-end flag
 // (bit 30), key-end flag (bit 31).
-constexpr int kRowShift = 8;
+constexpr int kRowShift = 9;   // shared-memory tile rows of 512 bytes (128 floats)
+constexpr int kRowBits = 9;    // row field width (tile rows < 512)
 constexpr uint32_t kRunEnd = 1u << 30;
 constexpr uint32_t kBinEnd = 1u << 31;
 
@@ -341,8 +342,10 @@ __global__ void k_scan_add(int32_t *__restrict__ out, int64_t L, const int32_t *
 // A run is a maximal stretch of sorted points sharing the sort key (part and
 // bin) and every axis index but the gathered one.  hpt[t] packs the t-th
 // sorted point's row inside its part of the gathered axis (<< shift; the
-// row's byte offset in a shared-memory tile of 2^shift-byte rows) and the
-// run-end / key-end flags (bits 30, 31).
+// row's byte offset in a shared-memory tile of 2^shift-byte rows, kRowBits
+// wide -- rows past that field only occur with parts too large for a tile,
+// whose kernel reads the row from the sorted order instead) and the run-end /
+// key-end flags (bits 30, 31).
 __global__ void k_run_flags(const int32_t *__restrict__ perm, const int32_t *__restrict__ keys,
                             int64_t N, int64_t n_last, int32_t *__restrict__ flags) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
@@ -375,7 +378,7 @@ __global__ void k_run_build(const int32_t *__restrict__ perm, const int32_t *__r
         const bool key_last = (t == N - 1) || keys[perm[t + 1]] != keys[i];
         const int64_t a = i % n_last;
         const uint32_t row = (uint32_t)(a - (a / part_rows) * part_rows);
-        hpt[t] = (row << shift) | (last ? kRunEnd : 0u) | (key_last ? kBinEnd : 0u);
+        hpt[t] = ((row & ((1u << kRowBits) - 1u)) << shift) | (last ? kRunEnd : 0u) | (key_last ? kBinEnd : 0u);
         if (t == N - 1) {
             n_runs[0] = rid + 1;
             run_start[rid + 1] = (int32_t)N;
@@ -384,17 +387,18 @@ __global__ void k_run_build(const int32_t *__restrict__ perm, const int32_t *__r
 }
 
 // The run-end word of run r also carries the rest-axis index of run r + 4
-// (the histogram kernel loads that run's factor four runs ahead) in the 15
-// bits beside the row field: `shift` low bits (0 .. shift-1) and 15 - shift
-// high bits (shift + 15 .. 29).  2-D grids split the rest index itself; 3-D
-// grids put a0 in the low field and a1 in the high field.  Zero past the end.
+// (the histogram kernel loads that run's factor four runs ahead) in the 21
+// bits beside the row field: `shift` low bits (0 .. shift-1) and
+// 30 - shift - kRowBits high bits (shift + kRowBits .. 29).  2-D grids split
+// the rest index itself; 3-D grids put a0 in the low field and a1 in the high
+// field.  Zero past the end.
 constexpr int kRunAhead = 4;
 __global__ void k_run_encode(const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_rest,
                              const int32_t *__restrict__ n_runs_p, int ndim, int64_t n1, int shift,
                              uint32_t *__restrict__ hpt) {
     const int32_t n_runs = n_runs_p[0];
     const uint32_t lo_mask = (1u << shift) - 1u;
-    const uint32_t hi_mask = (1u << (15 - shift)) - 1u;
+    const uint32_t hi_mask = (1u << (30 - shift - kRowBits)) - 1u;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_runs;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ra = r + kRunAhead;
@@ -409,7 +413,7 @@ __global__ void k_run_encode(const int32_t *__restrict__ run_start, const int32_
                 lo = (uint32_t)rest & lo_mask;
                 hi = (uint32_t)rest >> shift;
             }
-            code = (lo & lo_mask) | ((hi & hi_mask) << (shift + 15));
+            code = (lo & lo_mask) | ((hi & hi_mask) << (shift + kRowBits));
         }
         hpt[run_start[r + 1] - 1] |= code;
     }

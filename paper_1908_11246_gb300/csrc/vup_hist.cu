@@ -3,10 +3,10 @@
 // bin b.  The one-hot model matrix of Eq. MUP is applied as a segmented
 // reduction over the grid points pre-sorted by bin ("sort and sum").
 //
-// Layout: a warp serves 64 densities, two per lane; every lane walks the same
-// sorted point stream, so control flow is uniform and one 8-byte gather per
-// lane (64 consecutive shared-memory words per warp, conflict-free) yields two
-// distribution-points.  Points are grouped in runs that share the sort key
+// Layout: a warp serves 128 densities, four per lane; every lane walks the
+// same sorted point stream, so control flow is uniform and one 16-byte gather
+// per lane (128 consecutive shared-memory words per warp, conflict-free)
+// yields four distribution-points.  Points are grouped in runs that share the sort key
 // and every axis index but the gathered one: inside a run only the gathered
 // axis' factor is read, from a shared-memory tile; the product with the other
 // axes' factors is applied once per run.  Those factors are loaded four runs
@@ -27,11 +27,12 @@
 
 namespace {
 
-constexpr int kHistWarps = 32;
-constexpr int kKT = 64;                      // densities per k-tile (two per lane)
+constexpr int kHistWarps = 20;
+constexpr int kKT = 128;                     // densities per k-tile (four per lane)
 constexpr int kWin = 128;                    // sorted-point words per staging buffer
-constexpr int kMaxPartRows = 704;            // gathered-axis rows per shared-memory tile
-constexpr uint32_t kOffMask = 0x7fffu << 8;  // row byte offset in a 256-byte-row tile
+constexpr int kMaxPartRows = 392;            // gathered-axis rows per shared-memory tile
+constexpr int kRowShift = 9;                 // log2 of a tile row's bytes (kKT floats)
+constexpr uint32_t kOffMask = 0x1ffu << kRowShift;  // row byte offset (rows < 512)
 constexpr uint32_t kRunEnd = 1u << 30, kBinEnd = 1u << 31;
 constexpr uint32_t kFlags = kRunEnd | kBinEnd;
 constexpr uint32_t kSpin = 1u << 26;
@@ -39,6 +40,7 @@ constexpr int kPF = 16;                      // runs prefetched per block (globa
 
 struct LayoutArgs {
     const uint32_t *hpt;
+    const int32_t *perm;   // sorted position -> flat index of the layout (global fallback)
     const int32_t *run_start, *run_rest, *run_bin;
     const int32_t *chunk_pt, *chunk_run, *chunk_bin;
     const int32_t *koff;   // key offsets [P * B + 1]
@@ -109,127 +111,201 @@ __host__ __device__ inline size_t hist_smem_bytes(int64_t rows) {
     return hist_tile_bytes(rows) + kHistWarps * hist_warp_bytes() + kHistWarps * 2 * sizeof(uint64_t);
 }
 
-// Store the finished sums of key `key` for this lane's two densities.
+// Store the finished sums of key `key` for this lane's four densities (global
+// fallback kernel: the normalisers are applied here).
 struct Flusher {
     const HistArgs &A;
     const LayoutArgs &H;
     int c, p;
     int32_t p0, p1, first_key;
     int64_t k;
-    float2 invZ;
-    __device__ __forceinline__ void operator()(int32_t key, float2 v) const {
-        const float2 val = make_float2(v.x * invZ.x, v.y * invZ.y);
+    float4 invZ;
+    __device__ __forceinline__ void operator()(int32_t key, float4 v) const {
+        const float4 val = make_float4(v.x * invZ.x, v.y * invZ.y, v.z * invZ.z, v.w * invZ.w);
         const bool shared = H.koff[key] < p0 || H.koff[key + 1] > p1;
         if (shared) {
             const int side = (key == first_key) ? 0 : 1;
-            *reinterpret_cast<float2 *>(A.part + ((int64_t)c * 2 + side) * A.K_pad + k) = val;
+            *reinterpret_cast<float4 *>(A.part + ((int64_t)c * 2 + side) * A.K_pad + k) = val;
         } else {
             const int b = key - p * A.B;
             float *out = H.P > 1 ? A.direct + (int64_t)p * A.K * A.B : A.hist;
             if (k < A.K) out[k * A.B + b] = val.x;
             if (k + 1 < A.K) out[(k + 1) * A.B + b] = val.y;
+            if (k + 2 < A.K) out[(k + 2) * A.B + b] = val.z;
+            if (k + 3 < A.K) out[(k + 3) * A.B + b] = val.w;
         }
     }
 };
 
-__device__ __forceinline__ float2 load_inv_z(const HistArgs &A, int64_t k) {
-    float2 r = make_float2(0.f, 0.f);
-    for (int q = 0; q < 2; ++q) {
-        if (k + q < A.K) {
-            double z = 1.0;
-            for (int d = 0; d < A.ndim; ++d) z *= A.ds[(k + q) * A.ndim + d].invZ;
-            if (q == 0) r.x = (float)z; else r.y = (float)z;
-        }
-    }
-    return r;
+__device__ __forceinline__ float inv_z(const HistArgs &A, int64_t k) {
+    if (k >= A.K) return 0.f;
+    double z = 1.0;
+    for (int d = 0; d < A.ndim; ++d) z *= A.ds[k * A.ndim + d].invZ;
+    return (float)z;
 }
 
+__device__ __forceinline__ float4 load_inv_z(const HistArgs &A, int64_t k) {
+    return make_float4(inv_z(A, k), inv_z(A, k + 1), inv_z(A, k + 2), inv_z(A, k + 3));
+}
+
+__device__ __forceinline__ float4 ld4(const float *q) { return *reinterpret_cast<const float4 *>(q); }
+__device__ __forceinline__ float4 mul4(float4 a, float4 b) {
+    return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+__device__ __forceinline__ void add4(float4 &a, float4 b) {
+    a.x += b.x;
+    a.y += b.y;
+    a.z += b.z;
+    a.w += b.w;
+}
+__device__ __forceinline__ void fma4(float4 &a, float4 w, float4 b) {
+    a.x = fmaf(w.x, b.x, a.x);
+    a.y = fmaf(w.y, b.y, a.y);
+    a.z = fmaf(w.z, b.z, a.z);
+    a.w = fmaf(w.w, b.w, a.w);
+}
+
+// Per-item context, kept in shared memory: the chosen layout, the output
+// pointers and sizes.  Warps read it on demand, so none of it occupies
+// registers across the point loop.
+struct ItemCtx {
+    LayoutArgs H;
+    float *part;   // [P * C][2][K_pad] partial sums of keys cut by chunk bounds
+    float *out;    // [K][B] whole-key sums of this part (hist, or direct + p K B)
+    int64_t K, K_pad;
+    int B, C;
+    int *dstatus;
+};
+
 // One work item: part p, chunk group cg (kHistWarps chunks, one per warp) and
-// the 64 densities from k0 of layout H.  Called by every thread of the CTA;
-// `wseq` counts the staging windows this warp has consumed so far (it keeps
-// the per-warp mbarrier phases consistent across items).
+// the 128 densities from k0 of the instance *Ap (kernel parameter or global
+// memory).  Called by every thread of the CTA; `wseq` counts the staging
+// windows this warp has consumed so far (it keeps the per-warp mbarrier
+// phases consistent across items).
 template <int NF>
-__device__ __forceinline__ void hist_item(const HistArgs &A, const LayoutArgs &H, int p, int cg, int64_t k0,
-                                          uint8_t *sm, int64_t tile_rows, uint32_t &wseq, volatile int *abort) {
+__device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int64_t k0, uint8_t *sm,
+                                          int64_t tile_rows, uint32_t &wseq, volatile int *abort, ItemCtx &X,
+                                          float *s_invz) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t k = k0 + 2 * lane;
+    const int64_t k = k0 + 4 * lane;
     float *ws = reinterpret_cast<float *>(sm);
     const size_t tb = hist_tile_bytes(tile_rows);
     uint32_t *win = reinterpret_cast<uint32_t *>(sm + tb + (size_t)warp * hist_warp_bytes());
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + tb + kHistWarps * hist_warp_bytes()) + 2 * warp;
 
-    // this part's rows of the gathered-axis factor table (16-byte asynchronous
-    // copies) + a zero row; the previous item's readers are done first
+    // the previous item's readers of the tile and the context are done first
     __syncthreads();
     if (*abort) return;  // a wait of an earlier item expired (uniform: read after the barrier)
+    if (threadIdx.x == 0) {
+        const HistArgs &A = *Ap;
+        X.H = A.sel[0] ? A.L1 : A.L0;
+        X.part = A.part;
+        X.out = X.H.P > 1 ? A.direct + (int64_t)p * A.K * A.B : A.hist;
+        X.K = A.K;
+        X.K_pad = A.K_pad;
+        X.B = A.B;
+        X.C = A.C;
+        X.dstatus = A.dstatus;
+    }
+    if (threadIdx.x < kKT) s_invz[threadIdx.x] = inv_z(*Ap, k0 + threadIdx.x);
+    __syncthreads();
+    const LayoutArgs &H = X.H;
+    if (p >= H.P) return;  // uniform
+    // this part's rows of the gathered-axis factor table (16-byte asynchronous
+    // copies) + a zero row, then every column scaled by its density's
+    // normaliser 1 / prod_d Z_d
     const int64_t row0 = (int64_t)p * H.part_rows;
     const int64_t nrows = min(H.part_rows, H.n_last - row0);
-    for (int64_t e = threadIdx.x; e < nrows * 16; e += blockDim.x) {
-        const int64_t a = e >> 4, cc = e & 15;
-        cp_async16(ws + a * kKT + cc * 4, H.g_last + (row0 + a) * A.K_pad + k0 + cc * 4);
+    {
+        const float *src = H.g_last + row0 * X.K_pad + k0;
+        const int64_t K_pad = X.K_pad;
+        for (int64_t e = threadIdx.x; e < nrows * (kKT / 4); e += blockDim.x) {
+            const int64_t a = e / (kKT / 4), cc = e % (kKT / 4);
+            cp_async16(ws + a * kKT + cc * 4, src + a * K_pad + cc * 4);
+        }
     }
     cp_async_commit();
     if (threadIdx.x < kKT) ws[nrows * kKT + threadIdx.x] = 0.f;
     cp_async_wait_all();
     __syncthreads();
+    for (int64_t e = threadIdx.x; e < nrows * kKT; e += blockDim.x) ws[e] *= s_invz[e % kKT];
+    __syncthreads();
 
-    const int c = p * A.C + cg * kHistWarps + warp;
-    if (cg * kHistWarps + warp >= A.C) return;
+    const int wc = cg * kHistWarps + warp;
+    if (wc >= X.C) return;
+    const int c = p * X.C + wc;
     const int32_t p0 = H.chunk_pt[c], p1 = H.chunk_pt[c + 1];
     if (p0 >= p1) return;
     const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
-    const Flusher flush{A, H, c, p, p0, p1, H.chunk_bin[2 * c], k, load_inv_z(A, k)};
+    // keys cut by the chunk bounds can only be its first and last key
+    const int32_t first_key = H.chunk_bin[2 * c], last_key = H.chunk_bin[2 * c + 1];
+    const bool sh_first = H.koff[first_key] < p0 || H.koff[first_key + 1] > p1;
+    const bool sh_last = H.koff[last_key] < p0 || H.koff[last_key + 1] > p1;
+    auto flush = [&](int32_t key, float4 v) {
+        const bool shared = key == first_key ? sh_first : (key == last_key && sh_last);
+        if (shared) {
+            const int side = key == first_key ? 0 : 1;
+            *reinterpret_cast<float4 *>(X.part + ((int64_t)c * 2 + side) * X.K_pad + k) = v;
+        } else {
+            const int B = X.B;
+            const int64_t K = X.K;
+            float *o = X.out + k * B + (key - p * B);
+            if (k < K) o[0] = v.x;
+            if (k + 1 < K) o[B] = v.y;
+            if (k + 2 < K) o[2 * B] = v.z;
+            if (k + 3 < K) o[3 * B] = v.w;
+        }
+    };
 
     // staging of the sorted point stream: window i of this item lands in
     // buffer (wseq + i) & 1
+    const uint32_t *hpt = H.hpt;
     const int32_t wb0 = p0 & ~(kWin - 1);
     if (lane == 0) {
         const int b0 = wseq & 1;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier items' reads of both buffers
-        bulk_copy(win + b0 * kWin, H.hpt + wb0, kWin * 4, &mbar[b0]);
-        if (wb0 + kWin < p1) bulk_copy(win + (b0 ^ 1) * kWin, H.hpt + wb0 + kWin, kWin * 4, &mbar[b0 ^ 1]);
+        bulk_copy(win + b0 * kWin, hpt + wb0, kWin * 4, &mbar[b0]);
+        if (wb0 + kWin < p1) bulk_copy(win + (b0 ^ 1) * kWin, hpt + wb0 + kWin, kWin * 4, &mbar[b0 ^ 1]);
     }
     __syncwarp();
 
-    // rest-axis factors (two densities) of runs r .. r + 3, rotated through registers
+    // rest-axis factors (four densities) of runs r .. r + 3, rotated through registers
+    const int64_t K_pad = X.K_pad;
     const float *g0k = H.g0 + k;
     const float *g1k = NF == 2 ? H.g1 + k : nullptr;
-    const int64_t K_pad = A.K_pad;
-    auto ld2 = [](const float *q) { return *reinterpret_cast<const float2 *>(q); };
-    auto rest_factor = [&](int32_t r) -> float2 {
-        if (r >= r1) return make_float2(0.f, 0.f);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto rest_factor = [&](int32_t r) -> float4 {
+        if (r >= r1) return zero4;
         const int32_t rest = H.run_rest[r];
         if (NF == 2) {
             const int32_t a0 = rest / (int32_t)H.n1, a1 = rest - a0 * (int32_t)H.n1;
-            const float2 u = ld2(g0k + a0 * K_pad), w = ld2(g1k + a1 * K_pad);
-            return make_float2(u.x * w.x, u.y * w.y);
+            return mul4(ld4(g0k + a0 * K_pad), ld4(g1k + a1 * K_pad));
         }
-        return ld2(g0k + rest * K_pad);
+        return ld4(g0k + rest * K_pad);
     };
-    float2 f0 = rest_factor(r0), f1 = rest_factor(r0 + 1), f2 = rest_factor(r0 + 2), f3 = rest_factor(r0 + 3);
-    // factor of run r + 4, decoded from run r's end word (the load stays in flight)
-    auto coded_factor = [&](uint32_t u) -> float2 {
+    float4 f0 = rest_factor(r0), f1 = rest_factor(r0 + 1), f2 = rest_factor(r0 + 2), f3 = rest_factor(r0 + 3);
+    // factor of run r + 4, decoded from run r's end word (the load stays in
+    // flight): 9 low bits below the row field and 12 bits above it
+    auto coded_factor = [&](uint32_t u) -> float4 {
         if (NF == 2) {
-            const uint32_t a0 = u & 0xffu, a1 = (u >> 23) & 0x7fu;
-            const float2 x = ld2(g0k + (int64_t)a0 * K_pad), w = ld2(g1k + (int64_t)a1 * K_pad);
-            return make_float2(x.x * w.x, x.y * w.y);
+            const uint32_t a0 = u & 0x1ffu, a1 = (u >> 18) & 0xfffu;
+            return mul4(ld4(g0k + (int64_t)a0 * K_pad), ld4(g1k + (int64_t)a1 * K_pad));
         }
-        const uint32_t idx = (u & 0xffu) | ((u >> 15) & 0x7f00u);
-        return ld2(g0k + (int64_t)idx * K_pad);
+        const uint32_t idx = (u & 0x1ffu) | (((u >> 18) & 0xfffu) << 9);
+        return ld4(g0k + (int64_t)idx * K_pad);
     };
 
-    int32_t r = r0, cur_key = H.run_bin[r0];
-    float2 acc = make_float2(0.f, 0.f), bacc = make_float2(0.f, 0.f);
-    const uint32_t wsl = smem_u32(ws) + lane * 8;
-    const uint32_t null_word = (uint32_t)nrows << 8;  // zero row, no flags
+    int32_t r = r0, cur_key = first_key;
+    float4 acc = zero4, bacc = zero4;
+    const uint32_t wsl = smem_u32(ws) + lane * 16;
+    const uint32_t null_word = (uint32_t)nrows << kRowShift;  // zero row, no flags
 
     auto run_end = [&](uint32_t u) {
-        bacc.x = fmaf(f0.x, acc.x, bacc.x);
-        bacc.y = fmaf(f0.y, acc.y, bacc.y);
-        acc = make_float2(0.f, 0.f);
+        fma4(bacc, f0, acc);
+        acc = zero4;
         if (u & kBinEnd) {
             flush(cur_key, bacc);
-            bacc = make_float2(0.f, 0.f);
+            bacc = zero4;
             cur_key = r + 1 < r1 ? H.run_bin[r + 1] : -1;
         }
         ++r;
@@ -238,39 +314,32 @@ __device__ __forceinline__ void hist_item(const HistArgs &A, const LayoutArgs &H
         f2 = f3;
         f3 = coded_factor(u);
     };
-    auto gather = [&](uint32_t addr) -> float2 {
-        float2 v;
-        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    auto gather = [&](uint32_t addr) -> float4 {
+        float4 v;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "r"(addr));
         return v;
     };
     // words without flags carry nothing but the row byte offset (run codes sit
     // on run-end words only), so the common path needs no masking
     auto group = [&](const uint4 v) {
         if (((v.x | v.y | v.z | v.w) & kFlags) == 0) {
-            const float2 a0 = gather(wsl + v.x), a1 = gather(wsl + v.y), a2 = gather(wsl + v.z),
+            const float4 a0 = gather(wsl + v.x), a1 = gather(wsl + v.y), a2 = gather(wsl + v.z),
                          a3 = gather(wsl + v.w);
-            acc.x += a0.x;
-            acc.y += a0.y;
-            acc.x += a1.x;
-            acc.y += a1.y;
-            acc.x += a2.x;
-            acc.y += a2.y;
-            acc.x += a3.x;
-            acc.y += a3.y;
+            add4(acc, a0);
+            add4(acc, a1);
+            add4(acc, a2);
+            add4(acc, a3);
         } else {
-            const float2 a0 = gather(wsl + (v.x & kOffMask)), a1 = gather(wsl + (v.y & kOffMask)),
+            const float4 a0 = gather(wsl + (v.x & kOffMask)), a1 = gather(wsl + (v.y & kOffMask)),
                          a2 = gather(wsl + (v.z & kOffMask)), a3 = gather(wsl + (v.w & kOffMask));
-            acc.x += a0.x;
-            acc.y += a0.y;
+            add4(acc, a0);
             if (v.x & kFlags) run_end(v.x);
-            acc.x += a1.x;
-            acc.y += a1.y;
+            add4(acc, a1);
             if (v.y & kFlags) run_end(v.y);
-            acc.x += a2.x;
-            acc.y += a2.y;
+            add4(acc, a2);
             if (v.z & kFlags) run_end(v.z);
-            acc.x += a3.x;
-            acc.y += a3.y;
+            add4(acc, a3);
             if (v.w & kFlags) run_end(v.w);
         }
     };
@@ -288,7 +357,7 @@ __device__ __forceinline__ void hist_item(const HistArgs &A, const LayoutArgs &H
         for (uint32_t i = 0; !mbar_try_wait(&mbar[b], (wseq >> 1) & 1); ++i) {
             if (i > kSpin || *abort) {  // a staged copy never landed: record and stop
                 *abort = 1;
-                atomicCAS(A.dstatus, 0, VUP_DSTAT_TIMEOUT);
+                atomicCAS(X.dstatus, 0, VUP_DSTAT_TIMEOUT);
                 return;
             }
         }
@@ -306,7 +375,7 @@ __device__ __forceinline__ void hist_item(const HistArgs &A, const LayoutArgs &H
         __syncwarp();
         if (lane == 0 && wbase + 2 * kWin < p1) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            bulk_copy(win + b * kWin, H.hpt + wbase + 2 * kWin, kWin * 4, &mbar[b]);
+            bulk_copy(win + b * kWin, hpt + wbase + 2 * kWin, kWin * 4, &mbar[b]);
         }
     }
     if (cur_key >= 0) flush(cur_key, bacc);
@@ -327,16 +396,17 @@ __device__ __forceinline__ void hist_init_mbar(uint8_t *sm, int64_t tile_rows) {
 }
 
 template <int NF>
-__global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_smem(HistArgs A, int64_t tile_rows, int G) {
+__global__ void __launch_bounds__(kHistWarps * 32, 1)
+    k_hist_smem(const __grid_constant__ HistArgs A, int64_t tile_rows, int G) {
     extern __shared__ __align__(128) uint8_t sm[];
-    const LayoutArgs H = pick(A);
-    const int p = blockIdx.x / G, cg = blockIdx.x - p * G;
-    if (p >= H.P) return;
+    __shared__ ItemCtx X;
+    __shared__ float s_invz[kKT];
     __shared__ int abort;
+    const int p = blockIdx.x / G, cg = blockIdx.x - p * G;
     if (threadIdx.x == 0) abort = 0;
     hist_init_mbar(sm, tile_rows);
     uint32_t wseq = 0;
-    hist_item<NF>(A, H, p, cg, (int64_t)blockIdx.y * kKT, sm, tile_rows, wseq, &abort);
+    hist_item<NF>(&A, p, cg, (int64_t)blockIdx.y * kKT, sm, tile_rows, wseq, &abort, X, s_invz);
 }
 
 // Batched form: one persistent launch over the work items of many instances
@@ -350,16 +420,15 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_batched(const HistA
                                                                      const HistItem *__restrict__ items,
                                                                      int n_items, int64_t tile_rows) {
     extern __shared__ __align__(128) uint8_t sm[];
+    __shared__ ItemCtx X;
+    __shared__ float s_invz[kKT];
     __shared__ int abort;
     if (threadIdx.x == 0) abort = 0;
     hist_init_mbar(sm, tile_rows);
     uint32_t wseq = 0;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const HistItem w = items[it];
-        const HistArgs A = insts[w.inst];
-        const LayoutArgs H = pick(A);
-        if (w.p >= H.P) continue;  // uniform: every thread reads the same item
-        hist_item<NF>(A, H, w.p, w.cg, (int64_t)w.kt * kKT, sm, tile_rows, wseq, &abort);
+        hist_item<NF>(insts + w.inst, w.p, w.cg, (int64_t)w.kt * kKT, sm, tile_rows, wseq, &abort, X, s_invz);
     }
 }
 
@@ -371,46 +440,43 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_global(HistArgs A, 
     const int p = blockIdx.x / G, cg = blockIdx.x - p * G;
     if (p >= H.P) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t k = (int64_t)blockIdx.y * kKT + 2 * lane;
+    const int64_t k = (int64_t)blockIdx.y * kKT + 4 * lane;
     const int c = p * A.C + cg * kHistWarps + warp;
     if (cg * kHistWarps + warp >= A.C) return;
     const int32_t p0 = H.chunk_pt[c], p1 = H.chunk_pt[c + 1];
     if (p0 >= p1) return;
     const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
     const Flusher flush{A, H, c, p, p0, p1, H.chunk_bin[2 * c], k, load_inv_z(A, k)};
-    const float *wl = H.g_last + (int64_t)p * H.part_rows * A.K_pad + k;
-    auto ld2 = [](const float *q) { return *reinterpret_cast<const float2 *>(q); };
-    auto wrest = [&](int32_t r) -> float2 {
-        if (r >= r1) return make_float2(0.f, 0.f);
+    // the gathered-axis index comes from the sorted order itself (the point
+    // words' row field only covers shared-memory tiles)
+    const float *wl = H.g_last + k;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto wrest = [&](int32_t r) -> float4 {
+        if (r >= r1) return zero4;
         const int32_t rest = H.run_rest[r];
         if (A.ndim == 3) {
             const int64_t a0 = rest / H.n1, a1 = rest - a0 * H.n1;
-            const float2 u = ld2(H.g0 + a0 * A.K_pad + k), w = ld2(H.g1 + a1 * A.K_pad + k);
-            return make_float2(u.x * w.x, u.y * w.y);
+            return mul4(ld4(H.g0 + a0 * A.K_pad + k), ld4(H.g1 + a1 * A.K_pad + k));
         }
-        return ld2(H.g0 + (int64_t)rest * A.K_pad + k);
+        return ld4(H.g0 + (int64_t)rest * A.K_pad + k);
     };
     int32_t cur_key = H.run_bin[r0];
-    float2 bacc = make_float2(0.f, 0.f);
+    float4 bacc = zero4;
     for (int32_t rb = r0; rb < r1; rb += kPF) {
-        float2 w[kPF];
+        float4 w[kPF];
 #pragma unroll
         for (int u = 0; u < kPF; ++u) w[u] = wrest(rb + u);
         for (int u = 0; u < kPF; ++u) {
             const int32_t r = rb + u;
             if (r >= r1) break;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int32_t q = H.run_start[r]; q < H.run_start[r + 1]; ++q) {
-                const float2 v = ld2(wl + (int64_t)((H.hpt[q] & kOffMask) >> 8) * A.K_pad);
-                acc.x += v.x;
-                acc.y += v.y;
-            }
-            bacc.x = fmaf(w[u].x, acc.x, bacc.x);
-            bacc.y = fmaf(w[u].y, acc.y, bacc.y);
+            float4 acc = zero4;
+            for (int32_t q = H.run_start[r]; q < H.run_start[r + 1]; ++q)
+                add4(acc, ld4(wl + (int64_t)(H.perm[q] % H.n_last) * A.K_pad));
+            fma4(bacc, w[u], acc);
             const int32_t nk = r + 1 < r1 ? H.run_bin[r + 1] : -1;
             if (nk != cur_key) {
                 flush(cur_key, bacc);
-                bacc = make_float2(0.f, 0.f);
+                bacc = zero4;
                 cur_key = nk;
             }
         }
@@ -504,6 +570,7 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
         const auto &HL = g->hl[l < g->n_layouts ? l : 0];
         LayoutArgs &La = l == 0 ? A.L0 : A.L1;
         La.hpt = HL.hpt;
+        La.perm = HL.perm;
         La.run_start = HL.run_start;
         La.run_rest = HL.run_rest;
         La.run_bin = HL.run_bin;
@@ -547,8 +614,8 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
     int P_max;
     const HistArgs A = hist_args_for(g, K, hist, rows, P_max);
     const size_t smem = hist_smem_bytes(rows);
-    // run-end words encode the rest index in 15 bits (3-D: a0 < 256, a1 < 128)
-    const bool coded = nd == 2 || (g->n[0] <= 256 && g->n[1] <= 128);
+    // run-end words encode the rest index in 21 bits (3-D: a0 < 512, a1 < 4096)
+    const bool coded = nd == 2 || (g->n[0] <= 512 && g->n[1] <= 4096);
     const int G = A.C / kHistWarps;
     dim3 grd((unsigned)(P_max * G), (unsigned)ceil_div64(K, kKT));
     {
