@@ -14,8 +14,8 @@ namespace {
 
 constexpr int kSortTile = 2048;      // points per warp in the counting sort
 constexpr int kSortWarps = 4;        // warps per CTA in the counting sort
-// Packed sorted-point word: the gathered-axis row inside its part << 8 (the
-// byte offset of its row in a 64-float shared-memory tile), run-end flag
+// Packed sorted-point word: the gathered-axis row inside its part << 9 (the
+// byte offset of its row in a 128-float shared-memory tile), run-end flag
 // (bit 30), key-end flag (bit 31).
 constexpr int kRowShift = 9;   // shared-memory tile rows of 512 bytes (128 floats)
 constexpr int kRowBits = 9;    // row field width (tile rows < 512)

@@ -104,6 +104,101 @@ __global__ void __launch_bounds__(kThreads) k_weights(const float *__restrict__ 
     }
 }
 
+// Row-per-lane form for B <= 1024: lane l of every warp owns row k0 + l, so
+// the 32 shared-memory atomics of one instruction go to 32 different rows'
+// histograms (row stride B + 1: 32 different banks) and never collide.  Each
+// lane streams 64 contiguous bytes of its row per step; the z and bin values
+// of a step are the same for every lane (broadcast loads).  Warps split the
+// CTA's point range; the CTA's 32 histograms live in shared memory.
+constexpr int kRowsT = 32;
+constexpr int kPtsT = 16;   // points per lane per step
+__global__ void __launch_bounds__(kThreads) k_weights_t(const float *__restrict__ W, int64_t K, int64_t N,
+                                                        const float *__restrict__ z32,
+                                                        const int32_t *__restrict__ bins, int B, int64_t n_split,
+                                                        double *__restrict__ mpart, float *__restrict__ hpart) {
+    extern __shared__ float sh[];  // [kRowsT][B + 1]
+    __shared__ float red[kThreads / 32][kRowsT][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t split = blockIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.y * kRowsT;
+    const int ld = B + 1;
+    for (int e = threadIdx.x; e < kRowsT * ld; e += blockDim.x) sh[e] = 0.f;
+    __syncthreads();
+    const float *wrow = W + min(k0 + lane, K - 1) * N;  // rows past K are never stored
+    float *hrow = sh + lane * ld;
+    // moments: a step's 16 points are summed on their own, then added to the
+    // running sums (two-level FP32 summation keeps the rounding error of a
+    // lane's long point range small)
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+    auto point = [&](float w, float p, int b) {
+        float t = w * p;
+        t0 += t;
+        t *= p;
+        t1 += t;
+        t *= p;
+        t2 += t;
+        t *= p;
+        t3 += t;
+        atomicAdd(hrow + b, w);
+    };
+    auto fold = [&]() {
+        m0 += t0;
+        m1 += t1;
+        m2 += t2;
+        m3 += t3;
+        t0 = t1 = t2 = t3 = 0.f;
+    };
+    // vector steps of kPtsT points (rows 16-byte aligned only when N % 4 == 0)
+    const bool vec = N % 4 == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+    const int64_t n_steps = vec ? N / kPtsT : 0;
+    const int64_t per = (n_steps + n_split - 1) / n_split;
+    const int64_t s0 = split * per, s1 = min(n_steps, s0 + per);
+    for (int64_t st = s0 + warp; st < s1; st += kThreads / 32) {
+        const int64_t i = st * kPtsT;
+        float4 w[4], z[4];
+        int4 b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = __ldcs(reinterpret_cast<const float4 *>(wrow + i) + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            z[q] = *reinterpret_cast<const float4 *>(z32 + i + 4 * q);
+            b[q] = *reinterpret_cast<const int4 *>(bins + i + 4 * q);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            point(w[q].x, z[q].x, b[q].x);
+            point(w[q].y, z[q].y, b[q].y);
+            point(w[q].z, z[q].z, b[q].z);
+            point(w[q].w, z[q].w, b[q].w);
+        }
+        fold();
+    }
+    // points not covered by the vector steps, split evenly
+    {
+        const int64_t rem = N - n_steps * kPtsT;
+        const int64_t per1 = (rem + n_split - 1) / n_split;
+        const int64_t i0 = n_steps * kPtsT + split * per1, i1 = min(N, i0 + per1);
+        for (int64_t i = i0 + warp; i < i1; i += kThreads / 32) point(wrow[i], z32[i], bins[i]);
+        fold();
+    }
+    red[warp][lane][0] = m0;
+    red[warp][lane][1] = m1;
+    red[warp][lane][2] = m2;
+    red[warp][lane][3] = m3;
+    __syncthreads();
+    if (threadIdx.x < kRowsT * 4) {
+        const int r = threadIdx.x >> 2, j = threadIdx.x & 3;
+        double v = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) v += red[q][r][j];
+        if (k0 + r < K) mpart[(split * K + k0 + r) * 4 + j] = v;
+    }
+    for (int e = threadIdx.x; e < kRowsT * B; e += blockDim.x) {
+        const int r = e / B, bb = e - r * B;
+        if (k0 + r < K) hpart[(split * K + k0 + r) * B + bb] = sh[r * ld + bb];
+    }
+}
+
 __global__ void k_weights_finish(const double *__restrict__ mpart, const float *__restrict__ hpart,
                                  int64_t n_split, int64_t K, int B, int J, const double *__restrict__ scale,
                                  double *__restrict__ raw, float *__restrict__ hist) {
@@ -143,6 +238,25 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
     k_z32<<<(unsigned)std::min<int64_t>(ceil_div64(N, 256), 4096), 256, 0, s>>>(g->y, N, g->ydev_scale,
                                                                                 (float *)g_wz32.p);
     VUP_CHECK_LAUNCH();
+    if (B <= 1024) {
+        const int64_t rows = ceil_div64(K, kRowsT);
+        int64_t n_split = std::max<int64_t>(1, (int64_t)vup_num_sms() * 4 / std::max<int64_t>(rows, 1));
+        n_split = std::min<int64_t>(n_split, std::max<int64_t>(1, N / 8192));
+        if ((st = devbuf_reserve(g_wmpart, sizeof(double) * 4 * K * n_split)) != VUP_OK) return st;
+        if ((st = devbuf_reserve(g_whpart, sizeof(float) * (size_t)B * K * n_split)) != VUP_OK) return st;
+        const size_t smem = sizeof(float) * (size_t)kRowsT * (B + 1);
+        VUP_PROF("weights_stream", s, 3);
+        VUP_CHECK_CUDA(cudaFuncSetAttribute(k_weights_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_weights_t<<<dim3((unsigned)n_split, (unsigned)rows), kThreads, smem, s>>>(
+            W, K, N, (const float *)g_wz32.p, g->bins, B, n_split, (double *)g_wmpart.p, (float *)g_whpart.p);
+        VUP_CHECK_LAUNCH();
+        const int64_t tot = std::max<int64_t>(K * B, K * g->J);
+        k_weights_finish<<<(unsigned)ceil_div64(tot, 256), 256, 0, s>>>((const double *)g_wmpart.p,
+                                                                        (const float *)g_whpart.p, n_split, K, B,
+                                                                        g->J, g->ydev_scale, raw, hist);
+        VUP_CHECK_LAUNCH();
+        return VUP_OK;
+    }
     const int RB = B <= 3072 ? 8 : (B <= 6144 ? 4 : 2);
     const int64_t rows = ceil_div64(K, RB);
     int64_t n_split = std::max<int64_t>(1, (int64_t)vup_num_sms() * 8 / std::max<int64_t>(rows, 1));

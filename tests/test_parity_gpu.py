@@ -351,3 +351,22 @@ def test_max_bins_and_long_axis():
                      I.config("c1", "small").dens.take(range(5)), 8192)
     prob.dens.mu[:, 0] = np.linspace(-2, 2, 5)
     _parity(prob, "fp64")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_tiny_2d_case_matches_stored_values(precision):
+    """The stored oracle values of tests/golden (written by make_golden.py)."""
+    from tests.golden import make_golden as G
+    prob = [p for p in G.cases() if p.name == "tiny_2d_mixed"][0]
+    stored = G.read(prob.name)
+    vup = vupmod()
+    g, raw, cen, hs = gpu_run(prob, precision)
+    res = O.solve(prob)
+    scale = Hp.abs_moment_scale(prob, res["y"], np.arange(prob.K))
+    Hp.check_moments(raw, stored["raw"], scale, Hp.TOL[precision])
+    Hp.check_hist(hs, stored["hist"])
+    dmu, dsg = g.ipsa(vup.densities_to_device(prob.dens), precision)
+    g.sync()
+    sc = np.abs(stored["dmu"]).max() + np.abs(stored["dsigma"]).max()
+    assert np.abs(dmu.cpu().numpy() - stored["dmu"]).max() / sc < 10 * Hp.TOL[precision]
+    assert np.abs(dsg.cpu().numpy() - stored["dsigma"]).max() / sc < 10 * Hp.TOL[precision]
