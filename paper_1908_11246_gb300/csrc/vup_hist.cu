@@ -177,6 +177,25 @@ struct ItemCtx {
     int *dstatus;
 };
 
+// Store the finished sums of one key for a lane's four densities: keys cut by
+// the chunk bounds go to the chunk's partials (side 0 = its first key), the
+// others straight to the output.  Out of line: it runs once per key, and
+// keeping it out of the point loop keeps that loop's code small.
+__device__ __noinline__ void flush_key(const ItemCtx *X, int c, int p, int64_t k, int32_t key, float4 v,
+                                       bool shared, bool first) {
+    if (shared) {
+        *reinterpret_cast<float4 *>(X->part + ((int64_t)c * 2 + (first ? 0 : 1)) * X->K_pad + k) = v;
+    } else {
+        const int B = X->B;
+        const int64_t K = X->K;
+        float *o = X->out + k * B + (key - p * B);
+        if (k < K) o[0] = v.x;
+        if (k + 1 < K) o[B] = v.y;
+        if (k + 2 < K) o[2 * B] = v.z;
+        if (k + 3 < K) o[3 * B] = v.w;
+    }
+}
+
 // One work item: part p, chunk group cg (kHistWarps chunks, one per warp) and
 // the 128 densities from k0 of the instance *Ap (kernel parameter or global
 // memory).  Called by every thread of the CTA; `wseq` counts the staging
@@ -242,19 +261,8 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     const bool sh_first = H.koff[first_key] < p0 || H.koff[first_key + 1] > p1;
     const bool sh_last = H.koff[last_key] < p0 || H.koff[last_key + 1] > p1;
     auto flush = [&](int32_t key, float4 v) {
-        const bool shared = key == first_key ? sh_first : (key == last_key && sh_last);
-        if (shared) {
-            const int side = key == first_key ? 0 : 1;
-            *reinterpret_cast<float4 *>(X.part + ((int64_t)c * 2 + side) * X.K_pad + k) = v;
-        } else {
-            const int B = X.B;
-            const int64_t K = X.K;
-            float *o = X.out + k * B + (key - p * B);
-            if (k < K) o[0] = v.x;
-            if (k + 1 < K) o[B] = v.y;
-            if (k + 2 < K) o[2 * B] = v.z;
-            if (k + 3 < K) o[3 * B] = v.w;
-        }
+        const bool first = key == first_key;
+        flush_key(&X, c, p, k, key, v, first ? sh_first : (key == last_key && sh_last), first);
     };
 
     // staging of the sorted point stream: window i of this item lands in
@@ -283,9 +291,10 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         }
         return ld4(g0k + rest * K_pad);
     };
-    float4 f0 = rest_factor(r0), f1 = rest_factor(r0 + 1), f2 = rest_factor(r0 + 2), f3 = rest_factor(r0 + 3);
-    // factor of run r + 4, decoded from run r's end word (the load stays in
-    // flight): 9 low bits below the row field and 12 bits above it
+    // fc = factor of the current run, f1..f3 those of the next three runs
+    float4 fc = rest_factor(r0), f1 = rest_factor(r0 + 1), f2 = rest_factor(r0 + 2), f3 = rest_factor(r0 + 3);
+    // factor of run r + 4, decoded from run r's end word: 9 low bits below the
+    // row field and 12 bits above it
     auto coded_factor = [&](uint32_t u) -> float4 {
         if (NF == 2) {
             const uint32_t a0 = u & 0x1ffu, a1 = (u >> 18) & 0xfffu;
@@ -295,24 +304,25 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         return ld4(g0k + (int64_t)idx * K_pad);
     };
 
+    // every point's factor is multiplied by its run's rest-axis factor fc as it
+    // is added (one FMA per density, the same count as a plain add), so a run
+    // end only advances the factor pipeline
     int32_t r = r0, cur_key = first_key;
-    float4 acc = zero4, bacc = zero4;
+    float4 bacc = zero4;
     const uint32_t wsl = smem_u32(ws) + lane * 16;
     const uint32_t null_word = (uint32_t)nrows << kRowShift;  // zero row, no flags
 
     auto run_end = [&](uint32_t u) {
-        fma4(bacc, f0, acc);
-        acc = zero4;
         if (u & kBinEnd) {
             flush(cur_key, bacc);
             bacc = zero4;
             cur_key = r + 1 < r1 ? H.run_bin[r + 1] : -1;
         }
-        ++r;
-        f0 = f1;
+        fc = f1;
         f1 = f2;
         f2 = f3;
         f3 = coded_factor(u);
+        ++r;
     };
     auto gather = [&](uint32_t addr) -> float4 {
         float4 v;
@@ -326,20 +336,20 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         if (((v.x | v.y | v.z | v.w) & kFlags) == 0) {
             const float4 a0 = gather(wsl + v.x), a1 = gather(wsl + v.y), a2 = gather(wsl + v.z),
                          a3 = gather(wsl + v.w);
-            add4(acc, a0);
-            add4(acc, a1);
-            add4(acc, a2);
-            add4(acc, a3);
+            fma4(bacc, fc, a0);
+            fma4(bacc, fc, a1);
+            fma4(bacc, fc, a2);
+            fma4(bacc, fc, a3);
         } else {
             const float4 a0 = gather(wsl + (v.x & kOffMask)), a1 = gather(wsl + (v.y & kOffMask)),
                          a2 = gather(wsl + (v.z & kOffMask)), a3 = gather(wsl + (v.w & kOffMask));
-            add4(acc, a0);
+            fma4(bacc, fc, a0);
             if (v.x & kFlags) run_end(v.x);
-            add4(acc, a1);
+            fma4(bacc, fc, a1);
             if (v.y & kFlags) run_end(v.y);
-            add4(acc, a2);
+            fma4(bacc, fc, a2);
             if (v.z & kFlags) run_end(v.z);
-            add4(acc, a3);
+            fma4(bacc, fc, a3);
             if (v.w & kFlags) run_end(v.w);
         }
     };
