@@ -182,7 +182,7 @@ static void free_grid(vup_grid g) {
     cudaFree(g->flags_scan);
     cudaFree(g->ydev_scale);
     cudaFree(g->dstatus);
-    for (int o = 0; o < 2; ++o) {
+    for (int o = 0; o < kNumOrient; ++o) {
         cudaFree(g->zs[o]);
         cudaFree(g->zt_hi[o]);
         cudaFree(g->zt_lo[o]);
@@ -231,9 +231,23 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
         ori.Q = N / ori.R;
         ori.NC = ori.Q * 4;
         ori.n_rest_axes = 0;
+        ori.n_red_axes = 1;
         ori.rest_axes[0] = ori.rest_axes[1] = -1;
         for (int d = 0; d < ndim; ++d)
             if (d != ori.red_axis0 && ori.n_rest_axes < 2) ori.rest_axes[ori.n_rest_axes++] = d;
+    }
+    if (ndim == 3) {
+        // grouped: reduce over axes 1 and 2 (flat r = a1 n2 + a2), rest = axis 0
+        Orient &ori = g->orient[kOrientGrouped];
+        ori.red_axis0 = 1;
+        ori.n_red_axes = 2;
+        ori.R = g->n[1] * g->n[2];
+        ori.R_pad = ceil_div64(ori.R, 64) * 64;
+        ori.Q = g->n[0];
+        ori.NC = ori.Q * 4;
+        ori.n_rest_axes = 1;
+        ori.rest_axes[0] = 0;
+        ori.rest_axes[1] = -1;
     }
     g->n_chunks = vup_hist_chunks_for(N);
     const int C = g->n_chunks;
@@ -305,9 +319,9 @@ static vup_status finish_model(vup_grid g, cudaStream_t s) {
     vup_status st = vup_launch_grid_finish(g, s);
     if (st != VUP_OK) return st;
     if (g->ndim >= 2) {
-        st = vup_build_tables(g, 0, 0, s);
+        st = vup_build_tables(g, kOrientLast, 0, s);
         if (st != VUP_OK) return st;
-        st = vup_build_tables(g, 0, 1, s);
+        st = vup_build_tables(g, vup_tc_orient(g), 1, s);
         if (st != VUP_OK) return st;
     }
     g->have_model = 1;
@@ -372,7 +386,7 @@ vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa) {
     if ((st = devbuf_reserve(g->dstats, sizeof(DensStats) * K_pad * nd)) != VUP_OK) return st;
     if ((st = devbuf_reserve(g->ftab, sizeof(float) * K_pad * vup_ftab_floats(g))) != VUP_OK) return st;
     if (nd >= 2) {
-        const int64_t nct = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles(g->orient[0]));
+        const int64_t nct = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles(g->orient[vup_tc_orient(g)]));
         if ((st = devbuf_reserve(g->partials, sizeof(float) * 4 * K_pad * nct)) != VUP_OK) return st;
         if ((st = devbuf_reserve(g->hist_part, sizeof(float) * 2 * K_pad * g->n_chunks * g->hist_P)) != VUP_OK)
             return st;
@@ -380,7 +394,8 @@ vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa) {
             (st = devbuf_reserve(g->hist_direct, sizeof(float) * (size_t)g->hist_P * K * g->B)) != VUP_OK)
             return st;
         if (bf16) {
-            size_t a = (size_t)K_pad * g->orient[0].R_pad + (ipsa ? (size_t)K_pad * g->orient[1].R_pad : 0);
+            size_t a = (size_t)K_pad * g->orient[vup_tc_orient(g)].R_pad +
+                       (ipsa ? (size_t)K_pad * g->orient[1].R_pad : 0);
             if ((st = devbuf_reserve(g->atab_hi, sizeof(__nv_bfloat16) * a)) != VUP_OK) return st;
             if ((st = devbuf_reserve(g->atab_lo, sizeof(__nv_bfloat16) * a)) != VUP_OK) return st;
         }
@@ -413,12 +428,13 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
     const bool bf16 = precision == VUP_BF16X3;
     const bool want_m = moments_raw || moments_central;
     if ((st = vup_reserve_k(g, K, bf16, false)) != VUP_OK) return st;
-    if ((st = vup_density_prep(g, d, (bf16 && want_m) ? 1 : 0, s)) != VUP_OK) return st;
+    const int to = vup_tc_orient(g);
+    if ((st = vup_density_prep(g, d, (bf16 && want_m) ? (1 << to) : 0, s)) != VUP_OK) return st;
     if (want_m) {
         int64_t nct;
         if (bf16) {
-            if ((st = vup_moments_tc(g, K, 0, 1, (float *)g->partials.p, s)) != VUP_OK) return st;
-            nct = vup_tc_col_tiles(g->orient[0]);
+            if ((st = vup_moments_tc(g, K, to, 1, (float *)g->partials.p, s)) != VUP_OK) return st;
+            nct = vup_tc_col_tiles(g->orient[to]);
         } else {
             if ((st = vup_moments_simt(g, K, 0, 1, (float *)g->partials.p, s)) != VUP_OK) return st;
             nct = vup_simt_col_tiles(g->orient[0]);

@@ -225,6 +225,91 @@ __device__ __forceinline__ void split_transpose_body(const float *__restrict__ t
     __syncthreads();
 }
 
+// Grouped 3-D orientation: A[k][r] = w1[k][a1] w2[k][a2], r = a1 n2 + a2 (the
+// product density over the two reduction axes, formed in FP32 exactly as the
+// histogram kernel forms it), split into BF16 hi + lo and written K-major
+// ([K_pad][R_pad], r contiguous).  A 32 (r) x 32 (k) tile goes through shared
+// memory so that the factor reads (k contiguous) and the table writes (r
+// contiguous) are both coalesced.
+__global__ void k_split_product(const float *__restrict__ w1, const float *__restrict__ w2, int64_t n2,
+                                int64_t R, int64_t K_pad, int64_t R_pad, __nv_bfloat16 *__restrict__ hi,
+                                __nv_bfloat16 *__restrict__ lo) {
+    __shared__ float t[32][33];
+    const int64_t r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int64_t r = r0 + y, k = k0 + threadIdx.x;
+        float v = 0.f;
+        if (r < R && k < K_pad) {
+            const int64_t a1 = r / n2, a2 = r - a1 * n2;
+            v = w1[a1 * K_pad + k] * w2[a2 * K_pad + k];
+        }
+        t[y][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int64_t k = k0 + y, r = r0 + threadIdx.x;
+        if (k < K_pad && r < R_pad) {
+            const float v = t[threadIdx.x][y];
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            hi[k * R_pad + r] = h;
+            lo[k * R_pad + r] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+// Same table, one CTA per 32 densities when both axes' factors fit in shared
+// memory: the factors are staged once ([32][n + 1] per axis) and each warp
+// writes whole rows, two r per lane per step (128-byte coalesced stores).
+__global__ void __launch_bounds__(256) k_split_product_rows(const float *__restrict__ w1,
+                                                            const float *__restrict__ w2, int64_t n1, int64_t n2,
+                                                            int64_t R, int64_t K_pad, int64_t R_pad,
+                                                            __nv_bfloat16 *__restrict__ hi,
+                                                            __nv_bfloat16 *__restrict__ lo) {
+    extern __shared__ float sh[];
+    const int64_t l1 = n1 + 1, l2 = n2 + 1;
+    float *s1 = sh, *s2 = sh + 32 * l1;
+    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    for (int64_t e = threadIdx.x; e < 32 * n1; e += blockDim.x) {
+        const int64_t a = e >> 5, kk = e & 31;
+        s1[kk * l1 + a] = w1[a * K_pad + k0 + kk];
+    }
+    for (int64_t e = threadIdx.x; e < 32 * n2; e += blockDim.x) {
+        const int64_t a = e >> 5, kk = e & 31;
+        s2[kk * l2 + a] = w2[a * K_pad + k0 + kk];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int kk = warp; kk < 32; kk += blockDim.x >> 5) {
+        const float *f1 = s1 + kk * l1, *f2 = s2 + kk * l2;
+        uint32_t *oh = reinterpret_cast<uint32_t *>(hi + (k0 + kk) * R_pad);
+        uint32_t *ol = reinterpret_cast<uint32_t *>(lo + (k0 + kk) * R_pad);
+        int64_t r = 2 * lane;
+        int64_t a1 = r / n2, a2 = r - a1 * n2;
+        for (; r < R_pad; r += 64) {
+            float v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                int64_t b1 = a1, b2 = a2 + e;
+                if (b2 >= n2) {
+                    b2 -= n2;
+                    ++b1;
+                }
+                v[e] = r + e < R ? f1[b1] * f2[b2] : 0.f;
+            }
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]), h1 = __float2bfloat16_rn(v[1]);
+            const __nv_bfloat16 g0 = __float2bfloat16_rn(v[0] - __bfloat162float(h0));
+            const __nv_bfloat16 g1 = __float2bfloat16_rn(v[1] - __bfloat162float(h1));
+            oh[r >> 1] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            ol[r >> 1] = (uint32_t)__bfloat16_as_ushort(g0) | ((uint32_t)__bfloat16_as_ushort(g1) << 16);
+            a2 += 64;
+            while (a2 >= n2) {
+                a2 -= n2;
+                ++a1;
+            }
+        }
+    }
+}
+
 __global__ void k_density_prep(DensJob J) { density_prep_body(J, blockIdx.x, blockIdx.y, blockIdx.z); }
 __global__ void k_density_finish(DensJob J) { density_finish_body(J, blockIdx.x, blockIdx.y); }
 __global__ void k_split_transpose(const float *__restrict__ tab, int64_t nd, int64_t K_pad, int64_t R_pad,
@@ -309,6 +394,24 @@ vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_or
     dim3 fgrd((unsigned)ceil_div64(d->K, 128), (unsigned)g->ndim);
     k_density_finish<<<fgrd, 128, 0, s>>>(J);
     VUP_CHECK_LAUNCH();
+    if (need_bf16_orient_mask & (1 << kOrientGrouped)) {
+        const Orient &ori = g->orient[kOrientGrouped];
+        const float *w1 = (const float *)g->ftab.p + g->n[0] * K_pad;
+        const float *w2 = w1 + g->n[1] * K_pad;
+        const size_t smem = sizeof(float) * 32 * (size_t)(g->n[1] + g->n[2] + 2);
+        if (smem <= 160 * 1024) {
+            VUP_CHECK_CUDA(
+                cudaFuncSetAttribute(k_split_product_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_split_product_rows<<<(unsigned)(K_pad / 32), 256, smem, s>>>(
+                w1, w2, g->n[1], g->n[2], ori.R, K_pad, ori.R_pad, (__nv_bfloat16 *)g->atab_hi.p,
+                (__nv_bfloat16 *)g->atab_lo.p);
+        } else {
+            dim3 tg((unsigned)ceil_div64(ori.R_pad, 32), (unsigned)ceil_div64(K_pad, 32));
+            k_split_product<<<tg, dim3(32, 8), 0, s>>>(w1, w2, g->n[2], ori.R, K_pad, ori.R_pad,
+                                                       (__nv_bfloat16 *)g->atab_hi.p, (__nv_bfloat16 *)g->atab_lo.p);
+        }
+        VUP_CHECK_LAUNCH();
+    }
     for (int o = 0; o < 2; ++o) {
         if (!(need_bf16_orient_mask & (1 << o))) continue;
         const Orient &ori = g->orient[o];

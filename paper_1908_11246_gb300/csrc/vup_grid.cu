@@ -740,7 +740,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
         k_pick_layout<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->n_layouts > 1 ? g->hl[1].n_runs : nullptr, g->hist_sel);
         VUP_CHECK_LAUNCH();
     }
-    g->have_tab[0][0] = g->have_tab[0][1] = g->have_tab[1][0] = g->have_tab[1][1] = 0;
+    for (int o = 0; o < kNumOrient; ++o) g->have_tab[o][0] = g->have_tab[o][1] = 0;
     return VUP_OK;
 }
 
@@ -749,10 +749,12 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
 vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
     if (g->have_tab[orient][bf16]) return VUP_OK;
     const Orient &o = g->orient[orient];
-    // View y as [P][S]: orientation 0 -> P = rest (Q), S = red (R);
-    // orientation 1 (2-D) -> P = axis 0 = red, S = axis 1 = rest.
-    const int64_t P = orient == 0 ? o.Q : o.R;
-    const int64_t S = orient == 0 ? o.R : o.Q;
+    // View y as [P][S]: orientations 0 and 2 -> P = rest (Q), S = red (R)
+    // (the reduction axes are the trailing ones); orientation 1 (2-D) ->
+    // P = axis 0 = red, S = axis 1 = rest.
+    const bool first = orient == kOrientFirst;
+    const int64_t P = first ? o.R : o.Q;
+    const int64_t S = first ? o.Q : o.R;
     dim3 blk(32, 8), grd((unsigned)ceil_div64(S, 32), (unsigned)ceil_div64(P, 32));
     VUP_PROF(bf16 ? "power_table_bf16" : "power_table_fp32", s, 1);
     if (!bf16) {
@@ -761,7 +763,7 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
         if (!g->zs[orient]) VUP_CHECK_CUDA(cudaMalloc(&g->zs[orient], bytes));
         VUP_CHECK_CUDA(cudaMemsetAsync(g->zs[orient], 0, bytes, s));
         // SIMT wants [r][q*4+j]: orientation 0 -> rows s (mode 1); 1 -> rows p (mode 3)
-        k_power_table<float><<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, orient == 0 ? 1 : 3, ld,
+        k_power_table<float><<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, first ? 3 : 1, ld,
                                                  g->zs[orient], nullptr);
         VUP_CHECK_LAUNCH();
     } else {
@@ -775,7 +777,7 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
         VUP_CHECK_CUDA(cudaMemsetAsync(g->zt_hi[orient], 0, bytes, s));
         VUP_CHECK_CUDA(cudaMemsetAsync(g->zt_lo[orient], 0, bytes, s));
         // tensor wants [q*4+j][r]: orientation 0 -> rows (p, j) (mode 0); 1 -> rows (s, j) (mode 2)
-        k_power_table<__nv_bfloat16><<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, orient == 0 ? 0 : 2, ld,
+        k_power_table<__nv_bfloat16><<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, first ? 2 : 0, ld,
                                                          g->zt_hi[orient], g->zt_lo[orient]);
         VUP_CHECK_LAUNCH();
     }

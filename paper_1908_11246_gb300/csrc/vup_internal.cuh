@@ -62,7 +62,13 @@ struct Orient {
     int64_t NC;         // Q * J
     int rest_axes[2];   // rest axes (up to 2), -1 if unused
     int n_rest_axes;
+    int n_red_axes;     // 1, or 2 for the grouped 3-D orientation (axes 1 and 2)
 };
+
+// Orientation indices: 0 = reduce over the last axis, 1 = reduce over axis 0
+// (2-D, IPSA), 2 = 3-D grids reduce over axes 1 and 2 (tensor-core path; its
+// A operand is the product table w1 (x) w2).
+enum { kOrientLast = 0, kOrientFirst = 1, kOrientGrouped = 2, kNumOrient = 3 };
 
 struct vup_grid_s {
     int device = 0;
@@ -118,13 +124,12 @@ struct vup_grid_s {
     int32_t *flags_scan = nullptr; // [N] scratch
     int32_t n_chunks = 0;
 
-    // power tables; orientation 0 = reduce over the last axis,
-    // orientation 1 = reduce over axis 0 (2-D only, for the IPSA adjoint)
-    Orient orient[2];
-    int have_tab[2][2] = {{0, 0}, {0, 0}};  // [orient][0: fp32, 1: bf16]
-    float *zs[2] = {nullptr, nullptr};          // SIMT layout [R][NC]
-    __nv_bfloat16 *zt_hi[2] = {nullptr, nullptr};  // tensor layout [NC][R_pad]
-    __nv_bfloat16 *zt_lo[2] = {nullptr, nullptr};
+    // power tables per orientation (kOrient*)
+    Orient orient[kNumOrient];
+    int have_tab[kNumOrient][2] = {};               // [orient][0: fp32, 1: bf16]
+    float *zs[kNumOrient] = {};                      // SIMT layout [R][NC]
+    __nv_bfloat16 *zt_hi[kNumOrient] = {};           // tensor layout [NC][R_pad]
+    __nv_bfloat16 *zt_lo[kNumOrient] = {};
     double *ydev_scale = nullptr;  // [1] s on device
 
     // per-K scratch (density constants, factor tables, partials)
@@ -158,6 +163,8 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
                             cudaStream_t s);
 
 int vup_num_sms();
+// Orientation of the forward tensor-core contraction: grouped on 3-D grids.
+inline int vup_tc_orient(const vup_grid_s *g) { return g->ndim == 3 ? kOrientGrouped : kOrientLast; }
 bool vup_profiling();
 vup_status vup_check_dens(vup_grid g, const vup_densities *d);
 vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa);
