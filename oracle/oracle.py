@@ -61,6 +61,16 @@ def lib():
             l.oracle_ipsa.restype = C.c_int
             l.oracle_ipsa.argtypes = ([C.c_int, ip64, dp, dp, dp, C.c_int, C.c_int64, ip64]
                                       + dens + [dp, dp, C.c_int])
+            l.oracle_model_at.restype = C.c_int
+            l.oracle_model_at.argtypes = [C.c_int, dp, C.c_int, C.c_int64, dp, dp]
+            l.oracle_deviation_moments.restype = C.c_int
+            l.oracle_deviation_moments.argtypes = ([C.c_int, ip64, dp, dp, dp, C.c_int, C.c_int64, ip64, dp]
+                                                   + dens + [dp])
+            l.oracle_ipsa_matrix.restype = None
+            l.oracle_ipsa_matrix.argtypes = [C.c_int64, C.c_int, C.c_double, C.c_double, dp, dp, C.c_int,
+                                             C.c_double, C.c_double, dp]
+            l.oracle_sa_fields.restype = None
+            l.oracle_sa_fields.argtypes = [C.c_int64, C.c_int, dp, C.c_double, dp, ip32, ip32, dp]
             _lib = l
     return _lib
 
@@ -180,3 +190,58 @@ def solve(problem, rows=None, threads=0):
                     problem.dens, rows=rows, threads=threads)
     out.update(y=y, bins=b, ymin=ymin, ymax=ymax)
     return out
+
+
+# ---------------------------------------------------------------- Sec. 5.2 IPSA
+def model_at(model_id, theta, x):
+    """The model at arbitrary points x [K][ndim] (e.g. the estimated values
+    y(l) = M(l, 0) at the densities' centres)."""
+    x = _f64(np.atleast_2d(x))
+    K, nd = x.shape
+    th = np.zeros(8)
+    th[:len(theta)] = theta
+    y = np.empty(K)
+    if lib().oracle_model_at(int(model_id), _p(th, C.c_double), nd, K, _p(x, C.c_double), _p(y, C.c_double)):
+        raise OracleError("model not defined for this dimension")
+    return y
+
+
+def deviation_moments(n, lo, hi, y, J, dens, yref, rows=None):
+    """sum_i W[k,i] (y_i - yref[k])^j, j = 1..J (Eq. IPSAvar: Delta^2 = half of j = 2)."""
+    K = dens.K
+    rows = np.arange(K, dtype=np.int64) if rows is None else np.asarray(rows, np.int64)
+    out = np.empty((rows.size, J))
+    n64 = np.asarray(n, np.int64)
+    y, yref = _f64(y), _f64(yref)
+    lo64, hi64 = _f64(lo), _f64(hi)
+    dargs, keep = _dens_args(dens)
+    rc = lib().oracle_deviation_moments(len(n), _p(n64, C.c_int64), _p(lo64, C.c_double), _p(hi64, C.c_double),
+                                        _p(y, C.c_double), int(J), rows.size, _p(rows, C.c_int64),
+                                        _p(yref, C.c_double), *dargs, _p(out, C.c_double))
+    if rc:
+        raise OracleError("a selected distribution has an empty support on the grid")
+    return out
+
+
+def ipsa_matrix(H, ymin, ymax, yref, nd, dlo, dhi):
+    """IPSA probability matrix (Eq. IPSA): columns translated by -yref onto nd deviation bins."""
+    H = _f64(H)
+    K, B = H.shape
+    yref = _f64(yref)
+    out = np.empty((K, nd))
+    lib().oracle_ipsa_matrix(K, B, float(ymin), float(ymax), _p(H, C.c_double), _p(yref, C.c_double), int(nd),
+                             float(dlo), float(dhi), _p(out, C.c_double))
+    return out
+
+
+def sa_fields(H, level, rho=None):
+    """Argmax bin, confidence-interval bins and the rho-marginalised global vector (Sec. 5.2)."""
+    H = _f64(H)
+    K, nb = H.shape
+    am = np.empty(K, np.int32)
+    ci = np.empty((K, 2), np.int32)
+    g = np.empty(nb)
+    r = None if rho is None else _f64(rho)
+    lib().oracle_sa_fields(K, nb, _p(H, C.c_double), float(level), None if r is None else _p(r, C.c_double),
+                           _p(am, C.c_int32), _p(ci, C.c_int32), _p(g, C.c_double))
+    return am, ci, g

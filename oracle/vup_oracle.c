@@ -417,3 +417,125 @@ int oracle_ipsa(int ndim, const int64_t *n, const double *lo, const double *hi, 
     }
     return status;
 }
+
+/* ------------------------------------------------------------------------
+ * IPSA coarse-grained quantities (Sec. 5.2)
+ * ---------------------------------------------------------------------- */
+
+/* The model at arbitrary input points, e.g. the estimated values
+ * y(l) = M(l, 0) at the densities' centres (Sec. 5.2: the deviations of
+ * the IPSA probability matrix are measured from them).  x is [K][ndim]. */
+int oracle_model_at(int model_id, const double *theta, int ndim, int64_t K, const double *x, double *y)
+{
+    if (!model_ndim_ok(model_id, ndim)) return 1;
+    for (int64_t k = 0; k < K; ++k) y[k] = model_value(model_id, theta, ndim, x + k * ndim);
+    return 0;
+}
+
+/* Deviation moments about the estimated values, from their definition:
+ * out[s][j-1] = sum_i W[k,i] (y_i - yref[k])^j, j = 1..J, for the selected
+ * rows k = rows[s].  j = 2 gives twice the local expected square deviation
+ * Delta^2 of Eq. IPSAvar (the 1/2 of that equation is applied by callers). */
+int oracle_deviation_moments(int ndim, const int64_t *n, const double *lo, const double *hi, const double *y,
+                             int J, int64_t S, const int64_t *rows, const double *yref, int64_t K,
+                             const uint8_t *kind, const double *mu, const double *sigma, const double *tlo,
+                             const double *thi, double *out)
+{
+    oracle_dens D = {ndim, n, lo, hi, K, kind, mu, sigma, tlo, thi};
+    int64_t N = 1;
+    for (int d = 0; d < ndim; ++d) N *= n[d];
+    double *W = (double *)malloc(sizeof(double) * N);
+    if (!W) return 2;
+    int status = 0;
+    for (int64_t s = 0; s < S; ++s) {
+        int64_t k = rows[s];
+        if (weights(&D, k, N, W) <= 0.0) {
+            status = 1;
+            continue;
+        }
+        for (int j = 1; j <= J; ++j) {
+            double acc = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double u = y[i] - yref[k];
+                double p = 1.0;
+                for (int e = 0; e < j; ++e) p = p * u;
+                acc += W[i] * p;
+            }
+            out[s * J + (j - 1)] = acc;
+        }
+    }
+    free(W);
+    return status;
+}
+
+/*
+ * IPSA probability matrix (Eq. IPSA): every column of the output
+ * probability matrix translated by -yref[k] (y -> dy = y - y(l)) and
+ * collected on one grid of deviations: nd bins of width (dhi - dlo) / nd
+ * starting at dlo.  Output bin b of [ymin, ymax] (B bins) stands for its
+ * centre c_b = ymin + (b + 1/2) w; its mass goes to deviation bin
+ * floor((c_b - yref[k] - dlo) / wd), clamped to [0, nd - 1] so that every
+ * column keeps its mass.  Sums run over b in increasing order.
+ */
+void oracle_ipsa_matrix(int64_t K, int B, double ymin, double ymax, const double *H, const double *yref,
+                        int nd, double dlo, double dhi, double *out)
+{
+    double w = (ymax - ymin) / (double)B;
+    double wd = (dhi - dlo) / (double)nd;
+    for (int64_t k = 0; k < K; ++k) {
+        double *o = out + k * nd;
+        for (int e = 0; e < nd; ++e) o[e] = 0.0;
+        for (int b = 0; b < B; ++b) {
+            double t = (double)b + 0.5;
+            double c = ymin + t * w;
+            double dy = c - yref[k];
+            double f = floor((dy - dlo) / wd);
+            int e = f < 0.0 ? 0 : (f > (double)(nd - 1) ? nd - 1 : (int)f);
+            o[e] += H[k * B + b];
+        }
+    }
+}
+
+/*
+ * Coarse-grained fields of one probability vector per row (Sec. 5.2: the
+ * maximum probability per l and confidence intervals that vary with l),
+ * and the global vector marginalised over l with weights rho (uniform when
+ * rho is NULL):
+ *   argmax[k] = the first bin of maximum probability;
+ *   ci[k] = (lo, hi): lo the first bin whose cumulative mass exceeds
+ *           (1 - level)/2 of the row total, hi the first bin whose
+ *           cumulative mass reaches (1 + level)/2 of it (FP64 sums in bin
+ *           order);
+ *   global[b] = sum_k rho_k H[k][b] / sum_k rho_k.
+ */
+void oracle_sa_fields(int64_t K, int nb, const double *H, double level, const double *rho, int32_t *argmax,
+                      int32_t *ci, double *global)
+{
+    double lo_q = 0.5 * (1.0 - level), hi_q = 0.5 * (1.0 + level);
+    for (int b = 0; b < nb; ++b) global[b] = 0.0;
+    double rsum = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+        const double *h = H + k * nb;
+        int am = 0;
+        double total = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            if (h[b] > h[am]) am = b;
+            total += h[b];
+        }
+        argmax[k] = am;
+        double cum = 0.0;
+        int lo = nb - 1, hi = nb - 1, have_lo = 0, have_hi = 0;
+        for (int b = 0; b < nb; ++b) {
+            cum += h[b];
+            if (!have_lo && cum > lo_q * total) { lo = b; have_lo = 1; }
+            if (!have_hi && cum >= hi_q * total) { hi = b; have_hi = 1; }
+        }
+        ci[2 * k] = lo;
+        ci[2 * k + 1] = hi;
+        double r = rho ? rho[k] : 1.0;
+        rsum += r;
+        for (int b = 0; b < nb; ++b) global[b] += r * h[b];
+    }
+    if (rsum > 0.0)
+        for (int b = 0; b < nb; ++b) global[b] = global[b] / rsum;
+}
