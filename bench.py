@@ -227,6 +227,10 @@ WORKLOADS = {
            "(grids and model outputs built once)"),
     "weights": ("weights: supplied dense W (FP32 [K][N] in HBM), config-2 grid and model, K=1024, "
                 "4 moments + 256-bin histograms"),
+    "ipsa": ("ipsa: the Sec. 5.3 IPSA example, y = x^2 + 5 sin 3x + alpha on a 1000x1000 grid over "
+             "[-5,5]x[-1.5,1.5], L=1000 locations, sigma_l=0.5, sigma_alpha=0.25, 4 moments + 1000-bin "
+             "histograms, then estimated values, deviation moments, the 1000-bin IPSA probability matrix "
+             "and its argmax / 90% interval / marginalised fields"),
 }
 
 
@@ -241,6 +245,7 @@ class SingleGrid:
             prob.dens = prob.dens.take(range(min(k, prob.K)))
         self.prob = prob
         self.ipsa = name == "c4"
+        self.sa = name == "ipsa"
         self.prec = prec
         self.g = vup.Grid(prob.n, prob.lo, prob.hi)
         self.dev = vup.densities_to_device(prob.dens)
@@ -254,6 +259,18 @@ class SingleGrid:
             self.grad = torch.ones((K, J), dtype=torch.float64, device=dv)
             self.dmu = torch.empty((K, 2), dtype=torch.float32, device=dv)
             self.dsg = torch.empty((K, 2), dtype=torch.float32, device=dv)
+        if self.sa:
+            self.g.eval_model(prob.model_id, prob.theta, B, J)
+            info = self.g.info()
+            self.span = info.ymax - info.ymin
+            self.nd = 1000
+            self.centres = self.dev["mu"].contiguous()
+            self.yref = torch.empty(K, dtype=torch.float64, device=dv)
+            self.dev_m = torch.empty((K, J), dtype=torch.float64, device=dv)
+            self.mat = torch.empty((K, self.nd), dtype=torch.float32, device=dv)
+            self.am = torch.empty(K, dtype=torch.int32, device=dv)
+            self.ci = torch.empty((K, 2), dtype=torch.int32, device=dv)
+            self.glob = torch.empty(self.nd, dtype=torch.float64, device=dv)
         self.units = K * prob.N
         self.K = K
 
@@ -263,6 +280,11 @@ class SingleGrid:
         v.vup_propagate(self.g.h, self.ds, self.prec, self.raw, self.cen, self.hist, stream)
         if self.ipsa:
             v.vup_ipsa_sensitivity(self.g.h, self.ds, self.prec, self.dmu, self.dsg, self.grad, stream)
+        if self.sa:
+            v.vup_model_at(self.g.h, self.centres, self.yref, stream)
+            v.vup_deviation_moments(self.g.h, self.raw, self.yref, self.dev_m, stream)
+            v.vup_ipsa_matrix(self.g.h, self.hist, self.yref, self.nd, -self.span, self.span, self.mat, stream)
+            v.vup_sa_fields(self.mat, 0.9, None, self.am, self.ci, self.glob, stream)
 
     def sync(self):
         self.g.sync()
@@ -271,7 +293,8 @@ class SingleGrid:
         """Host buffers: inputs copied in, every output copied back, each step."""
         torch = self.torch
         host = {k: v.cpu().pin_memory() for k, v in self.dev.items()}
-        outs = [self.raw, self.cen, self.hist] + ([self.dmu, self.dsg] if self.ipsa else [])
+        outs = [self.raw, self.cen, self.hist] + ([self.dmu, self.dsg] if self.ipsa else []) + \
+            ([self.yref, self.dev_m, self.mat, self.am, self.ci, self.glob] if self.sa else [])
         outs_h = [torch.empty_like(x, device="cpu").pin_memory() for x in outs]
         bi = sum(v.numel() * v.element_size() for v in host.values())
         bo = sum(x.numel() * x.element_size() for x in outs_h)

@@ -108,6 +108,7 @@ typedef struct {
 #define VUP_MAX_BINS 8192
 #define VUP_MAX_MOMENTS 4
 #define VUP_MAX_AXIS_POINTS 32767
+#define VUP_MAX_DENSITIES (1 << 22)   /* K per call (larger K: split the call) */
 
 /*
  * Create a grid (Sec. 3 uniform midpoint grid).  n, lo, hi: host arrays of
@@ -165,6 +166,8 @@ vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_precision preci
  * explicitly, as the paper materialises it): W is a device [K][N] float
  * array of per-grid-point weights (used as given, not renormalised).
  *   moments_raw [K][J] double (device, or NULL), hist [K][B] float (device, or NULL).
+ * K <= 65535 x (2 .. 32) depending on B (VUP_ERR_UNSUPPORTED beyond); the
+ * memory of W bounds K long before that.
  */
 vup_status vup_propagate_weights(vup_grid g, int64_t K, const float *W, double *moments_raw,
                                  float *hist, vup_stream_t stream);
@@ -235,6 +238,65 @@ vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, vup_precisio
 vup_status vup_propagate_batched(int n_inst, const vup_grid *g, const vup_densities *d,
                                  vup_precision precision, double *const *moments_raw,
                                  float *const *hist, vup_stream_t stream);
+
+/*
+ * ---- Coarse-grained IPSA quantities (Sec. 5.2) ----------------------------
+ * The estimated value of column l is the model at the centre of its input
+ * density, y(l) = M(l, 0) (the mean of every axis' density); the IPSA
+ * probability matrix (Eq. IPSA) holds the probabilities of the deviations
+ * dy = y - y(l); Eq. IPSAvar's local expected square deviation is
+ * Delta^2 = E[dy^2] / 2.
+ */
+
+/*
+ * The grid's built-in model at K arbitrary points: y[k] = M(x[k]; theta).
+ *   x [K][ndim] double (device), y [K] double (device).
+ * VUP_ERR_STATE if the grid has no built-in model (no vup_eval_model yet,
+ * or outputs supplied with vup_set_outputs: evaluate y(l) yourself then).
+ */
+vup_status vup_model_at(vup_grid g, int64_t K, const double *x, double *y, vup_stream_t stream);
+
+/*
+ * Deviation moments about the estimated values:
+ *   out[k][j-1] = sum_i W[k,i] (y_i - y_ref[k])^j,  j = 1..J (J of the grid),
+ * formed from the raw moments of vup_propagate by the binomial expansion in
+ * FP64.  Delta^2 = out[k][1] / 2.  moments_raw [K][J], y_ref [K], out [K][J],
+ * all double (device).
+ */
+vup_status vup_deviation_moments(vup_grid g, int64_t K, const double *moments_raw, const double *y_ref,
+                                 double *out, vup_stream_t stream);
+
+/*
+ * IPSA probability matrix (Eq. IPSA): every column of the output probability
+ * matrix hist [K][B] (float, device, as written by vup_propagate on this
+ * grid) translated by -y_ref[k] onto n_dbins deviation bins of width
+ * (dhi - dlo) / n_dbins from dlo.  Output bin b stands for its centre
+ * c_b = ymin + (b + 1/2)(ymax - ymin)/B; its mass goes to deviation bin
+ * floor((c_b - y_ref[k] - dlo) / wd), clamped to [0, n_dbins - 1] so that
+ * every column keeps its mass.  All decisions in FP64 with correctly rounded
+ * operations; sums in increasing b.  out [K][n_dbins] float (device).
+ * 1 <= n_dbins <= VUP_MAX_BINS, dlo < dhi finite.
+ */
+vup_status vup_ipsa_matrix(vup_grid g, int64_t K, const float *hist, const double *y_ref, int n_dbins, double dlo,
+                           double dhi, float *out, vup_stream_t stream);
+
+/*
+ * Coarse-grained fields of K probability vectors hist [K][n_bins] (float,
+ * device; an output histogram or an IPSA matrix), Sec. 5.2:
+ *   argmax[k] (int32, or NULL): the first bin of maximum probability;
+ *   ci[k][2] (int32, or NULL): the confidence-interval bins at `level`
+ *       (0 < level < 1): the first bin whose cumulative mass exceeds
+ *       (1 - level)/2 of the row total and the first whose cumulative mass
+ *       reaches (1 + level)/2 of it (FP32 sums in bin order, each
+ *       operation correctly rounded);
+ *   global[n_bins] (double, or NULL): sum_k rho_k hist[k][b] / sum_k rho_k,
+ *       the vector marginalised over l (FP64, summed in blocks of 64 rows);
+ *       rho [K] double (device) or NULL for uniform weights.  The first call
+ *       with a larger K x n_bins than before allocates library scratch.
+ * At least one output must be requested.
+ */
+vup_status vup_sa_fields(int64_t K, int n_bins, const float *hist, double level, const double *rho,
+                         int32_t *argmax, int32_t *ci, double *global, vup_stream_t stream);
 
 /*
  * What the calling thread's most recent vup_propagate_batched did:

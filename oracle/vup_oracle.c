@@ -504,8 +504,10 @@ void oracle_ipsa_matrix(int64_t K, int B, double ymin, double ymax, const double
  *   argmax[k] = the first bin of maximum probability;
  *   ci[k] = (lo, hi): lo the first bin whose cumulative mass exceeds
  *           (1 - level)/2 of the row total, hi the first bin whose
- *           cumulative mass reaches (1 + level)/2 of it (FP64 sums in bin
- *           order);
+ *           cumulative mass reaches (1 + level)/2 of it.  The paper fixes
+ *           no precision for these; they are taken in FP32 (the precision
+ *           of the probabilities themselves): sums in bin order, each
+ *           operation rounded to float;
  *   global[b] = sum_k rho_k H[k][b] / sum_k rho_k.
  */
 void oracle_sa_fields(int64_t K, int nb, const double *H, double level, const double *rho, int32_t *argmax,
@@ -517,18 +519,19 @@ void oracle_sa_fields(int64_t K, int nb, const double *H, double level, const do
     for (int64_t k = 0; k < K; ++k) {
         const double *h = H + k * nb;
         int am = 0;
-        double total = 0.0;
+        float total = 0.0f;
         for (int b = 0; b < nb; ++b) {
             if (h[b] > h[am]) am = b;
-            total += h[b];
+            total = total + (float)h[b];
         }
         argmax[k] = am;
-        double cum = 0.0;
+        float tl = (float)lo_q * total, th = (float)hi_q * total;
+        float cum = 0.0f;
         int lo = nb - 1, hi = nb - 1, have_lo = 0, have_hi = 0;
         for (int b = 0; b < nb; ++b) {
-            cum += h[b];
-            if (!have_lo && cum > lo_q * total) { lo = b; have_lo = 1; }
-            if (!have_hi && cum >= hi_q * total) { hi = b; have_hi = 1; }
+            cum = cum + (float)h[b];
+            if (!have_lo && cum > tl) { lo = b; have_lo = 1; }
+            if (!have_hi && cum >= th) { hi = b; have_hi = 1; }
         }
         ci[2 * k] = lo;
         ci[2 * k + 1] = hi;

@@ -354,6 +354,8 @@ extern "C" vup_status vup_eval_model(vup_grid g, int model_id, const double *the
     if (st != VUP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     g->have_model = 0;
+    g->model_id = model_id;
+    for (int q = 0; q < 8; ++q) g->theta[q] = th[q];
     st = vup_launch_model_eval(g, model_id, th, s);
     if (st != VUP_OK) return st;
     return finish_model(g, s);
@@ -366,12 +368,13 @@ extern "C" vup_status vup_set_outputs(vup_grid g, const double *y_dev, int n_bin
     if (st != VUP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     g->have_model = 0;
+    g->model_id = 0;
     VUP_CHECK_CUDA(cudaMemcpyAsync(g->y, y_dev, sizeof(double) * g->N, cudaMemcpyDeviceToDevice, s));
     return finish_model(g, s);
 }
 
 vup_status vup_check_dens(vup_grid g, const vup_densities *d) {
-    if (!d || d->K < 1 || d->K > (int64_t)1 << 26 || d->ndim != g->ndim) return VUP_ERR_INVALID_ARG;
+    if (!d || d->K < 1 || d->K > VUP_MAX_DENSITIES || d->ndim != g->ndim) return VUP_ERR_INVALID_ARG;
     if (!d->kind || !d->mu || !d->sigma) return VUP_ERR_INVALID_ARG;
     if ((d->lo == nullptr) != (d->hi == nullptr)) return VUP_ERR_INVALID_ARG;
     return VUP_OK;
@@ -449,7 +452,7 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
 
 extern "C" vup_status vup_propagate_weights(vup_grid g, int64_t K, const float *W, double *moments_raw,
                                             float *hist, vup_stream_t stream) {
-    if (!g || !W || K < 1 || K > (int64_t)1 << 26) return VUP_ERR_INVALID_ARG;
+    if (!g || !W || K < 1 || K > VUP_MAX_DENSITIES) return VUP_ERR_INVALID_ARG;
     if (!g->have_model) return VUP_ERR_STATE;
     return vup_weights_path(g, K, W, moments_raw, hist, (cudaStream_t)stream);
 }

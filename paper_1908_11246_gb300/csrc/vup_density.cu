@@ -235,7 +235,7 @@ __global__ void k_split_product(const float *__restrict__ w1, const float *__res
                                 int64_t R, int64_t K_pad, int64_t R_pad, __nv_bfloat16 *__restrict__ hi,
                                 __nv_bfloat16 *__restrict__ lo) {
     __shared__ float t[32][33];
-    const int64_t r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    const int64_t r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;  // x: density tiles, y: reduction tiles
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
         const int64_t r = r0 + y, k = k0 + threadIdx.x;
         float v = 0.f;
@@ -312,9 +312,10 @@ __global__ void __launch_bounds__(256) k_split_product_rows(const float *__restr
 
 __global__ void k_density_prep(DensJob J) { density_prep_body(J, blockIdx.x, blockIdx.y, blockIdx.z); }
 __global__ void k_density_finish(DensJob J) { density_finish_body(J, blockIdx.x, blockIdx.y); }
+// grid: x = density tiles of 32 (K_pad / 32 may exceed the 65535 limit of y), y = axis tiles
 __global__ void k_split_transpose(const float *__restrict__ tab, int64_t nd, int64_t K_pad, int64_t R_pad,
                                   __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
-    split_transpose_body(tab, nd, K_pad, R_pad, hi, lo, blockIdx.x, blockIdx.y);
+    split_transpose_body(tab, nd, K_pad, R_pad, hi, lo, blockIdx.y, blockIdx.x);
 }
 
 // Batched forms: one launch for the blocks of every instance; items[b] =
@@ -406,7 +407,7 @@ vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_or
                 w1, w2, g->n[1], g->n[2], ori.R, K_pad, ori.R_pad, (__nv_bfloat16 *)g->atab_hi.p,
                 (__nv_bfloat16 *)g->atab_lo.p);
         } else {
-            dim3 tg((unsigned)ceil_div64(ori.R_pad, 32), (unsigned)ceil_div64(K_pad, 32));
+            dim3 tg((unsigned)ceil_div64(K_pad, 32), (unsigned)ceil_div64(ori.R_pad, 32));
             k_split_product<<<tg, dim3(32, 8), 0, s>>>(w1, w2, g->n[2], ori.R, K_pad, ori.R_pad,
                                                        (__nv_bfloat16 *)g->atab_hi.p, (__nv_bfloat16 *)g->atab_lo.p);
         }
@@ -426,7 +427,7 @@ vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_or
             hi += o0;
             lo += o0;
         }
-        dim3 tg((unsigned)ceil_div64(ori.R_pad, 32), (unsigned)ceil_div64(K_pad, 32));
+        dim3 tg((unsigned)ceil_div64(K_pad, 32), (unsigned)ceil_div64(ori.R_pad, 32));
         k_split_transpose<<<tg, dim3(32, 8), 0, s>>>((const float *)g->ftab.p + off, g->n[dred], K_pad, ori.R_pad,
                                                      hi, lo);
         VUP_CHECK_LAUNCH();

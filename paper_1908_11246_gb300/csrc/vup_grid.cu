@@ -576,6 +576,26 @@ static GridGeom geom_of(vup_grid g) {
     return G;
 }
 
+// The built-in model at K arbitrary points x [K][ndim] (same arithmetic as
+// the grid evaluation).
+__global__ void k_model_at(const double *__restrict__ x, int64_t K, int ndim, int model, Theta th,
+                           double *__restrict__ y) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double p[3] = {0, 0, 0};
+    for (int d = 0; d < ndim; ++d) p[d] = x[k * ndim + d];
+    y[k] = model_value(model, th, p, ndim);
+}
+
+vup_status vup_launch_model_at(vup_grid g, int64_t K, const double *x, double *y, cudaStream_t s) {
+    Theta th;
+    for (int q = 0; q < 8; ++q) th.t[q] = g->theta[q];
+    VUP_PROF("model_at", s, 1);
+    k_model_at<<<(unsigned)ceil_div64(K, 128), 128, 0, s>>>(x, K, g->ndim, g->model_id, th, y);
+    VUP_CHECK_LAUNCH();
+    return VUP_OK;
+}
+
 vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta, cudaStream_t s) {
     Theta th;
     for (int q = 0; q < 8; ++q) th.t[q] = theta[q];

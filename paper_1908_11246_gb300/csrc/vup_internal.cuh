@@ -80,6 +80,8 @@ struct vup_grid_s {
     // model outputs
     int have_model = 0;
     uint64_t model_gen = 0;        // bumped whenever the model (and its tables) are rebuilt
+    int model_id = 0;              // built-in model of vup_eval_model (0: outputs set by the caller)
+    double theta[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int B = 0, J = 0;
     double host_ext[3] = {0, 0, 1};  // ymin, ymax, s (filled lazily by vup_grid_info)
 
@@ -140,6 +142,7 @@ struct vup_grid_s {
 };
 
 // ---- kernels / launchers implemented in the .cu files -------------------
+vup_status vup_launch_model_at(vup_grid g, int64_t K, const double *x, double *y, cudaStream_t s);
 vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta,
                                  cudaStream_t s);
 vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s);  // range, bins, sort, runs, tables

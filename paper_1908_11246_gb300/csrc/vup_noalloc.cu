@@ -139,6 +139,7 @@ extern "C" vup_status vup_propagate_weights_noalloc(vup_grid g, int64_t K, const
     vup_status st = scratch_address(&scratch);
     if (st != VUP_OK) return st;
     const int64_t rows = ceil_div64(K, RB);
+    if (rows > 65535) return VUP_ERR_UNSUPPORTED;  // one CTA row per RB densities
     int64_t n_split = std::max<int64_t>(1, (int64_t)vup_num_sms() * 8 / std::max<int64_t>(rows, 1));
     n_split = std::min<int64_t>(n_split, std::max<int64_t>(1, N / 4096));
     n_split = std::min<int64_t>(n_split, (int64_t)(kScratchBytes / per_split));

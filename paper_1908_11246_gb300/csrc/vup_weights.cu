@@ -259,6 +259,7 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
     }
     const int RB = B <= 3072 ? 8 : (B <= 6144 ? 4 : 2);
     const int64_t rows = ceil_div64(K, RB);
+    if (rows > 65535) return VUP_ERR_UNSUPPORTED;  // one CTA row per RB densities
     int64_t n_split = std::max<int64_t>(1, (int64_t)vup_num_sms() * 8 / std::max<int64_t>(rows, 1));
     n_split = std::min<int64_t>(n_split, std::max<int64_t>(1, N / 4096));
     if ((st = devbuf_reserve(g_wmpart, sizeof(double) * 4 * K * n_split)) != VUP_OK) return st;

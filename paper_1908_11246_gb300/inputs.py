@@ -188,7 +188,28 @@ def config(name: str, scale: str = "full", seed: int | None = None) -> Problem:
         dens = random_densities(rng, K, lo, hi, kinds=(GAUSS, UNIFORM, TRUNCNORM), sig=sig,
                                 width=width)
         return Problem("c3", n, lo, hi, MODEL_MIXED_3D, (7.0, 0.1), dens, 512, 4, "bf16x3")
+    if name == "ipsa":
+        return ipsa_example(0.5, scale)
     raise ValueError(name)
+
+
+def ipsa_example(sigma_l: float = 0.5, scale: str = "full") -> Problem:
+    """The IPSA example of Sec. 5.3: y = x^2 + 5 sin(3x) + alpha on a
+    1000 x 1000 midpoint grid over [-5, 5] x [-1.5, 1.5], L = 1000
+    measurement locations l (cell-centred over [-5, 5]) with Gaussian
+    measurement uncertainty sigma_l on x and alpha ~ N(0, 0.25^2); 1000 bins.
+    The alpha range (+-6 sigma_alpha) and the x grid extent are readings of
+    the text, which states neither."""
+    small = scale == "small"
+    n = (300, 120) if small else (1000, 1000)
+    L = 37 if small else 1000
+    kind, mu, sigma, tlo, thi = _empty(L, 2)
+    mu[:, 0] = lattice_means(L, -5.0, 5.0)
+    sigma[:, 0] = sigma_l
+    mu[:, 1] = 0.0
+    sigma[:, 1] = 0.25
+    return Problem(f"ipsa_s{sigma_l:g}", n, (-5.0, -1.5), (5.0, 1.5), MODEL_IPSA_EXAMPLE_2D, (),
+                   Densities(kind, mu, sigma, tlo, thi), 100 if small else 1000, 4, "bf16x3")
 
 
 def oscillator_batch(seed: int = 5, n_inst: int = 512, side=(32, 1024), kk=(64, 8192),

@@ -25,7 +25,8 @@ PRECISIONS = {"fp64": VUP_FP64, "fp32": VUP_FP32, "bf16x3": VUP_BF16X3}
 # exported symbols declared in include/vup.h
 ABI_SYMBOLS = [
     "vup_grid_create", "vup_grid_destroy", "vup_eval_model", "vup_set_outputs", "vup_propagate",
-    "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_batched_report", "vup_sync", "vup_selftest_wait",
+    "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_batched_report", "vup_sync", "vup_selftest_wait", "vup_model_at",
+    "vup_deviation_moments", "vup_ipsa_matrix", "vup_sa_fields",
     "vup_grid_info", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
     "vup_profile_read",
 ]
@@ -72,6 +73,10 @@ def lib():
         l.vup_batched_report.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
         l.vup_sync.argtypes = [vp, vp]
         l.vup_selftest_wait.argtypes = [vp, C.c_uint32, vp]
+        l.vup_model_at.argtypes = [vp, i64, vp, vp, vp]
+        l.vup_deviation_moments.argtypes = [vp, i64, vp, vp, vp, vp]
+        l.vup_ipsa_matrix.argtypes = [vp, i64, vp, vp, C.c_int, C.c_double, C.c_double, vp, vp]
+        l.vup_sa_fields.argtypes = [i64, C.c_int, vp, C.c_double, vp, vp, vp, vp, vp]
         l.vup_grid_info.argtypes = [vp, C.POINTER(vup_grid_info_t)]
         l.vup_grid_copy.argtypes = [vp, C.c_int, vp, C.c_size_t, vp]
         l.vup_profile.argtypes = [C.c_int]
@@ -220,6 +225,25 @@ def propagate_batched(grids, dev_dens_list, precision="bf16x3", moments=True, hi
 
 def vup_selftest_wait(h, polls, stream=None):
     _check(lib().vup_selftest_wait(h, int(polls), _stream(stream)), "vup_selftest_wait")
+
+
+def vup_model_at(h, x, y, stream=None):
+    _check(lib().vup_model_at(h, int(x.shape[0]), _ptr(x), _ptr(y), _stream(stream)), "vup_model_at")
+
+
+def vup_deviation_moments(h, moments_raw, y_ref, out, stream=None):
+    _check(lib().vup_deviation_moments(h, int(moments_raw.shape[0]), _ptr(moments_raw), _ptr(y_ref), _ptr(out),
+                                       _stream(stream)), "vup_deviation_moments")
+
+
+def vup_ipsa_matrix(h, hist, y_ref, n_dbins, dlo, dhi, out, stream=None):
+    _check(lib().vup_ipsa_matrix(h, int(hist.shape[0]), _ptr(hist), _ptr(y_ref), int(n_dbins), float(dlo),
+                                 float(dhi), _ptr(out), _stream(stream)), "vup_ipsa_matrix")
+
+
+def vup_sa_fields(hist, level, rho=None, argmax=None, ci=None, global_=None, stream=None):
+    _check(lib().vup_sa_fields(int(hist.shape[0]), int(hist.shape[1]), _ptr(hist), float(level), _ptr(rho),
+                               _ptr(argmax), _ptr(ci), _ptr(global_), _stream(stream)), "vup_sa_fields")
 
 
 def vup_sync(h, stream=None):

@@ -107,10 +107,12 @@ def test_sa_fields_against_numpy():
     for level in (0.5, 0.9, 0.99):
         am, ci, g = O.sa_fields(H, level, rho)
         np.testing.assert_array_equal(am, np.argmax(H, axis=1))
-        cum = np.cumsum(H, axis=1)
+        # FP32 sequential sums (the probabilities' own precision)
+        Hf = H.astype(np.float32)
+        cum = np.cumsum(Hf, axis=1, dtype=np.float32)
         tot = cum[:, -1:]
-        lo = np.argmax(cum > 0.5 * (1 - level) * tot, axis=1)
-        hi = np.argmax(cum >= 0.5 * (1 + level) * tot, axis=1)
+        lo = np.argmax(cum > np.float32(0.5 * (1 - level)) * tot, axis=1)
+        hi = np.argmax(cum >= np.float32(0.5 * (1 + level)) * tot, axis=1)
         np.testing.assert_array_equal(ci[:, 0], lo)
         np.testing.assert_array_equal(ci[:, 1], hi)
         np.testing.assert_allclose(g, rho @ H / rho.sum(), rtol=1e-13)
