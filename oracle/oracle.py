@@ -69,6 +69,9 @@ def lib():
             l.oracle_ipsa_matrix.restype = None
             l.oracle_ipsa_matrix.argtypes = [C.c_int64, C.c_int, C.c_double, C.c_double, dp, dp, C.c_int,
                                              C.c_double, C.c_double, dp]
+            l.oracle_posterior_means.restype = C.c_int
+            l.oracle_posterior_means.argtypes = ([C.c_int, ip64, dp, dp, ip32, C.c_int, C.c_int64, ip64] + dens
+                                                 + [dp])
             l.oracle_sa_fields.restype = None
             l.oracle_sa_fields.argtypes = [C.c_int64, C.c_int, dp, C.c_double, dp, ip32, ip32, dp]
             _lib = l
@@ -245,3 +248,22 @@ def sa_fields(H, level, rho=None):
     lib().oracle_sa_fields(K, nb, _p(H, C.c_double), float(level), None if r is None else _p(r, C.c_double),
                            _p(am, C.c_int32), _p(ci, C.c_int32), _p(g, C.c_double))
     return am, ci, g
+
+
+def posterior_means(n, lo, hi, bin_ids, B, dens, rows=None):
+    """Bayes-inverted model matrix applied to the coordinates (Sec. 3):
+    E[x_d | y in bin b, l_k], shape [S][B][ndim] (0 for empty bins)."""
+    K = dens.K
+    rows = np.arange(K, dtype=np.int64) if rows is None else np.asarray(rows, np.int64)
+    nd = len(n)
+    out = np.empty((rows.size, B, nd))
+    n64 = np.asarray(n, np.int64)
+    b32 = np.ascontiguousarray(bin_ids, np.int32)
+    lo64, hi64 = _f64(lo), _f64(hi)
+    dargs, keep = _dens_args(dens)
+    rc = lib().oracle_posterior_means(nd, _p(n64, C.c_int64), _p(lo64, C.c_double), _p(hi64, C.c_double),
+                                      _p(b32, C.c_int32), int(B), rows.size, _p(rows, C.c_int64), *dargs,
+                                      _p(out, C.c_double))
+    if rc:
+        raise OracleError("a selected distribution has an empty support on the grid")
+    return out

@@ -542,3 +542,53 @@ void oracle_sa_fields(int64_t K, int nb, const double *H, double level, const do
     if (rsum > 0.0)
         for (int b = 0; b < nb; ++b) global[b] = global[b] / rsum;
 }
+
+/*
+ * Bayes-inverted model matrix applied to the input coordinates (Sec. 3, the
+ * inverted model matrix M_{(x,a),y} built from Bayes' theorem): for row k
+ * and output bin b, the posterior p(x_i | y in b, l_k) = W[k,i] [bin_i = b]
+ * / H[k,b], and its mean per input axis,
+ *   post[s][b][d] = sum_{i in b} W[k,i] x_{d,i} / H[k,b]
+ * (0 for a bin of zero probability).  Also the identity of the footnote on
+ * the inverted matrix, in its first-moment form: sum_b H[k,b] post[b][d]
+ * equals the input mean sum_i W[k,i] x_{d,i}.
+ */
+int oracle_posterior_means(int ndim, const int64_t *n, const double *lo, const double *hi, const int32_t *bins,
+                           int B, int64_t S, const int64_t *rows, int64_t K, const uint8_t *kind, const double *mu,
+                           const double *sigma, const double *tlo, const double *thi, double *post)
+{
+    oracle_dens D = {ndim, n, lo, hi, K, kind, mu, sigma, tlo, thi};
+    int64_t N = 1;
+    for (int d = 0; d < ndim; ++d) N *= n[d];
+    double *W = (double *)malloc(sizeof(double) * N);
+    double *h = (double *)malloc(sizeof(double) * B);
+    if (!W || !h) {
+        free(W);
+        free(h);
+        return 2;
+    }
+    int status = 0;
+    for (int64_t s = 0; s < S; ++s) {
+        int64_t k = rows[s];
+        double *o = post + s * (int64_t)B * ndim;
+        if (weights(&D, k, N, W) <= 0.0) {
+            status = 1;
+            continue;
+        }
+        for (int b = 0; b < B; ++b) h[b] = 0.0;
+        for (int64_t e = 0; e < (int64_t)B * ndim; ++e) o[e] = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            int64_t a[3];
+            unflatten(ndim, n, i, a);
+            h[bins[i]] += W[i];
+            for (int d = 0; d < ndim; ++d)
+                o[(int64_t)bins[i] * ndim + d] += W[i] * oracle_grid_coord(lo[d], hi[d], n[d], a[d]);
+        }
+        for (int b = 0; b < B; ++b)
+            for (int d = 0; d < ndim; ++d)
+                o[(int64_t)b * ndim + d] = h[b] > 0.0 ? o[(int64_t)b * ndim + d] / h[b] : 0.0;
+    }
+    free(W);
+    free(h);
+    return status;
+}

@@ -119,3 +119,54 @@ def test_sa_fields_against_numpy():
     _, ci, g = O.sa_fields(H, 0.9)
     np.testing.assert_allclose(g, H.mean(axis=0), rtol=1e-13)
     assert tuple(ci[3]) == (10, 10)
+
+
+# ------------------------------------------------------ Bayes-inverted matrix
+def test_posterior_means_identity_and_monotone_model():
+    """sum_b H[b] E[x | b] = E[x] (law of total expectation, exact in the
+    discrete setting); for the monotone y = x every posterior mean lies
+    inside its bin's x-range."""
+    n, lo, hi = (2000,), (-3.0,), (3.0,)
+    y = O.eval_model(I.MODEL_POLY, (0.0, 1.0, 0.0), n, lo, hi)
+    B = 37
+    b, ymin, ymax = O.bins(y, B)
+    dens = gauss([[0.4], [-1.0]], [[0.5], [0.8]])
+    post = O.posterior_means(n, lo, hi, b, B, dens)
+    H = O.propagate(n, lo, hi, y, b, B, 1, dens)["hist"]
+    x = O.grid_coords(n, lo, hi)[0]
+    for k in range(2):
+        W, _ = O.weights(n, lo, hi, dens, k)
+        assert H[k] @ post[k, :, 0] == pytest.approx(W @ x, rel=1e-12, abs=1e-13)
+        w = (ymax - ymin) / B
+        for bb in np.nonzero(H[k] > 0)[0]:
+            assert ymin + bb * w - 1e-12 <= post[k, bb, 0] <= ymin + (bb + 1) * w + 1e-12
+    assert np.all(post[0, H[0] == 0, :] == 0)
+
+
+def test_posterior_means_symmetric_square_model():
+    """y = x^2 under a Gaussian centred at 0 on a symmetric grid: the two
+    preimages +-sqrt(y) carry equal weight, so every posterior mean of x is 0."""
+    n, lo, hi = (1000,), (-2.0,), (2.0,)
+    y = O.eval_model(I.MODEL_POLY, (0.0, 0.0, 1.0), n, lo, hi)
+    b, _, _ = O.bins(y, 25)
+    post = O.posterior_means(n, lo, hi, b, 25, gauss([[0.0]], [[0.6]]))
+    assert np.abs(post).max() < 1e-12
+
+
+def test_posterior_means_2d_identity_against_direct_sums():
+    prob = I.config("c2", "small")
+    prob.dens = prob.dens.take(range(6))
+    res = O.solve(prob)
+    post = O.posterior_means(prob.n, prob.lo, prob.hi, res["bins"], prob.n_bins, prob.dens)
+    xs = O.grid_coords(prob.n, prob.lo, prob.hi)
+    X0 = np.repeat(xs[0], prob.n[1])
+    X1 = np.tile(xs[1], prob.n[0])
+    for k in range(6):
+        W, _ = O.weights(prob.n, prob.lo, prob.hi, prob.dens, k)
+        for d, X in enumerate((X0, X1)):
+            assert res["hist"][k] @ post[k, :, d] == pytest.approx(W @ X, rel=1e-11, abs=1e-12)
+            # direct per-bin sums by numpy
+            num = np.bincount(res["bins"], weights=W * X, minlength=prob.n_bins)
+            den = np.bincount(res["bins"], weights=W, minlength=prob.n_bins)
+            expect = np.where(den > 0, num / np.where(den > 0, den, 1), 0.0)
+            np.testing.assert_allclose(post[k, :, d], expect, rtol=1e-11, atol=1e-13)
