@@ -299,6 +299,21 @@ vup_status vup_sa_fields(int64_t K, int n_bins, const float *hist, double level,
                          int32_t *argmax, int32_t *ci, double *global, vup_stream_t stream);
 
 /*
+ * Bayes-inverted model matrix applied to the inputs (Sec. 3: the inverted
+ * model matrix maps an output bin back to the input points that reach it,
+ * each with posterior probability W[k,i] / H[k,b] by Bayes' theorem): the
+ * posterior mean of every input axis per output bin,
+ *   post[k][b][d] = sum_{i in bin b} W[k,i] x_{d,i} / H[k,b]  (0 where H = 0),
+ * from FP32 segmented sums: one histogram pass for H and one per axis with
+ * that axis' factors weighted by its coordinates (W is never formed).
+ *   hist [K][B] float (device, or NULL): receives H as well;
+ *   post [K][B][ndim] float (device).
+ * ndim >= 2 (VUP_ERR_UNSUPPORTED for 1-D grids).  The first call with a
+ * larger K than before allocates library scratch.
+ */
+vup_status vup_posterior_means(vup_grid g, const vup_densities *d, float *hist, float *post, vup_stream_t stream);
+
+/*
  * What the calling thread's most recent vup_propagate_batched did:
  *   bn_cap  : tile-width cap of the contraction (256 / 128 / 64; 0 for FP32)
  *   source  : 0 replayed a remembered graph, 1 built a graph with a remembered

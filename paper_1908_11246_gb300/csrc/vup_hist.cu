@@ -565,13 +565,15 @@ int vup_hist_parts_for(int64_t n_last, int n_bins) {
 
 // Arguments of the histogram kernels for one grid; `rows` receives the
 // largest shared-memory tile (rows of one part of a gathered axis).
-static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows, int &P_max) {
+static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows, int &P_max,
+                              const float *ftab = nullptr) {
     const int64_t K_pad = ceil_div64(K, 128) * 128;
     const int nd = g->ndim;
+    const float *ft = ftab ? ftab : (const float *)g->ftab.p;
     auto tab = [&](int axis) {
         int64_t off = 0;
         for (int q = 0; q < axis; ++q) off += g->n[q] * K_pad;
-        return (const float *)g->ftab.p + off;
+        return ft + off;
     };
     HistArgs A{};
     rows = 0;
@@ -618,11 +620,11 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
     return A;
 }
 
-vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s) {
+vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab) {
     const int nd = g->ndim;
     int64_t rows;
     int P_max;
-    const HistArgs A = hist_args_for(g, K, hist, rows, P_max);
+    const HistArgs A = hist_args_for(g, K, hist, rows, P_max, ftab);
     const size_t smem = hist_smem_bytes(rows);
     // run-end words encode the rest index in 21 bits (3-D: a0 < 512, a1 < 4096)
     const bool coded = nd == 2 || (g->n[0] <= 512 && g->n[1] <= 4096);

@@ -155,7 +155,9 @@ vup_status vup_moments_simt(vup_grid g, int64_t K, int orient, int n_out, float 
 vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s);
 vup_status vup_moments_finish(vup_grid g, int64_t K, int n_col_tiles, double *raw,
                               double *central, cudaStream_t s);
-vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s);
+// Segmented histogram of the K densities; `ftab` replaces the grid's factor
+// tables when not null (same layout), e.g. tables weighted by a coordinate.
+vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab = nullptr);
 vup_status vup_propagate_1d(vup_grid g, const vup_densities *d, double *raw, double *central,
                             float *hist, cudaStream_t s);
 vup_status vup_ipsa_1d(vup_grid g, const vup_densities *d, const double *grad, float *dmu,

@@ -26,7 +26,7 @@ PRECISIONS = {"fp64": VUP_FP64, "fp32": VUP_FP32, "bf16x3": VUP_BF16X3}
 ABI_SYMBOLS = [
     "vup_grid_create", "vup_grid_destroy", "vup_eval_model", "vup_set_outputs", "vup_propagate",
     "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_batched_report", "vup_sync", "vup_selftest_wait", "vup_model_at",
-    "vup_deviation_moments", "vup_ipsa_matrix", "vup_sa_fields",
+    "vup_deviation_moments", "vup_ipsa_matrix", "vup_sa_fields", "vup_posterior_means",
     "vup_grid_info", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
     "vup_profile_read",
 ]
@@ -77,6 +77,7 @@ def lib():
         l.vup_deviation_moments.argtypes = [vp, i64, vp, vp, vp, vp]
         l.vup_ipsa_matrix.argtypes = [vp, i64, vp, vp, C.c_int, C.c_double, C.c_double, vp, vp]
         l.vup_sa_fields.argtypes = [i64, C.c_int, vp, C.c_double, vp, vp, vp, vp, vp]
+        l.vup_posterior_means.argtypes = [vp, C.POINTER(vup_densities), vp, vp, vp]
         l.vup_grid_info.argtypes = [vp, C.POINTER(vup_grid_info_t)]
         l.vup_grid_copy.argtypes = [vp, C.c_int, vp, C.c_size_t, vp]
         l.vup_profile.argtypes = [C.c_int]
@@ -244,6 +245,11 @@ def vup_ipsa_matrix(h, hist, y_ref, n_dbins, dlo, dhi, out, stream=None):
 def vup_sa_fields(hist, level, rho=None, argmax=None, ci=None, global_=None, stream=None):
     _check(lib().vup_sa_fields(int(hist.shape[0]), int(hist.shape[1]), _ptr(hist), float(level), _ptr(rho),
                                _ptr(argmax), _ptr(ci), _ptr(global_), _stream(stream)), "vup_sa_fields")
+
+
+def vup_posterior_means(h, dens, hist, post, stream=None):
+    _check(lib().vup_posterior_means(h, C.byref(dens), _ptr(hist), _ptr(post), _stream(stream)),
+           "vup_posterior_means")
 
 
 def vup_sync(h, stream=None):

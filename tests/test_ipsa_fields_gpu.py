@@ -149,3 +149,50 @@ def test_sa_argument_and_state_errors():
     with pytest.raises(vup.VUPError) as e:
         vup.vup_model_at(g2.h, x, yy)
     assert e.value.status == vup.VUP_ERR_STATE
+
+
+# ------------------------------------------------------ Bayes-inverted matrix
+POST_CASES = [I.config("c2", "small"), I.ipsa_example(0.5, "small"), I.config("c3", "small"),
+              I.random_problem(231, ndim=2)]
+
+
+@pytest.mark.parametrize("prob", POST_CASES, ids=[p.name for p in POST_CASES])
+def test_posterior_means_match_oracle(prob):
+    import torch
+    vup = vupmod()
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.eval_model(prob.model_id, prob.theta, prob.n_bins, prob.n_moments)
+    dd = vup.densities_to_device(prob.dens)
+    K, B, nd = prob.K, prob.n_bins, prob.ndim
+    hist = torch.empty((K, B), dtype=torch.float32, device="cuda")
+    post = torch.empty((K, B, nd), dtype=torch.float32, device="cuda")
+    vup.vup_posterior_means(g.h, vup.make_densities(dd), hist, post)
+    g.sync()
+    res = O.solve(prob)
+    ref = O.posterior_means(prob.n, prob.lo, prob.hi, res["bins"], B, prob.dens)
+    p, h = post.cpu().numpy().astype(np.float64), hist.cpu().numpy()
+    Hp.check_hist(h, res["hist"])
+    xmax = np.array([max(abs(prob.lo[d]), abs(prob.hi[d])) for d in range(nd)])
+    live = res["hist"] > 1e-9
+    err = np.abs(p - ref)[live] / xmax
+    assert err.max() <= 2e-5, err.max()
+    # law of total expectation against the oracle's direct input means
+    xs = O.grid_coords(prob.n, prob.lo, prob.hi)
+    mesh = np.meshgrid(*xs, indexing="ij")
+    for k in range(0, K, max(1, K // 5)):
+        W, _ = O.weights(prob.n, prob.lo, prob.hi, prob.dens, k)
+        for d in range(nd):
+            assert abs(h[k] @ p[k, :, d] - W @ mesh[d].ravel()) <= 1e-5 * xmax[d]
+
+
+def test_posterior_means_reject_1d_grids():
+    vup = vupmod()
+    prob = I.config("c1", "small")
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.eval_model(prob.model_id, prob.theta, prob.n_bins, prob.n_moments)
+    import torch
+    dd = vup.densities_to_device(prob.dens)
+    post = torch.empty((prob.K, prob.n_bins, 1), dtype=torch.float32, device="cuda")
+    with pytest.raises(vup.VUPError) as e:
+        vup.vup_posterior_means(g.h, vup.make_densities(dd), None, post)
+    assert e.value.status == vup.VUP_ERR_UNSUPPORTED
