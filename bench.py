@@ -138,7 +138,7 @@ def run_reference(args):
             return len(rows) * p.N
         prob = None
     else:
-        prob = I.config("c2" if args.config == "weights" else args.config)
+        prob = I.config("c2" if args.config in ("weights", "bayes") else args.config)
         if args.k or args.config == "weights":
             prob.dens = prob.dens.take(range(min(args.k or 1024, prob.K)))
         y = O.eval_model(prob.model_id, prob.theta, prob.n, prob.lo, prob.hi)
@@ -193,11 +193,20 @@ def roofline_for(name, ms, launches, KN, pk, clk_mhz, workload):
     sms = 152
     tr = traffic_for(name, workload)
     if name.startswith("moments_bf16") or name.startswith("ipsa_bf16"):
-        fl = 24.0 if name.startswith("moments") else 72.0
+        # the IPSA launches run the same contraction once per orientation
+        fl = 24.0
         a = fl * KN / launches / per / 1e12
         return {"bound": "tensor", "achieved": a, "peak": pk["bf16_sus"], "unit": "TFLOP/s",
                 "frac": a / pk["bf16_sus"], "traffic": tr,
                 "note": f"{fl:g} tensor flops/dist-point (BF16x3, J=4) per launch; peak = sustained bf16, "
+                        f"of {pk['source']}"}
+    if name.startswith("moments_tf32"):
+        fl = 24.0 if name.startswith("moments_tf32x3") else 8.0
+        peak = pk["bf16_sus"] * 1.1 / 2.25   # TF32 dense = bf16 x (1.1 / 2.25) nominal ratio
+        a = fl * KN / launches / per / 1e12
+        return {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                "traffic": tr,
+                "note": f"{fl:g} tensor flops/dist-point (TF32, J=4); peak = sustained bf16 x 1.1/2.25, "
                         f"of {pk['source']}"}
     if name.startswith("moments_fp32") or name.startswith("ipsa_fp32"):
         fl = 8.0 if name.startswith("moments") else 24.0
@@ -227,6 +236,8 @@ WORKLOADS = {
            "(grids and model outputs built once)"),
     "weights": ("weights: supplied dense W (FP32 [K][N] in HBM), config-2 grid and model, K=1024, "
                 "4 moments + 256-bin histograms"),
+    "bayes": ("bayes: config-2 grid and model, K=16384 product Gaussians, 256 bins; the Bayes-inverted "
+              "model matrix applied to the inputs: posterior mean of both axes per output bin, with H"),
     "ipsa": ("ipsa: the Sec. 5.3 IPSA example, y = x^2 + 5 sin 3x + alpha on a 1000x1000 grid over "
              "[-5,5]x[-1.5,1.5], L=1000 locations, sigma_l=0.5, sigma_alpha=0.25, 4 moments + 1000-bin "
              "histograms, then estimated values, deviation moments, the 1000-bin IPSA probability matrix "
@@ -240,12 +251,13 @@ class SingleGrid:
 
     def __init__(self, name, k, prec, vup, torch):
         self.vup, self.torch = vup, torch
-        prob = I.config(name)
+        prob = I.config("c2" if name == "bayes" else name)
         if k:
             prob.dens = prob.dens.take(range(min(k, prob.K)))
         self.prob = prob
         self.ipsa = name == "c4"
         self.sa = name == "ipsa"
+        self.bayes = name == "bayes"
         self.prec = prec
         self.g = vup.Grid(prob.n, prob.lo, prob.hi)
         self.dev = vup.densities_to_device(prob.dens)
@@ -259,6 +271,8 @@ class SingleGrid:
             self.grad = torch.ones((K, J), dtype=torch.float64, device=dv)
             self.dmu = torch.empty((K, 2), dtype=torch.float32, device=dv)
             self.dsg = torch.empty((K, 2), dtype=torch.float32, device=dv)
+        if self.bayes:
+            self.post = torch.empty((K, B, prob.ndim), dtype=torch.float32, device=dv)
         if self.sa:
             self.g.eval_model(prob.model_id, prob.theta, B, J)
             info = self.g.info()
@@ -277,6 +291,9 @@ class SingleGrid:
     def step(self, stream):
         v, p = self.vup, self.prob
         v.vup_eval_model(self.g.h, p.model_id, p.theta, p.n_bins, p.n_moments, stream)
+        if self.bayes:
+            v.vup_posterior_means(self.g.h, self.ds, self.hist, self.post, stream)
+            return
         v.vup_propagate(self.g.h, self.ds, self.prec, self.raw, self.cen, self.hist, stream)
         if self.ipsa:
             v.vup_ipsa_sensitivity(self.g.h, self.ds, self.prec, self.dmu, self.dsg, self.grad, stream)
@@ -293,8 +310,10 @@ class SingleGrid:
         """Host buffers: inputs copied in, every output copied back, each step."""
         torch = self.torch
         host = {k: v.cpu().pin_memory() for k, v in self.dev.items()}
-        outs = [self.raw, self.cen, self.hist] + ([self.dmu, self.dsg] if self.ipsa else []) + \
-            ([self.yref, self.dev_m, self.mat, self.am, self.ci, self.glob] if self.sa else [])
+        outs = ([self.hist] if self.bayes else [self.raw, self.cen, self.hist]) + \
+            ([self.dmu, self.dsg] if self.ipsa else []) + \
+            ([self.yref, self.dev_m, self.mat, self.am, self.ci, self.glob] if self.sa else []) + \
+            ([self.post] if self.bayes else [])
         outs_h = [torch.empty_like(x, device="cpu").pin_memory() for x in outs]
         bi = sum(v.numel() * v.element_size() for v in host.values())
         bo = sum(x.numel() * x.element_size() for x in outs_h)
@@ -411,7 +430,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "tf32x3", "tf32"])
     ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--k", type=int, default=0, help="use the first K densities of the workload (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -520,7 +539,8 @@ def main():
         roof["kernel"] = dominant
     kern_roof = {k: roofline_for(k, v[1], v[0], KN, pk, clk_mhz, wl)
                  for k, v in prof.items()
-                 if k.startswith(("moments_bf16", "moments_fp32", "ipsa_bf16", "ipsa_fp32", "hist_seg", "weights"))}
+                 if k.startswith(("moments_bf16", "moments_fp32", "moments_tf32", "ipsa_bf16", "ipsa_fp32", "hist_seg",
+                                  "weights"))}
     stage = {"model_eval_bins_sort_tables": 0.0, "moments": 0.0, "histogram": 0.0, "ipsa": 0.0, "other": 0.0}
     for k, v in per_step.items():
         if k.startswith(("model_eval", "range_bins", "power_table")):
@@ -543,7 +563,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16x3" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"bf16x3": "bf16", "tf32x3": "tf32", "tf32": "tf32"}.get(args.precision, "f32"),
+        "data": "synthetic",
         "config": cfg,
         "roofline": roof,
         "kernels": {"per_step": per_step, "stage_ms_per_step": stage, "roofline": kern_roof,

@@ -70,7 +70,9 @@ typedef enum { VUP_GAUSS = 0, VUP_UNIFORM = 1, VUP_TRUNCNORM = 2 } vup_density_k
 typedef enum {
     VUP_FP64 = 0,   /* 1-D grids only: every step in double precision            */
     VUP_FP32 = 1,   /* plain FP32 CUDA-core contraction, FP64 final reduction     */
-    VUP_BF16X3 = 2  /* tcgen05 tensor cores, 3 split BF16 products, FP32 accumulate */
+    VUP_BF16X3 = 2, /* tcgen05 tensor cores, 3 split BF16 products, FP32 accumulate */
+    VUP_TF32 = 3,   /* tcgen05 tensor cores, one TF32 product (~1e-3: comparison only) */
+    VUP_TF32X3 = 4  /* tcgen05 tensor cores, 3 split TF32 products, FP32 accumulate */
 } vup_precision;
 
 /* Built-in models (model_id of vup_eval_model).  theta is a host array. */
@@ -151,11 +153,12 @@ vup_status vup_set_outputs(vup_grid g, const double *y_dev, int n_bins, int n_mo
  *   moments_central [K][J] double, device, or NULL
  *   hist            [K][B] float,  device, or NULL   (Eq. 4 output probabilities)
  * J and B are the values given to vup_eval_model.  precision selects the
- * contraction: VUP_FP64 requires ndim == 1; 1-D grids run in FP64 whatever
- * is requested; VUP_BF16X3 needs ndim >= 2.  W[k, i] is generated on the
- * fly and never stored.  The first call with a larger K than before
- * allocates per-K scratch (not capturable in a CUDA graph); later calls with
- * K no larger allocate nothing.
+ * contraction: VUP_FP64 requires ndim == 1; 1-D grids run in FP64 when
+ * VUP_FP64 or VUP_FP32 is requested; the tensor-core kinds (VUP_BF16X3,
+ * VUP_TF32, VUP_TF32X3) need ndim >= 2.  W[k, i] is generated on the fly
+ * and never stored.  The first call with a larger K than before allocates
+ * per-K scratch (not capturable in a CUDA graph), and the first TF32 call on
+ * a grid builds its TF32 power tables; later calls allocate nothing.
  */
 vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_precision precision,
                          double *moments_raw, double *moments_central, float *hist,
@@ -202,7 +205,8 @@ vup_status vup_propagate_weights_noalloc(vup_grid g, int64_t K, const float *W, 
  *   grad_moments [K][J] double (device): vector-Jacobian product,
  *                        dmu/dsigma are [K][ndim] float,
  *                        dmu[k][d] = sum_j grad[k][j] dM_j/dmu_{k,d}
- * precision: VUP_FP32 or VUP_BF16X3 (VUP_FP64 for ndim == 1).
+ * precision: VUP_FP32 or VUP_BF16X3 (VUP_FP64 for ndim == 1; the TF32 kinds
+ * return VUP_ERR_UNSUPPORTED).
  */
 vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, vup_precision precision,
                                 const double *grad_moments, float *dmu, float *dsigma,
@@ -218,7 +222,8 @@ vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, vup_precisio
  *       ([K_i][J_i] double) and hist[i] ([K_i][B_i] float) are device
  *       pointers or NULL, laid out as in vup_propagate; moments_raw or hist
  *       may itself be NULL (no instance wants that output).
- *   precision : VUP_FP32 or VUP_BF16X3 (VUP_FP64: VUP_ERR_UNSUPPORTED).
+ *   precision : VUP_FP32 or VUP_BF16X3 (VUP_FP64 and the TF32 kinds:
+ *       VUP_ERR_UNSUPPORTED).
  * Every grid must be 2-D with a model (VUP_ERR_STATE otherwise) and each
  * gathered-axis part of its histogram layout must fit one shared-memory tile
  * (704 rows; VUP_ERR_UNSUPPORTED otherwise).

@@ -183,6 +183,8 @@ static void free_grid(vup_grid g) {
     cudaFree(g->ydev_scale);
     cudaFree(g->dstatus);
     for (int o = 0; o < kNumOrient; ++o) {
+        cudaFree(g->ztf_hi[o]);
+        cudaFree(g->ztf_lo[o]);
         cudaFree(g->zs[o]);
         cudaFree(g->zt_hi[o]);
         cudaFree(g->zt_lo[o]);
@@ -199,6 +201,8 @@ static void free_grid(vup_grid g) {
     devbuf_free(g->hist_part);
     devbuf_free(g->hist_direct);
     devbuf_free(g->ipsa_part);
+    devbuf_free(g->atf_hi);
+    devbuf_free(g->atf_lo);
     delete g;
 }
 
@@ -381,7 +385,7 @@ vup_status vup_check_dens(vup_grid g, const vup_densities *d) {
 }
 
 // Per-K scratch: density constants, factor tables, split A tables, partials.
-vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa) {
+vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa, bool tf32) {
     const int64_t K_pad = ceil_div64(K, 128) * 128;
     const int nd = g->ndim;
     vup_status st;
@@ -396,6 +400,11 @@ vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa) {
         if (g->hist_P > 1 &&
             (st = devbuf_reserve(g->hist_direct, sizeof(float) * (size_t)g->hist_P * K * g->B)) != VUP_OK)
             return st;
+        if (tf32) {
+            const size_t a = (size_t)K_pad * g->orient[vup_tc_orient(g)].R_pad;
+            if ((st = devbuf_reserve(g->atf_hi, sizeof(float) * a)) != VUP_OK) return st;
+            if ((st = devbuf_reserve(g->atf_lo, sizeof(float) * a)) != VUP_OK) return st;
+        }
         if (bf16) {
             size_t a = (size_t)K_pad * g->orient[vup_tc_orient(g)].R_pad +
                        (ipsa ? (size_t)K_pad * g->orient[1].R_pad : 0);
@@ -419,24 +428,28 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
     if (!g) return VUP_ERR_INVALID_ARG;
     vup_status st = vup_check_dens(g, d);
     if (st != VUP_OK) return st;
-    if (precision != VUP_FP64 && precision != VUP_FP32 && precision != VUP_BF16X3) return VUP_ERR_INVALID_ARG;
+    if (precision < VUP_FP64 || precision > VUP_TF32X3) return VUP_ERR_INVALID_ARG;
     if (!g->have_model) return VUP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t K = d->K;
     if (g->ndim == 1) {
-        if (precision == VUP_BF16X3) return VUP_ERR_UNSUPPORTED;
+        if (precision != VUP_FP64 && precision != VUP_FP32) return VUP_ERR_UNSUPPORTED;
         return vup_propagate_1d(g, d, moments_raw, moments_central, hist, s);
     }
     if (precision == VUP_FP64) return VUP_ERR_UNSUPPORTED;
     const bool bf16 = precision == VUP_BF16X3;
+    const bool tf32 = precision == VUP_TF32 || precision == VUP_TF32X3;
     const bool want_m = moments_raw || moments_central;
-    if ((st = vup_reserve_k(g, K, bf16, false)) != VUP_OK) return st;
+    if ((st = vup_reserve_k(g, K, bf16, false, tf32)) != VUP_OK) return st;
     const int to = vup_tc_orient(g);
-    if ((st = vup_density_prep(g, d, (bf16 && want_m) ? (1 << to) : 0, s)) != VUP_OK) return st;
+    if (tf32 && want_m && (st = vup_build_tables(g, to, 2, s)) != VUP_OK) return st;
+    if ((st = vup_density_prep(g, d, ((bf16 || tf32) && want_m) ? (1 << to) : 0, s, tf32)) != VUP_OK) return st;
     if (want_m) {
         int64_t nct;
-        if (bf16) {
-            if ((st = vup_moments_tc(g, K, to, 1, (float *)g->partials.p, s)) != VUP_OK) return st;
+        if (bf16 || tf32) {
+            if ((st = vup_moments_tc(g, K, to, 1, (float *)g->partials.p, s, tf32 ? 1 : 0,
+                                     precision == VUP_TF32 ? 1 : 3)) != VUP_OK)
+                return st;
             nct = vup_tc_col_tiles(g->orient[to]);
         } else {
             if ((st = vup_moments_simt(g, K, 0, 1, (float *)g->partials.p, s)) != VUP_OK) return st;
@@ -463,7 +476,8 @@ extern "C" vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, v
     if (!g || !dmu || !dsigma) return VUP_ERR_INVALID_ARG;
     vup_status st = vup_check_dens(g, d);
     if (st != VUP_OK) return st;
-    if (precision != VUP_FP64 && precision != VUP_FP32 && precision != VUP_BF16X3) return VUP_ERR_INVALID_ARG;
+    if (precision < VUP_FP64 || precision > VUP_TF32X3) return VUP_ERR_INVALID_ARG;
+    if (precision == VUP_TF32 || precision == VUP_TF32X3) return VUP_ERR_UNSUPPORTED;
     if (!g->have_model) return VUP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     if (g->ndim == 1) {

@@ -210,9 +210,8 @@ extern "C" vup_status vup_propagate_batched(int n_inst, const vup_grid *g, const
                                             vup_precision precision, double *const *moments_raw,
                                             float *const *hist, vup_stream_t stream) {
     if (n_inst < 0 || (n_inst > 0 && (!g || !d))) return VUP_ERR_INVALID_ARG;
-    if (precision != VUP_FP32 && precision != VUP_BF16X3) {
-        return precision == VUP_FP64 ? VUP_ERR_UNSUPPORTED : VUP_ERR_INVALID_ARG;
-    }
+    if (precision < VUP_FP64 || precision > VUP_TF32X3) return VUP_ERR_INVALID_ARG;
+    if (precision != VUP_FP32 && precision != VUP_BF16X3) return VUP_ERR_UNSUPPORTED;
     if (n_inst == 0) return VUP_OK;
     const bool bf16 = precision == VUP_BF16X3;
     for (int i = 0; i < n_inst; ++i) {

@@ -202,9 +202,28 @@ __device__ __forceinline__ void density_finish_body(const DensJob &J, int64_t kb
 // A-operand table of the tensor-core contraction: rows k, reduction index a
 // contiguous (K-major), each FP32 factor split into BF16 hi + lo.  Block
 // (bx, by) transposes the 32 x 32 tile at a = 32 bx, k = 32 by.
+// Split of one FP32 value into hi + lo: BF16 pair (tensor kind::f16) or
+// TF32 pair stored in floats (kind::tf32).
+__device__ __forceinline__ void split_store(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t i, float v) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ void split_store(float *hi, float *lo, int64_t i, float v) {
+    const float h = to_tf32(v);
+    hi[i] = h;
+    lo[i] = to_tf32(v - h);
+}
+
+template <typename T>
 __device__ __forceinline__ void split_transpose_body(const float *__restrict__ tab, int64_t nd, int64_t K_pad,
-                                                     int64_t R_pad, __nv_bfloat16 *__restrict__ hi,
-                                                     __nv_bfloat16 *__restrict__ lo, int64_t bx, int64_t by) {
+                                                     int64_t R_pad, T *__restrict__ hi, T *__restrict__ lo,
+                                                     int64_t bx, int64_t by) {
     __shared__ float t[32][33];
     const int64_t a0 = bx * 32, k0 = by * 32;
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
@@ -214,13 +233,7 @@ __device__ __forceinline__ void split_transpose_body(const float *__restrict__ t
     __syncthreads();
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
         int64_t k = k0 + y, a = a0 + threadIdx.x;
-        if (k < K_pad && a < R_pad) {
-            float v = t[threadIdx.x][y];
-            __nv_bfloat16 h = __float2bfloat16_rn(v);
-            float rem = v - __bfloat162float(h);
-            hi[k * R_pad + a] = h;
-            lo[k * R_pad + a] = __float2bfloat16_rn(rem);
-        }
+        if (k < K_pad && a < R_pad) split_store(hi, lo, k * R_pad + a, t[threadIdx.x][y]);
     }
     __syncthreads();
 }
@@ -231,9 +244,9 @@ __device__ __forceinline__ void split_transpose_body(const float *__restrict__ t
 // ([K_pad][R_pad], r contiguous).  A 32 (r) x 32 (k) tile goes through shared
 // memory so that the factor reads (k contiguous) and the table writes (r
 // contiguous) are both coalesced.
+template <typename T>
 __global__ void k_split_product(const float *__restrict__ w1, const float *__restrict__ w2, int64_t n2,
-                                int64_t R, int64_t K_pad, int64_t R_pad, __nv_bfloat16 *__restrict__ hi,
-                                __nv_bfloat16 *__restrict__ lo) {
+                                int64_t R, int64_t K_pad, int64_t R_pad, T *__restrict__ hi, T *__restrict__ lo) {
     __shared__ float t[32][33];
     const int64_t r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;  // x: density tiles, y: reduction tiles
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
@@ -248,23 +261,18 @@ __global__ void k_split_product(const float *__restrict__ w1, const float *__res
     __syncthreads();
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
         const int64_t k = k0 + y, r = r0 + threadIdx.x;
-        if (k < K_pad && r < R_pad) {
-            const float v = t[threadIdx.x][y];
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            hi[k * R_pad + r] = h;
-            lo[k * R_pad + r] = __float2bfloat16_rn(v - __bfloat162float(h));
-        }
+        if (k < K_pad && r < R_pad) split_store(hi, lo, k * R_pad + r, t[threadIdx.x][y]);
     }
 }
 
 // Same table, one CTA per 32 densities when both axes' factors fit in shared
 // memory: the factors are staged once ([32][n + 1] per axis) and each warp
-// writes whole rows, two r per lane per step (128-byte coalesced stores).
+// writes whole rows, two consecutive r per lane per step (coalesced stores).
+template <typename T>
 __global__ void __launch_bounds__(256) k_split_product_rows(const float *__restrict__ w1,
                                                             const float *__restrict__ w2, int64_t n1, int64_t n2,
                                                             int64_t R, int64_t K_pad, int64_t R_pad,
-                                                            __nv_bfloat16 *__restrict__ hi,
-                                                            __nv_bfloat16 *__restrict__ lo) {
+                                                            T *__restrict__ hi, T *__restrict__ lo) {
     extern __shared__ float sh[];
     const int64_t l1 = n1 + 1, l2 = n2 + 1;
     float *s1 = sh, *s2 = sh + 32 * l1;
@@ -281,8 +289,8 @@ __global__ void __launch_bounds__(256) k_split_product_rows(const float *__restr
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int kk = warp; kk < 32; kk += blockDim.x >> 5) {
         const float *f1 = s1 + kk * l1, *f2 = s2 + kk * l2;
-        uint32_t *oh = reinterpret_cast<uint32_t *>(hi + (k0 + kk) * R_pad);
-        uint32_t *ol = reinterpret_cast<uint32_t *>(lo + (k0 + kk) * R_pad);
+        T *oh = hi + (k0 + kk) * R_pad;
+        T *ol = lo + (k0 + kk) * R_pad;
         int64_t r = 2 * lane;
         int64_t a1 = r / n2, a2 = r - a1 * n2;
         for (; r < R_pad; r += 64) {
@@ -296,11 +304,8 @@ __global__ void __launch_bounds__(256) k_split_product_rows(const float *__restr
                 }
                 v[e] = r + e < R ? f1[b1] * f2[b2] : 0.f;
             }
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]), h1 = __float2bfloat16_rn(v[1]);
-            const __nv_bfloat16 g0 = __float2bfloat16_rn(v[0] - __bfloat162float(h0));
-            const __nv_bfloat16 g1 = __float2bfloat16_rn(v[1] - __bfloat162float(h1));
-            oh[r >> 1] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            ol[r >> 1] = (uint32_t)__bfloat16_as_ushort(g0) | ((uint32_t)__bfloat16_as_ushort(g1) << 16);
+            split_store(oh, ol, r, v[0]);
+            split_store(oh, ol, r + 1, v[1]);
             a2 += 64;
             while (a2 >= n2) {
                 a2 -= n2;
@@ -313,9 +318,10 @@ __global__ void __launch_bounds__(256) k_split_product_rows(const float *__restr
 __global__ void k_density_prep(DensJob J) { density_prep_body(J, blockIdx.x, blockIdx.y, blockIdx.z); }
 __global__ void k_density_finish(DensJob J) { density_finish_body(J, blockIdx.x, blockIdx.y); }
 // grid: x = density tiles of 32 (K_pad / 32 may exceed the 65535 limit of y), y = axis tiles
+template <typename T>
 __global__ void k_split_transpose(const float *__restrict__ tab, int64_t nd, int64_t K_pad, int64_t R_pad,
-                                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
-    split_transpose_body(tab, nd, K_pad, R_pad, hi, lo, blockIdx.y, blockIdx.x);
+                                  T *__restrict__ hi, T *__restrict__ lo) {
+    split_transpose_body<T>(tab, nd, K_pad, R_pad, hi, lo, blockIdx.y, blockIdx.x);
 }
 
 // Batched forms: one launch for the blocks of every instance; items[b] =
@@ -331,7 +337,7 @@ __global__ void k_density_finish_batched(const DensJob *__restrict__ jobs, const
 __global__ void k_split_transpose_batched(const DensJob *__restrict__ jobs, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
     const DensJob &J = jobs[it.x];
-    split_transpose_body(J.red_tab, J.nd_red, J.K_pad, J.R_pad, J.ahi, J.alo, it.y, it.z);
+    split_transpose_body<__nv_bfloat16>(J.red_tab, J.nd_red, J.K_pad, J.R_pad, J.ahi, J.alo, it.y, it.z);
 }
 
 int density_segments(vup_grid g) {
@@ -383,7 +389,11 @@ vup_status vup_density_reserve(vup_grid g, int64_t K) {
 
 // need_bf16_orient_mask: bit o set -> build the split BF16 A table for the
 // reduction axis of orientation o.
-vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_orient_mask, cudaStream_t s) {
+template <typename T>
+static vup_status split_tables(vup_grid g, int mask, int64_t K_pad, T *hi0, T *lo0, cudaStream_t s);
+
+vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_orient_mask, cudaStream_t s,
+                            bool tf32) {
     vup_status st = vup_density_reserve(g, d->K);
     if (st != VUP_OK) return st;
     const DensJob J = make_job(g, d);
@@ -395,32 +405,39 @@ vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_or
     dim3 fgrd((unsigned)ceil_div64(d->K, 128), (unsigned)g->ndim);
     k_density_finish<<<fgrd, 128, 0, s>>>(J);
     VUP_CHECK_LAUNCH();
-    if (need_bf16_orient_mask & (1 << kOrientGrouped)) {
+    if (tf32) return split_tables<float>(g, need_bf16_orient_mask, K_pad, (float *)g->atf_hi.p,
+                                         (float *)g->atf_lo.p, s);
+    return split_tables<__nv_bfloat16>(g, need_bf16_orient_mask, K_pad, (__nv_bfloat16 *)g->atab_hi.p,
+                                       (__nv_bfloat16 *)g->atab_lo.p, s);
+}
+
+// Split tables of the A operand for the orientations in `mask` (T: BF16 or
+// TF32-in-float), written to hi / lo.
+template <typename T>
+static vup_status split_tables(vup_grid g, int mask, int64_t K_pad, T *hi0, T *lo0, cudaStream_t s) {
+    if (mask & (1 << kOrientGrouped)) {
         const Orient &ori = g->orient[kOrientGrouped];
         const float *w1 = (const float *)g->ftab.p + g->n[0] * K_pad;
         const float *w2 = w1 + g->n[1] * K_pad;
         const size_t smem = sizeof(float) * 32 * (size_t)(g->n[1] + g->n[2] + 2);
         if (smem <= 160 * 1024) {
             VUP_CHECK_CUDA(
-                cudaFuncSetAttribute(k_split_product_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_split_product_rows<<<(unsigned)(K_pad / 32), 256, smem, s>>>(
-                w1, w2, g->n[1], g->n[2], ori.R, K_pad, ori.R_pad, (__nv_bfloat16 *)g->atab_hi.p,
-                (__nv_bfloat16 *)g->atab_lo.p);
+                cudaFuncSetAttribute(k_split_product_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_split_product_rows<T><<<(unsigned)(K_pad / 32), 256, smem, s>>>(w1, w2, g->n[1], g->n[2], ori.R,
+                                                                             K_pad, ori.R_pad, hi0, lo0);
         } else {
             dim3 tg((unsigned)ceil_div64(K_pad, 32), (unsigned)ceil_div64(ori.R_pad, 32));
-            k_split_product<<<tg, dim3(32, 8), 0, s>>>(w1, w2, g->n[2], ori.R, K_pad, ori.R_pad,
-                                                       (__nv_bfloat16 *)g->atab_hi.p, (__nv_bfloat16 *)g->atab_lo.p);
+            k_split_product<T><<<tg, dim3(32, 8), 0, s>>>(w1, w2, g->n[2], ori.R, K_pad, ori.R_pad, hi0, lo0);
         }
         VUP_CHECK_LAUNCH();
     }
     for (int o = 0; o < 2; ++o) {
-        if (!(need_bf16_orient_mask & (1 << o))) continue;
+        if (!(mask & (1 << o))) continue;
         const Orient &ori = g->orient[o];
         const int dred = ori.red_axis0;
         int64_t off = 0;
         for (int q = 0; q < dred; ++q) off += g->n[q] * K_pad;
-        __nv_bfloat16 *hi = (__nv_bfloat16 *)g->atab_hi.p;
-        __nv_bfloat16 *lo = (__nv_bfloat16 *)g->atab_lo.p;
+        T *hi = hi0, *lo = lo0;
         if (o == 1) {
             // orientation-1 tables live after the orientation-0 tables
             const size_t o0 = (size_t)K_pad * g->orient[0].R_pad;
@@ -428,8 +445,8 @@ vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_or
             lo += o0;
         }
         dim3 tg((unsigned)ceil_div64(K_pad, 32), (unsigned)ceil_div64(ori.R_pad, 32));
-        k_split_transpose<<<tg, dim3(32, 8), 0, s>>>((const float *)g->ftab.p + off, g->n[dred], K_pad, ori.R_pad,
-                                                     hi, lo);
+        k_split_transpose<T><<<tg, dim3(32, 8), 0, s>>>((const float *)g->ftab.p + off, g->n[dred], K_pad,
+                                                        ori.R_pad, hi, lo);
         VUP_CHECK_LAUNCH();
     }
     return VUP_OK;

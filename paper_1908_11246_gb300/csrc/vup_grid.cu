@@ -483,10 +483,27 @@ struct Store<__nv_bfloat16> {
     }
 };
 
-template <typename T>
+// TF32 pair: hi = v rounded to TF32 (10 explicit mantissa bits, stored in a
+// float), lo = the remainder rounded to TF32.
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+struct Tf32Pair {};
+template <>
+struct Store<Tf32Pair> {
+    static __device__ __forceinline__ void put(float *o, float *o2, int64_t idx, double v) {
+        const float h = to_tf32((float)v);
+        o[idx] = h;
+        o2[idx] = to_tf32((float)(v - (double)h));
+    }
+};
+
+template <typename T, typename O = T>
 __global__ void k_power_table(const double *__restrict__ y, int64_t P, int64_t S,
                               const double *__restrict__ sc, int mode, int64_t ld,
-                              T *__restrict__ out, T *__restrict__ out2) {
+                              O *__restrict__ out, O *__restrict__ out2) {
     __shared__ double tile[32][33];
     const int64_t p0 = (int64_t)blockIdx.y * 32, s0 = (int64_t)blockIdx.x * 32;
     const double scale = sc[0];
@@ -760,7 +777,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
         k_pick_layout<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->n_layouts > 1 ? g->hl[1].n_runs : nullptr, g->hist_sel);
         VUP_CHECK_LAUNCH();
     }
-    for (int o = 0; o < kNumOrient; ++o) g->have_tab[o][0] = g->have_tab[o][1] = 0;
+    for (int o = 0; o < kNumOrient; ++o) g->have_tab[o][0] = g->have_tab[o][1] = g->have_tab[o][2] = 0;
     return VUP_OK;
 }
 
@@ -768,6 +785,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
 // layout [R][NC]) or split BF16 (tensor layout [NC][R_pad]).
 vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
     if (g->have_tab[orient][bf16]) return VUP_OK;
+    // bf16: 0 = FP32 (SIMT layout), 1 = BF16 hi/lo, 2 = TF32 hi/lo (tensor layouts)
     const Orient &o = g->orient[orient];
     // View y as [P][S]: orientations 0 and 2 -> P = rest (Q), S = red (R)
     // (the reduction axes are the trailing ones); orientation 1 (2-D) ->
@@ -776,7 +794,7 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
     const int64_t P = first ? o.R : o.Q;
     const int64_t S = first ? o.Q : o.R;
     dim3 blk(32, 8), grd((unsigned)ceil_div64(S, 32), (unsigned)ceil_div64(P, 32));
-    VUP_PROF(bf16 ? "power_table_bf16" : "power_table_fp32", s, 1);
+    VUP_PROF(bf16 == 2 ? "power_table_tf32" : (bf16 ? "power_table_bf16" : "power_table_fp32"), s, 1);
     if (!bf16) {
         const int64_t ld = ceil_div64(o.NC, 128) * 128;
         const size_t bytes = sizeof(float) * (size_t)ld * (size_t)o.R;
@@ -784,7 +802,20 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
         VUP_CHECK_CUDA(cudaMemsetAsync(g->zs[orient], 0, bytes, s));
         // SIMT wants [r][q*4+j]: orientation 0 -> rows s (mode 1); 1 -> rows p (mode 3)
         k_power_table<float><<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, first ? 3 : 1, ld,
-                                                 g->zs[orient], nullptr);
+                                                 g->zs[orient], (float *)nullptr);
+        VUP_CHECK_LAUNCH();
+    } else if (bf16 == 2) {
+        const int64_t ld = o.R_pad;
+        const int64_t rows = ceil_div64(o.NC, 256) * 256;
+        const size_t bytes = sizeof(float) * (size_t)ld * (size_t)rows;
+        if (!g->ztf_hi[orient]) {
+            VUP_CHECK_CUDA(cudaMalloc(&g->ztf_hi[orient], bytes));
+            VUP_CHECK_CUDA(cudaMalloc(&g->ztf_lo[orient], bytes));
+        }
+        VUP_CHECK_CUDA(cudaMemsetAsync(g->ztf_hi[orient], 0, bytes, s));
+        VUP_CHECK_CUDA(cudaMemsetAsync(g->ztf_lo[orient], 0, bytes, s));
+        k_power_table<Tf32Pair, float><<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, first ? 2 : 0, ld,
+                                                          g->ztf_hi[orient], g->ztf_lo[orient]);
         VUP_CHECK_LAUNCH();
     } else {
         const int64_t ld = o.R_pad;

@@ -128,15 +128,18 @@ struct vup_grid_s {
 
     // power tables per orientation (kOrient*)
     Orient orient[kNumOrient];
-    int have_tab[kNumOrient][2] = {};               // [orient][0: fp32, 1: bf16]
+    int have_tab[kNumOrient][3] = {};               // [orient][0: fp32, 1: bf16, 2: tf32]
     float *zs[kNumOrient] = {};                      // SIMT layout [R][NC]
     __nv_bfloat16 *zt_hi[kNumOrient] = {};           // tensor layout [NC][R_pad]
     __nv_bfloat16 *zt_lo[kNumOrient] = {};
+    float *ztf_hi[kNumOrient] = {};                  // tensor layout [NC][R_pad], TF32 values
+    float *ztf_lo[kNumOrient] = {};
     double *ydev_scale = nullptr;  // [1] s on device
 
     // per-K scratch (density constants, factor tables, partials)
     int64_t K_cap = 0;
     DevBuf dconst, dstats, dpart, ftab, atab_hi, atab_lo, partials, hist_part, hist_direct, ipsa_part;
+    DevBuf atf_hi, atf_lo;         // TF32 split of the A operand [K_pad][R_pad]
 
     int *dstatus = nullptr;        // [1] device status word
 };
@@ -149,10 +152,15 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s);  // range, bins, 
 vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s);
 vup_status vup_natural_sort(vup_grid g, cudaStream_t s);
 
+// Density factors and normalisers; the A-operand split tables of the
+// orientations in the mask (BF16 into atab_*, or TF32 into atf_* when tf32).
 vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_orient_mask,
-                            cudaStream_t s);
+                            cudaStream_t s, bool tf32 = false);
 vup_status vup_moments_simt(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s);
-vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s);
+// Tensor-core contraction; kind 0 = BF16 operands, 1 = TF32 operands;
+// terms = 3 split products or 1 (hi only).
+vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s,
+                          int kind = 0, int terms = 3);
 vup_status vup_moments_finish(vup_grid g, int64_t K, int n_col_tiles, double *raw,
                               double *central, cudaStream_t s);
 // Segmented histogram of the K densities; `ftab` replaces the grid's factor
@@ -172,7 +180,7 @@ int vup_num_sms();
 inline int vup_tc_orient(const vup_grid_s *g) { return g->ndim == 3 ? kOrientGrouped : kOrientLast; }
 bool vup_profiling();
 vup_status vup_check_dens(vup_grid g, const vup_densities *d);
-vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa);
+vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa, bool tf32 = false);
 
 // Batched stages over many 2-D instances.  Each *_plan builds host-side work
 // lists and uploads them into device memory it owns (synchronous; never call

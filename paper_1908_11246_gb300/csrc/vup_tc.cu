@@ -28,7 +28,9 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int BM = 128, BN = 256, BK = 64;  // BK in BF16 elements: 128-byte rows
+constexpr int BK_TF32 = 32;                     // TF32 operands: 32 x 4 bytes per row
+constexpr int kSplitTerms = 1024;               // reduction terms per accumulator
 constexpr int STAGES = 2;
 constexpr int A_BYTES = BM * BK * 2;            // 16 KB per bf16 plane
 constexpr int B_BYTES = BN * BK * 2;            // 32 KB per bf16 plane
@@ -96,20 +98,32 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major,
-// M = 128, N = bn (a multiple of 16 up to 256).
+// Instruction descriptor: D = FP32, A and B K-major, M = 128, N = bn (a
+// multiple of 16 up to 256); operand type BF16 (kind::f16) or TF32
+// (kind::tf32).
+template <int KIND>
 __host__ __device__ constexpr uint32_t idesc_for(int bn) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | ((KIND ? 2u : 1u) << 7) | ((KIND ? 2u : 1u) << 10) | ((uint32_t)(bn >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accum) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                     uint32_t accum) {
+    if (KIND == 0)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -160,13 +174,21 @@ struct TcTile {
 // kBatched == false: one instance, tensor maps as kernel parameters, tiles
 // t -> (m, n) = (t / n_n, t % n_n).  kBatched == true: tiles come from a work
 // list over many instances and each tile's maps and epilogue parameters from
-// its instance descriptor.
-template <int NOUT, bool kBatched>
+// its instance descriptor.  KIND 0: BF16 operands (kind::f16, 64 per
+// 128-byte row); KIND 1: TF32 operands (kind::tf32, 32 per row).  terms = 3:
+// hi*hi + hi*lo + lo*hi; terms = 1: hi*hi only (the lo planes are not read).
+template <int NOUT, bool kBatched, int KIND = 0>
 __global__ void __launch_bounds__(kThreads, 1)
 k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int n_m, int n_n,
              int n_kb, int64_t K_pad, TcEpi ep, float *__restrict__ part, const TcInst *__restrict__ insts,
-             const TcTile *__restrict__ tiles, int n_tiles_batched, int *__restrict__ dstatus) {
+             const TcTile *__restrict__ tiles, int n_tiles_batched, int *__restrict__ dstatus, int terms = 3,
+             int n_split = 1) {
+    constexpr int BKE = KIND ? BK_TF32 : BK;  // operand elements per 128-byte row
+    // split reduction: n_split accumulators of at most kSplitTerms terms each
+    // (the tensor cores' FP32 accumulation error grows with the reduction
+    // length); every split writes its own partial column, summed in FP64
+    constexpr int kSplitKb = kSplitTerms / BKE;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
@@ -178,21 +200,29 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = kBatched ? n_tiles_batched : n_m * n_n;
-    // tile t -> (instance, row tile, column tile, k-blocks, tile width)
-    auto tile_at = [&](int t, int &m, int &n, int &nkb, int &bn, const TcInst *&in) {
+    const int n_tiles = kBatched ? n_tiles_batched : n_m * n_split * n_n;
+    // tile t -> (instance, row tile, column tile, k-block range [kb0, kb1),
+    // partial column, tile width)
+    auto tile_at = [&](int t, int &m, int &n, int &kb0, int &kb1, int &col, int &bn, const TcInst *&in) {
         if (kBatched) {
             const TcTile tt = tiles[t];
             in = insts + tt.inst;
             m = tt.m;
             n = tt.n;
-            nkb = in->n_kb;
+            kb0 = 0;
+            kb1 = in->n_kb;
+            col = n;
             bn = in->bn;
         } else {
             in = nullptr;
-            m = t / n_n;
-            n = t - m * n_n;
-            nkb = n_kb;
+            const int per_m = n_split * n_n;
+            m = t / per_m;
+            const int r = t - m * per_m;
+            const int sp = r / n_n;
+            n = r - sp * n_n;
+            kb0 = sp * kSplitKb;
+            kb1 = min(n_kb, kb0 + kSplitKb);
+            col = sp * n_n + n;
             bn = BN;
         }
     };
@@ -227,22 +257,24 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
             uint32_t it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                int m, n, nkb, bn;
+                int m, n, kb0, kb1, col, bn;
                 const TcInst *in;
-                tile_at(t, m, n, nkb, bn, in);
+                tile_at(t, m, n, kb0, kb1, col, bn, in);
                 const CUtensorMap *mAh = kBatched ? &in->maps[0] : &tmAh;
                 const CUtensorMap *mAl = kBatched ? &in->maps[1] : &tmAl;
                 const CUtensorMap *mBh = kBatched ? &in->maps[2] : &tmBh;
                 const CUtensorMap *mBl = kBatched ? &in->maps[3] : &tmBl;
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int s = it % STAGES;
                     if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, dstatus)) { ok = false; break; }
                     uint8_t *st = smem + s * STAGE_BYTES;
-                    mbar_expect_tx(&full[s], 2 * A_BYTES + 4 * bn * BK);
-                    tma_load_2d(st, mAh, &full[s], kb * BK, m * BM);
-                    tma_load_2d(st + A_BYTES, mAl, &full[s], kb * BK, m * BM);
-                    tma_load_2d(st + 2 * A_BYTES, mBh, &full[s], kb * BK, n * bn);
-                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, mBl, &full[s], kb * BK, n * bn);
+                    mbar_expect_tx(&full[s], (terms == 3 ? 2 : 1) * (A_BYTES + 128 * bn));
+                    tma_load_2d(st, mAh, &full[s], kb * BKE, m * BM);
+                    tma_load_2d(st + 2 * A_BYTES, mBh, &full[s], kb * BKE, n * bn);
+                    if (terms == 3) {
+                        tma_load_2d(st + A_BYTES, mAl, &full[s], kb * BKE, m * BM);
+                        tma_load_2d(st + 2 * A_BYTES + B_BYTES, mBl, &full[s], kb * BKE, n * bn);
+                    }
                 }
             }
             // drain: every issued stage must land before shared memory is released
@@ -259,15 +291,15 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
             uint32_t it = 0, tile_it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tile_it) {
-                int m_, n_, nkb, bn;
+                int m_, n_, kb0, kb1, col_, bn;
                 const TcInst *in_;
-                tile_at(t, m_, n_, nkb, bn, in_);
-                const uint32_t idesc = idesc_for(bn);
+                tile_at(t, m_, n_, kb0, kb1, col_, bn, in_);
+                const uint32_t idesc = idesc_for<KIND>(bn);
                 const int b = tile_it & 1;
                 if (!mbar_wait(&tempty[b], ((tile_it >> 1) & 1) ^ 1, abort_flag, dstatus)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dcol = tmem_base + (uint32_t)(b * BN);
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int s = it % STAGES;
                     if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, dstatus)) { ok = false; break; }
                     tc_fence_after();
@@ -276,12 +308,17 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
                     const uint32_t b_hi = a_hi + 2 * A_BYTES;
                     const uint32_t b_lo = b_hi + B_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint32_t off = kk * 32;  // 16 bf16 along K inside the swizzle atom
-                        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-                        umma_bf16(dcol, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, acc0);
-                        umma_bf16(dcol, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
-                        umma_bf16(dcol, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, 1u);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        // 32 bytes along K inside the swizzle atom: 16 BF16 or 8 TF32
+                        const uint32_t off = kk * 32;
+                        const uint32_t acc0 = (kb > kb0 || kk > 0) ? 1u : 0u;
+                        if (terms == 3) {
+                            umma<KIND>(dcol, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, acc0);
+                            umma<KIND>(dcol, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+                            umma<KIND>(dcol, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, 1u);
+                        } else {
+                            umma<KIND>(dcol, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, acc0);
+                        }
                     }
                     umma_commit(&empty[s]);
                 }
@@ -299,12 +336,12 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
         const int row = quad * 32 + lane;
         uint32_t tile_it = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tile_it) {
-            int m, n, nkb, bn;
+            int m, n, kb0, kb1, col, bn;
             const TcInst *in;
-            tile_at(t, m, n, nkb, bn, in);
+            tile_at(t, m, n, kb0, kb1, col, bn, in);
             const TcEpi &E = kBatched ? in->ep : ep;
             const int64_t Kp = kBatched ? in->K_pad : K_pad;
-            const int nn = kBatched ? in->n_n : n_n;
+            const int nn = kBatched ? in->n_n : n_split * n_n;  // partial columns
             float *const P = kBatched ? in->part : part;
             const int b = tile_it & 1;
             if (!mbar_wait(&tfull[b], (tile_it >> 1) & 1, abort_flag, dstatus)) break;
@@ -359,7 +396,7 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
             if (lane == 0) mbar_arrive(&tempty[b]);
 #pragma unroll
             for (int o = 0; o < NOUT; ++o)
-                *reinterpret_cast<float4 *>(P + (((int64_t)o * nn + n) * Kp + k) * 4) =
+                *reinterpret_cast<float4 *>(P + (((int64_t)o * nn + col) * Kp + k) * 4) =
                     make_float4(out[o][0], out[o][1], out[o][2], out[o][3]);
         }
     }
@@ -390,15 +427,17 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2-D bf16 map over a row-major [rows][ld] array, box [box_rows][64].
-bool make_map(CUtensorMap *m, const void *base, int64_t ld, int64_t rows, int box_rows) {
+// 2-D map over a row-major [rows][ld] array of BF16 (box [box_rows][64])
+// or, with f32, of TF32-in-float values (box [box_rows][32]): 128-byte rows.
+bool make_map(CUtensorMap *m, const void *base, int64_t ld, int64_t rows, int box_rows, bool f32 = false) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * (f32 ? 4 : 2))};
+    cuuint32_t box[2] = {(cuuint32_t)(f32 ? BK_TF32 : BK), (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+    CUresult r = fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void *>(base), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -406,22 +445,31 @@ bool make_map(CUtensorMap *m, const void *base, int64_t ld, int64_t rows, int bo
 
 }  // namespace
 
-int64_t vup_tc_col_tiles(const Orient &o) { return ceil_div64(o.NC, BN); }
+// Partial columns of the contraction: column tiles x reduction splits.
+static int tc_splits(const Orient &o) { return (int)ceil_div64(o.R_pad, kSplitTerms); }
+int64_t vup_tc_col_tiles(const Orient &o) { return ceil_div64(o.NC, BN) * tc_splits(o); }
 
-vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s) {
+vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s, int kind,
+                          int terms) {
     const Orient &o = g->orient[orient];
     const int64_t K_pad = ceil_div64(K, 128) * 128;
-    const int64_t nn = vup_tc_col_tiles(o);
+    const int64_t nn = ceil_div64(o.NC, BN);
+    const int n_split = tc_splits(o);
     const int64_t rows_b = ceil_div64(o.NC, 256) * 256;
-    const __nv_bfloat16 *ah = (const __nv_bfloat16 *)g->atab_hi.p, *al = (const __nv_bfloat16 *)g->atab_lo.p;
+    const bool f32 = kind == 1;
+    const size_t esz = f32 ? 4 : 2;
+    const char *ah = (const char *)(f32 ? g->atf_hi.p : g->atab_hi.p);
+    const char *al = (const char *)(f32 ? g->atf_lo.p : g->atab_lo.p);
     if (orient == 1) {
-        const size_t o0 = (size_t)K_pad * g->orient[0].R_pad;
+        const size_t o0 = (size_t)K_pad * g->orient[0].R_pad * esz;
         ah += o0;
         al += o0;
     }
+    const void *bh = f32 ? (const void *)g->ztf_hi[orient] : (const void *)g->zt_hi[orient];
+    const void *bl = f32 ? (const void *)g->ztf_lo[orient] : (const void *)g->zt_lo[orient];
     CUtensorMap mAh, mAl, mBh, mBl;
-    if (!make_map(&mAh, ah, o.R_pad, K_pad, BM) || !make_map(&mAl, al, o.R_pad, K_pad, BM) ||
-        !make_map(&mBh, g->zt_hi[orient], o.R_pad, rows_b, BN) || !make_map(&mBl, g->zt_lo[orient], o.R_pad, rows_b, BN))
+    if (!make_map(&mAh, ah, o.R_pad, K_pad, BM, f32) || !make_map(&mAl, al, o.R_pad, K_pad, BM, f32) ||
+        !make_map(&mBh, bh, o.R_pad, rows_b, BN, f32) || !make_map(&mBl, bl, o.R_pad, rows_b, BN, f32))
         return VUP_ERR_CUDA;
     TcEpi ep{};
     auto tab = [&](int axis) {
@@ -436,19 +484,29 @@ vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *p
     ep.dconst = (const DensConst *)g->dconst.p;
     ep.ndim = g->ndim;
     ep.rest_axis = o.rest_axes[0];
-    const int n_m = (int)(K_pad / BM), n_n = (int)nn, n_kb = (int)(o.R_pad / BK);
-    const int n_tiles = n_m * n_n;
+    const int n_m = (int)(K_pad / BM), n_n = (int)nn, n_kb = (int)(o.R_pad / (f32 ? BK_TF32 : BK));
+    const int n_tiles = n_m * n_split * n_n;
     const int grid = std::min(n_tiles, vup_num_sms());
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+    if (f32) {
+        if (n_out != 1) return VUP_ERR_UNSUPPORTED;
+        VUP_PROF(terms == 3 ? "moments_tf32x3_tc" : "moments_tf32_tc", s, 1);
+        VUP_CHECK_CUDA(
+            cudaFuncSetAttribute(k_moments_tc<1, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_moments_tc<1, false, 1><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part,
+                                                               nullptr, nullptr, 0, g->dstatus, terms, n_split);
+        VUP_CHECK_LAUNCH();
+        return VUP_OK;
+    }
     VUP_PROF(n_out == 1 ? "moments_bf16x3_tc" : "ipsa_bf16x3_tc", s, 1);
     if (n_out == 1) {
         VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_moments_tc<1, false><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, nullptr,
-                                                            nullptr, 0, g->dstatus);
+                                                            nullptr, 0, g->dstatus, 3, n_split);
     } else {
         VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_moments_tc<3, false><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, nullptr,
-                                                            nullptr, 0, g->dstatus);
+                                                            nullptr, 0, g->dstatus, 3, n_split);
     }
     VUP_CHECK_LAUNCH();
     return VUP_OK;

@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libvup.so")
 VUP_OK, VUP_ERR_INVALID_ARG, VUP_ERR_CUDA, VUP_ERR_OOM, VUP_ERR_STATE = 0, 1, 2, 3, 4
 VUP_ERR_EMPTY_SUPPORT, VUP_ERR_TIMEOUT, VUP_ERR_UNSUPPORTED = 5, 6, 7
 VUP_GAUSS, VUP_UNIFORM, VUP_TRUNCNORM = 0, 1, 2
-VUP_FP64, VUP_FP32, VUP_BF16X3 = 0, 1, 2
-PRECISIONS = {"fp64": VUP_FP64, "fp32": VUP_FP32, "bf16x3": VUP_BF16X3}
+VUP_FP64, VUP_FP32, VUP_BF16X3, VUP_TF32, VUP_TF32X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": VUP_FP64, "fp32": VUP_FP32, "bf16x3": VUP_BF16X3, "tf32": VUP_TF32, "tf32x3": VUP_TF32X3}
 
 # exported symbols declared in include/vup.h
 ABI_SYMBOLS = [

@@ -370,3 +370,28 @@ def test_tiny_2d_case_matches_stored_values(precision):
     sc = np.abs(stored["dmu"]).max() + np.abs(stored["dsigma"]).max()
     assert np.abs(dmu.cpu().numpy() - stored["dmu"]).max() / sc < 10 * Hp.TOL[precision]
     assert np.abs(dsg.cpu().numpy() - stored["dsigma"]).max() / sc < 10 * Hp.TOL[precision]
+
+
+# ------------------------------------------------------------ TF32 kinds
+@pytest.mark.parametrize("name", ["c2", "c3", "c4"])
+def test_propagate_small_configs_tf32x3(name):
+    """3 x TF32 split products: gated at the BF16x3 tolerance (2e-5)."""
+    _parity(I.config(name, "small"), "tf32x3")
+
+
+@pytest.mark.parametrize("seed", [211, 212])
+def test_propagate_random_ragged_shapes_tf32x3(seed):
+    prob = I.random_problem(seed, ndim=2 + seed % 2)
+    _parity(prob, "tf32x3")
+
+
+def test_tf32_single_product_is_report_only_accuracy():
+    """One TF32 product (10-bit mantissa) is a comparison point: about 1e-3 of
+    the condition scale, far from the FP32 gate; histograms are unaffected."""
+    prob = I.config("c2", "small")
+    g, raw, cen, hs = gpu_run(prob, "tf32")
+    res = O.solve(prob)
+    scale = Hp.abs_moment_scale(prob, res["y"], np.arange(prob.K))
+    err = (np.abs(raw - res["raw"]) / scale).max()
+    assert 1e-7 < err < 5e-3, err
+    Hp.check_hist(hs, res["hist"])
