@@ -28,6 +28,8 @@
 namespace {
 
 constexpr int kHistWarps = 20;
+constexpr int kChunksPerWarp = 2;                    // chunks of a group per warp, handed out dynamically
+constexpr int kGroupChunks = kHistWarps * kChunksPerWarp;
 constexpr int kKT = 128;                     // densities per k-tile (four per lane)
 constexpr int kWin = 128;                    // sorted-point words per staging buffer
 constexpr int kMaxPartRows = 392;            // gathered-axis rows per shared-memory tile
@@ -196,7 +198,8 @@ __device__ __noinline__ void flush_key(const ItemCtx *X, int c, int p, int64_t k
     }
 }
 
-// One work item: part p, chunk group cg (kHistWarps chunks, one per warp) and
+// One work item: part p, chunk group cg (kGroupChunks chunks, drawn by the
+// warps one at a time) and
 // the 128 densities from k0 of the instance *Ap (kernel parameter or global
 // memory).  Called by every thread of the CTA; `wseq` counts the staging
 // windows this warp has consumed so far (it keeps the per-warp mbarrier
@@ -204,7 +207,7 @@ __device__ __noinline__ void flush_key(const ItemCtx *X, int c, int p, int64_t k
 template <int NF>
 __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int64_t k0, uint8_t *sm,
                                           int64_t tile_rows, uint32_t &wseq, volatile int *abort, ItemCtx &X,
-                                          float *s_invz) {
+                                          float *s_invz, int *next_chunk) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k = k0 + 4 * lane;
     float *ws = reinterpret_cast<float *>(sm);
@@ -217,6 +220,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     if (*abort) return;  // a wait of an earlier item expired (uniform: read after the barrier)
     if (threadIdx.x == 0) {
         const HistArgs &A = *Ap;
+        *next_chunk = 0;
         X.H = A.sel[0] ? A.L1 : A.L0;
         X.part = A.part;
         X.out = X.H.P > 1 ? A.direct + (int64_t)p * A.K * A.B : A.hist;
@@ -250,145 +254,156 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     for (int64_t e = threadIdx.x; e < nrows * kKT; e += blockDim.x) ws[e] *= s_invz[e % kKT];
     __syncthreads();
 
-    const int wc = cg * kHistWarps + warp;
-    if (wc >= X.C) return;
-    const int c = p * X.C + wc;
-    const int32_t p0 = H.chunk_pt[c], p1 = H.chunk_pt[c + 1];
-    if (p0 >= p1) return;
-    const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
-    // keys cut by the chunk bounds can only be its first and last key
-    const int32_t first_key = H.chunk_bin[2 * c], last_key = H.chunk_bin[2 * c + 1];
-    const bool sh_first = H.koff[first_key] < p0 || H.koff[first_key + 1] > p1;
-    const bool sh_last = H.koff[last_key] < p0 || H.koff[last_key + 1] > p1;
-    auto flush = [&](int32_t key, float4 v) {
-        const bool first = key == first_key;
-        flush_key(&X, c, p, k, key, v, first ? sh_first : (key == last_key && sh_last), first);
-    };
+    // the item's chunks are handed out one at a time (kChunksPerWarp per warp
+    // on average), so a warp that drew short chunks takes another instead of
+    // idling at the next item's barrier
+    auto run_chunk = [&](const int wc) -> bool {
+        const int c = p * X.C + wc;
+        const int32_t p0 = H.chunk_pt[c], p1 = H.chunk_pt[c + 1];
+        if (p0 >= p1) return true;
+        const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
+        // keys cut by the chunk bounds can only be its first and last key
+        const int32_t first_key = H.chunk_bin[2 * c], last_key = H.chunk_bin[2 * c + 1];
+        const bool sh_first = H.koff[first_key] < p0 || H.koff[first_key + 1] > p1;
+        const bool sh_last = H.koff[last_key] < p0 || H.koff[last_key + 1] > p1;
+        auto flush = [&](int32_t key, float4 v) {
+            const bool first = key == first_key;
+            flush_key(&X, c, p, k, key, v, first ? sh_first : (key == last_key && sh_last), first);
+        };
 
-    // staging of the sorted point stream: window i of this item lands in
-    // buffer (wseq + i) & 1
-    const uint32_t *hpt = H.hpt;
-    const int32_t wb0 = p0 & ~(kWin - 1);
-    if (lane == 0) {
-        const int b0 = wseq & 1;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier items' reads of both buffers
-        bulk_copy(win + b0 * kWin, hpt + wb0, kWin * 4, &mbar[b0]);
-        if (wb0 + kWin < p1) bulk_copy(win + (b0 ^ 1) * kWin, hpt + wb0 + kWin, kWin * 4, &mbar[b0 ^ 1]);
-    }
-    __syncwarp();
-
-    // rest-axis factors (four densities) of runs r .. r + 3, rotated through registers
-    const int64_t K_pad = X.K_pad;
-    const float *g0k = H.g0 + k;
-    const float *g1k = NF == 2 ? H.g1 + k : nullptr;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto rest_factor = [&](int32_t r) -> float4 {
-        if (r >= r1) return zero4;
-        const int32_t rest = H.run_rest[r];
-        if (NF == 2) {
-            const int32_t a0 = rest / (int32_t)H.n1, a1 = rest - a0 * (int32_t)H.n1;
-            return mul4(ld4(g0k + a0 * K_pad), ld4(g1k + a1 * K_pad));
+        // staging of the sorted point stream: window i of this item lands in
+        // buffer (wseq + i) & 1
+        const uint32_t *hpt = H.hpt;
+        const int32_t wb0 = p0 & ~(kWin - 1);
+        if (lane == 0) {
+            const int b0 = wseq & 1;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier items' reads of both buffers
+            bulk_copy(win + b0 * kWin, hpt + wb0, kWin * 4, &mbar[b0]);
+            if (wb0 + kWin < p1) bulk_copy(win + (b0 ^ 1) * kWin, hpt + wb0 + kWin, kWin * 4, &mbar[b0 ^ 1]);
         }
-        return ld4(g0k + rest * K_pad);
-    };
-    // fc = factor of the current run, f1..f3 those of the next three runs
-    float4 fc = rest_factor(r0), f1 = rest_factor(r0 + 1), f2 = rest_factor(r0 + 2), f3 = rest_factor(r0 + 3);
-    // factor of run r + 4, decoded from run r's end word: 9 low bits below the
-    // row field and 12 bits above it
-    auto coded_factor = [&](uint32_t u) -> float4 {
-        if (NF == 2) {
-            const uint32_t a0 = u & 0x1ffu, a1 = (u >> 18) & 0xfffu;
-            return mul4(ld4(g0k + (int64_t)a0 * K_pad), ld4(g1k + (int64_t)a1 * K_pad));
-        }
-        const uint32_t idx = (u & 0x1ffu) | (((u >> 18) & 0xfffu) << 9);
-        return ld4(g0k + (int64_t)idx * K_pad);
-    };
+        __syncwarp();
 
-    // every point's factor is multiplied by its run's rest-axis factor fc as it
-    // is added (one FMA per density, the same count as a plain add), so a run
-    // end only advances the factor pipeline
-    int32_t r = r0, cur_key = first_key;
-    float4 bacc = zero4;
-    const uint32_t wsl = smem_u32(ws) + lane * 16;
-    const uint32_t null_word = (uint32_t)nrows << kRowShift;  // zero row, no flags
+        // rest-axis factors (four densities) of runs r .. r + 3, rotated through registers
+        const int64_t K_pad = X.K_pad;
+        const float *g0k = H.g0 + k;
+        const float *g1k = NF == 2 ? H.g1 + k : nullptr;
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto rest_factor = [&](int32_t r) -> float4 {
+            if (r >= r1) return zero4;
+            const int32_t rest = H.run_rest[r];
+            if (NF == 2) {
+                const int32_t a0 = rest / (int32_t)H.n1, a1 = rest - a0 * (int32_t)H.n1;
+                return mul4(ld4(g0k + a0 * K_pad), ld4(g1k + a1 * K_pad));
+            }
+            return ld4(g0k + rest * K_pad);
+        };
+        // fc = factor of the current run, f1..f3 those of the next three runs
+        float4 fc = rest_factor(r0), f1 = rest_factor(r0 + 1), f2 = rest_factor(r0 + 2), f3 = rest_factor(r0 + 3);
+        // factor of run r + 4, decoded from run r's end word: 9 low bits below the
+        // row field and 12 bits above it
+        auto coded_factor = [&](uint32_t u) -> float4 {
+            if (NF == 2) {
+                const uint32_t a0 = u & 0x1ffu, a1 = (u >> 18) & 0xfffu;
+                return mul4(ld4(g0k + (int64_t)a0 * K_pad), ld4(g1k + (int64_t)a1 * K_pad));
+            }
+            const uint32_t idx = (u & 0x1ffu) | (((u >> 18) & 0xfffu) << 9);
+            return ld4(g0k + (int64_t)idx * K_pad);
+        };
 
-    auto run_end = [&](uint32_t u) {
-        if (u & kBinEnd) {
-            flush(cur_key, bacc);
-            bacc = zero4;
-            cur_key = r + 1 < r1 ? H.run_bin[r + 1] : -1;
-        }
-        fc = f1;
-        f1 = f2;
-        f2 = f3;
-        f3 = coded_factor(u);
-        ++r;
-    };
-    auto gather = [&](uint32_t addr) -> float4 {
-        float4 v;
-        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                     : "r"(addr));
-        return v;
-    };
-    // words without flags carry nothing but the row byte offset (run codes sit
-    // on run-end words only), so the common path needs no masking
-    auto group = [&](const uint4 v) {
-        if (((v.x | v.y | v.z | v.w) & kFlags) == 0) {
-            const float4 a0 = gather(wsl + v.x), a1 = gather(wsl + v.y), a2 = gather(wsl + v.z),
-                         a3 = gather(wsl + v.w);
-            fma4(bacc, fc, a0);
-            fma4(bacc, fc, a1);
-            fma4(bacc, fc, a2);
-            fma4(bacc, fc, a3);
-        } else {
-            const float4 a0 = gather(wsl + (v.x & kOffMask)), a1 = gather(wsl + (v.y & kOffMask)),
-                         a2 = gather(wsl + (v.z & kOffMask)), a3 = gather(wsl + (v.w & kOffMask));
-            fma4(bacc, fc, a0);
-            if (v.x & kFlags) run_end(v.x);
-            fma4(bacc, fc, a1);
-            if (v.y & kFlags) run_end(v.y);
-            fma4(bacc, fc, a2);
-            if (v.z & kFlags) run_end(v.z);
-            fma4(bacc, fc, a3);
-            if (v.w & kFlags) run_end(v.w);
-        }
-    };
-    // a group cut by the chunk bounds: foreign points read the zero row
-    auto masked = [&](uint4 v, int pa, int lo, int hi) {
-        if (pa + 0 < lo || pa + 0 >= hi) v.x = null_word;
-        if (pa + 1 < lo || pa + 1 >= hi) v.y = null_word;
-        if (pa + 2 < lo || pa + 2 >= hi) v.z = null_word;
-        if (pa + 3 < lo || pa + 3 >= hi) v.w = null_word;
-        return v;
-    };
+        // every point's factor is multiplied by its run's rest-axis factor fc as it
+        // is added (one FMA per density, the same count as a plain add), so a run
+        // end only advances the factor pipeline
+        int32_t r = r0, cur_key = first_key;
+        float4 bacc = zero4;
+        const uint32_t wsl = smem_u32(ws) + lane * 16;
+        const uint32_t null_word = (uint32_t)nrows << kRowShift;  // zero row, no flags
 
-    for (int32_t wbase = wb0; wbase < p1; wbase += kWin, ++wseq) {
-        const int b = wseq & 1;
-        for (uint32_t i = 0; !mbar_try_wait(&mbar[b], (wseq >> 1) & 1); ++i) {
-            if (i > kSpin || *abort) {  // a staged copy never landed: record and stop
-                *abort = 1;
-                atomicCAS(X.dstatus, 0, VUP_DSTAT_TIMEOUT);
-                return;
+        auto run_end = [&](uint32_t u) {
+            if (u & kBinEnd) {
+                flush(cur_key, bacc);
+                bacc = zero4;
+                cur_key = r + 1 < r1 ? H.run_bin[r + 1] : -1;
+            }
+            fc = f1;
+            f1 = f2;
+            f2 = f3;
+            f3 = coded_factor(u);
+            ++r;
+        };
+        auto gather = [&](uint32_t addr) -> float4 {
+            float4 v;
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                         : "r"(addr));
+            return v;
+        };
+        // words without flags carry nothing but the row byte offset (run codes sit
+        // on run-end words only), so the common path needs no masking
+        auto group = [&](const uint4 v) {
+            if (((v.x | v.y | v.z | v.w) & kFlags) == 0) {
+                const float4 a0 = gather(wsl + v.x), a1 = gather(wsl + v.y), a2 = gather(wsl + v.z),
+                             a3 = gather(wsl + v.w);
+                fma4(bacc, fc, a0);
+                fma4(bacc, fc, a1);
+                fma4(bacc, fc, a2);
+                fma4(bacc, fc, a3);
+            } else {
+                const float4 a0 = gather(wsl + (v.x & kOffMask)), a1 = gather(wsl + (v.y & kOffMask)),
+                             a2 = gather(wsl + (v.z & kOffMask)), a3 = gather(wsl + (v.w & kOffMask));
+                fma4(bacc, fc, a0);
+                if (v.x & kFlags) run_end(v.x);
+                fma4(bacc, fc, a1);
+                if (v.y & kFlags) run_end(v.y);
+                fma4(bacc, fc, a2);
+                if (v.z & kFlags) run_end(v.z);
+                fma4(bacc, fc, a3);
+                if (v.w & kFlags) run_end(v.w);
+            }
+        };
+        // a group cut by the chunk bounds: foreign points read the zero row
+        auto masked = [&](uint4 v, int pa, int lo, int hi) {
+            if (pa + 0 < lo || pa + 0 >= hi) v.x = null_word;
+            if (pa + 1 < lo || pa + 1 >= hi) v.y = null_word;
+            if (pa + 2 < lo || pa + 2 >= hi) v.z = null_word;
+            if (pa + 3 < lo || pa + 3 >= hi) v.w = null_word;
+            return v;
+        };
+
+        for (int32_t wbase = wb0; wbase < p1; wbase += kWin, ++wseq) {
+            const int b = wseq & 1;
+            for (uint32_t i = 0; !mbar_try_wait(&mbar[b], (wseq >> 1) & 1); ++i) {
+                if (i > kSpin || *abort) {  // a staged copy never landed: record and stop
+                    *abort = 1;
+                    atomicCAS(X.dstatus, 0, VUP_DSTAT_TIMEOUT);
+                    return false;
+                }
+            }
+            const uint32_t *wv = win + b * kWin;
+            const int lo = (p0 > wbase ? p0 : wbase) - wbase;
+            const int hi = (p1 < wbase + kWin ? p1 : wbase + kWin) - wbase;
+            const int ga = (lo + 3) & ~3, gb = hi & ~3;   // whole groups [ga, gb)
+            if (lo & 3) {
+                const int pa = lo & ~3;
+                group(masked(*reinterpret_cast<const uint4 *>(wv + pa), pa, lo, hi));
+            }
+    #pragma unroll 2
+            for (int pa = ga; pa < gb; pa += 4) group(*reinterpret_cast<const uint4 *>(wv + pa));
+            if ((hi & 3) && gb >= ga) group(masked(*reinterpret_cast<const uint4 *>(wv + gb), gb, lo, hi));
+            __syncwarp();
+            if (lane == 0 && wbase + 2 * kWin < p1) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bulk_copy(win + b * kWin, hpt + wbase + 2 * kWin, kWin * 4, &mbar[b]);
             }
         }
-        const uint32_t *wv = win + b * kWin;
-        const int lo = (p0 > wbase ? p0 : wbase) - wbase;
-        const int hi = (p1 < wbase + kWin ? p1 : wbase + kWin) - wbase;
-        const int ga = (lo + 3) & ~3, gb = hi & ~3;   // whole groups [ga, gb)
-        if (lo & 3) {
-            const int pa = lo & ~3;
-            group(masked(*reinterpret_cast<const uint4 *>(wv + pa), pa, lo, hi));
-        }
-#pragma unroll 2
-        for (int pa = ga; pa < gb; pa += 4) group(*reinterpret_cast<const uint4 *>(wv + pa));
-        if ((hi & 3) && gb >= ga) group(masked(*reinterpret_cast<const uint4 *>(wv + gb), gb, lo, hi));
-        __syncwarp();
-        if (lane == 0 && wbase + 2 * kWin < p1) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            bulk_copy(win + b * kWin, hpt + wbase + 2 * kWin, kWin * 4, &mbar[b]);
-        }
+        if (cur_key >= 0) flush(cur_key, bacc);
+        return true;
+    };
+    for (;;) {
+        int ci = 0;
+        if (lane == 0) ci = atomicAdd(next_chunk, 1);
+        ci = __shfl_sync(0xffffffffu, ci, 0);
+        if (ci >= kGroupChunks) break;
+        if (!run_chunk(cg * kGroupChunks + ci)) return;
     }
-    if (cur_key >= 0) flush(cur_key, bacc);
 }
 
 __device__ __forceinline__ uint64_t *hist_mbar(uint8_t *sm, int64_t tile_rows) {
@@ -411,12 +426,12 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1)
     extern __shared__ __align__(128) uint8_t sm[];
     __shared__ ItemCtx X;
     __shared__ float s_invz[kKT];
-    __shared__ int abort;
+    __shared__ int abort, next_chunk;
     const int p = blockIdx.x / G, cg = blockIdx.x - p * G;
     if (threadIdx.x == 0) abort = 0;
     hist_init_mbar(sm, tile_rows);
     uint32_t wseq = 0;
-    hist_item<NF>(&A, p, cg, (int64_t)blockIdx.y * kKT, sm, tile_rows, wseq, &abort, X, s_invz);
+    hist_item<NF>(&A, p, cg, (int64_t)blockIdx.y * kKT, sm, tile_rows, wseq, &abort, X, s_invz, &next_chunk);
 }
 
 // Batched form: one persistent launch over the work items of many instances
@@ -432,13 +447,14 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_batched(const HistA
     extern __shared__ __align__(128) uint8_t sm[];
     __shared__ ItemCtx X;
     __shared__ float s_invz[kKT];
-    __shared__ int abort;
+    __shared__ int abort, next_chunk;
     if (threadIdx.x == 0) abort = 0;
     hist_init_mbar(sm, tile_rows);
     uint32_t wseq = 0;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const HistItem w = items[it];
-        hist_item<NF>(insts + w.inst, w.p, w.cg, (int64_t)w.kt * kKT, sm, tile_rows, wseq, &abort, X, s_invz);
+        hist_item<NF>(insts + w.inst, w.p, w.cg, (int64_t)w.kt * kKT, sm, tile_rows, wseq, &abort, X, s_invz,
+                      &next_chunk);
     }
 }
 
@@ -451,43 +467,45 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_global(HistArgs A, 
     if (p >= H.P) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.y * kKT + 4 * lane;
-    const int c = p * A.C + cg * kHistWarps + warp;
-    if (cg * kHistWarps + warp >= A.C) return;
-    const int32_t p0 = H.chunk_pt[c], p1 = H.chunk_pt[c + 1];
-    if (p0 >= p1) return;
-    const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
-    const Flusher flush{A, H, c, p, p0, p1, H.chunk_bin[2 * c], k, load_inv_z(A, k)};
-    // the gathered-axis index comes from the sorted order itself (the point
-    // words' row field only covers shared-memory tiles)
-    const float *wl = H.g_last + k;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto wrest = [&](int32_t r) -> float4 {
-        if (r >= r1) return zero4;
-        const int32_t rest = H.run_rest[r];
-        if (A.ndim == 3) {
-            const int64_t a0 = rest / H.n1, a1 = rest - a0 * H.n1;
-            return mul4(ld4(H.g0 + a0 * A.K_pad + k), ld4(H.g1 + a1 * A.K_pad + k));
-        }
-        return ld4(H.g0 + (int64_t)rest * A.K_pad + k);
-    };
-    int32_t cur_key = H.run_bin[r0];
-    float4 bacc = zero4;
-    for (int32_t rb = r0; rb < r1; rb += kPF) {
-        float4 w[kPF];
-#pragma unroll
-        for (int u = 0; u < kPF; ++u) w[u] = wrest(rb + u);
-        for (int u = 0; u < kPF; ++u) {
-            const int32_t r = rb + u;
-            if (r >= r1) break;
-            float4 acc = zero4;
-            for (int32_t q = H.run_start[r]; q < H.run_start[r + 1]; ++q)
-                add4(acc, ld4(wl + (int64_t)(H.perm[q] % H.n_last) * A.K_pad));
-            fma4(bacc, w[u], acc);
-            const int32_t nk = r + 1 < r1 ? H.run_bin[r + 1] : -1;
-            if (nk != cur_key) {
-                flush(cur_key, bacc);
-                bacc = zero4;
-                cur_key = nk;
+    // chunks cg * kGroupChunks + j * kHistWarps + warp, j < kChunksPerWarp
+    for (int j = 0; j < kChunksPerWarp; ++j) {
+        const int c = p * A.C + cg * kGroupChunks + j * kHistWarps + warp;
+        const int32_t p0 = H.chunk_pt[c], p1 = H.chunk_pt[c + 1];
+        if (p0 >= p1) continue;
+        const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
+        const Flusher flush{A, H, c, p, p0, p1, H.chunk_bin[2 * c], k, load_inv_z(A, k)};
+        // the gathered-axis index comes from the sorted order itself (the point
+        // words' row field only covers shared-memory tiles)
+        const float *wl = H.g_last + k;
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto wrest = [&](int32_t r) -> float4 {
+            if (r >= r1) return zero4;
+            const int32_t rest = H.run_rest[r];
+            if (A.ndim == 3) {
+                const int64_t a0 = rest / H.n1, a1 = rest - a0 * H.n1;
+                return mul4(ld4(H.g0 + a0 * A.K_pad + k), ld4(H.g1 + a1 * A.K_pad + k));
+            }
+            return ld4(H.g0 + (int64_t)rest * A.K_pad + k);
+        };
+        int32_t cur_key = H.run_bin[r0];
+        float4 bacc = zero4;
+        for (int32_t rb = r0; rb < r1; rb += kPF) {
+            float4 w[kPF];
+    #pragma unroll
+            for (int u = 0; u < kPF; ++u) w[u] = wrest(rb + u);
+            for (int u = 0; u < kPF; ++u) {
+                const int32_t r = rb + u;
+                if (r >= r1) break;
+                float4 acc = zero4;
+                for (int32_t q = H.run_start[r]; q < H.run_start[r + 1]; ++q)
+                    add4(acc, ld4(wl + (int64_t)(H.perm[q] % H.n_last) * A.K_pad));
+                fma4(bacc, w[u], acc);
+                const int32_t nk = r + 1 < r1 ? H.run_bin[r + 1] : -1;
+                if (nk != cur_key) {
+                    flush(cur_key, bacc);
+                    bacc = zero4;
+                    cur_key = nk;
+                }
             }
         }
     }
@@ -549,10 +567,11 @@ __global__ void k_hist_finish_batched(const HistArgs *__restrict__ insts, const 
 
 }  // namespace
 
+// Chunks per part: groups of kGroupChunks, about one group per 327680 points.
 int vup_hist_chunks_for(int64_t N) {
     int64_t S = N / ((int64_t)kHistWarps * 16384);
     S = std::max<int64_t>(1, std::min<int64_t>(16, S));
-    return (int)(S * kHistWarps);
+    return (int)(S * kGroupChunks);
 }
 
 // Parts of a gathered axis of n_last rows (one 64-density tile each) for a
@@ -628,7 +647,7 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     const size_t smem = hist_smem_bytes(rows);
     // run-end words encode the rest index in 21 bits (3-D: a0 < 512, a1 < 4096)
     const bool coded = nd == 2 || (g->n[0] <= 512 && g->n[1] <= 4096);
-    const int G = A.C / kHistWarps;
+    const int G = A.C / kGroupChunks;
     dim3 grd((unsigned)(P_max * G), (unsigned)ceil_div64(K, kKT));
     {
         VUP_PROF("hist_segmented", s, 1);
@@ -680,7 +699,7 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
         args[i] = hist_args_for(gs[i], Ks[i], hists[i], rows, P_max);
         if (!hists[i]) continue;
         rows_max = std::max(rows_max, rows);
-        const int G = args[i].C / kHistWarps;
+        const int G = args[i].C / kGroupChunks;
         const int64_t nkt = ceil_div64(Ks[i], kKT);
         // cost of one item: points per chunk x densities per tile
         const int64_t cost = gs[i]->N / std::max<int64_t>(1, (int64_t)P_max * args[i].C);
@@ -731,11 +750,14 @@ vup_status vup_hist_batched(void *plan, cudaStream_t s) {
     if (P->n_items == 0) return VUP_OK;
     const size_t smem = hist_smem_bytes(P->rows);
     if (smem > 220 * 1024) return VUP_ERR_UNSUPPORTED;
-    VUP_PROF("hist_segmented_batched", s, 2);
-    const int grid = std::max(1, std::min(P->n_items, vup_num_sms()));
-    k_hist_batched<1><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p, (const HistItem *)P->items.p,
-                                                          P->n_items, P->rows);
-    VUP_CHECK_LAUNCH();
+    {
+        VUP_PROF("hist_segmented_batched", s, 1);
+        const int grid = std::max(1, std::min(P->n_items, vup_num_sms()));
+        k_hist_batched<1><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
+                                                              (const HistItem *)P->items.p, P->n_items, P->rows);
+        VUP_CHECK_LAUNCH();
+    }
+    VUP_PROF("hist_fixup_batched", s, 1);
     k_hist_finish_batched<<<P->n_fitems, 128, 0, s>>>((const HistArgs *)P->args.p, (const int4 *)P->fitems.p);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
