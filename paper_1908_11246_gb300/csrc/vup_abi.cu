@@ -136,7 +136,7 @@ int vup_num_sms() {
     return n;
 }
 
-int vup_hist_chunks_for(int64_t N);
+int vup_hist_chunks_for(int64_t N, int P);
 int vup_hist_parts_for(int64_t n_last, int n_bins);
 
 extern "C" const char *vup_status_string(vup_status s) {
@@ -253,7 +253,10 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
         ori.rest_axes[0] = 0;
         ori.rest_axes[1] = -1;
     }
-    g->n_chunks = vup_hist_chunks_for(N);
+    int p_all = 1;  // the most parts any layout of this grid can have
+    for (int l = 0; l < (ndim == 2 ? 2 : 1); ++l)
+        p_all = std::max(p_all, vup_hist_parts_for(g->n[l == 0 ? ndim - 1 : 0], 1));
+    g->n_chunks = vup_hist_chunks_for(N, p_all);
     const int C = g->n_chunks;
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, bytes) \

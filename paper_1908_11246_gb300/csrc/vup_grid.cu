@@ -624,7 +624,7 @@ vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta, 
     return VUP_OK;
 }
 
-int vup_hist_chunks_for(int64_t N);
+int vup_hist_chunks_for(int64_t N, int P);
 int vup_hist_parts_for(int64_t n_last, int n_bins);
 
 // Warps per CTA of the counting-sort kernels for a key space of Bk keys (the

@@ -28,8 +28,8 @@
 namespace {
 
 constexpr int kHistWarps = 20;
-constexpr int kChunksPerWarp = 2;                    // chunks of a group per warp, handed out dynamically
-constexpr int kGroupChunks = kHistWarps * kChunksPerWarp;
+constexpr int kChunksPerWarp = 4;                    // chunks per warp in the smallest group
+constexpr int kGroupChunks = kHistWarps * kChunksPerWarp;  // chunks per part come in multiples of this
 constexpr int kKT = 128;                     // densities per k-tile (four per lane)
 constexpr int kWin = 128;                    // sorted-point words per staging buffer
 constexpr int kMaxPartRows = 392;            // gathered-axis rows per shared-memory tile
@@ -61,6 +61,7 @@ struct HistArgs {
     int64_t K, K_pad;
     int B;
     int C;                // chunks per part
+    int group_chunks;     // chunks per work item (a multiple of kGroupChunks dividing C)
     float *hist;          // [K][B]
     float *part;          // [P * C][2][K_pad]
     float *direct;        // [P][K][B] (P > 1)
@@ -175,7 +176,7 @@ struct ItemCtx {
     float *part;   // [P * C][2][K_pad] partial sums of keys cut by chunk bounds
     float *out;    // [K][B] whole-key sums of this part (hist, or direct + p K B)
     int64_t K, K_pad;
-    int B, C;
+    int B, C, group_chunks;
     int *dstatus;
 };
 
@@ -228,6 +229,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         X.K_pad = A.K_pad;
         X.B = A.B;
         X.C = A.C;
+        X.group_chunks = A.group_chunks;
         X.dstatus = A.dstatus;
     }
     if (threadIdx.x < kKT) s_invz[threadIdx.x] = inv_z(*Ap, k0 + threadIdx.x);
@@ -254,7 +256,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     for (int64_t e = threadIdx.x; e < nrows * kKT; e += blockDim.x) ws[e] *= s_invz[e % kKT];
     __syncthreads();
 
-    // the item's chunks are handed out one at a time (kChunksPerWarp per warp
+    // the item's chunks are handed out one at a time (at least kChunksPerWarp per warp
     // on average), so a warp that drew short chunks takes another instead of
     // idling at the next item's barrier
     auto run_chunk = [&](const int wc) -> bool {
@@ -401,8 +403,8 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         int ci = 0;
         if (lane == 0) ci = atomicAdd(next_chunk, 1);
         ci = __shfl_sync(0xffffffffu, ci, 0);
-        if (ci >= kGroupChunks) break;
-        if (!run_chunk(cg * kGroupChunks + ci)) return;
+        if (ci >= X.group_chunks) break;
+        if (!run_chunk(cg * X.group_chunks + ci)) return;
     }
 }
 
@@ -467,9 +469,9 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_global(HistArgs A, 
     if (p >= H.P) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.y * kKT + 4 * lane;
-    // chunks cg * kGroupChunks + j * kHistWarps + warp, j < kChunksPerWarp
-    for (int j = 0; j < kChunksPerWarp; ++j) {
-        const int c = p * A.C + cg * kGroupChunks + j * kHistWarps + warp;
+    // chunks cg * group_chunks + j * kHistWarps + warp
+    for (int j = 0; j < A.group_chunks / kHistWarps; ++j) {
+        const int c = p * A.C + cg * A.group_chunks + j * kHistWarps + warp;
         const int32_t p0 = H.chunk_pt[c], p1 = H.chunk_pt[c + 1];
         if (p0 >= p1) continue;
         const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
@@ -567,9 +569,12 @@ __global__ void k_hist_finish_batched(const HistArgs *__restrict__ insts, const 
 
 }  // namespace
 
-// Chunks per part: groups of kGroupChunks, about one group per 327680 points.
-int vup_hist_chunks_for(int64_t N) {
-    int64_t S = N / ((int64_t)kHistWarps * 16384);
+// Chunks per part: groups of kGroupChunks chunks, as many groups (1..16) as
+// give chunks of about 1536 points when the gathered axis is cut into P
+// parts.  A launch then picks how many groups one CTA serves.
+int vup_hist_chunks_for(int64_t N, int P) {
+    const double per_group = (double)kGroupChunks * 1536.0;
+    int64_t S = (int64_t)llround((double)N / ((double)std::max(P, 1) * per_group));
     S = std::max<int64_t>(1, std::min<int64_t>(16, S));
     return (int)(S * kGroupChunks);
 }
@@ -595,6 +600,7 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
         return ft + off;
     };
     HistArgs A{};
+    A.group_chunks = kGroupChunks;
     rows = 0;
     P_max = 1;
     for (int l = 0; l < 2; ++l) {
@@ -643,11 +649,25 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     const int nd = g->ndim;
     int64_t rows;
     int P_max;
-    const HistArgs A = hist_args_for(g, K, hist, rows, P_max, ftab);
+    HistArgs A = hist_args_for(g, K, hist, rows, P_max, ftab);
     const size_t smem = hist_smem_bytes(rows);
     // run-end words encode the rest index in 21 bits (3-D: a0 < 512, a1 < 4096)
     const bool coded = nd == 2 || (g->n[0] <= 512 && g->n[1] <= 4096);
-    const int G = A.C / kGroupChunks;
+    // CTAs along the chunks: G groups of C / G chunks per part, G dividing
+    // C / kGroupChunks, chosen for the fewest idle SM slots in the last wave
+    const int S = A.C / kGroupChunks, nkt = (int)ceil_div64(K, kKT), sms = vup_num_sms();
+    int G = S;
+    double best = -1.0;
+    for (int gg = S; gg >= 1; --gg) {
+        if (S % gg) continue;
+        const int64_t ctas = (int64_t)P_max * gg * nkt;
+        const double eff = (double)ctas / (double)(ceil_div64(ctas, sms) * sms);
+        if (eff > best + 0.02) {
+            best = eff;
+            G = gg;
+        }
+    }
+    A.group_chunks = A.C / G;
     dim3 grd((unsigned)(P_max * G), (unsigned)ceil_div64(K, kKT));
     {
         VUP_PROF("hist_segmented", s, 1);
@@ -699,6 +719,7 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
         args[i] = hist_args_for(gs[i], Ks[i], hists[i], rows, P_max);
         if (!hists[i]) continue;
         rows_max = std::max(rows_max, rows);
+        args[i].group_chunks = kGroupChunks;
         const int G = args[i].C / kGroupChunks;
         const int64_t nkt = ceil_div64(Ks[i], kKT);
         // cost of one item: points per chunk x densities per tile
