@@ -325,12 +325,7 @@ static vup_status model_ready(vup_grid g, int n_bins, int n_moments) {
 static vup_status finish_model(vup_grid g, cudaStream_t s) {
     vup_status st = vup_launch_grid_finish(g, s);
     if (st != VUP_OK) return st;
-    if (g->ndim >= 2) {
-        st = vup_build_tables(g, kOrientLast, 0, s);
-        if (st != VUP_OK) return st;
-        st = vup_build_tables(g, vup_tc_orient(g), 1, s);
-        if (st != VUP_OK) return st;
-    }
+    // power tables are built on first use by the contraction that needs them
     g->have_model = 1;
     ++g->model_gen;
     return VUP_OK;
@@ -445,7 +440,9 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
     const bool want_m = moments_raw || moments_central;
     if ((st = vup_reserve_k(g, K, bf16, false, tf32)) != VUP_OK) return st;
     const int to = vup_tc_orient(g);
-    if (tf32 && want_m && (st = vup_build_tables(g, to, 2, s)) != VUP_OK) return st;
+    if (want_m && (st = vup_build_tables(g, (bf16 || tf32) ? to : kOrientLast, tf32 ? 2 : (bf16 ? 1 : 0), s)) !=
+                      VUP_OK)
+        return st;
     if ((st = vup_density_prep(g, d, ((bf16 || tf32) && want_m) ? (1 << to) : 0, s, tf32)) != VUP_OK) return st;
     if (want_m) {
         int64_t nct;
@@ -491,6 +488,7 @@ extern "C" vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, v
     const int64_t K = d->K;
     const bool bf16 = precision == VUP_BF16X3;
     if ((st = vup_reserve_k(g, K, bf16, true)) != VUP_OK) return st;
+    if ((st = vup_build_tables(g, 0, bf16 ? 1 : 0, s)) != VUP_OK) return st;
     if ((st = vup_build_tables(g, 1, bf16 ? 1 : 0, s)) != VUP_OK) return st;
     if ((st = vup_density_prep(g, d, bf16 ? 3 : 0, s)) != VUP_OK) return st;
     const int64_t K_pad = ceil_div64(K, 128) * 128;
