@@ -169,6 +169,7 @@ static void free_grid(vup_grid g) {
         cudaFree(L.binsT);
         cudaFree(L.keys_own);
         cudaFree(L.koff);
+        cudaFree(L.key_chunks);
         cudaFree(L.hpt);
         cudaFree(L.run_start);
         cudaFree(L.run_rest);

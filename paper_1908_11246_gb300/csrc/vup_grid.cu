@@ -456,6 +456,25 @@ __global__ void k_chunk_bins(const int32_t *__restrict__ chunk_run, const int32_
     chunk_bin[2 * c + 1] = r1 > r0 ? run_bin[r1 - 1] : -1;
 }
 
+// First and last chunk holding points of each key (-1, -1 for an empty key):
+// chunk c holds the points [chunk_pt[c], chunk_pt[c + 1]).
+__device__ __forceinline__ int chunk_holding(const int32_t *chunk_pt, int n, int32_t pt) {
+    int lo = 0, hi = n;  // last c in [0, n) with chunk_pt[c] <= pt
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (chunk_pt[mid] <= pt) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+__global__ void k_key_chunks(const int32_t *__restrict__ koff, int n_keys, const int32_t *__restrict__ chunk_pt,
+                             int n_chunks, int2 *__restrict__ out) {
+    const int key = blockIdx.x * blockDim.x + threadIdx.x;
+    if (key >= n_keys) return;
+    const int32_t o0 = koff[key], o1 = koff[key + 1];
+    out[key] = o0 == o1 ? make_int2(-1, -1)
+                        : make_int2(chunk_holding(chunk_pt, n_chunks, o0), chunk_holding(chunk_pt, n_chunks, o1 - 1));
+}
+
 // ---- power tables -----------------------------------------------------------
 // y viewed as a matrix Y[P][S] (flat i = p S + s).  Element (p, s) yields
 // z = y / s_scale and its powers z^j, j = 1..4 (FP64, then rounded).
@@ -700,8 +719,11 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
             g->hist_P = std::max(g->hist_P, HL.P);
             if (HL.koff_cap < HL.P * B + 1) {
                 cudaFree(HL.koff);
+                cudaFree(HL.key_chunks);
                 HL.koff = nullptr;
+                HL.key_chunks = nullptr;
                 VUP_CHECK_CUDA(cudaMalloc(&HL.koff, sizeof(int32_t) * (HL.P * B + 1)));
+                VUP_CHECK_CUDA(cudaMalloc(&HL.key_chunks, sizeof(int2) * (HL.P * B + 1)));
                 HL.koff_cap = HL.P * B + 1;
             }
         }
@@ -770,6 +792,8 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
                                                            HL.chunk_run);
             VUP_CHECK_LAUNCH();
             k_chunk_bins<<<(PC + 127) / 128, 128, 0, s>>>(HL.chunk_run, HL.run_bin, PC, HL.chunk_bin);
+            VUP_CHECK_LAUNCH();
+            k_key_chunks<<<(Bk + 127) / 128, 128, 0, s>>>(HL.koff, Bk, HL.chunk_pt, PC, HL.key_chunks);
             VUP_CHECK_LAUNCH();
         }
         k_natural_offsets<<<(B + 1 + 127) / 128, 128, 0, s>>>(g->hl[0].koff, g->hl[0].P, B, N, g->offsets);

@@ -46,6 +46,7 @@ struct LayoutArgs {
     const int32_t *run_start, *run_rest, *run_bin;
     const int32_t *chunk_pt, *chunk_run, *chunk_bin;
     const int32_t *koff;   // key offsets [P * B + 1]
+    const int2 *key_chunks;  // [P * B] first / last chunk of each key (-1 if empty)
     const float *g_last;   // factor table of the gathered axis  [n_last][K_pad]
     const float *g0, *g1;  // rest-axis factor tables (g1 only for 3-D)
     int64_t n_last, part_rows;
@@ -513,15 +514,6 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_global(HistArgs A, 
     }
 }
 
-__device__ __forceinline__ int chunk_of(const int32_t *chunk_pt, int n, int32_t p) {
-    int lo = 0, hi = n;  // last c in [0, n) with chunk_pt[c] <= p
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (chunk_pt[mid] <= p) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Finish H[k, b]: for every part, the key (part, b) is either empty, written
 // directly by the single chunk that holds it, or cut by chunk boundaries and
 // summed from the partials of the chunks overlapping it (in chunk order);
@@ -529,14 +521,13 @@ __device__ __forceinline__ int chunk_of(const int32_t *chunk_pt, int n, int32_t 
 __device__ __forceinline__ void hist_finish_body(const HistArgs &A, const LayoutArgs &H, int64_t kb, int b) {
     const int64_t k = kb * (int64_t)blockDim.x + threadIdx.x;
     if (k >= A.K || b >= A.B) return;
-    const int n_chunks = H.P * A.C;
     float total = 0.f;
     bool touched = H.P > 1;
     for (int p = 0; p < H.P; ++p) {
         const int32_t key = p * A.B + b;
-        const int32_t o0 = H.koff[key], o1 = H.koff[key + 1];
-        if (o0 == o1) continue;
-        const int c0 = chunk_of(H.chunk_pt, n_chunks, o0), c1 = chunk_of(H.chunk_pt, n_chunks, o1 - 1);
+        const int2 cc = H.key_chunks[key];  // chunks holding the key's points, precomputed per layout
+        if (cc.x < 0) continue;
+        const int c0 = cc.x, c1 = cc.y;
         if (c0 == c1) {
             if (H.P > 1) total += A.direct[((int64_t)p * A.K + k) * A.B + b];
             continue;
@@ -550,7 +541,7 @@ __device__ __forceinline__ void hist_finish_body(const HistArgs &A, const Layout
         }
         total += s;
     }
-    if (H.P == 1 && H.koff[b] == H.koff[b + 1]) touched = true;  // empty bin: zero
+    if (H.P == 1 && H.key_chunks[b].x < 0) touched = true;  // empty bin: zero
     if (touched) A.hist[k * A.B + b] = total;
 }
 
@@ -615,6 +606,7 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
         La.chunk_run = HL.chunk_run;
         La.chunk_bin = HL.chunk_bin;
         La.koff = HL.koff;
+        La.key_chunks = HL.key_chunks;
         La.g_last = tab(HL.last_axis);
         if (nd == 3) {
             La.g0 = tab(0);

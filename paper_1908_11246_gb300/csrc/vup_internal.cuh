@@ -109,6 +109,7 @@ struct vup_grid_s {
         int32_t *keys = nullptr;       // sort key of the layout's flat index: part * B + bin
         int32_t *keys_own = nullptr;   // [N] key storage when keys != bins
         int32_t *koff = nullptr;       // [P * B + 1] key offsets in the sorted stream
+        int2 *key_chunks = nullptr;    // [P * B] first and last chunk of each key's points (-1 if empty)
         int32_t koff_cap = 0;
         int32_t *perm = nullptr;       // [N] sorted position -> layout flat index
         uint32_t *hpt = nullptr;       // [N + 512] packed per-point word
