@@ -48,24 +48,17 @@ struct GaussArg {
     float qh, ql;    // u0^2 = qh + ql (u at the midpoint nearest the mean)
 };
 
-// Per-axis density value at midpoint a (unnormalised), and u = ((a - n) - f) r.
-// The exponent 0.5 (u^2 - u0^2) is carried as an FP32 pair (error ~2^-44
-// relative) and exp is split, exp(-(eh + el)) = expf(-eh) (1 - el), so the
-// factor keeps FP32 relative accuracy even far in the tails, where the
-// exponent is large and a plain FP32 argument would lose ~e * 2^-24.
-// Dividing by the value at the midpoint nearest the mean (u0) is a constant
-// per (k, d) that the normalisation removes; it keeps narrow densities from
-// underflowing.
-__device__ __forceinline__ float dens_value(int kind, int64_t a, const GaussArg &ga, double xa, double mu,
-                                            double sigma, double tlo, double thi, float &u) {
-    if (kind == VUP_UNIFORM) {
-        u = 0.f;
-        double half = __dmul_rn(0.5, sigma);
-        double dx = fabs(__dsub_rn(xa, mu));
-        return dx <= half ? 1.f : 0.f;
-    }
-    // t = (a - n) - f exactly as a pair
-    const float A = (float)((double)a - ga.nk);
+// Unnormalised Gaussian factor at index offset A = a - n (an integer held
+// exactly in FP32), and u = (A - f) r, the midpoint's distance from the mean
+// in units of sigma.  The exponent 0.5 (u^2 - u0^2) is carried as an FP32
+// pair (error ~2^-44 relative) and exp is split, exp(-(eh + el)) =
+// expf(-eh) (1 - el), so the factor keeps FP32 relative accuracy even far in
+// the tails, where the exponent is large and a plain FP32 argument would lose
+// ~e * 2^-24.  Dividing by the value at the midpoint nearest the mean (u0) is
+// a constant per (k, d) that the normalisation removes; it keeps narrow
+// densities from underflowing.
+__device__ __forceinline__ float gauss_value(float A, const GaussArg &ga, float &u) {
+    // t = A - f exactly as a pair
     float th, tl;
     two_sum(A, -ga.fh, th, tl);
     tl -= ga.fl;
@@ -73,7 +66,6 @@ __device__ __forceinline__ float dens_value(int kind, int64_t a, const GaussArg 
     const float uh = th * ga.rh;
     const float ul = fmaf(th, ga.rh, -uh) + (th * ga.rl + tl * ga.rh);
     u = uh + ul;
-    if (kind == VUP_TRUNCNORM && !(tlo <= xa && xa <= thi)) return 0.f;
     // u^2 - u0^2
     const float sh = uh * uh;
     const float sl = fmaf(uh, uh, -sh) + 2.f * uh * ul;
@@ -84,6 +76,56 @@ __device__ __forceinline__ float dens_value(int kind, int64_t a, const GaussArg 
     const float eh = eh0 + el0;
     const float el = el0 - (eh - eh0);
     return expf(-eh) * (1.f - el);
+}
+
+// Midpoint coordinate of cell a, x_a = lo + (a + 1/2) h, rounded in FP64 in
+// this order (the support decisions below compare it with FP64 bounds).
+__device__ __forceinline__ double midpoint(double lo, double h, int64_t a) {
+    return __dadd_rn(lo, __dmul_rn((double)a + 0.5, h));
+}
+
+// First a in [b, e) with pred(a) true, e if none, for a predicate that is
+// false then true along a (binary search: a few FP64 evaluations per segment
+// instead of one per point).
+template <class P>
+__device__ __forceinline__ int64_t first_true(int64_t b, int64_t e, P pred) {
+    while (b < e) {
+        const int64_t m = b + ((e - b) >> 1);
+        if (pred(m)) e = m; else b = m + 1;
+    }
+    return b;
+}
+
+// Factor values of one thread's segment [a_begin, a_end) of axis cells,
+// written to tab (stride K_pad) and summed (compensated) into S0 = sum g,
+// S1 = sum g u, S2 = sum g u^2.  Cells in [in_b, in_e) are inside the
+// support (uniform: g = 1 there; truncated normal: the Gaussian there, 0
+// outside).  EXACT_F32: every a - n in the segment is below 2^24 in
+// magnitude, so A is carried as an FP32 counter; otherwise A is rounded
+// from FP64 per cell.
+template <bool EXACT_F32>
+__device__ __forceinline__ void prep_segment(float *__restrict__ tab, int64_t K_pad, int kind, int64_t a_begin,
+                                             int64_t a_end, int64_t in_b, int64_t in_e, const GaussArg &ga,
+                                             KSum &S0, KSum &S1, KSum &S2) {
+    float Af = (float)((double)a_begin - ga.nk);
+    for (int64_t a = a_begin; a < a_end; ++a) {
+        const float A = EXACT_F32 ? Af : (float)((double)a - ga.nk);
+        Af += 1.f;
+        float u;
+        const float gv = gauss_value(A, ga, u);
+        const bool inside = a >= in_b && a < in_e;
+        float g;
+        if (kind == VUP_UNIFORM) {
+            g = inside ? 1.f : 0.f;
+            u = 0.f;
+        } else {
+            g = (kind == VUP_TRUNCNORM && !inside) ? 0.f : gv;
+        }
+        tab[a * K_pad] = g;
+        S0.add(g);
+        S1.add(g * u);
+        S2.add(g * u * u);
+    }
 }
 
 // Everything one density-prep launch needs for one grid (one instance).
@@ -151,17 +193,23 @@ __device__ __forceinline__ void density_prep_body(const DensJob &J, int64_t kb, 
     if (!(u0sq < 1e30)) u0sq = 0.0;
     ga.qh = (float)u0sq;
     ga.ql = (float)(u0sq - (double)ga.qh);
-    KSum S0, S1, S2;
-    for (int64_t a = a_begin; a < a_end; ++a) {
-        double xa = 0.0;
-        if (kind != VUP_GAUSS) xa = __dadd_rn(lo, __dmul_rn((double)a + 0.5, h));
-        float u;
-        float g = dens_value(kind, a, ga, xa, mu, sigma, tlo, thi, u);
-        tab[a * K_pad + k] = g;
-        S0.add(g);
-        S1.add(g * u);
-        S2.add(g * u * u);
+    // support of a uniform or truncated density: an interval of cells, since
+    // x_a is non-decreasing in a
+    int64_t in_b = a_begin, in_e = a_end;
+    if (kind == VUP_UNIFORM) {
+        const double half = __dmul_rn(0.5, sigma);
+        in_b = first_true(a_begin, a_end, [&](int64_t a) { return __dsub_rn(midpoint(lo, h, a), mu) >= -half; });
+        in_e = first_true(in_b, a_end, [&](int64_t a) { return !(__dsub_rn(midpoint(lo, h, a), mu) <= half); });
+    } else if (kind == VUP_TRUNCNORM) {
+        in_b = first_true(a_begin, a_end, [&](int64_t a) { return midpoint(lo, h, a) >= tlo; });
+        in_e = first_true(in_b, a_end, [&](int64_t a) { return !(midpoint(lo, h, a) <= thi); });
     }
+    KSum S0, S1, S2;
+    const double A0 = (double)a_begin - nk;
+    if (fabs(A0) + (double)(a_end - a_begin) < 16777216.0)
+        prep_segment<true>(tab + k, K_pad, kind, a_begin, a_end, in_b, in_e, ga, S0, S1, S2);
+    else
+        prep_segment<false>(tab + k, K_pad, kind, a_begin, a_end, in_b, in_e, ga, S0, S1, S2);
     if (z == 0) {
         DensConst dc;
         dc.n = (int32_t)fmax(fmin(nk, 2147483647.0), -2147483647.0);
