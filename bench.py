@@ -187,8 +187,11 @@ def traffic_for(kernel, workload):
     return None
 
 
-def roofline_for(name, ms, launches, KN, pk, clk_mhz, workload):
-    """Algorithmic work of one launch of `name` divided by its event-timed duration."""
+def roofline_for(name, ms, launches, KN, pk, clk_mhz, workload, hist_units=None):
+    """Algorithmic work of one launch of `name` divided by its event-timed duration.
+
+    hist_units: shared-memory factor gathers of one histogram launch (density x
+    point on the point stream, density x 2 per interval on the interval stream)."""
     per = ms / max(launches, 1) * 1e-3
     sms = 152
     tr = traffic_for(name, workload)
@@ -216,10 +219,12 @@ def roofline_for(name, ms, launches, KN, pk, clk_mhz, workload):
                 "traffic": tr, "note": f"{fl:g} FP32 flops/dist-point; peak = 152 SM x 128 FMA x 2 x median SM clock"}
     if name.startswith("hist_seg"):
         peak = sms * 128 * clk_mhz * 1e6 / 1e9
-        a = 4.0 * KN / launches / per / 1e9
+        units = hist_units if hist_units else KN / launches
+        a = 4.0 * units / per / 1e9
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": tr,
-                "note": "one 4-byte shared-memory factor gather per dist-point; peak = 152 SM x 128 B/clk "
-                        "shared-memory bandwidth x median SM clock"}
+                "note": "4-byte shared-memory factor gathers per launch (one per density and point on the "
+                        "point stream, two per density and interval on the interval stream); peak = 152 SM x "
+                        "128 B/clk shared-memory bandwidth x median SM clock"}
     a = 4.0 * KN / launches / per / 1e9
     return {"bound": "hbm", "achieved": a, "peak": pk["hbm"], "unit": "GB/s", "frac": a / pk["hbm"],
             "traffic": tr, "note": f"4 B/dist-point; peak = measured copy bandwidth, of {pk['source']}"}
@@ -306,6 +311,9 @@ class SingleGrid:
     def sync(self):
         self.g.sync()
 
+    def hist_grids(self):
+        return [(self.g, self.K)]
+
     def e2e(self):
         """Host buffers: inputs copied in, every output copied back, each step."""
         torch = self.torch
@@ -348,6 +356,9 @@ class Batched:
 
     def step(self, stream):
         self.call(self.prec, stream)
+
+    def hist_grids(self):
+        return [(g, p.K) for g, p in zip(self.grids, self.probs)]
 
     def sync(self):
         for g in self.grids:
@@ -402,6 +413,9 @@ class Weights:
         self.units = K * prob.N
         self.K = K
 
+    def hist_grids(self):
+        return []
+
     def step(self, stream):
         self.vup.vup_propagate_weights(self.g.h, self.W, self.raw, self.hist, stream)
 
@@ -435,6 +449,8 @@ def main():
     ap.add_argument("--k", type=int, default=0, help="use the first K densities of the workload (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--hist-stream", type=int, default=-1, choices=[-1, 0, 1],
+                    help="histogram stream: -1 automatic, 0 sorted points, 1 sorted intervals")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -462,6 +478,9 @@ def main():
     else:
         work = SingleGrid(args.config, args.k, prec, vup, torch)
     stream = torch.cuda.current_stream()
+    if args.hist_stream != -1:
+        for g, _ in work.hist_grids():
+            g.set_hist_stream(args.hist_stream)
 
     for _ in range(max(3, args.warmup)):
         work.step(stream)
@@ -534,10 +553,18 @@ def main():
     wl = args.config + (f"_k{work.K}" if args.k else "")
     dominant = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
     KN = work.units * args.steps
-    roof = roofline_for(dominant, prof[dominant][1], prof[dominant][0], KN, pk, clk_mhz, wl) if dominant else None
+    # gathers of one histogram launch on the stream each grid's layout chose
+    hist_units, streams = 0, set()
+    for g, K in work.hist_grids():
+        info = g.info()
+        if info.ndim >= 2:
+            streams.add("intervals" if info.hist_stream else "points")
+            hist_units += K * (2 * info.hist_intervals if info.hist_stream else info.N)
+    roof = (roofline_for(dominant, prof[dominant][1], prof[dominant][0], KN, pk, clk_mhz, wl, hist_units)
+            if dominant else None)
     if roof:
         roof["kernel"] = dominant
-    kern_roof = {k: roofline_for(k, v[1], v[0], KN, pk, clk_mhz, wl)
+    kern_roof = {k: roofline_for(k, v[1], v[0], KN, pk, clk_mhz, wl, hist_units)
                  for k, v in prof.items()
                  if k.startswith(("moments_bf16", "moments_fp32", "moments_tf32", "ipsa_bf16", "ipsa_fp32", "hist_seg",
                                   "weights"))}
@@ -558,6 +585,8 @@ def main():
            "l2": "flushed before every timed step (256 MB write, outside the step events)"}
     if args.k:
         cfg["k_subset"] = work.K
+    if streams:
+        cfg["hist_stream"] = "+".join(sorted(streams))
     if hasattr(work, "prob"):
         cfg.update({"N": work.prob.N, "bins": work.prob.n_bins, "moments": work.prob.n_moments})
     line = {

@@ -354,8 +354,25 @@ typedef struct {
     int32_t n_moments;
     double ymin, ymax, yscale;
     int32_t have_model;
+    /* histogram walk chosen for the current model (2-D / 3-D grids):
+     * layout 0 gathers the last axis, layout 1 axis 0 (2-D only); stream 0
+     * walks sorted points, stream 1 sorted intervals (stretches of one bin
+     * along the gathered axis, summed as differences of prefix sums).  Counts
+     * are those of the chosen layout. */
+    int32_t hist_layout, hist_stream;
+    int64_t hist_runs, hist_intervals;
 } vup_grid_info_t;
 vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info);
+
+/*
+ * Histogram stream choice of a 2-D / 3-D grid: -1 (default) picks, per model,
+ * the layout and stream with the least estimated work; 0 restricts the choice
+ * to point streams, 1 to interval streams.  Both give H[k, b] of Eq. 4 (sums
+ * of the same terms in a different order).  Takes effect for the current
+ * model (queued on `stream`) and for later ones.  VUP_ERR_INVALID_ARG for
+ * another value or a 1-D grid.
+ */
+vup_status vup_set_hist_stream(vup_grid g, int32_t stream_kind, vup_stream_t stream);
 
 /* Copy one of the grid's arrays into a caller device buffer (for checks).
  * which: 0 = y (double[N]), 1 = bin ids (int32[N]), 2 = sorted order

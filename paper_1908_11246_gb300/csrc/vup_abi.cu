@@ -81,7 +81,10 @@ ProfScope::ProfScope(const char *n, cudaStream_t s, int l) : name(n), stream(s),
 ProfScope::~ProfScope() {
     if (slot < 0) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (slot < (int)g_prof_recs.size()) cudaEventRecord(g_prof_recs[slot].b, stream);
+    if (slot < (int)g_prof_recs.size()) {
+        g_prof_recs[slot].launches = launches;  // a scope may count its launches as it goes
+        cudaEventRecord(g_prof_recs[slot].b, stream);
+    }
 }
 
 bool vup_profiling() { return g_prof_on; }
@@ -178,6 +181,10 @@ static void free_grid(vup_grid g) {
         cudaFree(L.chunk_pt);
         cudaFree(L.chunk_run);
         cudaFree(L.chunk_bin);
+        cudaFree(L.ipt);
+        cudaFree(L.iv_rest);
+        cudaFree(L.n_iv);
+        cudaFree(L.chunk_iv);
     }
     cudaFree(g->hist_sel);
     cudaFree(g->flags_scan);
@@ -283,15 +290,24 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
         ALLOC(L.chunk_pt, sizeof(int32_t) * (p_max * C + 1));
         ALLOC(L.chunk_run, sizeof(int32_t) * (p_max * C + 1));
         ALLOC(L.chunk_bin, sizeof(int32_t) * 2 * p_max * C);
+        if (ndim >= 2) {
+            ALLOC(L.ipt, sizeof(uint2) * (N + 128));  // tail slack for whole staged windows
+            ALLOC(L.iv_rest, sizeof(int32_t) * N);
+            ALLOC(L.n_iv, sizeof(int32_t));
+            ALLOC(L.chunk_iv, sizeof(int32_t) * (p_max * C + 1));
+            // words past the stream's end are read by whole-window staging and
+            // masked; zero keeps their rest codes valid indices
+            if (e == cudaSuccess) e = cudaMemset(L.ipt, 0, sizeof(uint2) * (N + 128));
+        }
     }
     if (ndim == 1) g->hl[0].perm = g->perm;
-    ALLOC(g->hist_sel, sizeof(int32_t));
+    ALLOC(g->hist_sel, sizeof(int32_t) * 2);
     ALLOC(g->flags_scan, sizeof(int32_t) * N);
     ALLOC(g->ydev_scale, sizeof(double));
     ALLOC(g->dstatus, sizeof(int));
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMemset(g->dstatus, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(g->hist_sel, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(g->hist_sel, 0, sizeof(int32_t) * 2);
     if (e != cudaSuccess) {
         vup_set_last_cuda_error(e, "vup_grid_create", __FILE__, __LINE__);
         cudaGetLastError();
@@ -549,7 +565,25 @@ extern "C" vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info) {
         info->ymin = inv(k[0]);
         info->ymax = inv(k[1]);
         info->yscale = sc;
+        if (g->ndim >= 2) {
+            int32_t sel[2] = {0, 0}, nr = 0, ni = 0;
+            VUP_CHECK_CUDA(cudaMemcpy(sel, g->hist_sel, sizeof(sel), cudaMemcpyDeviceToHost));
+            const auto &HL = g->hl[sel[0] == 1 && g->n_layouts > 1 ? 1 : 0];
+            VUP_CHECK_CUDA(cudaMemcpy(&nr, HL.n_runs, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            VUP_CHECK_CUDA(cudaMemcpy(&ni, HL.n_iv, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            info->hist_layout = sel[0];
+            info->hist_stream = sel[1];
+            info->hist_runs = nr;
+            info->hist_intervals = ni;
+        }
     }
+    return VUP_OK;
+}
+
+extern "C" vup_status vup_set_hist_stream(vup_grid g, int32_t stream_kind, vup_stream_t stream) {
+    if (!g || g->ndim < 2 || stream_kind < -1 || stream_kind > 1) return VUP_ERR_INVALID_ARG;
+    g->hist_force = stream_kind;
+    if (g->have_model) return vup_pick_hist_layout(g, (cudaStream_t)stream);
     return VUP_OK;
 }
 

@@ -52,7 +52,9 @@ extern "C" vup_status vup_posterior_means(vup_grid g, const vup_densities *d, fl
         hist = (float *)g_hist.p;
     }
     if ((st = vup_density_prep(g, d, 0, s)) != VUP_OK) return st;
-    if ((st = vup_hist_fused(g, K, hist, s)) != VUP_OK) return st;
+    // point stream: the ratios need the relative accuracy of low-mass bins,
+    // which differences of prefix sums (interval stream) do not keep
+    if ((st = vup_hist_fused(g, K, hist, s, nullptr, true)) != VUP_OK) return st;
     float *xtab = (float *)g_xtab.p;
     const float *ftab = (const float *)g->ftab.p;
     VUP_CHECK_CUDA(cudaMemcpyAsync(xtab, ftab, sizeof(float) * tab, cudaMemcpyDeviceToDevice, s));
@@ -65,7 +67,7 @@ extern "C" vup_status vup_posterior_means(vup_grid g, const vup_densities *d, fl
             k_weight_axis<<<(unsigned)ceil_div64(n * K_pad, 256), 256, 0, s>>>(ftab, xtab, row0, n, K_pad, g->lo[ax], h);
             VUP_CHECK_LAUNCH();
         }
-        if ((st = vup_hist_fused(g, K, (float *)g_hx.p + (size_t)ax * K * B, s, xtab)) != VUP_OK) return st;
+        if ((st = vup_hist_fused(g, K, (float *)g_hx.p + (size_t)ax * K * B, s, xtab, true)) != VUP_OK) return st;
         VUP_CHECK_CUDA(cudaMemcpyAsync(xtab + row0 * K_pad, ftab + row0 * K_pad, sizeof(float) * n * K_pad,
                                        cudaMemcpyDeviceToDevice, s));
         row0 += n;

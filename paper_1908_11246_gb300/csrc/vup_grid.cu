@@ -245,9 +245,33 @@ __global__ void k_natural_offsets(const int32_t *__restrict__ koff, int P, int B
     offsets[b] = s;
 }
 
-// The histogram walks the layout with fewer runs (less per-run work).
-__global__ void k_pick_layout(const int32_t *n_runs0, const int32_t *n_runs1, int32_t *sel) {
-    sel[0] = (n_runs1 && n_runs1[0] < n_runs0[0]) ? 1 : 0;
+// The histogram walks the layout and stream with the least estimated work,
+// in units of about 3.3 ps of kernel time per 128-density tile (fitted to
+// measured launches on 2-D and 3-D grids): point stream 4 per point (one
+// gather) + 20 per run (rest-factor pipeline); interval stream 19 per
+// interval (two gathers, a difference, a rest-factor load).
+__global__ void k_pick_layout(const int32_t *n_runs0, const int32_t *n_runs1, const int32_t *n_iv0,
+                              const int32_t *n_iv1, int64_t N, int force, int32_t *sel) {
+    int best_l = 0, best_m = 0;
+    int64_t best = INT64_MAX;
+    for (int l = 0; l < 2; ++l) {
+        const int32_t *nr = l == 0 ? n_runs0 : n_runs1, *ni = l == 0 ? n_iv0 : n_iv1;
+        if (!nr) continue;
+        const int64_t c_pt = force == 1 ? INT64_MAX - 1 : 4 * N + 20 * (int64_t)nr[0];
+        const int64_t c_iv = (ni && force != 0) ? 19 * (int64_t)ni[0] : INT64_MAX;
+        if (c_pt < best) {
+            best = c_pt;
+            best_l = l;
+            best_m = 0;
+        }
+        if (c_iv < best) {
+            best = c_iv;
+            best_l = l;
+            best_m = 1;
+        }
+    }
+    sel[0] = best_l;
+    sel[1] = best_m;
 }
 
 // Stable scatter: each warp walks its tile in order, 32 points at a time;
@@ -393,28 +417,27 @@ __global__ void k_run_build(const int32_t *__restrict__ perm, const int32_t *__r
 // the rest index itself; 3-D grids put a0 in the low field and a1 in the high
 // field.  Zero past the end.
 constexpr int kRunAhead = 4;
+__device__ __forceinline__ uint32_t rest_code(int32_t rest, int ndim, int64_t n1, int shift) {
+    const uint32_t lo_mask = (1u << shift) - 1u;
+    const uint32_t hi_mask = (1u << (30 - shift - kRowBits)) - 1u;
+    uint32_t lo, hi;
+    if (ndim == 3) {
+        lo = (uint32_t)(rest / n1);
+        hi = (uint32_t)(rest % n1);
+    } else {
+        lo = (uint32_t)rest & lo_mask;
+        hi = (uint32_t)rest >> shift;
+    }
+    return (lo & lo_mask) | ((hi & hi_mask) << (shift + kRowBits));
+}
 __global__ void k_run_encode(const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_rest,
                              const int32_t *__restrict__ n_runs_p, int ndim, int64_t n1, int shift,
                              uint32_t *__restrict__ hpt) {
     const int32_t n_runs = n_runs_p[0];
-    const uint32_t lo_mask = (1u << shift) - 1u;
-    const uint32_t hi_mask = (1u << (30 - shift - kRowBits)) - 1u;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_runs;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ra = r + kRunAhead;
-        uint32_t code = 0;
-        if (ra < n_runs) {
-            const int32_t rest = run_rest[ra];
-            uint32_t lo, hi;
-            if (ndim == 3) {
-                lo = (uint32_t)(rest / n1);
-                hi = (uint32_t)(rest % n1);
-            } else {
-                lo = (uint32_t)rest & lo_mask;
-                hi = (uint32_t)rest >> shift;
-            }
-            code = (lo & lo_mask) | ((hi & hi_mask) << (shift + kRowBits));
-        }
+        const uint32_t code = ra < n_runs ? rest_code(run_rest[ra], ndim, n1, shift) : 0u;
         hpt[run_start[r + 1] - 1] |= code;
     }
 }
@@ -473,6 +496,67 @@ __global__ void k_key_chunks(const int32_t *__restrict__ koff, int n_keys, const
     const int32_t o0 = koff[key], o1 = koff[key + 1];
     out[key] = o0 == o1 ? make_int2(-1, -1)
                         : make_int2(chunk_holding(chunk_pt, n_chunks, o0), chunk_holding(chunk_pt, n_chunks, o1 - 1));
+}
+
+// ---- interval stream -------------------------------------------------------
+// An interval is a maximal stretch of a run whose gathered-axis rows are
+// consecutive (the points of one bin along one line of the grid).  The
+// histogram kernel sums an interval's factors as the difference of two
+// prefix sums of the part's factor tile, so its cost does not grow with the
+// interval's length.  Interval i's word pair: x = first row << shift,
+// y = (last row + 1) << shift | run-end / key-end flags of its last point |
+// rest code of interval i + 4 (every interval loads its own rest factor,
+// four intervals ahead; same code fields as the point words).
+__global__ void k_iv_flags(const uint32_t *__restrict__ hpt, int64_t N, int shift, int32_t *__restrict__ flags) {
+    const uint32_t rmask = (1u << kRowBits) - 1u;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int32_t f = 1;
+        if (t > 0) {
+            const uint32_t u = hpt[t - 1], v = hpt[t];
+            f = (u & kRunEnd) || ((v >> shift) & rmask) != ((u >> shift) & rmask) + 1u;
+        }
+        flags[t] = f;
+    }
+}
+
+__global__ void k_iv_build(const uint32_t *__restrict__ hpt, const int32_t *__restrict__ perm, int64_t N,
+                           int64_t n_last, int shift, const int32_t *__restrict__ flags,
+                           const int32_t *__restrict__ excl, uint2 *__restrict__ ipt,
+                           int32_t *__restrict__ iv_rest, int32_t *__restrict__ n_iv) {
+    const uint32_t rmask = (1u << kRowBits) - 1u;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t f = flags[t];
+        const int64_t id = (int64_t)excl[t] + f - 1;
+        const uint32_t h = hpt[t];
+        const uint32_t row = (h >> shift) & rmask;
+        uint32_t *w = reinterpret_cast<uint32_t *>(ipt + id);
+        if (f) {
+            w[0] = row << shift;
+            iv_rest[id] = (int32_t)(perm[t] / n_last);
+        }
+        if (t == N - 1 || flags[t + 1]) w[1] = (((row + 1u) & rmask) << shift) | (h & (kRunEnd | kBinEnd));
+        if (t == N - 1) n_iv[0] = (int32_t)(id + 1);
+    }
+}
+
+__global__ void k_iv_encode(const int32_t *__restrict__ iv_rest, const int32_t *__restrict__ n_iv_p, int ndim,
+                            int64_t n1, int shift, uint2 *__restrict__ ipt) {
+    const int32_t n = n_iv_p[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ia = i + kRunAhead;
+        if (ia < n) reinterpret_cast<uint32_t *>(ipt + i)[1] |= rest_code(iv_rest[ia], ndim, n1, shift);
+    }
+}
+
+// First interval of every chunk (chunks start on run starts, which start intervals).
+__global__ void k_chunk_iv(const int32_t *__restrict__ chunk_pt, const int32_t *__restrict__ excl, int64_t N,
+                           const int32_t *__restrict__ n_iv_p, int n, int32_t *__restrict__ chunk_iv) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > n) return;
+    const int32_t pt = chunk_pt[c];
+    chunk_iv[c] = pt < N ? excl[pt] : n_iv_p[0];
 }
 
 // ---- power tables -----------------------------------------------------------
@@ -580,6 +664,12 @@ static int64_t scan_scratch_ints(int64_t L) {
     for (int64_t nb = ceil_div64(L, kScanBlock); nb > 1; nb = ceil_div64(nb, kScanBlock))
         total += 2 * nb + 64;
     return total + 64;
+}
+
+// Kernel launches of scan_exclusive over L elements.
+static int scan_launches(int64_t L) {
+    const int64_t nb = ceil_div64(L, kScanBlock);
+    return nb <= 1 ? 1 : 2 + scan_launches(nb);
 }
 
 static vup_status scan_exclusive(const int32_t *in, int32_t *out, int64_t L, int32_t *scratch,
@@ -697,7 +787,8 @@ vup_status vup_natural_sort(vup_grid g, cudaStream_t s) {
 vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     const int64_t N = g->N;
     const int B = g->B;
-    VUP_PROF("range_bins_sort_runs", s, g->ndim == 2 ? 36 : 20);
+    ProfScope prof("range_bins_sort_runs", s, 0);
+    int launches = 3;  // minmax, scale, bins
     // exact range of y
     VUP_CHECK_CUDA(cudaMemsetAsync(g->ext, 0xff, sizeof(unsigned long long), s));
     VUP_CHECK_CUDA(cudaMemsetAsync(g->ext + 1, 0x00, sizeof(unsigned long long), s));
@@ -773,6 +864,10 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
             const int Bk = HL.P * B;
             st = counting_sort(g, HL.keys, Bk, HL.perm, HL.koff, counts, scratch, false, s);
             if (st != VUP_OK) return st;
+            // transpose, keys, sort (count, scan, scatter, koff end), runs (flags, scan, build,
+            // encode, chunks, chunk keys, key chunks), intervals (flags, scan, build, encode, chunk starts)
+            launches += (l == 1) + (HL.P > 1) + 3 + scan_launches((int64_t)Bk * n_tiles) + 5 + scan_launches(N) +
+                        4 + scan_launches(N);
             // runs and chunks
             const int64_t n_last = HL.n_last;
             int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
@@ -795,13 +890,36 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
             VUP_CHECK_LAUNCH();
             k_key_chunks<<<(Bk + 127) / 128, 128, 0, s>>>(HL.koff, Bk, HL.chunk_pt, PC, HL.key_chunks);
             VUP_CHECK_LAUNCH();
+            // interval stream
+            k_iv_flags<<<rb, 256, 0, s>>>(HL.hpt, N, kRowShift, g->flags_scan);
+            VUP_CHECK_LAUNCH();
+            st = scan_exclusive(g->flags_scan, excl, N, scratch, s);
+            if (st != VUP_OK) return st;
+            k_iv_build<<<rb, 256, 0, s>>>(HL.hpt, HL.perm, N, n_last, kRowShift, g->flags_scan, excl, HL.ipt,
+                                          HL.iv_rest, HL.n_iv);
+            VUP_CHECK_LAUNCH();
+            k_iv_encode<<<rb, 256, 0, s>>>(HL.iv_rest, HL.n_iv, g->ndim, g->ndim == 3 ? g->n[1] : 1, kRowShift,
+                                           HL.ipt);
+            VUP_CHECK_LAUNCH();
+            k_chunk_iv<<<(PC + 1 + 127) / 128, 128, 0, s>>>(HL.chunk_pt, excl, N, HL.n_iv, PC, HL.chunk_iv);
+            VUP_CHECK_LAUNCH();
         }
         k_natural_offsets<<<(B + 1 + 127) / 128, 128, 0, s>>>(g->hl[0].koff, g->hl[0].P, B, N, g->offsets);
         VUP_CHECK_LAUNCH();
-        k_pick_layout<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->n_layouts > 1 ? g->hl[1].n_runs : nullptr, g->hist_sel);
-        VUP_CHECK_LAUNCH();
+        st = vup_pick_hist_layout(g, s);
+        if (st != VUP_OK) return st;
+        launches += 2;
     }
+    prof.launches = launches;
     for (int o = 0; o < kNumOrient; ++o) g->have_tab[o][0] = g->have_tab[o][1] = g->have_tab[o][2] = 0;
+    return VUP_OK;
+}
+
+vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s) {
+    const bool two = g->n_layouts > 1;
+    k_pick_layout<<<1, 1, 0, s>>>(g->hl[0].n_runs, two ? g->hl[1].n_runs : nullptr, g->hl[0].n_iv,
+                                  two ? g->hl[1].n_iv : nullptr, g->N, g->hist_force, g->hist_sel);
+    VUP_CHECK_LAUNCH();
     return VUP_OK;
 }
 

@@ -47,6 +47,8 @@ struct LayoutArgs {
     const int32_t *chunk_pt, *chunk_run, *chunk_bin;
     const int32_t *koff;   // key offsets [P * B + 1]
     const int2 *key_chunks;  // [P * B] first / last chunk of each key (-1 if empty)
+    const uint2 *ipt;      // interval stream (word pairs)
+    const int32_t *iv_rest, *chunk_iv;
     const float *g_last;   // factor table of the gathered axis  [n_last][K_pad]
     const float *g0, *g1;  // rest-axis factor tables (g1 only for 3-D)
     int64_t n_last, part_rows;
@@ -56,13 +58,14 @@ struct LayoutArgs {
 
 struct HistArgs {
     LayoutArgs L0, L1;
-    const int32_t *sel;   // device: chosen layout
+    const int32_t *sel;   // device: chosen layout, stream (1 = intervals)
     const DensStats *ds;
     int ndim;
     int64_t K, K_pad;
     int B;
     int C;                // chunks per part
     int group_chunks;     // chunks per work item (a multiple of kGroupChunks dividing C)
+    int points_only;      // 1: point stream whatever the layout choice says
     float *hist;          // [K][B]
     float *part;          // [P * C][2][K_pad]
     float *direct;        // [P][K][B] (P > 1)
@@ -178,6 +181,7 @@ struct ItemCtx {
     float *out;    // [K][B] whole-key sums of this part (hist, or direct + p K B)
     int64_t K, K_pad;
     int B, C, group_chunks;
+    int mode;      // 0: point stream, tile holds factors; 1: interval stream, tile holds prefix sums
     int *dstatus;
 };
 
@@ -198,6 +202,137 @@ __device__ __noinline__ void flush_key(const ItemCtx *X, int c, int p, int64_t k
         if (k + 2 < K) o[2 * B] = v.z;
         if (k + 3 < K) o[3 * B] = v.w;
     }
+}
+
+// Interval stream of chunk c (part p): interval i adds f_i (P[b_i] - P[a_i])
+// to its key's sum for the lane's four densities, P being the part's prefix
+// sums in the shared-memory tile and f_i its rest-axis factor.  Every
+// interval loads its own rest factor four intervals ahead into one of four
+// registers (the interval's index mod 4), so the loop runs in steps of four
+// intervals (two 16-byte broadcast loads of word pairs) and rotates nothing.
+template <int NF>
+__device__ __forceinline__ bool iv_chunk(const ItemCtx &X, int c, int p, int64_t k, const float *ws, uint32_t *win,
+                                         uint64_t *mbar, uint32_t &wseq, volatile int *abort) {
+    const LayoutArgs &H = X.H;
+    const int lane = threadIdx.x & 31;
+    const int32_t p0 = H.chunk_pt[c], p1 = H.chunk_pt[c + 1];
+    if (p0 >= p1) return true;
+    const int32_t i0 = H.chunk_iv[c], i1 = H.chunk_iv[c + 1];
+    const int32_t r0 = H.chunk_run[c], r1 = H.chunk_run[c + 1];
+    const int32_t first_key = H.chunk_bin[2 * c], last_key = H.chunk_bin[2 * c + 1];
+    const bool sh_first = H.koff[first_key] < p0 || H.koff[first_key + 1] > p1;
+    const bool sh_last = H.koff[last_key] < p0 || H.koff[last_key + 1] > p1;
+
+    // words [w0, w1): intervals from i0 rounded down to a multiple of four
+    const int32_t ib = i0 & ~3;
+    const int32_t w0 = 2 * ib, w1 = 2 * i1;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(H.ipt);
+    const int32_t wb0 = w0 & ~(kWin - 1);
+    if (lane == 0) {
+        const int b0 = wseq & 1;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of both buffers
+        bulk_copy(win + b0 * kWin, src + wb0, kWin * 4, &mbar[b0]);
+        if (wb0 + kWin < w1) bulk_copy(win + (b0 ^ 1) * kWin, src + wb0 + kWin, kWin * 4, &mbar[b0 ^ 1]);
+    }
+    __syncwarp();
+
+    // rest-factor rows: this lane's four densities of row `row` (byte stride)
+    const uint32_t stride = (uint32_t)(X.K_pad * 4);
+    const char *g0b = reinterpret_cast<const char *>(H.g0 + k);
+    const char *g1b = NF == 2 ? reinterpret_cast<const char *>(H.g1 + k) : nullptr;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto row4 = [&](const char *base, uint32_t row) -> float4 {
+        return *reinterpret_cast<const float4 *>(base + (uint64_t)row * stride);
+    };
+    // factor of interval i + 4 from interval i's code: 9 low bits below the row
+    // field and 12 bits above it (2-D: the rest index; 3-D: a0 low, a1 high)
+    auto coded_factor = [&](uint32_t u) -> float4 {
+        if (NF == 2) return mul4(row4(g0b, u & 0x1ffu), row4(g1b, (u >> 18) & 0xfffu));
+        return row4(g0b, (u & 0x1ffu) | ((u >> 9) & (0xfffu << 9)));
+    };
+    auto first_factor = [&](int32_t i) -> float4 {
+        if (i < i0 || i >= i1) return zero4;
+        const int32_t rest = H.iv_rest[i];
+        if (NF == 2) {
+            const int32_t a0 = rest / (int32_t)H.n1;
+            return mul4(row4(g0b, (uint32_t)a0), row4(g1b, (uint32_t)(rest - a0 * (int32_t)H.n1)));
+        }
+        return row4(g0b, (uint32_t)rest);
+    };
+    float4 f0 = first_factor(ib), f1 = first_factor(ib + 1), f2 = first_factor(ib + 2), f3 = first_factor(ib + 3);
+
+    float4 bacc = zero4;
+    int32_t r = r0, cur_key = first_key;
+    const uint32_t wsl = smem_u32(ws) + lane * 16;
+    auto gather = [&](uint32_t addr) -> float4 {
+        float4 v;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "r"(addr));
+        return v;
+    };
+    auto flush = [&](int32_t key, float4 v) {
+        const bool first = key == first_key;
+        flush_key(&X, c, p, k, key, v, first ? sh_first : (key == last_key && sh_last), first);
+    };
+    auto step = [&](uint32_t x, uint32_t y, float4 &f) {
+        const float4 pa = gather(wsl + x), pb = gather(wsl + (y & kOffMask));
+        const float4 d = make_float4(pb.x - pa.x, pb.y - pa.y, pb.z - pa.z, pb.w - pa.w);
+        fma4(bacc, f, d);
+        f = coded_factor(y);
+        if (y & kBinEnd) {
+            flush(cur_key, bacc);
+            bacc = zero4;
+            cur_key = r + 1 < r1 ? H.run_bin[r + 1] : -1;
+        }
+        r += (y >> 30) & 1u;  // run end
+    };
+    // foreign intervals read row 0 twice (difference 0) and carry no flags;
+    // those before the chunk keep their rest codes (they load the chunk's first factors)
+    constexpr uint32_t kCodes = ~(kOffMask | kFlags);
+    auto masked = [&](uint32_t &x, uint32_t &y, int32_t i) {
+        if (i < i0) {
+            x = 0u;
+            y &= kCodes;
+        } else if (i >= i1) {
+            x = 0u;
+            y = 0u;
+        }
+    };
+
+    for (int32_t wbase = wb0; wbase < w1; wbase += kWin, ++wseq) {
+        const int b = wseq & 1;
+        for (uint32_t i = 0; !mbar_try_wait(&mbar[b], (wseq >> 1) & 1); ++i) {
+            if (i > kSpin || *abort) {  // a staged copy never landed: record and stop
+                *abort = 1;
+                atomicCAS(X.dstatus, 0, VUP_DSTAT_TIMEOUT);
+                return false;
+            }
+        }
+        const uint32_t *wv = win + b * kWin;
+        const int lo = (w0 > wbase ? w0 : wbase) - wbase;
+        const int hi = (w1 < wbase + kWin ? w1 : wbase + kWin) - wbase;
+        for (int q = lo; q < hi; q += 8) {
+            uint4 u0 = *reinterpret_cast<const uint4 *>(wv + q), u1 = *reinterpret_cast<const uint4 *>(wv + q + 4);
+            const int32_t iq = (wbase + q) >> 1;
+            if (iq < i0 || iq + 4 > i1) {
+                masked(u0.x, u0.y, iq);
+                masked(u0.z, u0.w, iq + 1);
+                masked(u1.x, u1.y, iq + 2);
+                masked(u1.z, u1.w, iq + 3);
+            }
+            step(u0.x, u0.y, f0);
+            step(u0.z, u0.w, f1);
+            step(u1.x, u1.y, f2);
+            step(u1.z, u1.w, f3);
+        }
+        __syncwarp();
+        if (lane == 0 && wbase + 2 * kWin < w1) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bulk_copy(win + b * kWin, src + wbase + 2 * kWin, kWin * 4, &mbar[b]);
+        }
+    }
+    if (cur_key >= 0) flush(cur_key, bacc);
+    return true;
 }
 
 // One work item: part p, chunk group cg (kGroupChunks chunks, drawn by the
@@ -231,6 +366,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         X.B = A.B;
         X.C = A.C;
         X.group_chunks = A.group_chunks;
+        X.mode = A.points_only ? 0 : A.sel[1];
         X.dstatus = A.dstatus;
     }
     if (threadIdx.x < kKT) s_invz[threadIdx.x] = inv_z(*Ap, k0 + threadIdx.x);
@@ -254,7 +390,48 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     if (threadIdx.x < kKT) ws[nrows * kKT + threadIdx.x] = 0.f;
     cp_async_wait_all();
     __syncthreads();
-    for (int64_t e = threadIdx.x; e < nrows * kKT; e += blockDim.x) ws[e] *= s_invz[e % kKT];
+    if (X.mode) {
+        // interval stream: every column becomes the exclusive prefix sums
+        // P[0..nrows] of its scaled factors (compensated sums, each P rounded
+        // once to FP32), so that rows a .. b - 1 sum to P[b] - P[a].  The
+        // rows are cut into kScanSegs segments, one thread per (segment,
+        // column): segment totals first (kept in the idle staging buffers),
+        // then each segment rescanned from the sum of the totals before it.
+        constexpr int kScanSegs = kHistWarps * 32 / kKT;
+        const int col = threadIdx.x % kKT, sg = threadIdx.x / kKT;
+        const int64_t rs = (nrows + kScanSegs - 1) / kScanSegs;
+        const int64_t a0 = min(nrows, sg * rs), a1 = min(nrows, a0 + rs);
+        const float iz = s_invz[col];
+        float *tcol = ws + col;
+        float2 *segsum = reinterpret_cast<float2 *>(sm + tb);  // [kScanSegs][kKT]
+        auto add = [](float &sh, float &sl, float v) {
+            const float t = sh + v, bb = t - sh;
+            sl += (sh - (t - bb)) + (v - bb);
+            sh = t;
+        };
+        {
+            float sh = 0.f, sl = 0.f;
+            for (int64_t a = a0; a < a1; ++a) add(sh, sl, tcol[a * kKT] * iz);
+            segsum[sg * kKT + col] = make_float2(sh, sl);
+        }
+        __syncthreads();
+        float oh = 0.f, ol = 0.f;
+        for (int q = 0; q < sg; ++q) {
+            const float2 v = segsum[q * kKT + col];
+            add(oh, ol, v.x);
+            ol += v.y;
+        }
+        for (int64_t a = a0; a < a1; ++a) {
+            const float v = tcol[a * kKT] * iz;
+            tcol[a * kKT] = oh + ol;
+            add(oh, ol, v);
+        }
+        if (a1 == nrows && (a0 < a1 || sg == 0)) tcol[nrows * kKT] = oh + ol;
+        // the staging buffers are next written by bulk copies (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    } else {
+        for (int64_t e = threadIdx.x; e < nrows * kKT; e += blockDim.x) ws[e] *= s_invz[e % kKT];
+    }
     __syncthreads();
 
     // the item's chunks are handed out one at a time (at least kChunksPerWarp per warp
@@ -400,12 +577,16 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         if (cur_key >= 0) flush(cur_key, bacc);
         return true;
     };
+    const bool iv = X.mode != 0;
     for (;;) {
         int ci = 0;
         if (lane == 0) ci = atomicAdd(next_chunk, 1);
         ci = __shfl_sync(0xffffffffu, ci, 0);
         if (ci >= X.group_chunks) break;
-        if (!run_chunk(cg * X.group_chunks + ci)) return;
+        const int wc = cg * X.group_chunks + ci;
+        const bool ok = iv ? iv_chunk<NF>(X, p * X.C + wc, p, k, ws, win, mbar, wseq, abort)
+                           : run_chunk(wc);
+        if (!ok) return;
     }
 }
 
@@ -607,6 +788,9 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
         La.chunk_bin = HL.chunk_bin;
         La.koff = HL.koff;
         La.key_chunks = HL.key_chunks;
+        La.ipt = HL.ipt;
+        La.iv_rest = HL.iv_rest;
+        La.chunk_iv = HL.chunk_iv;
         La.g_last = tab(HL.last_axis);
         if (nd == 3) {
             La.g0 = tab(0);
@@ -637,11 +821,13 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
     return A;
 }
 
-vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab) {
+vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab,
+                          bool points_only) {
     const int nd = g->ndim;
     int64_t rows;
     int P_max;
     HistArgs A = hist_args_for(g, K, hist, rows, P_max, ftab);
+    A.points_only = points_only ? 1 : 0;
     const size_t smem = hist_smem_bytes(rows);
     // run-end words encode the rest index in 21 bits (3-D: a0 < 512, a1 < 4096)
     const bool coded = nd == 2 || (g->n[0] <= 512 && g->n[1] <= 4096);

@@ -120,10 +120,18 @@ struct vup_grid_s {
         int32_t *chunk_pt = nullptr;   // [P * n_chunks + 1] chunk start (point index)
         int32_t *chunk_run = nullptr;  // [P * n_chunks + 1] chunk start (run index)
         int32_t *chunk_bin = nullptr;  // [P * n_chunks * 2] first / last key of each chunk
+        // interval stream: maximal stretches of a run whose gathered-axis rows
+        // are consecutive; uint2 (first row << shift, (last row + 1) << shift |
+        // run-end / key-end flags | rest code of interval + 4)
+        uint2 *ipt = nullptr;          // [N + 128]
+        int32_t *iv_rest = nullptr;    // [N] rest index of each interval
+        int32_t *n_iv = nullptr;       // [1] device
+        int32_t *chunk_iv = nullptr;   // [P * n_chunks + 1] chunk start (interval index)
     } hl[2];
     int hist_P = 1;                // max parts over layouts (scratch sizing)
     int n_layouts = 1;
-    int32_t *hist_sel = nullptr;   // [1] device: chosen layout
+    int32_t *hist_sel = nullptr;   // [2] device: chosen layout, 1 = interval stream
+    int hist_force = -1;           // -1 auto, 0 points only, 1 intervals only
     int32_t *flags_scan = nullptr; // [N] scratch
     int32_t n_chunks = 0;
 
@@ -150,6 +158,7 @@ vup_status vup_launch_model_at(vup_grid g, int64_t K, const double *x, double *y
 vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta,
                                  cudaStream_t s);
 vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s);  // range, bins, sort, runs, tables
+vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s);
 vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s);
 vup_status vup_natural_sort(vup_grid g, cudaStream_t s);
 
@@ -166,7 +175,11 @@ vup_status vup_moments_finish(vup_grid g, int64_t K, int n_col_tiles, double *ra
                               double *central, cudaStream_t s);
 // Segmented histogram of the K densities; `ftab` replaces the grid's factor
 // tables when not null (same layout), e.g. tables weighted by a coordinate.
-vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab = nullptr);
+// points_only: walk the point stream even where the interval stream was
+// chosen (sums that must keep their relative accuracy in low-mass bins, as
+// the numerators and denominators of ratios do).
+vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab = nullptr,
+                          bool points_only = false);
 vup_status vup_propagate_1d(vup_grid g, const vup_densities *d, double *raw, double *central,
                             float *hist, cudaStream_t s);
 vup_status vup_ipsa_1d(vup_grid g, const vup_densities *d, const double *grad, float *dmu,

@@ -27,7 +27,7 @@ ABI_SYMBOLS = [
     "vup_grid_create", "vup_grid_destroy", "vup_eval_model", "vup_set_outputs", "vup_propagate",
     "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_batched_report", "vup_sync", "vup_selftest_wait", "vup_model_at",
     "vup_deviation_moments", "vup_ipsa_matrix", "vup_sa_fields", "vup_posterior_means",
-    "vup_grid_info", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
+    "vup_grid_info", "vup_set_hist_stream", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
     "vup_profile_read",
 ]
 
@@ -40,7 +40,8 @@ class vup_densities(C.Structure):
 class vup_grid_info_t(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("n", C.c_int64 * 3), ("N", C.c_int64), ("n_bins", C.c_int32),
                 ("n_moments", C.c_int32), ("ymin", C.c_double), ("ymax", C.c_double),
-                ("yscale", C.c_double), ("have_model", C.c_int32)]
+                ("yscale", C.c_double), ("have_model", C.c_int32), ("hist_layout", C.c_int32),
+                ("hist_stream", C.c_int32), ("hist_runs", C.c_int64), ("hist_intervals", C.c_int64)]
 
 
 class VUPError(RuntimeError):
@@ -79,6 +80,7 @@ def lib():
         l.vup_sa_fields.argtypes = [i64, C.c_int, vp, C.c_double, vp, vp, vp, vp, vp]
         l.vup_posterior_means.argtypes = [vp, C.POINTER(vup_densities), vp, vp, vp]
         l.vup_grid_info.argtypes = [vp, C.POINTER(vup_grid_info_t)]
+        l.vup_set_hist_stream.argtypes = [vp, C.c_int32, vp]
         l.vup_grid_copy.argtypes = [vp, C.c_int, vp, C.c_size_t, vp]
         l.vup_profile.argtypes = [C.c_int]
         l.vup_profile_read.argtypes = [C.c_char_p, C.c_size_t]
@@ -267,6 +269,11 @@ def vup_grid_info(h):
     return info
 
 
+def vup_set_hist_stream(h, kind: int, stream=None):
+    """Histogram stream choice: -1 auto, 0 sorted points, 1 sorted intervals."""
+    _check(lib().vup_set_hist_stream(h, int(kind), _stream(stream)), "vup_set_hist_stream")
+
+
 def vup_grid_copy(h, which, out, stream=None):
     _check(lib().vup_grid_copy(h, int(which), _ptr(out), out.numel() * out.element_size(), _stream(stream)),
            "vup_grid_copy")
@@ -353,6 +360,10 @@ class Grid:
 
     def info(self):
         return vup_grid_info(self.h)
+
+    def set_hist_stream(self, kind: int, stream=None):
+        """-1: automatic choice; 0: sorted points; 1: sorted intervals."""
+        vup_set_hist_stream(self.h, kind, stream)
 
     def array(self, which):
         import torch

@@ -1,0 +1,136 @@
+"""Histogram streams: sorted points vs sorted intervals (Eq. 4), both against the FP64 oracle.
+
+The interval stream sums each stretch of one bin along the gathered axis as a
+difference of prefix sums of the factor tile; the point stream adds every
+point.  Both are forced in turn on every case and must meet the histogram
+tolerance (1e-6 absolute per bin).  The run and interval counts the device
+reports are checked exactly against a count from the oracle's bins.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1908_11246_gb300 import inputs as I
+from tests import helpers as Hp
+
+pytestmark = pytest.mark.gpu
+
+MAX_PART_ROWS = 392
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_1908_11246_gb300 import build
+    build.build()
+
+
+def _cases():
+    return [
+        I.config("c2", "small"), I.config("c3", "small"), I.config("c4", "small"),
+        I.random_problem(301, ndim=2), I.random_problem(302, ndim=3), I.random_problem(303, ndim=2),
+        I.Problem("ipsa_ex", (300, 120), (-5.0, -1.5), (5.0, 1.5), I.MODEL_IPSA_EXAMPLE_2D, (),
+                  I.random_densities(np.random.default_rng(31), 200, (-5.0, -1.5), (5.0, 1.5),
+                                     sig=(0.05, 0.8)), 1000),
+        # gathered axis of 900 rows: three parts of 300 rows
+        I.Problem("parts3", (900, 70), (-3.0, -2.0), (3.0, 2.0), I.MODEL_SIN_SIN2_2D, (1.0, 7.0),
+                  I.random_densities(np.random.default_rng(32), 300, (-3.0, -2.0), (3.0, 2.0),
+                                     sig=(0.02, 0.8)), 64),
+    ]
+
+
+CASES = _cases()
+
+
+def layout_counts(bins_nd, B, layout):
+    """Runs and intervals of a layout, counted from the bins on the host.
+
+    layout 0 gathers the last axis, layout 1 (2-D) axis 0.  The gathered axis
+    is cut into parts of ceil(n / P) rows, P = ceil(n / 392) (one part when
+    P * B > 32768); runs are maximal stretches of one (part, bin) key and one
+    rest index in the stable sort by key, intervals the stretches of a run
+    whose gathered rows are consecutive.
+    """
+    b = bins_nd if layout == 0 else bins_nd.T
+    n_last = b.shape[-1]
+    b = b.reshape(-1, n_last)
+    P = -(-n_last // MAX_PART_ROWS)
+    if P * B > 32768:
+        P = 1
+    pr = -(-n_last // P)
+    R = b.shape[0]
+    a = np.tile(np.arange(n_last), R)
+    rest = np.repeat(np.arange(R), n_last)
+    key = (a // pr) * B + b.ravel()
+    order = np.argsort(key, kind="stable")
+    k, r, aa = key[order], rest[order], a[order]
+    new_run = np.ones(k.size, bool)
+    new_run[1:] = (k[1:] != k[:-1]) | (r[1:] != r[:-1])
+    new_iv = new_run.copy()
+    new_iv[1:] |= aa[1:] != aa[:-1] + 1
+    return int(new_run.sum()), int(new_iv.sum())
+
+
+def run_stream(prob, kind, rows=None):
+    from paper_1908_11246_gb300 import vup
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.eval_model(prob.model_id, prob.theta, prob.n_bins, prob.n_moments)
+    g.set_hist_stream(kind)
+    dd = vup.densities_to_device(prob.dens)
+    _, _, hs = g.propagate(dd, "fp32", False, False, True)
+    g.sync()
+    info = g.info()
+    b_g = g.array("bins").cpu().numpy()
+    hs = hs.cpu().numpy()
+    g.close()
+    return hs if rows is None else hs[rows], info, b_g
+
+
+@pytest.mark.parametrize("prob", CASES, ids=[p.name for p in CASES])
+def test_point_and_interval_streams_match_oracle(prob):
+    res = O.solve(prob, threads=Hp.oracle_threads())
+    amb = Hp.ambiguous_points(res["y"], res["bins"], prob.n_bins)
+    amb_mass = 0.0
+    if amb.any():
+        for k in range(prob.K):
+            W, _ = O.weights(prob.n, prob.lo, prob.hi, prob.dens, k)
+            amb_mass = max(amb_mass, float(W[amb].sum()))
+    out = {}
+    for kind in (0, 1):
+        hs, info, b_g = run_stream(prob, kind)
+        assert info.hist_stream == kind
+        Hp.check_hist(hs, res["hist"], amb_mass)
+        # the device's run and interval counts for its chosen layout, from its own bins
+        runs, ivs = layout_counts(b_g.reshape(prob.n), prob.n_bins, info.hist_layout)
+        assert (info.hist_runs, info.hist_intervals) == (runs, ivs)
+        out[kind] = hs
+    # the two orders of summation agree within the sum of their bounds
+    assert np.abs(out[0].astype(np.float64) - out[1]).max() <= 2 * (1e-6 + amb_mass)
+
+
+@pytest.mark.parametrize("name,expect", [("c2", (1, 1)), ("c3", (0, 0)), ("c4", (1, 1))])
+def test_automatic_choice_takes_the_cheaper_stream(name, expect):
+    """Full-size workloads.  c2 / c4: gathering axis 0 gives runs of ~9 / ~18
+    points in ~1.07 intervals each, so layout 1's interval stream is cheapest.
+    c3 (3-D): intervals average 1.8 points, so the point stream is."""
+    prob = I.config(name)
+    rows = np.array([0, 1, 4097, prob.K - 1])
+    hs, info, b_g = run_stream(prob, -1, rows=rows)
+    assert (info.hist_layout, info.hist_stream) == expect
+    runs, ivs = layout_counts(b_g.reshape(prob.n), prob.n_bins, info.hist_layout)
+    assert (info.hist_runs, info.hist_intervals) == (runs, ivs)
+    res = O.solve(prob, rows=rows, threads=Hp.oracle_threads())
+    Hp.check_hist(hs, res["hist"])
+
+
+def test_stream_choice_argument_errors():
+    from paper_1908_11246_gb300 import vup
+    g = vup.Grid((16,), (0.0,), (1.0,))
+    with pytest.raises(vup.VUPError):
+        g.set_hist_stream(1)  # 1-D grids have no layout stream
+    g.close()
+    g = vup.Grid((16, 8), (0.0, 0.0), (1.0, 1.0))
+    for bad in (-2, 2):
+        with pytest.raises(vup.VUPError):
+            g.set_hist_stream(bad)
+    g.set_hist_stream(0)  # before a model: kept for the next one
+    g.close()
