@@ -166,10 +166,9 @@ static void free_grid(vup_grid g) {
     cudaFree(g->bins);
     cudaFree(g->perm);
     cudaFree(g->offsets);
-    for (int l = 0; l < 2; ++l) {
-        auto &L = g->hl[l];
+    {  // the built layout's arrays (hl[1] aliases them)
+        auto &L = g->hl[0];
         if (L.perm != g->perm) cudaFree(L.perm);
-        cudaFree(L.binsT);
         cudaFree(L.keys_own);
         cudaFree(L.koff);
         cudaFree(L.key_chunks);
@@ -187,7 +186,6 @@ static void free_grid(vup_grid g) {
         cudaFree(L.chunk_iv);
     }
     cudaFree(g->hist_sel);
-    cudaFree(g->flags_scan);
     cudaFree(g->ydev_scale);
     cudaFree(g->dstatus);
     for (int o = 0; o < kNumOrient; ++o) {
@@ -199,6 +197,7 @@ static void free_grid(vup_grid g) {
     }
     devbuf_free(g->sort_counts);
     devbuf_free(g->scan_tmp);
+    devbuf_free(g->lay_tmp);
     devbuf_free(g->dconst);
     devbuf_free(g->dstats);
     devbuf_free(g->dpart);
@@ -274,14 +273,15 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
     ALLOC(g->bins, sizeof(int32_t) * N);
     ALLOC(g->perm, sizeof(int32_t) * N);
     g->n_layouts = ndim == 2 ? 2 : 1;
+    int p_max = 1;
     for (int l = 0; l < g->n_layouts; ++l) {
         auto &L = g->hl[l];
         L.last_axis = l == 0 ? ndim - 1 : 0;
         L.n_last = g->n[L.last_axis];
-        const int p_max = vup_hist_parts_for(L.n_last, 1);
-        if (l == 1) ALLOC(L.binsT, sizeof(int32_t) * N);
-        if (ndim >= 2) ALLOC(L.perm, sizeof(int32_t) * N);
-        if (l == 1 || p_max > 1) ALLOC(L.keys_own, sizeof(int32_t) * N);
+        p_max = std::max(p_max, vup_hist_parts_for(L.n_last, 1));
+    }
+    {
+        auto &L = g->hl[0];  // arrays of the one layout built per model
         ALLOC(L.hpt, sizeof(uint32_t) * (N + 512));  // tail slack for whole staged windows
         ALLOC(L.run_start, sizeof(int32_t) * (N + 1));
         ALLOC(L.run_rest, sizeof(int32_t) * N);
@@ -291,6 +291,8 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
         ALLOC(L.chunk_run, sizeof(int32_t) * (p_max * C + 1));
         ALLOC(L.chunk_bin, sizeof(int32_t) * 2 * p_max * C);
         if (ndim >= 2) {
+            ALLOC(L.perm, sizeof(int32_t) * N);
+            ALLOC(L.keys_own, sizeof(int32_t) * N);
             ALLOC(L.ipt, sizeof(uint2) * (N + 128));  // tail slack for whole staged windows
             ALLOC(L.iv_rest, sizeof(int32_t) * N);
             ALLOC(L.n_iv, sizeof(int32_t));
@@ -298,16 +300,34 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
             // words past the stream's end are read by whole-window staging and
             // masked; zero keeps their rest codes valid indices
             if (e == cudaSuccess) e = cudaMemset(L.ipt, 0, sizeof(uint2) * (N + 128));
+        } else {
+            L.perm = g->perm;
         }
     }
-    if (ndim == 1) g->hl[0].perm = g->perm;
-    ALLOC(g->hist_sel, sizeof(int32_t) * 2);
-    ALLOC(g->flags_scan, sizeof(int32_t) * N);
+    if (g->n_layouts > 1) {
+        auto &A = g->hl[0];
+        auto &L = g->hl[1];
+        L.perm = A.perm;
+        L.keys_own = A.keys_own;
+        L.hpt = A.hpt;
+        L.run_start = A.run_start;
+        L.run_rest = A.run_rest;
+        L.run_bin = A.run_bin;
+        L.n_runs = A.n_runs;
+        L.chunk_pt = A.chunk_pt;
+        L.chunk_run = A.chunk_run;
+        L.chunk_bin = A.chunk_bin;
+        L.ipt = A.ipt;
+        L.iv_rest = A.iv_rest;
+        L.n_iv = A.n_iv;
+        L.chunk_iv = A.chunk_iv;
+    }
+    ALLOC(g->hist_sel, sizeof(int32_t) * 4);
     ALLOC(g->ydev_scale, sizeof(double));
     ALLOC(g->dstatus, sizeof(int));
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMemset(g->dstatus, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(g->hist_sel, 0, sizeof(int32_t) * 2);
+    if (e == cudaSuccess) e = cudaMemset(g->hist_sel, 0, sizeof(int32_t) * 4);
     if (e != cudaSuccess) {
         vup_set_last_cuda_error(e, "vup_grid_create", __FILE__, __LINE__);
         cudaGetLastError();

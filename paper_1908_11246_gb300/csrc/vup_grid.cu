@@ -208,31 +208,83 @@ __global__ void k_count(const int32_t *__restrict__ keys, int64_t N, int Bk, int
     }
 }
 
-// out[a1 * n0 + a0] = in[a0 * n1 + a1]
-__global__ void k_transpose_i32(const int32_t *__restrict__ in, int64_t n0, int64_t n1, int32_t *__restrict__ out) {
+// ---- histogram layout ---------------------------------------------------------
+// A layout gathers one axis per point from a shared-memory factor tile (the
+// last axis, or on 2-D grids axis 0) and cuts it into P parts of part_rows
+// rows; its flat order puts the gathered index innermost.  Both candidate
+// geometries travel to the kernels and the device-side choice sel[0] picks
+// one, so only the chosen layout is sorted and walked.
+struct LayGeom {
+    int64_t n_last, part_rows;
+    int P;
+};
+struct LaySel {
+    LayGeom g[2];
+    const int32_t *sel;
+    __device__ __forceinline__ LayGeom get() const { return g[sel[0] ? 1 : 0]; }
+};
+
+// Intervals of both 2-D layouts (stretches of one (part, bin) key along the
+// gathered axis), counted without sorting: 1 + key changes along each line.
+__global__ void k_iv_count(const int32_t *__restrict__ bins, int64_t n0, int64_t n1, int B, LaySel L,
+                           int32_t *__restrict__ cnt) {
+    const int64_t N = n0 * n1;
+    int32_t c0 = 0, c1 = 0;
+    const int64_t pr0 = L.g[0].part_rows, pr1 = L.g[1].part_rows;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = i / n1, i1 = i - i0 * n1;
+        const int32_t b = bins[i];
+        // layout 0 gathers axis 1, layout 1 axis 0
+        c0 += i1 == 0 || (i1 / pr0) * B + b != ((i1 - 1) / pr0) * B + bins[i - 1];
+        c1 += i0 == 0 || (i0 / pr1) * B + b != ((i0 - 1) / pr1) * B + bins[i - n1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&cnt[0], c0);
+        atomicAdd(&cnt[1], c1);
+    }
+}
+
+// Layout choice: the one with fewer intervals (both streams' work grows with
+// the runs and intervals of the layout, and a layout's runs are at most its
+// intervals).
+__global__ void k_pick_layout(const int32_t *cnt, int32_t *sel) { sel[0] = cnt[1] < cnt[0] ? 1 : 0; }
+
+// Sort keys of the chosen layout: key = part of the gathered index * B + bin,
+// in the layout's flat order.  bins is viewed as an [R][C] matrix (C = the
+// last axis); layout 1 (2-D) walks its transpose.  32 x 32 tiles go through
+// shared memory so that reads and writes are coalesced either way.
+__global__ void k_layout_keys(const int32_t *__restrict__ bins, int64_t R, int64_t C, int B, LaySel L,
+                              int32_t *__restrict__ keys) {
     __shared__ int32_t t[32][33];
-    const int64_t a0b = (int64_t)blockIdx.y * 32, a1b = (int64_t)blockIdx.x * 32;
-    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
-        const int64_t a0 = a0b + yy, a1 = a1b + threadIdx.x;
-        if (a0 < n0 && a1 < n1) t[yy][threadIdx.x] = in[a0 * n1 + a1];
-    }
-    __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
-        const int64_t a1 = a1b + yy, a0 = a0b + threadIdx.x;
-        if (a0 < n0 && a1 < n1) out[a1 * n0 + a0] = t[threadIdx.x][yy];
+    const bool tr = L.sel[0] != 0;  // uniform over the grid
+    const LayGeom G = L.get();
+    const int64_t cb = (int64_t)blockIdx.x * 32;
+    for (int64_t rb = (int64_t)blockIdx.y * 32; rb < R; rb += (int64_t)gridDim.y * 32) {
+        for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+            const int64_t r = rb + yy, c = cb + threadIdx.x;
+            if (r < R && c < C) {
+                const int32_t b = bins[r * C + c];
+                if (tr) t[yy][threadIdx.x] = (int32_t)(r / G.part_rows) * B + b;
+                else keys[r * C + c] = (int32_t)(c / G.part_rows) * B + b;
+            }
+        }
+        if (!tr) continue;
+        __syncthreads();
+        for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+            const int64_t c = cb + yy, r = rb + threadIdx.x;
+            if (r < R && c < C) keys[c * R + r] = t[threadIdx.x][yy];
+        }
+        __syncthreads();
     }
 }
 
-// Sort key of a layout: the part of the gathered axis first, then the bin.
-__global__ void k_make_keys(const int32_t *__restrict__ bins, int64_t N, int64_t n_last, int64_t part_rows, int B,
-                            int32_t *__restrict__ keys) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
-        keys[j] = (int32_t)((j % n_last) / part_rows) * B + bins[j];
-}
-
-// Bin offsets of the model matrix from a layout's key offsets:
+// Bin offsets of the model matrix from the layout's key offsets:
 // offsets[b] = sum over parts of the points of that part in bins below b.
-__global__ void k_natural_offsets(const int32_t *__restrict__ koff, int P, int B, int64_t N,
+__global__ void k_natural_offsets(const int32_t *__restrict__ koff, LaySel L, int B, int64_t N,
                                   int32_t *__restrict__ offsets) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b > B) return;
@@ -240,38 +292,22 @@ __global__ void k_natural_offsets(const int32_t *__restrict__ koff, int P, int B
         offsets[B] = (int32_t)N;
         return;
     }
+    const int P = L.get().P;
     int32_t s = 0;
     for (int p = 0; p < P; ++p) s += koff[p * B + b] - koff[p * B];
     offsets[b] = s;
 }
 
-// The histogram walks the layout and stream with the least estimated work,
-// in units of about 3.3 ps of kernel time per 128-density tile (fitted to
+// Stream choice for the chosen layout, with the least estimated work in
+// units of about 3.3 ps of kernel time per 128-density tile (fitted to
 // measured launches on 2-D and 3-D grids): point stream 4 per point (one
 // gather) + 20 per run (rest-factor pipeline); interval stream 19 per
-// interval (two gathers, a difference, a rest-factor load).
-__global__ void k_pick_layout(const int32_t *n_runs0, const int32_t *n_runs1, const int32_t *n_iv0,
-                              const int32_t *n_iv1, int64_t N, int force, int32_t *sel) {
-    int best_l = 0, best_m = 0;
-    int64_t best = INT64_MAX;
-    for (int l = 0; l < 2; ++l) {
-        const int32_t *nr = l == 0 ? n_runs0 : n_runs1, *ni = l == 0 ? n_iv0 : n_iv1;
-        if (!nr) continue;
-        const int64_t c_pt = force == 1 ? INT64_MAX - 1 : 4 * N + 20 * (int64_t)nr[0];
-        const int64_t c_iv = (ni && force != 0) ? 19 * (int64_t)ni[0] : INT64_MAX;
-        if (c_pt < best) {
-            best = c_pt;
-            best_l = l;
-            best_m = 0;
-        }
-        if (c_iv < best) {
-            best = c_iv;
-            best_l = l;
-            best_m = 1;
-        }
-    }
-    sel[0] = best_l;
-    sel[1] = best_m;
+// interval (two gathers, a difference, a rest-factor load).  force: -1 both
+// allowed, 0 points only, 1 intervals only.
+__global__ void k_pick_stream(const int32_t *n_runs, const int32_t *n_iv, int64_t N, int force, int32_t *sel) {
+    const int64_t c_pt = 4 * N + 20 * (int64_t)n_runs[0];
+    const int64_t c_iv = 19 * (int64_t)n_iv[0];
+    sel[1] = force == 1 ? 1 : force == 0 ? 0 : (c_iv < c_pt ? 1 : 0);
 }
 
 // Stable scatter: each warp walks its tile in order, 32 points at a time;
@@ -307,47 +343,48 @@ __global__ void k_sort_scatter(const int32_t *__restrict__ keys, int64_t N, int 
     }
 }
 
-// ---- exclusive scan of int32 (three-phase, deterministic) ----------------
+// ---- exclusive scan (three-phase, deterministic), int32 or int64 -----------
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kScanThreads * kScanItems;
 
-__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *s_warp, int32_t &total) {
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *s_warp, T &total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t x = v;
+    T x = v;
     for (int o = 1; o < 32; o <<= 1) {
-        int32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        T t = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += t;
     }
     if (lane == 31) s_warp[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        int32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+        T w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : T(0);
         for (int o = 1; o < 32; o <<= 1) {
-            int32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            T t = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += t;
         }
         s_warp[lane] = w;
     }
     __syncthreads();
-    int32_t warp_off = warp > 0 ? s_warp[warp - 1] : 0;
+    T warp_off = warp > 0 ? s_warp[warp - 1] : T(0);
     total = s_warp[(blockDim.x >> 5) - 1];
     __syncthreads();
     return warp_off + x - v;
 }
 
-__global__ void k_scan_blocks(const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t L,
-                              int32_t *__restrict__ block_sums) {
-    __shared__ int32_t s_warp[32];
+template <typename T>
+__global__ void k_scan_blocks(const T *__restrict__ in, T *__restrict__ out, int64_t L, T *__restrict__ block_sums) {
+    __shared__ T s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
-    int32_t v[kScanItems];
-    int32_t tsum = 0;
+    T v[kScanItems];
+    T tsum = 0;
     for (int j = 0; j < kScanItems; ++j) {
-        v[j] = base + j < L ? in[base + j] : 0;
+        v[j] = base + j < L ? in[base + j] : T(0);
         tsum += v[j];
     }
-    int32_t total;
-    int32_t off = block_excl_scan(tsum, s_warp, total);
+    T total;
+    T off = block_excl_scan(tsum, s_warp, total);
     for (int j = 0; j < kScanItems; ++j) {
         if (base + j < L) out[base + j] = off;
         off += v[j];
@@ -355,67 +392,94 @@ __global__ void k_scan_blocks(const int32_t *__restrict__ in, int32_t *__restric
     if (threadIdx.x == 0 && block_sums) block_sums[blockIdx.x] = total;
 }
 
-__global__ void k_scan_add(int32_t *__restrict__ out, int64_t L, const int32_t *__restrict__ block_off) {
+template <typename T>
+__global__ void k_scan_add(T *__restrict__ out, int64_t L, const T *__restrict__ block_off) {
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
-    const int32_t add = block_off[blockIdx.x];
+    const T add = block_off[blockIdx.x];
     for (int j = threadIdx.x; j < kScanBlock; j += blockDim.x)
         if (base + j < L) out[base + j] += add;
 }
 
-// ---- runs and chunks for the segmented histogram --------------------------
+// ---- runs, intervals and chunks of the segmented histogram ------------------
 // A run is a maximal stretch of sorted points sharing the sort key (part and
-// bin) and every axis index but the gathered one.  hpt[t] packs the t-th
-// sorted point's row inside its part of the gathered axis (<< shift; the
-// row's byte offset in a shared-memory tile of 2^shift-byte rows, kRowBits
-// wide -- rows past that field only occur with parts too large for a tile,
-// whose kernel reads the row from the sorted order instead) and the run-end /
-// key-end flags (bits 30, 31).
-__global__ void k_run_flags(const int32_t *__restrict__ perm, const int32_t *__restrict__ keys,
-                            int64_t N, int64_t n_last, int32_t *__restrict__ flags) {
+// bin) and every axis index but the gathered one; an interval is a maximal
+// stretch of a run whose gathered rows are consecutive (the points of one bin
+// along one line of the grid).  One flag word per sorted point holds both
+// start flags (run: bit 0, interval: bit 32), so a single 64-bit scan numbers
+// runs (low half) and intervals (high half).
+__global__ void k_layout_flags(const int32_t *__restrict__ perm, const int32_t *__restrict__ keys, int64_t N,
+                               LaySel L, unsigned long long *__restrict__ flags) {
+    const int64_t n_last = L.get().n_last;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
          t += (int64_t)gridDim.x * blockDim.x) {
-        int32_t f = 1;
+        unsigned long long f = 1ull | (1ull << 32);
         if (t > 0) {
-            int32_t i = perm[t], ip = perm[t - 1];
-            f = (keys[i] != keys[ip]) || (i / n_last != ip / n_last);
+            const int32_t i = perm[t], ip = perm[t - 1];
+            const bool run = keys[i] != keys[ip] || i / n_last != ip / n_last;
+            const bool iv = run || i != ip + 1;  // same line: consecutive gathered rows
+            f = (run ? 1ull : 0ull) | (iv ? 1ull << 32 : 0ull);
         }
         flags[t] = f;
     }
 }
 
-__global__ void k_run_build(const int32_t *__restrict__ perm, const int32_t *__restrict__ keys,
-                            int64_t N, int64_t n_last, int64_t part_rows, int shift,
-                            const int32_t *__restrict__ flags, const int32_t *__restrict__ excl,
-                            int32_t *__restrict__ run_start, int32_t *__restrict__ run_rest,
-                            int32_t *__restrict__ run_bin, uint32_t *__restrict__ hpt,
-                            int32_t *__restrict__ n_runs) {
+// Per sorted point t: the run arrays at run starts; hpt[t] = the point's row
+// inside its part (<< shift: its byte offset in a shared-memory tile of
+// 2^shift-byte rows, kRowBits wide -- rows past that field only occur with
+// parts too large for a tile, whose kernel reads the row from the sorted
+// order instead) | run-end / key-end flags (bits 30, 31); the interval words
+// (first row << shift; (last row + 1) << shift | the flags of its last point)
+// and each interval's rest index.
+__global__ void k_layout_build(const int32_t *__restrict__ perm, const int32_t *__restrict__ keys, int64_t N,
+                               LaySel L, int shift, const unsigned long long *__restrict__ flags,
+                               const unsigned long long *__restrict__ excl, int32_t *__restrict__ run_start,
+                               int32_t *__restrict__ run_rest, int32_t *__restrict__ run_bin,
+                               uint32_t *__restrict__ hpt, int32_t *__restrict__ n_runs, uint2 *__restrict__ ipt,
+                               int32_t *__restrict__ iv_rest, int32_t *__restrict__ n_iv) {
+    const LayGeom G = L.get();
+    const uint32_t rmask = (1u << kRowBits) - 1u;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = perm[t];
-        const int32_t rid = excl[t] + flags[t] - 1;
-        if (flags[t]) {
+        const unsigned long long f = flags[t], e = excl[t];
+        const int32_t run_f = (int32_t)(f & 1ull), iv_f = (int32_t)(f >> 32);
+        const int32_t rid = (int32_t)(e & 0xffffffffull) + run_f - 1;
+        const int32_t iid = (int32_t)(e >> 32) + iv_f - 1;
+        const int32_t key = keys[i];
+        const int32_t rest = (int32_t)(i / G.n_last);
+        if (run_f) {
             run_start[rid] = (int32_t)t;
-            run_rest[rid] = (int32_t)(i / n_last);
-            run_bin[rid] = keys[i];
+            run_rest[rid] = rest;
+            run_bin[rid] = key;
         }
-        const bool last = (t == N - 1) || flags[t + 1];
-        const bool key_last = (t == N - 1) || keys[perm[t + 1]] != keys[i];
-        const int64_t a = i % n_last;
-        const uint32_t row = (uint32_t)(a - (a / part_rows) * part_rows);
-        hpt[t] = ((row & ((1u << kRowBits) - 1u)) << shift) | (last ? kRunEnd : 0u) | (key_last ? kBinEnd : 0u);
-        if (t == N - 1) {
+        const bool end = t == N - 1;
+        const unsigned long long fn = end ? (1ull | (1ull << 32)) : flags[t + 1];
+        const bool last = (fn & 1ull) != 0, iv_last = (fn >> 32) != 0;
+        const bool key_last = end || keys[perm[t + 1]] != key;
+        const int64_t a = i - (int64_t)rest * G.n_last;
+        const uint32_t row = (uint32_t)(a - (a / G.part_rows) * G.part_rows) & rmask;
+        const uint32_t fl = (last ? kRunEnd : 0u) | (key_last ? kBinEnd : 0u);
+        hpt[t] = (row << shift) | fl;
+        uint32_t *w = reinterpret_cast<uint32_t *>(ipt + iid);
+        if (iv_f) {
+            w[0] = row << shift;
+            iv_rest[iid] = rest;
+        }
+        if (iv_last) w[1] = (((row + 1u) & rmask) << shift) | fl;
+        if (end) {
             n_runs[0] = rid + 1;
             run_start[rid + 1] = (int32_t)N;
+            n_iv[0] = iid + 1;
         }
     }
 }
 
-// The run-end word of run r also carries the rest-axis index of run r + 4
-// (the histogram kernel loads that run's factor four runs ahead) in the 21
-// bits beside the row field: `shift` low bits (0 .. shift-1) and
-// 30 - shift - kRowBits high bits (shift + kRowBits .. 29).  2-D grids split
-// the rest index itself; 3-D grids put a0 in the low field and a1 in the high
-// field.  Zero past the end.
+// The run-end word of run r (and the word pair of interval i) also carries
+// the rest-axis index of run r + 4 (interval i + 4): the histogram kernel
+// loads that factor four ahead.  The code sits in the 21 bits beside the row
+// field: `shift` low bits (0 .. shift-1) and 30 - shift - kRowBits high bits
+// (shift + kRowBits .. 29).  2-D grids split the rest index itself; 3-D grids
+// put a0 in the low field and a1 in the high field.  Zero past the end.
 constexpr int kRunAhead = 4;
 __device__ __forceinline__ uint32_t rest_code(int32_t rest, int ndim, int64_t n1, int shift) {
     const uint32_t lo_mask = (1u << shift) - 1u;
@@ -430,24 +494,30 @@ __device__ __forceinline__ uint32_t rest_code(int32_t rest, int ndim, int64_t n1
     }
     return (lo & lo_mask) | ((hi & hi_mask) << (shift + kRowBits));
 }
-__global__ void k_run_encode(const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_rest,
-                             const int32_t *__restrict__ n_runs_p, int ndim, int64_t n1, int shift,
-                             uint32_t *__restrict__ hpt) {
-    const int32_t n_runs = n_runs_p[0];
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_runs;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t ra = r + kRunAhead;
-        const uint32_t code = ra < n_runs ? rest_code(run_rest[ra], ndim, n1, shift) : 0u;
-        hpt[run_start[r + 1] - 1] |= code;
+__global__ void k_layout_encode(const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_rest,
+                                const int32_t *__restrict__ n_runs_p, const int32_t *__restrict__ iv_rest,
+                                const int32_t *__restrict__ n_iv_p, int ndim, int64_t n1, int shift,
+                                uint32_t *__restrict__ hpt, uint2 *__restrict__ ipt) {
+    const int32_t n_runs = n_runs_p[0], n_iv = n_iv_p[0];
+    const int32_t n = n_runs > n_iv ? n_runs : n_iv;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t xa = x + kRunAhead;
+        if (x < n_runs && xa < n_runs) hpt[run_start[x + 1] - 1] |= rest_code(run_rest[xa], ndim, n1, shift);
+        if (x < n_iv && xa < n_iv) reinterpret_cast<uint32_t *>(ipt + x)[1] |= rest_code(iv_rest[xa], ndim, n1, shift);
     }
 }
 
 // Chunks, C per part: chunk c of part p starts at the first run whose first
-// point is >= lo_p + (hi_p - lo_p) c / C, [lo_p, hi_p) being the part's points.
+// point is >= lo_p + (hi_p - lo_p) c / C, [lo_p, hi_p) being the part's
+// points; chunk_iv[c] is its first interval (chunks start on runs, which
+// start intervals).  Entry P C is the end.
 __global__ void k_chunks(const int32_t *__restrict__ run_start, const int32_t *__restrict__ n_runs_p,
-                         const int32_t *__restrict__ koff, int B, int P, int C,
-                         int32_t *__restrict__ chunk_pt, int32_t *__restrict__ chunk_run) {
+                         const int32_t *__restrict__ koff, int B, LaySel L, int C,
+                         const unsigned long long *__restrict__ excl, int64_t N, const int32_t *__restrict__ n_iv_p,
+                         int32_t *__restrict__ chunk_pt, int32_t *__restrict__ chunk_run,
+                         int32_t *__restrict__ chunk_iv) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int P = L.get().P;
     if (c > P * C) return;
     const int32_t n_runs = n_runs_p[0];
     int32_t r;
@@ -464,16 +534,18 @@ __global__ void k_chunks(const int32_t *__restrict__ run_start, const int32_t *_
         }
         r = a;
     }
+    const int32_t pt = run_start[r];
     chunk_run[c] = r;
-    chunk_pt[c] = run_start[r];
+    chunk_pt[c] = pt;
+    chunk_iv[c] = pt < N ? (int32_t)(excl[pt] >> 32) : n_iv_p[0];
 }
 
 __global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
 
-__global__ void k_chunk_bins(const int32_t *__restrict__ chunk_run, const int32_t *__restrict__ run_bin,
+__global__ void k_chunk_bins(const int32_t *__restrict__ chunk_run, const int32_t *__restrict__ run_bin, LaySel L,
                              int C, int32_t *__restrict__ chunk_bin) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+    if (c >= L.get().P * C) return;
     const int32_t r0 = chunk_run[c], r1 = chunk_run[c + 1];
     chunk_bin[2 * c] = r1 > r0 ? run_bin[r0] : -1;
     chunk_bin[2 * c + 1] = r1 > r0 ? run_bin[r1 - 1] : -1;
@@ -489,74 +561,15 @@ __device__ __forceinline__ int chunk_holding(const int32_t *chunk_pt, int n, int
     }
     return lo;
 }
-__global__ void k_key_chunks(const int32_t *__restrict__ koff, int n_keys, const int32_t *__restrict__ chunk_pt,
-                             int n_chunks, int2 *__restrict__ out) {
+__global__ void k_key_chunks(const int32_t *__restrict__ koff, LaySel L, int B, const int32_t *__restrict__ chunk_pt,
+                             int C, int2 *__restrict__ out) {
     const int key = blockIdx.x * blockDim.x + threadIdx.x;
-    if (key >= n_keys) return;
+    const int P = L.get().P;
+    if (key >= P * B) return;
+    const int n_chunks = P * C;
     const int32_t o0 = koff[key], o1 = koff[key + 1];
     out[key] = o0 == o1 ? make_int2(-1, -1)
                         : make_int2(chunk_holding(chunk_pt, n_chunks, o0), chunk_holding(chunk_pt, n_chunks, o1 - 1));
-}
-
-// ---- interval stream -------------------------------------------------------
-// An interval is a maximal stretch of a run whose gathered-axis rows are
-// consecutive (the points of one bin along one line of the grid).  The
-// histogram kernel sums an interval's factors as the difference of two
-// prefix sums of the part's factor tile, so its cost does not grow with the
-// interval's length.  Interval i's word pair: x = first row << shift,
-// y = (last row + 1) << shift | run-end / key-end flags of its last point |
-// rest code of interval i + 4 (every interval loads its own rest factor,
-// four intervals ahead; same code fields as the point words).
-__global__ void k_iv_flags(const uint32_t *__restrict__ hpt, int64_t N, int shift, int32_t *__restrict__ flags) {
-    const uint32_t rmask = (1u << kRowBits) - 1u;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        int32_t f = 1;
-        if (t > 0) {
-            const uint32_t u = hpt[t - 1], v = hpt[t];
-            f = (u & kRunEnd) || ((v >> shift) & rmask) != ((u >> shift) & rmask) + 1u;
-        }
-        flags[t] = f;
-    }
-}
-
-__global__ void k_iv_build(const uint32_t *__restrict__ hpt, const int32_t *__restrict__ perm, int64_t N,
-                           int64_t n_last, int shift, const int32_t *__restrict__ flags,
-                           const int32_t *__restrict__ excl, uint2 *__restrict__ ipt,
-                           int32_t *__restrict__ iv_rest, int32_t *__restrict__ n_iv) {
-    const uint32_t rmask = (1u << kRowBits) - 1u;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t f = flags[t];
-        const int64_t id = (int64_t)excl[t] + f - 1;
-        const uint32_t h = hpt[t];
-        const uint32_t row = (h >> shift) & rmask;
-        uint32_t *w = reinterpret_cast<uint32_t *>(ipt + id);
-        if (f) {
-            w[0] = row << shift;
-            iv_rest[id] = (int32_t)(perm[t] / n_last);
-        }
-        if (t == N - 1 || flags[t + 1]) w[1] = (((row + 1u) & rmask) << shift) | (h & (kRunEnd | kBinEnd));
-        if (t == N - 1) n_iv[0] = (int32_t)(id + 1);
-    }
-}
-
-__global__ void k_iv_encode(const int32_t *__restrict__ iv_rest, const int32_t *__restrict__ n_iv_p, int ndim,
-                            int64_t n1, int shift, uint2 *__restrict__ ipt) {
-    const int32_t n = n_iv_p[0];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t ia = i + kRunAhead;
-        if (ia < n) reinterpret_cast<uint32_t *>(ipt + i)[1] |= rest_code(iv_rest[ia], ndim, n1, shift);
-    }
-}
-
-// First interval of every chunk (chunks start on run starts, which start intervals).
-__global__ void k_chunk_iv(const int32_t *__restrict__ chunk_pt, const int32_t *__restrict__ excl, int64_t N,
-                           const int32_t *__restrict__ n_iv_p, int n, int32_t *__restrict__ chunk_iv) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > n) return;
-    const int32_t pt = chunk_pt[c];
-    chunk_iv[c] = pt < N ? excl[pt] : n_iv_p[0];
 }
 
 // ---- power tables -----------------------------------------------------------
@@ -672,21 +685,22 @@ static int scan_launches(int64_t L) {
     return nb <= 1 ? 1 : 2 + scan_launches(nb);
 }
 
-static vup_status scan_exclusive(const int32_t *in, int32_t *out, int64_t L, int32_t *scratch,
-                                 cudaStream_t s) {
+// (T = int32_t or unsigned long long; scratch counted in T elements)
+template <typename T>
+static vup_status scan_exclusive(const T *in, T *out, int64_t L, T *scratch, cudaStream_t s) {
     const int64_t nb = ceil_div64(L, kScanBlock);
     if (nb <= 1) {
-        k_scan_blocks<<<1, kScanThreads, 0, s>>>(in, out, L, nullptr);
+        k_scan_blocks<T><<<1, kScanThreads, 0, s>>>(in, out, L, nullptr);
         VUP_CHECK_LAUNCH();
         return VUP_OK;
     }
-    int32_t *sums = scratch;
-    int32_t *sums_scan = scratch + nb + 32;
-    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, L, sums);
+    T *sums = scratch;
+    T *sums_scan = scratch + nb + 32;
+    k_scan_blocks<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, L, sums);
     VUP_CHECK_LAUNCH();
-    vup_status st = scan_exclusive(sums, sums_scan, nb, scratch + 2 * nb + 64, s);
+    vup_status st = scan_exclusive<T>(sums, sums_scan, nb, scratch + 2 * nb + 64, s);
     if (st != VUP_OK) return st;
-    k_scan_add<<<(unsigned)nb, 256, 0, s>>>(out, L, sums_scan);
+    k_scan_add<T><<<(unsigned)nb, 256, 0, s>>>(out, L, sums_scan);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }
@@ -798,7 +812,8 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     k_scale<<<1, 1, 0, s>>>(g->ext, g->ydev_scale);
     VUP_CHECK_LAUNCH();
 
-    // parts of each layout's gathered axis for this bin count
+    // parts of each candidate layout's gathered axis for this bin count; the
+    // arrays of the one layout that is built live in hl[0] (hl[1] aliases them)
     int Bk_max = B;
     g->hist_P = 1;
     if (g->ndim >= 2) {
@@ -808,22 +823,29 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
             HL.part_rows = ceil_div64(HL.n_last, HL.P);
             Bk_max = std::max(Bk_max, HL.P * B);
             g->hist_P = std::max(g->hist_P, HL.P);
-            if (HL.koff_cap < HL.P * B + 1) {
-                cudaFree(HL.koff);
-                cudaFree(HL.key_chunks);
-                HL.koff = nullptr;
-                HL.key_chunks = nullptr;
-                VUP_CHECK_CUDA(cudaMalloc(&HL.koff, sizeof(int32_t) * (HL.P * B + 1)));
-                VUP_CHECK_CUDA(cudaMalloc(&HL.key_chunks, sizeof(int2) * (HL.P * B + 1)));
-                HL.koff_cap = HL.P * B + 1;
-            }
+        }
+        auto &HL = g->hl[0];
+        if (HL.koff_cap < Bk_max + 1) {
+            cudaFree(HL.koff);
+            cudaFree(HL.key_chunks);
+            HL.koff = nullptr;
+            HL.key_chunks = nullptr;
+            VUP_CHECK_CUDA(cudaMalloc(&HL.koff, sizeof(int32_t) * (Bk_max + 1)));
+            VUP_CHECK_CUDA(cudaMalloc(&HL.key_chunks, sizeof(int2) * (Bk_max + 1)));
+            HL.koff_cap = Bk_max + 1;
+        }
+        if (g->n_layouts > 1) {
+            g->hl[1].koff = HL.koff;
+            g->hl[1].key_chunks = HL.key_chunks;
+            g->hl[1].koff_cap = HL.koff_cap;
         }
     }
     const int64_t n_tiles = ceil_div64(N, kSortTile);
     const int64_t Lmax = (int64_t)Bk_max * n_tiles;
     vup_status st = devbuf_reserve(g->sort_counts, sizeof(int32_t) * (size_t)std::max<int64_t>(2 * Lmax + 8, N + 8));
     if (st != VUP_OK) return st;
-    st = devbuf_reserve(g->scan_tmp, sizeof(int32_t) * (size_t)scan_scratch_ints(std::max<int64_t>(Lmax, N)));
+    st = devbuf_reserve(g->scan_tmp, sizeof(unsigned long long) *
+                                         (size_t)scan_scratch_ints(std::max<int64_t>(Lmax, N)));
     if (st != VUP_OK) return st;
     int32_t *scratch = (int32_t *)g->scan_tmp.p;
     int32_t *counts = (int32_t *)g->sort_counts.p;
@@ -844,71 +866,66 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
         st = counting_sort(g, g->bins, B, g->perm, g->offsets, counts, scratch, true, s);
         if (st != VUP_OK) return st;
         g->natural_valid = 1;
+        launches += 2 + scan_launches((int64_t)B * n_tiles);
     } else {
         const int C = g->n_chunks;
-        for (int l = 0; l < g->n_layouts; ++l) {
-            auto &HL = g->hl[l];
-            const int32_t *src = g->bins;
-            if (l == 1) {  // transposed order, j = a1 * n0 + a0
-                dim3 tg((unsigned)ceil_div64(g->n[1], 32), (unsigned)ceil_div64(g->n[0], 32));
-                k_transpose_i32<<<tg, dim3(32, 8), 0, s>>>(g->bins, g->n[0], g->n[1], HL.binsT);
-                VUP_CHECK_LAUNCH();
-                src = HL.binsT;
-            }
-            HL.keys = const_cast<int32_t *>(src);
-            if (HL.P > 1) {
-                k_make_keys<<<blocks, 256, 0, s>>>(src, N, HL.n_last, HL.part_rows, B, HL.keys_own);
-                VUP_CHECK_LAUNCH();
-                HL.keys = HL.keys_own;
-            }
-            const int Bk = HL.P * B;
-            st = counting_sort(g, HL.keys, Bk, HL.perm, HL.koff, counts, scratch, false, s);
-            if (st != VUP_OK) return st;
-            // transpose, keys, sort (count, scan, scatter, koff end), runs (flags, scan, build,
-            // encode, chunks, chunk keys, key chunks), intervals (flags, scan, build, encode, chunk starts)
-            launches += (l == 1) + (HL.P > 1) + 3 + scan_launches((int64_t)Bk * n_tiles) + 5 + scan_launches(N) +
-                        4 + scan_launches(N);
-            // runs and chunks
-            const int64_t n_last = HL.n_last;
-            int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
-            k_run_flags<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, n_last, g->flags_scan);
-            VUP_CHECK_LAUNCH();
-            int32_t *excl = counts;  // the sort counts are dead once the scatter ran
-            st = scan_exclusive(g->flags_scan, excl, N, scratch, s);
-            if (st != VUP_OK) return st;
-            k_run_build<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, n_last, HL.part_rows, kRowShift, g->flags_scan, excl,
-                                           HL.run_start, HL.run_rest, HL.run_bin, HL.hpt, HL.n_runs);
-            VUP_CHECK_LAUNCH();
-            k_run_encode<<<rb, 256, 0, s>>>(HL.run_start, HL.run_rest, HL.n_runs, g->ndim, g->ndim == 3 ? g->n[1] : 1,
-                                            kRowShift, HL.hpt);
-            VUP_CHECK_LAUNCH();
-            const int PC = HL.P * C;
-            k_chunks<<<(PC + 1 + 127) / 128, 128, 0, s>>>(HL.run_start, HL.n_runs, HL.koff, B, HL.P, C, HL.chunk_pt,
-                                                           HL.chunk_run);
-            VUP_CHECK_LAUNCH();
-            k_chunk_bins<<<(PC + 127) / 128, 128, 0, s>>>(HL.chunk_run, HL.run_bin, PC, HL.chunk_bin);
-            VUP_CHECK_LAUNCH();
-            k_key_chunks<<<(Bk + 127) / 128, 128, 0, s>>>(HL.koff, Bk, HL.chunk_pt, PC, HL.key_chunks);
-            VUP_CHECK_LAUNCH();
-            // interval stream
-            k_iv_flags<<<rb, 256, 0, s>>>(HL.hpt, N, kRowShift, g->flags_scan);
-            VUP_CHECK_LAUNCH();
-            st = scan_exclusive(g->flags_scan, excl, N, scratch, s);
-            if (st != VUP_OK) return st;
-            k_iv_build<<<rb, 256, 0, s>>>(HL.hpt, HL.perm, N, n_last, kRowShift, g->flags_scan, excl, HL.ipt,
-                                          HL.iv_rest, HL.n_iv);
-            VUP_CHECK_LAUNCH();
-            k_iv_encode<<<rb, 256, 0, s>>>(HL.iv_rest, HL.n_iv, g->ndim, g->ndim == 3 ? g->n[1] : 1, kRowShift,
-                                           HL.ipt);
-            VUP_CHECK_LAUNCH();
-            k_chunk_iv<<<(PC + 1 + 127) / 128, 128, 0, s>>>(HL.chunk_pt, excl, N, HL.n_iv, PC, HL.chunk_iv);
-            VUP_CHECK_LAUNCH();
+        auto &HL = g->hl[0];
+        LaySel L;
+        for (int l = 0; l < 2; ++l) {
+            const auto &h = g->hl[l < g->n_layouts ? l : 0];
+            L.g[l] = LayGeom{h.n_last, h.part_rows, h.P};
         }
-        k_natural_offsets<<<(B + 1 + 127) / 128, 128, 0, s>>>(g->hl[0].koff, g->hl[0].P, B, N, g->offsets);
+        L.sel = g->hist_sel;
+        int32_t *iv_cnt = g->hist_sel + 2;
+        if (g->n_layouts > 1) {
+            // the layout with fewer intervals (counted without sorting)
+            VUP_CHECK_CUDA(cudaMemsetAsync(iv_cnt, 0, 2 * sizeof(int32_t), s));
+            k_iv_count<<<blocks, 256, 0, s>>>(g->bins, g->n[0], g->n[1], B, L, iv_cnt);
+            VUP_CHECK_LAUNCH();
+            k_pick_layout<<<1, 1, 0, s>>>(iv_cnt, g->hist_sel);
+            VUP_CHECK_LAUNCH();
+            launches += 2;
+        }
+        // sort keys of the chosen layout, stable counting sort
+        const int64_t Cn = HL.n_last, Rn = N / Cn;   // layout 0 geometry: [R][C], C = last axis
+        dim3 tg((unsigned)ceil_div64(Cn, 32), (unsigned)std::min<int64_t>(ceil_div64(Rn, 32), 65535));
+        k_layout_keys<<<tg, dim3(32, 8), 0, s>>>(g->bins, Rn, Cn, B, L, HL.keys_own);
+        VUP_CHECK_LAUNCH();
+        HL.keys = HL.keys_own;
+        st = counting_sort(g, HL.keys, Bk_max, HL.perm, HL.koff, counts, scratch, false, s);
+        if (st != VUP_OK) return st;
+        // runs and intervals: one flag word per point, one 64-bit scan
+        st = devbuf_reserve(g->lay_tmp, sizeof(unsigned long long) * 2 * (size_t)N);
+        if (st != VUP_OK) return st;
+        auto *flags = (unsigned long long *)g->lay_tmp.p;
+        auto *excl = flags + N;
+        const int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
+        k_layout_flags<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, L, flags);
+        VUP_CHECK_LAUNCH();
+        st = scan_exclusive<unsigned long long>(flags, excl, N, (unsigned long long *)g->scan_tmp.p, s);
+        if (st != VUP_OK) return st;
+        k_layout_build<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, L, kRowShift, flags, excl, HL.run_start, HL.run_rest,
+                                          HL.run_bin, HL.hpt, HL.n_runs, HL.ipt, HL.iv_rest, HL.n_iv);
+        VUP_CHECK_LAUNCH();
+        k_layout_encode<<<rb, 256, 0, s>>>(HL.run_start, HL.run_rest, HL.n_runs, HL.iv_rest, HL.n_iv, g->ndim,
+                                           g->ndim == 3 ? g->n[1] : 1, kRowShift, HL.hpt, HL.ipt);
+        VUP_CHECK_LAUNCH();
+        // chunks of every part
+        const int PC = g->hist_P * C;
+        k_chunks<<<(PC + 1 + 127) / 128, 128, 0, s>>>(HL.run_start, HL.n_runs, HL.koff, B, L, C, excl, N, HL.n_iv,
+                                                       HL.chunk_pt, HL.chunk_run, HL.chunk_iv);
+        VUP_CHECK_LAUNCH();
+        k_chunk_bins<<<(PC + 127) / 128, 128, 0, s>>>(HL.chunk_run, HL.run_bin, L, C, HL.chunk_bin);
+        VUP_CHECK_LAUNCH();
+        k_key_chunks<<<(Bk_max + 127) / 128, 128, 0, s>>>(HL.koff, L, B, HL.chunk_pt, C, HL.key_chunks);
+        VUP_CHECK_LAUNCH();
+        k_natural_offsets<<<(B + 1 + 127) / 128, 128, 0, s>>>(HL.koff, L, B, N, g->offsets);
         VUP_CHECK_LAUNCH();
         st = vup_pick_hist_layout(g, s);
         if (st != VUP_OK) return st;
-        launches += 2;
+        // keys, sort (count, scan, scatter, koff end), flags, scan, build, encode, chunks,
+        // chunk keys, key chunks, natural offsets, stream choice
+        launches += 1 + 3 + scan_launches((int64_t)Bk_max * n_tiles) + 1 + scan_launches(N) + 2 + 5;
     }
     prof.launches = launches;
     for (int o = 0; o < kNumOrient; ++o) g->have_tab[o][0] = g->have_tab[o][1] = g->have_tab[o][2] = 0;
@@ -916,9 +933,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
 }
 
 vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s) {
-    const bool two = g->n_layouts > 1;
-    k_pick_layout<<<1, 1, 0, s>>>(g->hl[0].n_runs, two ? g->hl[1].n_runs : nullptr, g->hl[0].n_iv,
-                                  two ? g->hl[1].n_iv : nullptr, g->N, g->hist_force, g->hist_sel);
+    k_pick_stream<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->hl[0].n_iv, g->N, g->hist_force, g->hist_sel);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }

@@ -341,7 +341,7 @@ __device__ __forceinline__ bool iv_chunk(const ItemCtx &X, int c, int p, int64_t
 // memory).  Called by every thread of the CTA; `wseq` counts the staging
 // windows this warp has consumed so far (it keeps the per-warp mbarrier
 // phases consistent across items).
-template <int NF>
+template <int NF, int MODE>
 __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int64_t k0, uint8_t *sm,
                                           int64_t tile_rows, uint32_t &wseq, volatile int *abort, ItemCtx &X,
                                           float *s_invz, int *next_chunk) {
@@ -366,7 +366,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         X.B = A.B;
         X.C = A.C;
         X.group_chunks = A.group_chunks;
-        X.mode = A.points_only ? 0 : A.sel[1];
+        X.mode = MODE;
         X.dstatus = A.dstatus;
     }
     if (threadIdx.x < kKT) s_invz[threadIdx.x] = inv_z(*Ap, k0 + threadIdx.x);
@@ -390,7 +390,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     if (threadIdx.x < kKT) ws[nrows * kKT + threadIdx.x] = 0.f;
     cp_async_wait_all();
     __syncthreads();
-    if (X.mode) {
+    if (MODE) {
         // interval stream: every column becomes the exclusive prefix sums
         // P[0..nrows] of its scaled factors (compensated sums, each P rounded
         // once to FP32), so that rows a .. b - 1 sum to P[b] - P[a].  The
@@ -577,15 +577,15 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         if (cur_key >= 0) flush(cur_key, bacc);
         return true;
     };
-    const bool iv = X.mode != 0;
     for (;;) {
         int ci = 0;
         if (lane == 0) ci = atomicAdd(next_chunk, 1);
         ci = __shfl_sync(0xffffffffu, ci, 0);
         if (ci >= X.group_chunks) break;
         const int wc = cg * X.group_chunks + ci;
-        const bool ok = iv ? iv_chunk<NF>(X, p * X.C + wc, p, k, ws, win, mbar, wseq, abort)
-                           : run_chunk(wc);
+        bool ok;
+        if constexpr (MODE == 1) ok = iv_chunk<NF>(X, p * X.C + wc, p, k, ws, win, mbar, wseq, abort);
+        else ok = run_chunk(wc);
         if (!ok) return;
     }
 }
@@ -604,27 +604,43 @@ __device__ __forceinline__ void hist_init_mbar(uint8_t *sm, int64_t tile_rows) {
     __syncwarp();
 }
 
-template <int NF>
+// Stream of an instance's histogram: 1 = intervals (the layout's choice,
+// unless the caller asked for points).
+__device__ __forceinline__ int hist_stream(const HistArgs &A) { return A.points_only ? 0 : A.sel[1]; }
+
+// One CTA per item, it = (k-tile * P + part) * G + chunk group, so that
+// CTAs running together share k-tiles (rest-factor rows stay in L2) and the
+// hardware hands items to SMs as they free up (item costs vary; a static
+// split of items over persistent CTAs measured 12 % slower on the 3-D
+// workload).  Each stream is its own kernel (their register allocations
+// stay apart); the host launches both and every CTA of the one the device
+// did not choose returns at once.
+template <int NF, int MODE>
 __global__ void __launch_bounds__(kHistWarps * 32, 1)
-    k_hist_smem(const __grid_constant__ HistArgs A, int64_t tile_rows, int G) {
+    k_hist_smem(const __grid_constant__ HistArgs A, int64_t tile_rows, int P, int G, int n_items) {
+    if (hist_stream(A) != MODE) return;  // uniform
     extern __shared__ __align__(128) uint8_t sm[];
     __shared__ ItemCtx X;
     __shared__ float s_invz[kKT];
     __shared__ int abort, next_chunk;
-    const int p = blockIdx.x / G, cg = blockIdx.x - p * G;
     if (threadIdx.x == 0) abort = 0;
     hist_init_mbar(sm, tile_rows);
     uint32_t wseq = 0;
-    hist_item<NF>(&A, p, cg, (int64_t)blockIdx.y * kKT, sm, tile_rows, wseq, &abort, X, s_invz, &next_chunk);
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int cg = it % G, pk = it / G;
+        const int p = pk % P, kt = pk / P;
+        hist_item<NF, MODE>(&A, p, cg, (int64_t)kt * kKT, sm, tile_rows, wseq, &abort, X, s_invz, &next_chunk);
+    }
 }
 
-// Batched form: one persistent launch over the work items of many instances
-// (each with its own grid, densities and outputs), longest items first.
+// Batched form: one persistent launch per stream over the work items of
+// many instances (each with its own grid, densities and outputs), longest
+// items first; items of instances on the other stream are skipped.
 struct HistItem {
     int32_t inst, p, cg, kt;
 };
 
-template <int NF>
+template <int NF, int MODE>
 __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_batched(const HistArgs *__restrict__ insts,
                                                                      const HistItem *__restrict__ items,
                                                                      int n_items, int64_t tile_rows) {
@@ -637,8 +653,9 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_batched(const HistA
     uint32_t wseq = 0;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const HistItem w = items[it];
-        hist_item<NF>(insts + w.inst, w.p, w.cg, (int64_t)w.kt * kKT, sm, tile_rows, wseq, &abort, X, s_invz,
-                      &next_chunk);
+        if (hist_stream(insts[w.inst]) != MODE) continue;  // uniform
+        hist_item<NF, MODE>(insts + w.inst, w.p, w.cg, (int64_t)w.kt * kKT, sm, tile_rows, wseq, &abort, X, s_invz,
+                            &next_chunk);
     }
 }
 
@@ -831,36 +848,44 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     const size_t smem = hist_smem_bytes(rows);
     // run-end words encode the rest index in 21 bits (3-D: a0 < 512, a1 < 4096)
     const bool coded = nd == 2 || (g->n[0] <= 512 && g->n[1] <= 4096);
-    // CTAs along the chunks: G groups of C / G chunks per part, G dividing
-    // C / kGroupChunks, chosen for the fewest idle SM slots in the last wave
+    // items: G groups of C / G chunks per part, G dividing C / kGroupChunks,
+    // chosen for the fewest idle SM slots in the last wave (one CTA per SM)
     const int S = A.C / kGroupChunks, nkt = (int)ceil_div64(K, kKT), sms = vup_num_sms();
     int G = S;
     double best = -1.0;
     for (int gg = S; gg >= 1; --gg) {
         if (S % gg) continue;
-        const int64_t ctas = (int64_t)P_max * gg * nkt;
-        const double eff = (double)ctas / (double)(ceil_div64(ctas, sms) * sms);
+        const int64_t items = (int64_t)P_max * gg * nkt;
+        const double eff = (double)items / (double)(ceil_div64(items, sms) * sms);
         if (eff > best + 0.02) {
             best = eff;
             G = gg;
         }
     }
     A.group_chunks = A.C / G;
-    dim3 grd((unsigned)(P_max * G), (unsigned)ceil_div64(K, kKT));
+    const int n_items = P_max * G * nkt;
+    const int grid = n_items;
     {
-        VUP_PROF("hist_segmented", s, 1);
-        if (smem <= 220 * 1024 && coded) {
-            if (nd == 3) {
-                VUP_CHECK_CUDA(cudaFuncSetAttribute(k_hist_smem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_hist_smem<2><<<grd, kHistWarps * 32, smem, s>>>(A, rows, G);
-            } else {
-                VUP_CHECK_CUDA(cudaFuncSetAttribute(k_hist_smem<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_hist_smem<1><<<grd, kHistWarps * 32, smem, s>>>(A, rows, G);
+        const bool in_smem = smem <= 220 * 1024 && coded;
+        VUP_PROF("hist_segmented", s, in_smem && !points_only ? 2 : 1);
+        if (in_smem) {
+            auto launch = [&](auto kern) -> vup_status {
+                VUP_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                kern<<<grid, kHistWarps * 32, smem, s>>>(A, rows, P_max, G, n_items);
+                VUP_CHECK_LAUNCH();
+                return VUP_OK;
+            };
+            vup_status st = nd == 3 ? launch(k_hist_smem<2, 0>) : launch(k_hist_smem<1, 0>);
+            if (st != VUP_OK) return st;
+            if (!points_only) {
+                st = nd == 3 ? launch(k_hist_smem<2, 1>) : launch(k_hist_smem<1, 1>);
+                if (st != VUP_OK) return st;
             }
         } else {
+            dim3 grd((unsigned)(P_max * G), (unsigned)nkt);
             k_hist_global<<<grd, kHistWarps * 32, 0, s>>>(A, G);
+            VUP_CHECK_LAUNCH();
         }
-        VUP_CHECK_LAUNCH();
     }
     VUP_PROF("hist_fixup", s, 1);
     dim3 fg((unsigned)ceil_div64(K, 128), (unsigned)g->B);
@@ -930,7 +955,9 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
     VUP_CHECK_CUDA(cudaMemcpy(P->fitems.p, fin.data(), sizeof(int4) * fin.size(), cudaMemcpyHostToDevice));
     // the largest tile any plan may use, so that graphs of earlier plans stay launchable
     VUP_CHECK_CUDA(
-        cudaFuncSetAttribute(k_hist_batched<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+        cudaFuncSetAttribute(k_hist_batched<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    VUP_CHECK_CUDA(
+        cudaFuncSetAttribute(k_hist_batched<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     *out = P;
     return VUP_OK;
 }
@@ -950,10 +977,13 @@ vup_status vup_hist_batched(void *plan, cudaStream_t s) {
     const size_t smem = hist_smem_bytes(P->rows);
     if (smem > 220 * 1024) return VUP_ERR_UNSUPPORTED;
     {
-        VUP_PROF("hist_segmented_batched", s, 1);
+        VUP_PROF("hist_segmented_batched", s, 2);
         const int grid = std::max(1, std::min(P->n_items, vup_num_sms()));
-        k_hist_batched<1><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
-                                                              (const HistItem *)P->items.p, P->n_items, P->rows);
+        k_hist_batched<1, 0><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
+                                                                 (const HistItem *)P->items.p, P->n_items, P->rows);
+        VUP_CHECK_LAUNCH();
+        k_hist_batched<1, 1><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
+                                                                 (const HistItem *)P->items.p, P->n_items, P->rows);
         VUP_CHECK_LAUNCH();
     }
     VUP_PROF("hist_fixup_batched", s, 1);

@@ -94,20 +94,21 @@ struct vup_grid_s {
     int natural_valid = 0;         // perm holds the stable sort by bin
 
     // counting-sort scratch
-    DevBuf sort_counts, scan_tmp;
+    DevBuf sort_counts, scan_tmp, lay_tmp;
 
     // histogram point streams.  Layout 0 gathers the last axis per point and
     // forms runs over the other axes; on 2-D grids layout 1 swaps the roles
     // (points ordered by (bin, a1, a0)).  The device picks the layout with
-    // fewer runs (hist_sel) after both are built.
+    // fewer intervals (hist_sel[0], counted before sorting) and builds only
+    // that one: the arrays live in hl[0], hl[1] holds layout 1's geometry and
+    // aliases them.
     struct HistLayout {
         int last_axis = -1;            // axis gathered per point
         int64_t n_last = 0;
         int P = 1;                     // parts of the gathered axis (shared-memory tiles)
         int64_t part_rows = 0;         // gathered-axis rows per part
-        int32_t *binsT = nullptr;      // layout 1: bins in transposed order
         int32_t *keys = nullptr;       // sort key of the layout's flat index: part * B + bin
-        int32_t *keys_own = nullptr;   // [N] key storage when keys != bins
+        int32_t *keys_own = nullptr;   // [N] key storage
         int32_t *koff = nullptr;       // [P * B + 1] key offsets in the sorted stream
         int2 *key_chunks = nullptr;    // [P * B] first and last chunk of each key's points (-1 if empty)
         int32_t koff_cap = 0;
@@ -130,9 +131,8 @@ struct vup_grid_s {
     } hl[2];
     int hist_P = 1;                // max parts over layouts (scratch sizing)
     int n_layouts = 1;
-    int32_t *hist_sel = nullptr;   // [2] device: chosen layout, 1 = interval stream
+    int32_t *hist_sel = nullptr;   // [4] device: chosen layout, 1 = interval stream, intervals of layouts 0 / 1
     int hist_force = -1;           // -1 auto, 0 points only, 1 intervals only
-    int32_t *flags_scan = nullptr; // [N] scratch
     int32_t n_chunks = 0;
 
     // power tables per orientation (kOrient*)
