@@ -162,6 +162,7 @@ extern "C" const char *vup_last_error_detail(void) { return g_last_err; }
 
 static void free_grid(vup_grid g) {
     cudaFree(g->y);
+    cudaFree(g->axis_terms);
     cudaFree(g->ext);
     cudaFree(g->bins);
     cudaFree(g->perm);
@@ -269,6 +270,7 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
 #define ALLOC(ptr, bytes) \
     if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
     ALLOC(g->y, sizeof(double) * N);
+    ALLOC(g->axis_terms, sizeof(double2) * (size_t)(g->n[0] + (ndim > 1 ? g->n[1] : 0) + (ndim > 2 ? g->n[2] : 0)));
     ALLOC(g->ext, sizeof(unsigned long long) * 2);
     ALLOC(g->bins, sizeof(int32_t) * N);
     ALLOC(g->perm, sizeof(int32_t) * N);
@@ -432,8 +434,7 @@ vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa, bool tf32)
         if ((st = devbuf_reserve(g->partials, sizeof(float) * 4 * K_pad * nct)) != VUP_OK) return st;
         if ((st = devbuf_reserve(g->hist_part, sizeof(float) * 2 * K_pad * g->n_chunks * g->hist_P)) != VUP_OK)
             return st;
-        if (g->hist_P > 1 &&
-            (st = devbuf_reserve(g->hist_direct, sizeof(float) * (size_t)g->hist_P * K * g->B)) != VUP_OK)
+        if ((st = devbuf_reserve(g->hist_direct, sizeof(float) * (size_t)g->hist_P * g->B * K_pad)) != VUP_OK)
             return st;
         if (tf32) {
             const size_t a = (size_t)K_pad * g->orient[vup_tc_orient(g)].R_pad;

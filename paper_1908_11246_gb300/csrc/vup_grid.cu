@@ -111,6 +111,96 @@ __global__ void k_model_eval(double *__restrict__ y, int64_t N, GridGeom G, int 
     }
 }
 
+// Separable built-in models: the transcendental and per-axis products are
+// evaluated once per axis index (two FP64 terms per index, stored after the
+// previous axes' terms), and every grid point only adds and multiplies its
+// axes' terms -- the same operations in the same order as model_value, so y
+// is bit-identical to the per-point evaluation.
+__host__ __device__ inline bool model_separable(int model, int ndim) {
+    return (model == VUP_MODEL_SIN_SIN2_2D && ndim == 2) || (model == VUP_MODEL_MIXED_3D && ndim == 3) ||
+           (model == VUP_MODEL_IPSA_EXAMPLE_2D && ndim == 2) || (model == VUP_MODEL_POLY && ndim >= 2);
+}
+
+__global__ void k_axis_terms(GridGeom G, int model, Theta th, double2 *__restrict__ terms) {
+    int64_t off = 0;
+    for (int d = 0; d < G.ndim; ++d) {
+        for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < G.n[d];
+             a += (int64_t)gridDim.x * blockDim.x) {
+            const double x = grid_x(G.lo[d], G.h[d], a);
+            double2 t = make_double2(0.0, 0.0);
+            switch (model) {
+            case VUP_MODEL_SIN_SIN2_2D:
+                if (d == 0) {
+                    t.x = __dmul_rn(th.t[0], sin(x));
+                } else {
+                    const double s2 = sin(x);
+                    t.x = __dmul_rn(th.t[1], __dmul_rn(s2, s2));
+                }
+                break;
+            case VUP_MODEL_MIXED_3D:
+                if (d == 0) {
+                    t.x = sin(x);
+                } else if (d == 1) {
+                    const double s2 = sin(x);
+                    t.x = __dmul_rn(th.t[0], __dmul_rn(s2, s2));
+                } else {
+                    const double x2 = __dmul_rn(x, x);
+                    t.x = __dmul_rn(th.t[1], __dmul_rn(x2, x2));
+                }
+                break;
+            case VUP_MODEL_IPSA_EXAMPLE_2D:
+                if (d == 0) t.x = __dadd_rn(__dmul_rn(x, x), __dmul_rn(5.0, sin(__dmul_rn(3.0, x))));
+                else t.x = x;
+                break;
+            default:  // VUP_MODEL_POLY
+                t.x = __dmul_rn(th.t[1 + 2 * d], x);
+                t.y = __dmul_rn(th.t[2 + 2 * d], __dmul_rn(x, x));
+                break;
+            }
+            terms[off + a] = t;
+        }
+        off += G.n[d];
+    }
+}
+
+__global__ void k_model_combine(double *__restrict__ y, int64_t N, GridGeom G, int model, Theta th,
+                                const double2 *__restrict__ terms) {
+    const int64_t o1 = G.n[0], o2 = G.n[0] + G.n[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a[3];
+        int64_t rem = i;
+        for (int d = G.ndim - 1; d >= 0; --d) {
+            a[d] = rem % G.n[d];
+            rem /= G.n[d];
+        }
+        double v;
+        switch (model) {
+        case VUP_MODEL_SIN_SIN2_2D:
+        case VUP_MODEL_IPSA_EXAMPLE_2D:
+            v = __dadd_rn(terms[a[0]].x, terms[o1 + a[1]].x);
+            break;
+        case VUP_MODEL_MIXED_3D: {
+            const double s1 = terms[a[0]].x, b = terms[o1 + a[1]].x, c = terms[o2 + a[2]].x;
+            v = __dadd_rn(__dadd_rn(s1, b), __dmul_rn(c, s1));
+            break;
+        }
+        default: {  // VUP_MODEL_POLY
+            v = th.t[0];
+            int64_t off = 0;
+            for (int d = 0; d < G.ndim; ++d) {
+                const double2 t = terms[off + a[d]];
+                v = __dadd_rn(v, t.x);
+                v = __dadd_rn(v, t.y);
+                off += G.n[d];
+            }
+            break;
+        }
+        }
+        y[i] = v;
+    }
+}
+
 // Order-preserving map of a double to an unsigned key (for exact atomic min/max).
 __device__ __forceinline__ unsigned long long dkey(double v) {
     unsigned long long u = (unsigned long long)__double_as_longlong(v);
@@ -589,15 +679,6 @@ struct Store<float> {
         o[idx] = (float)v;
     }
 };
-template <>
-struct Store<__nv_bfloat16> {
-    static __device__ __forceinline__ void put(__nv_bfloat16 *o, __nv_bfloat16 *o2, int64_t idx, double v) {
-        __nv_bfloat16 h = __double2bfloat16(v);
-        double r = v - (double)__bfloat162float(h);
-        o[idx] = h;
-        o2[idx] = __double2bfloat16(r);
-    }
-};
 
 // TF32 pair: hi = v rounded to TF32 (10 explicit mantissa bits, stored in a
 // float), lo = the remainder rounded to TF32.
@@ -664,6 +745,45 @@ __global__ void k_power_table(const double *__restrict__ y, int64_t P, int64_t S
         double v = z;
         for (int q = 0; q < j; ++q) v = v * z;
         Store<T>::put(out, out2, idx, v);
+    }
+}
+
+// Split BF16 power table (the tensor-core B operand): z = y / s_scale, then
+// z^j in FP32 and the BF16 hi / lo split of each.  z comes from one FP64
+// product with 1 / s_scale rounded once to FP32 (within an FP32 ulp of
+// y / s_scale), the powers carry at most three more FP32 roundings: far below
+// the 2^-17 relative resolution of the hi + lo pair.  FP64 stays on the
+// per-element path only for that one product (FP64 is the slow pipe here).
+// Modes 0 and 2 of k_power_table.
+__global__ void k_power_table_bf16(const double *__restrict__ y, int64_t P, int64_t S,
+                                   const double *__restrict__ sc, int mode, int64_t ld,
+                                   __nv_bfloat16 *__restrict__ out, __nv_bfloat16 *__restrict__ out2) {
+    __shared__ float tile[32][33];
+    const int64_t p0 = (int64_t)blockIdx.y * 32, s0 = (int64_t)blockIdx.x * 32;
+    const double inv = 1.0 / sc[0];
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t p = p0 + r, s = s0 + threadIdx.x;
+        tile[r][threadIdx.x] = (p < P && s < S) ? (float)__dmul_rn(y[p * S + s], inv) : 0.f;
+    }
+    __syncthreads();
+    const int tid = threadIdx.y * 32 + threadIdx.x, nthr = 32 * blockDim.y;
+    for (int e = tid; e < 32 * 32 * 4; e += nthr) {
+        int lp, ls, j;
+        int64_t idx;
+        if (mode == 0) {  // rows (p, j), cols s
+            ls = e & 31; j = (e >> 5) & 3; lp = e >> 7;
+            idx = ((p0 + lp) * 4 + j) * ld + (s0 + ls);
+        } else {          // rows (s, j), cols p
+            lp = e & 31; j = (e >> 5) & 3; ls = e >> 7;
+            idx = ((s0 + ls) * 4 + j) * ld + (p0 + lp);
+        }
+        if (p0 + lp >= P || s0 + ls >= S) continue;
+        const float z = tile[lp][ls];
+        float v = z;
+        for (int q = 0; q < j; ++q) v *= z;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        out[idx] = h;
+        out2[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
 }
 
@@ -741,8 +861,17 @@ vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta, 
     for (int q = 0; q < 8; ++q) th.t[q] = theta[q];
     GridGeom G = geom_of(g);
     int blocks = (int)std::min<int64_t>(ceil_div64(g->N, 256), (int64_t)vup_num_sms() * 16);
-    VUP_PROF("model_eval", s, 1);
-    k_model_eval<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th);
+    const bool sep = model_separable(model_id, g->ndim);
+    VUP_PROF("model_eval", s, sep ? 2 : 1);
+    if (sep) {
+        int64_t nmax = 1;
+        for (int d = 0; d < g->ndim; ++d) nmax = std::max(nmax, g->n[d]);
+        k_axis_terms<<<(unsigned)ceil_div64(nmax, 128), 128, 0, s>>>(G, model_id, th, g->axis_terms);
+        VUP_CHECK_LAUNCH();
+        k_model_combine<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th, g->axis_terms);
+    } else {
+        k_model_eval<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th);
+    }
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }
@@ -985,8 +1114,8 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
         VUP_CHECK_CUDA(cudaMemsetAsync(g->zt_hi[orient], 0, bytes, s));
         VUP_CHECK_CUDA(cudaMemsetAsync(g->zt_lo[orient], 0, bytes, s));
         // tensor wants [q*4+j][r]: orientation 0 -> rows (p, j) (mode 0); 1 -> rows (s, j) (mode 2)
-        k_power_table<__nv_bfloat16><<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, first ? 2 : 0, ld,
-                                                         g->zt_hi[orient], g->zt_lo[orient]);
+        k_power_table_bf16<<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, first ? 2 : 0, ld, g->zt_hi[orient],
+                                               g->zt_lo[orient]);
         VUP_CHECK_LAUNCH();
     }
     g->have_tab[orient][bf16] = 1;

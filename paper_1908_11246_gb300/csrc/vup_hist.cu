@@ -134,12 +134,7 @@ struct Flusher {
             const int side = (key == first_key) ? 0 : 1;
             *reinterpret_cast<float4 *>(A.part + ((int64_t)c * 2 + side) * A.K_pad + k) = val;
         } else {
-            const int b = key - p * A.B;
-            float *out = H.P > 1 ? A.direct + (int64_t)p * A.K * A.B : A.hist;
-            if (k < A.K) out[k * A.B + b] = val.x;
-            if (k + 1 < A.K) out[(k + 1) * A.B + b] = val.y;
-            if (k + 2 < A.K) out[(k + 2) * A.B + b] = val.z;
-            if (k + 3 < A.K) out[(k + 3) * A.B + b] = val.w;
+            *reinterpret_cast<float4 *>(A.direct + (int64_t)key * A.K_pad + k) = val;
         }
     }
 };
@@ -178,30 +173,26 @@ __device__ __forceinline__ void fma4(float4 &a, float4 w, float4 b) {
 struct ItemCtx {
     LayoutArgs H;
     float *part;   // [P * C][2][K_pad] partial sums of keys cut by chunk bounds
-    float *out;    // [K][B] whole-key sums of this part (hist, or direct + p K B)
+    float *direct; // [P * B][K_pad] sums of keys held by one chunk
     int64_t K, K_pad;
     int B, C, group_chunks;
     int mode;      // 0: point stream, tile holds factors; 1: interval stream, tile holds prefix sums
     int *dstatus;
 };
 
-// Store the finished sums of one key for a lane's four densities: keys cut by
-// the chunk bounds go to the chunk's partials (side 0 = its first key), the
-// others straight to the output.  Out of line: it runs once per key, and
-// keeping it out of the point loop keeps that loop's code small.
+// Store the finished sums of one key for a lane's four densities (16 bytes,
+// density-contiguous: one coalesced 512-byte row per warp): keys cut by the
+// chunk bounds go to the chunk's partials (side 0 = its first key), the
+// others to the key's row of the direct sums.  A one-part histogram also
+// goes through the direct rows: scattered 4-byte stores into the [K][B]
+// output from the point loop measured slower than the coalesced rows plus
+// the finishing copy.  Out of line: it runs once per key, and keeping it
+// out of the point loop keeps that loop's code small.
 __device__ __noinline__ void flush_key(const ItemCtx *X, int c, int p, int64_t k, int32_t key, float4 v,
                                        bool shared, bool first) {
-    if (shared) {
-        *reinterpret_cast<float4 *>(X->part + ((int64_t)c * 2 + (first ? 0 : 1)) * X->K_pad + k) = v;
-    } else {
-        const int B = X->B;
-        const int64_t K = X->K;
-        float *o = X->out + k * B + (key - p * B);
-        if (k < K) o[0] = v.x;
-        if (k + 1 < K) o[B] = v.y;
-        if (k + 2 < K) o[2 * B] = v.z;
-        if (k + 3 < K) o[3 * B] = v.w;
-    }
+    float *dst = shared ? X->part + ((int64_t)c * 2 + (first ? 0 : 1)) * X->K_pad + k
+                        : X->direct + (int64_t)key * X->K_pad + k;
+    *reinterpret_cast<float4 *>(dst) = v;
 }
 
 // Interval stream of chunk c (part p): interval i adds f_i (P[b_i] - P[a_i])
@@ -360,7 +351,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         *next_chunk = 0;
         X.H = A.sel[0] ? A.L1 : A.L0;
         X.part = A.part;
-        X.out = X.H.P > 1 ? A.direct + (int64_t)p * A.K * A.B : A.hist;
+        X.direct = A.direct;
         X.K = A.K;
         X.K_pad = A.K_pad;
         X.B = A.B;
@@ -712,48 +703,73 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_global(HistArgs A, 
     }
 }
 
-// Finish H[k, b]: for every part, the key (part, b) is either empty, written
-// directly by the single chunk that holds it, or cut by chunk boundaries and
-// summed from the partials of the chunks overlapping it (in chunk order);
-// parts are added in order.  With one part, directly written bins are final.
-__device__ __forceinline__ void hist_finish_body(const HistArgs &A, const LayoutArgs &H, int64_t kb, int b) {
-    const int64_t k = kb * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= A.K || b >= A.B) return;
-    float total = 0.f;
-    bool touched = H.P > 1;
-    for (int p = 0; p < H.P; ++p) {
-        const int32_t key = p * A.B + b;
-        const int2 cc = H.key_chunks[key];  // chunks holding the key's points, precomputed per layout
-        if (cc.x < 0) continue;
-        const int c0 = cc.x, c1 = cc.y;
-        if (c0 == c1) {
-            if (H.P > 1) total += A.direct[((int64_t)p * A.K + k) * A.B + b];
-            continue;
-        }
-        touched = true;
-        float s = 0.f;
-        for (int c = c0; c <= c1; ++c) {
-            if (H.chunk_pt[c] >= H.chunk_pt[c + 1]) continue;
-            const int side = H.chunk_bin[2 * c] == key ? 0 : 1;
-            s += A.part[((int64_t)c * 2 + side) * A.K_pad + k];
-        }
-        total += s;
+// Finish H[k, b]: for every part, the key (part, b) is either empty, summed
+// whole by the single chunk that holds it (direct row), or cut by chunk
+// boundaries and summed from the partials of the chunks overlapping it (in
+// chunk order); parts are added in order.  A tile of 128 densities x 8 bins
+// per 256 threads: warp w takes bin w, each lane four consecutive densities,
+// so the direct rows and partials are read as coalesced 512-byte rows; the
+// tile goes to the [K][B] output through shared memory (8 consecutive bins,
+// one 32-byte sector, per row).
+constexpr int kFinK = 128, kFinB = 8;
+constexpr int kFinMaxP = 96;  // >= parts of any axis: ceil(32767 / kMaxPartRows) = 84
+__device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0, int nkt, int bt) {
+    __shared__ float tile[kFinB][kFinK + 1];
+    __shared__ int2 s_cc[kFinMaxP][kFinB];
+    const LayoutArgs &H = A.sel[0] ? A.L1 : A.L0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int P = H.P;
+    // the chunk range of every (part, bin) key of the bin tile
+    for (int e = threadIdx.x; e < P * kFinB; e += blockDim.x) {
+        const int p = e / kFinB, bb = e - p * kFinB, b = bt * kFinB + bb;
+        s_cc[p][bb] = b < A.B ? H.key_chunks[p * A.B + b] : make_int2(-1, -1);
     }
-    if (H.P == 1 && H.key_chunks[b].x < 0) touched = true;  // empty bin: zero
-    if (touched) A.hist[k * A.B + b] = total;
+    __syncthreads();
+    const int b = bt * kFinB + warp;
+    for (int64_t kt = kt0; kt < kt0 + nkt; ++kt) {
+        const int64_t k = kt * kFinK + 4 * lane;
+        float4 total = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (b < A.B) {
+#pragma unroll 4
+            for (int p = 0; p < P; ++p) {
+                const int2 cc = s_cc[p][warp];
+                const int32_t key = p * A.B + b;
+                if (cc.x < 0) continue;
+                    if (cc.x == cc.y) {
+                    add4(total, *reinterpret_cast<const float4 *>(A.direct + (int64_t)key * A.K_pad + k));
+                    continue;
+                }
+                float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int c = cc.x; c <= cc.y; ++c) {
+                    if (H.chunk_pt[c] >= H.chunk_pt[c + 1]) continue;
+                    const int side = H.chunk_bin[2 * c] == key ? 0 : 1;
+                    add4(sum, *reinterpret_cast<const float4 *>(A.part + ((int64_t)c * 2 + side) * A.K_pad + k));
+                }
+                add4(total, sum);
+            }
+        }
+        float *row = tile[warp] + 4 * lane;
+        row[0] = total.x;
+        row[1] = total.y;
+        row[2] = total.z;
+        row[3] = total.w;
+        __syncthreads();
+        for (int e = threadIdx.x; e < kFinK * kFinB; e += blockDim.x) {
+            const int kk = e / kFinB, bb = e - kk * kFinB;
+            const int64_t kr = kt * kFinK + kk;
+            const int bo = bt * kFinB + bb;
+            if (kr < A.K && bo < A.B) A.hist[kr * A.B + bo] = tile[bb][kk];
+        }
+        __syncthreads();  // the tile is reused by the next density tile
+    }
 }
 
-__global__ void k_hist_finish(HistArgs A) {
-    const LayoutArgs H = pick(A);
-    hist_finish_body(A, H, blockIdx.x, blockIdx.y);
-}
+__global__ void k_hist_finish(const __grid_constant__ HistArgs A) { hist_finish_tiles(A, blockIdx.x, 1, blockIdx.y); }
 
-// Batched finish: items[i] = (instance, density block, first of 8 bins).
+// Batched finish: items[i] = (instance, density tile, bin tile).
 __global__ void k_hist_finish_batched(const HistArgs *__restrict__ insts, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
-    const HistArgs A = insts[it.x];
-    const LayoutArgs H = pick(A);
-    for (int b = it.z; b < it.z + 8; ++b) hist_finish_body(A, H, it.y, b);
+    hist_finish_tiles(insts[it.x], it.y, 1, it.z);
 }
 
 }  // namespace
@@ -888,8 +904,8 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
         }
     }
     VUP_PROF("hist_fixup", s, 1);
-    dim3 fg((unsigned)ceil_div64(K, 128), (unsigned)g->B);
-    k_hist_finish<<<fg, 128, 0, s>>>(A);
+    dim3 fg((unsigned)ceil_div64(K, kFinK), (unsigned)ceil_div64(g->B, kFinB));
+    k_hist_finish<<<fg, 32 * kFinB, 0, s>>>(A);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }
@@ -930,8 +946,8 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
         for (int p = 0; p < P_max; ++p)
             for (int cg = 0; cg < G; ++cg)
                 for (int64_t kt = 0; kt < nkt; ++kt) work.push_back({cost, HistItem{i, p, cg, (int32_t)kt}});
-        for (int64_t kb = 0; kb < ceil_div64(Ks[i], 128); ++kb)
-            for (int b0 = 0; b0 < gs[i]->B; b0 += 8) fin.push_back(make_int4(i, (int)kb, b0, 0));
+        for (int64_t kb = 0; kb < ceil_div64(Ks[i], kFinK); ++kb)
+            for (int bt = 0; bt < (int)ceil_div64(gs[i]->B, kFinB); ++bt) fin.push_back(make_int4(i, (int)kb, bt, 0));
     }
     std::stable_sort(work.begin(), work.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
     std::vector<HistItem> items(work.size());
@@ -987,7 +1003,8 @@ vup_status vup_hist_batched(void *plan, cudaStream_t s) {
         VUP_CHECK_LAUNCH();
     }
     VUP_PROF("hist_fixup_batched", s, 1);
-    k_hist_finish_batched<<<P->n_fitems, 128, 0, s>>>((const HistArgs *)P->args.p, (const int4 *)P->fitems.p);
+    k_hist_finish_batched<<<P->n_fitems, 32 * kFinB, 0, s>>>((const HistArgs *)P->args.p,
+                                                             (const int4 *)P->fitems.p);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }

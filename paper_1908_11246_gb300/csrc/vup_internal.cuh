@@ -86,6 +86,7 @@ struct vup_grid_s {
     double host_ext[3] = {0, 0, 1};  // ymin, ymax, s (filled lazily by vup_grid_info)
 
     double *y = nullptr;           // [N]
+    double2 *axis_terms = nullptr; // [sum_d n_d] per-axis terms of separable built-in models
     unsigned long long *ext = nullptr;  // [2] ordered-bits min / max of y
     int32_t *bins = nullptr;       // [N]
     int32_t *perm = nullptr;       // [N] sorted position -> flat index
