@@ -570,7 +570,7 @@ def main():
                                   "weights"))}
     stage = {"model_eval_bins_sort_tables": 0.0, "moments": 0.0, "histogram": 0.0, "ipsa": 0.0, "other": 0.0}
     for k, v in per_step.items():
-        if k.startswith(("model_eval", "range_bins", "power_table")):
+        if k.startswith(("model_eval", "range_bins", "layout_sort", "power_table")):
             stage["model_eval_bins_sort_tables"] += v["ms_per_step"]
         elif k.startswith(("moments", "density_prep")):
             stage["moments"] += v["ms_per_step"]
@@ -597,7 +597,9 @@ def main():
         "config": cfg,
         "roofline": roof,
         "kernels": {"per_step": per_step, "stage_ms_per_step": stage, "roofline": kern_roof,
-                    "timing": "CUDA events per kernel group inside the timed region" if profile_live
+                    "timing": ("CUDA events per kernel group inside the timed region (the layout build runs "
+                               "on a second stream beside the density preparation and the contraction, so "
+                               "group times can add up to more than ms_per_step)") if profile_live
                     else "per-stage CUDA events from a second pass of the same steps (stage by stage)"},
         "gpu_launches": int(sum(v[0] for v in prof.values())),
         "clocks": clk,

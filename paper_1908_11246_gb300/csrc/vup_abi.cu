@@ -187,6 +187,9 @@ static void free_grid(vup_grid g) {
         cudaFree(L.chunk_iv);
     }
     cudaFree(g->hist_sel);
+    if (g->side) cudaStreamDestroy(g->side);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
     cudaFree(g->ydev_scale);
     cudaFree(g->dstatus);
     for (int o = 0; o < kNumOrient; ++o) {
@@ -477,6 +480,34 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
     const bool tf32 = precision == VUP_TF32 || precision == VUP_TF32X3;
     const bool want_m = moments_raw || moments_central;
     if ((st = vup_reserve_k(g, K, bf16, false, tf32)) != VUP_OK) return st;
+    // the histogram layout (when not built for this model yet) on the second
+    // stream, beside the density preparation and the contraction
+    bool forked = false;
+    if (hist && !g->layout_valid) {
+        if (!g->side) {
+            VUP_CHECK_CUDA(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+            VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+            VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+        }
+        VUP_CHECK_CUDA(cudaEventRecord(g->ev_fork, s));
+        VUP_CHECK_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+        vup_status lst = vup_build_layout(g, g->side);
+        VUP_CHECK_CUDA(cudaEventRecord(g->ev_join, g->side));
+        forked = true;
+        if (lst != VUP_OK) {
+            cudaStreamWaitEvent(s, g->ev_join, 0);
+            return lst;
+        }
+    }
+    // every return below joins the second stream back into the caller's
+    struct Join {
+        bool on;
+        cudaStream_t s;
+        cudaEvent_t e;
+        ~Join() {
+            if (on) cudaStreamWaitEvent(s, e, 0);
+        }
+    } join{forked, s, g->ev_join};
     const int to = vup_tc_orient(g);
     if (want_m && (st = vup_build_tables(g, (bf16 || tf32) ? to : kOrientLast, tf32 ? 2 : (bf16 ? 1 : 0), s)) !=
                       VUP_OK)
@@ -496,6 +527,10 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
         if ((st = vup_moments_finish(g, K, (int)nct, moments_raw, moments_central, s)) != VUP_OK) return st;
     }
     if (hist) {
+        if (forked) {
+            VUP_CHECK_CUDA(cudaStreamWaitEvent(s, g->ev_join, 0));
+            join.on = false;
+        }
         if ((st = vup_hist_fused(g, K, hist, s)) != VUP_OK) return st;
     }
     return VUP_OK;
@@ -587,6 +622,11 @@ extern "C" vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info) {
         info->ymax = inv(k[1]);
         info->yscale = sc;
         if (g->ndim >= 2) {
+            if (!g->layout_valid) {
+                vup_status st = vup_build_layout(g, 0);
+                if (st != VUP_OK) return st;
+                VUP_CHECK_CUDA(cudaDeviceSynchronize());
+            }
             int32_t sel[2] = {0, 0}, nr = 0, ni = 0;
             VUP_CHECK_CUDA(cudaMemcpy(sel, g->hist_sel, sizeof(sel), cudaMemcpyDeviceToHost));
             const auto &HL = g->hl[sel[0] == 1 && g->n_layouts > 1 ? 1 : 0];
@@ -604,7 +644,8 @@ extern "C" vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info) {
 extern "C" vup_status vup_set_hist_stream(vup_grid g, int32_t stream_kind, vup_stream_t stream) {
     if (!g || g->ndim < 2 || stream_kind < -1 || stream_kind > 1) return VUP_ERR_INVALID_ARG;
     g->hist_force = stream_kind;
-    if (g->have_model) return vup_pick_hist_layout(g, (cudaStream_t)stream);
+    // a layout built later applies the choice itself
+    if (g->have_model && g->layout_valid) return vup_pick_hist_layout(g, (cudaStream_t)stream);
     return VUP_OK;
 }
 
@@ -623,7 +664,14 @@ extern "C" vup_status vup_grid_copy(vup_grid g, int which, void *dst_dev, size_t
         need = sizeof(int32_t) * g->N;
         break;
     }
-    case 3: src = g->offsets; need = sizeof(int32_t) * (g->B + 1); break;
+    case 3: {
+        // 2-D / 3-D grids take the bin offsets from the histogram layout
+        vup_status st = vup_ensure_layout(g, (cudaStream_t)stream);
+        if (st != VUP_OK) return st;
+        src = g->offsets;
+        need = sizeof(int32_t) * (g->B + 1);
+        break;
+    }
     default: return VUP_ERR_INVALID_ARG;
     }
     if (nbytes != need) return VUP_ERR_INVALID_ARG;

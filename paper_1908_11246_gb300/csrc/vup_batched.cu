@@ -236,6 +236,7 @@ extern "C" vup_status vup_propagate_batched(int n_inst, const vup_grid *g, const
             vup_status st;
             if ((st = vup_reserve_k(g[i], K, bf16, false)) != VUP_OK) return st;
             if ((st = vup_build_tables(g[i], kOrientLast, bf16 ? 1 : 0, s)) != VUP_OK) return st;
+            if (hist && hist[i] && (st = vup_ensure_layout(g[i], s)) != VUP_OK) return st;
             if ((st = vup_density_reserve(g[i], K)) != VUP_OK) return st;
             if (bf16 &&
                 (st = devbuf_reserve(g[i]->partials,

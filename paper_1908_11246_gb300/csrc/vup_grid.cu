@@ -260,15 +260,31 @@ __global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
     double ymin, ymax;
     read_range(ext, ymin, ymax);
     const double range = __dsub_rn(ymax, ymin);
+    // FP32 screen: t32 = (y - ymin) B / range within eps of the exact t; where
+    // no integer lies within eps of t32, floor(t32) is the bin, otherwise the
+    // FP64 expression decides (about one point in 10^4 on smooth models).
+    // Error of t32: the FP32 roundings of y, ymin, the difference, B / range
+    // and the product, each <= 2^-24 relative: |t32 - t| <= 2^-24 ((|y| +
+    // |ymin|) B / range (2 + 2) + |t| 2); eps doubles that bound.
+    const float ymin32 = (float)ymin;
+    const float sc32 = range > 0.0 ? (float)((double)B / range) : 0.f;
     if (tile < n_tiles) {
         const int64_t i0 = tile * kSortTile;
         const int64_t i1 = min(N, i0 + kSortTile);
         for (int64_t i = i0 + lane; i < i1; i += 32) {
             int32_t b = 0;
             if (range > 0.0) {
-                double t = __ddiv_rn(__dsub_rn(y[i], ymin), range);
-                double f = floor(__dmul_rn(t, (double)B));
-                b = (int32_t)f;
+                const double yv = y[i];
+                const float y32 = (float)yv;
+                const float t32 = (y32 - ymin32) * sc32;
+                const float fl32 = floorf(t32);
+                const float eps = 0x1p-21f * ((fabsf(y32) + fabsf(ymin32)) * sc32 * 2.f + fabsf(t32)) + 0x1p-60f;
+                if (t32 - fl32 > eps && fl32 + 1.f - t32 > eps) {
+                    b = (int32_t)fl32;
+                } else {
+                    const double t = __ddiv_rn(__dsub_rn(yv, ymin), range);
+                    b = (int32_t)floor(__dmul_rn(t, (double)B));
+                }
                 b = b > B - 1 ? B - 1 : b;
                 b = b < 0 ? 0 : b;
             }
@@ -320,13 +336,14 @@ __global__ void k_iv_count(const int32_t *__restrict__ bins, int64_t n0, int64_t
                            int32_t *__restrict__ cnt) {
     const int64_t N = n0 * n1;
     int32_t c0 = 0, c1 = 0;
-    const int64_t pr0 = L.g[0].part_rows, pr1 = L.g[1].part_rows;
+    const uint32_t p0 = (uint32_t)L.g[0].part_rows, p1 = (uint32_t)L.g[1].part_rows;
+    const uint32_t m1 = (uint32_t)n1;  // N < 2^31: 32-bit index arithmetic
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i0 = i / n1, i1 = i - i0 * n1;
+        const uint32_t i0 = (uint32_t)i / m1, i1 = (uint32_t)i - i0 * m1;
         const int32_t b = bins[i];
         // layout 0 gathers axis 1, layout 1 axis 0
-        c0 += i1 == 0 || (i1 / pr0) * B + b != ((i1 - 1) / pr0) * B + bins[i - 1];
-        c1 += i0 == 0 || (i0 / pr1) * B + b != ((i0 - 1) / pr1) * B + bins[i - n1];
+        c0 += i1 == 0 || (i1 / p0) * B + b != ((i1 - 1) / p0) * B + bins[i - 1];
+        c1 += i0 == 0 || (i0 / p1) * B + b != ((i0 - 1) / p1) * B + bins[i - n1];
     }
     for (int o = 16; o > 0; o >>= 1) {
         c0 += __shfl_xor_sync(0xffffffffu, c0, o);
@@ -930,7 +947,7 @@ vup_status vup_natural_sort(vup_grid g, cudaStream_t s) {
 vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     const int64_t N = g->N;
     const int B = g->B;
-    ProfScope prof("range_bins_sort_runs", s, 0);
+    ProfScope prof("range_bins", s, 0);
     int launches = 3;  // minmax, scale, bins
     // exact range of y
     VUP_CHECK_CUDA(cudaMemsetAsync(g->ext, 0xff, sizeof(unsigned long long), s));
@@ -996,7 +1013,30 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
         if (st != VUP_OK) return st;
         g->natural_valid = 1;
         launches += 2 + scan_launches((int64_t)B * n_tiles);
-    } else {
+    }
+    g->layout_valid = g->ndim == 1;
+    prof.launches = launches;
+    for (int o = 0; o < kNumOrient; ++o) g->have_tab[o][0] = g->have_tab[o][1] = g->have_tab[o][2] = 0;
+    return VUP_OK;
+}
+
+// The histogram layout of a 2-D / 3-D grid (sorted point and interval
+// streams, chunks, the natural bin offsets) for the current bins.  Built on
+// first use after a model evaluation (the histogram, the bin offsets), so a
+// caller may run it on a second stream beside the density preparation.
+vup_status vup_build_layout(vup_grid g, cudaStream_t s) {
+    const int64_t N = g->N;
+    const int B = g->B;
+    ProfScope prof("layout_sort_runs", s, 0);
+    int launches = 0;
+    int Bk_max = B;
+    for (int l = 0; l < g->n_layouts; ++l) Bk_max = std::max(Bk_max, g->hl[l].P * B);
+    const int64_t n_tiles = ceil_div64(N, kSortTile);
+    int32_t *scratch = (int32_t *)g->scan_tmp.p;
+    int32_t *counts = (int32_t *)g->sort_counts.p;
+    const int blocks = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
+    vup_status st;
+    {
         const int C = g->n_chunks;
         auto &HL = g->hl[0];
         LaySel L;
@@ -1056,9 +1096,13 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
         // chunk keys, key chunks, natural offsets, stream choice
         launches += 1 + 3 + scan_launches((int64_t)Bk_max * n_tiles) + 1 + scan_launches(N) + 2 + 5;
     }
+    g->layout_valid = 1;
     prof.launches = launches;
-    for (int o = 0; o < kNumOrient; ++o) g->have_tab[o][0] = g->have_tab[o][1] = g->have_tab[o][2] = 0;
     return VUP_OK;
+}
+
+vup_status vup_ensure_layout(vup_grid g, cudaStream_t s) {
+    return g->layout_valid ? VUP_OK : vup_build_layout(g, s);
 }
 
 vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s) {

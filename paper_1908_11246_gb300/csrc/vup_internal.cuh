@@ -93,6 +93,11 @@ struct vup_grid_s {
     int32_t *offsets = nullptr;    // [B_cap + 1]
     int32_t B_cap = 0;
     int natural_valid = 0;         // perm holds the stable sort by bin
+    int layout_valid = 0;          // the histogram layout matches the current bins
+    // second stream for the layout build beside the density preparation
+    // (forked from and joined back into the caller's stream)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // counting-sort scratch
     DevBuf sort_counts, scan_tmp, lay_tmp;
@@ -158,8 +163,11 @@ struct vup_grid_s {
 vup_status vup_launch_model_at(vup_grid g, int64_t K, const double *x, double *y, cudaStream_t s);
 vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta,
                                  cudaStream_t s);
-vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s);  // range, bins, sort, runs, tables
+vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s);  // range, bins (1-D: the sorted order)
 vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s);
+// Histogram layout (2-D / 3-D): built on first use after a model evaluation.
+vup_status vup_build_layout(vup_grid g, cudaStream_t s);
+vup_status vup_ensure_layout(vup_grid g, cudaStream_t s);
 vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s);
 vup_status vup_natural_sort(vup_grid g, cudaStream_t s);
 
