@@ -187,18 +187,22 @@ def traffic_for(kernel, workload):
     return None
 
 
-def roofline_for(name, ms, launches, KN, pk, clk_mhz, workload, hist_units=None):
-    """Algorithmic work of one launch of `name` divided by its event-timed duration.
+def roofline_for(name, ms, n_work, units, pk, clk_mhz, workload, hist_units=None):
+    """Algorithmic work of one working launch of `name` divided by its event-timed duration.
 
-    hist_units: shared-memory factor gathers of one histogram launch (density x
-    point on the point stream, density x 2 per interval on the interval stream)."""
-    per = ms / max(launches, 1) * 1e-3
+    ms: device time of the group over the timed steps; n_work: the launches in
+    it that do the work (the histogram's launch for the stream the device did
+    not choose returns at once and is not counted); units: dist-points one
+    working launch covers (every contraction launch, moments or one IPSA
+    orientation, covers all K x N); hist_units: shared-memory factor gathers of
+    one histogram pass (density x point on the point stream, density x 2 per
+    interval on the interval stream)."""
+    per = ms / max(n_work, 1) * 1e-3
     sms = 152
     tr = traffic_for(name, workload)
     if name.startswith("moments_bf16") or name.startswith("ipsa_bf16"):
-        # the IPSA launches run the same contraction once per orientation
         fl = 24.0
-        a = fl * KN / launches / per / 1e12
+        a = fl * units / per / 1e12
         return {"bound": "tensor", "achieved": a, "peak": pk["bf16_sus"], "unit": "TFLOP/s",
                 "frac": a / pk["bf16_sus"], "traffic": tr,
                 "note": f"{fl:g} tensor flops/dist-point (BF16x3, J=4) per launch; peak = sustained bf16, "
@@ -206,7 +210,7 @@ def roofline_for(name, ms, launches, KN, pk, clk_mhz, workload, hist_units=None)
     if name.startswith("moments_tf32"):
         fl = 24.0 if name.startswith("moments_tf32x3") else 8.0
         peak = pk["bf16_sus"] * 1.1 / 2.25   # TF32 dense = bf16 x (1.1 / 2.25) nominal ratio
-        a = fl * KN / launches / per / 1e12
+        a = fl * units / per / 1e12
         return {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
                 "traffic": tr,
                 "note": f"{fl:g} tensor flops/dist-point (TF32, J=4); peak = sustained bf16 x 1.1/2.25, "
@@ -214,20 +218,22 @@ def roofline_for(name, ms, launches, KN, pk, clk_mhz, workload, hist_units=None)
     if name.startswith("moments_fp32") or name.startswith("ipsa_fp32"):
         fl = 8.0 if name.startswith("moments") else 24.0
         peak = sms * 128 * 2 * clk_mhz * 1e6 / 1e12
-        a = fl * KN / launches / per / 1e12
+        a = fl * units / per / 1e12
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
                 "traffic": tr, "note": f"{fl:g} FP32 flops/dist-point; peak = 152 SM x 128 FMA x 2 x median SM clock"}
     if name.startswith("hist_seg"):
         peak = sms * 128 * clk_mhz * 1e6 / 1e9
-        units = hist_units if hist_units else KN / launches
-        a = 4.0 * units / per / 1e9
+        a = 4.0 * (hist_units or units) / per / 1e9
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": tr,
-                "note": "4-byte shared-memory factor gathers per launch (one per density and point on the "
+                "note": "4-byte shared-memory factor gathers per pass (one per density and point on the "
                         "point stream, two per density and interval on the interval stream); peak = 152 SM x "
                         "128 B/clk shared-memory bandwidth x median SM clock"}
-    a = 4.0 * KN / launches / per / 1e9
+    a = 4.0 * units / per / 1e9
     return {"bound": "hbm", "achieved": a, "peak": pk["hbm"], "unit": "GB/s", "frac": a / pk["hbm"],
             "traffic": tr, "note": f"4 B/dist-point; peak = measured copy bandwidth, of {pk['source']}"}
+
+
+ROOF_GROUPS = ("moments_bf16", "moments_fp32", "moments_tf32", "ipsa_bf16", "ipsa_fp32", "hist_seg", "weights")
 
 
 WORKLOADS = {
@@ -263,6 +269,7 @@ class SingleGrid:
         self.ipsa = name == "c4"
         self.sa = name == "ipsa"
         self.bayes = name == "bayes"
+        self.hist_passes = 1 + prob.ndim if self.bayes else 1  # posterior means: H, then one pass per axis
         self.prec = prec
         self.g = vup.Grid(prob.n, prob.lo, prob.hi)
         self.dev = vup.densities_to_device(prob.dens)
@@ -551,8 +558,10 @@ def main():
     clk_mhz = clk["sm_mhz"] if clk else pk["sm_max"]
     per_step = {k: {"launches": v[0] / args.steps, "ms_per_step": v[1] / args.steps} for k, v in prof.items()}
     wl = args.config + (f"_k{work.K}" if args.k else "")
-    dominant = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
-    KN = work.units * args.steps
+    # dominant: the costliest group with a roofline (groups on the second stream
+    # overlap others and are not candidates)
+    cands = {k: v for k, v in prof.items() if k.startswith(ROOF_GROUPS)}
+    dominant = max(cands.items(), key=lambda kv: kv[1][1])[0] if cands else None
     # gathers of one histogram launch on the stream each grid's layout chose
     hist_units, streams = 0, set()
     for g, K in work.hist_grids():
@@ -560,14 +569,18 @@ def main():
         if info.ndim >= 2:
             streams.add("intervals" if info.hist_stream else "points")
             hist_units += K * (2 * info.hist_intervals if info.hist_stream else info.N)
-    roof = (roofline_for(dominant, prof[dominant][1], prof[dominant][0], KN, pk, clk_mhz, wl, hist_units)
-            if dominant else None)
+    def n_work(k, launches):
+        # histogram: one working launch per pass (the other stream's launch exits at once)
+        if k.startswith("hist_seg"):
+            return args.steps * getattr(work, "hist_passes", 1)
+        return launches
+
+    def roof_of(k, v):
+        return roofline_for(k, v[1], n_work(k, v[0]), work.units, pk, clk_mhz, wl, hist_units)
+    roof = roof_of(dominant, prof[dominant]) if dominant else None
     if roof:
         roof["kernel"] = dominant
-    kern_roof = {k: roofline_for(k, v[1], v[0], KN, pk, clk_mhz, wl, hist_units)
-                 for k, v in prof.items()
-                 if k.startswith(("moments_bf16", "moments_fp32", "moments_tf32", "ipsa_bf16", "ipsa_fp32", "hist_seg",
-                                  "weights"))}
+    kern_roof = {k: roof_of(k, v) for k, v in prof.items() if k.startswith(ROOF_GROUPS)}
     stage = {"model_eval_bins_sort_tables": 0.0, "moments": 0.0, "histogram": 0.0, "ipsa": 0.0, "other": 0.0}
     for k, v in per_step.items():
         if k.startswith(("model_eval", "range_bins", "layout_sort", "power_table")):
