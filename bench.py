@@ -564,11 +564,13 @@ def main():
     dominant = max(cands.items(), key=lambda kv: kv[1][1])[0] if cands else None
     # gathers of one histogram launch on the stream each grid's layout chose
     hist_units, streams = 0, set()
+    points_only = getattr(work, "bayes", False)  # posterior means walk the point stream
     for g, K in work.hist_grids():
         info = g.info()
         if info.ndim >= 2:
-            streams.add("intervals" if info.hist_stream else "points")
-            hist_units += K * (2 * info.hist_intervals if info.hist_stream else info.N)
+            iv = info.hist_stream and not points_only
+            streams.add("intervals" if iv else "points")
+            hist_units += K * (2 * info.hist_intervals if iv else info.N)
     def n_work(k, launches):
         # histogram: one working launch per pass (the other stream's launch exits at once)
         if k.startswith("hist_seg"):
