@@ -634,15 +634,22 @@ struct HistItem {
 template <int NF, int MODE>
 __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_batched(const HistArgs *__restrict__ insts,
                                                                      const HistItem *__restrict__ items,
-                                                                     int n_items, int64_t tile_rows) {
+                                                                     int n_items, int64_t tile_rows,
+                                                                     int *__restrict__ next_item) {
     extern __shared__ __align__(128) uint8_t sm[];
     __shared__ ItemCtx X;
     __shared__ float s_invz[kKT];
-    __shared__ int abort, next_chunk;
+    __shared__ int abort, next_chunk, s_it;
     if (threadIdx.x == 0) abort = 0;
     hist_init_mbar(sm, tile_rows);
     uint32_t wseq = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    // items are handed out one at a time in their (longest first) order
+    for (;;) {
+        __syncthreads();  // every thread has read the previous s_it
+        if (threadIdx.x == 0) s_it = atomicAdd(next_item, 1);
+        __syncthreads();
+        const int it = s_it;
+        if (it >= n_items) break;
         const HistItem w = items[it];
         if (hist_stream(insts[w.inst]) != MODE) continue;  // uniform
         hist_item<NF, MODE>(insts + w.inst, w.p, w.cg, (int64_t)w.kt * kKT, sm, tile_rows, wseq, &abort, X, s_invz,
@@ -922,7 +929,7 @@ bool vup_hist_batchable(vup_grid g) {
 // instance's (part, chunk group, density tile) items, longest first, and one
 // finishing launch.
 struct HistPlan {
-    DevBuf args, items, fitems;
+    DevBuf args, items, fitems, ctr;  // ctr: next item of each stream's launch
     int n_items = 0, n_fitems = 0;
     int64_t rows = 0;
 };
@@ -959,10 +966,12 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
     vup_status st;
     if ((st = devbuf_reserve(P->args, sizeof(HistArgs) * n)) != VUP_OK ||
         (st = devbuf_reserve(P->items, sizeof(HistItem) * std::max<size_t>(1, items.size()))) != VUP_OK ||
-        (st = devbuf_reserve(P->fitems, sizeof(int4) * std::max<size_t>(1, fin.size()))) != VUP_OK) {
+        (st = devbuf_reserve(P->fitems, sizeof(int4) * std::max<size_t>(1, fin.size()))) != VUP_OK ||
+        (st = devbuf_reserve(P->ctr, sizeof(int) * 2)) != VUP_OK) {
         devbuf_free(P->args);
         devbuf_free(P->items);
         devbuf_free(P->fitems);
+        devbuf_free(P->ctr);
         delete P;
         return st;
     }
@@ -984,6 +993,7 @@ void vup_hist_plan_free(void *plan) {
     devbuf_free(P->args);
     devbuf_free(P->items);
     devbuf_free(P->fitems);
+    devbuf_free(P->ctr);
     delete P;
 }
 
@@ -995,11 +1005,15 @@ vup_status vup_hist_batched(void *plan, cudaStream_t s) {
     {
         VUP_PROF("hist_segmented_batched", s, 2);
         const int grid = std::max(1, std::min(P->n_items, vup_num_sms()));
+        int *ctr = (int *)P->ctr.p;
+        VUP_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(int), s));
         k_hist_batched<1, 0><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
-                                                                 (const HistItem *)P->items.p, P->n_items, P->rows);
+                                                                 (const HistItem *)P->items.p, P->n_items, P->rows,
+                                                                 ctr);
         VUP_CHECK_LAUNCH();
         k_hist_batched<1, 1><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
-                                                                 (const HistItem *)P->items.p, P->n_items, P->rows);
+                                                                 (const HistItem *)P->items.p, P->n_items, P->rows,
+                                                                 ctr + 1);
         VUP_CHECK_LAUNCH();
     }
     VUP_PROF("hist_fixup_batched", s, 1);
