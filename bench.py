@@ -194,9 +194,10 @@ def roofline_for(name, ms, n_work, units, pk, clk_mhz, workload, hist_units=None
     it that do the work (the histogram's launch for the stream the device did
     not choose returns at once and is not counted); units: dist-points one
     working launch covers (every contraction launch, moments or one IPSA
-    orientation, covers all K x N); hist_units: shared-memory factor gathers of
-    one histogram pass (density x point on the point stream, density x 2 per
-    interval on the interval stream)."""
+    orientation, covers all K x N); hist_units: bytes one histogram pass moves
+    through the SM's L1 data pipe by its algorithm (per density: 4 per point +
+    4 per rest-factor row per run on the point stream; 8 of prefix sums + 4 per
+    rest-factor row per interval on the interval stream)."""
     per = ms / max(n_work, 1) * 1e-3
     sms = 152
     tr = traffic_for(name, workload)
@@ -223,11 +224,11 @@ def roofline_for(name, ms, n_work, units, pk, clk_mhz, workload, hist_units=None
                 "traffic": tr, "note": f"{fl:g} FP32 flops/dist-point; peak = 152 SM x 128 FMA x 2 x median SM clock"}
     if name.startswith("hist_seg"):
         peak = sms * 128 * clk_mhz * 1e6 / 1e9
-        a = 4.0 * (hist_units or units) / per / 1e9
+        a = (hist_units or 4.0 * units) / per / 1e9
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": tr,
-                "note": "4-byte shared-memory factor gathers per pass (one per density and point on the "
-                        "point stream, two per density and interval on the interval stream); peak = 152 SM x "
-                        "128 B/clk shared-memory bandwidth x median SM clock"}
+                "note": "bytes through the L1 data pipe that the walk needs per pass (per density: point stream "
+                        "4 per point + 4 per rest-factor row per run; interval stream 8 of prefix sums + 4 per "
+                        "rest-factor row per interval); peak = 152 SM x 128 B/clk x median SM clock"}
     a = 4.0 * units / per / 1e9
     return {"bound": "hbm", "achieved": a, "peak": pk["hbm"], "unit": "GB/s", "frac": a / pk["hbm"],
             "traffic": tr, "note": f"4 B/dist-point; peak = measured copy bandwidth, of {pk['source']}"}
@@ -570,7 +571,11 @@ def main():
         if info.ndim >= 2:
             iv = info.hist_stream and not points_only
             streams.add("intervals" if iv else "points")
-            hist_units += K * (2 * info.hist_intervals if iv else info.N)
+            nf = info.ndim - 1  # rest-factor rows per run or interval
+            if iv:
+                hist_units += K * info.hist_intervals * (8 + 4 * nf)
+            else:
+                hist_units += K * (4 * info.N + 4 * nf * info.hist_runs)
     def n_work(k, launches):
         # histogram: one working launch per pass (the other stream's launch exits at once)
         if k.startswith("hist_seg"):

@@ -563,7 +563,7 @@ extern "C" vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, v
     if ((st = vup_reserve_k(g, K, bf16, true)) != VUP_OK) return st;
     if ((st = vup_build_tables(g, 0, bf16 ? 1 : 0, s)) != VUP_OK) return st;
     if ((st = vup_build_tables(g, 1, bf16 ? 1 : 0, s)) != VUP_OK) return st;
-    if ((st = vup_density_prep(g, d, bf16 ? 3 : 0, s)) != VUP_OK) return st;
+    if ((st = vup_density_prep(g, d, bf16 ? 3 : 0, s, false, true)) != VUP_OK) return st;
     const int64_t K_pad = ceil_div64(K, 128) * 128;
     float *p0 = (float *)g->ipsa_part.p;
     int64_t n0, n1;

@@ -103,7 +103,7 @@ __device__ __forceinline__ int64_t first_true(int64_t b, int64_t e, P pred) {
 // outside).  EXACT_F32: every a - n in the segment is below 2^24 in
 // magnitude, so A is carried as an FP32 counter; otherwise A is rounded
 // from FP64 per cell.
-template <bool EXACT_F32>
+template <bool EXACT_F32, bool STATS>
 __device__ __forceinline__ void prep_segment(float *__restrict__ tab, int64_t K_pad, int kind, int64_t a_begin,
                                              int64_t a_end, int64_t in_b, int64_t in_e, const GaussArg &ga,
                                              KSum &S0, KSum &S1, KSum &S2) {
@@ -123,8 +123,10 @@ __device__ __forceinline__ void prep_segment(float *__restrict__ tab, int64_t K_
         }
         tab[a * K_pad] = g;
         S0.add(g);
-        S1.add(g * u);
-        S2.add(g * u * u);
+        if (STATS) {
+            S1.add(g * u);
+            S2.add(g * u * u);
+        }
     }
 }
 
@@ -149,6 +151,7 @@ struct DensJob {
 
 // Density factors of densities kb*128 .. kb*128+127 on axis d, segment z of
 // that axis: the factor table entries and partial compensated sums.
+template <bool STATS>
 __device__ __forceinline__ void density_prep_body(const DensJob &J, int64_t kb, int d, int z) {
     const int64_t k = kb * (int64_t)blockDim.x + threadIdx.x;
     if (k >= J.K_pad) return;
@@ -207,9 +210,9 @@ __device__ __forceinline__ void density_prep_body(const DensJob &J, int64_t kb, 
     KSum S0, S1, S2;
     const double A0 = (double)a_begin - nk;
     if (fabs(A0) + (double)(a_end - a_begin) < 16777216.0)
-        prep_segment<true>(tab + k, K_pad, kind, a_begin, a_end, in_b, in_e, ga, S0, S1, S2);
+        prep_segment<true, STATS>(tab + k, K_pad, kind, a_begin, a_end, in_b, in_e, ga, S0, S1, S2);
     else
-        prep_segment<false>(tab + k, K_pad, kind, a_begin, a_end, in_b, in_e, ga, S0, S1, S2);
+        prep_segment<false, STATS>(tab + k, K_pad, kind, a_begin, a_end, in_b, in_e, ga, S0, S1, S2);
     if (z == 0) {
         DensConst dc;
         dc.n = (int32_t)fmax(fmin(nk, 2147483647.0), -2147483647.0);
@@ -363,7 +366,9 @@ __global__ void __launch_bounds__(256) k_split_product_rows(const float *__restr
     }
 }
 
-__global__ void k_density_prep(DensJob J) { density_prep_body(J, blockIdx.x, blockIdx.y, blockIdx.z); }
+// STATS: also the sums of g u and g u^2 (E[u], E[u^2] of the IPSA derivatives)
+template <bool STATS>
+__global__ void k_density_prep(DensJob J) { density_prep_body<STATS>(J, blockIdx.x, blockIdx.y, blockIdx.z); }
 __global__ void k_density_finish(DensJob J) { density_finish_body(J, blockIdx.x, blockIdx.y); }
 // grid: x = density tiles of 32 (K_pad / 32 may exceed the 65535 limit of y), y = axis tiles
 template <typename T>
@@ -376,7 +381,7 @@ __global__ void k_split_transpose(const float *__restrict__ tab, int64_t nd, int
 // (instance, block coordinates) of block b.
 __global__ void k_density_prep_batched(const DensJob *__restrict__ jobs, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
-    density_prep_body(jobs[it.x], it.y, it.z, it.w);
+    density_prep_body<false>(jobs[it.x], it.y, it.z, it.w);
 }
 __global__ void k_density_finish_batched(const DensJob *__restrict__ jobs, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
@@ -441,14 +446,15 @@ template <typename T>
 static vup_status split_tables(vup_grid g, int mask, int64_t K_pad, T *hi0, T *lo0, cudaStream_t s);
 
 vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_orient_mask, cudaStream_t s,
-                            bool tf32) {
+                            bool tf32, bool stats) {
     vup_status st = vup_density_reserve(g, d->K);
     if (st != VUP_OK) return st;
     const DensJob J = make_job(g, d);
     const int64_t K_pad = J.K_pad;
     dim3 grd((unsigned)ceil_div64(K_pad, 128), (unsigned)g->ndim, (unsigned)J.S);
     VUP_PROF("density_prep", s, 2 + __builtin_popcount(need_bf16_orient_mask));
-    k_density_prep<<<grd, 128, 0, s>>>(J);
+    if (stats) k_density_prep<true><<<grd, 128, 0, s>>>(J);
+    else k_density_prep<false><<<grd, 128, 0, s>>>(J);
     VUP_CHECK_LAUNCH();
     dim3 fgrd((unsigned)ceil_div64(d->K, 128), (unsigned)g->ndim);
     k_density_finish<<<fgrd, 128, 0, s>>>(J);

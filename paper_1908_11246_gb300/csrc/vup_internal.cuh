@@ -172,9 +172,10 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s);
 vup_status vup_natural_sort(vup_grid g, cudaStream_t s);
 
 // Density factors and normalisers; the A-operand split tables of the
-// orientations in the mask (BF16 into atab_*, or TF32 into atf_* when tf32).
+// orientations in the mask (BF16 into atab_*, or TF32 into atf_* when tf32);
+// stats: also E[u] and E[u^2] per (k, d) (the IPSA derivatives need them).
 vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_orient_mask,
-                            cudaStream_t s, bool tf32 = false);
+                            cudaStream_t s, bool tf32 = false, bool stats = false);
 vup_status vup_moments_simt(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s);
 // Tensor-core contraction; kind 0 = BF16 operands, 1 = TF32 operands;
 // terms = 3 split products or 1 (hi only).
