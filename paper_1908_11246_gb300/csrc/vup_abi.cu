@@ -485,7 +485,11 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
     bool forked = false;
     if (hist && !g->layout_valid) {
         if (!g->side) {
-            VUP_CHECK_CUDA(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+            // high priority: the layout's small latency-bound launches take SMs as
+            // they free up, ahead of the main stream's large kernels
+            int lo_prio = 0, hi_prio = 0;
+            VUP_CHECK_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+            VUP_CHECK_CUDA(cudaStreamCreateWithPriority(&g->side, cudaStreamNonBlocking, hi_prio));
             VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
             VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
         }
