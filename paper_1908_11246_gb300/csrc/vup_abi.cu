@@ -414,6 +414,7 @@ extern "C" vup_status vup_set_outputs(vup_grid g, const double *y_dev, int n_bin
     g->have_model = 0;
     g->model_id = 0;
     VUP_CHECK_CUDA(cudaMemcpyAsync(g->y, y_dev, sizeof(double) * g->N, cudaMemcpyDeviceToDevice, s));
+    g->range_ready = 0;
     return finish_model(g, s);
 }
 

@@ -97,7 +97,53 @@ struct GridGeom {
     double h[3];
 };
 
-__global__ void k_model_eval(double *__restrict__ y, int64_t N, GridGeom G, int model, Theta th) {
+// Order-preserving map of a double to an unsigned key (for exact atomic min/max).
+__device__ __forceinline__ unsigned long long dkey(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+    unsigned long long u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)u);
+}
+
+// Exact min / max of y into ext[0], ext[1] (order-preserving keys): reduced
+// over the block first, then one atomic pair per block.  Called by every
+// thread of the block (blockDim.x <= 1024).
+__device__ __forceinline__ void range_reduce(unsigned long long mn, unsigned long long mx, unsigned long long *ext) {
+    __shared__ unsigned long long s_mn[32], s_mx[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+        mn = a < mn ? a : mn;
+        mx = b > mx ? b : mx;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        s_mn[warp] = mn;
+        s_mx[warp] = mx;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        mn = lane < nw ? s_mn[lane] : ~0ull;
+        mx = lane < nw ? s_mx[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+            mn = a < mn ? a : mn;
+            mx = b > mx ? b : mx;
+        }
+        if (lane == 0) {
+            atomicMin(&ext[0], mn);
+            atomicMax(&ext[1], mx);
+        }
+    }
+}
+
+// y at every grid point, and its exact range into ext (reset beforehand).
+__global__ void k_model_eval(double *__restrict__ y, int64_t N, GridGeom G, int model, Theta th,
+                             unsigned long long *ext) {
+    unsigned long long mn = ~0ull, mx = 0ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t rem = i;
@@ -107,8 +153,13 @@ __global__ void k_model_eval(double *__restrict__ y, int64_t N, GridGeom G, int 
             rem /= G.n[d];
             x[d] = grid_x(G.lo[d], G.h[d], a);
         }
-        y[i] = model_value(model, th, x, G.ndim);
+        const double v = model_value(model, th, x, G.ndim);
+        y[i] = v;
+        const unsigned long long k = dkey(v);
+        mn = k < mn ? k : mn;
+        mx = k > mx ? k : mx;
     }
+    range_reduce(mn, mx, ext);
 }
 
 // Separable built-in models: the transcendental and per-axis products are
@@ -164,8 +215,9 @@ __global__ void k_axis_terms(GridGeom G, int model, Theta th, double2 *__restric
 }
 
 __global__ void k_model_combine(double *__restrict__ y, int64_t N, GridGeom G, int model, Theta th,
-                                const double2 *__restrict__ terms) {
+                                const double2 *__restrict__ terms, unsigned long long *ext) {
     const int64_t o1 = G.n[0], o2 = G.n[0] + G.n[1];
+    unsigned long long mn = ~0ull, mx = 0ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t a[3];
@@ -198,19 +250,14 @@ __global__ void k_model_combine(double *__restrict__ y, int64_t N, GridGeom G, i
         }
         }
         y[i] = v;
+        const unsigned long long kv = dkey(v);
+        mn = kv < mn ? kv : mn;
+        mx = kv > mx ? kv : mx;
     }
+    range_reduce(mn, mx, ext);
 }
 
-// Order-preserving map of a double to an unsigned key (for exact atomic min/max).
-__device__ __forceinline__ unsigned long long dkey(double v) {
-    unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double dkey_inv(unsigned long long k) {
-    unsigned long long u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
-    return __longlong_as_double((long long)u);
-}
-
+// Exact range of caller-supplied outputs (the model kernels reduce it as they write y).
 __global__ void k_minmax(const double *__restrict__ y, int64_t N, unsigned long long *ext) {
     unsigned long long mn = ~0ull, mx = 0ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
@@ -219,16 +266,7 @@ __global__ void k_minmax(const double *__restrict__ y, int64_t N, unsigned long 
         mn = k < mn ? k : mn;
         mx = k > mx ? k : mx;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
-        unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
-        mn = a < mn ? a : mn;
-        mx = b > mx ? b : mx;
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(&ext[0], mn);
-        atomicMax(&ext[1], mx);
-    }
+    range_reduce(mn, mx, ext);
 }
 
 // Output range and the power-table scale s = max(|ymin|, |ymax|) (1 if 0).
@@ -248,14 +286,18 @@ __global__ void k_scale(const unsigned long long *ext, double *s_out) {
 // every operation correctly rounded and unfused, as in the FP64 oracle.
 // Also counts points per (bin, warp tile) for the stable counting sort.
 // The CTA has blockDim.x / 32 warps, each owning one tile of kSortTile points.
+// COUNT = false (2-D / 3-D grids, whose layouts sort their own keys): bins only.
+template <bool COUNT>
 __global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
                              const unsigned long long *ext, int32_t *__restrict__ bins,
                              int32_t *__restrict__ counts, int64_t n_tiles) {
     extern __shared__ int32_t s_cnt[];  // [warps][B]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t *cnt = s_cnt + warp * B;
-    for (int b = lane; b < B; b += 32) cnt[b] = 0;
-    __syncwarp();
+    if (COUNT) {
+        for (int b = lane; b < B; b += 32) cnt[b] = 0;
+        __syncwarp();
+    }
     const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     double ymin, ymax;
     read_range(ext, ymin, ymax);
@@ -289,10 +331,12 @@ __global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
                 b = b < 0 ? 0 : b;
             }
             bins[i] = b;
-            atomicAdd(&cnt[b], 1);
+            if (COUNT) atomicAdd(&cnt[b], 1);
         }
-        __syncwarp();
-        for (int b = lane; b < B; b += 32) counts[(int64_t)b * n_tiles + tile] = cnt[b];
+        if (COUNT) {
+            __syncwarp();
+            for (int b = lane; b < B; b += 32) counts[(int64_t)b * n_tiles + tile] = cnt[b];
+        }
     }
 }
 
@@ -877,18 +921,21 @@ vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta, 
     Theta th;
     for (int q = 0; q < 8; ++q) th.t[q] = theta[q];
     GridGeom G = geom_of(g);
-    int blocks = (int)std::min<int64_t>(ceil_div64(g->N, 256), (int64_t)vup_num_sms() * 16);
+    int blocks = (int)std::min<int64_t>(ceil_div64(g->N, 256), (int64_t)vup_num_sms() * 8);
     const bool sep = model_separable(model_id, g->ndim);
     VUP_PROF("model_eval", s, sep ? 2 : 1);
+    VUP_CHECK_CUDA(cudaMemsetAsync(g->ext, 0xff, sizeof(unsigned long long), s));
+    VUP_CHECK_CUDA(cudaMemsetAsync(g->ext + 1, 0x00, sizeof(unsigned long long), s));
     if (sep) {
         int64_t nmax = 1;
         for (int d = 0; d < g->ndim; ++d) nmax = std::max(nmax, g->n[d]);
         k_axis_terms<<<(unsigned)ceil_div64(nmax, 128), 128, 0, s>>>(G, model_id, th, g->axis_terms);
         VUP_CHECK_LAUNCH();
-        k_model_combine<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th, g->axis_terms);
+        k_model_combine<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th, g->axis_terms, g->ext);
     } else {
-        k_model_eval<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th);
+        k_model_eval<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th, g->ext);
     }
+    g->range_ready = 1;
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }
@@ -948,13 +995,17 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     const int64_t N = g->N;
     const int B = g->B;
     ProfScope prof("range_bins", s, 0);
-    int launches = 3;  // minmax, scale, bins
-    // exact range of y
-    VUP_CHECK_CUDA(cudaMemsetAsync(g->ext, 0xff, sizeof(unsigned long long), s));
-    VUP_CHECK_CUDA(cudaMemsetAsync(g->ext + 1, 0x00, sizeof(unsigned long long), s));
+    int launches = 2;  // scale, bins
+    // exact range of y (already reduced by the model kernels for built-in models)
     int blocks = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
-    k_minmax<<<blocks, 256, 0, s>>>(g->y, N, g->ext);
-    VUP_CHECK_LAUNCH();
+    if (!g->range_ready) {
+        VUP_CHECK_CUDA(cudaMemsetAsync(g->ext, 0xff, sizeof(unsigned long long), s));
+        VUP_CHECK_CUDA(cudaMemsetAsync(g->ext + 1, 0x00, sizeof(unsigned long long), s));
+        k_minmax<<<blocks, 256, 0, s>>>(g->y, N, g->ext);
+        VUP_CHECK_LAUNCH();
+        ++launches;
+    }
+    g->range_ready = 0;
     k_scale<<<1, 1, 0, s>>>(g->ext, g->ydev_scale);
     VUP_CHECK_LAUNCH();
 
@@ -998,12 +1049,18 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
 
     // bins (Eq. 4), counted per tile for the sort by bin
     {
-        const int nw = sort_warps(B);
-        const size_t smem = sizeof(int32_t) * (size_t)B * nw;
-        if (smem > 48 * 1024)
-            VUP_CHECK_CUDA(cudaFuncSetAttribute(k_bins_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_bins_count<<<(unsigned)ceil_div64(n_tiles, nw), 32 * nw, smem, s>>>(g->y, N, B, g->ext, g->bins, counts,
-                                                                              n_tiles);
+        if (g->ndim == 1) {
+            const int nw = sort_warps(B);
+            const size_t smem = sizeof(int32_t) * (size_t)B * nw;
+            if (smem > 48 * 1024)
+                VUP_CHECK_CUDA(
+                    cudaFuncSetAttribute(k_bins_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_bins_count<true><<<(unsigned)ceil_div64(n_tiles, nw), 32 * nw, smem, s>>>(g->y, N, B, g->ext, g->bins,
+                                                                                      counts, n_tiles);
+        } else {
+            k_bins_count<false><<<(unsigned)ceil_div64(n_tiles, kSortWarps), 32 * kSortWarps, 0, s>>>(
+                g->y, N, B, g->ext, g->bins, counts, n_tiles);
+        }
         VUP_CHECK_LAUNCH();
     }
     g->natural_valid = 0;

@@ -94,6 +94,7 @@ struct vup_grid_s {
     int32_t B_cap = 0;
     int natural_valid = 0;         // perm holds the stable sort by bin
     int layout_valid = 0;          // the histogram layout matches the current bins
+    int range_ready = 0;           // ext holds the range of y (reduced by the model kernels)
     // second stream for the layout build beside the density preparation
     // (forked from and joined back into the caller's stream)
     cudaStream_t side = nullptr;
