@@ -197,7 +197,8 @@ def roofline_for(name, ms, n_work, units, pk, clk_mhz, workload, hist_units=None
     orientation, covers all K x N); hist_units: bytes one histogram pass moves
     through the SM's L1 data pipe by its algorithm (per density: 4 per point +
     4 per rest-factor row per run on the point stream; 8 of prefix sums + 4 per
-    rest-factor row per interval on the interval stream)."""
+    rest-factor row per interval on the interval stream; 20 of prefix sums + 4
+    per rest-factor row per record on the record stream)."""
     per = ms / max(n_work, 1) * 1e-3
     sms = 152
     tr = traffic_for(name, workload)
@@ -228,7 +229,8 @@ def roofline_for(name, ms, n_work, units, pk, clk_mhz, workload, hist_units=None
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": tr,
                 "note": "bytes through the L1 data pipe that the walk needs per pass (per density: point stream "
                         "4 per point + 4 per rest-factor row per run; interval stream 8 of prefix sums + 4 per "
-                        "rest-factor row per interval); peak = 152 SM x 128 B/clk x median SM clock"}
+                        "rest-factor row per interval; record stream 20 of prefix sums + 4 per rest-factor row "
+                        "per record); peak = 152 SM x 128 B/clk x median SM clock"}
     a = 4.0 * units / per / 1e9
     return {"bound": "hbm", "achieved": a, "peak": pk["hbm"], "unit": "GB/s", "frac": a / pk["hbm"],
             "traffic": tr, "note": f"4 B/dist-point; peak = measured copy bandwidth, of {pk['source']}"}
@@ -457,8 +459,8 @@ def main():
     ap.add_argument("--k", type=int, default=0, help="use the first K densities of the workload (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--hist-stream", type=int, default=-1, choices=[-1, 0, 1],
-                    help="histogram stream: -1 automatic, 0 sorted points, 1 sorted intervals")
+    ap.add_argument("--hist-stream", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="histogram stream: -1 automatic, 0 sorted points, 1 sorted intervals, 2 records")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -569,10 +571,12 @@ def main():
     for g, K in work.hist_grids():
         info = g.info()
         if info.ndim >= 2:
-            iv = info.hist_stream and not points_only
-            streams.add("intervals" if iv else "points")
-            nf = info.ndim - 1  # rest-factor rows per run or interval
-            if iv:
+            mode = 0 if points_only else info.hist_stream
+            streams.add(("points", "intervals", "records")[mode])
+            nf = info.ndim - 1  # rest-factor rows per run, interval or record
+            if mode == 2:
+                hist_units += K * info.hist_records * (20 + 4 * nf)
+            elif mode == 1:
                 hist_units += K * info.hist_intervals * (8 + 4 * nf)
             else:
                 hist_units += K * (4 * info.N + 4 * nf * info.hist_runs)

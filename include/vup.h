@@ -357,18 +357,22 @@ typedef struct {
     /* histogram walk chosen for the current model (2-D / 3-D grids):
      * layout 0 gathers the last axis, layout 1 axis 0 (2-D only); stream 0
      * walks sorted points, stream 1 sorted intervals (stretches of one bin
-     * along the gathered axis, summed as differences of prefix sums).  Counts
-     * are those of the chosen layout. */
+     * along the gathered axis, summed as differences of prefix sums), stream
+     * 2 records (stretches of one line over a group of 4 consecutive bins,
+     * monotone, five prefix sums for four bins).  Counts are those of the
+     * chosen layout. */
     int32_t hist_layout, hist_stream;
-    int64_t hist_runs, hist_intervals;
+    int64_t hist_runs, hist_intervals, hist_records;
 } vup_grid_info_t;
 vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info);
 
 /*
  * Histogram stream choice of a 2-D / 3-D grid: -1 (default) picks, per model,
- * the layout and stream with the least estimated work; 0 restricts the choice
- * to point streams, 1 to interval streams.  Both give H[k, b] of Eq. 4 (sums
- * of the same terms in a different order).  Takes effect for the current
+ * the stream with the least estimated work; 0 forces the point stream, 1 the
+ * interval stream, 2 the record stream.  All give H[k, b] of Eq. 4 (sums of
+ * the same terms in a different order; the interval and record streams sum
+ * stretches as differences of prefix sums, whose error is absolute, about
+ * 2^-24 of a part's mass per stretch).  Takes effect for the current
  * model (queued on `stream`) and for later ones.  VUP_ERR_INVALID_ARG for
  * another value or a 1-D grid.
  */

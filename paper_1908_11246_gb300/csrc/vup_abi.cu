@@ -141,6 +141,7 @@ int vup_num_sms() {
 
 int vup_hist_chunks_for(int64_t N, int P);
 int vup_hist_parts_for(int64_t n_last, int n_bins);
+int vup_hist_rec_chunks_for(int n_chunks);
 
 extern "C" const char *vup_status_string(vup_status s) {
     switch (s) {
@@ -185,6 +186,13 @@ static void free_grid(vup_grid g) {
         cudaFree(L.iv_rest);
         cudaFree(L.n_iv);
         cudaFree(L.chunk_iv);
+        cudaFree(L.n_rec);
+        cudaFree(L.rec_chunk);
+        cudaFree(L.rec_chunk_grp);
+        devbuf_free(L.rec);
+        devbuf_free(L.rec_rest);
+        devbuf_free(L.rec_goff);
+        devbuf_free(L.rec_gch);
     }
     cudaFree(g->hist_sel);
     if (g->side) cudaStreamDestroy(g->side);
@@ -202,6 +210,7 @@ static void free_grid(vup_grid g) {
     devbuf_free(g->sort_counts);
     devbuf_free(g->scan_tmp);
     devbuf_free(g->lay_tmp);
+    devbuf_free(g->rec_tmp);
     devbuf_free(g->dconst);
     devbuf_free(g->dstats);
     devbuf_free(g->dpart);
@@ -268,6 +277,7 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
     for (int l = 0; l < (ndim == 2 ? 2 : 1); ++l)
         p_all = std::max(p_all, vup_hist_parts_for(g->n[l == 0 ? ndim - 1 : 0], 1));
     g->n_chunks = vup_hist_chunks_for(N, p_all);
+    g->n_chunks_rec = vup_hist_rec_chunks_for(g->n_chunks);
     const int C = g->n_chunks;
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, bytes) \
@@ -302,6 +312,9 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
             ALLOC(L.iv_rest, sizeof(int32_t) * N);
             ALLOC(L.n_iv, sizeof(int32_t));
             ALLOC(L.chunk_iv, sizeof(int32_t) * (p_max * C + 1));
+            ALLOC(L.n_rec, sizeof(int32_t));
+            ALLOC(L.rec_chunk, sizeof(int32_t) * (p_max * g->n_chunks_rec + 1));
+            ALLOC(L.rec_chunk_grp, sizeof(int32_t) * 2 * p_max * g->n_chunks_rec);
             // words past the stream's end are read by whole-window staging and
             // masked; zero keeps their rest codes valid indices
             if (e == cudaSuccess) e = cudaMemset(L.ipt, 0, sizeof(uint2) * (N + 128));
@@ -326,6 +339,9 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
         L.iv_rest = A.iv_rest;
         L.n_iv = A.n_iv;
         L.chunk_iv = A.chunk_iv;
+        L.n_rec = A.n_rec;
+        L.rec_chunk = A.rec_chunk;
+        L.rec_chunk_grp = A.rec_chunk_grp;
     }
     ALLOC(g->hist_sel, sizeof(int32_t) * 4);
     ALLOC(g->ydev_scale, sizeof(double));
@@ -436,7 +452,9 @@ vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa, bool tf32)
     if (nd >= 2) {
         const int64_t nct = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles(g->orient[vup_tc_orient(g)]));
         if ((st = devbuf_reserve(g->partials, sizeof(float) * 4 * K_pad * nct)) != VUP_OK) return st;
-        if ((st = devbuf_reserve(g->hist_part, sizeof(float) * 2 * K_pad * g->n_chunks * g->hist_P)) != VUP_OK)
+        // partial rows of cut keys (2 per chunk) or cut record groups (2 x 4 per record chunk)
+        const size_t part_rows = std::max<size_t>(2 * (size_t)g->n_chunks, 8 * (size_t)g->n_chunks_rec);
+        if ((st = devbuf_reserve(g->hist_part, sizeof(float) * part_rows * K_pad * g->hist_P)) != VUP_OK)
             return st;
         if ((st = devbuf_reserve(g->hist_direct, sizeof(float) * (size_t)g->hist_P * g->B * K_pad)) != VUP_OK)
             return st;
@@ -632,22 +650,24 @@ extern "C" vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info) {
                 if (st != VUP_OK) return st;
                 VUP_CHECK_CUDA(cudaDeviceSynchronize());
             }
-            int32_t sel[2] = {0, 0}, nr = 0, ni = 0;
+            int32_t sel[2] = {0, 0}, nr = 0, ni = 0, nrec = 0;
             VUP_CHECK_CUDA(cudaMemcpy(sel, g->hist_sel, sizeof(sel), cudaMemcpyDeviceToHost));
-            const auto &HL = g->hl[sel[0] == 1 && g->n_layouts > 1 ? 1 : 0];
+            const auto &HL = g->hl[0];  // the built layout's arrays
             VUP_CHECK_CUDA(cudaMemcpy(&nr, HL.n_runs, sizeof(int32_t), cudaMemcpyDeviceToHost));
             VUP_CHECK_CUDA(cudaMemcpy(&ni, HL.n_iv, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            VUP_CHECK_CUDA(cudaMemcpy(&nrec, HL.n_rec, sizeof(int32_t), cudaMemcpyDeviceToHost));
             info->hist_layout = sel[0];
             info->hist_stream = sel[1];
             info->hist_runs = nr;
             info->hist_intervals = ni;
+            info->hist_records = nrec;
         }
     }
     return VUP_OK;
 }
 
 extern "C" vup_status vup_set_hist_stream(vup_grid g, int32_t stream_kind, vup_stream_t stream) {
-    if (!g || g->ndim < 2 || stream_kind < -1 || stream_kind > 1) return VUP_ERR_INVALID_ARG;
+    if (!g || g->ndim < 2 || stream_kind < -1 || stream_kind > 2) return VUP_ERR_INVALID_ARG;
     g->hist_force = stream_kind;
     // a layout built later applies the choice itself
     if (g->have_model && g->layout_valid) return vup_pick_hist_layout(g, (cudaStream_t)stream);

@@ -453,12 +453,26 @@ __global__ void k_natural_offsets(const int32_t *__restrict__ koff, LaySel L, in
 // units of about 3.3 ps of kernel time per 128-density tile (fitted to
 // measured launches on 2-D and 3-D grids): point stream 4 per point (one
 // gather) + 20 per run (rest-factor pipeline); interval stream 19 per
-// interval (two gathers, a difference, a rest-factor load).  force: -1 both
-// allowed, 0 points only, 1 intervals only.
-__global__ void k_pick_stream(const int32_t *n_runs, const int32_t *n_iv, int64_t N, int force, int32_t *sel) {
+// interval (two gathers, a difference, a rest-factor load); record stream
+// 40 + 6 per extra rest axis per record (five gathers, four differences, one
+// rest-factor load per rest axis).  force: -1 any, else that stream.
+__global__ void k_pick_stream(const int32_t *n_runs, const int32_t *n_iv, const int32_t *n_rec, int64_t N,
+                              int nf, int force, int32_t *sel) {
     const int64_t c_pt = 4 * N + 20 * (int64_t)n_runs[0];
     const int64_t c_iv = 19 * (int64_t)n_iv[0];
-    sel[1] = force == 1 ? 1 : force == 0 ? 0 : (c_iv < c_pt ? 1 : 0);
+    const int64_t c_rec = (40 + 6 * nf) * (int64_t)n_rec[0];
+    int m = 0;
+    if (force >= 0) {
+        m = force;
+    } else {
+        int64_t best = c_pt;
+        if (c_iv < best) {
+            best = c_iv;
+            m = 1;
+        }
+        if (c_rec < best) m = 2;
+    }
+    sel[1] = m;
 }
 
 // Stable scatter: each warp walks its tile in order, 32 points at a time;
@@ -721,6 +735,208 @@ __global__ void k_key_chunks(const int32_t *__restrict__ koff, LaySel L, int B, 
     const int32_t o0 = koff[key], o1 = koff[key + 1];
     out[key] = o0 == o1 ? make_int2(-1, -1)
                         : make_int2(chunk_holding(chunk_pt, n_chunks, o0), chunk_holding(chunk_pt, n_chunks, o1 - 1));
+}
+
+// ---- record stream ------------------------------------------------------------
+// A record is a stretch of one line (every axis but the gathered one fixed)
+// inside one part whose points fall in one group of kRecBins consecutive bins
+// and whose bins change monotonically along the gathered axis.  Each bin of
+// the group then holds one sub-range of the stretch, and five boundaries
+// B_0..B_4 describe them all: bin 4q + j holds rows [B_j, B_j+1) when the
+// bins rise along the line, [B_j+1, B_j) when they fall (the record's sign),
+// an empty range when absent.  The histogram adds sign f_rest (P[B_j+1] -
+// P[B_j]) to each of the four bins from five prefix-sum gathers and one
+// rest-factor load, where the interval stream needs two gathers and a load per
+// bin.  Records come from the intervals in line order (maximal stretches of
+// one key along a line): a record starts at a line-part start, a group change,
+// or where the bin steps change sign inside a group.
+constexpr int kRecBins = 4;
+constexpr uint32_t kRecNeg = 1u << 30;  // bins fall along the line
+
+// Interval starts in layout order: the first point of a line-part or a key change.
+__global__ void k_liv_flags(const int32_t *__restrict__ keys, int64_t N, LaySel L, int32_t *__restrict__ flags) {
+    const int64_t n_last = L.get().n_last;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
+        flags[j] = (j % n_last == 0 || keys[j] != keys[j - 1]) ? 1 : 0;
+}
+
+__global__ void k_liv_emit(const int32_t *__restrict__ keys, int64_t N, const int32_t *__restrict__ flags,
+                           const int32_t *__restrict__ excl, int32_t *__restrict__ liv_key,
+                           int32_t *__restrict__ liv_pos, int32_t *__restrict__ n_liv) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        if (flags[j]) {
+            const int32_t i = excl[j];
+            liv_key[i] = keys[j];
+            liv_pos[i] = (int32_t)j;
+        }
+        if (j == N - 1) n_liv[0] = excl[j] + flags[j];
+    }
+}
+
+// Record starts among the line-order intervals (same line and key part as the
+// two before, same group, same direction of the bin steps: no start).
+__global__ void k_rec_flags(const int32_t *__restrict__ liv_key, const int32_t *__restrict__ liv_pos,
+                            const int32_t *__restrict__ n_liv_p, int B, LaySel L, int32_t *__restrict__ flags,
+                            int64_t N) {
+    const int64_t n_last = L.get().n_last;
+    const int32_t n = n_liv_p[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i >= n) {
+            flags[i] = 0;
+            continue;
+        }
+        // same line and part <=> same line and same key part; group within a part: bin / kRecBins
+        auto same = [&](int64_t u, int64_t v) {
+            return liv_pos[u] / n_last == liv_pos[v] / n_last && liv_key[u] / B == liv_key[v] / B &&
+                   (liv_key[u] % B) / kRecBins == (liv_key[v] % B) / kRecBins;
+        };
+        int32_t f = 1;
+        if (i > 0 && same(i, i - 1)) {
+            f = 0;
+            if (i > 1 && same(i - 1, i - 2)) {
+                const int32_t d1 = liv_key[i] - liv_key[i - 1], d0 = liv_key[i - 1] - liv_key[i - 2];
+                f = (d1 > 0) != (d0 > 0);
+            }
+        }
+        flags[i] = f;
+    }
+}
+
+// Unsorted records in line order: words (B_0, B_1, B_2, B_3 as row byte offsets
+// inside the part's tile) and (B_4 | sign, rest code (filled later), group, 0);
+// the sort key (group) and the rest index (line).
+__global__ void k_rec_emit(const int32_t *__restrict__ liv_key, const int32_t *__restrict__ liv_pos,
+                           const int32_t *__restrict__ n_liv_p, const int32_t *__restrict__ rflags,
+                           const int32_t *__restrict__ rexcl, int B, int GB, LaySel L, int shift,
+                           uint4 *__restrict__ rec, int32_t *__restrict__ rkey, int32_t *__restrict__ rrest,
+                           int32_t *__restrict__ n_rec_p, int64_t N) {
+    const LayGeom G = L.get();
+    const int32_t n = n_liv_p[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i == n - 1) n_rec_p[0] = rexcl[i] + rflags[i];
+        if (!rflags[i]) continue;
+        const int32_t r = rexcl[i];
+        const int32_t key0 = liv_key[i];
+        const int p = key0 / B, q = (key0 % B) / kRecBins;
+        const int64_t line = liv_pos[i] / G.n_last, base = line * G.n_last;
+        const int64_t row0 = (int64_t)p * G.part_rows;
+        const int64_t part_end = base + min(G.n_last, row0 + G.part_rows);
+        int64_t st[kRecBins];
+        for (int j = 0; j < kRecBins; ++j) st[j] = -1;
+        int dir = 0;
+        int64_t e = part_end;
+        int64_t t = i;
+        int32_t prev = -1;
+        do {
+            const int32_t b = liv_key[t] % B;
+            st[b - q * kRecBins] = liv_pos[t];
+            if (prev >= 0 && dir == 0) dir = b > prev ? 1 : -1;
+            prev = b;
+            ++t;
+        } while (t < n && !rflags[t]);
+        if (t < n && liv_pos[t] < part_end) e = liv_pos[t];  // next interval of this line-part
+        uint32_t w[kRecBins + 1];
+        for (int j = 0; j <= kRecBins; ++j) {
+            int64_t v = e;
+            for (int jj = 0; jj < kRecBins; ++jj) {
+                const bool take = dir >= 0 ? jj >= j : jj < j;
+                if (take && st[jj] >= 0 && st[jj] < v) v = st[jj];
+            }
+            w[j] = (uint32_t)(v - base - row0) << shift;
+        }
+        rec[2 * (int64_t)r] = make_uint4(w[0], w[1], w[2], w[3]);
+        rec[2 * (int64_t)r + 1] = make_uint4(w[4] | (dir < 0 ? kRecNeg : 0u), 0u, (uint32_t)(p * GB + q), 0u);
+        rkey[r] = p * GB + q;
+        rrest[r] = (int32_t)line;
+    }
+}
+
+// Sort keys past the last record sort last (bucket n_groups).
+__global__ void k_rec_pad_keys(int32_t *__restrict__ rkey, const int32_t *__restrict__ n_rec_p, int64_t N,
+                               int32_t sentinel) {
+    const int32_t n = n_rec_p[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        if (i >= n) rkey[i] = sentinel;
+}
+
+// Records in (part, group, line) order, each with the rest code of the record
+// four places after it (the histogram loads that factor four ahead).
+constexpr uint32_t kRecEnd = 1u << 31;  // last record of its group
+__global__ void k_rec_gather(const uint4 *__restrict__ tmp, const int32_t *__restrict__ rrest,
+                             const int32_t *__restrict__ perm, const int32_t *__restrict__ n_rec_p,
+                             const int32_t *__restrict__ goff, uint4 *__restrict__ rec, int32_t *__restrict__ rest) {
+    const int32_t n = n_rec_p[0];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = perm[t];
+        rec[2 * t] = tmp[2 * (int64_t)r];
+        uint4 v = tmp[2 * (int64_t)r + 1];
+        if (t + 1 == goff[v.z + 1]) v.x |= kRecEnd;
+        rec[2 * t + 1] = v;
+        rest[t] = rrest[r];
+    }
+}
+__global__ void k_rec_encode(const int32_t *__restrict__ rest, const int32_t *__restrict__ n_rec_p, int ndim,
+                             int64_t n1, uint4 *__restrict__ rec) {
+    const int32_t n = n_rec_p[0];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ta = t + kRunAhead;
+        uint32_t code = 0;
+        if (ta < n) {
+            const int32_t r = rest[ta];
+            code = ndim == 3 ? (uint32_t)(r / n1) | ((uint32_t)(r % n1) << 15) : (uint32_t)r;
+        }
+        rec[2 * t + 1].y = code;
+    }
+}
+
+// Record chunks, C per part (equal record counts; records cost alike):
+// chunk c of part p starts at record lo_p + (hi_p - lo_p) c / C; its first and
+// last groups (-1 when empty); entry P C is the end.  A group may be cut by
+// chunk bounds, like a key of the point stream.
+__global__ void k_rec_chunks(const int32_t *__restrict__ goff, const int32_t *__restrict__ n_rec_p, int GB,
+                             LaySel L, int C, const uint4 *__restrict__ rec, int32_t *__restrict__ chunk_rec,
+                             int32_t *__restrict__ chunk_grp) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int P = L.get().P;
+    if (c > P * C) return;
+    int32_t r;
+    if (c == P * C) {
+        r = n_rec_p[0];
+    } else {
+        const int p = c / C, cc = c - p * C;
+        const int64_t lo = goff[p * GB], hi = goff[(p + 1) * GB];
+        r = (int32_t)(lo + ((hi - lo) * (int64_t)cc) / C);
+    }
+    chunk_rec[c] = r;
+    if (c < P * C) {
+        const int p = c / C, cc = c - p * C;
+        const int64_t lo = goff[p * GB], hi = goff[(p + 1) * GB];
+        const int32_t r1 = (int32_t)(lo + ((hi - lo) * (int64_t)(cc + 1)) / C);
+        chunk_grp[2 * c] = r1 > r ? (int32_t)rec[2 * (int64_t)r + 1].z : -1;
+        chunk_grp[2 * c + 1] = r1 > r ? (int32_t)rec[2 * (int64_t)(r1 - 1) + 1].z : -1;
+    }
+}
+
+// First and last chunk holding records of each group (-1, -1 for an empty group).
+__global__ void k_rec_group_chunks(const int32_t *__restrict__ goff, int n_groups,
+                                   const int32_t *__restrict__ chunk_rec, LaySel L, int C, int2 *__restrict__ out) {
+    const int gr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gr >= n_groups) return;
+    const int n_chunks = L.get().P * C;  // the chosen layout's chunks
+    const int32_t o0 = goff[gr], o1 = goff[gr + 1];
+    if (o0 == o1) {
+        out[gr] = make_int2(-1, -1);
+        return;
+    }
+    auto holding = [&](int32_t t) {  // last c in [0, n_chunks) with chunk_rec[c] <= t
+        int lo = 0, hi = n_chunks;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (chunk_rec[mid] <= t) lo = mid; else hi = mid;
+        }
+        return lo;
+    };
+    out[gr] = make_int2(holding(o0), holding(o1 - 1));
 }
 
 // ---- power tables -----------------------------------------------------------
@@ -1019,6 +1235,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
             HL.P = vup_hist_parts_for(HL.n_last, B);
             HL.part_rows = ceil_div64(HL.n_last, HL.P);
             Bk_max = std::max(Bk_max, HL.P * B);
+            Bk_max = std::max(Bk_max, HL.P * (int)ceil_div64(B, kRecBins) + 1);  // record sort
             g->hist_P = std::max(g->hist_P, HL.P);
         }
         auto &HL = g->hl[0];
@@ -1118,6 +1335,61 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s) {
         k_layout_keys<<<tg, dim3(32, 8), 0, s>>>(g->bins, Rn, Cn, B, L, HL.keys_own);
         VUP_CHECK_LAUNCH();
         HL.keys = HL.keys_own;
+        const int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
+        // record stream (from the keys in layout order)
+        {
+            const int GB = (int)ceil_div64(B, kRecBins);
+            int P_sel = 1;
+            for (int l = 0; l < g->n_layouts; ++l) P_sel = std::max(P_sel, g->hl[l].P);
+            const int n_groups = P_sel * GB;  // room for either layout's parts
+            st = devbuf_reserve(g->rec_tmp, (size_t)N * (9 * sizeof(int32_t) + 2 * sizeof(uint4)));
+            if (st != VUP_OK) return st;
+            // the uint4 records first: 16-byte aligned whatever N is
+            uint4 *rtmp = (uint4 *)g->rec_tmp.p;
+            int32_t *t32 = (int32_t *)(rtmp + 2 * N);
+            int32_t *fl = t32, *ex = t32 + N, *lkey = t32 + 2 * N, *lpos = t32 + 3 * N, *rfl = t32 + 4 * N,
+                    *rex = t32 + 5 * N, *rkey = t32 + 6 * N, *rrest = t32 + 7 * N, *rperm = t32 + 8 * N;
+            if ((st = devbuf_reserve(HL.rec, sizeof(uint4) * 2 * (size_t)(N + 64))) != VUP_OK ||
+                (st = devbuf_reserve(HL.rec_rest, sizeof(int32_t) * (size_t)(N + 64))) != VUP_OK ||
+                (st = devbuf_reserve(HL.rec_goff, sizeof(int32_t) * (size_t)(n_groups + 2))) != VUP_OK ||
+                (st = devbuf_reserve(HL.rec_gch, sizeof(int2) * (size_t)n_groups)) != VUP_OK)
+                return st;
+            k_liv_flags<<<rb, 256, 0, s>>>(HL.keys, N, L, fl);
+            VUP_CHECK_LAUNCH();
+            if ((st = scan_exclusive(fl, ex, N, scratch, s)) != VUP_OK) return st;
+            k_liv_emit<<<rb, 256, 0, s>>>(HL.keys, N, fl, ex, lkey, lpos, HL.n_iv);
+            VUP_CHECK_LAUNCH();
+            k_rec_flags<<<rb, 256, 0, s>>>(lkey, lpos, HL.n_iv, B, L, rfl, N);
+            VUP_CHECK_LAUNCH();
+            if ((st = scan_exclusive(rfl, rex, N, scratch, s)) != VUP_OK) return st;
+            k_rec_emit<<<rb, 256, 0, s>>>(lkey, lpos, HL.n_iv, rfl, rex, B, GB, L, kRowShift, rtmp, rkey, rrest,
+                                          HL.n_rec, N);
+            VUP_CHECK_LAUNCH();
+            k_rec_pad_keys<<<rb, 256, 0, s>>>(rkey, HL.n_rec, N, n_groups);
+            VUP_CHECK_LAUNCH();
+            st = counting_sort(g, rkey, n_groups + 1, rperm, (int32_t *)HL.rec_goff.p, counts, scratch, false, s);
+            if (st != VUP_OK) return st;
+            VUP_CHECK_CUDA(cudaMemsetAsync(HL.rec.p, 0, sizeof(uint4) * 2 * (size_t)(N + 64), s));
+            k_rec_gather<<<rb, 256, 0, s>>>(rtmp, rrest, rperm, HL.n_rec, (const int32_t *)HL.rec_goff.p,
+                                            (uint4 *)HL.rec.p, (int32_t *)HL.rec_rest.p);
+            VUP_CHECK_LAUNCH();
+            k_rec_encode<<<rb, 256, 0, s>>>((const int32_t *)HL.rec_rest.p, HL.n_rec, g->ndim,
+                                            g->ndim == 3 ? g->n[1] : 1, (uint4 *)HL.rec.p);
+            VUP_CHECK_LAUNCH();
+            // chunks of records (the same count per part as the other streams' chunks / 4)
+            const int Cr = g->n_chunks_rec;
+            k_rec_chunks<<<(P_sel * Cr + 1 + 127) / 128, 128, 0, s>>>((const int32_t *)HL.rec_goff.p, HL.n_rec, GB, L,
+                                                                      Cr, (const uint4 *)HL.rec.p, HL.rec_chunk,
+                                                                      HL.rec_chunk_grp);
+            VUP_CHECK_LAUNCH();
+            k_rec_group_chunks<<<(n_groups + 127) / 128, 128, 0, s>>>((const int32_t *)HL.rec_goff.p, n_groups,
+                                                                       HL.rec_chunk, L, Cr,
+                                                                       (int2 *)HL.rec_gch.p);
+            VUP_CHECK_LAUNCH();
+            // flags, scan, intervals, record flags, scan, records, padding, sort (count, scan,
+            // scatter, koff end), gather, codes, chunks, group chunks
+            launches += 2 * scan_launches(N) + 5 + 3 + scan_launches((int64_t)(n_groups + 1) * n_tiles) + 4;
+        }
         st = counting_sort(g, HL.keys, Bk_max, HL.perm, HL.koff, counts, scratch, false, s);
         if (st != VUP_OK) return st;
         // runs and intervals: one flag word per point, one 64-bit scan
@@ -1125,7 +1397,6 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s) {
         if (st != VUP_OK) return st;
         auto *flags = (unsigned long long *)g->lay_tmp.p;
         auto *excl = flags + N;
-        const int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
         k_layout_flags<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, L, flags);
         VUP_CHECK_LAUNCH();
         st = scan_exclusive<unsigned long long>(flags, excl, N, (unsigned long long *)g->scan_tmp.p, s);
@@ -1163,7 +1434,8 @@ vup_status vup_ensure_layout(vup_grid g, cudaStream_t s) {
 }
 
 vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s) {
-    k_pick_stream<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->hl[0].n_iv, g->N, g->hist_force, g->hist_sel);
+    k_pick_stream<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->hl[0].n_iv, g->hl[0].n_rec, g->N, g->ndim - 1, g->hist_force,
+                                  g->hist_sel);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }

@@ -39,6 +39,7 @@ constexpr uint32_t kRunEnd = 1u << 30, kBinEnd = 1u << 31;
 constexpr uint32_t kFlags = kRunEnd | kBinEnd;
 constexpr uint32_t kSpin = 1u << 26;
 constexpr int kPF = 16;                      // runs prefetched per block (global fallback)
+constexpr int kRecBinsH = 4;                 // bins per record group (the layout builder's kRecBins)
 
 struct LayoutArgs {
     const uint32_t *hpt;
@@ -49,6 +50,10 @@ struct LayoutArgs {
     const int2 *key_chunks;  // [P * B] first / last chunk of each key (-1 if empty)
     const uint2 *ipt;      // interval stream (word pairs)
     const int32_t *iv_rest, *chunk_iv;
+    const uint4 *rec;      // record stream (two uint4 per record)
+    const int32_t *rec_rest, *rec_goff;
+    const int2 *rec_gch;   // first / last chunk holding each group
+    const int32_t *rec_chunk, *rec_chunk_grp;
     const float *g_last;   // factor table of the gathered axis  [n_last][K_pad]
     const float *g0, *g1;  // rest-axis factor tables (g1 only for 3-D)
     int64_t n_last, part_rows;
@@ -65,6 +70,9 @@ struct HistArgs {
     int B;
     int C;                // chunks per part
     int group_chunks;     // chunks per work item (a multiple of kGroupChunks dividing C)
+    int rec_sets;         // record stream: work items per part (each a range of the part's record chunks)
+    int C_rec;            // record chunks per part
+    int GB;               // record groups per part: ceil(B / kRecBins)
     int points_only;      // 1: point stream whatever the layout choice says
     float *hist;          // [K][B]
     float *part;          // [P * C][2][K_pad]
@@ -175,7 +183,7 @@ struct ItemCtx {
     float *part;   // [P * C][2][K_pad] partial sums of keys cut by chunk bounds
     float *direct; // [P * B][K_pad] sums of keys held by one chunk
     int64_t K, K_pad;
-    int B, C, group_chunks;
+    int B, C, group_chunks, rec_sets, C_rec, GB;
     int mode;      // 0: point stream, tile holds factors; 1: interval stream, tile holds prefix sums
     int *dstatus;
 };
@@ -326,6 +334,142 @@ __device__ __forceinline__ bool iv_chunk(const ItemCtx &X, int c, int p, int64_t
     return true;
 }
 
+// Record stream, chunk c of part p: record t adds s_t f_t (P[B_j+1] - P[B_j])
+// to bin 4q + j for j = 0..3 (five prefix-sum gathers, one rest-factor load
+// four records ahead, s_t its sign); a group's four sums are stored when its
+// last record passes (groups cut by the chunk bounds -- only its first and
+// last -- go to the chunk's partial rows, as keys do on the other streams).
+constexpr uint32_t kRecNegFlag = 1u << 30;
+constexpr uint32_t kRecEndFlag = 1u << 31;
+constexpr uint32_t kRecOffMask = (1u << 18) - 1u;
+template <int NF>
+__device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, int64_t k, const float *ws,
+                                               uint32_t *win, uint64_t *mbar, uint32_t &wseq, volatile int *abort) {
+    const LayoutArgs &H = X.H;
+    const int lane = threadIdx.x & 31;
+    const int32_t r0 = H.rec_chunk[c], r1 = H.rec_chunk[c + 1];
+    if (r0 >= r1) return true;
+    const int32_t first_grp = H.rec_chunk_grp[2 * c], last_grp = H.rec_chunk_grp[2 * c + 1];
+    // a group is cut when it starts before or ends after the chunk
+    const bool sh_first = H.rec_goff[first_grp] < r0 || H.rec_goff[first_grp + 1] > r1;
+    const bool sh_last = H.rec_goff[last_grp] < r0 || H.rec_goff[last_grp + 1] > r1;
+    const bool last_ends = (H.rec[2 * (int64_t)(r1 - 1) + 1].x & kRecEndFlag) != 0;
+    // words [w0, w1): records from r0 rounded down to a multiple of four
+    const int32_t rb = r0 & ~3;
+    const int64_t w0 = 8 * (int64_t)rb, w1 = 8 * (int64_t)r1;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(H.rec);
+    const int64_t wb0 = w0 & ~(int64_t)(kWin - 1);
+    if (lane == 0) {
+        const int b0 = wseq & 1;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of both buffers
+        bulk_copy(win + b0 * kWin, src + wb0, kWin * 4, &mbar[b0]);
+        if (wb0 + kWin < w1) bulk_copy(win + (b0 ^ 1) * kWin, src + wb0 + kWin, kWin * 4, &mbar[b0 ^ 1]);
+    }
+    __syncwarp();
+
+    const uint32_t stride = (uint32_t)(X.K_pad * 4);
+    const char *g0b = reinterpret_cast<const char *>(H.g0 + k);
+    const char *g1b = NF == 2 ? reinterpret_cast<const char *>(H.g1 + k) : nullptr;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto row4 = [&](const char *base, uint32_t row) -> float4 {
+        return *reinterpret_cast<const float4 *>(base + (uint64_t)row * stride);
+    };
+    // rest factor from a record's code (2-D: the rest index; 3-D: a0 | a1 << 15)
+    auto coded_factor = [&](uint32_t u) -> float4 {
+        if (NF == 2) return mul4(row4(g0b, u & 0x7fffu), row4(g1b, u >> 15));
+        return row4(g0b, u);
+    };
+    auto first_factor = [&](int32_t t) -> float4 {
+        if (t < r0 || t >= r1) return zero4;
+        const int32_t rest = H.rec_rest[t];
+        if (NF == 2) {
+            const int32_t a0 = rest / (int32_t)H.n1;
+            return mul4(row4(g0b, (uint32_t)a0), row4(g1b, (uint32_t)(rest - a0 * (int32_t)H.n1)));
+        }
+        return row4(g0b, (uint32_t)rest);
+    };
+    float4 f0 = first_factor(rb), f1 = first_factor(rb + 1), f2 = first_factor(rb + 2), f3 = first_factor(rb + 3);
+
+    float4 acc0 = zero4, acc1 = zero4, acc2 = zero4, acc3 = zero4;
+    // a group's four sums: whole groups to their direct rows, cut ones to the chunk's partials
+    auto flush = [&](int32_t gr) {
+        const bool first = gr == first_grp;
+        const bool shared = first ? sh_first : (gr == last_grp && sh_last);
+        const int b0 = (gr - p * X.GB) * kRecBinsH;
+        float *row = shared ? X.part + ((int64_t)c * 2 + (first ? 0 : 1)) * 4 * X.K_pad + k
+                            : X.direct + ((int64_t)p * X.B + b0) * X.K_pad + k;
+        *reinterpret_cast<float4 *>(row) = acc0;
+        if (shared || b0 + 1 < X.B) *reinterpret_cast<float4 *>(row + X.K_pad) = acc1;
+        if (shared || b0 + 2 < X.B) *reinterpret_cast<float4 *>(row + 2 * X.K_pad) = acc2;
+        if (shared || b0 + 3 < X.B) *reinterpret_cast<float4 *>(row + 3 * X.K_pad) = acc3;
+        acc0 = acc1 = acc2 = acc3 = zero4;
+    };
+    const uint32_t wsl = smem_u32(ws) + lane * 16;
+    auto gather = [&](uint32_t addr) -> float4 {
+        float4 v;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "r"(addr));
+        return v;
+    };
+    auto sub4 = [](float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); };
+    auto step = [&](const uint4 u, const uint4 v, float4 &f) {
+        const float4 p0 = gather(wsl + u.x), p1 = gather(wsl + u.y), p2 = gather(wsl + u.z),
+                     p3 = gather(wsl + u.w), p4 = gather(wsl + (v.x & kRecOffMask));
+        const float4 fs = (v.x & kRecNegFlag) ? make_float4(-f.x, -f.y, -f.z, -f.w) : f;
+        fma4(acc0, fs, sub4(p1, p0));
+        fma4(acc1, fs, sub4(p2, p1));
+        fma4(acc2, fs, sub4(p3, p2));
+        fma4(acc3, fs, sub4(p4, p3));
+        f = coded_factor(v.y);
+        if (v.x & kRecEndFlag) flush((int32_t)v.z);
+    };
+    // foreign records: every boundary row 0 (differences 0), no group end;
+    // those before the chunk keep their rest codes (they load its first factors)
+    auto masked = [&](uint4 &u, uint4 &v, int32_t t) {
+        if (t < r0) {
+            u = make_uint4(0u, 0u, 0u, 0u);
+            v = make_uint4(0u, v.y, 0u, 0u);
+        } else if (t >= r1) {
+            u = make_uint4(0u, 0u, 0u, 0u);
+            v = make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+
+    for (int64_t wbase = wb0; wbase < w1; wbase += kWin, ++wseq) {
+        const int b = wseq & 1;
+        for (uint32_t i = 0; !mbar_try_wait(&mbar[b], (wseq >> 1) & 1); ++i) {
+            if (i > kSpin || *abort) {  // a staged copy never landed: record and stop
+                *abort = 1;
+                atomicCAS(X.dstatus, 0, VUP_DSTAT_TIMEOUT);
+                return false;
+            }
+        }
+        const uint4 *wq = reinterpret_cast<const uint4 *>(win + b * kWin);
+        const int lo = (int)((w0 > wbase ? w0 : wbase) - wbase);
+        const int hi = (int)((w1 < wbase + kWin ? w1 : wbase + kWin) - wbase);
+        for (int qq = lo; qq < hi; qq += 32) {
+            const int32_t t0 = (int32_t)((wbase + qq) >> 3);
+            const bool edge = t0 < r0 || t0 + 4 > r1;
+            auto one = [&](int m, float4 &f) {
+                uint4 u = wq[qq / 4 + 2 * m], v = wq[qq / 4 + 2 * m + 1];
+                if (edge) masked(u, v, t0 + m);
+                step(u, v, f);
+            };
+            one(0, f0);
+            one(1, f1);
+            one(2, f2);
+            one(3, f3);
+        }
+        __syncwarp();
+        if (lane == 0 && wbase + 2 * kWin < w1) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bulk_copy(win + b * kWin, src + wbase + 2 * kWin, kWin * 4, &mbar[b]);
+        }
+    }
+    if (!last_ends) flush(last_grp);  // the chunk ends inside its last group
+    return true;
+}
+
 // One work item: part p, chunk group cg (kGroupChunks chunks, drawn by the
 // warps one at a time) and
 // the 128 densities from k0 of the instance *Ap (kernel parameter or global
@@ -357,6 +501,9 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         X.B = A.B;
         X.C = A.C;
         X.group_chunks = A.group_chunks;
+        X.rec_sets = A.rec_sets;
+        X.C_rec = A.C_rec;
+        X.GB = A.GB;
         X.mode = MODE;
         X.dstatus = A.dstatus;
     }
@@ -568,6 +715,18 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         if (cur_key >= 0) flush(cur_key, bacc);
         return true;
     };
+    if constexpr (MODE == 2) {
+        // this item's range of the part's record chunks, handed out one at a time
+        const int c_lo = (int)((int64_t)cg * X.C_rec / X.rec_sets), c_hi = (int)((int64_t)(cg + 1) * X.C_rec / X.rec_sets);
+        for (;;) {
+            int ci = 0;
+            if (lane == 0) ci = atomicAdd(next_chunk, 1);
+            ci = __shfl_sync(0xffffffffu, ci, 0);
+            if (c_lo + ci >= c_hi) break;
+            if (!rec_chunk_walk<NF>(X, p * X.C_rec + c_lo + ci, p, k, ws, win, mbar, wseq, abort)) return;
+        }
+        return;
+    }
     for (;;) {
         int ci = 0;
         if (lane == 0) ci = atomicAdd(next_chunk, 1);
@@ -733,10 +892,32 @@ __device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0
     }
     __syncthreads();
     const int b = bt * kFinB + warp;
+    const bool recs = !A.points_only && A.sel[1] == 2;  // record stream: every non-empty group wrote its rows
     for (int64_t kt = kt0; kt < kt0 + nkt; ++kt) {
         const int64_t k = kt * kFinK + 4 * lane;
         float4 total = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (b < A.B) {
+        if (recs) {
+            // the group (part, b / 4) of the record stream: whole in one chunk
+            // (direct row) or cut (partials of its chunks, in chunk order)
+            if (b < A.B)
+                for (int p = 0; p < P; ++p) {
+                    const int32_t gr = p * A.GB + b / kRecBinsH;
+                    const int2 cc = H.rec_gch[gr];
+                    if (cc.x < 0) continue;
+                    if (cc.x == cc.y) {
+                        add4(total, *reinterpret_cast<const float4 *>(A.direct + ((int64_t)p * A.B + b) * A.K_pad + k));
+                        continue;
+                    }
+                    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int c = cc.x; c <= cc.y; ++c) {
+                        if (H.rec_chunk[c] >= H.rec_chunk[c + 1]) continue;
+                        const int side = H.rec_chunk_grp[2 * c] == gr ? 0 : 1;
+                        add4(sum, *reinterpret_cast<const float4 *>(A.part + (((int64_t)c * 2 + side) * 4 + b % kRecBinsH) *
+                                                                                 A.K_pad + k));
+                    }
+                    add4(total, sum);
+                }
+        } else if (b < A.B) {
 #pragma unroll 4
             for (int p = 0; p < P; ++p) {
                 const int2 cc = s_cc[p][warp];
@@ -791,6 +972,12 @@ int vup_hist_chunks_for(int64_t N, int P) {
     return (int)(S * kGroupChunks);
 }
 
+// Record chunks per part: a quarter of the point chunks (records are several
+// times fewer than intervals), in whole groups of kGroupChunks.
+int vup_hist_rec_chunks_for(int n_chunks) {
+    return kGroupChunks * std::max(1, n_chunks / kGroupChunks / 4);
+}
+
 // Parts of a gathered axis of n_last rows (one 64-density tile each) for a
 // bin count; one part when the (part, bin) key space would exceed the sort.
 int vup_hist_parts_for(int64_t n_last, int n_bins) {
@@ -831,6 +1018,12 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
         La.ipt = HL.ipt;
         La.iv_rest = HL.iv_rest;
         La.chunk_iv = HL.chunk_iv;
+        La.rec = (const uint4 *)g->hl[0].rec.p;  // the built layout's arrays
+        La.rec_rest = (const int32_t *)g->hl[0].rec_rest.p;
+        La.rec_goff = (const int32_t *)g->hl[0].rec_goff.p;
+        La.rec_gch = (const int2 *)g->hl[0].rec_gch.p;
+        La.rec_chunk = g->hl[0].rec_chunk;
+        La.rec_chunk_grp = g->hl[0].rec_chunk_grp;
         La.g_last = tab(HL.last_axis);
         if (nd == 3) {
             La.g0 = tab(0);
@@ -848,6 +1041,9 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
         P_max = std::max(P_max, HL.P);
     }
     A.sel = g->hist_sel;
+    A.GB = (int)ceil_div64(g->B, kRecBinsH);
+    A.rec_sets = 1;
+    A.C_rec = g->n_chunks_rec;
     A.ds = (const DensStats *)g->dstats.p;
     A.ndim = nd;
     A.K = K;
@@ -867,10 +1063,13 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     int64_t rows;
     int P_max;
     HistArgs A = hist_args_for(g, K, hist, rows, P_max, ftab);
-    A.points_only = points_only ? 1 : 0;
     const size_t smem = hist_smem_bytes(rows);
     // run-end words encode the rest index in 21 bits (3-D: a0 < 512, a1 < 4096)
     const bool coded = nd == 2 || (g->n[0] <= 512 && g->n[1] <= 4096);
+    const bool in_smem = smem <= 220 * 1024 && coded;
+    // the global-memory fallback walks points whatever the device chose
+    points_only = points_only || !in_smem;
+    A.points_only = points_only ? 1 : 0;
     // items: G groups of C / G chunks per part, G dividing C / kGroupChunks,
     // chosen for the fewest idle SM slots in the last wave (one CTA per SM)
     const int S = A.C / kGroupChunks, nkt = (int)ceil_div64(K, kKT), sms = vup_num_sms();
@@ -887,21 +1086,38 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     }
     A.group_chunks = A.C / G;
     const int n_items = P_max * G * nkt;
-    const int grid = n_items;
+    // record stream: S items per part, each a range of its record chunks, S for
+    // the fullest last wave
+    int Sr = 1;
     {
-        const bool in_smem = smem <= 220 * 1024 && coded;
-        VUP_PROF("hist_segmented", s, in_smem && !points_only ? 2 : 1);
+        double best_r = -1.0;
+        for (int ss = 1; ss <= std::max(1, A.C_rec / kHistWarps); ++ss) {  // at least a chunk per warp
+            const int64_t items = (int64_t)P_max * ss * nkt;
+            const double eff = (double)items / (double)(ceil_div64(items, sms) * sms);
+            if (eff > best_r + 0.02) {
+                best_r = eff;
+                Sr = ss;
+            }
+        }
+    }
+    A.rec_sets = Sr;
+    const int n_items_rec = P_max * Sr * nkt;
+    {
+        VUP_PROF("hist_segmented", s, in_smem && !points_only ? 3 : 1);
         if (in_smem) {
-            auto launch = [&](auto kern) -> vup_status {
+            auto launch = [&](auto kern, int gg, int items) -> vup_status {
                 VUP_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                kern<<<grid, kHistWarps * 32, smem, s>>>(A, rows, P_max, G, n_items);
+                kern<<<items, kHistWarps * 32, smem, s>>>(A, rows, P_max, gg, items);
                 VUP_CHECK_LAUNCH();
                 return VUP_OK;
             };
-            vup_status st = nd == 3 ? launch(k_hist_smem<2, 0>) : launch(k_hist_smem<1, 0>);
+            vup_status st = nd == 3 ? launch(k_hist_smem<2, 0>, G, n_items) : launch(k_hist_smem<1, 0>, G, n_items);
             if (st != VUP_OK) return st;
             if (!points_only) {
-                st = nd == 3 ? launch(k_hist_smem<2, 1>) : launch(k_hist_smem<1, 1>);
+                st = nd == 3 ? launch(k_hist_smem<2, 1>, G, n_items) : launch(k_hist_smem<1, 1>, G, n_items);
+                if (st != VUP_OK) return st;
+                st = nd == 3 ? launch(k_hist_smem<2, 2>, Sr, n_items_rec)
+                             : launch(k_hist_smem<1, 2>, Sr, n_items_rec);
                 if (st != VUP_OK) return st;
             }
         } else {
@@ -947,6 +1163,7 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
         rows_max = std::max(rows_max, rows);
         args[i].group_chunks = kGroupChunks;
         const int G = args[i].C / kGroupChunks;
+        args[i].rec_sets = G;  // record stream: item cg takes the cg-th of G ranges of the part's record chunks
         const int64_t nkt = ceil_div64(Ks[i], kKT);
         // cost of one item: points per chunk x densities per tile
         const int64_t cost = gs[i]->N / std::max<int64_t>(1, (int64_t)P_max * args[i].C);
@@ -967,7 +1184,7 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
     if ((st = devbuf_reserve(P->args, sizeof(HistArgs) * n)) != VUP_OK ||
         (st = devbuf_reserve(P->items, sizeof(HistItem) * std::max<size_t>(1, items.size()))) != VUP_OK ||
         (st = devbuf_reserve(P->fitems, sizeof(int4) * std::max<size_t>(1, fin.size()))) != VUP_OK ||
-        (st = devbuf_reserve(P->ctr, sizeof(int) * 2)) != VUP_OK) {
+        (st = devbuf_reserve(P->ctr, sizeof(int) * 3)) != VUP_OK) {
         devbuf_free(P->args);
         devbuf_free(P->items);
         devbuf_free(P->fitems);
@@ -983,6 +1200,8 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
         cudaFuncSetAttribute(k_hist_batched<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     VUP_CHECK_CUDA(
         cudaFuncSetAttribute(k_hist_batched<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    VUP_CHECK_CUDA(
+        cudaFuncSetAttribute(k_hist_batched<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     *out = P;
     return VUP_OK;
 }
@@ -1003,10 +1222,10 @@ vup_status vup_hist_batched(void *plan, cudaStream_t s) {
     const size_t smem = hist_smem_bytes(P->rows);
     if (smem > 220 * 1024) return VUP_ERR_UNSUPPORTED;
     {
-        VUP_PROF("hist_segmented_batched", s, 2);
+        VUP_PROF("hist_segmented_batched", s, 3);
         const int grid = std::max(1, std::min(P->n_items, vup_num_sms()));
         int *ctr = (int *)P->ctr.p;
-        VUP_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(int), s));
+        VUP_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(int), s));
         k_hist_batched<1, 0><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
                                                                  (const HistItem *)P->items.p, P->n_items, P->rows,
                                                                  ctr);
@@ -1014,6 +1233,10 @@ vup_status vup_hist_batched(void *plan, cudaStream_t s) {
         k_hist_batched<1, 1><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
                                                                  (const HistItem *)P->items.p, P->n_items, P->rows,
                                                                  ctr + 1);
+        VUP_CHECK_LAUNCH();
+        k_hist_batched<1, 2><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
+                                                                 (const HistItem *)P->items.p, P->n_items, P->rows,
+                                                                 ctr + 2);
         VUP_CHECK_LAUNCH();
     }
     VUP_PROF("hist_fixup_batched", s, 1);

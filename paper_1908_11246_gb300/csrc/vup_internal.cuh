@@ -101,7 +101,7 @@ struct vup_grid_s {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // counting-sort scratch
-    DevBuf sort_counts, scan_tmp, lay_tmp;
+    DevBuf sort_counts, scan_tmp, lay_tmp, rec_tmp;
 
     // histogram point streams.  Layout 0 gathers the last axis per point and
     // forms runs over the other axes; on 2-D grids layout 1 swaps the roles
@@ -135,12 +135,22 @@ struct vup_grid_s {
         int32_t *iv_rest = nullptr;    // [N] rest index of each interval
         int32_t *n_iv = nullptr;       // [1] device
         int32_t *chunk_iv = nullptr;   // [P * n_chunks + 1] chunk start (interval index)
+        // record stream: one record per (line, group of 4 consecutive bins,
+        // monotone stretch): two uint4 per record, sorted by (part, group, line)
+        DevBuf rec;                    // [n_rec + 16][2] uint4
+        DevBuf rec_rest;               // [n_rec] rest index of each record
+        DevBuf rec_goff;               // [n_groups + 2] first record of each group
+        DevBuf rec_gch;                // [n_groups] int2: first / last chunk holding the group (-1 if empty)
+        int32_t *rec_chunk = nullptr;  // [P * n_chunks_rec + 1] chunk start (record index)
+        int32_t *rec_chunk_grp = nullptr;  // [P * n_chunks_rec * 2] first / last group of each chunk
+        int32_t *n_rec = nullptr;      // [1] device
     } hl[2];
     int hist_P = 1;                // max parts over layouts (scratch sizing)
     int n_layouts = 1;
     int32_t *hist_sel = nullptr;   // [4] device: chosen layout, 1 = interval stream, intervals of layouts 0 / 1
     int hist_force = -1;           // -1 auto, 0 points only, 1 intervals only
     int32_t n_chunks = 0;
+    int32_t n_chunks_rec = 0;      // record chunks per part (records are several times fewer than points)
 
     // power tables per orientation (kOrient*)
     Orient orient[kNumOrient];

@@ -41,7 +41,8 @@ class vup_grid_info_t(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("n", C.c_int64 * 3), ("N", C.c_int64), ("n_bins", C.c_int32),
                 ("n_moments", C.c_int32), ("ymin", C.c_double), ("ymax", C.c_double),
                 ("yscale", C.c_double), ("have_model", C.c_int32), ("hist_layout", C.c_int32),
-                ("hist_stream", C.c_int32), ("hist_runs", C.c_int64), ("hist_intervals", C.c_int64)]
+                ("hist_stream", C.c_int32), ("hist_runs", C.c_int64), ("hist_intervals", C.c_int64),
+                ("hist_records", C.c_int64)]
 
 
 class VUPError(RuntimeError):
@@ -270,7 +271,7 @@ def vup_grid_info(h):
 
 
 def vup_set_hist_stream(h, kind: int, stream=None):
-    """Histogram stream choice: -1 auto, 0 sorted points, 1 sorted intervals."""
+    """Histogram stream choice: -1 auto, 0 sorted points, 1 sorted intervals, 2 records."""
     _check(lib().vup_set_hist_stream(h, int(kind), _stream(stream)), "vup_set_hist_stream")
 
 
@@ -362,7 +363,7 @@ class Grid:
         return vup_grid_info(self.h)
 
     def set_hist_stream(self, kind: int, stream=None):
-        """-1: automatic choice; 0: sorted points; 1: sorted intervals."""
+        """-1: automatic choice; 0: sorted points; 1: sorted intervals; 2: records."""
         vup_set_hist_stream(self.h, kind, stream)
 
     def array(self, which):

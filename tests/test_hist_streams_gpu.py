@@ -1,10 +1,11 @@
-"""Histogram streams: sorted points vs sorted intervals (Eq. 4), both against the FP64 oracle.
+"""Histogram streams: sorted points, intervals and records (Eq. 4), each against the FP64 oracle.
 
 The interval stream sums each stretch of one bin along the gathered axis as a
-difference of prefix sums of the factor tile; the point stream adds every
-point.  Both are forced in turn on every case and must meet the histogram
-tolerance (1e-6 absolute per bin).  The run and interval counts the device
-reports are checked exactly against a count from the oracle's bins.
+difference of prefix sums of the factor tile; the record stream does the same
+for four consecutive bins of one line at once (five prefix sums); the point
+stream adds every point.  Each is forced in turn on every case and must meet
+the histogram tolerance (1e-6 absolute per bin).  The run, interval and record
+counts the device reports are checked exactly against counts from its bins.
 """
 import numpy as np
 import pytest
@@ -67,7 +68,29 @@ def layout_counts(bins_nd, B, layout):
     new_run[1:] = (k[1:] != k[:-1]) | (r[1:] != r[:-1])
     new_iv = new_run.copy()
     new_iv[1:] |= aa[1:] != aa[:-1] + 1
-    return int(new_run.sum()), int(new_iv.sum())
+    return int(new_run.sum()), int(new_iv.sum()), record_count(b.ravel(), n_last, pr, B)
+
+
+def record_count(bins_lines, n_last, pr, B, G=4):
+    """Records of the record stream: the intervals of every line in line order
+    (maximal stretches of one (part, bin) key), grouped while the line, the
+    part and the group of G bins stay the same and the bin steps keep their
+    sign (a step whose sign differs from the step before starts a record)."""
+    a = np.tile(np.arange(n_last), bins_lines.size // n_last)
+    key = (a // pr) * B + bins_lines
+    start = np.ones(key.size, bool)
+    start[1:] = (a[1:] == 0) | (key[1:] != key[:-1])
+    k = key[start]
+    line = (np.flatnonzero(start) // n_last)
+    part, grp = k // B, (k % B) // G
+    same = np.zeros(k.size, bool)
+    same[1:] = (line[1:] == line[:-1]) & (part[1:] == part[:-1]) & (grp[1:] == grp[:-1])
+    rec = ~same
+    up = np.zeros(k.size, bool)
+    up[1:] = k[1:] > k[:-1]
+    turn = np.zeros(k.size, bool)
+    turn[2:] = same[2:] & same[1:-1] & (up[2:] != up[1:-1])
+    return int((rec | turn).sum())
 
 
 def run_stream(prob, kind, rows=None):
@@ -95,29 +118,31 @@ def test_point_and_interval_streams_match_oracle(prob):
             W, _ = O.weights(prob.n, prob.lo, prob.hi, prob.dens, k)
             amb_mass = max(amb_mass, float(W[amb].sum()))
     out = {}
-    for kind in (0, 1):
+    for kind in (0, 1, 2):
         hs, info, b_g = run_stream(prob, kind)
         assert info.hist_stream == kind
         Hp.check_hist(hs, res["hist"], amb_mass)
-        # the device's run and interval counts for its chosen layout, from its own bins
-        runs, ivs = layout_counts(b_g.reshape(prob.n), prob.n_bins, info.hist_layout)
-        assert (info.hist_runs, info.hist_intervals) == (runs, ivs)
+        # the device's run, interval and record counts for its chosen layout, from its own bins
+        counts = layout_counts(b_g.reshape(prob.n), prob.n_bins, info.hist_layout)
+        assert (info.hist_runs, info.hist_intervals, info.hist_records) == counts
         out[kind] = hs
-    # the two orders of summation agree within the sum of their bounds
-    assert np.abs(out[0].astype(np.float64) - out[1]).max() <= 2 * (1e-6 + amb_mass)
+    # the orders of summation agree within the sum of their bounds
+    for kind in (1, 2):
+        assert np.abs(out[0].astype(np.float64) - out[kind]).max() <= 2 * (1e-6 + amb_mass)
 
 
-@pytest.mark.parametrize("name,expect", [("c2", (1, 1)), ("c3", (0, 0)), ("c4", (1, 1))])
+@pytest.mark.parametrize("name,expect", [("c2", (1, 2)), ("c3", (0, 0)), ("c4", (1, 2))])
 def test_automatic_choice_takes_the_cheaper_stream(name, expect):
     """Full-size workloads.  c2 / c4: gathering axis 0 gives runs of ~9 / ~18
-    points in ~1.07 intervals each, so layout 1's interval stream is cheapest.
-    c3 (3-D): intervals average 1.8 points, so the point stream is."""
+    points in ~1.07 intervals each and ~3.5 intervals per record, so layout
+    1's record stream is cheapest.  c3 (3-D): intervals average 1.8 points and
+    records 1.6 intervals, so the point stream is."""
     prob = I.config(name)
     rows = np.array([0, 1, 4097, prob.K - 1])
     hs, info, b_g = run_stream(prob, -1, rows=rows)
     assert (info.hist_layout, info.hist_stream) == expect
-    runs, ivs = layout_counts(b_g.reshape(prob.n), prob.n_bins, info.hist_layout)
-    assert (info.hist_runs, info.hist_intervals) == (runs, ivs)
+    counts = layout_counts(b_g.reshape(prob.n), prob.n_bins, info.hist_layout)
+    assert (info.hist_runs, info.hist_intervals, info.hist_records) == counts
     res = O.solve(prob, rows=rows, threads=Hp.oracle_threads())
     Hp.check_hist(hs, res["hist"])
 
@@ -129,7 +154,7 @@ def test_stream_choice_argument_errors():
         g.set_hist_stream(1)  # 1-D grids have no layout stream
     g.close()
     g = vup.Grid((16, 8), (0.0, 0.0), (1.0, 1.0))
-    for bad in (-2, 2):
+    for bad in (-2, 3):
         with pytest.raises(vup.VUPError):
             g.set_hist_stream(bad)
     g.set_hist_stream(0)  # before a model: kept for the next one
