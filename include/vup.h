@@ -360,7 +360,8 @@ typedef struct {
      * along the gathered axis, summed as differences of prefix sums), stream
      * 2 records (stretches of one line over a group of 4 consecutive bins,
      * monotone, five prefix sums for four bins).  Counts are those of the
-     * chosen layout. */
+     * chosen layout; hist_runs is 0 when the point and interval streams were
+     * not built (the record stream was cheaper than both). */
     int32_t hist_layout, hist_stream;
     int64_t hist_runs, hist_intervals, hist_records;
 } vup_grid_info_t;

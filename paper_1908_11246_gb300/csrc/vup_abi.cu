@@ -343,12 +343,12 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
         L.rec_chunk = A.rec_chunk;
         L.rec_chunk_grp = A.rec_chunk_grp;
     }
-    ALLOC(g->hist_sel, sizeof(int32_t) * 4);
+    ALLOC(g->hist_sel, sizeof(int32_t) * 8);
     ALLOC(g->ydev_scale, sizeof(double));
     ALLOC(g->dstatus, sizeof(int));
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMemset(g->dstatus, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(g->hist_sel, 0, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMemset(g->hist_sel, 0, sizeof(int32_t) * 8);
     if (e != cudaSuccess) {
         vup_set_last_cuda_error(e, "vup_grid_create", __FILE__, __LINE__);
         cudaGetLastError();
@@ -668,9 +668,10 @@ extern "C" vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info) {
 
 extern "C" vup_status vup_set_hist_stream(vup_grid g, int32_t stream_kind, vup_stream_t stream) {
     if (!g || g->ndim < 2 || stream_kind < -1 || stream_kind > 2) return VUP_ERR_INVALID_ARG;
+    // the layout is rebuilt on next use with the choice (a forced point or
+    // interval stream needs the key-sorted streams a record choice skips)
+    if (stream_kind != g->hist_force) g->layout_valid = g->ndim == 1;
     g->hist_force = stream_kind;
-    // a layout built later applies the choice itself
-    if (g->have_model && g->layout_valid) return vup_pick_hist_layout(g, (cudaStream_t)stream);
     return VUP_OK;
 }
 
@@ -690,8 +691,8 @@ extern "C" vup_status vup_grid_copy(vup_grid g, int which, void *dst_dev, size_t
         break;
     }
     case 3: {
-        // 2-D / 3-D grids take the bin offsets from the histogram layout
-        vup_status st = vup_ensure_layout(g, (cudaStream_t)stream);
+        // bin offsets of the stable sort by bin (built with it on 2-D / 3-D grids)
+        vup_status st = vup_natural_sort(g, (cudaStream_t)stream);
         if (st != VUP_OK) return st;
         src = g->offsets;
         need = sizeof(int32_t) * (g->B + 1);

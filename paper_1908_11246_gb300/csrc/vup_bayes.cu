@@ -51,7 +51,7 @@ extern "C" vup_status vup_posterior_means(vup_grid g, const vup_densities *d, fl
         if ((st = devbuf_reserve(g_hist, sizeof(float) * (size_t)K * B)) != VUP_OK) return st;
         hist = (float *)g_hist.p;
     }
-    if ((st = vup_ensure_layout(g, s)) != VUP_OK) return st;
+    if ((st = vup_ensure_layout(g, s, true)) != VUP_OK) return st;  // the ratios walk the point stream
     if ((st = vup_density_prep(g, d, 0, s)) != VUP_OK) return st;
     // point stream: the ratios need the relative accuracy of low-mass bins,
     // which differences of prefix sums (interval stream) do not keep

@@ -340,9 +340,14 @@ __global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
     }
 }
 
+// A kernel of the key-sorted streams' build returns at once when the device
+// found the record stream cheaper than either of them (gate 0).
+__device__ __forceinline__ bool gated_off(const int32_t *gate) { return gate && gate[0] == 0; }
+
 // Points per (key, warp tile) of a key array with key < Bk.
 __global__ void k_count(const int32_t *__restrict__ keys, int64_t N, int Bk, int32_t *__restrict__ counts,
-                        int64_t n_tiles) {
+                        int64_t n_tiles, const int32_t *gate) {
+    if (gated_off(gate)) return;
     extern __shared__ int32_t s_cnt[];  // [warps][Bk]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t *cnt = s_cnt + warp * Bk;
@@ -433,20 +438,16 @@ __global__ void k_layout_keys(const int32_t *__restrict__ bins, int64_t R, int64
     }
 }
 
-// Bin offsets of the model matrix from the layout's key offsets:
-// offsets[b] = sum over parts of the points of that part in bins below b.
-__global__ void k_natural_offsets(const int32_t *__restrict__ koff, LaySel L, int B, int64_t N,
-                                  int32_t *__restrict__ offsets) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b > B) return;
-    if (b == B) {
-        offsets[B] = (int32_t)N;
-        return;
-    }
-    const int P = L.get().P;
-    int32_t s = 0;
-    for (int p = 0; p < P; ++p) s += koff[p * B + b] - koff[p * B];
-    offsets[b] = s;
+// Whether the key-sorted point and interval streams are built (sel[4]): not
+// when the record stream costs less than the interval stream and less than
+// any point stream can (4 per point, the runs' share not counted), unless a
+// caller asked for one of them.
+__global__ void k_need_keys(const int32_t *n_rec, const int32_t *n_iv, int64_t N, int nf, int force,
+                            int force_keys, int32_t *need, int32_t *n_runs) {
+    const int64_t c_iv = 19 * (int64_t)n_iv[0];
+    const int64_t c_rec = (40 + 6 * nf) * (int64_t)n_rec[0];
+    need[0] = force_keys || force == 0 || force == 1 || (force < 0 && !(c_rec < 4 * N && c_rec <= c_iv));
+    if (!need[0]) n_runs[0] = 0;  // no point stream built
 }
 
 // Stream choice for the chosen layout, with the least estimated work in
@@ -464,6 +465,8 @@ __global__ void k_pick_stream(const int32_t *n_runs, const int32_t *n_iv, const 
     int m = 0;
     if (force >= 0) {
         m = force;
+    } else if (sel[4] == 0) {
+        m = 2;  // only the record stream was built
     } else {
         int64_t best = c_pt;
         if (c_iv < best) {
@@ -477,9 +480,10 @@ __global__ void k_pick_stream(const int32_t *n_runs, const int32_t *n_iv, const 
 
 // Stable scatter: each warp walks its tile in order, 32 points at a time;
 // equal keys inside a step are ranked by lane with __match_any_sync.
-__global__ void k_sort_scatter(const int32_t *__restrict__ keys, int64_t N, int Bk,
+__global__ void k_sort_scatter(const int32_t *__restrict__ keys, int64_t N, int Bk, const int32_t *gate,
                                const int32_t *__restrict__ starts, int64_t n_tiles,
                                int32_t *__restrict__ perm) {
+    if (gated_off(gate)) return;
     extern __shared__ int32_t s_cnt[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t *cnt = s_cnt + warp * Bk;
@@ -539,7 +543,9 @@ __device__ __forceinline__ T block_excl_scan(T v, T *s_warp, T &total) {
 }
 
 template <typename T>
-__global__ void k_scan_blocks(const T *__restrict__ in, T *__restrict__ out, int64_t L, T *__restrict__ block_sums) {
+__global__ void k_scan_blocks(const T *__restrict__ in, T *__restrict__ out, int64_t L, T *__restrict__ block_sums,
+                              const int32_t *gate) {
+    if (gated_off(gate)) return;
     __shared__ T s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
     T v[kScanItems];
@@ -558,7 +564,8 @@ __global__ void k_scan_blocks(const T *__restrict__ in, T *__restrict__ out, int
 }
 
 template <typename T>
-__global__ void k_scan_add(T *__restrict__ out, int64_t L, const T *__restrict__ block_off) {
+__global__ void k_scan_add(T *__restrict__ out, int64_t L, const T *__restrict__ block_off, const int32_t *gate) {
+    if (gated_off(gate)) return;
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
     const T add = block_off[blockIdx.x];
     for (int j = threadIdx.x; j < kScanBlock; j += blockDim.x)
@@ -573,7 +580,8 @@ __global__ void k_scan_add(T *__restrict__ out, int64_t L, const T *__restrict__
 // start flags (run: bit 0, interval: bit 32), so a single 64-bit scan numbers
 // runs (low half) and intervals (high half).
 __global__ void k_layout_flags(const int32_t *__restrict__ perm, const int32_t *__restrict__ keys, int64_t N,
-                               LaySel L, unsigned long long *__restrict__ flags) {
+                               LaySel L, unsigned long long *__restrict__ flags, const int32_t *gate) {
+    if (gated_off(gate)) return;
     const int64_t n_last = L.get().n_last;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -600,7 +608,8 @@ __global__ void k_layout_build(const int32_t *__restrict__ perm, const int32_t *
                                const unsigned long long *__restrict__ excl, int32_t *__restrict__ run_start,
                                int32_t *__restrict__ run_rest, int32_t *__restrict__ run_bin,
                                uint32_t *__restrict__ hpt, int32_t *__restrict__ n_runs, uint2 *__restrict__ ipt,
-                               int32_t *__restrict__ iv_rest, int32_t *__restrict__ n_iv) {
+                               int32_t *__restrict__ iv_rest, int32_t *__restrict__ n_iv, const int32_t *gate) {
+    if (gated_off(gate)) return;
     const LayGeom G = L.get();
     const uint32_t rmask = (1u << kRowBits) - 1u;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
@@ -662,7 +671,8 @@ __device__ __forceinline__ uint32_t rest_code(int32_t rest, int ndim, int64_t n1
 __global__ void k_layout_encode(const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_rest,
                                 const int32_t *__restrict__ n_runs_p, const int32_t *__restrict__ iv_rest,
                                 const int32_t *__restrict__ n_iv_p, int ndim, int64_t n1, int shift,
-                                uint32_t *__restrict__ hpt, uint2 *__restrict__ ipt) {
+                                uint32_t *__restrict__ hpt, uint2 *__restrict__ ipt, const int32_t *gate) {
+    if (gated_off(gate)) return;
     const int32_t n_runs = n_runs_p[0], n_iv = n_iv_p[0];
     const int32_t n = n_runs > n_iv ? n_runs : n_iv;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
@@ -680,7 +690,8 @@ __global__ void k_chunks(const int32_t *__restrict__ run_start, const int32_t *_
                          const int32_t *__restrict__ koff, int B, LaySel L, int C,
                          const unsigned long long *__restrict__ excl, int64_t N, const int32_t *__restrict__ n_iv_p,
                          int32_t *__restrict__ chunk_pt, int32_t *__restrict__ chunk_run,
-                         int32_t *__restrict__ chunk_iv) {
+                         int32_t *__restrict__ chunk_iv, const int32_t *gate) {
+    if (gated_off(gate)) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int P = L.get().P;
     if (c > P * C) return;
@@ -707,8 +718,18 @@ __global__ void k_chunks(const int32_t *__restrict__ run_start, const int32_t *_
 
 __global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
 
+// Key offsets of a counting sort: koff[b] = starts[b * n_tiles], koff[Bk] = N.
+__global__ void k_koff(const int32_t *__restrict__ starts, int64_t n_tiles, int Bk, int64_t N,
+                       int32_t *__restrict__ koff, const int32_t *gate) {
+    if (gated_off(gate)) return;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < Bk) koff[b] = starts[(int64_t)b * n_tiles];
+    else if (b == Bk) koff[b] = (int32_t)N;
+}
+
 __global__ void k_chunk_bins(const int32_t *__restrict__ chunk_run, const int32_t *__restrict__ run_bin, LaySel L,
-                             int C, int32_t *__restrict__ chunk_bin) {
+                             int C, int32_t *__restrict__ chunk_bin, const int32_t *gate) {
+    if (gated_off(gate)) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= L.get().P * C) return;
     const int32_t r0 = chunk_run[c], r1 = chunk_run[c + 1];
@@ -727,7 +748,8 @@ __device__ __forceinline__ int chunk_holding(const int32_t *chunk_pt, int n, int
     return lo;
 }
 __global__ void k_key_chunks(const int32_t *__restrict__ koff, LaySel L, int B, const int32_t *__restrict__ chunk_pt,
-                             int C, int2 *__restrict__ out) {
+                             int C, int2 *__restrict__ out, const int32_t *gate) {
+    if (gated_off(gate)) return;
     const int key = blockIdx.x * blockDim.x + threadIdx.x;
     const int P = L.get().P;
     if (key >= P * B) return;
@@ -1084,20 +1106,21 @@ static int scan_launches(int64_t L) {
 
 // (T = int32_t or unsigned long long; scratch counted in T elements)
 template <typename T>
-static vup_status scan_exclusive(const T *in, T *out, int64_t L, T *scratch, cudaStream_t s) {
+static vup_status scan_exclusive(const T *in, T *out, int64_t L, T *scratch, cudaStream_t s,
+                                 const int32_t *gate = nullptr) {
     const int64_t nb = ceil_div64(L, kScanBlock);
     if (nb <= 1) {
-        k_scan_blocks<T><<<1, kScanThreads, 0, s>>>(in, out, L, nullptr);
+        k_scan_blocks<T><<<1, kScanThreads, 0, s>>>(in, out, L, nullptr, gate);
         VUP_CHECK_LAUNCH();
         return VUP_OK;
     }
     T *sums = scratch;
     T *sums_scan = scratch + nb + 32;
-    k_scan_blocks<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, L, sums);
+    k_scan_blocks<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, L, sums, gate);
     VUP_CHECK_LAUNCH();
-    vup_status st = scan_exclusive<T>(sums, sums_scan, nb, scratch + 2 * nb + 64, s);
+    vup_status st = scan_exclusive<T>(sums, sums_scan, nb, scratch + 2 * nb + 64, s, gate);
     if (st != VUP_OK) return st;
-    k_scan_add<T><<<(unsigned)nb, 256, 0, s>>>(out, L, sums_scan);
+    k_scan_add<T><<<(unsigned)nb, 256, 0, s>>>(out, L, sums_scan, gate);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }
@@ -1166,7 +1189,8 @@ static int sort_warps(int Bk) { return std::max(1, std::min(kSortWarps, 32768 / 
 // Stable counting sort of `keys` (values < Bk) into perm; key offsets to koff
 // (Bk + 1 entries) when koff is not null.  `counts` must hold 2 Bk n_tiles + 8.
 static vup_status counting_sort(vup_grid g, const int32_t *keys, int Bk, int32_t *perm, int32_t *koff,
-                                int32_t *counts, int32_t *scratch, bool counts_ready, cudaStream_t s) {
+                                int32_t *counts, int32_t *scratch, bool counts_ready, cudaStream_t s,
+                                const int32_t *gate = nullptr) {
     const int64_t N = g->N;
     const int64_t n_tiles = ceil_div64(N, kSortTile);
     const int64_t L = (int64_t)Bk * n_tiles;
@@ -1179,18 +1203,15 @@ static vup_status counting_sort(vup_grid g, const int32_t *keys, int Bk, int32_t
         VUP_CHECK_CUDA(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     if (!counts_ready) {
-        k_count<<<blocks, 32 * nw, smem, s>>>(keys, N, Bk, counts, n_tiles);
+        k_count<<<blocks, 32 * nw, smem, s>>>(keys, N, Bk, counts, n_tiles, gate);
         VUP_CHECK_LAUNCH();
     }
-    vup_status st = scan_exclusive(counts, starts, L, scratch, s);
+    vup_status st = scan_exclusive(counts, starts, L, scratch, s, gate);
     if (st != VUP_OK) return st;
-    k_sort_scatter<<<blocks, 32 * nw, smem, s>>>(keys, N, Bk, starts, n_tiles, perm);
+    k_sort_scatter<<<blocks, 32 * nw, smem, s>>>(keys, N, Bk, gate, starts, n_tiles, perm);
     VUP_CHECK_LAUNCH();
     if (koff) {
-        // koff[b] = starts[b * n_tiles], koff[Bk] = N
-        VUP_CHECK_CUDA(cudaMemcpy2DAsync(koff, sizeof(int32_t), starts, sizeof(int32_t) * n_tiles, sizeof(int32_t),
-                                         Bk, cudaMemcpyDeviceToDevice, s));
-        k_set_i32<<<1, 1, 0, s>>>(koff + Bk, (int32_t)N);
+        k_koff<<<(Bk + 1 + 255) / 256, 256, 0, s>>>(starts, n_tiles, Bk, N, koff, gate);
         VUP_CHECK_LAUNCH();
     }
     return VUP_OK;
@@ -1201,7 +1222,7 @@ static vup_status counting_sort(vup_grid g, const int32_t *keys, int Bk, int32_t
 vup_status vup_natural_sort(vup_grid g, cudaStream_t s) {
     if (g->natural_valid) return VUP_OK;
     int32_t *scratch = (int32_t *)g->scan_tmp.p;
-    vup_status st = counting_sort(g, g->bins, g->B, g->perm, nullptr, (int32_t *)g->sort_counts.p, scratch, false, s);
+    vup_status st = counting_sort(g, g->bins, g->B, g->perm, g->offsets, (int32_t *)g->sort_counts.p, scratch, false, s);
     if (st != VUP_OK) return st;
     g->natural_valid = 1;
     return VUP_OK;
@@ -1298,7 +1319,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
 // streams, chunks, the natural bin offsets) for the current bins.  Built on
 // first use after a model evaluation (the histogram, the bin offsets), so a
 // caller may run it on a second stream beside the density preparation.
-vup_status vup_build_layout(vup_grid g, cudaStream_t s) {
+vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed) {
     const int64_t N = g->N;
     const int B = g->B;
     ProfScope prof("layout_sort_runs", s, 0);
@@ -1387,50 +1408,59 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s) {
                                                                        (int2 *)HL.rec_gch.p);
             VUP_CHECK_LAUNCH();
             // flags, scan, intervals, record flags, scan, records, padding, sort (count, scan,
-            // scatter, koff end), gather, codes, chunks, group chunks
-            launches += 2 * scan_launches(N) + 5 + 3 + scan_launches((int64_t)(n_groups + 1) * n_tiles) + 4;
+            // scatter, koff end), gather, codes, chunks, group chunks, gate
+            launches += 2 * scan_launches(N) + 5 + 3 + scan_launches((int64_t)(n_groups + 1) * n_tiles) + 5;
         }
-        st = counting_sort(g, HL.keys, Bk_max, HL.perm, HL.koff, counts, scratch, false, s);
+        // the key-sorted point and interval streams, unless the record stream is
+        // cheaper than both (every kernel below then returns at once)
+        const int32_t *gate = g->hist_sel + 4;
+        // (the point stream is always built for callers that walk it -- posterior
+        // means -- and where the shared-memory kernels cannot run)
+        const bool force_keys = points_needed || !vup_hist_tile_fits(g);
+        k_need_keys<<<1, 1, 0, s>>>(HL.n_rec, HL.n_iv, N, g->ndim - 1, g->hist_force, force_keys ? 1 : 0,
+                                    g->hist_sel + 4, HL.n_runs);
+        VUP_CHECK_LAUNCH();
+        st = counting_sort(g, HL.keys, Bk_max, HL.perm, HL.koff, counts, scratch, false, s, gate);
         if (st != VUP_OK) return st;
         // runs and intervals: one flag word per point, one 64-bit scan
         st = devbuf_reserve(g->lay_tmp, sizeof(unsigned long long) * 2 * (size_t)N);
         if (st != VUP_OK) return st;
         auto *flags = (unsigned long long *)g->lay_tmp.p;
         auto *excl = flags + N;
-        k_layout_flags<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, L, flags);
+        k_layout_flags<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, L, flags, gate);
         VUP_CHECK_LAUNCH();
-        st = scan_exclusive<unsigned long long>(flags, excl, N, (unsigned long long *)g->scan_tmp.p, s);
+        st = scan_exclusive<unsigned long long>(flags, excl, N, (unsigned long long *)g->scan_tmp.p, s, gate);
         if (st != VUP_OK) return st;
         k_layout_build<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, L, kRowShift, flags, excl, HL.run_start, HL.run_rest,
-                                          HL.run_bin, HL.hpt, HL.n_runs, HL.ipt, HL.iv_rest, HL.n_iv);
+                                          HL.run_bin, HL.hpt, HL.n_runs, HL.ipt, HL.iv_rest, HL.n_iv, gate);
         VUP_CHECK_LAUNCH();
         k_layout_encode<<<rb, 256, 0, s>>>(HL.run_start, HL.run_rest, HL.n_runs, HL.iv_rest, HL.n_iv, g->ndim,
-                                           g->ndim == 3 ? g->n[1] : 1, kRowShift, HL.hpt, HL.ipt);
+                                           g->ndim == 3 ? g->n[1] : 1, kRowShift, HL.hpt, HL.ipt, gate);
         VUP_CHECK_LAUNCH();
         // chunks of every part
         const int PC = g->hist_P * C;
         k_chunks<<<(PC + 1 + 127) / 128, 128, 0, s>>>(HL.run_start, HL.n_runs, HL.koff, B, L, C, excl, N, HL.n_iv,
-                                                       HL.chunk_pt, HL.chunk_run, HL.chunk_iv);
+                                                       HL.chunk_pt, HL.chunk_run, HL.chunk_iv, gate);
         VUP_CHECK_LAUNCH();
-        k_chunk_bins<<<(PC + 127) / 128, 128, 0, s>>>(HL.chunk_run, HL.run_bin, L, C, HL.chunk_bin);
+        k_chunk_bins<<<(PC + 127) / 128, 128, 0, s>>>(HL.chunk_run, HL.run_bin, L, C, HL.chunk_bin, gate);
         VUP_CHECK_LAUNCH();
-        k_key_chunks<<<(Bk_max + 127) / 128, 128, 0, s>>>(HL.koff, L, B, HL.chunk_pt, C, HL.key_chunks);
-        VUP_CHECK_LAUNCH();
-        k_natural_offsets<<<(B + 1 + 127) / 128, 128, 0, s>>>(HL.koff, L, B, N, g->offsets);
+        k_key_chunks<<<(Bk_max + 127) / 128, 128, 0, s>>>(HL.koff, L, B, HL.chunk_pt, C, HL.key_chunks, gate);
         VUP_CHECK_LAUNCH();
         st = vup_pick_hist_layout(g, s);
         if (st != VUP_OK) return st;
         // keys, sort (count, scan, scatter, koff end), flags, scan, build, encode, chunks,
-        // chunk keys, key chunks, natural offsets, stream choice
-        launches += 1 + 3 + scan_launches((int64_t)Bk_max * n_tiles) + 1 + scan_launches(N) + 2 + 5;
+        // chunk keys, key chunks, stream choice
+        launches += 1 + 3 + scan_launches((int64_t)Bk_max * n_tiles) + 1 + scan_launches(N) + 2 + 4;
     }
     g->layout_valid = 1;
+    g->layout_has_points = points_needed || g->ndim == 1;
     prof.launches = launches;
     return VUP_OK;
 }
 
-vup_status vup_ensure_layout(vup_grid g, cudaStream_t s) {
-    return g->layout_valid ? VUP_OK : vup_build_layout(g, s);
+vup_status vup_ensure_layout(vup_grid g, cudaStream_t s, bool points_needed) {
+    if (g->layout_valid && (!points_needed || g->layout_has_points)) return VUP_OK;
+    return vup_build_layout(g, s, points_needed);
 }
 
 vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s) {

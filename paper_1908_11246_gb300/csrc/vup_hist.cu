@@ -1133,6 +1133,13 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     return VUP_OK;
 }
 
+bool vup_hist_tile_fits(vup_grid g) {
+    const bool coded = g->ndim == 2 || (g->n[0] <= 512 && g->n[1] <= 4096);
+    for (int l = 0; l < g->n_layouts; ++l)
+        if (hist_smem_bytes(g->hl[l].part_rows) > 220 * 1024) return false;
+    return coded;
+}
+
 // A 2-D grid whose every part fits the shared-memory tile.
 bool vup_hist_batchable(vup_grid g) {
     if (g->ndim != 2) return false;

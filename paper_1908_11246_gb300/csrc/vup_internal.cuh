@@ -94,6 +94,7 @@ struct vup_grid_s {
     int32_t B_cap = 0;
     int natural_valid = 0;         // perm holds the stable sort by bin
     int layout_valid = 0;          // the histogram layout matches the current bins
+    int layout_has_points = 0;     // ... and its key-sorted streams were built on request
     int range_ready = 0;           // ext holds the range of y (reduced by the model kernels)
     // second stream for the layout build beside the density preparation
     // (forked from and joined back into the caller's stream)
@@ -177,8 +178,12 @@ vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta,
 vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s);  // range, bins (1-D: the sorted order)
 vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s);
 // Histogram layout (2-D / 3-D): built on first use after a model evaluation.
-vup_status vup_build_layout(vup_grid g, cudaStream_t s);
-vup_status vup_ensure_layout(vup_grid g, cudaStream_t s);
+// points_needed: the key-sorted point stream is built whatever the device
+// would choose (callers that walk it: posterior means).
+vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed = false);
+vup_status vup_ensure_layout(vup_grid g, cudaStream_t s, bool points_needed = false);
+// every layout's part tile fits the shared-memory histogram kernels
+bool vup_hist_tile_fits(vup_grid g);
 vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s);
 vup_status vup_natural_sort(vup_grid g, cudaStream_t s);
 
