@@ -198,6 +198,7 @@ static void free_grid(vup_grid g) {
     if (g->side) cudaStreamDestroy(g->side);
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->ev_rec) cudaEventDestroy(g->ev_rec);
     cudaFree(g->ydev_scale);
     cudaFree(g->dstatus);
     for (int o = 0; o < kNumOrient; ++o) {
@@ -511,10 +512,11 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
             VUP_CHECK_CUDA(cudaStreamCreateWithPriority(&g->side, cudaStreamNonBlocking, hi_prio));
             VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
             VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+            VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_rec, cudaEventDisableTiming));
         }
         VUP_CHECK_CUDA(cudaEventRecord(g->ev_fork, s));
         VUP_CHECK_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
-        vup_status lst = vup_build_layout(g, g->side);
+        vup_status lst = vup_build_layout(g, g->side, false, g->ev_rec);
         VUP_CHECK_CUDA(cudaEventRecord(g->ev_join, g->side));
         forked = true;
         if (lst != VUP_OK) {
@@ -550,11 +552,11 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
         if ((st = vup_moments_finish(g, K, (int)nct, moments_raw, moments_central, s)) != VUP_OK) return st;
     }
     if (hist) {
-        if (forked) {
-            VUP_CHECK_CUDA(cudaStreamWaitEvent(s, g->ev_join, 0));
-            join.on = false;
-        }
-        if ((st = vup_hist_fused(g, K, hist, s)) != VUP_OK) return st;
+        // the record-stream histogram waits for the records only; the other
+        // streams' kernels (and the finish) for the whole layout
+        if (forked) VUP_CHECK_CUDA(cudaStreamWaitEvent(s, g->ev_rec, 0));
+        if ((st = vup_hist_fused(g, K, hist, s, nullptr, false, forked ? g->ev_join : nullptr)) != VUP_OK) return st;
+        join.on = false;
     }
     return VUP_OK;
 }

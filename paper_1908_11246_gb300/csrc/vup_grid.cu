@@ -441,41 +441,32 @@ __global__ void k_layout_keys(const int32_t *__restrict__ bins, int64_t R, int64
 // Whether the key-sorted point and interval streams are built (sel[4]): not
 // when the record stream costs less than the interval stream and less than
 // any point stream can (4 per point, the runs' share not counted), unless a
-// caller asked for one of them.
+// caller asked for one of them.  The record stream is then chosen at once
+// (sel[1] = 2, before the rest of the layout is built); otherwise the choice
+// waits for the run counts (sel[1] = -1 meanwhile) and is one of the others.
 __global__ void k_need_keys(const int32_t *n_rec, const int32_t *n_iv, int64_t N, int nf, int force,
-                            int force_keys, int32_t *need, int32_t *n_runs) {
+                            int force_keys, int32_t *sel, int32_t *n_runs) {
     const int64_t c_iv = 19 * (int64_t)n_iv[0];
     const int64_t c_rec = (40 + 6 * nf) * (int64_t)n_rec[0];
-    need[0] = force_keys || force == 0 || force == 1 || (force < 0 && !(c_rec < 4 * N && c_rec <= c_iv));
-    if (!need[0]) n_runs[0] = 0;  // no point stream built
+    const int need = force_keys || force == 0 || force == 1 || (force < 0 && !(c_rec < 4 * N && c_rec <= c_iv));
+    sel[4] = need;
+    sel[1] = need ? -1 : 2;
+    if (!need) n_runs[0] = 0;  // no point stream built
 }
 
-// Stream choice for the chosen layout, with the least estimated work in
-// units of about 3.3 ps of kernel time per 128-density tile (fitted to
-// measured launches on 2-D and 3-D grids): point stream 4 per point (one
-// gather) + 20 per run (rest-factor pipeline); interval stream 19 per
-// interval (two gathers, a difference, a rest-factor load); record stream
+// Stream costs, in units of about 3.3 ps of kernel time per 128-density tile
+// (fitted to measured launches on 2-D and 3-D grids): point stream 4 per
+// point (one gather) + 20 per run (rest-factor pipeline); interval stream 19
+// per interval (two gathers, a difference, a rest-factor load); record stream
 // 40 + 6 per extra rest axis per record (five gathers, four differences, one
-// rest-factor load per rest axis).  force: -1 any, else that stream.
-__global__ void k_pick_stream(const int32_t *n_runs, const int32_t *n_iv, const int32_t *n_rec, int64_t N,
-                              int nf, int force, int32_t *sel) {
+// rest-factor load per rest axis).  After the key sort: the point or the
+// interval stream, whichever costs less (unless forced), when the record
+// stream was not chosen before it.
+__global__ void k_pick_stream(const int32_t *n_runs, const int32_t *n_iv, int64_t N, int force, int32_t *sel) {
+    if (sel[4] == 0) return;  // the record stream, chosen before the key sort
     const int64_t c_pt = 4 * N + 20 * (int64_t)n_runs[0];
     const int64_t c_iv = 19 * (int64_t)n_iv[0];
-    const int64_t c_rec = (40 + 6 * nf) * (int64_t)n_rec[0];
-    int m = 0;
-    if (force >= 0) {
-        m = force;
-    } else if (sel[4] == 0) {
-        m = 2;  // only the record stream was built
-    } else {
-        int64_t best = c_pt;
-        if (c_iv < best) {
-            best = c_iv;
-            m = 1;
-        }
-        if (c_rec < best) m = 2;
-    }
-    sel[1] = m;
+    sel[1] = (force == 0 || force == 1) ? force : (c_iv < c_pt ? 1 : 0);
 }
 
 // Stable scatter: each warp walks its tile in order, 32 points at a time;
@@ -1319,7 +1310,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
 // streams, chunks, the natural bin offsets) for the current bins.  Built on
 // first use after a model evaluation (the histogram, the bin offsets), so a
 // caller may run it on a second stream beside the density preparation.
-vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed) {
+vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cudaEvent_t records_done) {
     const int64_t N = g->N;
     const int B = g->B;
     ProfScope prof("layout_sort_runs", s, 0);
@@ -1412,14 +1403,16 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed) {
             launches += 2 * scan_launches(N) + 5 + 3 + scan_launches((int64_t)(n_groups + 1) * n_tiles) + 5;
         }
         // the key-sorted point and interval streams, unless the record stream is
-        // cheaper than both (every kernel below then returns at once)
+        // cheaper than both (every kernel below then returns at once); the
+        // point stream is always built for callers that walk it -- posterior
+        // means -- and where the shared-memory kernels cannot run
         const int32_t *gate = g->hist_sel + 4;
-        // (the point stream is always built for callers that walk it -- posterior
-        // means -- and where the shared-memory kernels cannot run)
         const bool force_keys = points_needed || !vup_hist_tile_fits(g);
         k_need_keys<<<1, 1, 0, s>>>(HL.n_rec, HL.n_iv, N, g->ndim - 1, g->hist_force, force_keys ? 1 : 0,
-                                    g->hist_sel + 4, HL.n_runs);
+                                    g->hist_sel, HL.n_runs);
         VUP_CHECK_LAUNCH();
+        // a caller may start the record-stream histogram from here on
+        if (records_done) VUP_CHECK_CUDA(cudaEventRecord(records_done, s));
         st = counting_sort(g, HL.keys, Bk_max, HL.perm, HL.koff, counts, scratch, false, s, gate);
         if (st != VUP_OK) return st;
         // runs and intervals: one flag word per point, one 64-bit scan
@@ -1464,8 +1457,7 @@ vup_status vup_ensure_layout(vup_grid g, cudaStream_t s, bool points_needed) {
 }
 
 vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s) {
-    k_pick_stream<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->hl[0].n_iv, g->hl[0].n_rec, g->N, g->ndim - 1, g->hist_force,
-                                  g->hist_sel);
+    k_pick_stream<<<1, 1, 0, s>>>(g->hl[0].n_runs, g->hl[0].n_iv, g->N, g->hist_force, g->hist_sel);
     VUP_CHECK_LAUNCH();
     return VUP_OK;
 }

@@ -1058,7 +1058,7 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
 }
 
 vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab,
-                          bool points_only) {
+                          bool points_only, cudaEvent_t keys_ready) {
     const int nd = g->ndim;
     int64_t rows;
     int P_max;
@@ -1111,16 +1111,21 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
                 VUP_CHECK_LAUNCH();
                 return VUP_OK;
             };
-            vup_status st = nd == 3 ? launch(k_hist_smem<2, 0>, G, n_items) : launch(k_hist_smem<1, 0>, G, n_items);
-            if (st != VUP_OK) return st;
-            if (!points_only) {
-                st = nd == 3 ? launch(k_hist_smem<2, 1>, G, n_items) : launch(k_hist_smem<1, 1>, G, n_items);
-                if (st != VUP_OK) return st;
+            vup_status st;
+            if (!points_only) {  // the record stream first: it needs no key sort
                 st = nd == 3 ? launch(k_hist_smem<2, 2>, Sr, n_items_rec)
                              : launch(k_hist_smem<1, 2>, Sr, n_items_rec);
                 if (st != VUP_OK) return st;
             }
+            if (keys_ready) VUP_CHECK_CUDA(cudaStreamWaitEvent(s, keys_ready, 0));
+            st = nd == 3 ? launch(k_hist_smem<2, 0>, G, n_items) : launch(k_hist_smem<1, 0>, G, n_items);
+            if (st != VUP_OK) return st;
+            if (!points_only) {
+                st = nd == 3 ? launch(k_hist_smem<2, 1>, G, n_items) : launch(k_hist_smem<1, 1>, G, n_items);
+                if (st != VUP_OK) return st;
+            }
         } else {
+            if (keys_ready) VUP_CHECK_CUDA(cudaStreamWaitEvent(s, keys_ready, 0));
             dim3 grd((unsigned)(P_max * G), (unsigned)nkt);
             k_hist_global<<<grd, kHistWarps * 32, 0, s>>>(A, G);
             VUP_CHECK_LAUNCH();

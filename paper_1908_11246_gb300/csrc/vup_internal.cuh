@@ -99,7 +99,7 @@ struct vup_grid_s {
     // second stream for the layout build beside the density preparation
     // (forked from and joined back into the caller's stream)
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_rec = nullptr;
 
     // counting-sort scratch
     DevBuf sort_counts, scan_tmp, lay_tmp, rec_tmp;
@@ -180,7 +180,10 @@ vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s);
 // Histogram layout (2-D / 3-D): built on first use after a model evaluation.
 // points_needed: the key-sorted point stream is built whatever the device
 // would choose (callers that walk it: posterior means).
-vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed = false);
+// records_done (optional) is recorded on s once the record stream is complete
+// (the key-sorted streams follow).
+vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed = false,
+                            cudaEvent_t records_done = nullptr);
 vup_status vup_ensure_layout(vup_grid g, cudaStream_t s, bool points_needed = false);
 // every layout's part tile fits the shared-memory histogram kernels
 bool vup_hist_tile_fits(vup_grid g);
@@ -204,8 +207,10 @@ vup_status vup_moments_finish(vup_grid g, int64_t K, int n_col_tiles, double *ra
 // points_only: walk the point stream even where the interval stream was
 // chosen (sums that must keep their relative accuracy in low-mass bins, as
 // the numerators and denominators of ratios do).
+// keys_ready (optional): an event the point and interval kernels (and the
+// finish) wait for; the record-stream kernel is launched before that wait.
 vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab = nullptr,
-                          bool points_only = false);
+                          bool points_only = false, cudaEvent_t keys_ready = nullptr);
 vup_status vup_propagate_1d(vup_grid g, const vup_densities *d, double *raw, double *central,
                             float *hist, cudaStream_t s);
 vup_status vup_ipsa_1d(vup_grid g, const vup_densities *d, const double *grad, float *dmu,
