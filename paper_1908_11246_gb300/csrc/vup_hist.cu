@@ -122,8 +122,16 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
 // words, 2 mbarriers per warp.
 __host__ __device__ inline size_t hist_tile_bytes(int64_t rows) { return (size_t)((rows + 1) * kKT * 4); }
 __host__ __device__ inline size_t hist_warp_bytes() { return (size_t)2 * kWin * 4; }
-__host__ __device__ inline size_t hist_smem_bytes(int64_t rows) {
-    return hist_tile_bytes(rows) + kHistWarps * hist_warp_bytes() + kHistWarps * 2 * sizeof(uint64_t);
+// Kernel variants: 0 point stream, 1 interval stream, 2 record stream, 3
+// record stream with 16 warps of up to 128 registers (more of its five
+// gathers and four accumulators in flight per warp; measured faster when the
+// rest-factor table stays in L2, slower when its rows come from HBM and more
+// warps hide the latency).  The others run 20 warps of 96 registers.  Each
+// fills the register file of the one CTA per SM that the tile allows.
+__host__ __device__ constexpr int hist_warps(int mode) { return mode == 3 ? 16 : kHistWarps; }
+__host__ __device__ constexpr int hist_stream_of(int mode) { return mode == 3 ? 2 : mode; }
+__host__ __device__ inline size_t hist_smem_bytes(int64_t rows, int warps = kHistWarps) {
+    return hist_tile_bytes(rows) + warps * hist_warp_bytes() + warps * 2 * sizeof(uint64_t);
 }
 
 // Store the finished sums of key `key` for this lane's four densities (global
@@ -342,6 +350,21 @@ __device__ __forceinline__ bool iv_chunk(const ItemCtx &X, int c, int p, int64_t
 constexpr uint32_t kRecNegFlag = 1u << 30;
 constexpr uint32_t kRecEndFlag = 1u << 31;
 constexpr uint32_t kRecOffMask = (1u << 18) - 1u;
+
+// Store a record group's four sums (a lane's four densities each): whole
+// groups to their direct rows, cut ones to the chunk's partial rows (side 0:
+// its first group).  Out of line, like flush_key: it runs once per group.
+__device__ __noinline__ void flush_group(const ItemCtx *X, int c, int p, int64_t k, int32_t gr, bool shared,
+                                         bool first, float4 a0, float4 a1, float4 a2, float4 a3) {
+    const int b0 = (gr - p * X->GB) * kRecBinsH;
+    const int64_t K_pad = X->K_pad;
+    float *row = shared ? X->part + ((int64_t)c * 2 + (first ? 0 : 1)) * 4 * K_pad + k
+                        : X->direct + ((int64_t)p * X->B + b0) * K_pad + k;
+    *reinterpret_cast<float4 *>(row) = a0;
+    if (shared || b0 + 1 < X->B) *reinterpret_cast<float4 *>(row + K_pad) = a1;
+    if (shared || b0 + 2 < X->B) *reinterpret_cast<float4 *>(row + 2 * K_pad) = a2;
+    if (shared || b0 + 3 < X->B) *reinterpret_cast<float4 *>(row + 3 * K_pad) = a3;
+}
 template <int NF>
 __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, int64_t k, const float *ws,
                                                uint32_t *win, uint64_t *mbar, uint32_t &wseq, volatile int *abort) {
@@ -394,14 +417,7 @@ __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, i
     // a group's four sums: whole groups to their direct rows, cut ones to the chunk's partials
     auto flush = [&](int32_t gr) {
         const bool first = gr == first_grp;
-        const bool shared = first ? sh_first : (gr == last_grp && sh_last);
-        const int b0 = (gr - p * X.GB) * kRecBinsH;
-        float *row = shared ? X.part + ((int64_t)c * 2 + (first ? 0 : 1)) * 4 * X.K_pad + k
-                            : X.direct + ((int64_t)p * X.B + b0) * X.K_pad + k;
-        *reinterpret_cast<float4 *>(row) = acc0;
-        if (shared || b0 + 1 < X.B) *reinterpret_cast<float4 *>(row + X.K_pad) = acc1;
-        if (shared || b0 + 2 < X.B) *reinterpret_cast<float4 *>(row + 2 * X.K_pad) = acc2;
-        if (shared || b0 + 3 < X.B) *reinterpret_cast<float4 *>(row + 3 * X.K_pad) = acc3;
+        flush_group(&X, c, p, k, gr, first ? sh_first : (gr == last_grp && sh_last), first, acc0, acc1, acc2, acc3);
         acc0 = acc1 = acc2 = acc3 = zero4;
     };
     const uint32_t wsl = smem_u32(ws) + lane * 16;
@@ -421,7 +437,7 @@ __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, i
         fma4(acc2, fs, sub4(p3, p2));
         fma4(acc3, fs, sub4(p4, p3));
         f = coded_factor(v.y);
-        if (v.x & kRecEndFlag) flush((int32_t)v.z);
+        if (__builtin_expect((v.x & kRecEndFlag) != 0, 0)) flush((int32_t)v.z);
     };
     // foreign records: every boundary row 0 (differences 0), no group end;
     // those before the chunk keep their rest codes (they load its first factors)
@@ -452,7 +468,7 @@ __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, i
             const bool edge = t0 < r0 || t0 + 4 > r1;
             auto one = [&](int m, float4 &f) {
                 uint4 u = wq[qq / 4 + 2 * m], v = wq[qq / 4 + 2 * m + 1];
-                if (edge) masked(u, v, t0 + m);
+                if (__builtin_expect(edge, 0)) masked(u, v, t0 + m);
                 step(u, v, f);
             };
             one(0, f0);
@@ -485,7 +501,8 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     float *ws = reinterpret_cast<float *>(sm);
     const size_t tb = hist_tile_bytes(tile_rows);
     uint32_t *win = reinterpret_cast<uint32_t *>(sm + tb + (size_t)warp * hist_warp_bytes());
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + tb + kHistWarps * hist_warp_bytes()) + 2 * warp;
+    constexpr int kWarps = hist_warps(MODE);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + tb + kWarps * hist_warp_bytes()) + 2 * warp;
 
     // the previous item's readers of the tile and the context are done first
     __syncthreads();
@@ -504,7 +521,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         X.rec_sets = A.rec_sets;
         X.C_rec = A.C_rec;
         X.GB = A.GB;
-        X.mode = MODE;
+        X.mode = hist_stream_of(MODE);
         X.dstatus = A.dstatus;
     }
     if (threadIdx.x < kKT) s_invz[threadIdx.x] = inv_z(*Ap, k0 + threadIdx.x);
@@ -535,7 +552,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         // rows are cut into kScanSegs segments, one thread per (segment,
         // column): segment totals first (kept in the idle staging buffers),
         // then each segment rescanned from the sum of the totals before it.
-        constexpr int kScanSegs = kHistWarps * 32 / kKT;
+        constexpr int kScanSegs = kWarps * 32 / kKT;
         const int col = threadIdx.x % kKT, sg = threadIdx.x / kKT;
         const int64_t rs = (nrows + kScanSegs - 1) / kScanSegs;
         const int64_t a0 = min(nrows, sg * rs), a1 = min(nrows, a0 + rs);
@@ -715,7 +732,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         if (cur_key >= 0) flush(cur_key, bacc);
         return true;
     };
-    if constexpr (MODE == 2) {
+    if constexpr (MODE >= 2) {
         // this item's range of the part's record chunks, handed out one at a time
         const int c_lo = (int)((int64_t)cg * X.C_rec / X.rec_sets), c_hi = (int)((int64_t)(cg + 1) * X.C_rec / X.rec_sets);
         for (;;) {
@@ -740,13 +757,13 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     }
 }
 
-__device__ __forceinline__ uint64_t *hist_mbar(uint8_t *sm, int64_t tile_rows) {
-    return reinterpret_cast<uint64_t *>(sm + hist_tile_bytes(tile_rows) + kHistWarps * hist_warp_bytes()) +
+__device__ __forceinline__ uint64_t *hist_mbar(uint8_t *sm, int64_t tile_rows, int warps) {
+    return reinterpret_cast<uint64_t *>(sm + hist_tile_bytes(tile_rows) + warps * hist_warp_bytes()) +
            2 * (threadIdx.x >> 5);
 }
-__device__ __forceinline__ void hist_init_mbar(uint8_t *sm, int64_t tile_rows) {
+__device__ __forceinline__ void hist_init_mbar(uint8_t *sm, int64_t tile_rows, int warps) {
     if ((threadIdx.x & 31) == 0) {
-        uint64_t *mbar = hist_mbar(sm, tile_rows);
+        uint64_t *mbar = hist_mbar(sm, tile_rows, warps);
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -766,15 +783,15 @@ __device__ __forceinline__ int hist_stream(const HistArgs &A) { return A.points_
 // stay apart); the host launches both and every CTA of the one the device
 // did not choose returns at once.
 template <int NF, int MODE>
-__global__ void __launch_bounds__(kHistWarps * 32, 1)
+__global__ void __launch_bounds__(hist_warps(MODE) * 32, 1)
     k_hist_smem(const __grid_constant__ HistArgs A, int64_t tile_rows, int P, int G, int n_items) {
-    if (hist_stream(A) != MODE) return;  // uniform
+    if (hist_stream(A) != hist_stream_of(MODE)) return;  // uniform
     extern __shared__ __align__(128) uint8_t sm[];
     __shared__ ItemCtx X;
     __shared__ float s_invz[kKT];
     __shared__ int abort, next_chunk;
     if (threadIdx.x == 0) abort = 0;
-    hist_init_mbar(sm, tile_rows);
+    hist_init_mbar(sm, tile_rows, hist_warps(MODE));
     uint32_t wseq = 0;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int cg = it % G, pk = it / G;
@@ -791,7 +808,7 @@ struct HistItem {
 };
 
 template <int NF, int MODE>
-__global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_batched(const HistArgs *__restrict__ insts,
+__global__ void __launch_bounds__(hist_warps(MODE) * 32, 1) k_hist_batched(const HistArgs *__restrict__ insts,
                                                                      const HistItem *__restrict__ items,
                                                                      int n_items, int64_t tile_rows,
                                                                      int *__restrict__ next_item) {
@@ -800,7 +817,7 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_batched(const HistA
     __shared__ float s_invz[kKT];
     __shared__ int abort, next_chunk, s_it;
     if (threadIdx.x == 0) abort = 0;
-    hist_init_mbar(sm, tile_rows);
+    hist_init_mbar(sm, tile_rows, hist_warps(MODE));
     uint32_t wseq = 0;
     // items are handed out one at a time in their (longest first) order
     for (;;) {
@@ -810,7 +827,7 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_batched(const HistA
         const int it = s_it;
         if (it >= n_items) break;
         const HistItem w = items[it];
-        if (hist_stream(insts[w.inst]) != MODE) continue;  // uniform
+        if (hist_stream(insts[w.inst]) != hist_stream_of(MODE)) continue;  // uniform
         hist_item<NF, MODE>(insts + w.inst, w.p, w.cg, (int64_t)w.kt * kKT, sm, tile_rows, wseq, &abort, X, s_invz,
                             &next_chunk);
     }
@@ -1091,7 +1108,7 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     int Sr = 1;
     {
         double best_r = -1.0;
-        for (int ss = 1; ss <= std::max(1, A.C_rec / kHistWarps); ++ss) {  // at least a chunk per warp
+        for (int ss = 1; ss <= std::max(1, A.C_rec / hist_warps(3)); ++ss) {  // at least a chunk per warp
             const int64_t items = (int64_t)P_max * ss * nkt;
             const double eff = (double)items / (double)(ceil_div64(items, sms) * sms);
             if (eff > best_r + 0.02) {
@@ -1105,23 +1122,33 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     {
         VUP_PROF("hist_segmented", s, in_smem && !points_only ? 3 : 1);
         if (in_smem) {
-            auto launch = [&](auto kern, int gg, int items) -> vup_status {
-                VUP_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                kern<<<items, kHistWarps * 32, smem, s>>>(A, rows, P_max, gg, items);
+            auto launch = [&](auto kern, int gg, int items, int mode) -> vup_status {
+                const size_t sm_bytes = hist_smem_bytes(rows, hist_warps(mode));
+                VUP_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes));
+                kern<<<items, hist_warps(mode) * 32, sm_bytes, s>>>(A, rows, P_max, gg, items);
                 VUP_CHECK_LAUNCH();
                 return VUP_OK;
             };
             vup_status st;
             if (!points_only) {  // the record stream first: it needs no key sort
-                st = nd == 3 ? launch(k_hist_smem<2, 2>, Sr, n_items_rec)
-                             : launch(k_hist_smem<1, 2>, Sr, n_items_rec);
+                // 16 warps when the rest-factor rows (of either layout) fit well in L2
+                int64_t rest_rows = 0;
+                for (int l = 0; l < g->n_layouts; ++l) rest_rows = std::max(rest_rows, g->N / g->hl[l].n_last);
+                if (nd == 3) rest_rows = g->n[0] + g->n[1];
+                const bool l2_rest = (double)rest_rows * A.K_pad * 4.0 <= 96.0 * 1024 * 1024;
+                if (l2_rest)
+                    st = nd == 3 ? launch(k_hist_smem<2, 3>, Sr, n_items_rec, 3)
+                                 : launch(k_hist_smem<1, 3>, Sr, n_items_rec, 3);
+                else
+                    st = nd == 3 ? launch(k_hist_smem<2, 2>, Sr, n_items_rec, 2)
+                                 : launch(k_hist_smem<1, 2>, Sr, n_items_rec, 2);
                 if (st != VUP_OK) return st;
             }
             if (keys_ready) VUP_CHECK_CUDA(cudaStreamWaitEvent(s, keys_ready, 0));
-            st = nd == 3 ? launch(k_hist_smem<2, 0>, G, n_items) : launch(k_hist_smem<1, 0>, G, n_items);
+            st = nd == 3 ? launch(k_hist_smem<2, 0>, G, n_items, 0) : launch(k_hist_smem<1, 0>, G, n_items, 0);
             if (st != VUP_OK) return st;
             if (!points_only) {
-                st = nd == 3 ? launch(k_hist_smem<2, 1>, G, n_items) : launch(k_hist_smem<1, 1>, G, n_items);
+                st = nd == 3 ? launch(k_hist_smem<2, 1>, G, n_items, 1) : launch(k_hist_smem<1, 1>, G, n_items, 1);
                 if (st != VUP_OK) return st;
             }
         } else {
@@ -1246,7 +1273,8 @@ vup_status vup_hist_batched(void *plan, cudaStream_t s) {
                                                                  (const HistItem *)P->items.p, P->n_items, P->rows,
                                                                  ctr + 1);
         VUP_CHECK_LAUNCH();
-        k_hist_batched<1, 2><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
+        k_hist_batched<1, 2><<<grid, hist_warps(2) * 32, hist_smem_bytes(P->rows, hist_warps(2)), s>>>(
+            (const HistArgs *)P->args.p,
                                                                  (const HistItem *)P->items.p, P->n_items, P->rows,
                                                                  ctr + 2);
         VUP_CHECK_LAUNCH();
