@@ -396,6 +396,13 @@ vup_status vup_grid_copy(vup_grid g, int which, void *dst_dev, size_t nbytes,
 vup_status vup_profile(int enable);
 vup_status vup_profile_read(char *buf, size_t cap);
 
+/* The same record as a timeline: synchronises the device and writes a
+ * NUL-terminated JSON array [[name, stream, launches, begin_ms, end_ms], ...]
+ * in launch order into buf (cap bytes); times are relative to the first
+ * record's begin event, stream numbers count the distinct launching streams
+ * in order of first use.  VUP_ERR_INVALID_ARG if buf is null or too small. */
+vup_status vup_profile_timeline(char *buf, size_t cap);
+
 /* Static description of a status code. */
 const char *vup_status_string(vup_status s);
 

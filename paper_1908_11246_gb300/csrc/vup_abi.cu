@@ -49,6 +49,7 @@ struct ProfRec {
     const char *name;
     cudaEvent_t a, b;
     int launches;
+    cudaStream_t stream;
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
@@ -72,7 +73,7 @@ ProfScope::ProfScope(const char *n, cudaStream_t s, int l) : name(n), stream(s),
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    ProfRec r{n, prof_event(), prof_event(), l};
+    ProfRec r{n, prof_event(), prof_event(), l, s};
     cudaEventRecord(r.a, s);
     g_prof_recs.push_back(r);
     slot = (int)g_prof_recs.size() - 1;
@@ -127,6 +128,35 @@ extern "C" vup_status vup_profile_read(char *buf, size_t cap) {
         first = false;
     }
     out += "}";
+    if (out.size() + 1 > cap) return VUP_ERR_INVALID_ARG;
+    memcpy(buf, out.c_str(), out.size() + 1);
+    return VUP_OK;
+}
+
+extern "C" vup_status vup_profile_timeline(char *buf, size_t cap) {
+    if (!buf || cap < 3) return VUP_ERR_INVALID_ARG;
+    VUP_CHECK_CUDA(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::vector<cudaStream_t> streams;
+    std::string out = "[";
+    bool first = true;
+    for (auto &r : g_prof_recs) {
+        float t0 = 0.f, t1 = 0.f;
+        if (cudaEventElapsedTime(&t0, g_prof_recs[0].a, r.a) != cudaSuccess ||
+            cudaEventElapsedTime(&t1, g_prof_recs[0].a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        size_t si = 0;
+        while (si < streams.size() && streams[si] != r.stream) ++si;
+        if (si == streams.size()) streams.push_back(r.stream);
+        char tmp[256];
+        snprintf(tmp, sizeof(tmp), "%s[\"%s\", %zu, %d, %.6f, %.6f]", first ? "" : ", ", r.name, si, r.launches, t0,
+                 t1);
+        out += tmp;
+        first = false;
+    }
+    out += "]";
     if (out.size() + 1 > cap) return VUP_ERR_INVALID_ARG;
     memcpy(buf, out.c_str(), out.size() + 1);
     return VUP_OK;

@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <memory>
 
 namespace {
 
@@ -282,62 +283,86 @@ __global__ void k_scale(const unsigned long long *ext, double *s_out) {
     s_out[0] = s > 0.0 ? s : 1.0;
 }
 
-// Eq. 4 bins: t = (y - ymin) / (ymax - ymin), bin = min(floor(t B), B - 1),
-// every operation correctly rounded and unfused, as in the FP64 oracle.
-// Also counts points per (bin, warp tile) for the stable counting sort.
-// The CTA has blockDim.x / 32 warps, each owning one tile of kSortTile points.
-// COUNT = false (2-D / 3-D grids, whose layouts sort their own keys): bins only.
-template <bool COUNT>
+// Eq. 4 bin of one output value: t = (y - ymin) / (ymax - ymin), bin =
+// min(floor(t B), B - 1), every operation correctly rounded and unfused, as
+// in the FP64 oracle.  FP32 screen: t32 = (y - ymin) B / range lies within
+// eps of the exact t; where no integer lies within eps of t32, floor(t32) is
+// the bin, otherwise the FP64 expression decides (about one point in 10^4 on
+// smooth models).  Error of t32: the FP32 roundings of y, ymin, the
+// difference, B / range and the product, each <= 2^-24 relative: |t32 - t| <=
+// 2^-24 ((|y| + |ymin|) B / range (2 + 2) + |t| 2); eps doubles that bound.
+struct BinRule {
+    double ymin, ymax, range;
+    float ymin32, sc32;
+    int B;
+    __device__ __forceinline__ BinRule(const unsigned long long *ext, int B_) : B(B_) {
+        read_range(ext, ymin, ymax);
+        range = __dsub_rn(ymax, ymin);
+        ymin32 = (float)ymin;
+        sc32 = range > 0.0 ? (float)((double)B / range) : 0.f;
+    }
+    __device__ __forceinline__ int32_t operator()(double yv) const {
+        if (!(range > 0.0)) return 0;
+        const float y32 = (float)yv;
+        const float t32 = (y32 - ymin32) * sc32;
+        const float fl32 = floorf(t32);
+        const float eps = 0x1p-21f * ((fabsf(y32) + fabsf(ymin32)) * sc32 * 2.f + fabsf(t32)) + 0x1p-60f;
+        int32_t b;
+        if (t32 - fl32 > eps && fl32 + 1.f - t32 > eps) {
+            b = (int32_t)fl32;
+        } else {
+            const double t = __ddiv_rn(__dsub_rn(yv, ymin), range);
+            b = (int32_t)floor(__dmul_rn(t, (double)B));
+        }
+        b = b > B - 1 ? B - 1 : b;
+        return b < 0 ? 0 : b;
+    }
+};
+
+// Bins of a 1-D grid, counted per (bin, warp tile) for the stable counting
+// sort that gives the model matrix's CSR form.  The CTA has blockDim.x / 32
+// warps, each owning one tile of kSortTile points.
 __global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
                              const unsigned long long *ext, int32_t *__restrict__ bins,
                              int32_t *__restrict__ counts, int64_t n_tiles) {
     extern __shared__ int32_t s_cnt[];  // [warps][B]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t *cnt = s_cnt + warp * B;
-    if (COUNT) {
-        for (int b = lane; b < B; b += 32) cnt[b] = 0;
-        __syncwarp();
-    }
+    for (int b = lane; b < B; b += 32) cnt[b] = 0;
+    __syncwarp();
     const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    double ymin, ymax;
-    read_range(ext, ymin, ymax);
-    const double range = __dsub_rn(ymax, ymin);
-    // FP32 screen: t32 = (y - ymin) B / range within eps of the exact t; where
-    // no integer lies within eps of t32, floor(t32) is the bin, otherwise the
-    // FP64 expression decides (about one point in 10^4 on smooth models).
-    // Error of t32: the FP32 roundings of y, ymin, the difference, B / range
-    // and the product, each <= 2^-24 relative: |t32 - t| <= 2^-24 ((|y| +
-    // |ymin|) B / range (2 + 2) + |t| 2); eps doubles that bound.
-    const float ymin32 = (float)ymin;
-    const float sc32 = range > 0.0 ? (float)((double)B / range) : 0.f;
+    const BinRule rule(ext, B);
     if (tile < n_tiles) {
         const int64_t i0 = tile * kSortTile;
         const int64_t i1 = min(N, i0 + kSortTile);
         for (int64_t i = i0 + lane; i < i1; i += 32) {
-            int32_t b = 0;
-            if (range > 0.0) {
-                const double yv = y[i];
-                const float y32 = (float)yv;
-                const float t32 = (y32 - ymin32) * sc32;
-                const float fl32 = floorf(t32);
-                const float eps = 0x1p-21f * ((fabsf(y32) + fabsf(ymin32)) * sc32 * 2.f + fabsf(t32)) + 0x1p-60f;
-                if (t32 - fl32 > eps && fl32 + 1.f - t32 > eps) {
-                    b = (int32_t)fl32;
-                } else {
-                    const double t = __ddiv_rn(__dsub_rn(yv, ymin), range);
-                    b = (int32_t)floor(__dmul_rn(t, (double)B));
-                }
-                b = b > B - 1 ? B - 1 : b;
-                b = b < 0 ? 0 : b;
-            }
+            const int32_t b = rule(y[i]);
             bins[i] = b;
-            if (COUNT) atomicAdd(&cnt[b], 1);
+            atomicAdd(&cnt[b], 1);
         }
-        if (COUNT) {
-            __syncwarp();
-            for (int b = lane; b < B; b += 32) counts[(int64_t)b * n_tiles + tile] = cnt[b];
-        }
+        __syncwarp();
+        for (int b = lane; b < B; b += 32) counts[(int64_t)b * n_tiles + tile] = cnt[b];
     }
+}
+
+// Bins of a 2-D / 3-D grid (its histogram layouts sort their own keys):
+// grid-stride over pairs of points, and the power-table scale s =
+// max(|ymin|, |ymax|) (1 if 0) from the first thread.
+__global__ void k_bins_scale(const double *__restrict__ y, int64_t N, int B, const unsigned long long *ext,
+                             int32_t *__restrict__ bins, double *s_out) {
+    const BinRule rule(ext, B);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double s = fmax(fabs(rule.ymin), fabs(rule.ymax));
+        s_out[0] = s > 0.0 ? s : 1.0;
+    }
+    const int64_t n2 = N >> 1;
+    const double2 *y2 = reinterpret_cast<const double2 *>(y);
+    int2 *b2 = reinterpret_cast<int2 *>(bins);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = y2[i];
+        b2[i] = make_int2(rule(v.x), rule(v.y));
+    }
+    if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) bins[N - 1] = rule(y[N - 1]);
 }
 
 // A kernel of the key-sorted streams' build returns at once when the device
@@ -414,7 +439,8 @@ __global__ void k_pick_layout(const int32_t *cnt, int32_t *sel) { sel[0] = cnt[1
 // last axis); layout 1 (2-D) walks its transpose.  32 x 32 tiles go through
 // shared memory so that reads and writes are coalesced either way.
 __global__ void k_layout_keys(const int32_t *__restrict__ bins, int64_t R, int64_t C, int B, LaySel L,
-                              int32_t *__restrict__ keys) {
+                              int32_t *__restrict__ keys, const int32_t *gate) {
+    if (gated_off(gate)) return;
     __shared__ int32_t t[32][33];
     const bool tr = L.sel[0] != 0;  // uniform over the grid
     const LayGeom G = L.get();
@@ -707,8 +733,6 @@ __global__ void k_chunks(const int32_t *__restrict__ run_start, const int32_t *_
     chunk_iv[c] = pt < N ? (int32_t)(excl[pt] >> 32) : n_iv_p[0];
 }
 
-__global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
-
 // Key offsets of a counting sort: koff[b] = starts[b * n_tiles], koff[Bk] = N.
 __global__ void k_koff(const int32_t *__restrict__ starts, int64_t n_tiles, int Bk, int64_t N,
                        int32_t *__restrict__ koff, const int32_t *gate) {
@@ -766,140 +790,150 @@ __global__ void k_key_chunks(const int32_t *__restrict__ koff, LaySel L, int B, 
 constexpr int kRecBins = 4;
 constexpr uint32_t kRecNeg = 1u << 30;  // bins fall along the line
 
-// Interval starts in layout order: the first point of a line-part or a key change.
-__global__ void k_liv_flags(const int32_t *__restrict__ keys, int64_t N, LaySel L, int32_t *__restrict__ flags) {
-    const int64_t n_last = L.get().n_last;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
-        flags[j] = (j % n_last == 0 || keys[j] != keys[j - 1]) ? 1 : 0;
-}
+constexpr uint32_t kRecEnd = 1u << 31;  // last record of its group
 
-__global__ void k_liv_emit(const int32_t *__restrict__ keys, int64_t N, const int32_t *__restrict__ flags,
-                           const int32_t *__restrict__ excl, int32_t *__restrict__ liv_key,
-                           int32_t *__restrict__ liv_pos, int32_t *__restrict__ n_liv) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        if (flags[j]) {
-            const int32_t i = excl[j];
-            liv_key[i] = keys[j];
-            liv_pos[i] = (int32_t)j;
-        }
-        if (j == N - 1) n_liv[0] = excl[j] + flags[j];
-    }
-}
+// The record stream, one thread per (part, line) segment of the chosen layout
+// (records never cross one), walking the bins in place in row order: an
+// interval starts at the segment's first row or where the bin changes; a
+// record starts at an interval whose group differs from the interval before
+// it, or whose bin step turns against the step before it when the three
+// intervals share a group.  PASS 1 (WRITE = false) counts the records of
+// every (group, line) into cnt[group * NL + line] and adds the intervals to
+// n_iv; after an exclusive scan of those counts, PASS 2 (WRITE = true) takes
+// cnt as cursors and writes each record at its place in (group, line, row)
+// order: words (B_0..B_3 as row byte offsets inside the part's tile) and (B_4 |
+// sign | group end, rest code of the record kRunAhead places later, group, 0),
+// and its rest index (the line).  bins is viewed as [R][C], C the last axis;
+// layout 1 (2-D) walks the columns.
+struct RecGeom {
+    int64_t R, C;
+    int B, GB;
+    int64_t NL;   // line stride of the count matrix (the most lines of either layout)
+    int shift;    // row byte shift of the histogram's prefix tile
+    int ndim;
+    int64_t n1;   // 3-D rest code: line = a0 n1 + a1 -> a0 | a1 << 15
+};
 
-// Record starts among the line-order intervals (same line and key part as the
-// two before, same group, same direction of the bin steps: no start).
-__global__ void k_rec_flags(const int32_t *__restrict__ liv_key, const int32_t *__restrict__ liv_pos,
-                            const int32_t *__restrict__ n_liv_p, int B, LaySel L, int32_t *__restrict__ flags,
-                            int64_t N) {
-    const int64_t n_last = L.get().n_last;
-    const int32_t n = n_liv_p[0];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        if (i >= n) {
-            flags[i] = 0;
-            continue;
-        }
-        // same line and part <=> same line and same key part; group within a part: bin / kRecBins
-        auto same = [&](int64_t u, int64_t v) {
-            return liv_pos[u] / n_last == liv_pos[v] / n_last && liv_key[u] / B == liv_key[v] / B &&
-                   (liv_key[u] % B) / kRecBins == (liv_key[v] % B) / kRecBins;
-        };
-        int32_t f = 1;
-        if (i > 0 && same(i, i - 1)) {
-            f = 0;
-            if (i > 1 && same(i - 1, i - 2)) {
-                const int32_t d1 = liv_key[i] - liv_key[i - 1], d0 = liv_key[i - 1] - liv_key[i - 2];
-                f = (d1 > 0) != (d0 > 0);
-            }
-        }
-        flags[i] = f;
-    }
-}
-
-// Unsorted records in line order: words (B_0, B_1, B_2, B_3 as row byte offsets
-// inside the part's tile) and (B_4 | sign, rest code (filled later), group, 0);
-// the sort key (group) and the rest index (line).
-__global__ void k_rec_emit(const int32_t *__restrict__ liv_key, const int32_t *__restrict__ liv_pos,
-                           const int32_t *__restrict__ n_liv_p, const int32_t *__restrict__ rflags,
-                           const int32_t *__restrict__ rexcl, int B, int GB, LaySel L, int shift,
-                           uint4 *__restrict__ rec, int32_t *__restrict__ rkey, int32_t *__restrict__ rrest,
-                           int32_t *__restrict__ n_rec_p, int64_t N) {
+template <bool WRITE>
+__global__ void __launch_bounds__(64) k_rec_walk(const int32_t *__restrict__ bins, RecGeom Q, LaySel L,
+                                                 int32_t *__restrict__ cnt, int32_t *__restrict__ n_iv,
+                                                 const int32_t *__restrict__ goff, const int32_t *__restrict__ n_rec_p,
+                                                 uint4 *__restrict__ rec, int32_t *__restrict__ rec_rest) {
+    const bool tr = L.sel[0] != 0;
     const LayGeom G = L.get();
-    const int32_t n = n_liv_p[0];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (i == n - 1) n_rec_p[0] = rexcl[i] + rflags[i];
-        if (!rflags[i]) continue;
-        const int32_t r = rexcl[i];
-        const int32_t key0 = liv_key[i];
-        const int p = key0 / B, q = (key0 % B) / kRecBins;
-        const int64_t line = liv_pos[i] / G.n_last, base = line * G.n_last;
-        const int64_t row0 = (int64_t)p * G.part_rows;
-        const int64_t part_end = base + min(G.n_last, row0 + G.part_rows);
-        int64_t st[kRecBins];
-        for (int j = 0; j < kRecBins; ++j) st[j] = -1;
-        int dir = 0;
-        int64_t e = part_end;
-        int64_t t = i;
-        int32_t prev = -1;
-        do {
-            const int32_t b = liv_key[t] % B;
-            st[b - q * kRecBins] = liv_pos[t];
-            if (prev >= 0 && dir == 0) dir = b > prev ? 1 : -1;
-            prev = b;
-            ++t;
-        } while (t < n && !rflags[t]);
-        if (t < n && liv_pos[t] < part_end) e = liv_pos[t];  // next interval of this line-part
+    const int64_t n_lines = tr ? Q.C : Q.R;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid >= (int64_t)G.P * n_lines) return;
+    const int p = (int)(tid / n_lines);
+    const int64_t line = tid - (int64_t)p * n_lines;
+    const int64_t row0 = (int64_t)p * G.part_rows, row1 = min(G.n_last, row0 + G.part_rows);
+    if (row0 >= row1) return;
+    const int64_t stride = tr ? Q.C : 1;
+    const int32_t *src = bins + (tr ? line : line * Q.C);
+    const int32_t n_rec = WRITE ? n_rec_p[0] : 0;
+    const uint32_t code = Q.ndim == 3 ? (uint32_t)(line / Q.n1) | ((uint32_t)(line % Q.n1) << 15) : (uint32_t)line;
+
+    int32_t bcur = -1, b1 = -1, b2 = -1;  // bins of the current interval and of the two before it
+    int rq = -1, dir = 0, rprev = -1;     // open record: group in the part, step sign, last bin
+    int32_t st0 = -1, st1 = -1, st2 = -1, st3 = -1;  // its bins' first rows (relative to row0)
+    int32_t niv = 0;
+    int32_t cg = -1, cc = 0;  // (group, count) run of pass 1; (group, cursor) of pass 2
+    auto emit = [&](int64_t e_row) {
+        const int32_t e = (int32_t)(e_row - row0);
+        const int32_t st[kRecBins] = {st0, st1, st2, st3};
         uint32_t w[kRecBins + 1];
+#pragma unroll
         for (int j = 0; j <= kRecBins; ++j) {
-            int64_t v = e;
+            int32_t v = e;
+#pragma unroll
             for (int jj = 0; jj < kRecBins; ++jj) {
                 const bool take = dir >= 0 ? jj >= j : jj < j;
                 if (take && st[jj] >= 0 && st[jj] < v) v = st[jj];
             }
-            w[j] = (uint32_t)(v - base - row0) << shift;
+            w[j] = (uint32_t)v << Q.shift;
         }
-        rec[2 * (int64_t)r] = make_uint4(w[0], w[1], w[2], w[3]);
-        rec[2 * (int64_t)r + 1] = make_uint4(w[4] | (dir < 0 ? kRecNeg : 0u), 0u, (uint32_t)(p * GB + q), 0u);
-        rkey[r] = p * GB + q;
-        rrest[r] = (int32_t)line;
+        const int32_t g = p * Q.GB + rq;
+        if (!WRITE) {
+            if (g != cg) {
+                if (cg >= 0) cnt[cg * Q.NL + line] += cc;
+                cg = g;
+                cc = 0;
+            }
+            ++cc;
+        } else {
+            if (g != cg) {
+                if (cg >= 0) cnt[cg * Q.NL + line] = cc;
+                cg = g;
+                cc = cnt[g * Q.NL + line];
+            }
+            const int64_t pos = cc++;
+            rec[2 * pos] = make_uint4(w[0], w[1], w[2], w[3]);
+            uint32_t *w1 = reinterpret_cast<uint32_t *>(rec + 2 * pos + 1);
+            w1[0] = w[4] | (dir < 0 ? kRecNeg : 0u) | (pos + 1 == goff[g + 1] ? kRecEnd : 0u);
+            if (pos + kRunAhead >= n_rec) w1[1] = 0u;
+            w1[2] = (uint32_t)g;
+            w1[3] = 0u;
+            if (pos >= kRunAhead) reinterpret_cast<uint32_t *>(rec + 2 * (pos - kRunAhead) + 1)[1] = code;
+            rec_rest[pos] = (int32_t)line;
+        }
+    };
+    constexpr int kAhead = 16;  // rows loaded ahead
+    for (int64_t r = row0; r < row1; r += kAhead) {
+        int32_t v[kAhead];
+#pragma unroll
+        for (int u = 0; u < kAhead; ++u) v[u] = r + u < row1 ? src[(r + u) * stride] : -1;
+#pragma unroll
+        for (int u = 0; u < kAhead; ++u) {
+            if (r + u >= row1) break;
+            const int32_t b = v[u];
+            if (b == bcur) continue;  // same interval
+            ++niv;
+            const int q = b / kRecBins;
+            bool start;
+            if (b1 < 0 || q != b1 / kRecBins) start = true;
+            else if (b2 >= 0 && b2 / kRecBins == q) start = ((b - b1) > 0) != ((b1 - b2) > 0);
+            else start = false;
+            if (start) {
+                if (rq >= 0) emit(r + u);
+                rq = q;
+                dir = 0;
+                rprev = -1;
+                st0 = st1 = st2 = st3 = -1;
+            }
+            const int j = b - q * kRecBins;
+            const int32_t rel = (int32_t)(r + u - row0);
+            st0 = j == 0 ? rel : st0;
+            st1 = j == 1 ? rel : st1;
+            st2 = j == 2 ? rel : st2;
+            st3 = j == 3 ? rel : st3;
+            if (rprev >= 0 && dir == 0) dir = b > rprev ? 1 : -1;
+            rprev = b;
+            b2 = b1;
+            b1 = b;
+            bcur = b;
+        }
+    }
+    emit(row1);
+    if (!WRITE) {
+        cnt[cg * Q.NL + line] += cc;
+        atomicAdd(n_iv, niv);
+    } else if (tid == 0) {
+        // the records past the last read as empty
+        for (int t = 0; t < 16; ++t) {
+            rec[2 * ((int64_t)n_rec + t)] = make_uint4(0u, 0u, 0u, 0u);
+            rec[2 * ((int64_t)n_rec + t) + 1] = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
 }
 
-// Sort keys past the last record sort last (bucket n_groups).
-__global__ void k_rec_pad_keys(int32_t *__restrict__ rkey, const int32_t *__restrict__ n_rec_p, int64_t N,
-                               int32_t sentinel) {
-    const int32_t n = n_rec_p[0];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        if (i >= n) rkey[i] = sentinel;
-}
-
-// Records in (part, group, line) order, each with the rest code of the record
-// four places after it (the histogram loads that factor four ahead).
-constexpr uint32_t kRecEnd = 1u << 31;  // last record of its group
-__global__ void k_rec_gather(const uint4 *__restrict__ tmp, const int32_t *__restrict__ rrest,
-                             const int32_t *__restrict__ perm, const int32_t *__restrict__ n_rec_p,
-                             const int32_t *__restrict__ goff, uint4 *__restrict__ rec, int32_t *__restrict__ rest) {
-    const int32_t n = n_rec_p[0];
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r = perm[t];
-        rec[2 * t] = tmp[2 * (int64_t)r];
-        uint4 v = tmp[2 * (int64_t)r + 1];
-        if (t + 1 == goff[v.z + 1]) v.x |= kRecEnd;
-        rec[2 * t + 1] = v;
-        rest[t] = rrest[r];
-    }
-}
-__global__ void k_rec_encode(const int32_t *__restrict__ rest, const int32_t *__restrict__ n_rec_p, int ndim,
-                             int64_t n1, uint4 *__restrict__ rec) {
-    const int32_t n = n_rec_p[0];
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t ta = t + kRunAhead;
-        uint32_t code = 0;
-        if (ta < n) {
-            const int32_t r = rest[ta];
-            code = ndim == 3 ? (uint32_t)(r / n1) | ((uint32_t)(r % n1) << 15) : (uint32_t)r;
-        }
-        rec[2 * t + 1].y = code;
-    }
+// First record of every group (n_groups + 2 entries: the last two = the
+// record count) from the scanned (group, line) counts.
+__global__ void k_rec_goff(const int32_t *__restrict__ starts, const int32_t *__restrict__ counts, int64_t Lr,
+                           int64_t NL, int n_groups, int32_t *__restrict__ goff, int32_t *__restrict__ n_rec) {
+    const int32_t total = starts[Lr - 1] + counts[Lr - 1];
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups + 2; g += gridDim.x * blockDim.x)
+        goff[g] = g < n_groups ? starts[g * NL] : total;
+    if (blockIdx.x == 0 && threadIdx.x == 0) n_rec[0] = total;
 }
 
 // Record chunks, C per part (equal record counts; records cost alike):
@@ -1223,7 +1257,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     const int64_t N = g->N;
     const int B = g->B;
     ProfScope prof("range_bins", s, 0);
-    int launches = 2;  // scale, bins
+    int launches = g->ndim == 1 ? 2 : 1;  // scale, bins
     // exact range of y (already reduced by the model kernels for built-in models)
     int blocks = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
     if (!g->range_ready) {
@@ -1234,8 +1268,10 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
         ++launches;
     }
     g->range_ready = 0;
-    k_scale<<<1, 1, 0, s>>>(g->ext, g->ydev_scale);
-    VUP_CHECK_LAUNCH();
+    if (g->ndim == 1) {
+        k_scale<<<1, 1, 0, s>>>(g->ext, g->ydev_scale);
+        VUP_CHECK_LAUNCH();
+    }
 
     // parts of each candidate layout's gathered axis for this bin count; the
     // arrays of the one layout that is built live in hl[0] (hl[1] aliases them)
@@ -1283,12 +1319,12 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
             const size_t smem = sizeof(int32_t) * (size_t)B * nw;
             if (smem > 48 * 1024)
                 VUP_CHECK_CUDA(
-                    cudaFuncSetAttribute(k_bins_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_bins_count<true><<<(unsigned)ceil_div64(n_tiles, nw), 32 * nw, smem, s>>>(g->y, N, B, g->ext, g->bins,
-                                                                                      counts, n_tiles);
+                    cudaFuncSetAttribute(k_bins_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_bins_count<<<(unsigned)ceil_div64(n_tiles, nw), 32 * nw, smem, s>>>(g->y, N, B, g->ext, g->bins,
+                                                                                counts, n_tiles);
         } else {
-            k_bins_count<false><<<(unsigned)ceil_div64(n_tiles, kSortWarps), 32 * kSortWarps, 0, s>>>(
-                g->y, N, B, g->ext, g->bins, counts, n_tiles);
+            const int bb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(N / 2, 256), (int64_t)vup_num_sms() * 8));
+            k_bins_scale<<<bb, 256, 0, s>>>(g->y, N, B, g->ext, g->bins, g->ydev_scale);
         }
         VUP_CHECK_LAUNCH();
     }
@@ -1313,7 +1349,8 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
 vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cudaEvent_t records_done) {
     const int64_t N = g->N;
     const int B = g->B;
-    ProfScope prof("layout_sort_runs", s, 0);
+    // two timed parts: up to the record-stream decision, and the key-sorted streams
+    std::unique_ptr<ProfScope> prof_rec(new ProfScope("layout_sort_records", s, 0));
     int launches = 0;
     int Bk_max = B;
     for (int l = 0; l < g->n_layouts; ++l) Bk_max = std::max(Bk_max, g->hl[l].P * B);
@@ -1341,52 +1378,51 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
             VUP_CHECK_LAUNCH();
             launches += 2;
         }
-        // sort keys of the chosen layout, stable counting sort
-        const int64_t Cn = HL.n_last, Rn = N / Cn;   // layout 0 geometry: [R][C], C = last axis
-        dim3 tg((unsigned)ceil_div64(Cn, 32), (unsigned)std::min<int64_t>(ceil_div64(Rn, 32), 65535));
-        k_layout_keys<<<tg, dim3(32, 8), 0, s>>>(g->bins, Rn, Cn, B, L, HL.keys_own);
-        VUP_CHECK_LAUNCH();
-        HL.keys = HL.keys_own;
         const int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
-        // record stream (from the keys in layout order)
+        const int64_t Cn = HL.n_last, Rn = N / Cn;  // bins as [R][C], C = the last axis
+        // record stream, walked line by line from the bins
         {
             const int GB = (int)ceil_div64(B, kRecBins);
             int P_sel = 1;
-            for (int l = 0; l < g->n_layouts; ++l) P_sel = std::max(P_sel, g->hl[l].P);
+            int64_t NL = 1, walkers = 1;
+            for (int l = 0; l < g->n_layouts; ++l) {
+                const int64_t lines = l == 0 ? Rn : Cn;
+                P_sel = std::max(P_sel, g->hl[l].P);
+                NL = std::max(NL, lines);
+                walkers = std::max(walkers, (int64_t)g->hl[l].P * lines);
+            }
             const int n_groups = P_sel * GB;  // room for either layout's parts
-            st = devbuf_reserve(g->rec_tmp, (size_t)N * (9 * sizeof(int32_t) + 2 * sizeof(uint4)));
-            if (st != VUP_OK) return st;
-            // the uint4 records first: 16-byte aligned whatever N is
-            uint4 *rtmp = (uint4 *)g->rec_tmp.p;
-            int32_t *t32 = (int32_t *)(rtmp + 2 * N);
-            int32_t *fl = t32, *ex = t32 + N, *lkey = t32 + 2 * N, *lpos = t32 + 3 * N, *rfl = t32 + 4 * N,
-                    *rex = t32 + 5 * N, *rkey = t32 + 6 * N, *rrest = t32 + 7 * N, *rperm = t32 + 8 * N;
-            if ((st = devbuf_reserve(HL.rec, sizeof(uint4) * 2 * (size_t)(N + 64))) != VUP_OK ||
+            const int64_t Lr = (int64_t)n_groups * NL;
+            if ((st = devbuf_reserve(g->rec_tmp, sizeof(int32_t) * 2 * (size_t)Lr)) != VUP_OK ||
+                (st = devbuf_reserve(g->scan_tmp, sizeof(unsigned long long) * (size_t)scan_scratch_ints(Lr))) !=
+                    VUP_OK ||
+                (st = devbuf_reserve(HL.rec, sizeof(uint4) * 2 * (size_t)(N + 64))) != VUP_OK ||
                 (st = devbuf_reserve(HL.rec_rest, sizeof(int32_t) * (size_t)(N + 64))) != VUP_OK ||
                 (st = devbuf_reserve(HL.rec_goff, sizeof(int32_t) * (size_t)(n_groups + 2))) != VUP_OK ||
                 (st = devbuf_reserve(HL.rec_gch, sizeof(int2) * (size_t)n_groups)) != VUP_OK)
                 return st;
-            k_liv_flags<<<rb, 256, 0, s>>>(HL.keys, N, L, fl);
+            scratch = (int32_t *)g->scan_tmp.p;
+            int32_t *rcnt = (int32_t *)g->rec_tmp.p, *rstart = rcnt + Lr;
+            RecGeom Q;
+            Q.R = Rn;
+            Q.C = Cn;
+            Q.B = B;
+            Q.GB = GB;
+            Q.NL = NL;
+            Q.shift = kRowShift;
+            Q.ndim = g->ndim;
+            Q.n1 = g->ndim == 3 ? g->n[1] : 1;
+            VUP_CHECK_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(int32_t) * (size_t)Lr, s));
+            VUP_CHECK_CUDA(cudaMemsetAsync(HL.n_iv, 0, sizeof(int32_t), s));
+            const unsigned wb = (unsigned)ceil_div64(walkers, 64);
+            k_rec_walk<false><<<wb, 64, 0, s>>>(g->bins, Q, L, rcnt, HL.n_iv, nullptr, nullptr, nullptr, nullptr);
             VUP_CHECK_LAUNCH();
-            if ((st = scan_exclusive(fl, ex, N, scratch, s)) != VUP_OK) return st;
-            k_liv_emit<<<rb, 256, 0, s>>>(HL.keys, N, fl, ex, lkey, lpos, HL.n_iv);
+            if ((st = scan_exclusive(rcnt, rstart, Lr, scratch, s)) != VUP_OK) return st;
+            k_rec_goff<<<(n_groups + 2 + 255) / 256, 256, 0, s>>>(rstart, rcnt, Lr, NL, n_groups,
+                                                                  (int32_t *)HL.rec_goff.p, HL.n_rec);
             VUP_CHECK_LAUNCH();
-            k_rec_flags<<<rb, 256, 0, s>>>(lkey, lpos, HL.n_iv, B, L, rfl, N);
-            VUP_CHECK_LAUNCH();
-            if ((st = scan_exclusive(rfl, rex, N, scratch, s)) != VUP_OK) return st;
-            k_rec_emit<<<rb, 256, 0, s>>>(lkey, lpos, HL.n_iv, rfl, rex, B, GB, L, kRowShift, rtmp, rkey, rrest,
-                                          HL.n_rec, N);
-            VUP_CHECK_LAUNCH();
-            k_rec_pad_keys<<<rb, 256, 0, s>>>(rkey, HL.n_rec, N, n_groups);
-            VUP_CHECK_LAUNCH();
-            st = counting_sort(g, rkey, n_groups + 1, rperm, (int32_t *)HL.rec_goff.p, counts, scratch, false, s);
-            if (st != VUP_OK) return st;
-            VUP_CHECK_CUDA(cudaMemsetAsync(HL.rec.p, 0, sizeof(uint4) * 2 * (size_t)(N + 64), s));
-            k_rec_gather<<<rb, 256, 0, s>>>(rtmp, rrest, rperm, HL.n_rec, (const int32_t *)HL.rec_goff.p,
-                                            (uint4 *)HL.rec.p, (int32_t *)HL.rec_rest.p);
-            VUP_CHECK_LAUNCH();
-            k_rec_encode<<<rb, 256, 0, s>>>((const int32_t *)HL.rec_rest.p, HL.n_rec, g->ndim,
-                                            g->ndim == 3 ? g->n[1] : 1, (uint4 *)HL.rec.p);
+            k_rec_walk<true><<<wb, 64, 0, s>>>(g->bins, Q, L, rstart, nullptr, (const int32_t *)HL.rec_goff.p,
+                                               HL.n_rec, (uint4 *)HL.rec.p, (int32_t *)HL.rec_rest.p);
             VUP_CHECK_LAUNCH();
             // chunks of records (the same count per part as the other streams' chunks / 4)
             const int Cr = g->n_chunks_rec;
@@ -1398,9 +1434,8 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
                                                                        HL.rec_chunk, L, Cr,
                                                                        (int2 *)HL.rec_gch.p);
             VUP_CHECK_LAUNCH();
-            // flags, scan, intervals, record flags, scan, records, padding, sort (count, scan,
-            // scatter, koff end), gather, codes, chunks, group chunks, gate
-            launches += 2 * scan_launches(N) + 5 + 3 + scan_launches((int64_t)(n_groups + 1) * n_tiles) + 5;
+            // count pass, scan, first records, write pass, chunks, group chunks, gate
+            launches += 2 + scan_launches(Lr) + 2 + 2 + 1;
         }
         // the key-sorted point and interval streams, unless the record stream is
         // cheaper than both (every kernel below then returns at once); the
@@ -1412,7 +1447,16 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
                                     g->hist_sel, HL.n_runs);
         VUP_CHECK_LAUNCH();
         // a caller may start the record-stream histogram from here on
+        prof_rec->launches = launches;
+        prof_rec.reset();
+        launches = 0;
         if (records_done) VUP_CHECK_CUDA(cudaEventRecord(records_done, s));
+        ProfScope prof("layout_sort_runs", s, 0);
+        // sort keys of the chosen layout in its order, stable counting sort
+        dim3 tg((unsigned)ceil_div64(Cn, 32), (unsigned)std::min<int64_t>(ceil_div64(Rn, 32), 65535));
+        k_layout_keys<<<tg, dim3(32, 8), 0, s>>>(g->bins, Rn, Cn, B, L, HL.keys_own, gate);
+        VUP_CHECK_LAUNCH();
+        HL.keys = HL.keys_own;
         st = counting_sort(g, HL.keys, Bk_max, HL.perm, HL.koff, counts, scratch, false, s, gate);
         if (st != VUP_OK) return st;
         // runs and intervals: one flag word per point, one 64-bit scan
@@ -1444,10 +1488,10 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
         // keys, sort (count, scan, scatter, koff end), flags, scan, build, encode, chunks,
         // chunk keys, key chunks, stream choice
         launches += 1 + 3 + scan_launches((int64_t)Bk_max * n_tiles) + 1 + scan_launches(N) + 2 + 4;
+        prof.launches = launches;
     }
     g->layout_valid = 1;
     g->layout_has_points = points_needed || g->ndim == 1;
-    prof.launches = launches;
     return VUP_OK;
 }
 

@@ -902,55 +902,64 @@ __device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0
     const LayoutArgs &H = A.sel[0] ? A.L1 : A.L0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int P = H.P;
-    // the chunk range of every (part, bin) key of the bin tile
+    const bool recs = !A.points_only && A.sel[1] == 2;  // record stream: every non-empty group wrote its rows
+    // the chunk range of every (part, bin) key of the bin tile; on the record
+    // stream that of the part's group of the bin
     for (int e = threadIdx.x; e < P * kFinB; e += blockDim.x) {
         const int p = e / kFinB, bb = e - p * kFinB, b = bt * kFinB + bb;
-        s_cc[p][bb] = b < A.B ? H.key_chunks[p * A.B + b] : make_int2(-1, -1);
+        s_cc[p][bb] = b >= A.B ? make_int2(-1, -1)
+                      : recs   ? H.rec_gch[p * A.GB + b / kRecBinsH]
+                               : H.key_chunks[p * A.B + b];
     }
     __syncthreads();
     const int b = bt * kFinB + warp;
-    const bool recs = !A.points_only && A.sel[1] == 2;  // record stream: every non-empty group wrote its rows
     for (int64_t kt = kt0; kt < kt0 + nkt; ++kt) {
         const int64_t k = kt * kFinK + 4 * lane;
         float4 total = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (recs) {
-            // the group (part, b / 4) of the record stream: whole in one chunk
-            // (direct row) or cut (partials of its chunks, in chunk order)
-            if (b < A.B)
-                for (int p = 0; p < P; ++p) {
-                    const int32_t gr = p * A.GB + b / kRecBinsH;
-                    const int2 cc = H.rec_gch[gr];
+        if (b < A.B) {
+            // four parts at a time: their direct rows in flight together, then
+            // added in part order (cut keys from their chunks' partials)
+            for (int p0 = 0; p0 < P; p0 += 4) {
+                float4 v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int p = p0 + q;
+                    v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (p < P) {
+                        const int2 cc = s_cc[p][warp];
+                        if (cc.x >= 0 && cc.x == cc.y)
+                            v[q] = *reinterpret_cast<const float4 *>(A.direct + ((int64_t)p * A.B + b) * A.K_pad + k);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int p = p0 + q;
+                    if (p >= P) break;
+                    const int2 cc = s_cc[p][warp];
                     if (cc.x < 0) continue;
                     if (cc.x == cc.y) {
-                        add4(total, *reinterpret_cast<const float4 *>(A.direct + ((int64_t)p * A.B + b) * A.K_pad + k));
+                        add4(total, v[q]);
                         continue;
                     }
                     float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-                    for (int c = cc.x; c <= cc.y; ++c) {
-                        if (H.rec_chunk[c] >= H.rec_chunk[c + 1]) continue;
-                        const int side = H.rec_chunk_grp[2 * c] == gr ? 0 : 1;
-                        add4(sum, *reinterpret_cast<const float4 *>(A.part + (((int64_t)c * 2 + side) * 4 + b % kRecBinsH) *
-                                                                                 A.K_pad + k));
+                    if (recs) {
+                        const int32_t gr = p * A.GB + b / kRecBinsH;
+                        for (int c = cc.x; c <= cc.y; ++c) {
+                            if (H.rec_chunk[c] >= H.rec_chunk[c + 1]) continue;
+                            const int side = H.rec_chunk_grp[2 * c] == gr ? 0 : 1;
+                            add4(sum, *reinterpret_cast<const float4 *>(
+                                          A.part + (((int64_t)c * 2 + side) * 4 + b % kRecBinsH) * A.K_pad + k));
+                        }
+                    } else {
+                        const int32_t key = p * A.B + b;
+                        for (int c = cc.x; c <= cc.y; ++c) {
+                            if (H.chunk_pt[c] >= H.chunk_pt[c + 1]) continue;
+                            const int side = H.chunk_bin[2 * c] == key ? 0 : 1;
+                            add4(sum, *reinterpret_cast<const float4 *>(A.part + ((int64_t)c * 2 + side) * A.K_pad + k));
+                        }
                     }
                     add4(total, sum);
                 }
-        } else if (b < A.B) {
-#pragma unroll 4
-            for (int p = 0; p < P; ++p) {
-                const int2 cc = s_cc[p][warp];
-                const int32_t key = p * A.B + b;
-                if (cc.x < 0) continue;
-                    if (cc.x == cc.y) {
-                    add4(total, *reinterpret_cast<const float4 *>(A.direct + (int64_t)key * A.K_pad + k));
-                    continue;
-                }
-                float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int c = cc.x; c <= cc.y; ++c) {
-                    if (H.chunk_pt[c] >= H.chunk_pt[c + 1]) continue;
-                    const int side = H.chunk_bin[2 * c] == key ? 0 : 1;
-                    add4(sum, *reinterpret_cast<const float4 *>(A.part + ((int64_t)c * 2 + side) * A.K_pad + k));
-                }
-                add4(total, sum);
             }
         }
         float *row = tile[warp] + 4 * lane;
@@ -969,10 +978,10 @@ __device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0
     }
 }
 
-__global__ void k_hist_finish(const __grid_constant__ HistArgs A) { hist_finish_tiles(A, blockIdx.x, 1, blockIdx.y); }
+__global__ void __launch_bounds__(256, 5) k_hist_finish(const __grid_constant__ HistArgs A) { hist_finish_tiles(A, blockIdx.x, 1, blockIdx.y); }
 
 // Batched finish: items[i] = (instance, density tile, bin tile).
-__global__ void k_hist_finish_batched(const HistArgs *__restrict__ insts, const int4 *__restrict__ items) {
+__global__ void __launch_bounds__(256, 5) k_hist_finish_batched(const HistArgs *__restrict__ insts, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
     hist_finish_tiles(insts[it.x], it.y, 1, it.z);
 }

@@ -28,7 +28,7 @@ ABI_SYMBOLS = [
     "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_batched_report", "vup_sync", "vup_selftest_wait", "vup_model_at",
     "vup_deviation_moments", "vup_ipsa_matrix", "vup_sa_fields", "vup_posterior_means",
     "vup_grid_info", "vup_set_hist_stream", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
-    "vup_profile_read",
+    "vup_profile_read", "vup_profile_timeline",
 ]
 
 
@@ -85,6 +85,7 @@ def lib():
         l.vup_grid_copy.argtypes = [vp, C.c_int, vp, C.c_size_t, vp]
         l.vup_profile.argtypes = [C.c_int]
         l.vup_profile_read.argtypes = [C.c_char_p, C.c_size_t]
+        l.vup_profile_timeline.argtypes = [C.c_char_p, C.c_size_t]
         for f in ABI_SYMBOLS:
             if f not in ("vup_status_string", "vup_version"):
                 getattr(l, f).restype = C.c_int
@@ -290,6 +291,15 @@ def vup_profile_read() -> dict:
     buf = C.create_string_buffer(1 << 16)
     _check(lib().vup_profile_read(buf, len(buf)), "vup_profile_read")
     return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
+
+
+def vup_profile_timeline() -> list:
+    """[(kernel group, stream number, launches, begin_ms, end_ms)] in launch
+    order, relative to the first record, since vup_profile(True)."""
+    import json
+    buf = C.create_string_buffer(1 << 22)
+    _check(lib().vup_profile_timeline(buf, len(buf)), "vup_profile_timeline")
+    return [(str(n), int(s), int(l), float(a), float(b)) for n, s, l, a, b in json.loads(buf.value.decode())]
 
 
 # ------------------------------------------------------ torch-facing helpers
