@@ -483,8 +483,8 @@ vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa, bool tf32)
     if (nd >= 2) {
         const int64_t nct = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles(g->orient[vup_tc_orient(g)]));
         if ((st = devbuf_reserve(g->partials, sizeof(float) * 4 * K_pad * nct)) != VUP_OK) return st;
-        // partial rows of cut keys (2 per chunk) or cut record groups (2 x 4 per record chunk)
-        const size_t part_rows = std::max<size_t>(2 * (size_t)g->n_chunks, 8 * (size_t)g->n_chunks_rec);
+        // partial rows of cut keys (2 per chunk) or cut record groups (2 x 8 bins per record chunk)
+        const size_t part_rows = std::max<size_t>(2 * (size_t)g->n_chunks, 16 * (size_t)g->n_chunks_rec);
         if ((st = devbuf_reserve(g->hist_part, sizeof(float) * part_rows * K_pad * g->hist_P)) != VUP_OK)
             return st;
         if ((st = devbuf_reserve(g->hist_direct, sizeof(float) * (size_t)g->hist_P * g->B * K_pad)) != VUP_OK)

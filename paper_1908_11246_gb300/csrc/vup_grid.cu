@@ -473,7 +473,7 @@ __global__ void k_layout_keys(const int32_t *__restrict__ bins, int64_t R, int64
 __global__ void k_need_keys(const int32_t *n_rec, const int32_t *n_iv, int64_t N, int nf, int force,
                             int force_keys, int32_t *sel, int32_t *n_runs) {
     const int64_t c_iv = 19 * (int64_t)n_iv[0];
-    const int64_t c_rec = (40 + 6 * nf) * (int64_t)n_rec[0];
+    const int64_t c_rec = (16 + 6 * nf) * (int64_t)n_rec[0] + 6 * ((int64_t)n_iv[0] + 2 * (int64_t)n_rec[0]);
     const int need = force_keys || force == 0 || force == 1 || (force < 0 && !(c_rec < 4 * N && c_rec <= c_iv));
     sel[4] = need;
     sel[1] = need ? -1 : 2;
@@ -484,8 +484,10 @@ __global__ void k_need_keys(const int32_t *n_rec, const int32_t *n_iv, int64_t N
 // (fitted to measured launches on 2-D and 3-D grids): point stream 4 per
 // point (one gather) + 20 per run (rest-factor pipeline); interval stream 19
 // per interval (two gathers, a difference, a rest-factor load); record stream
-// 40 + 6 per extra rest axis per record (five gathers, four differences, one
-// rest-factor load per rest axis).  After the key sort: the point or the
+// 16 + 6 per extra rest axis per record (record words, one rest-factor load
+// per rest axis, the group flushes) + 6 per prefix-sum gather (a record gathers
+// 1 + 4 per half-group holding a bin: about m + 2 for m bins, m summing to the
+// interval count).  After the key sort: the point or the
 // interval stream, whichever costs less (unless forced), when the record
 // stream was not chosen before it.
 __global__ void k_pick_stream(const int32_t *n_runs, const int32_t *n_iv, int64_t N, int force, int32_t *sel) {
@@ -778,16 +780,17 @@ __global__ void k_key_chunks(const int32_t *__restrict__ koff, LaySel L, int B, 
 // A record is a stretch of one line (every axis but the gathered one fixed)
 // inside one part whose points fall in one group of kRecBins consecutive bins
 // and whose bins change monotonically along the gathered axis.  Each bin of
-// the group then holds one sub-range of the stretch, and five boundaries
-// B_0..B_4 describe them all: bin 4q + j holds rows [B_j, B_j+1) when the
+// the group then holds one sub-range of the stretch, and nine boundaries
+// B_0..B_8 describe them all: bin 8q + j holds rows [B_j, B_j+1) when the
 // bins rise along the line, [B_j+1, B_j) when they fall (the record's sign),
-// an empty range when absent.  The histogram adds sign f_rest (P[B_j+1] -
-// P[B_j]) to each of the four bins from five prefix-sum gathers and one
-// rest-factor load, where the interval stream needs two gathers and a load per
-// bin.  Records come from the intervals in line order (maximal stretches of
-// one key along a line): a record starts at a line-part start, a group change,
-// or where the bin steps change sign inside a group.
-constexpr int kRecBins = 4;
+// an empty range (B_j+1 = B_j) when absent.  The histogram adds sign f_rest
+// (P[B_j+1] - P[B_j]) to each bin present: m + 1 prefix-sum gathers and one
+// rest-factor load for a record over m bins, where the interval stream needs
+// two gathers and a load per bin.  Records come from the intervals in line
+// order (maximal stretches of one key along a line): a record starts at a
+// line-part start, a group change, or where the bin steps change sign inside
+// a group.
+constexpr int kRecBins = 8;
 constexpr uint32_t kRecNeg = 1u << 30;  // bins fall along the line
 
 constexpr uint32_t kRecEnd = 1u << 31;  // last record of its group
@@ -801,15 +804,14 @@ constexpr uint32_t kRecEnd = 1u << 31;  // last record of its group
 // every (group, line) into cnt[group * NL + line] and adds the intervals to
 // n_iv; after an exclusive scan of those counts, PASS 2 (WRITE = true) takes
 // cnt as cursors and writes each record at its place in (group, line, row)
-// order: words (B_0..B_3 as row byte offsets inside the part's tile) and (B_4 |
-// sign | group end, rest code of the record kRunAhead places later, group, 0),
-// and its rest index (the line).  bins is viewed as [R][C], C the last axis;
-// layout 1 (2-D) walks the columns.
+// order: words (B_0 | B_1 << 16, .., B_6 | B_7 << 16, rows inside the part) and
+// (B_8 | sign | group end, rest code of the record kRunAhead places later,
+// group, 0), and its rest index (the line).  bins is viewed as [R][C], C the
+// last axis; layout 1 (2-D) walks the columns.
 struct RecGeom {
     int64_t R, C;
     int B, GB;
     int64_t NL;   // line stride of the count matrix (the most lines of either layout)
-    int shift;    // row byte shift of the histogram's prefix tile
     int ndim;
     int64_t n1;   // 3-D rest code: line = a0 n1 + a1 -> a0 | a1 << 15
 };
@@ -835,12 +837,13 @@ __global__ void __launch_bounds__(64) k_rec_walk(const int32_t *__restrict__ bin
 
     int32_t bcur = -1, b1 = -1, b2 = -1;  // bins of the current interval and of the two before it
     int rq = -1, dir = 0, rprev = -1;     // open record: group in the part, step sign, last bin
-    int32_t st0 = -1, st1 = -1, st2 = -1, st3 = -1;  // its bins' first rows (relative to row0)
+    int32_t st[kRecBins];  // its bins' first rows (relative to row0), -1 if absent
+#pragma unroll
+    for (int j = 0; j < kRecBins; ++j) st[j] = -1;
     int32_t niv = 0;
     int32_t cg = -1, cc = 0;  // (group, count) run of pass 1; (group, cursor) of pass 2
     auto emit = [&](int64_t e_row) {
         const int32_t e = (int32_t)(e_row - row0);
-        const int32_t st[kRecBins] = {st0, st1, st2, st3};
         uint32_t w[kRecBins + 1];
 #pragma unroll
         for (int j = 0; j <= kRecBins; ++j) {
@@ -850,7 +853,7 @@ __global__ void __launch_bounds__(64) k_rec_walk(const int32_t *__restrict__ bin
                 const bool take = dir >= 0 ? jj >= j : jj < j;
                 if (take && st[jj] >= 0 && st[jj] < v) v = st[jj];
             }
-            w[j] = (uint32_t)v << Q.shift;
+            w[j] = (uint32_t)v;
         }
         const int32_t g = p * Q.GB + rq;
         if (!WRITE) {
@@ -867,9 +870,9 @@ __global__ void __launch_bounds__(64) k_rec_walk(const int32_t *__restrict__ bin
                 cc = cnt[g * Q.NL + line];
             }
             const int64_t pos = cc++;
-            rec[2 * pos] = make_uint4(w[0], w[1], w[2], w[3]);
+            rec[2 * pos] = make_uint4(w[0] | w[1] << 16, w[2] | w[3] << 16, w[4] | w[5] << 16, w[6] | w[7] << 16);
             uint32_t *w1 = reinterpret_cast<uint32_t *>(rec + 2 * pos + 1);
-            w1[0] = w[4] | (dir < 0 ? kRecNeg : 0u) | (pos + 1 == goff[g + 1] ? kRecEnd : 0u);
+            w1[0] = w[8] | (dir < 0 ? kRecNeg : 0u) | (pos + 1 == goff[g + 1] ? kRecEnd : 0u);
             if (pos + kRunAhead >= n_rec) w1[1] = 0u;
             w1[2] = (uint32_t)g;
             w1[3] = 0u;
@@ -898,14 +901,13 @@ __global__ void __launch_bounds__(64) k_rec_walk(const int32_t *__restrict__ bin
                 rq = q;
                 dir = 0;
                 rprev = -1;
-                st0 = st1 = st2 = st3 = -1;
+#pragma unroll
+                for (int jj = 0; jj < kRecBins; ++jj) st[jj] = -1;
             }
             const int j = b - q * kRecBins;
             const int32_t rel = (int32_t)(r + u - row0);
-            st0 = j == 0 ? rel : st0;
-            st1 = j == 1 ? rel : st1;
-            st2 = j == 2 ? rel : st2;
-            st3 = j == 3 ? rel : st3;
+#pragma unroll
+            for (int jj = 0; jj < kRecBins; ++jj) st[jj] = j == jj ? rel : st[jj];
             if (rprev >= 0 && dir == 0) dir = b > rprev ? 1 : -1;
             rprev = b;
             b2 = b1;
@@ -1079,35 +1081,50 @@ __global__ void k_power_table(const double *__restrict__ y, int64_t P, int64_t S
 // the 2^-17 relative resolution of the hi + lo pair.  FP64 stays on the
 // per-element path only for that one product (FP64 is the slow pipe here).
 // Modes 0 and 2 of k_power_table.
-__global__ void k_power_table_bf16(const double *__restrict__ y, int64_t P, int64_t S,
-                                   const double *__restrict__ sc, int mode, int64_t ld,
-                                   __nv_bfloat16 *__restrict__ out, __nv_bfloat16 *__restrict__ out2) {
-    __shared__ float tile[32][33];
-    const int64_t p0 = (int64_t)blockIdx.y * 32, s0 = (int64_t)blockIdx.x * 32;
+// Split BF16 power table of the tensor-core contraction, [rest * 4 + j][red]
+// with row stride ld: element (rest, red) of y (y[rest * Rn + red] when
+// REST_ROWS, else y[red * Qn + rest]) yields z = y / s_scale and z^(j+1),
+// j = 0..3, each split into BF16 hi + lo.  The grid covers the padded table
+// (rests up to Qext, reds up to ld, both multiples of 64) and writes zeros
+// there.  A 32 (rest) x 64 (red) tile of z goes through shared memory; each
+// thread stores two consecutive reds (4 bytes) per row.
+template <bool REST_ROWS>
+__global__ void k_power_table_bf16(const double *__restrict__ y, int64_t Qn, int64_t Rn, int64_t Qext,
+                                   const double *__restrict__ sc, int64_t ld, __nv_bfloat16 *__restrict__ out,
+                                   __nv_bfloat16 *__restrict__ out2) {
+    __shared__ float tile[32][65];
+    const int64_t q0 = (int64_t)blockIdx.y * 32, r0 = (int64_t)blockIdx.x * 64;
     const double inv = 1.0 / sc[0];
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int64_t p = p0 + r, s = s0 + threadIdx.x;
-        tile[r][threadIdx.x] = (p < P && s < S) ? (float)__dmul_rn(y[p * S + s], inv) : 0.f;
+    for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+        int lq, lr;
+        if (REST_ROWS) {
+            lq = e >> 6;
+            lr = e & 63;
+        } else {
+            lq = e & 31;
+            lr = e >> 5;
+        }
+        const int64_t q = q0 + lq, r = r0 + lr;
+        float z = 0.f;
+        if (q < Qn && r < Rn) z = (float)__dmul_rn(y[REST_ROWS ? q * Rn + r : r * Qn + q], inv);
+        tile[lq][lr] = z;
     }
     __syncthreads();
-    const int tid = threadIdx.y * 32 + threadIdx.x, nthr = 32 * blockDim.y;
-    for (int e = tid; e < 32 * 32 * 4; e += nthr) {
-        int lp, ls, j;
-        int64_t idx;
-        if (mode == 0) {  // rows (p, j), cols s
-            ls = e & 31; j = (e >> 5) & 3; lp = e >> 7;
-            idx = ((p0 + lp) * 4 + j) * ld + (s0 + ls);
-        } else {          // rows (s, j), cols p
-            lp = e & 31; j = (e >> 5) & 3; ls = e >> 7;
-            idx = ((s0 + ls) * 4 + j) * ld + (p0 + lp);
+    for (int e = threadIdx.x; e < 32 * 4 * 32; e += blockDim.x) {
+        const int pr = e & 31, j = (e >> 5) & 3, lq = e >> 7;
+        const int64_t q = q0 + lq, r = r0 + 2 * pr;
+        if (q >= Qext) continue;
+        const float z0 = tile[lq][2 * pr], z1 = tile[lq][2 * pr + 1];
+        float v0 = z0, v1 = z1;
+        for (int t = 0; t < j; ++t) {
+            v0 *= z0;
+            v1 *= z1;
         }
-        if (p0 + lp >= P || s0 + ls >= S) continue;
-        const float z = tile[lp][ls];
-        float v = z;
-        for (int q = 0; q < j; ++q) v *= z;
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        out[idx] = h;
-        out2[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+        const int64_t idx = (q * 4 + j) * ld + r;
+        *reinterpret_cast<__nv_bfloat162 *>(out + idx) = __halves2bfloat162(h0, h1);
+        *reinterpret_cast<__nv_bfloat162 *>(out2 + idx) = __halves2bfloat162(
+            __float2bfloat16_rn(v0 - __bfloat162float(h0)), __float2bfloat16_rn(v1 - __bfloat162float(h1)));
     }
 }
 
@@ -1409,7 +1426,6 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
             Q.B = B;
             Q.GB = GB;
             Q.NL = NL;
-            Q.shift = kRowShift;
             Q.ndim = g->ndim;
             Q.n1 = g->ndim == 3 ? g->n[1] : 1;
             VUP_CHECK_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(int32_t) * (size_t)Lr, s));
@@ -1550,11 +1566,16 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
             VUP_CHECK_CUDA(cudaMalloc(&g->zt_hi[orient], bytes));
             VUP_CHECK_CUDA(cudaMalloc(&g->zt_lo[orient], bytes));
         }
-        VUP_CHECK_CUDA(cudaMemsetAsync(g->zt_hi[orient], 0, bytes, s));
-        VUP_CHECK_CUDA(cudaMemsetAsync(g->zt_lo[orient], 0, bytes, s));
-        // tensor wants [q*4+j][r]: orientation 0 -> rows (p, j) (mode 0); 1 -> rows (s, j) (mode 2)
-        k_power_table_bf16<<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, first ? 2 : 0, ld, g->zt_hi[orient],
-                                               g->zt_lo[orient]);
+        // tensor wants [q*4+j][r], padding included: y is [Q][R] (orientations 0
+        // and 2) or [R][Q] (orientation 1)
+        const int64_t Qext = rows / 4;
+        dim3 pg((unsigned)(ld / 64), (unsigned)(Qext / 32));
+        if (first)
+            k_power_table_bf16<false><<<pg, 256, 0, s>>>(g->y, o.Q, o.R, Qext, g->ydev_scale, ld, g->zt_hi[orient],
+                                                         g->zt_lo[orient]);
+        else
+            k_power_table_bf16<true><<<pg, 256, 0, s>>>(g->y, o.Q, o.R, Qext, g->ydev_scale, ld, g->zt_hi[orient],
+                                                        g->zt_lo[orient]);
         VUP_CHECK_LAUNCH();
     }
     g->have_tab[orient][bf16] = 1;

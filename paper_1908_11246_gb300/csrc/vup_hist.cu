@@ -39,7 +39,7 @@ constexpr uint32_t kRunEnd = 1u << 30, kBinEnd = 1u << 31;
 constexpr uint32_t kFlags = kRunEnd | kBinEnd;
 constexpr uint32_t kSpin = 1u << 26;
 constexpr int kPF = 16;                      // runs prefetched per block (global fallback)
-constexpr int kRecBinsH = 4;                 // bins per record group (the layout builder's kRecBins)
+constexpr int kRecBinsH = 8;                 // bins per record group (the layout builder's kRecBins)
 
 struct LayoutArgs {
     const uint32_t *hpt;
@@ -128,7 +128,7 @@ __host__ __device__ inline size_t hist_warp_bytes() { return (size_t)2 * kWin * 
 // rest-factor table stays in L2, slower when its rows come from HBM and more
 // warps hide the latency).  The others run 20 warps of 96 registers.  Each
 // fills the register file of the one CTA per SM that the tile allows.
-__host__ __device__ constexpr int hist_warps(int mode) { return mode == 3 ? 16 : kHistWarps; }
+__host__ __device__ constexpr int hist_warps(int mode) { return mode >= 2 ? 16 : kHistWarps; }
 __host__ __device__ constexpr int hist_stream_of(int mode) { return mode == 3 ? 2 : mode; }
 __host__ __device__ inline size_t hist_smem_bytes(int64_t rows, int warps = kHistWarps) {
     return hist_tile_bytes(rows) + warps * hist_warp_bytes() + warps * 2 * sizeof(uint64_t);
@@ -343,27 +343,28 @@ __device__ __forceinline__ bool iv_chunk(const ItemCtx &X, int c, int p, int64_t
 }
 
 // Record stream, chunk c of part p: record t adds s_t f_t (P[B_j+1] - P[B_j])
-// to bin 4q + j for j = 0..3 (five prefix-sum gathers, one rest-factor load
-// four records ahead, s_t its sign); a group's four sums are stored when its
-// last record passes (groups cut by the chunk bounds -- only its first and
-// last -- go to the chunk's partial rows, as keys do on the other streams).
+// to bin 8q + j, j = 0..7: a gather of P[B_0] and four more for each half of
+// the group that holds a bin, one rest-factor load four records ahead, s_t
+// its sign; a group's eight sums are stored when its last record passes (groups
+// cut by the chunk bounds -- only its first and last -- go to the chunk's
+// partial rows, as keys do on the other streams).
 constexpr uint32_t kRecNegFlag = 1u << 30;
 constexpr uint32_t kRecEndFlag = 1u << 31;
-constexpr uint32_t kRecOffMask = (1u << 18) - 1u;
 
-// Store a record group's four sums (a lane's four densities each): whole
+// Store a record group's eight sums (a lane's four densities each): whole
 // groups to their direct rows, cut ones to the chunk's partial rows (side 0:
 // its first group).  Out of line, like flush_key: it runs once per group.
 __device__ __noinline__ void flush_group(const ItemCtx *X, int c, int p, int64_t k, int32_t gr, bool shared,
-                                         bool first, float4 a0, float4 a1, float4 a2, float4 a3) {
+                                         bool first, float4 a0, float4 a1, float4 a2, float4 a3, float4 a4,
+                                         float4 a5, float4 a6, float4 a7) {
     const int b0 = (gr - p * X->GB) * kRecBinsH;
     const int64_t K_pad = X->K_pad;
-    float *row = shared ? X->part + ((int64_t)c * 2 + (first ? 0 : 1)) * 4 * K_pad + k
+    float *row = shared ? X->part + ((int64_t)c * 2 + (first ? 0 : 1)) * kRecBinsH * K_pad + k
                         : X->direct + ((int64_t)p * X->B + b0) * K_pad + k;
-    *reinterpret_cast<float4 *>(row) = a0;
-    if (shared || b0 + 1 < X->B) *reinterpret_cast<float4 *>(row + K_pad) = a1;
-    if (shared || b0 + 2 < X->B) *reinterpret_cast<float4 *>(row + 2 * K_pad) = a2;
-    if (shared || b0 + 3 < X->B) *reinterpret_cast<float4 *>(row + 3 * K_pad) = a3;
+    const float4 a[kRecBinsH] = {a0, a1, a2, a3, a4, a5, a6, a7};
+#pragma unroll
+    for (int j = 0; j < kRecBinsH; ++j)
+        if (shared || b0 + j < X->B) *reinterpret_cast<float4 *>(row + j * K_pad) = a[j];
 }
 template <int NF>
 __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, int64_t k, const float *ws,
@@ -413,12 +414,16 @@ __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, i
     };
     float4 f0 = first_factor(rb), f1 = first_factor(rb + 1), f2 = first_factor(rb + 2), f3 = first_factor(rb + 3);
 
-    float4 acc0 = zero4, acc1 = zero4, acc2 = zero4, acc3 = zero4;
-    // a group's four sums: whole groups to their direct rows, cut ones to the chunk's partials
+    float4 acc[kRecBinsH];
+#pragma unroll
+    for (int j = 0; j < kRecBinsH; ++j) acc[j] = zero4;
+    // a group's eight sums: whole groups to their direct rows, cut ones to the chunk's partials
     auto flush = [&](int32_t gr) {
         const bool first = gr == first_grp;
-        flush_group(&X, c, p, k, gr, first ? sh_first : (gr == last_grp && sh_last), first, acc0, acc1, acc2, acc3);
-        acc0 = acc1 = acc2 = acc3 = zero4;
+        flush_group(&X, c, p, k, gr, first ? sh_first : (gr == last_grp && sh_last), first, acc[0], acc[1], acc[2],
+                    acc[3], acc[4], acc[5], acc[6], acc[7]);
+#pragma unroll
+        for (int j = 0; j < kRecBinsH; ++j) acc[j] = zero4;
     };
     const uint32_t wsl = smem_u32(ws) + lane * 16;
     auto gather = [&](uint32_t addr) -> float4 {
@@ -429,13 +434,25 @@ __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, i
     };
     auto sub4 = [](float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); };
     auto step = [&](const uint4 u, const uint4 v, float4 &f) {
-        const float4 p0 = gather(wsl + u.x), p1 = gather(wsl + u.y), p2 = gather(wsl + u.z),
-                     p3 = gather(wsl + u.w), p4 = gather(wsl + (v.x & kRecOffMask));
+        // boundary rows B_0..B_8 (16 bits each); bins with B_j+1 == B_j are absent
+        const uint32_t rw[kRecBinsH + 1] = {u.x & 0xffffu, u.x >> 16, u.y & 0xffffu, u.y >> 16, u.z & 0xffffu,
+                                            u.z >> 16,     u.w & 0xffffu, u.w >> 16, v.x & 0xffffu};
         const float4 fs = (v.x & kRecNegFlag) ? make_float4(-f.x, -f.y, -f.z, -f.w) : f;
-        fma4(acc0, fs, sub4(p1, p0));
-        fma4(acc1, fs, sub4(p2, p1));
-        fma4(acc2, fs, sub4(p3, p2));
-        fma4(acc3, fs, sub4(p4, p3));
+        // each half of the group is skipped when it holds no bin (its
+        // boundaries then all equal its first)
+        float4 prev = gather(wsl + (rw[0] << kRowShift));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            constexpr int kH = kRecBinsH / 2;
+            if (rw[kH * h + kH] != rw[kH * h]) {
+#pragma unroll
+                for (int j = kH * h; j < kH * h + kH; ++j) {
+                    const float4 nx = gather(wsl + (rw[j + 1] << kRowShift));
+                    fma4(acc[j], fs, sub4(nx, prev));
+                    prev = nx;
+                }
+            }
+        }
         f = coded_factor(v.y);
         if (__builtin_expect((v.x & kRecEndFlag) != 0, 0)) flush((int32_t)v.z);
     };
@@ -948,7 +965,7 @@ __device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0
                             if (H.rec_chunk[c] >= H.rec_chunk[c + 1]) continue;
                             const int side = H.rec_chunk_grp[2 * c] == gr ? 0 : 1;
                             add4(sum, *reinterpret_cast<const float4 *>(
-                                          A.part + (((int64_t)c * 2 + side) * 4 + b % kRecBinsH) * A.K_pad + k));
+                                          A.part + (((int64_t)c * 2 + side) * kRecBinsH + b % kRecBinsH) * A.K_pad + k));
                         }
                     } else {
                         const int32_t key = p * A.B + b;

@@ -2,7 +2,8 @@
 
 The interval stream sums each stretch of one bin along the gathered axis as a
 difference of prefix sums of the factor tile; the record stream does the same
-for four consecutive bins of one line at once (five prefix sums); the point
+for up to eight consecutive bins of one line at once (one prefix sum more
+than the bins present); the point
 stream adds every point.  Each is forced in turn on every case and must meet
 the histogram tolerance (1e-6 absolute per bin).  The run, interval and record
 counts the device reports are checked exactly against counts from its bins.
@@ -71,7 +72,7 @@ def layout_counts(bins_nd, B, layout):
     return int(new_run.sum()), int(new_iv.sum()), record_count(b.ravel(), n_last, pr, B)
 
 
-def record_count(bins_lines, n_last, pr, B, G=4):
+def record_count(bins_lines, n_last, pr, B, G=8):
     """Records of the record stream: the intervals of every line in line order
     (maximal stretches of one (part, bin) key), grouped while the line, the
     part and the group of G bins stay the same and the bin steps keep their
@@ -140,7 +141,7 @@ def test_point_and_interval_streams_match_oracle(prob):
 @pytest.mark.parametrize("name,expect", [("c2", (1, 2)), ("c3", (0, 0)), ("c4", (1, 2))])
 def test_automatic_choice_takes_the_cheaper_stream(name, expect):
     """Full-size workloads.  c2 / c4: gathering axis 0 gives runs of ~9 / ~18
-    points in ~1.07 intervals each and ~3.5 intervals per record, so layout
+    points in ~1.07 intervals each and ~6 intervals per record, so layout
     1's record stream is cheapest.  c3 (3-D): intervals average 1.8 points and
     records 1.6 intervals, so the point stream is."""
     prob = I.config(name)
