@@ -229,6 +229,10 @@ static void free_grid(vup_grid g) {
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
     if (g->ev_rec) cudaEventDestroy(g->ev_rec);
+    if (g->ev_lay) cudaEventDestroy(g->ev_lay);
+    if (g->ev_dens) cudaEventDestroy(g->ev_dens);
+    if (g->ev_pre) cudaEventDestroy(g->ev_pre);
+    if (g->side2) cudaStreamDestroy(g->side2);
     cudaFree(g->ydev_scale);
     cudaFree(g->dstatus);
     for (int o = 0; o < kNumOrient; ++o) {
@@ -251,6 +255,7 @@ static void free_grid(vup_grid g) {
     devbuf_free(g->partials);
     devbuf_free(g->hist_part);
     devbuf_free(g->hist_direct);
+    devbuf_free(g->hist_prefix);
     devbuf_free(g->ipsa_part);
     devbuf_free(g->atf_hi);
     devbuf_free(g->atf_lo);
@@ -489,6 +494,12 @@ vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa, bool tf32)
             return st;
         if ((st = devbuf_reserve(g->hist_direct, sizeof(float) * (size_t)g->hist_P * g->B * K_pad)) != VUP_OK)
             return st;
+        {
+            int64_t rows = 1;
+            for (int l = 0; l < g->n_layouts; ++l) rows = std::max(rows, g->hl[l].part_rows);
+            if ((st = devbuf_reserve(g->hist_prefix, sizeof(float) * (size_t)g->hist_P * K_pad * (rows + 1))) != VUP_OK)
+                return st;
+        }
         if (tf32) {
             const size_t a = (size_t)K_pad * g->orient[vup_tc_orient(g)].R_pad;
             if ((st = devbuf_reserve(g->atf_hi, sizeof(float) * a)) != VUP_OK) return st;
@@ -543,10 +554,11 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
             VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
             VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
             VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_rec, cudaEventDisableTiming));
+            VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_lay, cudaEventDisableTiming));
         }
         VUP_CHECK_CUDA(cudaEventRecord(g->ev_fork, s));
         VUP_CHECK_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
-        vup_status lst = vup_build_layout(g, g->side, false, g->ev_rec);
+        vup_status lst = vup_build_layout(g, g->side, false, g->ev_rec, g->ev_lay);
         VUP_CHECK_CUDA(cudaEventRecord(g->ev_join, g->side));
         forked = true;
         if (lst != VUP_OK) {
@@ -568,6 +580,21 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
                       VUP_OK)
         return st;
     if ((st = vup_density_prep(g, d, ((bf16 || tf32) && want_m) ? (1 << to) : 0, s, tf32)) != VUP_OK) return st;
+    // the histogram's prefix-sum tiles on a third stream, beside the
+    // contraction (they need the densities and the layout choice only)
+    bool prefix_ready = false;
+    if (hist && forked && want_m) {
+        if (!g->side2) {
+            VUP_CHECK_CUDA(cudaStreamCreateWithFlags(&g->side2, cudaStreamNonBlocking));
+            VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_dens, cudaEventDisableTiming));
+            VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_pre, cudaEventDisableTiming));
+        }
+        VUP_CHECK_CUDA(cudaEventRecord(g->ev_dens, s));
+        VUP_CHECK_CUDA(cudaStreamWaitEvent(g->side2, g->ev_dens, 0));
+        VUP_CHECK_CUDA(cudaStreamWaitEvent(g->side2, g->ev_lay, 0));
+        prefix_ready = vup_hist_prefix(g, K, g->side2);
+        VUP_CHECK_CUDA(cudaEventRecord(g->ev_pre, g->side2));
+    }
     if (want_m) {
         int64_t nct;
         if (bf16 || tf32) {
@@ -585,7 +612,10 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
         // the record-stream histogram waits for the records only; the other
         // streams' kernels (and the finish) for the whole layout
         if (forked) VUP_CHECK_CUDA(cudaStreamWaitEvent(s, g->ev_rec, 0));
-        if ((st = vup_hist_fused(g, K, hist, s, nullptr, false, forked ? g->ev_join : nullptr)) != VUP_OK) return st;
+        if (prefix_ready) VUP_CHECK_CUDA(cudaStreamWaitEvent(s, g->ev_pre, 0));
+        if ((st = vup_hist_fused(g, K, hist, s, nullptr, false, forked ? g->ev_join : nullptr, prefix_ready)) !=
+            VUP_OK)
+            return st;
         join.on = false;
     }
     return VUP_OK;

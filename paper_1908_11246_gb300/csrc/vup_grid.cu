@@ -1363,7 +1363,8 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
 // streams, chunks, the natural bin offsets) for the current bins.  Built on
 // first use after a model evaluation (the histogram, the bin offsets), so a
 // caller may run it on a second stream beside the density preparation.
-vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cudaEvent_t records_done) {
+vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cudaEvent_t records_done,
+                            cudaEvent_t layout_picked) {
     const int64_t N = g->N;
     const int B = g->B;
     // two timed parts: up to the record-stream decision, and the key-sorted streams
@@ -1395,6 +1396,7 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
             VUP_CHECK_LAUNCH();
             launches += 2;
         }
+        if (layout_picked) VUP_CHECK_CUDA(cudaEventRecord(layout_picked, s));
         const int rb = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
         const int64_t Cn = HL.n_last, Rn = N / Cn;  // bins as [R][C], C = the last axis
         // record stream, walked line by line from the bins

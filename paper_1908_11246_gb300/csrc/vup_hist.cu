@@ -77,6 +77,8 @@ struct HistArgs {
     float *hist;          // [K][B]
     float *part;          // [P * C][2][K_pad]
     float *direct;        // [P][K][B] (P > 1)
+    const float *prefix;  // prefix-sum tiles [P][K_pad / 128][pre_rows][128] (null: each CTA sums its own)
+    int64_t pre_rows;     // rows of a prefix tile (the most part rows + 1)
     int *dstatus;
 };
 
@@ -193,6 +195,8 @@ struct ItemCtx {
     int64_t K, K_pad;
     int B, C, group_chunks, rec_sets, C_rec, GB;
     int mode;      // 0: point stream, tile holds factors; 1: interval stream, tile holds prefix sums
+    const float *prefix;
+    int64_t pre_rows;
     int *dstatus;
 };
 
@@ -539,6 +543,8 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         X.C_rec = A.C_rec;
         X.GB = A.GB;
         X.mode = hist_stream_of(MODE);
+        X.prefix = A.prefix;
+        X.pre_rows = A.pre_rows;
         X.dstatus = A.dstatus;
     }
     if (threadIdx.x < kKT) s_invz[threadIdx.x] = inv_z(*Ap, k0 + threadIdx.x);
@@ -550,7 +556,11 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     // normaliser 1 / prod_d Z_d
     const int64_t row0 = (int64_t)p * H.part_rows;
     const int64_t nrows = min(H.part_rows, H.n_last - row0);
-    {
+    const bool pre = MODE && X.prefix != nullptr;  // the prefix sums come ready-made
+    if (pre) {
+        const float *src = X.prefix + ((int64_t)p * (X.K_pad / kKT) + k0 / kKT) * X.pre_rows * kKT;
+        for (int64_t e = threadIdx.x; e < (nrows + 1) * (kKT / 4); e += blockDim.x) cp_async16(ws + e * 4, src + e * 4);
+    } else {
         const float *src = H.g_last + row0 * X.K_pad + k0;
         const int64_t K_pad = X.K_pad;
         for (int64_t e = threadIdx.x; e < nrows * (kKT / 4); e += blockDim.x) {
@@ -559,10 +569,13 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         }
     }
     cp_async_commit();
-    if (threadIdx.x < kKT) ws[nrows * kKT + threadIdx.x] = 0.f;
+    if (!pre && threadIdx.x < kKT) ws[nrows * kKT + threadIdx.x] = 0.f;
     cp_async_wait_all();
     __syncthreads();
-    if (MODE) {
+    if (pre) {
+        // the staging buffers are next written by bulk copies (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    } else if (MODE) {
         // interval stream: every column becomes the exclusive prefix sums
         // P[0..nrows] of its scaled factors (compensated sums, each P rounded
         // once to FP32), so that rows a .. b - 1 sum to P[b] - P[a].  The
@@ -903,6 +916,45 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_global(HistArgs A, 
     }
 }
 
+// Prefix-sum tiles of the interval and record streams, once per (part,
+// density): thread (p, k) walks the part's rows of the gathered-axis factor
+// table, each factor scaled by the density's normaliser 1 / prod_d Z_d, and
+// writes the exclusive prefix sums P[0..nrows] (compensated, each P rounded
+// once to FP32) so that rows a .. b - 1 sum to P[b] - P[a].  Tile (p, k-tile)
+// is one contiguous block of pre_rows x 128 floats, copied as is into the
+// histogram kernel's shared memory.  Returns at once when the device chose
+// the point stream, whose tile holds the scaled factors themselves.
+__global__ void __launch_bounds__(128) k_prefix_tiles(const __grid_constant__ HistArgs A, float *__restrict__ out,
+                                                      int gate_stream) {
+    if (A.points_only || (gate_stream && A.sel[1] == 0)) return;
+    const LayoutArgs &H = A.sel[0] ? A.L1 : A.L0;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (p >= H.P || k >= A.K_pad) return;
+    const int64_t row0 = (int64_t)p * H.part_rows;
+    const int64_t nrows = min(H.part_rows, H.n_last - row0);
+    const float iz = inv_z(A, k);
+    const float *src = H.g_last + row0 * A.K_pad + k;
+    float *dst = out + ((int64_t)p * (A.K_pad / kKT) + k / kKT) * A.pre_rows * kKT + (k % kKT);
+    float sh = 0.f, sl = 0.f;
+    constexpr int kAhead = 32;  // rows loaded ahead (the walk is bound by loads in flight)
+    for (int64_t a = 0; a < nrows; a += kAhead) {
+        float v[kAhead];
+#pragma unroll
+        for (int u = 0; u < kAhead; ++u) v[u] = a + u < nrows ? src[(a + u) * A.K_pad] : 0.f;
+#pragma unroll
+        for (int u = 0; u < kAhead; ++u) {
+            if (a + u >= nrows) break;
+            dst[(a + u) * kKT] = sh + sl;
+            const float x = v[u] * iz;
+            const float t = sh + x, bb = t - sh;
+            sl += (sh - (t - bb)) + (x - bb);
+            sh = t;
+        }
+    }
+    dst[nrows * kKT] = sh + sl;
+}
+
 // Finish H[k, b]: for every part, the key (part, b) is either empty, summed
 // whole by the single chunk that holds it (direct row), or cut by chunk
 // boundaries and summed from the partials of the chunks overlapping it (in
@@ -1100,8 +1152,20 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
     return A;
 }
 
+bool vup_hist_prefix(vup_grid g, int64_t K, cudaStream_t s) {
+    if (!vup_hist_tile_fits(g)) return false;
+    int64_t rows;
+    int P_max;
+    HistArgs A = hist_args_for(g, K, nullptr, rows, P_max);
+    A.pre_rows = rows + 1;
+    VUP_PROF("hist_prefix", s, 1);
+    dim3 pg((unsigned)(A.K_pad / 128), (unsigned)P_max);
+    k_prefix_tiles<<<pg, 128, 0, s>>>(A, (float *)g->hist_prefix.p, 0);
+    return cudaGetLastError() == cudaSuccess;
+}
+
 vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab,
-                          bool points_only, cudaEvent_t keys_ready) {
+                          bool points_only, cudaEvent_t keys_ready, bool prefix_ready) {
     const int nd = g->ndim;
     int64_t rows;
     int P_max;
@@ -1145,6 +1209,18 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     }
     A.rec_sets = Sr;
     const int n_items_rec = P_max * Sr * nkt;
+    if (in_smem && !points_only && !ftab) {
+        // prefix-sum tiles for the interval and record streams (the kernel
+        // returns at once when the device chose the point stream)
+        A.prefix = (const float *)g->hist_prefix.p;
+        A.pre_rows = rows + 1;
+        if (!prefix_ready) {
+            VUP_PROF("hist_prefix", s, 1);
+            dim3 pg((unsigned)(A.K_pad / 128), (unsigned)P_max);
+            k_prefix_tiles<<<pg, 128, 0, s>>>(A, (float *)g->hist_prefix.p, 1);
+            VUP_CHECK_LAUNCH();
+        }
+    }
     {
         VUP_PROF("hist_segmented", s, in_smem && !points_only ? 3 : 1);
         if (in_smem) {

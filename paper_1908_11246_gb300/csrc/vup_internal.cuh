@@ -100,6 +100,8 @@ struct vup_grid_s {
     // (forked from and joined back into the caller's stream)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_rec = nullptr;
+    cudaStream_t side2 = nullptr;                       // the prefix-sum tiles beside the contraction
+    cudaEvent_t ev_lay = nullptr, ev_dens = nullptr, ev_pre = nullptr;
 
     // counting-sort scratch
     DevBuf sort_counts, scan_tmp, lay_tmp, rec_tmp;
@@ -166,6 +168,7 @@ struct vup_grid_s {
     // per-K scratch (density constants, factor tables, partials)
     int64_t K_cap = 0;
     DevBuf dconst, dstats, dpart, ftab, atab_hi, atab_lo, partials, hist_part, hist_direct, ipsa_part;
+    DevBuf hist_prefix;  // prefix-sum tiles of the gathered axis [P][K_pad / 128][rows + 1][128]
     DevBuf atf_hi, atf_lo;         // TF32 split of the A operand [K_pad][R_pad]
 
     int *dstatus = nullptr;        // [1] device status word
@@ -181,9 +184,10 @@ vup_status vup_pick_hist_layout(vup_grid g, cudaStream_t s);
 // points_needed: the key-sorted point stream is built whatever the device
 // would choose (callers that walk it: posterior means).
 // records_done (optional) is recorded on s once the record stream is complete
-// (the key-sorted streams follow).
+// (the key-sorted streams follow); layout_picked (optional) once the layout
+// (hist_sel[0]) is chosen.
 vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed = false,
-                            cudaEvent_t records_done = nullptr);
+                            cudaEvent_t records_done = nullptr, cudaEvent_t layout_picked = nullptr);
 vup_status vup_ensure_layout(vup_grid g, cudaStream_t s, bool points_needed = false);
 // every layout's part tile fits the shared-memory histogram kernels
 bool vup_hist_tile_fits(vup_grid g);
@@ -209,8 +213,15 @@ vup_status vup_moments_finish(vup_grid g, int64_t K, int n_col_tiles, double *ra
 // the numerators and denominators of ratios do).
 // keys_ready (optional): an event the point and interval kernels (and the
 // finish) wait for; the record-stream kernel is launched before that wait.
+// prefix_ready: vup_hist_prefix already wrote the prefix-sum tiles for
+// these densities (on a stream s has waited for).
 vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab = nullptr,
-                          bool points_only = false, cudaEvent_t keys_ready = nullptr);
+                          bool points_only = false, cudaEvent_t keys_ready = nullptr, bool prefix_ready = false);
+// The interval and record streams' prefix-sum tiles of the chosen layout for K
+// densities (after their preparation and the layout choice), whichever
+// stream the device picks later; false when the grid's histogram does not
+// run the shared-memory kernels (nothing launched).
+bool vup_hist_prefix(vup_grid g, int64_t K, cudaStream_t s);
 vup_status vup_propagate_1d(vup_grid g, const vup_densities *d, double *raw, double *central,
                             float *hist, cudaStream_t s);
 vup_status vup_ipsa_1d(vup_grid g, const vup_densities *d, const double *grad, float *dmu,
