@@ -271,20 +271,37 @@ __device__ __forceinline__ void split_store(float *hi, float *lo, int64_t i, flo
     lo[i] = to_tf32(v - h);
 }
 
+// Two consecutive reduction indices of one density row split together (one
+// 4-byte BF16 pair or 8-byte TF32 pair store per array).
+__device__ __forceinline__ void split_store2(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t i, float v0, float v1) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+    *reinterpret_cast<__nv_bfloat162 *>(hi + i) = __halves2bfloat162(h0, h1);
+    *reinterpret_cast<__nv_bfloat162 *>(lo + i) = __halves2bfloat162(__float2bfloat16_rn(v0 - __bfloat162float(h0)),
+                                                                     __float2bfloat16_rn(v1 - __bfloat162float(h1)));
+}
+__device__ __forceinline__ void split_store2(float *hi, float *lo, int64_t i, float v0, float v1) {
+    const float h0 = to_tf32(v0), h1 = to_tf32(v1);
+    *reinterpret_cast<float2 *>(hi + i) = make_float2(h0, h1);
+    *reinterpret_cast<float2 *>(lo + i) = make_float2(to_tf32(v0 - h0), to_tf32(v1 - h1));
+}
+
+// Block (bx, by) transposes the 64 (a) x 32 (k) tile at a = 64 bx, k = 32 by;
+// each lane writes two consecutive a of one density row.  R_pad is a
+// multiple of 64.
 template <typename T>
 __device__ __forceinline__ void split_transpose_body(const float *__restrict__ tab, int64_t nd, int64_t K_pad,
                                                      int64_t R_pad, T *__restrict__ hi, T *__restrict__ lo,
                                                      int64_t bx, int64_t by) {
-    __shared__ float t[32][33];
-    const int64_t a0 = bx * 32, k0 = by * 32;
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    __shared__ float t[64][33];
+    const int64_t a0 = bx * 64, k0 = by * 32;
+    for (int y = threadIdx.y; y < 64; y += blockDim.y) {
         int64_t a = a0 + y, k = k0 + threadIdx.x;
         t[y][threadIdx.x] = (a < nd && k < K_pad) ? tab[a * K_pad + k] : 0.f;
     }
     __syncthreads();
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        int64_t k = k0 + y, a = a0 + threadIdx.x;
-        if (k < K_pad && a < R_pad) split_store(hi, lo, k * R_pad + a, t[threadIdx.x][y]);
+        const int64_t k = k0 + y, a = a0 + 2 * threadIdx.x;
+        if (k < K_pad && a < R_pad) split_store2(hi, lo, k * R_pad + a, t[2 * threadIdx.x][y], t[2 * threadIdx.x + 1][y]);
     }
     __syncthreads();
 }
@@ -498,7 +515,7 @@ static vup_status split_tables(vup_grid g, int mask, int64_t K_pad, T *hi0, T *l
             hi += o0;
             lo += o0;
         }
-        dim3 tg((unsigned)ceil_div64(K_pad, 32), (unsigned)ceil_div64(ori.R_pad, 32));
+        dim3 tg((unsigned)ceil_div64(K_pad, 32), (unsigned)ceil_div64(ori.R_pad, 64));
         k_split_transpose<T><<<tg, dim3(32, 8), 0, s>>>((const float *)g->ftab.p + off, g->n[dred], K_pad,
                                                         ori.R_pad, hi, lo);
         VUP_CHECK_LAUNCH();
@@ -530,7 +547,7 @@ vup_status vup_density_plan(int n, const vup_grid *gs, const vup_densities *ds, 
             for (int64_t kb = 0; kb < nkb; ++kb) fin.push_back(make_int4(i, (int)kb, d, 0));
         if (bf16)
             for (int64_t by = 0; by < ceil_div64(J.K_pad, 32); ++by)
-                for (int64_t bx = 0; bx < ceil_div64(J.R_pad, 32); ++bx)
+                for (int64_t bx = 0; bx < ceil_div64(J.R_pad, 64); ++bx)
                     split.push_back(make_int4(i, (int)bx, (int)by, 0));
     }
     P->n_prep = (int)prep.size();

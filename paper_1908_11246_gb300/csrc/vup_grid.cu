@@ -800,27 +800,25 @@ constexpr uint32_t kRecEnd = 1u << 31;  // last record of its group
 // interval starts at the segment's first row or where the bin changes; a
 // record starts at an interval whose group differs from the interval before
 // it, or whose bin step turns against the step before it when the three
-// intervals share a group.  PASS 1 (WRITE = false) counts the records of
-// every (group, line) into cnt[group * NL + line] and adds the intervals to
-// n_iv; after an exclusive scan of those counts, PASS 2 (WRITE = true) takes
-// cnt as cursors and writes each record at its place in (group, line, row)
-// order: words (B_0 | B_1 << 16, .., B_6 | B_7 << 16, rows inside the part) and
-// (B_8 | sign | group end, rest code of the record kRunAhead places later,
-// group, 0), and its rest index (the line).  bins is viewed as [R][C], C the
-// last axis; layout 1 (2-D) walks the columns.
+// intervals share a group.  Each record goes to the segment's slots
+// tmp[seg * cap + i] with its group and its rank among the segment's records
+// of that group; cnt[group * NL + line] counts the records of every (group,
+// line) and n_iv the intervals.  bins is viewed as [R][C], C the last axis;
+// layout 1 (2-D) walks the columns.  A record's boundary rows B_0..B_8 (rows
+// inside the part): bin 8q + j holds rows [B_j, B_j+1) when the bins rise
+// along the line, [B_j+1, B_j) when they fall.
 struct RecGeom {
     int64_t R, C;
     int B, GB;
     int64_t NL;   // line stride of the count matrix (the most lines of either layout)
+    int64_t cap;  // slots per segment (the most part rows)
     int ndim;
     int64_t n1;   // 3-D rest code: line = a0 n1 + a1 -> a0 | a1 << 15
 };
 
-template <bool WRITE>
 __global__ void __launch_bounds__(64) k_rec_walk(const int32_t *__restrict__ bins, RecGeom Q, LaySel L,
                                                  int32_t *__restrict__ cnt, int32_t *__restrict__ n_iv,
-                                                 const int32_t *__restrict__ goff, const int32_t *__restrict__ n_rec_p,
-                                                 uint4 *__restrict__ rec, int32_t *__restrict__ rec_rest) {
+                                                 uint4 *__restrict__ tmp, int32_t *__restrict__ seg_n) {
     const bool tr = L.sel[0] != 0;
     const LayGeom G = L.get();
     const int64_t n_lines = tr ? Q.C : Q.R;
@@ -829,19 +827,21 @@ __global__ void __launch_bounds__(64) k_rec_walk(const int32_t *__restrict__ bin
     const int p = (int)(tid / n_lines);
     const int64_t line = tid - (int64_t)p * n_lines;
     const int64_t row0 = (int64_t)p * G.part_rows, row1 = min(G.n_last, row0 + G.part_rows);
-    if (row0 >= row1) return;
+    if (row0 >= row1) {
+        seg_n[tid] = 0;
+        return;
+    }
     const int64_t stride = tr ? Q.C : 1;
     const int32_t *src = bins + (tr ? line : line * Q.C);
-    const int32_t n_rec = WRITE ? n_rec_p[0] : 0;
-    const uint32_t code = Q.ndim == 3 ? (uint32_t)(line / Q.n1) | ((uint32_t)(line % Q.n1) << 15) : (uint32_t)line;
+    uint4 *slot = tmp + 2 * tid * Q.cap;
 
     int32_t bcur = -1, b1 = -1, b2 = -1;  // bins of the current interval and of the two before it
     int rq = -1, dir = 0, rprev = -1;     // open record: group in the part, step sign, last bin
     int32_t st[kRecBins];  // its bins' first rows (relative to row0), -1 if absent
 #pragma unroll
     for (int j = 0; j < kRecBins; ++j) st[j] = -1;
-    int32_t niv = 0;
-    int32_t cg = -1, cc = 0;  // (group, count) run of pass 1; (group, cursor) of pass 2
+    int32_t niv = 0, nrec = 0;
+    int32_t cg = -1, base = 0, cc = 0;  // run of one group: its rank base and count
     auto emit = [&](int64_t e_row) {
         const int32_t e = (int32_t)(e_row - row0);
         uint32_t w[kRecBins + 1];
@@ -856,29 +856,17 @@ __global__ void __launch_bounds__(64) k_rec_walk(const int32_t *__restrict__ bin
             w[j] = (uint32_t)v;
         }
         const int32_t g = p * Q.GB + rq;
-        if (!WRITE) {
-            if (g != cg) {
-                if (cg >= 0) cnt[cg * Q.NL + line] += cc;
-                cg = g;
-                cc = 0;
-            }
-            ++cc;
-        } else {
-            if (g != cg) {
-                if (cg >= 0) cnt[cg * Q.NL + line] = cc;
-                cg = g;
-                cc = cnt[g * Q.NL + line];
-            }
-            const int64_t pos = cc++;
-            rec[2 * pos] = make_uint4(w[0] | w[1] << 16, w[2] | w[3] << 16, w[4] | w[5] << 16, w[6] | w[7] << 16);
-            uint32_t *w1 = reinterpret_cast<uint32_t *>(rec + 2 * pos + 1);
-            w1[0] = w[8] | (dir < 0 ? kRecNeg : 0u) | (pos + 1 == goff[g + 1] ? kRecEnd : 0u);
-            if (pos + kRunAhead >= n_rec) w1[1] = 0u;
-            w1[2] = (uint32_t)g;
-            w1[3] = 0u;
-            if (pos >= kRunAhead) reinterpret_cast<uint32_t *>(rec + 2 * (pos - kRunAhead) + 1)[1] = code;
-            rec_rest[pos] = (int32_t)line;
+        if (g != cg) {
+            if (cg >= 0) cnt[cg * Q.NL + line] = base + cc;
+            cg = g;
+            base = cnt[g * Q.NL + line];
+            cc = 0;
         }
+        slot[2 * nrec] = make_uint4(w[0] | w[1] << 16, w[2] | w[3] << 16, w[4] | w[5] << 16, w[6] | w[7] << 16);
+        slot[2 * nrec + 1] = make_uint4(w[8] | (dir < 0 ? kRecNeg : 0u), (uint32_t)line, (uint32_t)g,
+                                        (uint32_t)(base + cc));
+        ++cc;
+        ++nrec;
     };
     constexpr int kAhead = 16;  // rows loaded ahead
     for (int64_t r = row0; r < row1; r += kAhead) {
@@ -916,14 +904,48 @@ __global__ void __launch_bounds__(64) k_rec_walk(const int32_t *__restrict__ bin
         }
     }
     emit(row1);
-    if (!WRITE) {
-        cnt[cg * Q.NL + line] += cc;
-        atomicAdd(n_iv, niv);
-    } else if (tid == 0) {
-        // the records past the last read as empty
-        for (int t = 0; t < 16; ++t) {
-            rec[2 * ((int64_t)n_rec + t)] = make_uint4(0u, 0u, 0u, 0u);
-            rec[2 * ((int64_t)n_rec + t) + 1] = make_uint4(0u, 0u, 0u, 0u);
+    cnt[cg * Q.NL + line] = base + cc;
+    seg_n[tid] = nrec;
+    atomicAdd(n_iv, niv);
+}
+
+// Every record from its segment slot to its place in (group, line, row)
+// order (starts: the exclusive scan of the (group, line) counts): words (B_0 |
+// B_1 << 16, .., B_6 | B_7 << 16) and (B_8 | sign | group end, rest code of
+// the record kRunAhead places later, group, 0), and its rest index (the
+// line).  One warp per segment.
+__global__ void k_rec_scatter(const uint4 *__restrict__ tmp, const int32_t *__restrict__ seg_n, RecGeom Q,
+                              LaySel L, const int32_t *__restrict__ starts, const int32_t *__restrict__ goff,
+                              const int32_t *__restrict__ n_rec_p, uint4 *__restrict__ rec,
+                              int32_t *__restrict__ rec_rest) {
+    const bool tr = L.sel[0] != 0;
+    const LayGeom G = L.get();
+    const int64_t n_seg = (int64_t)G.P * (tr ? Q.C : Q.R);
+    const int32_t n_rec = n_rec_p[0];
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (w0 == 0 && lane < 16) {  // the records past the last read as empty
+        rec[2 * ((int64_t)n_rec + lane)] = make_uint4(0u, 0u, 0u, 0u);
+        rec[2 * ((int64_t)n_rec + lane) + 1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int64_t sg = w0; sg < n_seg; sg += nw) {
+        const int32_t n = seg_n[sg];
+        const uint4 *slot = tmp + 2 * sg * Q.cap;
+        for (int32_t i = lane; i < n; i += 32) {
+            const uint4 u = slot[2 * i], v = slot[2 * i + 1];
+            const uint32_t line = v.y, g = v.z;
+            const int64_t pos = (int64_t)starts[(int64_t)g * Q.NL + line] + v.w;
+            rec[2 * pos] = u;
+            uint32_t *w1 = reinterpret_cast<uint32_t *>(rec + 2 * pos + 1);
+            w1[0] = v.x | (pos + 1 == goff[g + 1] ? kRecEnd : 0u);
+            if (pos + kRunAhead >= n_rec) w1[1] = 0u;
+            w1[2] = g;
+            w1[3] = 0u;
+            const uint32_t code =
+                Q.ndim == 3 ? (uint32_t)(line / Q.n1) | ((uint32_t)(line % Q.n1) << 15) : (uint32_t)line;
+            if (pos >= kRunAhead) reinterpret_cast<uint32_t *>(rec + 2 * (pos - kRunAhead) + 1)[1] = code;
+            rec_rest[pos] = (int32_t)line;
         }
     }
 }
@@ -1412,7 +1434,12 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
             }
             const int n_groups = P_sel * GB;  // room for either layout's parts
             const int64_t Lr = (int64_t)n_groups * NL;
-            if ((st = devbuf_reserve(g->rec_tmp, sizeof(int32_t) * 2 * (size_t)Lr)) != VUP_OK ||
+            int64_t cap = 1;
+            for (int l = 0; l < g->n_layouts; ++l) cap = std::max(cap, g->hl[l].part_rows);
+            // counts, their scan, segment record counts, then the uint4 slots (16-byte aligned)
+            const int64_t ints = ((2 * Lr + walkers + 3) / 4) * 4;
+            if ((st = devbuf_reserve(g->rec_tmp, sizeof(int32_t) * (size_t)ints +
+                                                     sizeof(uint4) * 2 * (size_t)(walkers * cap))) != VUP_OK ||
                 (st = devbuf_reserve(g->scan_tmp, sizeof(unsigned long long) * (size_t)scan_scratch_ints(Lr))) !=
                     VUP_OK ||
                 (st = devbuf_reserve(HL.rec, sizeof(uint4) * 2 * (size_t)(N + 64))) != VUP_OK ||
@@ -1421,26 +1448,28 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
                 (st = devbuf_reserve(HL.rec_gch, sizeof(int2) * (size_t)n_groups)) != VUP_OK)
                 return st;
             scratch = (int32_t *)g->scan_tmp.p;
-            int32_t *rcnt = (int32_t *)g->rec_tmp.p, *rstart = rcnt + Lr;
+            int32_t *rcnt = (int32_t *)g->rec_tmp.p, *rstart = rcnt + Lr, *seg_n = rcnt + 2 * Lr;
+            uint4 *rslot = reinterpret_cast<uint4 *>(rcnt + ints);
             RecGeom Q;
             Q.R = Rn;
             Q.C = Cn;
             Q.B = B;
             Q.GB = GB;
             Q.NL = NL;
+            Q.cap = cap;
             Q.ndim = g->ndim;
             Q.n1 = g->ndim == 3 ? g->n[1] : 1;
             VUP_CHECK_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(int32_t) * (size_t)Lr, s));
             VUP_CHECK_CUDA(cudaMemsetAsync(HL.n_iv, 0, sizeof(int32_t), s));
-            const unsigned wb = (unsigned)ceil_div64(walkers, 64);
-            k_rec_walk<false><<<wb, 64, 0, s>>>(g->bins, Q, L, rcnt, HL.n_iv, nullptr, nullptr, nullptr, nullptr);
+            k_rec_walk<<<(unsigned)ceil_div64(walkers, 64), 64, 0, s>>>(g->bins, Q, L, rcnt, HL.n_iv, rslot, seg_n);
             VUP_CHECK_LAUNCH();
             if ((st = scan_exclusive(rcnt, rstart, Lr, scratch, s)) != VUP_OK) return st;
             k_rec_goff<<<(n_groups + 2 + 255) / 256, 256, 0, s>>>(rstart, rcnt, Lr, NL, n_groups,
                                                                   (int32_t *)HL.rec_goff.p, HL.n_rec);
             VUP_CHECK_LAUNCH();
-            k_rec_walk<true><<<wb, 64, 0, s>>>(g->bins, Q, L, rstart, nullptr, (const int32_t *)HL.rec_goff.p,
-                                               HL.n_rec, (uint4 *)HL.rec.p, (int32_t *)HL.rec_rest.p);
+            k_rec_scatter<<<(unsigned)std::min<int64_t>(ceil_div64(walkers, 8), (int64_t)vup_num_sms() * 16), 256, 0,
+                            s>>>(rslot, seg_n, Q, L, rstart, (const int32_t *)HL.rec_goff.p, HL.n_rec,
+                                 (uint4 *)HL.rec.p, (int32_t *)HL.rec_rest.p);
             VUP_CHECK_LAUNCH();
             // chunks of records (the same count per part as the other streams' chunks / 4)
             const int Cr = g->n_chunks_rec;
@@ -1452,7 +1481,7 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
                                                                        HL.rec_chunk, L, Cr,
                                                                        (int2 *)HL.rec_gch.p);
             VUP_CHECK_LAUNCH();
-            // count pass, scan, first records, write pass, chunks, group chunks, gate
+            // walk, scan, first records, scatter, chunks, group chunks, gate
             launches += 2 + scan_launches(Lr) + 2 + 2 + 1;
         }
         // the key-sorted point and interval streams, unless the record stream is

@@ -924,13 +924,8 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_global(HistArgs A, 
 // is one contiguous block of pre_rows x 128 floats, copied as is into the
 // histogram kernel's shared memory.  Returns at once when the device chose
 // the point stream, whose tile holds the scaled factors themselves.
-__global__ void __launch_bounds__(128) k_prefix_tiles(const __grid_constant__ HistArgs A, float *__restrict__ out,
-                                                      int gate_stream) {
-    if (A.points_only || (gate_stream && A.sel[1] == 0)) return;
-    const LayoutArgs &H = A.sel[0] ? A.L1 : A.L0;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = blockIdx.y;
-    if (p >= H.P || k >= A.K_pad) return;
+__device__ __forceinline__ void prefix_tile(const HistArgs &A, const LayoutArgs &H, float *__restrict__ out, int p,
+                                            int64_t k) {
     const int64_t row0 = (int64_t)p * H.part_rows;
     const int64_t nrows = min(H.part_rows, H.n_last - row0);
     const float iz = inv_z(A, k);
@@ -953,6 +948,16 @@ __global__ void __launch_bounds__(128) k_prefix_tiles(const __grid_constant__ Hi
         }
     }
     dst[nrows * kKT] = sh + sl;
+}
+
+__global__ void __launch_bounds__(128) k_prefix_tiles(const __grid_constant__ HistArgs A, float *__restrict__ out,
+                                                      int gate_stream) {
+    if (A.points_only || (gate_stream && A.sel[1] == 0)) return;
+    const LayoutArgs &H = A.sel[0] ? A.L1 : A.L0;
+    // tiles (p, k-tile) strided over the grid
+    const int64_t nkt = A.K_pad / kKT;
+    for (int64_t u = blockIdx.x; u < (int64_t)H.P * nkt; u += gridDim.x)
+        prefix_tile(A, H, out, (int)(u / nkt), (u % nkt) * kKT + threadIdx.x);
 }
 
 // Finish H[k, b]: for every part, the key (part, b) is either empty, summed
@@ -1159,8 +1164,7 @@ bool vup_hist_prefix(vup_grid g, int64_t K, cudaStream_t s) {
     HistArgs A = hist_args_for(g, K, nullptr, rows, P_max);
     A.pre_rows = rows + 1;
     VUP_PROF("hist_prefix", s, 1);
-    dim3 pg((unsigned)(A.K_pad / 128), (unsigned)P_max);
-    k_prefix_tiles<<<pg, 128, 0, s>>>(A, (float *)g->hist_prefix.p, 0);
+    k_prefix_tiles<<<(unsigned)(P_max * (A.K_pad / 128)), 128, 0, s>>>(A, (float *)g->hist_prefix.p, 0);
     return cudaGetLastError() == cudaSuccess;
 }
 
@@ -1216,8 +1220,7 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
         A.pre_rows = rows + 1;
         if (!prefix_ready) {
             VUP_PROF("hist_prefix", s, 1);
-            dim3 pg((unsigned)(A.K_pad / 128), (unsigned)P_max);
-            k_prefix_tiles<<<pg, 128, 0, s>>>(A, (float *)g->hist_prefix.p, 1);
+            k_prefix_tiles<<<(unsigned)(P_max * (A.K_pad / 128)), 128, 0, s>>>(A, (float *)g->hist_prefix.p, 1);
             VUP_CHECK_LAUNCH();
         }
     }
