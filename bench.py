@@ -197,8 +197,9 @@ def roofline_for(name, ms, n_work, units, pk, clk_mhz, workload, hist_units=None
     orientation, covers all K x N); hist_units: bytes one histogram pass moves
     through the SM's L1 data pipe by its algorithm (per density: 4 per point +
     4 per rest-factor row per run on the point stream; 8 of prefix sums + 4 per
-    rest-factor row per interval on the interval stream; 20 of prefix sums + 4
-    per rest-factor row per record on the record stream)."""
+    rest-factor row per interval on the interval stream; on the record stream
+    4 per prefix sum a record needs -- one per bin it holds and one more, the
+    intervals plus the records in all -- + 4 per rest-factor row per record)."""
     per = ms / max(n_work, 1) * 1e-3
     sms = 152
     tr = traffic_for(name, workload)
@@ -229,7 +230,8 @@ def roofline_for(name, ms, n_work, units, pk, clk_mhz, workload, hist_units=None
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": tr,
                 "note": "bytes through the L1 data pipe that the walk needs per pass (per density: point stream "
                         "4 per point + 4 per rest-factor row per run; interval stream 8 of prefix sums + 4 per "
-                        "rest-factor row per interval; record stream 20 of prefix sums + 4 per rest-factor row "
+                        "rest-factor row per interval; record stream 4 per prefix sum it needs (one per bin a "
+                        "record holds + one per record) + 4 per rest-factor row "
                         "per record); peak = 152 SM x 128 B/clk x median SM clock"}
     a = 4.0 * units / per / 1e9
     return {"bound": "hbm", "achieved": a, "peak": pk["hbm"], "unit": "GB/s", "frac": a / pk["hbm"],
@@ -575,7 +577,7 @@ def main():
             streams.add(("points", "intervals", "records")[mode])
             nf = info.ndim - 1  # rest-factor rows per run, interval or record
             if mode == 2:
-                hist_units += K * info.hist_records * (20 + 4 * nf)
+                hist_units += K * (4 * (info.hist_intervals + info.hist_records) + 4 * nf * info.hist_records)
             elif mode == 1:
                 hist_units += K * info.hist_intervals * (8 + 4 * nf)
             else:
