@@ -232,6 +232,8 @@ static void free_grid(vup_grid g) {
     if (g->ev_lay) cudaEventDestroy(g->ev_lay);
     if (g->ev_dens) cudaEventDestroy(g->ev_dens);
     if (g->ev_pre) cudaEventDestroy(g->ev_pre);
+    if (g->ev_mom) cudaEventDestroy(g->ev_mom);
+    if (g->ev_mfin) cudaEventDestroy(g->ev_mfin);
     if (g->side2) cudaStreamDestroy(g->side2);
     cudaFree(g->ydev_scale);
     cudaFree(g->dstatus);
@@ -574,7 +576,7 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
         ~Join() {
             if (on) cudaStreamWaitEvent(s, e, 0);
         }
-    } join{forked, s, g->ev_join};
+    } join{forked, s, g->ev_join}, join_fin{false, s, g->ev_mfin};
     const int to = vup_tc_orient(g);
     if (want_m && (st = vup_build_tables(g, (bf16 || tf32) ? to : kOrientLast, tf32 ? 2 : (bf16 ? 1 : 0), s)) !=
                       VUP_OK)
@@ -588,6 +590,9 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
             VUP_CHECK_CUDA(cudaStreamCreateWithFlags(&g->side2, cudaStreamNonBlocking));
             VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_dens, cudaEventDisableTiming));
             VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_pre, cudaEventDisableTiming));
+            VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_mom, cudaEventDisableTiming));
+            VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_mfin, cudaEventDisableTiming));
+            join_fin.e = g->ev_mfin;
         }
         VUP_CHECK_CUDA(cudaEventRecord(g->ev_dens, s));
         VUP_CHECK_CUDA(cudaStreamWaitEvent(g->side2, g->ev_dens, 0));
@@ -606,7 +611,17 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
             if ((st = vup_moments_simt(g, K, 0, 1, (float *)g->partials.p, s)) != VUP_OK) return st;
             nct = vup_simt_col_tiles(g->orient[0]);
         }
-        if ((st = vup_moments_finish(g, K, (int)nct, moments_raw, moments_central, s)) != VUP_OK) return st;
+        if (prefix_ready) {
+            // the FP64 finish on the third stream: the histogram does not need it
+            VUP_CHECK_CUDA(cudaEventRecord(g->ev_mom, s));
+            VUP_CHECK_CUDA(cudaStreamWaitEvent(g->side2, g->ev_mom, 0));
+            join_fin.on = true;
+            st = vup_moments_finish(g, K, (int)nct, moments_raw, moments_central, g->side2);
+            VUP_CHECK_CUDA(cudaEventRecord(g->ev_mfin, g->side2));
+            if (st != VUP_OK) return st;
+        } else if ((st = vup_moments_finish(g, K, (int)nct, moments_raw, moments_central, s)) != VUP_OK) {
+            return st;
+        }
     }
     if (hist) {
         // the record-stream histogram waits for the records only; the other

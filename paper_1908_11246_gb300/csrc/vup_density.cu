@@ -385,12 +385,22 @@ __global__ void __launch_bounds__(256) k_split_product_rows(const float *__restr
 
 // STATS: also the sums of g u and g u^2 (E[u], E[u^2] of the IPSA derivatives)
 template <bool STATS>
-__global__ void k_density_prep(DensJob J) { density_prep_body<STATS>(J, blockIdx.x, blockIdx.y, blockIdx.z); }
-__global__ void k_density_finish(DensJob J) { density_finish_body(J, blockIdx.x, blockIdx.y); }
+__global__ void k_density_prep(DensJob J) {
+    pdl_trigger();
+    pdl_wait();
+    density_prep_body<STATS>(J, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+__global__ void k_density_finish(DensJob J) {
+    pdl_trigger();
+    pdl_wait();
+    density_finish_body(J, blockIdx.x, blockIdx.y);
+}
 // grid: x = density tiles of 32 (K_pad / 32 may exceed the 65535 limit of y), y = axis tiles
 template <typename T>
 __global__ void k_split_transpose(const float *__restrict__ tab, int64_t nd, int64_t K_pad, int64_t R_pad,
                                   T *__restrict__ hi, T *__restrict__ lo) {
+    pdl_trigger();
+    pdl_wait();
     split_transpose_body<T>(tab, nd, K_pad, R_pad, hi, lo, blockIdx.y, blockIdx.x);
 }
 
@@ -470,12 +480,10 @@ vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_or
     const int64_t K_pad = J.K_pad;
     dim3 grd((unsigned)ceil_div64(K_pad, 128), (unsigned)g->ndim, (unsigned)J.S);
     VUP_PROF("density_prep", s, 2 + __builtin_popcount(need_bf16_orient_mask));
-    if (stats) k_density_prep<true><<<grd, 128, 0, s>>>(J);
-    else k_density_prep<false><<<grd, 128, 0, s>>>(J);
-    VUP_CHECK_LAUNCH();
+    VUP_CHECK_CUDA(stats ? launch_pdl(k_density_prep<true>, grd, 128, 0, s, J)
+                         : launch_pdl(k_density_prep<false>, grd, 128, 0, s, J));
     dim3 fgrd((unsigned)ceil_div64(d->K, 128), (unsigned)g->ndim);
-    k_density_finish<<<fgrd, 128, 0, s>>>(J);
-    VUP_CHECK_LAUNCH();
+    VUP_CHECK_CUDA(launch_pdl(k_density_finish, fgrd, 128, 0, s, J));
     if (tf32) return split_tables<float>(g, need_bf16_orient_mask, K_pad, (float *)g->atf_hi.p,
                                          (float *)g->atf_lo.p, s);
     return split_tables<__nv_bfloat16>(g, need_bf16_orient_mask, K_pad, (__nv_bfloat16 *)g->atab_hi.p,
@@ -516,9 +524,8 @@ static vup_status split_tables(vup_grid g, int mask, int64_t K_pad, T *hi0, T *l
             lo += o0;
         }
         dim3 tg((unsigned)ceil_div64(K_pad, 32), (unsigned)ceil_div64(ori.R_pad, 64));
-        k_split_transpose<T><<<tg, dim3(32, 8), 0, s>>>((const float *)g->ftab.p + off, g->n[dred], K_pad,
-                                                        ori.R_pad, hi, lo);
-        VUP_CHECK_LAUNCH();
+        VUP_CHECK_CUDA(launch_pdl(k_split_transpose<T>, tg, dim3(32, 8), 0, s, (const float *)g->ftab.p + off,
+                                  (int64_t)g->n[dred], K_pad, ori.R_pad, hi, lo));
     }
     return VUP_OK;
 }

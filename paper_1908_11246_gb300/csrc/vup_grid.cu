@@ -144,6 +144,8 @@ __device__ __forceinline__ void range_reduce(unsigned long long mn, unsigned lon
 // y at every grid point, and its exact range into ext (reset beforehand).
 __global__ void k_model_eval(double *__restrict__ y, int64_t N, GridGeom G, int model, Theta th,
                              unsigned long long *ext) {
+    pdl_trigger();
+    pdl_wait();
     unsigned long long mn = ~0ull, mx = 0ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -174,6 +176,8 @@ __host__ __device__ inline bool model_separable(int model, int ndim) {
 }
 
 __global__ void k_axis_terms(GridGeom G, int model, Theta th, double2 *__restrict__ terms) {
+    pdl_trigger();
+    pdl_wait();
     int64_t off = 0;
     for (int d = 0; d < G.ndim; ++d) {
         for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < G.n[d];
@@ -217,6 +221,8 @@ __global__ void k_axis_terms(GridGeom G, int model, Theta th, double2 *__restric
 
 __global__ void k_model_combine(double *__restrict__ y, int64_t N, GridGeom G, int model, Theta th,
                                 const double2 *__restrict__ terms, unsigned long long *ext) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t o1 = G.n[0], o2 = G.n[0] + G.n[1];
     unsigned long long mn = ~0ull, mx = 0ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
@@ -350,6 +356,8 @@ __global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
 // max(|ymin|, |ymax|) (1 if 0) from the first thread.
 __global__ void k_bins_scale(const double *__restrict__ y, int64_t N, int B, const unsigned long long *ext,
                              int32_t *__restrict__ bins, double *s_out) {
+    pdl_trigger();
+    pdl_wait();
     const BinRule rule(ext, B);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double s = fmax(fabs(rule.ymin), fabs(rule.ymax));
@@ -1114,6 +1122,8 @@ template <bool REST_ROWS>
 __global__ void k_power_table_bf16(const double *__restrict__ y, int64_t Qn, int64_t Rn, int64_t Qext,
                                    const double *__restrict__ sc, int64_t ld, __nv_bfloat16 *__restrict__ out,
                                    __nv_bfloat16 *__restrict__ out2) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ float tile[32][65];
     const int64_t q0 = (int64_t)blockIdx.y * 32, r0 = (int64_t)blockIdx.x * 64;
     const double inv = 1.0 / sc[0];
@@ -1232,9 +1242,11 @@ vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta, 
     if (sep) {
         int64_t nmax = 1;
         for (int d = 0; d < g->ndim; ++d) nmax = std::max(nmax, g->n[d]);
-        k_axis_terms<<<(unsigned)ceil_div64(nmax, 128), 128, 0, s>>>(G, model_id, th, g->axis_terms);
+        VUP_CHECK_CUDA(launch_pdl(k_axis_terms, dim3((unsigned)ceil_div64(nmax, 128)), dim3(128), 0, s, G, model_id, th,
+                                  g->axis_terms));
         VUP_CHECK_LAUNCH();
-        k_model_combine<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th, g->axis_terms, g->ext);
+        VUP_CHECK_CUDA(launch_pdl(k_model_combine, dim3(blocks), dim3(256), 0, s, g->y, g->N, G, model_id, th,
+                                  (const double2 *)g->axis_terms, g->ext));
     } else {
         k_model_eval<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th, g->ext);
     }
@@ -1363,7 +1375,8 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
                                                                                 counts, n_tiles);
         } else {
             const int bb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(N / 2, 256), (int64_t)vup_num_sms() * 8));
-            k_bins_scale<<<bb, 256, 0, s>>>(g->y, N, B, g->ext, g->bins, g->ydev_scale);
+            VUP_CHECK_CUDA(launch_pdl(k_bins_scale, dim3(bb), dim3(256), 0, s, (const double *)g->y, N, B,
+                                      (const unsigned long long *)g->ext, g->bins, g->ydev_scale));
         }
         VUP_CHECK_LAUNCH();
     }
@@ -1602,12 +1615,11 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
         const int64_t Qext = rows / 4;
         dim3 pg((unsigned)(ld / 64), (unsigned)(Qext / 32));
         if (first)
-            k_power_table_bf16<false><<<pg, 256, 0, s>>>(g->y, o.Q, o.R, Qext, g->ydev_scale, ld, g->zt_hi[orient],
-                                                         g->zt_lo[orient]);
+            VUP_CHECK_CUDA(launch_pdl(k_power_table_bf16<false>, pg, dim3(256), 0, s, (const double *)g->y, o.Q, o.R,
+                                      Qext, (const double *)g->ydev_scale, ld, g->zt_hi[orient], g->zt_lo[orient]));
         else
-            k_power_table_bf16<true><<<pg, 256, 0, s>>>(g->y, o.Q, o.R, Qext, g->ydev_scale, ld, g->zt_hi[orient],
-                                                        g->zt_lo[orient]);
-        VUP_CHECK_LAUNCH();
+            VUP_CHECK_CUDA(launch_pdl(k_power_table_bf16<true>, pg, dim3(256), 0, s, (const double *)g->y, o.Q, o.R,
+                                      Qext, (const double *)g->ydev_scale, ld, g->zt_hi[orient], g->zt_lo[orient]));
     }
     g->have_tab[orient][bf16] = 1;
     return VUP_OK;

@@ -815,6 +815,8 @@ __device__ __forceinline__ int hist_stream(const HistArgs &A) { return A.points_
 template <int NF, int MODE>
 __global__ void __launch_bounds__(hist_warps(MODE) * 32, 1)
     k_hist_smem(const __grid_constant__ HistArgs A, int64_t tile_rows, int P, int G, int n_items) {
+    pdl_trigger();
+    pdl_wait();
     if (hist_stream(A) != hist_stream_of(MODE)) return;  // uniform
     extern __shared__ __align__(128) uint8_t sm[];
     __shared__ ItemCtx X;
@@ -1052,7 +1054,11 @@ __device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0
     }
 }
 
-__global__ void __launch_bounds__(256, 5) k_hist_finish(const __grid_constant__ HistArgs A) { hist_finish_tiles(A, blockIdx.x, 1, blockIdx.y); }
+__global__ void __launch_bounds__(256, 5) k_hist_finish(const __grid_constant__ HistArgs A) {
+    pdl_trigger();
+    pdl_wait();
+    hist_finish_tiles(A, blockIdx.x, 1, blockIdx.y);
+}
 
 // Batched finish: items[i] = (instance, density tile, bin tile).
 __global__ void __launch_bounds__(256, 5) k_hist_finish_batched(const HistArgs *__restrict__ insts, const int4 *__restrict__ items) {
@@ -1230,8 +1236,8 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
             auto launch = [&](auto kern, int gg, int items, int mode) -> vup_status {
                 const size_t sm_bytes = hist_smem_bytes(rows, hist_warps(mode));
                 VUP_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes));
-                kern<<<items, hist_warps(mode) * 32, sm_bytes, s>>>(A, rows, P_max, gg, items);
-                VUP_CHECK_LAUNCH();
+                VUP_CHECK_CUDA(launch_pdl(kern, dim3(items), dim3(hist_warps(mode) * 32), sm_bytes, s, A, rows,
+                                          P_max, gg, items));
                 return VUP_OK;
             };
             vup_status st;
@@ -1265,8 +1271,7 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     }
     VUP_PROF("hist_fixup", s, 1);
     dim3 fg((unsigned)ceil_div64(K, kFinK), (unsigned)ceil_div64(g->B, kFinB));
-    k_hist_finish<<<fg, 32 * kFinB, 0, s>>>(A);
-    VUP_CHECK_LAUNCH();
+    VUP_CHECK_CUDA(launch_pdl(k_hist_finish, fg, dim3(32 * kFinB), 0, s, A));
     return VUP_OK;
 }
 

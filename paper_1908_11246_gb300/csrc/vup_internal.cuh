@@ -19,6 +19,31 @@
 
 #define VUP_CHECK_LAUNCH() VUP_CHECK_CUDA(cudaGetLastError())
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while the kernel before it in the stream is still running; it
+// calls pdl_wait() before touching anything that kernel reads or writes
+// (griddepcontrol.wait returns once the prerequisite grid has completed and
+// its memory is visible; without a programmatic launch it returns at once).
+// pdl_trigger() lets the next kernel be scheduled once every block of this
+// one has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 void vup_set_last_cuda_error(cudaError_t e, const char *expr, const char *file, int line);
 
 // Device status word codes (grid->dstatus[0]); the first non-zero code wins.
@@ -101,7 +126,7 @@ struct vup_grid_s {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_rec = nullptr;
     cudaStream_t side2 = nullptr;                       // the prefix-sum tiles beside the contraction
-    cudaEvent_t ev_lay = nullptr, ev_dens = nullptr, ev_pre = nullptr;
+    cudaEvent_t ev_lay = nullptr, ev_dens = nullptr, ev_pre = nullptr, ev_mom = nullptr, ev_mfin = nullptr;
 
     // counting-sort scratch
     DevBuf sort_counts, scan_tmp, lay_tmp, rec_tmp;

@@ -241,6 +241,8 @@ __device__ __forceinline__ void moments_finish_body(const float *__restrict__ pa
 __global__ void k_moments_finish(const float *__restrict__ part, int64_t n_ct, int64_t K, int64_t K_pad, int J,
                                  const DensStats *__restrict__ ds, int ndim, const double *__restrict__ scale,
                                  double *__restrict__ raw, double *__restrict__ central) {
+    pdl_trigger();
+    pdl_wait();
     moments_finish_body(part, n_ct, K, K_pad, J, ds, ndim, scale, raw, central, blockIdx.x);
 }
 
@@ -350,10 +352,9 @@ vup_status vup_moments_finish(vup_grid g, int64_t K, int n_col_tiles, double *ra
                               cudaStream_t s) {
     const int64_t K_pad = ceil_div64(K, 128) * 128;
     VUP_PROF("moments_finish_fp64", s, 1);
-    k_moments_finish<<<(unsigned)ceil_div64(K, 128), 128, 0, s>>>(
-        (const float *)g->partials.p, n_col_tiles, K, K_pad, g->J, (const DensStats *)g->dstats.p, g->ndim,
-        g->ydev_scale, raw, central);
-    VUP_CHECK_LAUNCH();
+    VUP_CHECK_CUDA(launch_pdl(k_moments_finish, dim3((unsigned)ceil_div64(K, 128)), dim3(128), 0, s,
+                              (const float *)g->partials.p, (int64_t)n_col_tiles, K, K_pad, g->J,
+                              (const DensStats *)g->dstats.p, g->ndim, (const double *)g->ydev_scale, raw, central));
     return VUP_OK;
 }
 

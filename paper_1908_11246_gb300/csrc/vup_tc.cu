@@ -184,6 +184,8 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
              int n_kb, int64_t K_pad, TcEpi ep, float *__restrict__ part, const TcInst *__restrict__ insts,
              const TcTile *__restrict__ tiles, int n_tiles_batched, int *__restrict__ dstatus, int terms = 3,
              int n_split = 1) {
+    pdl_trigger();
+    pdl_wait();
     constexpr int BKE = KIND ? BK_TF32 : BK;  // operand elements per 128-byte row
     // split reduction: n_split accumulators of at most kSplitTerms terms each
     // (the tensor cores' FP32 accumulation error grows with the reduction
@@ -501,8 +503,9 @@ vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *p
     VUP_PROF(n_out == 1 ? "moments_bf16x3_tc" : "ipsa_bf16x3_tc", s, 1);
     if (n_out == 1) {
         VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_moments_tc<1, false><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, nullptr,
-                                                            nullptr, 0, g->dstatus, 3, n_split);
+        VUP_CHECK_CUDA(launch_pdl(k_moments_tc<1, false>, dim3(grid), dim3(kThreads), smem, s, mAh, mAl, mBh, mBl, n_m,
+                                  n_n, n_kb, K_pad, ep, part, (const TcInst *)nullptr, (const TcTile *)nullptr, 0,
+                                  g->dstatus, 3, n_split));
     } else {
         VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_moments_tc<3, false><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, nullptr,
