@@ -824,97 +824,112 @@ struct RecGeom {
     int64_t n1;   // 3-D rest code: line = a0 n1 + a1 -> a0 | a1 << 15
 };
 
-__global__ void __launch_bounds__(64) k_rec_walk(const int32_t *__restrict__ bins, RecGeom Q, LaySel L,
-                                                 int32_t *__restrict__ cnt, int32_t *__restrict__ n_iv,
-                                                 uint4 *__restrict__ tmp, int32_t *__restrict__ seg_n) {
+constexpr int kWalkWarps = 8;  // segments (warps) per block of the record walk
+__global__ void __launch_bounds__(kWalkWarps * 32) k_rec_walk(const int32_t *__restrict__ bins, RecGeom Q, LaySel L,
+                                                              int32_t *__restrict__ cnt, int32_t *__restrict__ n_iv,
+                                                              uint4 *__restrict__ tmp, int32_t *__restrict__ seg_n) {
+    extern __shared__ int32_t s_rank[];  // [warps][GB]: records so far of each group of the part
     const bool tr = L.sel[0] != 0;
     const LayGeom G = L.get();
     const int64_t n_lines = tr ? Q.C : Q.R;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (tid >= (int64_t)G.P * n_lines) return;
-    const int p = (int)(tid / n_lines);
-    const int64_t line = tid - (int64_t)p * n_lines;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // one warp per segment; the warps of a block walk consecutive lines of one part
+    const int64_t seg = (int64_t)blockIdx.x * kWalkWarps + warp;
+    if (seg >= (int64_t)G.P * n_lines) return;
+    const int p = (int)(seg / n_lines);
+    const int64_t line = seg - (int64_t)p * n_lines;
     const int64_t row0 = (int64_t)p * G.part_rows, row1 = min(G.n_last, row0 + G.part_rows);
-    if (row0 >= row1) {
-        seg_n[tid] = 0;
-        return;
-    }
+    int32_t *rank = s_rank + warp * Q.GB;
+    for (int q = lane; q < Q.GB; q += 32) rank[q] = 0;
+    __syncwarp();
     const int64_t stride = tr ? Q.C : 1;
     const int32_t *src = bins + (tr ? line : line * Q.C);
-    uint4 *slot = tmp + 2 * tid * Q.cap;
+    uint4 *slot = tmp + 2 * seg * Q.cap;
 
-    int32_t bcur = -1, b1 = -1, b2 = -1;  // bins of the current interval and of the two before it
-    int rq = -1, dir = 0, rprev = -1;     // open record: group in the part, step sign, last bin
-    int32_t st[kRecBins];  // its bins' first rows (relative to row0), -1 if absent
-#pragma unroll
-    for (int j = 0; j < kRecBins; ++j) st[j] = -1;
+    // record state, the same in every lane; lane j < 8 holds st_j, the first
+    // row (relative to row0) of bin 8 rq + j in the open record, -1 if absent
+    int32_t b1 = -1, b2 = -1;  // bins of the current interval and of the one before it
+    int rq = -1, dir = 0, rprev = -1;
+    int32_t st = -1;
     int32_t niv = 0, nrec = 0;
-    int32_t cg = -1, base = 0, cc = 0;  // run of one group: its rank base and count
     auto emit = [&](int64_t e_row) {
         const int32_t e = (int32_t)(e_row - row0);
-        uint32_t w[kRecBins + 1];
+        // B_j: the least first row among the bins at or above j (rising) or
+        // below j (falling), e if none -- a suffix / prefix minimum over lanes
+        const int32_t mine = (lane < kRecBins && st >= 0) ? st : e;
+        int32_t w = mine;
+        if (dir >= 0) {
 #pragma unroll
-        for (int j = 0; j <= kRecBins; ++j) {
-            int32_t v = e;
-#pragma unroll
-            for (int jj = 0; jj < kRecBins; ++jj) {
-                const bool take = dir >= 0 ? jj >= j : jj < j;
-                if (take && st[jj] >= 0 && st[jj] < v) v = st[jj];
+            for (int o = 1; o < kRecBins; o <<= 1) {
+                const int32_t t = __shfl_down_sync(0xffffffffu, w, o);
+                if (lane + o < kRecBins) w = min(w, t);
             }
-            w[j] = (uint32_t)v;
+        } else {
+            int32_t x = __shfl_up_sync(0xffffffffu, mine, 1);  // exclusive: bins below j
+            x = lane == 0 ? e : x;
+            w = x;
+#pragma unroll
+            for (int o = 1; o < kRecBins + 1; o <<= 1) {
+                const int32_t t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w = min(w, t);
+            }
         }
-        const int32_t g = p * Q.GB + rq;
-        if (g != cg) {
-            if (cg >= 0) cnt[cg * Q.NL + line] = base + cc;
-            cg = g;
-            base = cnt[g * Q.NL + line];
-            cc = 0;
+        if (lane > kRecBins) w = 0;
+        // lanes 0, 2, 4, 6 pack (B_j, B_j+1); lane 8 holds B_8
+        const uint32_t pair = (uint32_t)w | ((uint32_t)__shfl_down_sync(0xffffffffu, w, 1) << 16);
+        const uint32_t u0 = __shfl_sync(0xffffffffu, pair, 0), u1 = __shfl_sync(0xffffffffu, pair, 2),
+                       u2 = __shfl_sync(0xffffffffu, pair, 4), u3 = __shfl_sync(0xffffffffu, pair, 6);
+        const uint32_t w8 = (uint32_t)__shfl_sync(0xffffffffu, w, kRecBins);
+        if (lane == 0) {
+            const int32_t g = p * Q.GB + rq;
+            const int32_t r = rank[rq]++;
+            slot[2 * nrec] = make_uint4(u0, u1, u2, u3);
+            slot[2 * nrec + 1] = make_uint4(w8 | (dir < 0 ? kRecNeg : 0u), (uint32_t)line, (uint32_t)g, (uint32_t)r);
         }
-        slot[2 * nrec] = make_uint4(w[0] | w[1] << 16, w[2] | w[3] << 16, w[4] | w[5] << 16, w[6] | w[7] << 16);
-        slot[2 * nrec + 1] = make_uint4(w[8] | (dir < 0 ? kRecNeg : 0u), (uint32_t)line, (uint32_t)g,
-                                        (uint32_t)(base + cc));
-        ++cc;
+        __syncwarp();
         ++nrec;
     };
-    constexpr int kAhead = 16;  // rows loaded ahead
-    for (int64_t r = row0; r < row1; r += kAhead) {
-        int32_t v[kAhead];
-#pragma unroll
-        for (int u = 0; u < kAhead; ++u) v[u] = r + u < row1 ? src[(r + u) * stride] : -1;
-#pragma unroll
-        for (int u = 0; u < kAhead; ++u) {
-            if (r + u >= row1) break;
-            const int32_t b = v[u];
-            if (b == bcur) continue;  // same interval
+    int32_t carry = -1;  // bin of the row before the window
+    for (int64_t r0w = row0; r0w < row1; r0w += 32) {
+        const int64_t r = r0w + lane;
+        const int32_t b = r < row1 ? src[r * stride] : -1;
+        int32_t bp = __shfl_up_sync(0xffffffffu, b, 1);
+        if (lane == 0) bp = carry;
+        uint32_t starts = __ballot_sync(0xffffffffu, r < row1 && b != bp);
+        carry = __shfl_sync(0xffffffffu, b, 31);
+        while (starts) {
+            const int L = __ffs(starts) - 1;
+            starts &= starts - 1;
+            const int32_t bi = __shfl_sync(0xffffffffu, b, L);
+            const int64_t ri = r0w + L;
             ++niv;
-            const int q = b / kRecBins;
+            const int q = bi / kRecBins;
             bool start;
             if (b1 < 0 || q != b1 / kRecBins) start = true;
-            else if (b2 >= 0 && b2 / kRecBins == q) start = ((b - b1) > 0) != ((b1 - b2) > 0);
+            else if (b2 >= 0 && b2 / kRecBins == q) start = ((bi - b1) > 0) != ((b1 - b2) > 0);
             else start = false;
             if (start) {
-                if (rq >= 0) emit(r + u);
+                if (rq >= 0) emit(ri);
                 rq = q;
                 dir = 0;
                 rprev = -1;
-#pragma unroll
-                for (int jj = 0; jj < kRecBins; ++jj) st[jj] = -1;
+                st = -1;
             }
-            const int j = b - q * kRecBins;
-            const int32_t rel = (int32_t)(r + u - row0);
-#pragma unroll
-            for (int jj = 0; jj < kRecBins; ++jj) st[jj] = j == jj ? rel : st[jj];
-            if (rprev >= 0 && dir == 0) dir = b > rprev ? 1 : -1;
-            rprev = b;
+            if (lane == bi - q * kRecBins) st = (int32_t)(ri - row0);
+            if (rprev >= 0 && dir == 0) dir = bi > rprev ? 1 : -1;
+            rprev = bi;
             b2 = b1;
-            b1 = b;
-            bcur = b;
+            b1 = bi;
         }
     }
-    emit(row1);
-    cnt[cg * Q.NL + line] = base + cc;
-    seg_n[tid] = nrec;
-    atomicAdd(n_iv, niv);
+    if (rq >= 0) emit(row1);
+    __syncwarp();
+    for (int q = lane; q < Q.GB; q += 32)
+        if (rank[q]) cnt[((int64_t)p * Q.GB + q) * Q.NL + line] = rank[q];
+    if (lane == 0) {
+        seg_n[seg] = nrec;
+        atomicAdd(n_iv, niv);
+    }
 }
 
 // Every record from its segment slot to its place in (group, line, row)
@@ -1474,7 +1489,11 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
             Q.n1 = g->ndim == 3 ? g->n[1] : 1;
             VUP_CHECK_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(int32_t) * (size_t)Lr, s));
             VUP_CHECK_CUDA(cudaMemsetAsync(HL.n_iv, 0, sizeof(int32_t), s));
-            k_rec_walk<<<(unsigned)ceil_div64(walkers, 64), 64, 0, s>>>(g->bins, Q, L, rcnt, HL.n_iv, rslot, seg_n);
+            const size_t wsm = sizeof(int32_t) * (size_t)kWalkWarps * GB;
+            if (wsm > 48 * 1024)
+                VUP_CHECK_CUDA(cudaFuncSetAttribute(k_rec_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+            k_rec_walk<<<(unsigned)ceil_div64(walkers, kWalkWarps), kWalkWarps * 32, wsm, s>>>(g->bins, Q, L, rcnt,
+                                                                                             HL.n_iv, rslot, seg_n);
             VUP_CHECK_LAUNCH();
             if ((st = scan_exclusive(rcnt, rstart, Lr, scratch, s)) != VUP_OK) return st;
             k_rec_goff<<<(n_groups + 2 + 255) / 256, 256, 0, s>>>(rstart, rcnt, Lr, NL, n_groups,

@@ -925,7 +925,9 @@ __global__ void __launch_bounds__(kHistWarps * 32, 1) k_hist_global(HistArgs A, 
 // once to FP32) so that rows a .. b - 1 sum to P[b] - P[a].  Tile (p, k-tile)
 // is one contiguous block of pre_rows x 128 floats, copied as is into the
 // histogram kernel's shared memory.  Returns at once when the device chose
-// the point stream, whose tile holds the scaled factors themselves.
+// the point stream, whose tile holds the scaled factors themselves.  Loads
+// and stores are marked evict-first: the kernel runs beside the contraction,
+// whose operands should keep L2.
 __device__ __forceinline__ void prefix_tile(const HistArgs &A, const LayoutArgs &H, float *__restrict__ out, int p,
                                             int64_t k) {
     const int64_t row0 = (int64_t)p * H.part_rows;
@@ -938,18 +940,18 @@ __device__ __forceinline__ void prefix_tile(const HistArgs &A, const LayoutArgs 
     for (int64_t a = 0; a < nrows; a += kAhead) {
         float v[kAhead];
 #pragma unroll
-        for (int u = 0; u < kAhead; ++u) v[u] = a + u < nrows ? src[(a + u) * A.K_pad] : 0.f;
+        for (int u = 0; u < kAhead; ++u) v[u] = a + u < nrows ? __ldcs(src + (a + u) * A.K_pad) : 0.f;
 #pragma unroll
         for (int u = 0; u < kAhead; ++u) {
             if (a + u >= nrows) break;
-            dst[(a + u) * kKT] = sh + sl;
+            __stcs(dst + (a + u) * kKT, sh + sl);
             const float x = v[u] * iz;
             const float t = sh + x, bb = t - sh;
             sl += (sh - (t - bb)) + (x - bb);
             sh = t;
         }
     }
-    dst[nrows * kKT] = sh + sl;
+    __stcs(dst + nrows * kKT, sh + sl);
 }
 
 __global__ void __launch_bounds__(128) k_prefix_tiles(const __grid_constant__ HistArgs A, float *__restrict__ out,
