@@ -322,7 +322,7 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
     if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
     ALLOC(g->y, sizeof(double) * N);
     ALLOC(g->axis_terms, sizeof(double2) * (size_t)(g->n[0] + (ndim > 1 ? g->n[1] : 0) + (ndim > 2 ? g->n[2] : 0)));
-    ALLOC(g->ext, sizeof(unsigned long long) * 2);
+    ALLOC(g->ext, sizeof(unsigned long long) * 3);  // range keys (min, max) and a grid-barrier counter
     ALLOC(g->bins, sizeof(int32_t) * N);
     ALLOC(g->perm, sizeof(int32_t) * N);
     g->n_layouts = ndim == 2 ? 2 : 1;

@@ -219,43 +219,77 @@ __global__ void k_axis_terms(GridGeom G, int model, Theta th, double2 *__restric
     }
 }
 
+// Axis indices of a grid-stride walk over the flat index: decomposed once,
+// then advanced by the stride's own decomposition with carries (no division
+// per point).
+struct IndexWalk {
+    int32_t a[3], d[3], n[3];
+    int ndim;
+    __device__ __forceinline__ IndexWalk(const GridGeom &G, int64_t i0, int64_t step) : ndim(G.ndim) {
+        int64_t r = i0, t = step;
+        for (int q = 2; q >= 0; --q) {
+            const int64_t nq = q < ndim ? G.n[q] : 1;
+            n[q] = (int32_t)nq;
+            a[q] = (int32_t)(r % nq);
+            d[q] = (int32_t)(t % nq);
+            r /= nq;
+            t /= nq;
+        }
+        // the leading axis takes the rest of the stride without wrapping
+        if (ndim >= 1) d[0] += (int32_t)(t * (int64_t)n[0]);
+    }
+    __device__ __forceinline__ void next() {
+        int32_t c = 0;
+        for (int q = 2; q >= 1; --q) {
+            if (q >= ndim) continue;
+            int32_t v = a[q] + d[q] + c;
+            c = v >= n[q] ? 1 : 0;
+            a[q] = c ? v - n[q] : v;
+        }
+        a[0] += d[0] + c;
+    }
+};
+
+// y at axis indices a of a separable built-in model from its per-axis terms
+// (bit-identical to the per-point evaluation).
+__device__ __forceinline__ double combine_terms(const int32_t *a, const GridGeom &G, int model, const Theta &th,
+                                                const double2 *__restrict__ terms) {
+    const int64_t o1 = G.n[0], o2 = G.n[0] + G.n[1];
+    double v;
+    switch (model) {
+    case VUP_MODEL_SIN_SIN2_2D:
+    case VUP_MODEL_IPSA_EXAMPLE_2D:
+        v = __dadd_rn(terms[a[0]].x, terms[o1 + a[1]].x);
+        break;
+    case VUP_MODEL_MIXED_3D: {
+        const double s1 = terms[a[0]].x, b = terms[o1 + a[1]].x, c = terms[o2 + a[2]].x;
+        v = __dadd_rn(__dadd_rn(s1, b), __dmul_rn(c, s1));
+        break;
+    }
+    default: {  // VUP_MODEL_POLY
+        v = th.t[0];
+        int64_t off = 0;
+        for (int d = 0; d < G.ndim; ++d) {
+            const double2 t = terms[off + a[d]];
+            v = __dadd_rn(v, t.x);
+            v = __dadd_rn(v, t.y);
+            off += G.n[d];
+        }
+        break;
+    }
+    }
+    return v;
+}
+
 __global__ void k_model_combine(double *__restrict__ y, int64_t N, GridGeom G, int model, Theta th,
                                 const double2 *__restrict__ terms, unsigned long long *ext) {
     pdl_trigger();
     pdl_wait();
-    const int64_t o1 = G.n[0], o2 = G.n[0] + G.n[1];
     unsigned long long mn = ~0ull, mx = 0ull;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t a[3];
-        int64_t rem = i;
-        for (int d = G.ndim - 1; d >= 0; --d) {
-            a[d] = rem % G.n[d];
-            rem /= G.n[d];
-        }
-        double v;
-        switch (model) {
-        case VUP_MODEL_SIN_SIN2_2D:
-        case VUP_MODEL_IPSA_EXAMPLE_2D:
-            v = __dadd_rn(terms[a[0]].x, terms[o1 + a[1]].x);
-            break;
-        case VUP_MODEL_MIXED_3D: {
-            const double s1 = terms[a[0]].x, b = terms[o1 + a[1]].x, c = terms[o2 + a[2]].x;
-            v = __dadd_rn(__dadd_rn(s1, b), __dmul_rn(c, s1));
-            break;
-        }
-        default: {  // VUP_MODEL_POLY
-            v = th.t[0];
-            int64_t off = 0;
-            for (int d = 0; d < G.ndim; ++d) {
-                const double2 t = terms[off + a[d]];
-                v = __dadd_rn(v, t.x);
-                v = __dadd_rn(v, t.y);
-                off += G.n[d];
-            }
-            break;
-        }
-        }
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, step = (int64_t)gridDim.x * blockDim.x;
+    IndexWalk w(G, i0, step);
+    for (int64_t i = i0; i < N; i += step, w.next()) {
+        const double v = combine_terms(w.a, G, model, th, terms);
         y[i] = v;
         const unsigned long long kv = dkey(v);
         mn = kv < mn ? kv : mn;
@@ -371,6 +405,79 @@ __global__ void k_bins_scale(const double *__restrict__ y, int64_t N, int B, con
         b2[i] = make_int2(rule(v.x), rule(v.y));
     }
     if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) bins[N - 1] = rule(y[N - 1]);
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident): one
+// counter, zeroed before the launch, that every block increments once; the
+// wait is bounded (the device status records an expired wait and the
+// caller's blocks return false).
+constexpr uint32_t kGridSpin = 1u << 22;
+__device__ __forceinline__ bool grid_barrier(unsigned long long *ctr, int *dstatus) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1ull);
+        int ok = 1;
+        for (uint32_t i = 0; *reinterpret_cast<volatile unsigned long long *>(ctr) < gridDim.x; ++i) {
+            if (i > kGridSpin) {
+                atomicCAS(dstatus, 0, VUP_DSTAT_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Model evaluation and bins of a separable built-in model on a 2-D / 3-D
+// grid in one cooperative launch: y and its exact range (as k_model_combine),
+// a grid-wide barrier, then the bins (Eq. 4, as k_bins_scale) from the
+// values each thread kept, and the power-table scale.  ext[2] is the barrier
+// counter.
+constexpr int kKeepY = 8;  // values of y a thread keeps in registers across the barrier
+__global__ void __launch_bounds__(256) k_model_bins(double *__restrict__ y, int64_t N, GridGeom G, int model,
+                                                    Theta th, const double2 *__restrict__ terms,
+                                                    unsigned long long *ext, int B, int32_t *__restrict__ bins,
+                                                    double *s_out, int *dstatus) {
+    pdl_trigger();
+    pdl_wait();
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, step = (int64_t)gridDim.x * blockDim.x;
+    double keep[kKeepY];
+    unsigned long long mn = ~0ull, mx = 0ull;
+    IndexWalk w(G, i0, step);
+    auto value = [&](int64_t i) {
+        const double v = combine_terms(w.a, G, model, th, terms);
+        w.next();
+        y[i] = v;
+        const unsigned long long kv = dkey(v);
+        mn = kv < mn ? kv : mn;
+        mx = kv > mx ? kv : mx;
+        return v;
+    };
+#pragma unroll
+    for (int q = 0; q < kKeepY; ++q) {
+        const int64_t i = i0 + q * step;
+        keep[q] = i < N ? value(i) : 0.0;
+    }
+    for (int64_t i = i0 + kKeepY * step; i < N; i += step) value(i);
+    range_reduce(mn, mx, ext);
+    if (!grid_barrier(ext + 2, dstatus)) return;
+    const BinRule rule(ext, B);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double sc = fmax(fabs(rule.ymin), fabs(rule.ymax));
+        s_out[0] = sc > 0.0 ? sc : 1.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kKeepY; ++q) {
+        const int64_t i = i0 + q * step;
+        if (i < N) bins[i] = rule(keep[q]);
+    }
+    for (int64_t i = i0 + kKeepY * step; i < N; i += step) bins[i] = rule(y[i]);
 }
 
 // A kernel of the key-sorted streams' build returns at once when the device
@@ -1253,15 +1360,36 @@ vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta, 
     const bool sep = model_separable(model_id, g->ndim);
     VUP_PROF("model_eval", s, sep ? 2 : 1);
     VUP_CHECK_CUDA(cudaMemsetAsync(g->ext, 0xff, sizeof(unsigned long long), s));
-    VUP_CHECK_CUDA(cudaMemsetAsync(g->ext + 1, 0x00, sizeof(unsigned long long), s));
+    VUP_CHECK_CUDA(cudaMemsetAsync(g->ext + 1, 0x00, 2 * sizeof(unsigned long long), s));
+    g->bins_ready = 0;
     if (sep) {
         int64_t nmax = 1;
         for (int d = 0; d < g->ndim; ++d) nmax = std::max(nmax, g->n[d]);
         VUP_CHECK_CUDA(launch_pdl(k_axis_terms, dim3((unsigned)ceil_div64(nmax, 128)), dim3(128), 0, s, G, model_id, th,
                                   g->axis_terms));
         VUP_CHECK_LAUNCH();
-        VUP_CHECK_CUDA(launch_pdl(k_model_combine, dim3(blocks), dim3(256), 0, s, g->y, g->N, G, model_id, th,
-                                  (const double2 *)g->axis_terms, g->ext));
+        if (g->ndim >= 2) {
+            // values, range and bins in one cooperative launch (every block resident)
+            static int per_sm = 0;
+            if (!per_sm) VUP_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_model_bins, 256, 0));
+            const int cb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(g->N, 256),
+                                                                        (int64_t)vup_num_sms() * std::max(1, per_sm)));
+            double *y = g->y;
+            int64_t N = g->N;
+            const double2 *terms = (const double2 *)g->axis_terms;
+            unsigned long long *ext = g->ext;
+            int B = g->B;
+            int32_t *bins = g->bins;
+            double *sc = g->ydev_scale;
+            int *dstatus = g->dstatus;
+            int mid = model_id;
+            void *args[] = {&y, &N, &G, &mid, &th, &terms, &ext, &B, &bins, &sc, &dstatus};
+            VUP_CHECK_CUDA(cudaLaunchCooperativeKernel((const void *)k_model_bins, dim3(cb), dim3(256), args, 0, s));
+            g->bins_ready = 1;
+        } else {
+            VUP_CHECK_CUDA(launch_pdl(k_model_combine, dim3(blocks), dim3(256), 0, s, g->y, g->N, G, model_id, th,
+                                      (const double2 *)g->axis_terms, g->ext));
+        }
     } else {
         k_model_eval<<<blocks, 256, 0, s>>>(g->y, g->N, G, model_id, th, g->ext);
     }
@@ -1323,7 +1451,9 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     const int64_t N = g->N;
     const int B = g->B;
     ProfScope prof("range_bins", s, 0);
-    int launches = g->ndim == 1 ? 2 : 1;  // scale, bins
+    const bool bins_done = g->bins_ready && g->range_ready;  // the model kernel wrote them
+    g->bins_ready = 0;
+    int launches = g->ndim == 1 ? 2 : (bins_done ? 0 : 1);  // scale, bins
     // exact range of y (already reduced by the model kernels for built-in models)
     int blocks = (int)std::min<int64_t>(ceil_div64(N, 256), (int64_t)vup_num_sms() * 8);
     if (!g->range_ready) {
@@ -1388,7 +1518,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
                     cudaFuncSetAttribute(k_bins_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_bins_count<<<(unsigned)ceil_div64(n_tiles, nw), 32 * nw, smem, s>>>(g->y, N, B, g->ext, g->bins,
                                                                                 counts, n_tiles);
-        } else {
+        } else if (!bins_done) {
             const int bb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div64(N / 2, 256), (int64_t)vup_num_sms() * 8));
             VUP_CHECK_CUDA(launch_pdl(k_bins_scale, dim3(bb), dim3(256), 0, s, (const double *)g->y, N, B,
                                       (const unsigned long long *)g->ext, g->bins, g->ydev_scale));

@@ -121,6 +121,7 @@ struct vup_grid_s {
     int layout_valid = 0;          // the histogram layout matches the current bins
     int layout_has_points = 0;     // ... and its key-sorted streams were built on request
     int range_ready = 0;           // ext holds the range of y (reduced by the model kernels)
+    int bins_ready = 0;            // the model kernel also wrote the bins and the power-table scale
     // second stream for the layout build beside the density preparation
     // (forked from and joined back into the caller's stream)
     cudaStream_t side = nullptr;
