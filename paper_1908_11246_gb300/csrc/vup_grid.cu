@@ -438,12 +438,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *ctr, int *dstat
 // grid in one cooperative launch: y and its exact range (as k_model_combine),
 // a grid-wide barrier, then the bins (Eq. 4, as k_bins_scale) from the
 // values each thread kept, and the power-table scale.  ext[2] is the barrier
-// counter.
+// counter.  With zh / zl given, also the contraction's split BF16 power table
+// of the rest-row orientation (as k_power_table_bf16<true>: y[rest * R + red]
+// -> [rest * 4 + j][red], row stride ld, zeros in the padding up to Qext rests
+// and ld reds).
 constexpr int kKeepY = 8;  // values of y a thread keeps in registers across the barrier
 __global__ void __launch_bounds__(256) k_model_bins(double *__restrict__ y, int64_t N, GridGeom G, int model,
                                                     Theta th, const double2 *__restrict__ terms,
                                                     unsigned long long *ext, int B, int32_t *__restrict__ bins,
-                                                    double *s_out, int *dstatus) {
+                                                    double *s_out, int *dstatus, __nv_bfloat16 *__restrict__ zh,
+                                                    __nv_bfloat16 *__restrict__ zl, int64_t R, int64_t ld,
+                                                    int64_t Qext) {
     pdl_trigger();
     pdl_wait();
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, step = (int64_t)gridDim.x * blockDim.x;
@@ -472,12 +477,55 @@ __global__ void __launch_bounds__(256) k_model_bins(double *__restrict__ y, int6
         const double sc = fmax(fabs(rule.ymin), fabs(rule.ymax));
         s_out[0] = sc > 0.0 ? sc : 1.0;
     }
+    const double smax = fmax(fabs(rule.ymin), fabs(rule.ymax));
+    const double inv = 1.0 / (smax > 0.0 ? smax : 1.0);  // 1 / the power-table scale
+    IndexWalk w2(G, i0, step);  // rest = a0, red = the remaining axes' flat index
+    auto table = [&](double v) {
+        const int64_t rest = w2.a[0], red = G.ndim == 3 ? (int64_t)w2.a[1] * G.n[2] + w2.a[2] : w2.a[1];
+        w2.next();
+        const float z = (float)__dmul_rn(v, inv);
+        float p = z;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j) p *= z;
+            const __nv_bfloat16 hh = __float2bfloat16_rn(p);
+            const int64_t idx = (rest * 4 + j) * ld + red;
+            zh[idx] = hh;
+            zl[idx] = __float2bfloat16_rn(p - __bfloat162float(hh));
+        }
+    };
 #pragma unroll
     for (int q = 0; q < kKeepY; ++q) {
         const int64_t i = i0 + q * step;
-        if (i < N) bins[i] = rule(keep[q]);
+        if (i < N) {
+            bins[i] = rule(keep[q]);
+            if (zh) table(keep[q]);
+        }
     }
-    for (int64_t i = i0 + kKeepY * step; i < N; i += step) bins[i] = rule(y[i]);
+    for (int64_t i = i0 + kKeepY * step; i < N; i += step) {
+        const double v = y[i];
+        bins[i] = rule(v);
+        if (zh) table(v);
+    }
+    if (zh) {
+        // padding: reds R .. ld of every rest, and every red of rests Q .. Qext
+        const int64_t Q = N / R, pad_r = ld - R, n_pad = Q * pad_r + (Qext - Q) * ld;
+        for (int64_t e = i0; e < n_pad * 4; e += step) {
+            const int64_t c = e >> 2, j = e & 3;
+            int64_t rest, red;
+            if (c < Q * pad_r) {
+                rest = c / pad_r;
+                red = R + (c - rest * pad_r);
+            } else {
+                const int64_t c2 = c - Q * pad_r;
+                rest = Q + c2 / ld;
+                red = c2 - (rest - Q) * ld;
+            }
+            const int64_t idx = (rest * 4 + j) * ld + red;
+            zh[idx] = __float2bfloat16_rn(0.f);
+            zl[idx] = __float2bfloat16_rn(0.f);
+        }
+    }
 }
 
 // A kernel of the key-sorted streams' build returns at once when the device
@@ -1383,7 +1431,18 @@ vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta, 
             double *sc = g->ydev_scale;
             int *dstatus = g->dstatus;
             int mid = model_id;
-            void *args[] = {&y, &N, &G, &mid, &th, &terms, &ext, &B, &bins, &sc, &dstatus};
+            // the tensor-core orientation's split BF16 power table as well
+            // (built here for the default precision; kept until the next model)
+            const int to = vup_tc_orient(g);
+            const Orient &o = g->orient[to];
+            int64_t ld = o.R_pad, R = o.R, Qext = ceil_div64(o.NC, 256) * 256 / 4;
+            const size_t tbytes = sizeof(__nv_bfloat16) * (size_t)ld * (size_t)(Qext * 4);
+            if (!g->zt_hi[to]) {
+                VUP_CHECK_CUDA(cudaMalloc(&g->zt_hi[to], tbytes));
+                VUP_CHECK_CUDA(cudaMalloc(&g->zt_lo[to], tbytes));
+            }
+            __nv_bfloat16 *zh = g->zt_hi[to], *zl = g->zt_lo[to];
+            void *args[] = {&y, &N, &G, &mid, &th, &terms, &ext, &B, &bins, &sc, &dstatus, &zh, &zl, &R, &ld, &Qext};
             VUP_CHECK_CUDA(cudaLaunchCooperativeKernel((const void *)k_model_bins, dim3(cb), dim3(256), args, 0, s));
             g->bins_ready = 1;
         } else {
@@ -1536,6 +1595,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     g->layout_valid = g->ndim == 1;
     prof.launches = launches;
     for (int o = 0; o < kNumOrient; ++o) g->have_tab[o][0] = g->have_tab[o][1] = g->have_tab[o][2] = 0;
+    if (bins_done) g->have_tab[vup_tc_orient(g)][1] = 1;  // written with the bins
     return VUP_OK;
 }
 
