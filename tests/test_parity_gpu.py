@@ -395,3 +395,53 @@ def test_tf32_single_product_is_report_only_accuracy():
     err = (np.abs(raw - res["raw"]) / scale).max()
     assert 1e-7 < err < 5e-3, err
     Hp.check_hist(hs, res["hist"])
+
+
+@pytest.mark.parametrize("prob", [I.config("c2", "small"), I.config("c3", "small"), I.random_problem(411, ndim=2)],
+                         ids=["c2", "c3", "ragged2d"])
+def test_cooperative_model_bins_match_separate_kernels(prob):
+    """A built-in separable model's values, bins and BF16 power table come
+    from one cooperative launch; caller-supplied outputs (the same y) take
+    the separate range, bins and table kernels.  Bins, moments and histograms
+    must be bit-identical (the table bits decide the moments)."""
+    vup = vupmod()
+    dd = vup.densities_to_device(prob.dens)
+    ga = vup.Grid(prob.n, prob.lo, prob.hi)
+    ga.eval_model(prob.model_id, prob.theta, prob.n_bins, prob.n_moments)
+    ra, _, ha = ga.propagate(dd, "bf16x3", True, False, True)
+    ga.sync()
+    y = ga.array("y")
+    gb = vup.Grid(prob.n, prob.lo, prob.hi)
+    gb.set_outputs(y, prob.n_bins, prob.n_moments)
+    rb, _, hb = gb.propagate(dd, "bf16x3", True, False, True)
+    gb.sync()
+    np.testing.assert_array_equal(ga.array("bins").cpu().numpy(), gb.array("bins").cpu().numpy())
+    np.testing.assert_array_equal(ra.cpu().numpy(), rb.cpu().numpy())
+    np.testing.assert_array_equal(ha.cpu().numpy(), hb.cpu().numpy())
+    ga.close()
+    gb.close()
+
+
+def test_profile_timeline_spans_the_streams():
+    """vup_profile_timeline: every timed group with its launching stream and
+    begin / end times; a propagation that builds its layout uses three streams."""
+    vup = vupmod()
+    prob = I.config("c2", "small")
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    dd = vup.densities_to_device(prob.dens)
+    vup.vup_profile(True)
+    try:
+        g.eval_model(prob.model_id, prob.theta, prob.n_bins, prob.n_moments)
+        g.propagate(dd, "bf16x3")
+        g.sync()
+        tl = vup.vup_profile_timeline()
+        agg = vup.vup_profile_read()
+    finally:
+        vup.vup_profile(False)
+    names = {n for n, _, _, _, _ in tl}
+    assert {"model_eval", "density_prep", "hist_segmented", "hist_fixup"} <= names
+    assert names == set(agg)
+    for n, sid, launches, b, e in tl:
+        assert 0.0 <= b <= e and launches >= 0
+    assert len({sid for _, sid, _, _, _ in tl}) == 3
+    g.close()
