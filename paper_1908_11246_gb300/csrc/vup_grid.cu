@@ -972,7 +972,7 @@ constexpr uint32_t kRecEnd = 1u << 31;  // last record of its group
 // along the line, [B_j+1, B_j) when they fall.
 struct RecGeom {
     int64_t R, C;
-    int B, GB;
+    int GB;       // groups of kRecBins bins per part
     int64_t NL;   // line stride of the count matrix (the most lines of either layout)
     int64_t cap;  // slots per segment (the most part rows)
     int ndim;
@@ -1538,7 +1538,6 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
             HL.P = vup_hist_parts_for(HL.n_last, B);
             HL.part_rows = ceil_div64(HL.n_last, HL.P);
             Bk_max = std::max(Bk_max, HL.P * B);
-            Bk_max = std::max(Bk_max, HL.P * (int)ceil_div64(B, kRecBins) + 1);  // record sort
             g->hist_P = std::max(g->hist_P, HL.P);
         }
         auto &HL = g->hl[0];
@@ -1671,7 +1670,6 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
             RecGeom Q;
             Q.R = Rn;
             Q.C = Cn;
-            Q.B = B;
             Q.GB = GB;
             Q.NL = NL;
             Q.cap = cap;

@@ -772,18 +772,18 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
             if (c_lo + ci >= c_hi) break;
             if (!rec_chunk_walk<NF>(X, p * X.C_rec + c_lo + ci, p, k, ws, win, mbar, wseq, abort)) return;
         }
-        return;
-    }
-    for (;;) {
-        int ci = 0;
-        if (lane == 0) ci = atomicAdd(next_chunk, 1);
-        ci = __shfl_sync(0xffffffffu, ci, 0);
-        if (ci >= X.group_chunks) break;
-        const int wc = cg * X.group_chunks + ci;
-        bool ok;
-        if constexpr (MODE == 1) ok = iv_chunk<NF>(X, p * X.C + wc, p, k, ws, win, mbar, wseq, abort);
-        else ok = run_chunk(wc);
-        if (!ok) return;
+    } else {
+        for (;;) {
+            int ci = 0;
+            if (lane == 0) ci = atomicAdd(next_chunk, 1);
+            ci = __shfl_sync(0xffffffffu, ci, 0);
+            if (ci >= X.group_chunks) break;
+            const int wc = cg * X.group_chunks + ci;
+            bool ok;
+            if constexpr (MODE == 1) ok = iv_chunk<NF>(X, p * X.C + wc, p, k, ws, win, mbar, wseq, abort);
+            else ok = run_chunk(wc);
+            if (!ok) return;
+        }
     }
 }
 
