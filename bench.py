@@ -623,9 +623,11 @@ def main():
         "config": cfg,
         "roofline": roof,
         "kernels": {"per_step": per_step, "stage_ms_per_step": stage, "roofline": kern_roof,
-                    "timing": ("CUDA events per kernel group inside the timed region (the layout build runs "
-                               "on a second stream beside the density preparation and the contraction, so "
-                               "group times can add up to more than ms_per_step)") if profile_live
+                    "timing": ("CUDA events per kernel group inside the timed region, on each group's own "
+                               "stream: the layout build runs on a second stream beside the density "
+                               "preparation and the contraction, the prefix tiles and the FP64 moments finish "
+                               "on a third (the finish waits there for SM room beside the histogram), so "
+                               "group spans overlap and can add up to more than ms_per_step") if profile_live
                     else "per-stage CUDA events from a second pass of the same steps (stage by stage)"},
         "gpu_launches": int(sum(v[0] for v in prof.values())),
         "clocks": clk,
