@@ -128,10 +128,16 @@ vup_status vup_grid_destroy(vup_grid g);
  * Evaluate a built-in model on the grid and build the model matrix (Sec. 2
  * model function; Algorithm "VUP - Single probability" steps 1-2 and the
  * sparse model-matrix construction; Eq. MUP):
- *   y_i = M(x_i; theta) in FP64, [min y, max y], per-point bin ids,
- *   a stable counting sort of the grid points by bin (the CSR form of the
- *   one-hot model matrix), and the power tables (y / s)^j, j = 1..n_moments,
- *   with s = max(|min y|, |max y|).
+ *   y_i = M(x_i; theta) in FP64, [min y, max y], per-point bin ids; on 1-D
+ *   grids a stable counting sort of the grid points by bin (the CSR form of
+ *   the one-hot model matrix), on 2-D / 3-D grids the sorted histogram
+ *   layout is built by the first vup_propagate that needs it; the power
+ *   tables (y / s)^j, j = 1..n_moments, with s = max(|min y|, |max y|), are
+ *   built on first use, except that a separable built-in model on a 2-D /
+ *   3-D grid writes the tensor-core contraction's split BF16 table here: its
+ *   values, range, bins and that table come from one cooperative launch,
+ *   whose blocks meet at a bounded grid barrier (an expired wait is reported
+ *   by vup_sync as VUP_ERR_TIMEOUT).
  * theta: host array of n_theta doubles (n_theta <= 8).
  * 1 <= n_bins <= VUP_MAX_BINS, 1 <= n_moments <= VUP_MAX_MOMENTS.
  * Model values must be finite.
@@ -159,6 +165,13 @@ vup_status vup_set_outputs(vup_grid g, const double *y_dev, int n_bins, int n_mo
  * and never stored.  The first call with a larger K than before allocates
  * per-K scratch (not capturable in a CUDA graph), and the first TF32 call on
  * a grid builds its TF32 power tables; later calls allocate nothing.
+ * When the histogram's layout is (re)built by the call (the first call after
+ * vup_eval_model or vup_set_outputs), the grid runs parts of the work on two
+ * streams of its own (the layout beside the density preparation and the
+ * contraction; the prefix sums and the FP64 moments finish beside those) that
+ * fork from and join back into `stream`: every result is complete, in stream
+ * order, once the work queued on `stream` by this call is.  The grid creates
+ * those streams and their events on first use.
  */
 vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_precision precision,
                          double *moments_raw, double *moments_central, float *hist,
