@@ -61,6 +61,9 @@ def lib():
             l.oracle_ipsa.restype = C.c_int
             l.oracle_ipsa.argtypes = ([C.c_int, ip64, dp, dp, dp, C.c_int, C.c_int64, ip64]
                                       + dens + [dp, dp, C.c_int])
+            l.oracle_ipsa_scale.restype = C.c_int
+            l.oracle_ipsa_scale.argtypes = ([C.c_int, ip64, dp, dp, dp, C.c_int, C.c_int64, ip64]
+                                            + dens + [dp, dp, C.c_int])
             l.oracle_model_at.restype = C.c_int
             l.oracle_model_at.argtypes = [C.c_int, dp, C.c_int, C.c_int64, dp, dp]
             l.oracle_deviation_moments.restype = C.c_int
@@ -183,6 +186,26 @@ def ipsa(n, lo, hi, y, J, dens, rows=None, threads=0):
     if rc:
         raise OracleError("a selected distribution has an empty support on the grid")
     return dmu, dsg
+
+
+def ipsa_scale(n, lo, hi, y, J, dens, rows=None, threads=0):
+    """Condition scale of the IPSA sensitivities, shape [S, ndim, J] each:
+    sum_i W |s_p| |y|^j + |sbar_p| sum_i W |y|^j for p = mu and sigma (the sum
+    of the absolute values of the products that make up dM_j/dp)."""
+    K = dens.K
+    rows = np.arange(K, dtype=np.int64) if rows is None else np.asarray(rows, np.int64)
+    S, nd = rows.size, len(n)
+    cmu = np.empty((S, nd, J)); csg = np.empty((S, nd, J))
+    n64 = np.asarray(n, np.int64)
+    y = _f64(y)
+    lo64, hi64 = _f64(lo), _f64(hi)
+    dargs, keep = _dens_args(dens)
+    rc = lib().oracle_ipsa_scale(nd, _p(n64, C.c_int64), _p(lo64, C.c_double), _p(hi64, C.c_double),
+                                 _p(y, C.c_double), int(J), S, _p(rows, C.c_int64), *dargs,
+                                 _p(cmu, C.c_double), _p(csg, C.c_double), int(threads))
+    if rc:
+        raise OracleError("a selected distribution has an empty support on the grid")
+    return cmu, csg
 
 
 def solve(problem, rows=None, threads=0):

@@ -418,6 +418,81 @@ int oracle_ipsa(int ndim, const int64_t *n, const double *lo, const double *hi, 
     return status;
 }
 
+/*
+ * Condition scale of the IPSA sensitivities above (test infrastructure for
+ * the tolerance of a reduced-precision computation of the same sums).  The
+ * derivative is a covariance, dM_j/dp = sum_i W s_p y^j - sbar_p sum_i W y^j;
+ * the sum of the absolute values of all of its products is
+ *   cmu[s][d][j-1] = sum_i W |s_mu| |y|^j + |sbar_mu| sum_i W |y|^j,
+ *   csg[s][d][j-1] = sum_i W  s_sg  |y|^j +  sbar_sg  sum_i W |y|^j,
+ * the quantity a rounding error relative to each product is measured
+ * against (as sum_i W |y|^j is for the raw moments).  Every axis gets its
+ * scale, uniform ones included.  Outputs [n_sel][ndim][J].
+ */
+int oracle_ipsa_scale(int ndim, const int64_t *n, const double *lo, const double *hi, const double *y,
+                      int J, int64_t n_sel, const int64_t *k_sel, int64_t K, const uint8_t *kind,
+                      const double *mu, const double *sigma, const double *tlo, const double *thi,
+                      double *cmu, double *csg, int nthreads)
+{
+    oracle_dens D = {ndim, n, lo, hi, K, kind, mu, sigma, tlo, thi};
+    int64_t N = 1;
+    for (int d = 0; d < ndim; ++d) N *= n[d];
+    int status = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        double *W = (double *)malloc(sizeof(double) * (size_t)N);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t s = 0; s < n_sel; ++s) {
+            int64_t k = k_sel[s];
+            double Z = weights(&D, k, N, W);
+            if (!(Z > 0.0)) {
+#pragma omp atomic write
+                status = 5;
+                continue;
+            }
+            for (int d = 0; d < ndim; ++d) {
+                int64_t p = k * ndim + d;
+                double m = mu[p], sg = sigma[p];
+                double sbar_mu = 0.0, sbar_sg = 0.0;
+                for (int64_t i = 0; i < N; ++i) {
+                    int64_t a[3];
+                    unflatten(ndim, n, i, a);
+                    double x = oracle_grid_coord(lo[d], hi[d], n[d], a[d]);
+                    double u = x - m;
+                    sbar_mu += W[i] * (u / (sg * sg));
+                    sbar_sg += W[i] * ((u * u) / (sg * sg * sg));
+                }
+                for (int j = 1; j <= J; ++j) {
+                    double am = 0.0, as = 0.0, ay = 0.0;
+                    for (int64_t i = 0; i < N; ++i) {
+                        int64_t a[3];
+                        unflatten(ndim, n, i, a);
+                        double x = oracle_grid_coord(lo[d], hi[d], n[d], a[d]);
+                        double u = x - m;
+                        double smu = u / (sg * sg);
+                        double ssg = (u * u) / (sg * sg * sg);
+                        double pw = 1.0;
+                        for (int e = 0; e < j; ++e) pw = pw * fabs(y[i]);
+                        am += W[i] * fabs(smu) * pw;
+                        as += W[i] * ssg * pw;
+                        ay += W[i] * pw;
+                    }
+                    int64_t o = (s * ndim + d) * J + (j - 1);
+                    cmu[o] = am + fabs(sbar_mu) * ay;
+                    csg[o] = as + sbar_sg * ay;
+                }
+            }
+        }
+        free(W);
+    }
+    return status;
+}
+
 /* ------------------------------------------------------------------------
  * IPSA coarse-grained quantities (Sec. 5.2)
  * ---------------------------------------------------------------------- */

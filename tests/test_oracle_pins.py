@@ -320,6 +320,53 @@ def test_ipsa_uniform_axes_are_zero():
     assert dmu[0, 1, 0] != 0
 
 
+def _abs_normal_moment(p):
+    """E|u|^p for a standard normal u: 2^(p/2) Gamma((p+1)/2) / sqrt(pi)."""
+    return 2 ** (p / 2) * math.gamma((p + 1) / 2) / math.sqrt(math.pi)
+
+
+def test_ipsa_scale_closed_forms():
+    """Condition scale of dM_j/dmu and dM_j/dsigma (sums of |products|):
+    y = a x under a centred Gaussian gives sbar_mu = 0, sbar_sigma = 1/sigma and
+    cmu_j = |a sigma|^j E|u|^(j+1) / sigma,
+    csg_j = |a sigma|^j (E|u|^(j+2) + E|u|^j) / sigma, u standard normal."""
+    sg, a = 0.35, -1.7
+    n, lo, hi = (20000,), (-8 * sg,), (8 * sg,)
+    y = O.eval_model(I.MODEL_POLY, (0.0, a, 0.0), n, lo, hi)
+    cmu, csg = O.ipsa_scale(n, lo, hi, y, 4, gauss_dens([[0.0]], [[sg]]))
+    for j in range(1, 5):
+        f = abs(a * sg) ** j / sg
+        assert cmu[0, 0, j - 1] == pytest.approx(f * _abs_normal_moment(j + 1), rel=1e-4), j
+        assert csg[0, 0, j - 1] == pytest.approx(f * (_abs_normal_moment(j + 2) + _abs_normal_moment(j)),
+                                                 rel=1e-4), j
+
+
+def test_ipsa_scale_half_truncated_constant_model():
+    """Mean on the domain's lower edge (half the Gaussian truncated away), y = c:
+    E s_mu = E|s_mu| = sqrt(2/pi)/sigma, so both terms of cmu count:
+    cmu_j = 2 sqrt(2/pi) c^j / sigma; E s_sigma = 1/sigma, csg_j = 2 c^j / sigma."""
+    sg, c = 0.4, 1.3
+    n, lo, hi = (16000,), (0.0,), (8 * sg,)
+    y = O.eval_model(I.MODEL_POLY, (c, 0.0, 0.0), n, lo, hi)
+    cmu, csg = O.ipsa_scale(n, lo, hi, y, 3, gauss_dens([[0.0]], [[sg]]))
+    for j in range(1, 4):
+        assert cmu[0, 0, j - 1] == pytest.approx(2 * math.sqrt(2 / math.pi) * c ** j / sg, rel=1e-4)
+        assert csg[0, 0, j - 1] == pytest.approx(2 * c ** j / sg, rel=1e-6)
+
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_ipsa_scale_bounds_the_sensitivities(seed):
+    """Triangle inequality: |dM_j/dp| <= its condition scale, every axis kind."""
+    prob = I.random_problem(seed, ndim=2 + seed % 2, max_side=30)
+    dens = prob.dens.take(range(min(prob.K, 12)))
+    y = O.eval_model(prob.model_id, prob.theta, prob.n, prob.lo, prob.hi)
+    dmu, dsg = O.ipsa(prob.n, prob.lo, prob.hi, y, 4, dens)
+    cmu, csg = O.ipsa_scale(prob.n, prob.lo, prob.hi, y, 4, dens)
+    assert (np.abs(dmu) <= cmu * (1 + 1e-12)).all()
+    assert (np.abs(dsg) <= csg * (1 + 1e-12)).all()
+    assert (cmu > 0).all() and (csg > 0).all()
+
+
 def test_empty_support_is_an_error():
     n, lo, hi = (10,), (0.0,), (1.0,)
     y = O.eval_model(I.MODEL_POLY, (0.0, 1.0, 0.0), n, lo, hi)
