@@ -132,7 +132,9 @@ vup_status vup_grid_destroy(vup_grid g);
  *   grids a stable counting sort of the grid points by bin (the CSR form of
  *   the one-hot model matrix), on 2-D / 3-D grids the sorted histogram
  *   layout is built by the first vup_propagate that needs it; the power
- *   tables (y / s)^j, j = 1..n_moments, with s = max(|min y|, |max y|), are
+ *   tables z^j, j = 1..n_moments, of z = (y - c) / s (c the point of
+ *   [min y, max y] nearest 0, s = max |y - c|: raw moments are re-expanded
+ *   from them in FP64, central moments formed from them directly) are
  *   built on first use, except that a separable built-in model on a 2-D /
  *   3-D grid writes the tensor-core contraction's split BF16 table here: its
  *   values, range, bins and that table come from one cooperative launch,
@@ -199,8 +201,10 @@ vup_status vup_propagate_weights(vup_grid g, int64_t K, const float *W, double *
  * library; every GPU that loads libvup holds it until the process exits.
  * Each call needs K * (32 + 4 * n_bins) bytes of it at least; larger requests
  * return VUP_ERR_INVALID_ARG before any work is queued.
- * The first call on a device resolves the array's device address (set-up);
- * make that first call before any stream capture.  All calls share the array
+ * The first call on a device resolves the array's device address (set-up)
+ * and keeps it for the life of the process; make that first call before any
+ * stream capture.  A device reset (cudaDeviceReset) invalidates that address,
+ * as it invalidates every grid: the library is not usable across one.  All calls share the array
  * and it keeps the last call's contents (nothing in it needs clearing): two
  * calls whose work overlaps on the GPU race, so serialise them (one stream).
  */
@@ -377,6 +381,9 @@ typedef struct {
      * not built (the record stream was cheaper than both). */
     int32_t hist_layout, hist_stream;
     int64_t hist_runs, hist_intervals, hist_records;
+    /* the power tables hold z = (y - yshift) / yscale: yshift is the point of
+     * [ymin, ymax] nearest 0 (0 when the range holds 0), yscale = max |y - yshift| */
+    double yshift;
 } vup_grid_info_t;
 vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info);
 
@@ -418,6 +425,24 @@ vup_status vup_profile_timeline(char *buf, size_t cap);
 
 /* Static description of a status code. */
 const char *vup_status_string(vup_status s);
+
+/*
+ * The calling thread's last CUDA failure as text ("error name: failing call
+ * (file:line)"), set whenever a call returns VUP_ERR_CUDA or VUP_ERR_OOM; a
+ * thread-local static buffer owned by the library, valid until the thread's
+ * next failing call.  Empty if no call of this thread has failed.
+ */
+const char *vup_last_error_detail(void);
+
+/*
+ * Allocation-failure hook for tests of the out-of-memory paths (not part of
+ * the method): after `after` more device allocations by the library succeed,
+ * every later one fails as if the device were out of memory, until the hook
+ * is disarmed with after < 0 (its state at load).  Process-wide.  A call
+ * whose allocation fails returns VUP_ERR_OOM before it queues any work that
+ * writes the caller's outputs, and the grid stays usable.
+ */
+vup_status vup_debug_fail_alloc(int64_t after);
 
 /* Library version string. */
 const char *vup_version(void);

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -18,6 +19,27 @@ void vup_set_last_cuda_error(cudaError_t e, const char *expr, const char *file, 
     snprintf(g_last_err, sizeof(g_last_err), "%s: %s (%s:%d)", cudaGetErrorName(e), expr, file, line);
 }
 
+// Allocation-failure hook: < 0 disarmed; otherwise the number of device
+// allocations that still succeed before every later one fails.
+static std::atomic<int64_t> g_fail_after{-1};
+
+cudaError_t vup_dev_malloc_raw(void **p, size_t bytes) {
+    int64_t n = g_fail_after.load();
+    while (n >= 0) {
+        if (n == 0) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        if (g_fail_after.compare_exchange_weak(n, n - 1)) break;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+extern "C" vup_status vup_debug_fail_alloc(int64_t after) {
+    g_fail_after.store(after < 0 ? -1 : after);
+    return VUP_OK;
+}
+
 vup_status devbuf_reserve(DevBuf &b, size_t bytes) {
     if (b.bytes >= bytes && b.p) return VUP_OK;
     if (b.p) {
@@ -26,7 +48,7 @@ vup_status devbuf_reserve(DevBuf &b, size_t bytes) {
         b.bytes = 0;
     }
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes < 256 ? 256 : bytes);
+    cudaError_t e = vup_dev_malloc(&p, bytes < 256 ? 256 : bytes);
     if (e != cudaSuccess) {
         vup_set_last_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
         cudaGetLastError();
@@ -319,7 +341,7 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
     const int C = g->n_chunks;
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, bytes) \
-    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
+    if (e == cudaSuccess) e = vup_dev_malloc((void **)&(ptr), (bytes))
     ALLOC(g->y, sizeof(double) * N);
     ALLOC(g->axis_terms, sizeof(double2) * (size_t)(g->n[0] + (ndim > 1 ? g->n[1] : 0) + (ndim > 2 ? g->n[2] : 0)));
     ALLOC(g->ext, sizeof(unsigned long long) * 3);  // range keys (min, max) and a grid-barrier counter
@@ -382,7 +404,7 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
         L.rec_chunk_grp = A.rec_chunk_grp;
     }
     ALLOC(g->hist_sel, sizeof(int32_t) * 8);
-    ALLOC(g->ydev_scale, sizeof(double));
+    ALLOC(g->ydev_scale, sizeof(double) * kScaleSlots);
     ALLOC(g->dstatus, sizeof(int));
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMemset(g->dstatus, 0, sizeof(int));
@@ -410,7 +432,7 @@ static vup_status model_ready(vup_grid g, int n_bins, int n_moments) {
     if (g->B_cap < n_bins) {
         cudaFree(g->offsets);
         g->offsets = nullptr;
-        VUP_CHECK_CUDA(cudaMalloc(&g->offsets, sizeof(int32_t) * (n_bins + 1)));
+        VUP_CHECK_CUDA(vup_dev_malloc(&g->offsets, sizeof(int32_t) * (n_bins + 1)));
         g->B_cap = n_bins;
     }
     g->B = n_bins;
@@ -708,10 +730,10 @@ extern "C" vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info) {
     info->have_model = g->have_model;
     if (g->have_model) {
         unsigned long long k[2];
-        double sc = 1.0;
+        double sc[kScaleSlots] = {1.0, 0.0, 1.0};
         VUP_CHECK_CUDA(cudaDeviceSynchronize());
         VUP_CHECK_CUDA(cudaMemcpy(k, g->ext, sizeof(k), cudaMemcpyDeviceToHost));
-        VUP_CHECK_CUDA(cudaMemcpy(&sc, g->ydev_scale, sizeof(double), cudaMemcpyDeviceToHost));
+        VUP_CHECK_CUDA(cudaMemcpy(sc, g->ydev_scale, sizeof(sc), cudaMemcpyDeviceToHost));
         auto inv = [](unsigned long long key) {
             unsigned long long u = (key >> 63) ? (key & 0x7fffffffffffffffull) : ~key;
             double v;
@@ -720,7 +742,8 @@ extern "C" vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info) {
         };
         info->ymin = inv(k[0]);
         info->ymax = inv(k[1]);
-        info->yscale = sc;
+        info->yscale = sc[kScaleS];
+        info->yshift = sc[kScaleC];
         if (g->ndim >= 2) {
             if (!g->layout_valid) {
                 vup_status st = vup_build_layout(g, 0);

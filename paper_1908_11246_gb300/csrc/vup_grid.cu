@@ -3,7 +3,7 @@
 //   Sec. 3 composite midpoint rule), the exact output range, per-point bin ids
 //   (Eq. 4), a stable counting sort of the grid points by bin -- the CSR form
 //   of the one-hot model matrix of Eq. MUP -- the run/chunk structure the
-//   segmented histogram kernel walks, and the power tables (y/s)^j.
+//   segmented histogram kernel walks, and the power tables ((y - c)/s)^j.
 #include "vup_internal.cuh"
 
 #include <math.h>
@@ -310,17 +310,26 @@ __global__ void k_minmax(const double *__restrict__ y, int64_t N, unsigned long 
     range_reduce(mn, mx, ext);
 }
 
-// Output range and the power-table scale s = max(|ymin|, |ymax|) (1 if 0).
+// Output range, and the power tables' reference point and scales {s, c,
+// s_abs} (power_ref) written to s_out[0..2].
 __device__ __forceinline__ void read_range(const unsigned long long *ext, double &ymin, double &ymax) {
     ymin = dkey_inv(ext[0]);
     ymax = dkey_inv(ext[1]);
 }
 
-__global__ void k_scale(const unsigned long long *ext, double *s_out) {
+__device__ __forceinline__ void write_scale(double ymin, double ymax, int64_t N, double *s_out) {
+    double c, s, sa;
+    power_ref(ymin, ymax, c, s, sa);
+    s_out[kScaleS] = s;
+    s_out[kScaleC] = c;
+    s_out[kScaleAbs] = sa;
+    s_out[kScaleP] = power_factor(N);
+}
+
+__global__ void k_scale(const unsigned long long *ext, int64_t N, double *s_out) {
     double ymin, ymax;
     read_range(ext, ymin, ymax);
-    double s = fmax(fabs(ymin), fabs(ymax));
-    s_out[0] = s > 0.0 ? s : 1.0;
+    write_scale(ymin, ymax, N, s_out);
 }
 
 // Eq. 4 bin of one output value: t = (y - ymin) / (ymax - ymin), bin =
@@ -386,17 +395,14 @@ __global__ void k_bins_count(const double *__restrict__ y, int64_t N, int B,
 }
 
 // Bins of a 2-D / 3-D grid (its histogram layouts sort their own keys):
-// grid-stride over pairs of points, and the power-table scale s =
-// max(|ymin|, |ymax|) (1 if 0) from the first thread.
+// grid-stride over pairs of points, and the power tables' reference point
+// and scales from the first thread.
 __global__ void k_bins_scale(const double *__restrict__ y, int64_t N, int B, const unsigned long long *ext,
                              int32_t *__restrict__ bins, double *s_out) {
     pdl_trigger();
     pdl_wait();
     const BinRule rule(ext, B);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const double s = fmax(fabs(rule.ymin), fabs(rule.ymax));
-        s_out[0] = s > 0.0 ? s : 1.0;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) write_scale(rule.ymin, rule.ymax, N, s_out);
     const int64_t n2 = N >> 1;
     const double2 *y2 = reinterpret_cast<const double2 *>(y);
     int2 *b2 = reinterpret_cast<int2 *>(bins);
@@ -473,18 +479,17 @@ __global__ void __launch_bounds__(256) k_model_bins(double *__restrict__ y, int6
     range_reduce(mn, mx, ext);
     if (!grid_barrier(ext + 2, dstatus)) return;
     const BinRule rule(ext, B);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const double sc = fmax(fabs(rule.ymin), fabs(rule.ymax));
-        s_out[0] = sc > 0.0 ? sc : 1.0;
-    }
-    const double smax = fmax(fabs(rule.ymin), fabs(rule.ymax));
-    const double inv = 1.0 / (smax > 0.0 ? smax : 1.0);  // 1 / the power-table scale
+    if (blockIdx.x == 0 && threadIdx.x == 0) write_scale(rule.ymin, rule.ymax, N, s_out);
+    double zc, zs, zsa;
+    power_ref(rule.ymin, rule.ymax, zc, zs, zsa);
+    const double inv = 1.0 / zs;  // z = (y - c) / s
+    const float pf = (float)power_factor(N);  // tables hold z^j 2^e
     IndexWalk w2(G, i0, step);  // rest = a0, red = the remaining axes' flat index
     auto table = [&](double v) {
         const int64_t rest = w2.a[0], red = G.ndim == 3 ? (int64_t)w2.a[1] * G.n[2] + w2.a[2] : w2.a[1];
         w2.next();
-        const float z = (float)__dmul_rn(v, inv);
-        float p = z;
+        const float z = (float)__dmul_rn(__dsub_rn(v, zc), inv);
+        float p = z * pf;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (j) p *= z;
@@ -1190,7 +1195,7 @@ __global__ void k_rec_group_chunks(const int32_t *__restrict__ goff, int n_group
 
 // ---- power tables -----------------------------------------------------------
 // y viewed as a matrix Y[P][S] (flat i = p S + s).  Element (p, s) yields
-// z = y / s_scale and its powers z^j, j = 1..4 (FP64, then rounded).
+// z = (y - c) / s_scale and its powers z^j 2^e, j = 1..4 (FP64, then rounded).
 // mode 0: out[(p*4 + j) * ld + s]      (rows (p, j), cols s)
 // mode 1: out[s * ld + p*4 + j]        (rows s, cols (p, j))
 // mode 2: out[(s*4 + j) * ld + p]      (rows (s, j), cols p)
@@ -1229,11 +1234,11 @@ __global__ void k_power_table(const double *__restrict__ y, int64_t P, int64_t S
                               O *__restrict__ out, O *__restrict__ out2) {
     __shared__ double tile[32][33];
     const int64_t p0 = (int64_t)blockIdx.y * 32, s0 = (int64_t)blockIdx.x * 32;
-    const double scale = sc[0];
+    const double scale = sc[kScaleS], shift = sc[kScaleC], pf = sc[kScaleP];
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         int64_t p = p0 + r, s = s0 + threadIdx.x;
         double z = 0.0;
-        if (p < P && s < S) z = __ddiv_rn(y[p * S + s], scale);
+        if (p < P && s < S) z = __ddiv_rn(__dsub_rn(y[p * S + s], shift), scale);
         tile[r][threadIdx.x] = z;
     }
     __syncthreads();
@@ -1270,20 +1275,21 @@ __global__ void k_power_table(const double *__restrict__ y, int64_t P, int64_t S
         double z = tile[lp][ls];
         double v = z;
         for (int q = 0; q < j; ++q) v = v * z;
-        Store<T>::put(out, out2, idx, v);
+        Store<T>::put(out, out2, idx, v * pf);
     }
 }
 
-// Split BF16 power table (the tensor-core B operand): z = y / s_scale, then
-// z^j in FP32 and the BF16 hi / lo split of each.  z comes from one FP64
-// product with 1 / s_scale rounded once to FP32 (within an FP32 ulp of
-// y / s_scale), the powers carry at most three more FP32 roundings: far below
+// Split BF16 power table (the tensor-core B operand): z = (y - c) / s_scale,
+// then z^j 2^e in FP32 (z 2^e, then times z: the power-of-two factor is exact
+// and keeps the powers of small z normal) and the BF16 hi / lo split of each.  z comes from one FP64
+// difference and product with 1 / s_scale rounded once to FP32 (within an
+// FP32 ulp of the quotient), the powers carry at most three more FP32 roundings: far below
 // the 2^-17 relative resolution of the hi + lo pair.  FP64 stays on the
 // per-element path only for that one product (FP64 is the slow pipe here).
 // Modes 0 and 2 of k_power_table.
 // Split BF16 power table of the tensor-core contraction, [rest * 4 + j][red]
 // with row stride ld: element (rest, red) of y (y[rest * Rn + red] when
-// REST_ROWS, else y[red * Qn + rest]) yields z = y / s_scale and z^(j+1),
+// REST_ROWS, else y[red * Qn + rest]) yields z = (y - c) / s_scale and z^(j+1),
 // j = 0..3, each split into BF16 hi + lo.  The grid covers the padded table
 // (rests up to Qext, reds up to ld, both multiples of 64) and writes zeros
 // there.  A 32 (rest) x 64 (red) tile of z goes through shared memory; each
@@ -1296,7 +1302,8 @@ __global__ void k_power_table_bf16(const double *__restrict__ y, int64_t Qn, int
     pdl_wait();
     __shared__ float tile[32][65];
     const int64_t q0 = (int64_t)blockIdx.y * 32, r0 = (int64_t)blockIdx.x * 64;
-    const double inv = 1.0 / sc[0];
+    const double inv = 1.0 / sc[kScaleS], shift = sc[kScaleC];
+    const float pf = (float)sc[kScaleP];
     for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
         int lq, lr;
         if (REST_ROWS) {
@@ -1308,7 +1315,7 @@ __global__ void k_power_table_bf16(const double *__restrict__ y, int64_t Qn, int
         }
         const int64_t q = q0 + lq, r = r0 + lr;
         float z = 0.f;
-        if (q < Qn && r < Rn) z = (float)__dmul_rn(y[REST_ROWS ? q * Rn + r : r * Qn + q], inv);
+        if (q < Qn && r < Rn) z = (float)__dmul_rn(__dsub_rn(y[REST_ROWS ? q * Rn + r : r * Qn + q], shift), inv);
         tile[lq][lr] = z;
     }
     __syncthreads();
@@ -1317,7 +1324,7 @@ __global__ void k_power_table_bf16(const double *__restrict__ y, int64_t Qn, int
         const int64_t q = q0 + lq, r = r0 + 2 * pr;
         if (q >= Qext) continue;
         const float z0 = tile[lq][2 * pr], z1 = tile[lq][2 * pr + 1];
-        float v0 = z0, v1 = z1;
+        float v0 = z0 * pf, v1 = z1 * pf;
         for (int t = 0; t < j; ++t) {
             v0 *= z0;
             v1 *= z1;
@@ -1438,8 +1445,8 @@ vup_status vup_launch_model_eval(vup_grid g, int model_id, const double *theta, 
             int64_t ld = o.R_pad, R = o.R, Qext = ceil_div64(o.NC, 256) * 256 / 4;
             const size_t tbytes = sizeof(__nv_bfloat16) * (size_t)ld * (size_t)(Qext * 4);
             if (!g->zt_hi[to]) {
-                VUP_CHECK_CUDA(cudaMalloc(&g->zt_hi[to], tbytes));
-                VUP_CHECK_CUDA(cudaMalloc(&g->zt_lo[to], tbytes));
+                VUP_CHECK_CUDA(vup_dev_malloc(&g->zt_hi[to], tbytes));
+                VUP_CHECK_CUDA(vup_dev_malloc(&g->zt_lo[to], tbytes));
             }
             __nv_bfloat16 *zh = g->zt_hi[to], *zl = g->zt_lo[to];
             void *args[] = {&y, &N, &G, &mid, &th, &terms, &ext, &B, &bins, &sc, &dstatus, &zh, &zl, &R, &ld, &Qext};
@@ -1524,7 +1531,7 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
     }
     g->range_ready = 0;
     if (g->ndim == 1) {
-        k_scale<<<1, 1, 0, s>>>(g->ext, g->ydev_scale);
+        k_scale<<<1, 1, 0, s>>>(g->ext, N, g->ydev_scale);
         VUP_CHECK_LAUNCH();
     }
 
@@ -1546,8 +1553,8 @@ vup_status vup_launch_grid_finish(vup_grid g, cudaStream_t s) {
             cudaFree(HL.key_chunks);
             HL.koff = nullptr;
             HL.key_chunks = nullptr;
-            VUP_CHECK_CUDA(cudaMalloc(&HL.koff, sizeof(int32_t) * (Bk_max + 1)));
-            VUP_CHECK_CUDA(cudaMalloc(&HL.key_chunks, sizeof(int2) * (Bk_max + 1)));
+            VUP_CHECK_CUDA(vup_dev_malloc(&HL.koff, sizeof(int32_t) * (Bk_max + 1)));
+            VUP_CHECK_CUDA(vup_dev_malloc(&HL.key_chunks, sizeof(int2) * (Bk_max + 1)));
             HL.koff_cap = Bk_max + 1;
         }
         if (g->n_layouts > 1) {
@@ -1790,7 +1797,7 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
     if (!bf16) {
         const int64_t ld = ceil_div64(o.NC, 128) * 128;
         const size_t bytes = sizeof(float) * (size_t)ld * (size_t)o.R;
-        if (!g->zs[orient]) VUP_CHECK_CUDA(cudaMalloc(&g->zs[orient], bytes));
+        if (!g->zs[orient]) VUP_CHECK_CUDA(vup_dev_malloc(&g->zs[orient], bytes));
         VUP_CHECK_CUDA(cudaMemsetAsync(g->zs[orient], 0, bytes, s));
         // SIMT wants [r][q*4+j]: orientation 0 -> rows s (mode 1); 1 -> rows p (mode 3)
         k_power_table<float><<<grd, blk, 0, s>>>(g->y, P, S, g->ydev_scale, first ? 3 : 1, ld,
@@ -1801,8 +1808,8 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
         const int64_t rows = ceil_div64(o.NC, 256) * 256;
         const size_t bytes = sizeof(float) * (size_t)ld * (size_t)rows;
         if (!g->ztf_hi[orient]) {
-            VUP_CHECK_CUDA(cudaMalloc(&g->ztf_hi[orient], bytes));
-            VUP_CHECK_CUDA(cudaMalloc(&g->ztf_lo[orient], bytes));
+            VUP_CHECK_CUDA(vup_dev_malloc(&g->ztf_hi[orient], bytes));
+            VUP_CHECK_CUDA(vup_dev_malloc(&g->ztf_lo[orient], bytes));
         }
         VUP_CHECK_CUDA(cudaMemsetAsync(g->ztf_hi[orient], 0, bytes, s));
         VUP_CHECK_CUDA(cudaMemsetAsync(g->ztf_lo[orient], 0, bytes, s));
@@ -1814,8 +1821,8 @@ vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s) {
         const int64_t rows = ceil_div64(o.NC, 256) * 256;
         const size_t bytes = sizeof(__nv_bfloat16) * (size_t)ld * (size_t)rows;
         if (!g->zt_hi[orient]) {
-            VUP_CHECK_CUDA(cudaMalloc(&g->zt_hi[orient], bytes));
-            VUP_CHECK_CUDA(cudaMalloc(&g->zt_lo[orient], bytes));
+            VUP_CHECK_CUDA(vup_dev_malloc(&g->zt_hi[orient], bytes));
+            VUP_CHECK_CUDA(vup_dev_malloc(&g->zt_lo[orient], bytes));
         }
         // tensor wants [q*4+j][r], padding included: y is [Q][R] (orientations 0
         // and 2) or [R][Q] (orientation 1)

@@ -46,6 +46,15 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 
 void vup_set_last_cuda_error(cudaError_t e, const char *expr, const char *file, int line);
 
+// Every device allocation of the library goes through vup_dev_malloc, which
+// honours the allocation-failure hook of vup_debug_fail_alloc (tests of the
+// out-of-memory paths) and otherwise calls cudaMalloc.
+cudaError_t vup_dev_malloc_raw(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t vup_dev_malloc(T **p, size_t bytes) {
+    return vup_dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+
 // Device status word codes (grid->dstatus[0]); the first non-zero code wins.
 enum { VUP_DSTAT_OK = 0, VUP_DSTAT_EMPTY = 5, VUP_DSTAT_TIMEOUT = 6 };
 
@@ -67,6 +76,73 @@ struct DensStats {
     double Eu2;     // sum_a g u^2 / sum_a g
     double inv_sigma;
 };
+
+// Reference point and scale of the power tables: z = (y - c) / s with c the
+// point of [ymin, ymax] nearest 0 (0 when the range holds it) and
+// s = max |y - c| over the grid (1 when that is 0), so |z| <= 1.  With this c
+// every |y| = |c| + s |z| (y and c have one sign), so the binomial
+// re-expansion M_j = sum_m C(j, m) c^(j-m) s^m Mz_m of the raw moments keeps
+// the error bound of the unshifted sum, while central moments are formed
+// from Mz alone and lose nothing to a large common offset of y.
+// The grid's device array holds {s, c, s_abs} with s_abs = max(|ymin|, |ymax|)
+// (1 when 0), the unshifted scale of the supplied-weights paths.
+__host__ __device__ inline void power_ref(double ymin, double ymax, double &c, double &s, double &s_abs) {
+    c = ymin > 0.0 ? ymin : (ymax < 0.0 ? ymax : 0.0);
+    const double a = fabs(ymin - c), b = fabs(ymax - c);
+    s = a > b ? a : b;
+    if (!(s > 0.0)) s = 1.0;
+    const double m = fabs(ymin) > fabs(ymax) ? fabs(ymin) : fabs(ymax);
+    s_abs = m > 0.0 ? m : 1.0;
+}
+// The power tables hold z^j 2^e (an exact power-of-two factor, removed again
+// in FP64 by the finish): moments of outputs far below the grid's largest
+// |y - c| keep FP32 / BF16 normal numbers (z^j down to 2^(-126-e)) instead of
+// underflowing.  The largest contraction sum, sum_i g |z|^j 2^e with every
+// factor g <= 1, stays below N 2^e; e = 120 - ceil(log2 N) leaves 2^6 of
+// headroom under the FP32 range.
+__host__ __device__ inline double power_factor(int64_t N) {
+    int lg = 0;
+    while (((int64_t)1 << lg) < N) ++lg;
+    return ldexp(1.0, 120 - lg);
+}
+enum { kScaleS = 0, kScaleC = 1, kScaleAbs = 2, kScaleP = 3, kScaleSlots = 4 };
+
+// Raw moments M_j = sum_i W y^j (j = 1..4) from mz[m-1] = sum_i W z^m
+// (m = 1..4) and sum_i W = 1: M_j = sum_{m=0..j} C(j, m) c^(j-m) s^m Mz_m.
+__host__ __device__ inline void raw_from_shifted(const double mz[4], double c, double s, double M[4]) {
+    const double z[5] = {1.0, mz[0], mz[1], mz[2], mz[3]};
+    double sp[5], cp[5];
+    sp[0] = cp[0] = 1.0;
+    for (int q = 1; q < 5; ++q) {
+        sp[q] = sp[q - 1] * s;
+        cp[q] = cp[q - 1] * c;
+    }
+    const double C[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+    for (int j = 1; j <= 4; ++j) {
+        double v = 0.0;
+        for (int m = 0; m <= j; ++m) v += C[j][m] * cp[j - m] * sp[m] * z[m];
+        M[j - 1] = v;
+    }
+}
+
+// Central moments from the shifted ones: mean = c + s Mz_1 and, for j >= 2,
+// E[(y - mean)^j] = s^j sum_{m=0..j} C(j, m) (-Mz_1)^(j-m) Mz_m.
+__host__ __device__ inline void central_from_shifted(const double mz[4], double c, double s, double out[4]) {
+    const double z[5] = {1.0, mz[0], mz[1], mz[2], mz[3]};
+    const double C[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+    const double a = -mz[0];
+    double ap[5];
+    ap[0] = 1.0;
+    for (int q = 1; q < 5; ++q) ap[q] = ap[q - 1] * a;
+    out[0] = c + s * mz[0];
+    double sj = s;
+    for (int j = 2; j <= 4; ++j) {
+        sj *= s;
+        double v = 0.0;
+        for (int m = 0; m <= j; ++m) v += C[j][m] * ap[j - m] * z[m];
+        out[j - 1] = sj * v;
+    }
+}
 
 // Capacity-tracked device buffer.
 struct DevBuf {

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_weights_static(const float *__rest
     const int64_t k0 = (int64_t)blockIdx.y * RB;
     for (int e = threadIdx.x; e < RB * B; e += blockDim.x) sh[e] = 0.f;
     __syncthreads();
-    const double s = scale[0];
+    const double s = scale[kScaleAbs];
     const int64_t per = (N + n_split - 1) / n_split;
     const int64_t i0 = split * per, i1 = min(N, i0 + per);
     float m[RB][4];
@@ -99,8 +99,8 @@ __global__ void k_weights_static_finish(const double *__restrict__ mpart, const 
         const int j = (int)(e - k * J);
         double s = 0.0;
         for (int64_t q = 0; q < n_split; ++q) s += mpart[(q * K + k) * 4 + j];
-        double sp = scale[0];
-        for (int q = 0; q < j; ++q) sp *= scale[0];
+        double sp = scale[kScaleAbs];
+        for (int q = 0; q < j; ++q) sp *= scale[kScaleAbs];
         raw[e] = s * sp;
     }
 }

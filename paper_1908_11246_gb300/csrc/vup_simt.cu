@@ -39,22 +39,77 @@ struct SimtJob {
     float *part;
 };
 
-template <int NOUT>
+// Reduction terms summed in one plain FP32 chain before the chain is folded
+// into the tile's weighted sums.  Rounding bound of one chain: (kChain - 1)
+// eps of the sum of its terms' magnitudes; the fold is compensated (Kahan),
+// so the long sums over the reduction axis add only ~2 eps more: the
+// contraction stays within ~12 eps (7e-7) of sum_i W |z|^j whatever R is,
+// where one chain over the whole axis would grow like sqrt(R) eps.
+constexpr int kChain = 8;
+
+// Epilogue weight of rest point q for density k: the rest-axis factor e
+// (wmode 0), or e u and e u^2 with u the rest-axis index coordinate's
+// distance from the mean in units of sigma (wmode 1, 2: the IPSA sums).
+__device__ __forceinline__ float epi_weight(const EpiArgs &ep, int64_t K_pad, int64_t k, int64_t q, int wmode) {
+    if (q >= ep.Q) return 0.f;
+    int64_t qa = q, qb = 0;
+    if (ep.g_rest1) {
+        qa = q / ep.n_rest1;
+        qb = q - qa * ep.n_rest1;
+    }
+    float e = ep.g_rest0[qa * K_pad + k];
+    if (ep.g_rest1) e *= ep.g_rest1[qb * K_pad + k];
+    if (wmode) {
+        const DensConst dc = ep.dconst[k * ep.ndim + ep.rest_axis];
+        const float u = ((float)(q - dc.n) - dc.f) * dc.r;
+        e *= wmode == 1 ? u : u * u;
+    }
+    return e;
+}
+
+// One 128 (densities) x 128 (columns (q, j)) tile.  Each thread owns 8 rows
+// x 8 columns (2 rest points x 4 powers): the GEMM part accumulates kChain
+// reduction terms per plain FP32 chain, then folds the chain into
+// out[row][j] += w(row, q) * chain with Kahan compensation; the 16 column
+// threads of a row are reduced in FP64 and the tile writes one FP32 partial
+// per (row, power) for the FP64 finish.
 __device__ __forceinline__ void simt_tile(const float *__restrict__ A, const float *__restrict__ Zt, int64_t R,
                                           int64_t K_pad, int64_t ldz, const EpiArgs &ep, int64_t n_ct,
-                                          float *__restrict__ part, int64_t ct, int64_t row_tile) {
+                                          float *__restrict__ part, int64_t ct, int64_t row_tile, int wmode) {
     __shared__ __align__(16) float As[2][BK][BM];
     __shared__ __align__(16) float Bs[2][BK][BN];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int64_t k0 = row_tile * BM;
     const int64_t c0 = ct * BN;
+    auto row_of = [&](int i) { return k0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4)); };
 
-    float acc[8][8];
+    // epilogue weights of the thread's rows and rest points, fixed for the tile
+    float w[8][2];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int gq = 0; gq < 2; ++gq) w[i][gq] = epi_weight(ep, K_pad, row_of(i), c0 / 4 + gq * 16 + tx, wmode);
+
+    float acc[8][8];
+    float out[8][4], cmp[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[i][j] = cmp[i][j] = 0.f;
+    auto fold = [&]() {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int gq = 0; gq < 2; ++gq) {
+                    const float yv = fmaf(w[i][gq], acc[i][gq * 4 + j], -cmp[i][j]);
+                    const float t = out[i][j] + yv;
+                    cmp[i][j] = (t - out[i][j]) - yv;
+                    out[i][j] = t;
+                }
+    };
 
     float4 ra[2], rb[2];
     auto load_regs = [&](int64_t r0) {
@@ -96,10 +151,18 @@ __device__ __forceinline__ void simt_tile(const float *__restrict__ A, const flo
             *reinterpret_cast<float4 *>(&a[4]) = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
             *reinterpret_cast<float4 *>(&b[0]) = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
             *reinterpret_cast<float4 *>(&b[4]) = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+            if (kk % kChain == 0) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                    for (int j = 0; j < 8; ++j) acc[i][j] = a[i] * b[j];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
+            if (kk % kChain == kChain - 1) fold();
         }
         if (rt + 1 < n_rt) {
             store_smem(buf ^ 1);
@@ -107,93 +170,47 @@ __device__ __forceinline__ void simt_tile(const float *__restrict__ A, const flo
         __syncthreads();
     }
 
-    // epilogue: contract with the rest-axis factors (and IPSA weights)
-    float out[NOUT][8][4];
+    // reduce over the 16 column threads of a half-warp (FP64)
 #pragma unroll
-    for (int o = 0; o < NOUT; ++o)
+    for (int i = 0; i < 8; ++i) {
+        double v[4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) out[o][i][j] = 0.f;
-#pragma unroll
-    for (int gq = 0; gq < 2; ++gq) {
-        const int64_t q = c0 / 4 + gq * 16 + tx;
-        const bool qok = q < ep.Q;
-        int64_t qa = q, qb = 0;
-        if (ep.g_rest1) {
-            qa = q / ep.n_rest1;
-            qb = q - qa * ep.n_rest1;
+        for (int j = 0; j < 4; ++j) {
+            v[j] = (double)out[i][j] - (double)cmp[i][j];
+            v[j] += __shfl_xor_sync(0xffffffffu, v[j], 8);
+            v[j] += __shfl_xor_sync(0xffffffffu, v[j], 4);
+            v[j] += __shfl_xor_sync(0xffffffffu, v[j], 2);
+            v[j] += __shfl_xor_sync(0xffffffffu, v[j], 1);
         }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t k = k0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-            float e = 0.f;
-            if (qok) {
-                e = ep.g_rest0[qa * K_pad + k];
-                if (ep.g_rest1) e *= ep.g_rest1[qb * K_pad + k];
-            }
-            float w[NOUT];
-            w[0] = e;
-            if (NOUT == 3) {
-                const DensConst dc = ep.dconst[k * ep.ndim + ep.rest_axis];
-                const float t = (float)(q - dc.n) - dc.f;
-                const float u = t * dc.r;
-                w[NOUT == 3 ? 1 : 0] = e * u;
-                w[NOUT == 3 ? 2 : 0] = e * u * u;
-            }
-#pragma unroll
-            for (int o = 0; o < NOUT; ++o)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) out[o][i][j] = fmaf(w[o], acc[i][gq * 4 + j], out[o][i][j]);
-        }
-    }
-    // reduce over the 16 column threads of a half-warp
-#pragma unroll
-    for (int o = 0; o < NOUT; ++o)
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float v = out[o][i][j];
-                v += __shfl_xor_sync(0xffffffffu, v, 8);
-                v += __shfl_xor_sync(0xffffffffu, v, 4);
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                v += __shfl_xor_sync(0xffffffffu, v, 1);
-                out[o][i][j] = v;
-            }
-    if (tx == 0) {
-#pragma unroll
-        for (int o = 0; o < NOUT; ++o)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int64_t k = k0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-                *reinterpret_cast<float4 *>(part + (((int64_t)o * n_ct + ct) * K_pad + k) * 4) =
-                    make_float4(out[o][i][0], out[o][i][1], out[o][i][2], out[o][i][3]);
-            }
+        if (tx == 0)
+            *reinterpret_cast<float4 *>(part + (((int64_t)wmode * n_ct + ct) * K_pad + row_of(i)) * 4) =
+                make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
     }
 }
 
-template <int NOUT>
-__global__ void __launch_bounds__(256, NOUT == 1 ? 2 : 1)
+// wmode 0: moments; 1, 2: the IPSA sums with weights e u and e u^2 (one
+// launch each, into partial slice wmode).
+__global__ void __launch_bounds__(256, 1)
 k_moments_simt(const float *__restrict__ A, const float *__restrict__ Zt, int64_t R, int64_t K_pad,
-               int64_t ldz, EpiArgs ep, int64_t n_ct, float *__restrict__ part) {
-    simt_tile<NOUT>(A, Zt, R, K_pad, ldz, ep, n_ct, part, blockIdx.x, blockIdx.y);
+               int64_t ldz, EpiArgs ep, int64_t n_ct, float *__restrict__ part, int wmode) {
+    simt_tile(A, Zt, R, K_pad, ldz, ep, n_ct, part, blockIdx.x, blockIdx.y, wmode);
 }
 
 // Batched form: one persistent launch over the tiles of many instances,
 // longest reductions first (items[t] = (instance, column tile, row tile)).
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 1)
 k_moments_simt_batched(const SimtJob *__restrict__ jobs, const int4 *__restrict__ items, int n_items) {
     for (int t = blockIdx.x; t < n_items; t += gridDim.x) {
         const int4 it = items[t];
         const SimtJob J = jobs[it.x];
-        simt_tile<1>(J.A, J.Zt, J.R, J.K_pad, J.ldz, J.ep, J.n_ct, J.part, it.y, it.z);
+        simt_tile(J.A, J.Zt, J.R, J.K_pad, J.ldz, J.ep, J.n_ct, J.part, it.y, it.z, 0);
         __syncthreads();
     }
 }
 
-// Sum the per-column-tile partials in FP64, undo the normalisation and the
-// power-table scale, and form central moments about the mean.
+// Sum the per-column-tile partials in FP64, undo the normalisation, re-expand
+// the moments of z = (y - c) / s into raw moments of y, and form the central
+// moments about the mean from the moments of z.
 struct FinishJob {
     const float *part;
     int64_t n_ct, K, K_pad;
@@ -218,23 +235,18 @@ __device__ __forceinline__ void moments_finish_body(const float *__restrict__ pa
     }
     double invZ = 1.0;
     for (int d = 0; d < ndim; ++d) invZ *= ds[k * ndim + d].invZ;
-    const double s = scale[0];
-    double M[4];
-    double sp = s;
-    for (int j = 0; j < 4; ++j) {
-        M[j] = mz[j] * invZ * sp;
-        sp *= s;
-    }
-    if (raw)
+    invZ /= scale[kScaleP];  // the tables' power-of-two factor
+    for (int j = 0; j < 4; ++j) mz[j] *= invZ;
+    const double s = scale[kScaleS], c = scale[kScaleC];
+    if (raw) {
+        double M[4];
+        raw_from_shifted(mz, c, s, M);
         for (int j = 0; j < J; ++j) raw[k * J + j] = M[j];
+    }
     if (central) {
-        const double m = M[0];
-        double c[4];
-        c[0] = m;
-        c[1] = M[1] - m * m;
-        c[2] = M[2] - 3.0 * m * M[1] + 2.0 * m * m * m;
-        c[3] = M[3] - 4.0 * m * M[2] + 6.0 * m * m * M[1] - 3.0 * m * m * m * m;
-        for (int j = 0; j < J; ++j) central[k * J + j] = c[j];
+        double cm[4];
+        central_from_shifted(mz, c, s, cm);
+        for (int j = 0; j < J; ++j) central[k * J + j] = cm[j];
     }
 }
 
@@ -252,9 +264,11 @@ __global__ void k_moments_finish_batched(const FinishJob *__restrict__ jobs, con
     moments_finish_body(F.part, F.n_ct, F.K, F.K_pad, F.J, F.ds, F.ndim, F.scale, F.raw, F.central, it.y);
 }
 
-// IPSA combine.  With u_d = (x_d - mu_d) / sigma_d and W = g / sum g,
-//   dM_j/dmu_d    = s^j / sigma_d (sum_i W u_d z^j   - E_d[u]   Mz_j)
-//   dM_j/dsigma_d = s^j / sigma_d (sum_i W u_d^2 z^j - E_d[u^2] Mz_j)
+// IPSA combine.  With u_d = (x_d - mu_d) / sigma_d, W = g / sum g and
+// z = (y - c) / s, the moments of z have the derivatives
+//   dMz_m/dmu_d    = (sum_i W u_d z^m   - E_d[u]   Mz_m) / sigma_d
+//   dMz_m/dsigma_d = (sum_i W u_d^2 z^m - E_d[u^2] Mz_m) / sigma_d
+// and dM_j/dp = sum_{m=1..j} C(j, m) c^(j-m) s^m dMz_m/dp (Mz_0 = 1 is constant).
 // part0 holds orientation 0 (rest = axis 0): [w, w u_0, w u_0^2] partials,
 // part1 orientation 1 (rest = axis 1, 2-D only).
 __global__ void k_ipsa_finish(const float *__restrict__ part0, int64_t nct0, const float *__restrict__ part1,
@@ -264,9 +278,9 @@ __global__ void k_ipsa_finish(const float *__restrict__ part0, int64_t nct0, con
                               float *__restrict__ dsg) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= K) return;
-    double invZ = 1.0;
+    double invZ = 1.0 / scale[kScaleP];  // the tables' power-of-two factor
     for (int d = 0; d < ndim; ++d) invZ *= ds[k * ndim + d].invZ;
-    const double s = scale[0];
+    const double s = scale[kScaleS], c = scale[kScaleC];
     double S[2][3][4];
     for (int o = 0; o < 2; ++o)
         for (int w = 0; w < 3; ++w)
@@ -283,15 +297,35 @@ __global__ void k_ipsa_finish(const float *__restrict__ part0, int64_t nct0, con
     for (int d = 0; d < ndim; ++d) {
         const DensStats st = ds[k * ndim + d];
         const bool diff = dc[k * ndim + d].kind != VUP_UNIFORM;
+        double dmz[4], dsz[4];
+        for (int m = 0; m < 4; ++m) {
+            const double Mz = S[0][0][m] * invZ;
+            const double Su = S[d][1][m] * invZ;
+            const double Su2 = S[d][2][m] * invZ;
+            dmz[m] = st.inv_sigma * (Su - st.Eu * Mz);
+            dsz[m] = st.inv_sigma * (Su2 - st.Eu2 * Mz);
+        }
+        // re-expansion without the constant term (c^j of Mz_0 = 1)
+        double dM[4], dS[4];
+        {
+            const double C[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+            for (int j = 1; j <= 4; ++j) {
+                double vm = 0.0, vs = 0.0, cp = 1.0;
+                for (int m = j; m >= 1; --m) {  // c^(j-m) grows as m falls
+                    double sm = 1.0;
+                    for (int q = 0; q < m; ++q) sm *= s;
+                    vm += C[j][m] * cp * sm * dmz[m - 1];
+                    vs += C[j][m] * cp * sm * dsz[m - 1];
+                    cp *= c;
+                }
+                dM[j - 1] = vm;
+                dS[j - 1] = vs;
+            }
+        }
         double gm = 0.0, gs = 0.0;
-        double sp = s;
         for (int j = 0; j < J; ++j) {
-            const double Mz = S[0][0][j] * invZ;
-            const double Su = S[d][1][j] * invZ;
-            const double Su2 = S[d][2][j] * invZ;
-            double dm = diff ? sp * st.inv_sigma * (Su - st.Eu * Mz) : 0.0;
-            double dsd = diff ? sp * st.inv_sigma * (Su2 - st.Eu2 * Mz) : 0.0;
-            sp *= s;
+            const double dm = diff ? dM[j] : 0.0;
+            const double dsd = diff ? dS[j] : 0.0;
             if (grad) {
                 gm += grad[k * J + j] * dm;
                 gs += grad[k * J + j] * dsd;
@@ -339,12 +373,11 @@ vup_status vup_moments_simt(vup_grid g, int64_t K, int orient, int n_out, float 
     const int64_t ldz = ceil_div64(o.NC, 128) * 128;
     EpiArgs ep = epi_for(g, orient, K_pad);
     dim3 grd((unsigned)n_ct, (unsigned)(K_pad / BM));
-    VUP_PROF(n_out == 1 ? "moments_fp32_simt" : "ipsa_fp32_simt", s, 1);
-    if (n_out == 1)
-        k_moments_simt<1><<<grd, 256, 0, s>>>(A, g->zs[orient], o.R, K_pad, ldz, ep, n_ct, part);
-    else
-        k_moments_simt<3><<<grd, 256, 0, s>>>(A, g->zs[orient], o.R, K_pad, ldz, ep, n_ct, part);
-    VUP_CHECK_LAUNCH();
+    VUP_PROF(n_out == 1 ? "moments_fp32_simt" : "ipsa_fp32_simt", s, n_out);
+    for (int wm = 0; wm < n_out; ++wm) {
+        k_moments_simt<<<grd, 256, 0, s>>>(A, g->zs[orient], o.R, K_pad, ldz, ep, n_ct, part, wm);
+        VUP_CHECK_LAUNCH();
+    }
     return VUP_OK;
 }
 

@@ -1,6 +1,6 @@
 // Moment contraction on the 5th-generation tensor cores (tcgen05 + TMEM).
 //
-//   T[k, (q, j)] = sum_r g_red(k, r) (y_(q,r) / s)^(j+1)        (GEMM, Eq. VUP
+//   T[k, (q, j)] = sum_r g_red(k, r) z_(q,r)^(j+1), z = (y - c) / s (GEMM, Eq. VUP
 //   M[k, j]     += sum_q g_rest(k, q) T[k, (q, j)]               as moments)
 //
 // BF16x3: every FP32 operand is split into bf16 hi + lo and the product is

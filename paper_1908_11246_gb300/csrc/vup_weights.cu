@@ -213,15 +213,15 @@ __global__ void k_weights_finish(const double *__restrict__ mpart, const float *
         const int j = (int)(e - k * J);
         double s = 0.0;
         for (int64_t q = 0; q < n_split; ++q) s += mpart[(q * K + k) * 4 + j];
-        double sp = scale[0];
-        for (int q = 0; q < j; ++q) sp *= scale[0];
+        double sp = scale[kScaleAbs];
+        for (int q = 0; q < j; ++q) sp *= scale[kScaleAbs];
         raw[e] = s * sp;
     }
 }
 
 __global__ void k_z32(const double *__restrict__ y, int64_t N, const double *__restrict__ scale,
                       float *__restrict__ z32) {
-    const double s = scale[0];
+    const double s = scale[kScaleAbs];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
         z32[i] = (float)(y[i] / s);
 }

@@ -28,7 +28,7 @@ ABI_SYMBOLS = [
     "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_batched_report", "vup_sync", "vup_selftest_wait", "vup_model_at",
     "vup_deviation_moments", "vup_ipsa_matrix", "vup_sa_fields", "vup_posterior_means",
     "vup_grid_info", "vup_set_hist_stream", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
-    "vup_profile_read", "vup_profile_timeline",
+    "vup_profile_read", "vup_profile_timeline", "vup_last_error_detail", "vup_debug_fail_alloc",
 ]
 
 
@@ -42,7 +42,7 @@ class vup_grid_info_t(C.Structure):
                 ("n_moments", C.c_int32), ("ymin", C.c_double), ("ymax", C.c_double),
                 ("yscale", C.c_double), ("have_model", C.c_int32), ("hist_layout", C.c_int32),
                 ("hist_stream", C.c_int32), ("hist_runs", C.c_int64), ("hist_intervals", C.c_int64),
-                ("hist_records", C.c_int64)]
+                ("hist_records", C.c_int64), ("yshift", C.c_double)]
 
 
 class VUPError(RuntimeError):
@@ -86,8 +86,9 @@ def lib():
         l.vup_profile.argtypes = [C.c_int]
         l.vup_profile_read.argtypes = [C.c_char_p, C.c_size_t]
         l.vup_profile_timeline.argtypes = [C.c_char_p, C.c_size_t]
+        l.vup_debug_fail_alloc.argtypes = [i64]
         for f in ABI_SYMBOLS:
-            if f not in ("vup_status_string", "vup_version"):
+            if f not in ("vup_status_string", "vup_version", "vup_last_error_detail"):
                 getattr(l, f).restype = C.c_int
         l.vup_status_string.argtypes = [C.c_int]
         l.vup_status_string.restype = C.c_char_p
@@ -95,6 +96,16 @@ def lib():
         l.vup_last_error_detail.restype = C.c_char_p
         _lib = l
     return _lib
+
+
+def vup_last_error_detail() -> str:
+    return lib().vup_last_error_detail().decode()
+
+
+def vup_debug_fail_alloc(after: int):
+    """Make every device allocation of the library fail after `after` more
+    succeed (after < 0 disarms): a test hook for the out-of-memory paths."""
+    _check(lib().vup_debug_fail_alloc(int(after)), "vup_debug_fail_alloc")
 
 
 def vup_status_string(status: int) -> str:

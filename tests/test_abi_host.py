@@ -81,3 +81,21 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(vup, "_lib", None)
     with pytest.raises(ImportError):
         vup.lib()
+
+
+def test_allocation_failure_hook_on_host(L):
+    """With the hook armed, grid creation fails with VUP_ERR_OOM at its first
+    device allocation (no CUDA device is needed to reach it) and returns no
+    handle; the detail names the failing allocation."""
+    import ctypes as C
+    h = C.c_void_p(1234)
+    n = (C.c_int64 * 2)(10, 10)
+    lo = (C.c_double * 2)(0, 0)
+    hi = (C.c_double * 2)(1, 1)
+    vup.vup_debug_fail_alloc(0)
+    try:
+        assert L.vup_grid_create(2, n, lo, hi, C.byref(h)) == vup.VUP_ERR_OOM
+        assert not h.value
+        assert "cudaErrorMemoryAllocation" in vup.vup_last_error_detail()
+    finally:
+        vup.vup_debug_fail_alloc(-1)

@@ -73,12 +73,7 @@ def test_batched_matches_oracle(batch, precision):
         scale = Hp.abs_moment_scale(p, res["y"], rows)
         Hp.check_moments(r, res["raw"], scale, Hp.TOL[precision], what=p.name)
         amb = Hp.ambiguous_points(res["y"], res["bins"], p.n_bins)
-        amb_mass = 0.0
-        if amb.any():
-            for k in rows:
-                W, _ = O.weights(p.n, p.lo, p.hi, p.dens, k)
-                amb_mass = max(amb_mass, float(W[amb].sum()))
-        Hp.check_hist(h, res["hist"], amb_mass)
+        Hp.check_hist(h, res["hist"], Hp.ambiguous_mass(p, amb, rows))
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
@@ -215,3 +210,50 @@ def test_batched_argument_errors(batch):
     assert e.value.status == vup.VUP_ERR_INVALID_ARG
     # an empty batch is a no-op
     vup.vup_propagate_batched([], [], vup.VUP_FP32, [], [])
+
+
+# ------------------------------------------------- the full c5 batch
+_C5 = {}
+
+
+def _c5_oracle(n_sample=32):
+    """The 512-instance batch the bench times, and the oracle on every row of
+    a seeded sample of its instances (computed once per module)."""
+    if not _C5:
+        probs = I.oscillator_batch(5, n_inst=512)
+        pick = np.sort(np.random.default_rng(55).choice(len(probs), size=n_sample, replace=False))
+        res = {}
+        for i in pick:
+            p = probs[i]
+            r = O.solve(p, threads=Hp.oracle_threads())
+            r["scale"] = Hp.abs_moment_scale(p, r["y"], np.arange(p.K))
+            res[int(i)] = r
+        _C5.update(probs=probs, pick=pick, res=res)
+    return _C5["probs"], _C5["pick"], _C5["res"]
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+def test_c5_full_batch_sampled_instances(precision):
+    """The real c5 batch (512 oscillator instances, sides 32..1024, K 64..8192)
+    in one batched call as bench.py makes it; 32 seeded instances against the
+    oracle on all of their rows, and every instance's histograms sum to 1."""
+    vup = vupmod()
+    probs, pick, res = _c5_oracle()
+    grids, dens = [], []
+    for p in probs:
+        g = vup.Grid(p.n, p.lo, p.hi)
+        g.eval_model(p.model_id, p.theta, p.n_bins, p.n_moments)
+        grids.append(g)
+        dens.append(vup.densities_to_device(p.dens))
+    raws, hists = vup.propagate_batched(grids, dens, precision)
+    _sync(grids)
+    tol = Hp.TOL[precision]
+    for i in pick:
+        p, r = probs[i], res[int(i)]
+        Hp.check_moments(raws[i].cpu().numpy(), r["raw"], r["scale"], tol, what=p.name)
+        amb = Hp.ambiguous_points(r["y"], r["bins"], p.n_bins)
+        Hp.check_hist(hists[i].cpu().numpy(), r["hist"], Hp.ambiguous_mass(p, amb, np.arange(p.K)))
+    for h in hists:
+        assert np.abs(h.double().sum(dim=1).cpu().numpy() - 1.0).max() <= 1e-6
+    for g in grids:
+        g.close()

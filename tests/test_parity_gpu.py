@@ -88,14 +88,11 @@ def _parity(prob, precision, rows=None, check_central=True):
     tol = Hp.TOL[precision if prob.ndim > 1 else "fp64"]
     scale = Hp.abs_moment_scale(prob, res["y"], rows_)
     w_raw = Hp.check_moments(raw[rows_], res["raw"], scale, tol)
-    w_cen = Hp.check_central(cen[rows_], res["central"], scale, tol) if check_central else None
+    w_cen = None
+    if check_central:
+        w_cen = Hp.check_central(cen[rows_], res["central"], Hp.central_moment_scale(prob, res["y"], rows_), tol)
     amb = Hp.ambiguous_points(res["y"], res["bins"], prob.n_bins)
-    amb_mass = 0.0
-    if amb.any():
-        for s, k in enumerate(rows_):
-            W, _ = O.weights(prob.n, prob.lo, prob.hi, prob.dens, k)
-            amb_mass = max(amb_mass, float(W[amb].sum()))
-    w_h = Hp.check_hist(hs[rows_], res["hist"], amb_mass)
+    w_h = Hp.check_hist(hs[rows_], res["hist"], Hp.ambiguous_mass(prob, amb, rows_))
     return w_raw, w_cen, w_h
 
 
@@ -130,24 +127,123 @@ def test_propagate_random_ragged_shapes_bf16x3(seed):
     _parity(prob, "bf16x3")
 
 
+# ------------------------------------------------- full-size workloads
+# The bench's own configurations, run whole on the GPU (the launch
+# configuration bench.py times); the oracle computes a seeded set of rows one
+# by one: rows 0 and K - 1, one row in every 128-row tile, the rest random.
+_FULL = {}
+
+
+def _full_oracle(name, n_rows):
+    """Oracle values (moments, histograms, condition scales) of `n_rows`
+    seeded rows of a full-size workload, computed once per module."""
+    key = (name, n_rows)
+    if key not in _FULL:
+        prob = I.config(name)
+        rows = Hp.tile_rows(prob.K, n_rows, seed=1000 + int(name[1:]))
+        res = O.solve(prob, rows=rows, threads=Hp.oracle_threads())
+        res["rows"] = rows
+        res["scale"] = Hp.abs_moment_scale(prob, res["y"], rows)
+        res["cscale"] = Hp.central_moment_scale(prob, res["y"], rows)
+        res["amb"] = Hp.ambiguous_points(res["y"], res["bins"], prob.n_bins)
+        _FULL[key] = (prob, res)
+    return _FULL[key]
+
+
+def _full_parity(name, precision, n_rows):
+    prob, res = _full_oracle(name, n_rows)
+    rows = res["rows"]
+    g, raw, cen, hs = gpu_run(prob, precision)
+    tol = Hp.TOL[precision]
+    Hp.check_moments(raw[rows], res["raw"], res["scale"], tol)
+    Hp.check_central(cen[rows], res["central"], res["cscale"], tol)
+    amb_mass = Hp.ambiguous_mass(prob, res["amb"], rows)
+    Hp.check_hist(hs[rows], res["hist"], amb_mass)
+    # every row (not only the oracle's): a probability vector
+    assert np.abs(hs.astype(np.float64).sum(axis=1) - 1.0).max() <= 1e-6 + amb_mass
+    assert np.isfinite(raw).all() and np.isfinite(cen).all()
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
 @pytest.mark.parametrize("name", ["c2", "c3"])
-def test_propagate_full_size_sampled_rows_bf16x3(name):
-    prob = I.config(name)
-    rows = np.random.default_rng(8).choice(prob.K, size=24, replace=False)
-    rows = np.concatenate([[0, prob.K - 1], rows])
-    _parity(prob, "bf16x3", rows=rows)
+def test_propagate_full_size_1024_rows(name, precision):
+    _full_parity(name, precision, 1024)
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+def test_propagate_c4_full_size_512_rows(precision):
+    _full_parity("c4", precision, 512)
 
 
 def test_propagate_c1_full_fp64_all_rows():
     _parity(I.config("c1"), "fp64")
 
 
-@pytest.mark.parametrize("name", ["c2", "c3"])
-def test_propagate_full_size_sampled_rows_fp32(name):
+@pytest.mark.parametrize("name", ["c2", "c3", "c4"])
+def test_full_size_bins_bit_exact(name):
+    """Per-point bin ids of the full-size grids (the cooperative model-and-
+    bins kernel with its FP32 screen) against the oracle's exact FP64 rule;
+    a point may differ only where the two libms' values straddle an edge."""
     prob = I.config(name)
-    rows = np.random.default_rng(7).choice(prob.K, size=24, replace=False)
-    rows = np.concatenate([[0, prob.K - 1], rows])
-    _parity(prob, "fp32", rows=rows)
+    vup = vupmod()
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.eval_model(prob.model_id, prob.theta, prob.n_bins, prob.n_moments)
+    g.sync()
+    y_g = g.array("y").cpu().numpy()
+    b_g = g.array("bins").cpu().numpy()
+    y_o = O.eval_model(prob.model_id, prob.theta, prob.n, prob.lo, prob.hi)
+    b_o, ymin, ymax = O.bins(y_o, prob.n_bins)
+    np.testing.assert_allclose(y_g, y_o, rtol=0, atol=1e-13 * max(1.0, np.abs(y_o).max()))
+    # the GPU's bins are exactly the oracle's rule applied to the GPU's values
+    b_gy, _, _ = O.bins(y_g, prob.n_bins)
+    np.testing.assert_array_equal(b_g, b_gy)
+    amb = Hp.ambiguous_points(y_o, b_o, prob.n_bins)
+    mism = b_g != b_o
+    assert not (mism & ~amb).any(), f"{int((mism & ~amb).sum())} bins differ away from edges"
+    info = g.info()
+    assert info.ymin == y_g.min() and info.ymax == y_g.max()
+    g.close()
+
+
+def test_large_output_offset_keeps_central_moments():
+    """y = 1000 + sin x1 + 7 sin^2 x2: the power tables are taken about the
+    point of the output range nearest 0 (here min y), so the variance of a
+    density is not lost to the common offset; raw moments keep their gate."""
+    vup = vupmod()
+    import torch
+    prob = I.config("c2", "small")
+    y_o = O.eval_model(prob.model_id, prob.theta, prob.n, prob.lo, prob.hi) + 1000.0
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.set_outputs(torch.as_tensor(y_o, device="cuda"), prob.n_bins, 4)
+    b_o, _, _ = O.bins(y_o, prob.n_bins)
+    res = O.propagate(prob.n, prob.lo, prob.hi, y_o, b_o, prob.n_bins, 4, prob.dens, threads=Hp.oracle_threads())
+    rows = np.arange(prob.K)
+    zero = np.zeros(y_o.size, np.int32)
+    scale = O.propagate(prob.n, prob.lo, prob.hi, np.abs(y_o), zero, 1, 4, prob.dens, threads=Hp.oracle_threads())["raw"]
+    c = Hp.shift_point(y_o)
+    assert c == y_o.min()
+    cscale = O.propagate(prob.n, prob.lo, prob.hi, np.abs(y_o - c), zero, 1, 4, prob.dens,
+                         threads=Hp.oracle_threads())["raw"]
+    dd = vup.densities_to_device(prob.dens)
+    info_checked = False
+    for precision in ("fp32", "bf16x3"):
+        raw, cen, hs = g.propagate(dd, precision)
+        g.sync()
+        if not info_checked:
+            info = g.info()
+            assert info.yshift == c and info.yscale == pytest.approx(y_o.max() - c, rel=1e-15)
+            info_checked = True
+        tol = Hp.TOL[precision]
+        Hp.check_moments(raw.cpu().numpy(), res["raw"], scale, tol)
+        Hp.check_central(cen.cpu().numpy(), res["central"], cscale, tol)
+        # the variance keeps its relative accuracy where it is not tiny
+        var_g, var_o = cen.cpu().numpy()[:, 1], res["central"][:, 1]
+        big = var_o > 0.5
+        assert big.any()
+        assert (np.abs(var_g[big] - var_o[big]) / var_o[big]).max() < 1e3 * tol
+        Hp.check_hist(hs.cpu().numpy(), res["hist"])
+    g.close()
 
 
 def test_weights_path_matches_oracle():
@@ -165,48 +261,70 @@ def test_weights_path_matches_oracle():
     g.sync()
     res = O.solve(prob, rows=np.arange(K))
     scale = Hp.abs_moment_scale(prob, res["y"], np.arange(K))
-    Hp.check_moments(raw.cpu().numpy(), res["raw"], scale, 2e-6)
-    Hp.check_hist(hist.cpu().numpy(), res["hist"], tol=2e-6)
+    Hp.check_moments(raw.cpu().numpy(), res["raw"], scale, Hp.TOL["fp32"])
+    Hp.check_hist(hist.cpu().numpy(), res["hist"])
 
 
 # ------------------------------------------------------------ IPSA adjoint
-def _ipsa_gate(g_gpu, g_or, scale, tol):
-    err = np.abs(g_gpu - g_or) / scale
-    assert err.max() <= tol, f"worst {err.max():.3e}"
-    return float(err.max())
+# Gradients are gated at tol x their condition scale (oracle ipsa_scale: the
+# sum of the absolute values of the products that make up dM_j/dp), the same
+# measure as the raw moments' sum W |y|^j.  Var = M2 - M1^2 has the scale
+# cond_2 + 2 |M1| cond_1; a central finite difference with h = 1e-3 sigma
+# carries a truncation error of (h^2 / 6) times the third derivative, about
+# 1.7e-7 of the first (derivatives of a moment under a density of width sigma
+# grow by ~1/sigma per order), covered by 1e-6 |fd|.
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
-def test_ipsa_matches_oracle_and_fd(precision):
+_IPSA_ORACLE = {}
+
+
+def _ipsa_oracle(prob, y, rows):
+    """Oracle Jacobian and condition scales of `rows`, once per module."""
+    key = (prob.name, prob.n, rows.size, int(rows[0]), int(rows[-1]))
+    if key not in _IPSA_ORACLE:
+        omu, osg = O.ipsa(prob.n, prob.lo, prob.hi, y, 4, prob.dens, rows=rows, threads=Hp.oracle_threads())
+        _IPSA_ORACLE[key] = (omu, osg) + Hp.ipsa_condition(prob, y, rows)
+    return _IPSA_ORACLE[key]
+
+
+def _ipsa_case(prob, precision, rows, grad_seed=3):
     vup = vupmod()
     import torch
-    prob = I.config("c4", "small")
     g = vup.Grid(prob.n, prob.lo, prob.hi)
     g.eval_model(prob.model_id, prob.theta, prob.n_bins, 4)
     dd = vup.densities_to_device(prob.dens)
     dmu, dsg = g.ipsa(dd, precision)
     g.sync()
     dmu, dsg = dmu.cpu().numpy(), dsg.cpu().numpy()
-    rows = np.arange(0, prob.K, 7)
     y = O.eval_model(prob.model_id, prob.theta, prob.n, prob.lo, prob.hi)
-    omu, osg = O.ipsa(prob.n, prob.lo, prob.hi, y, 4, prob.dens, rows=rows, threads=Hp.oracle_threads())
-    A = Hp.abs_moment_scale(prob, y, rows)                  # sum W |y|^j
-    sig = prob.dens.sigma[rows]                             # [S, ndim]
-    scale = 5.0 * A[:, None, :] / sig[:, :, None]
-    tol = 1e-6 if precision == "fp32" else 2e-5
-    _ipsa_gate(dmu[rows], omu, scale, tol)
-    _ipsa_gate(dsg[rows], osg, scale, tol)
-    # vector-Jacobian product form equals the contraction of the Jacobian
-    grad = torch.as_tensor(np.random.default_rng(3).normal(size=(prob.K, 4)), device="cuda")
+    omu, osg, cmu, csg = _ipsa_oracle(prob, y, rows)
+    tol = Hp.TOL[precision]
+    Hp.check_ipsa(dmu[rows], omu, cmu, tol, "dM/dmu")
+    Hp.check_ipsa(dsg[rows], osg, csg, tol, "dM/dsigma")
+    # vector-Jacobian product against the oracle's Jacobian contracted with
+    # the same seed: scale sum_j |grad_j| cond_j
+    grad = torch.as_tensor(np.random.default_rng(grad_seed).normal(size=(prob.K, 4)), device="cuda")
     vmu, vsg = g.ipsa(dd, precision, grad=grad)
     g.sync()
-    gn = grad.cpu().numpy()
-    np.testing.assert_allclose(vmu.cpu().numpy(), np.einsum("kdj,kj->kd", dmu, gn), rtol=1e-4, atol=1e-5 * np.abs(dmu).max())
-    np.testing.assert_allclose(vsg.cpu().numpy(), np.einsum("kdj,kj->kd", dsg, gn), rtol=1e-4, atol=1e-5 * np.abs(dsg).max())
+    gn = grad.cpu().numpy()[rows]
+    for got, og, cond in ((vmu, omu, cmu), (vsg, osg, csg)):
+        want = np.einsum("kdj,kj->kd", og, gn)
+        sc = np.einsum("kdj,kj->kd", cond, np.abs(gn))
+        Hp.check_ipsa(got.cpu().numpy()[rows], want, sc, tol, "vjp")
+    return g, y, dmu, dsg, cmu, csg
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_ipsa_matches_oracle_and_fd(precision):
+    prob = I.config("c4", "small")
+    rows = np.arange(0, prob.K, 7)
+    g, y, dmu, dsg, cmu, csg = _ipsa_case(prob, precision, rows)
+    tol = Hp.TOL[precision]
     # central finite differences of the oracle, h = 1e-3 sigma: dE/dmu, dVar/dsigma
     zero = np.zeros(y.size, np.int32)
     for s in range(3):
         k = rows[s]
+        m1 = O.propagate(prob.n, prob.lo, prob.hi, y, zero, 1, 4, prob.dens.take([k]))["raw"][0, 0]
         for d in range(2):
             for which in ("mu", "sigma"):
                 h = 1e-3 * prob.dens.sigma[k, d]
@@ -216,13 +334,24 @@ def test_ipsa_matches_oracle_and_fd(precision):
                     getattr(dd1, which)[0, d] += sg_ * h
                     v.append(O.propagate(prob.n, prob.lo, prob.hi, y, zero, 1, 4, dd1)["central"][0])
                 fd = (v[0] - v[1]) / (2 * h)
-                m1 = O.propagate(prob.n, prob.lo, prob.hi, y, zero, 1, 4, prob.dens.take([k]))["raw"][0, 0]
                 gpu = (dmu if which == "mu" else dsg)[k, d]
+                cond = (cmu if which == "mu" else csg)[s, d]
                 gE = gpu[0]
                 gVar = gpu[1] - 2 * m1 * gpu[0]
-                sc = 5.0 * A[s] / prob.dens.sigma[k, d]
-                assert abs(gE - fd[0]) <= tol * sc[0] + 1e-6 * abs(fd[0]), (which, d, gE, fd[0])
-                assert abs(gVar - fd[1]) <= 3 * tol * sc[1] + 1e-6 * abs(fd[1]), (which, d, gVar, fd[1])
+                assert abs(gE - fd[0]) <= tol * cond[0] + 1e-6 * abs(fd[0]), (which, d, gE, fd[0])
+                assert abs(gVar - fd[1]) <= tol * (cond[1] + 2 * abs(m1) * cond[0]) + 1e-6 * abs(fd[1]), \
+                    (which, d, gVar, fd[1])
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+def test_ipsa_c4_full_size_256_rows(precision):
+    """The c4 workload whole (2048^2 grid, K = 65536): the Jacobian and the
+    vector-Jacobian product on 256 seeded rows (one in every other 128-row
+    tile, rows 0 and K - 1), the launch bench.py times for c4."""
+    prob = I.config("c4")
+    rows = Hp.tile_rows(prob.K, 256, seed=44, tile=256)
+    g, *_ = _ipsa_case(prob, precision, rows)
+    g.close()
 
 
 def test_ipsa_1d_fp64_matches_oracle():
@@ -367,9 +496,11 @@ def test_tiny_2d_case_matches_stored_values(precision):
     Hp.check_hist(hs, stored["hist"])
     dmu, dsg = g.ipsa(vup.densities_to_device(prob.dens), precision)
     g.sync()
-    sc = np.abs(stored["dmu"]).max() + np.abs(stored["dsigma"]).max()
-    assert np.abs(dmu.cpu().numpy() - stored["dmu"]).max() / sc < 10 * Hp.TOL[precision]
-    assert np.abs(dsg.cpu().numpy() - stored["dsigma"]).max() / sc < 10 * Hp.TOL[precision]
+    # the stored values are written with repr (17 significant digits): their
+    # own rounding is far below the gate
+    cmu, csg = Hp.ipsa_condition(prob, res["y"], np.arange(prob.K))
+    Hp.check_ipsa(dmu.cpu().numpy(), stored["dmu"], cmu, Hp.TOL[precision], "dM/dmu")
+    Hp.check_ipsa(dsg.cpu().numpy(), stored["dsigma"], csg, Hp.TOL[precision], "dM/dsigma")
 
 
 # ------------------------------------------------------------ TF32 kinds
@@ -444,4 +575,44 @@ def test_profile_timeline_spans_the_streams():
     for n, sid, launches, b, e in tl:
         assert 0.0 <= b <= e and launches >= 0
     assert len({sid for _, sid, _, _, _ in tl}) == 3
+    g.close()
+
+
+def test_allocation_failure_returns_oom_and_leaves_outputs_untouched():
+    """With the allocation-failure hook armed, a propagation that must grow
+    its per-K scratch returns VUP_ERR_OOM before queueing any work (the
+    outputs keep their NaN fill); disarmed, the same call succeeds on the same
+    grid, and grid creation fails cleanly the same way."""
+    vup = vupmod()
+    import torch
+    prob = I.config("c2", "small")
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.eval_model(prob.model_id, prob.theta, prob.n_bins, 4)
+    g.propagate(vup.densities_to_device(prob.dens.take(range(10))), "bf16x3")
+    g.sync()
+    dd = vup.densities_to_device(prob.dens)  # K = 225: more rows than the scratch holds
+    K, B = prob.K, prob.n_bins
+    raw = torch.full((K, 4), float("nan"), dtype=torch.float64, device="cuda")
+    cen = torch.full((K, 4), float("nan"), dtype=torch.float64, device="cuda")
+    hist = torch.full((K, B), float("nan"), dtype=torch.float32, device="cuda")
+    ds = vup.make_densities(dd)
+    vup.vup_debug_fail_alloc(0)
+    try:
+        with pytest.raises(vup.VUPError) as e:
+            vup.vup_propagate(g.h, ds, vup.VUP_BF16X3, raw, cen, hist)
+        assert e.value.status == vup.VUP_ERR_OOM
+        with pytest.raises(vup.VUPError) as e:
+            vup.Grid(prob.n, prob.lo, prob.hi)
+        assert e.value.status == vup.VUP_ERR_OOM
+    finally:
+        vup.vup_debug_fail_alloc(-1)
+    g.sync()
+    torch.cuda.synchronize()
+    assert torch.isnan(raw).all() and torch.isnan(cen).all() and torch.isnan(hist).all()
+    vup.vup_propagate(g.h, ds, vup.VUP_BF16X3, raw, cen, hist)
+    g.sync()
+    res = O.solve(prob, threads=Hp.oracle_threads())
+    scale = Hp.abs_moment_scale(prob, res["y"], np.arange(K))
+    Hp.check_moments(raw.cpu().numpy(), res["raw"], scale, Hp.TOL["bf16x3"])
+    Hp.check_hist(hist.cpu().numpy(), res["hist"])
     g.close()
