@@ -187,7 +187,7 @@ def traffic_for(kernel, workload):
     return None
 
 
-def roofline_for(name, ms, n_work, units, pk, clk_mhz, workload, hist_units=None):
+def roofline_for(name, ms, n_work, units, pk, workload, hist_units=None):
     """Algorithmic work of one working launch of `name` divided by its event-timed duration.
 
     ms: device time of the group over the timed steps; n_work: the launches in
@@ -201,38 +201,36 @@ def roofline_for(name, ms, n_work, units, pk, clk_mhz, workload, hist_units=None
     4 per prefix sum a record needs -- one per bin it holds and one more, the
     intervals plus the records in all -- + 4 per rest-factor row per record)."""
     per = ms / max(n_work, 1) * 1e-3
-    sms = 152
     tr = traffic_for(name, workload)
-    if name.startswith("moments_bf16") or name.startswith("ipsa_bf16"):
-        fl = 24.0
+    if name.startswith(("moments_bf16", "ipsa_bf16", "moments_tf32")):
+        tf32 = name.startswith("moments_tf32")
+        fl = 8.0 if name.startswith("moments_tf32_") else 24.0
+        # TF32 dense = bf16 x (1.1 / 2.25), the nominal ratio of the two peaks
+        ratio = 1.1 / 2.25 if tf32 else 1.0
+        burst, sus = pk["bf16"] * ratio, pk["bf16_sus"] * ratio
         a = fl * units / per / 1e12
-        return {"bound": "tensor", "achieved": a, "peak": pk["bf16_sus"], "unit": "TFLOP/s",
-                "frac": a / pk["bf16_sus"], "traffic": tr,
-                "note": f"{fl:g} tensor flops/dist-point (BF16x3, J=4) per launch; peak = sustained bf16, "
-                        f"of {pk['source']}"}
-    if name.startswith("moments_tf32"):
-        fl = 24.0 if name.startswith("moments_tf32x3") else 8.0
-        peak = pk["bf16_sus"] * 1.1 / 2.25   # TF32 dense = bf16 x (1.1 / 2.25) nominal ratio
-        a = fl * units / per / 1e12
-        return {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-                "traffic": tr,
-                "note": f"{fl:g} tensor flops/dist-point (TF32, J=4); peak = sustained bf16 x 1.1/2.25, "
-                        f"of {pk['source']}"}
+        return {"bound": "tensor", "achieved": a, "peak": burst, "unit": "TFLOP/s", "frac": a / burst,
+                "peak_sustained": sus, "frac_sustained": a / sus, "traffic": tr,
+                "note": f"{fl:g} tensor flops/dist-point ({'TF32' if tf32 else 'BF16x3'}, J=4) per launch; "
+                        f"peak = burst {'TF32 (bf16 x 1.1/2.25)' if tf32 else 'bf16'} (the kernel runs well "
+                        f"under a second), sustained beside it, of {pk['source']}"}
     if name.startswith("moments_fp32") or name.startswith("ipsa_fp32"):
         fl = 8.0 if name.startswith("moments") else 24.0
-        peak = sms * 128 * 2 * clk_mhz * 1e6 / 1e12
+        peak = pk["ffma_tflops"]
         a = fl * units / per / 1e12
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-                "traffic": tr, "note": f"{fl:g} FP32 flops/dist-point; peak = 152 SM x 128 FMA x 2 x median SM clock"}
+                "traffic": tr, "note": f"{fl:g} FP32 flops/dist-point; peak = FP32 FMA throughput measured by "
+                                      "vup_measure_peak(0) in this run"}
     if name.startswith("hist_seg"):
-        peak = sms * 128 * clk_mhz * 1e6 / 1e9
+        peak = pk["gather_gbs"]
         a = (hist_units or 4.0 * units) / per / 1e9
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": tr,
                 "note": "bytes through the L1 data pipe that the walk needs per pass (per density: point stream "
                         "4 per point + 4 per rest-factor row per run; interval stream 8 of prefix sums + 4 per "
                         "rest-factor row per interval; record stream 4 per prefix sum it needs (one per bin a "
                         "record holds + one per record) + 4 per rest-factor row "
-                        "per record); peak = 152 SM x 128 B/clk x median SM clock"}
+                        "per record); peak = shared-memory 512-byte row gathers measured by "
+                        "vup_measure_peak(1) in this run"}
     a = 4.0 * units / per / 1e9
     return {"bound": "hbm", "achieved": a, "peak": pk["hbm"], "unit": "GB/s", "frac": a / pk["hbm"],
             "traffic": tr, "note": f"4 B/dist-point; peak = measured copy bandwidth, of {pk['source']}"}
@@ -461,6 +459,7 @@ def main():
     ap.add_argument("--k", type=int, default=0, help="use the first K densities of the workload (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32-arm", action="store_true", help="skip the plain FP32 comparator run")
     ap.add_argument("--hist-stream", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="histogram stream: -1 automatic, 0 sorted points, 1 sorted intervals, 2 records")
     args = ap.parse_args()
@@ -482,6 +481,9 @@ def main():
     from paper_1908_11246_gb300 import vup
 
     pk = peaks()
+    # measured ceilings of the CUDA-core resources (FP32 FMA, shared-memory gathers)
+    pk["ffma_tflops"] = vup.vup_measure_peak(0) / 1e12
+    pk["gather_gbs"] = vup.vup_measure_peak(1) / 1e9
     prec = vup.PRECISIONS[args.precision]
     if args.config == "c5":
         work = Batched(prec, vup, torch)
@@ -555,12 +557,57 @@ def main():
         e2e = {"value": world * work.units / (tot / n_e2e), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": 1e3 * tot / n_e2e}
 
+    # the plain FP32 GPU path on the same workload (the metric's comparator):
+    # a shorter timed run after the main one, its contraction timed alone
+    fp32_arm = None
+    if args.precision != "fp32" and not args.no_fp32_arm and args.config not in ("weights", "bayes"):
+        work.prec = vup.PRECISIONS["fp32"]
+        n32 = max(3, args.steps // 4)
+        for _ in range(3):
+            work.step(stream)
+        work.sync()
+        torch.cuda.synchronize()
+        if profile_live:
+            vup.vup_profile(True)
+        e32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n32)]
+        for s in range(n32):
+            flush.zero_()
+            e32[s][0].record(stream)
+            work.step(stream)
+            e32[s][1].record(stream)
+        torch.cuda.synchronize()
+        if not profile_live:  # the batched graph launches stage by stage while profiled
+            vup.vup_profile(True)
+            for s in range(n32):
+                flush.zero_()
+                work.step(stream)
+            torch.cuda.synchronize()
+        vup.vup_profile(False)
+        prof32 = vup.vup_profile_read()
+        work.sync()
+        work.prec = prec
+        ms32 = sum(a.elapsed_time(b) for a, b in e32) / n32
+        t = torch.tensor([ms32], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms32 = float(t.item())
+        v32 = world * work.units / (ms32 * 1e-3)
+
+        def contraction_ms(pr, n):
+            return sum(v[1] for k, v in pr.items() if k.startswith("moments_") and "finish" not in k) / n
+        c_main, c_32 = contraction_ms(prof, args.steps), contraction_ms(prof32, n32)
+        fp32_arm = {"value": v32, "unit": UNIT, "ms_per_step": ms32, "steps": n32,
+                    "factor_step": value / v32, "contraction_ms": {args.precision: c_main, "fp32": c_32},
+                    "factor_contraction": (c_32 / c_main) if c_main > 0 else None,
+                    "note": "the same workload with the plain FP32 CUDA-core contraction (8-term FP32 chains, "
+                            "compensated folds), timed the same way after the main run; contraction_ms "
+                            "sums the contraction launches per step (profiled pass for c5)"}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    clk_mhz = clk["sm_mhz"] if clk else pk["sm_max"]
     per_step = {k: {"launches": v[0] / args.steps, "ms_per_step": v[1] / args.steps} for k, v in prof.items()}
     wl = args.config + (f"_k{work.K}" if args.k else "")
     # dominant: the costliest group with a roofline (groups on the second stream
@@ -589,7 +636,7 @@ def main():
         return launches
 
     def roof_of(k, v):
-        return roofline_for(k, v[1], n_work(k, v[0]), work.units, pk, clk_mhz, wl, hist_units)
+        return roofline_for(k, v[1], n_work(k, v[0]), work.units, pk, wl, hist_units)
     roof = roof_of(dominant, prof[dominant]) if dominant else None
     if roof:
         roof["kernel"] = dominant
@@ -629,6 +676,10 @@ def main():
                                "on a third (the finish waits there for SM room beside the histogram), so "
                                "group spans overlap and can add up to more than ms_per_step") if profile_live
                     else "per-stage CUDA events from a second pass of the same steps (stage by stage)"},
+        "fp32_arm": fp32_arm,
+        "measured_ceilings": {"fp32_ffma_tflops": pk["ffma_tflops"], "smem_gather_gbs": pk["gather_gbs"],
+                              "how": "vup_measure_peak: FMA chains and 512-byte shared-memory row gathers on "
+                                     "every SM, CUDA events, in this run"},
         "gpu_launches": int(sum(v[0] for v in prof.values())),
         "clocks": clk,
         "e2e": e2e,

@@ -423,6 +423,19 @@ vup_status vup_profile_read(char *buf, size_t cap);
  * in order of first use.  VUP_ERR_INVALID_ARG if buf is null or too small. */
 vup_status vup_profile_timeline(char *buf, size_t cap);
 
+/*
+ * Measured ceiling of a CUDA-core resource, the denominator of the roofline
+ * fractions of kernels bound by it (not part of the method):
+ *   kind 0: FP32 fused multiply-add throughput, FLOP/s (an FMA counts two);
+ *   kind 1: shared-memory gathers of 512-byte rows by whole warps (16 bytes
+ *           per lane, a data-dependent row per warp), bytes/s through the
+ *           SM's L1 data pipe.
+ * Runs a few milliseconds of work on every SM of the current device on
+ * `stream`, waits for it and writes the rate to *value (host).  Allocates
+ * and frees a small device buffer.
+ */
+vup_status vup_measure_peak(int kind, vup_stream_t stream, double *value);
+
 /* Static description of a status code. */
 const char *vup_status_string(vup_status s);
 

@@ -29,6 +29,7 @@ ABI_SYMBOLS = [
     "vup_deviation_moments", "vup_ipsa_matrix", "vup_sa_fields", "vup_posterior_means",
     "vup_grid_info", "vup_set_hist_stream", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
     "vup_profile_read", "vup_profile_timeline", "vup_last_error_detail", "vup_debug_fail_alloc",
+    "vup_measure_peak",
 ]
 
 
@@ -87,6 +88,7 @@ def lib():
         l.vup_profile_read.argtypes = [C.c_char_p, C.c_size_t]
         l.vup_profile_timeline.argtypes = [C.c_char_p, C.c_size_t]
         l.vup_debug_fail_alloc.argtypes = [i64]
+        l.vup_measure_peak.argtypes = [C.c_int, vp, C.POINTER(C.c_double)]
         for f in ABI_SYMBOLS:
             if f not in ("vup_status_string", "vup_version", "vup_last_error_detail"):
                 getattr(l, f).restype = C.c_int
@@ -100,6 +102,14 @@ def lib():
 
 def vup_last_error_detail() -> str:
     return lib().vup_last_error_detail().decode()
+
+
+def vup_measure_peak(kind: int, stream=None) -> float:
+    """Measured ceiling: kind 0 FP32 FMA FLOP/s, kind 1 shared-memory row
+    gathers in bytes/s (see include/vup.h)."""
+    v = C.c_double()
+    _check(lib().vup_measure_peak(int(kind), _stream(stream), C.byref(v)), "vup_measure_peak")
+    return v.value
 
 
 def vup_debug_fail_alloc(after: int):
