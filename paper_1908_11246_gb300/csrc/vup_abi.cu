@@ -315,23 +315,13 @@ extern "C" vup_status vup_grid_create(int ndim, const int64_t *n, const double *
         ori.Q = N / ori.R;
         ori.NC = ori.Q * 4;
         ori.n_rest_axes = 0;
-        ori.n_red_axes = 1;
         ori.rest_axes[0] = ori.rest_axes[1] = -1;
+        ori.rest_n[0] = ori.rest_n[1] = 1;
         for (int d = 0; d < ndim; ++d)
-            if (d != ori.red_axis0 && ori.n_rest_axes < 2) ori.rest_axes[ori.n_rest_axes++] = d;
-    }
-    if (ndim == 3) {
-        // grouped: reduce over axes 1 and 2 (flat r = a1 n2 + a2), rest = axis 0
-        Orient &ori = g->orient[kOrientGrouped];
-        ori.red_axis0 = 1;
-        ori.n_red_axes = 2;
-        ori.R = g->n[1] * g->n[2];
-        ori.R_pad = ceil_div64(ori.R, 64) * 64;
-        ori.Q = g->n[0];
-        ori.NC = ori.Q * 4;
-        ori.n_rest_axes = 1;
-        ori.rest_axes[0] = 0;
-        ori.rest_axes[1] = -1;
+            if (d != ori.red_axis0 && ori.n_rest_axes < 2) {
+                ori.rest_n[ori.n_rest_axes] = g->n[d];
+                ori.rest_axes[ori.n_rest_axes++] = d;
+            }
     }
     int p_all = 1;  // the most parts any layout of this grid can have
     for (int l = 0; l < (ndim == 2 ? 2 : 1); ++l)

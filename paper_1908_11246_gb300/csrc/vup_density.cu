@@ -255,20 +255,10 @@ __device__ __forceinline__ void density_finish_body(const DensJob &J, int64_t kb
 // (bx, by) transposes the 32 x 32 tile at a = 32 bx, k = 32 by.
 // Split of one FP32 value into hi + lo: BF16 pair (tensor kind::f16) or
 // TF32 pair stored in floats (kind::tf32).
-__device__ __forceinline__ void split_store(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t i, float v) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[i] = h;
-    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
-}
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
-}
-__device__ __forceinline__ void split_store(float *hi, float *lo, int64_t i, float v) {
-    const float h = to_tf32(v);
-    hi[i] = h;
-    lo[i] = to_tf32(v - h);
 }
 
 // Two consecutive reduction indices of one density row split together (one
@@ -304,83 +294,6 @@ __device__ __forceinline__ void split_transpose_body(const float *__restrict__ t
         if (k < K_pad && a < R_pad) split_store2(hi, lo, k * R_pad + a, t[2 * threadIdx.x][y], t[2 * threadIdx.x + 1][y]);
     }
     __syncthreads();
-}
-
-// Grouped 3-D orientation: A[k][r] = w1[k][a1] w2[k][a2], r = a1 n2 + a2 (the
-// product density over the two reduction axes, formed in FP32 exactly as the
-// histogram kernel forms it), split into BF16 hi + lo and written K-major
-// ([K_pad][R_pad], r contiguous).  A 32 (r) x 32 (k) tile goes through shared
-// memory so that the factor reads (k contiguous) and the table writes (r
-// contiguous) are both coalesced.
-template <typename T>
-__global__ void k_split_product(const float *__restrict__ w1, const float *__restrict__ w2, int64_t n2,
-                                int64_t R, int64_t K_pad, int64_t R_pad, T *__restrict__ hi, T *__restrict__ lo) {
-    __shared__ float t[32][33];
-    const int64_t r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;  // x: density tiles, y: reduction tiles
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int64_t r = r0 + y, k = k0 + threadIdx.x;
-        float v = 0.f;
-        if (r < R && k < K_pad) {
-            const int64_t a1 = r / n2, a2 = r - a1 * n2;
-            v = w1[a1 * K_pad + k] * w2[a2 * K_pad + k];
-        }
-        t[y][threadIdx.x] = v;
-    }
-    __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int64_t k = k0 + y, r = r0 + threadIdx.x;
-        if (k < K_pad && r < R_pad) split_store(hi, lo, k * R_pad + r, t[threadIdx.x][y]);
-    }
-}
-
-// Same table, one CTA per 32 densities when both axes' factors fit in shared
-// memory: the factors are staged once ([32][n + 1] per axis) and each warp
-// writes whole rows, two consecutive r per lane per step (coalesced stores).
-template <typename T>
-__global__ void __launch_bounds__(256) k_split_product_rows(const float *__restrict__ w1,
-                                                            const float *__restrict__ w2, int64_t n1, int64_t n2,
-                                                            int64_t R, int64_t K_pad, int64_t R_pad,
-                                                            T *__restrict__ hi, T *__restrict__ lo) {
-    extern __shared__ float sh[];
-    const int64_t l1 = n1 + 1, l2 = n2 + 1;
-    float *s1 = sh, *s2 = sh + 32 * l1;
-    const int64_t k0 = (int64_t)blockIdx.x * 32;
-    for (int64_t e = threadIdx.x; e < 32 * n1; e += blockDim.x) {
-        const int64_t a = e >> 5, kk = e & 31;
-        s1[kk * l1 + a] = w1[a * K_pad + k0 + kk];
-    }
-    for (int64_t e = threadIdx.x; e < 32 * n2; e += blockDim.x) {
-        const int64_t a = e >> 5, kk = e & 31;
-        s2[kk * l2 + a] = w2[a * K_pad + k0 + kk];
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int kk = warp; kk < 32; kk += blockDim.x >> 5) {
-        const float *f1 = s1 + kk * l1, *f2 = s2 + kk * l2;
-        T *oh = hi + (k0 + kk) * R_pad;
-        T *ol = lo + (k0 + kk) * R_pad;
-        int64_t r = 2 * lane;
-        int64_t a1 = r / n2, a2 = r - a1 * n2;
-        for (; r < R_pad; r += 64) {
-            float v[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                int64_t b1 = a1, b2 = a2 + e;
-                if (b2 >= n2) {
-                    b2 -= n2;
-                    ++b1;
-                }
-                v[e] = r + e < R ? f1[b1] * f2[b2] : 0.f;
-            }
-            split_store(oh, ol, r, v[0]);
-            split_store(oh, ol, r + 1, v[1]);
-            a2 += 64;
-            while (a2 >= n2) {
-                a2 -= n2;
-                ++a1;
-            }
-        }
-    }
 }
 
 // STATS: also the sums of g u and g u^2 (E[u], E[u^2] of the IPSA derivatives)
@@ -494,22 +407,6 @@ vup_status vup_density_prep(vup_grid g, const vup_densities *d, int need_bf16_or
 // TF32-in-float), written to hi / lo.
 template <typename T>
 static vup_status split_tables(vup_grid g, int mask, int64_t K_pad, T *hi0, T *lo0, cudaStream_t s) {
-    if (mask & (1 << kOrientGrouped)) {
-        const Orient &ori = g->orient[kOrientGrouped];
-        const float *w1 = (const float *)g->ftab.p + g->n[0] * K_pad;
-        const float *w2 = w1 + g->n[1] * K_pad;
-        const size_t smem = sizeof(float) * 32 * (size_t)(g->n[1] + g->n[2] + 2);
-        if (smem <= 160 * 1024) {
-            VUP_CHECK_CUDA(
-                cudaFuncSetAttribute(k_split_product_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_split_product_rows<T><<<(unsigned)(K_pad / 32), 256, smem, s>>>(w1, w2, g->n[1], g->n[2], ori.R,
-                                                                             K_pad, ori.R_pad, hi0, lo0);
-        } else {
-            dim3 tg((unsigned)ceil_div64(K_pad, 32), (unsigned)ceil_div64(ori.R_pad, 32));
-            k_split_product<T><<<tg, dim3(32, 8), 0, s>>>(w1, w2, g->n[2], ori.R, K_pad, ori.R_pad, hi0, lo0);
-        }
-        VUP_CHECK_LAUNCH();
-    }
     for (int o = 0; o < 2; ++o) {
         if (!(mask & (1 << o))) continue;
         const Orient &ori = g->orient[o];

@@ -484,9 +484,10 @@ __global__ void __launch_bounds__(256) k_model_bins(double *__restrict__ y, int6
     power_ref(rule.ymin, rule.ymax, zc, zs, zsa);
     const double inv = 1.0 / zs;  // z = (y - c) / s
     const float pf = (float)power_factor(N);  // tables hold z^j 2^e
-    IndexWalk w2(G, i0, step);  // rest = a0, red = the remaining axes' flat index
+    IndexWalk w2(G, i0, step);  // red = the last axis, rest = the other axes' flat index
     auto table = [&](double v) {
-        const int64_t rest = w2.a[0], red = G.ndim == 3 ? (int64_t)w2.a[1] * G.n[2] + w2.a[2] : w2.a[1];
+        const int64_t rest = G.ndim == 3 ? (int64_t)w2.a[0] * G.n[1] + w2.a[1] : w2.a[0];
+        const int64_t red = G.ndim == 3 ? w2.a[2] : w2.a[1];
         w2.next();
         const float z = (float)__dmul_rn(__dsub_rn(v, zc), inv);
         float p = z * pf;

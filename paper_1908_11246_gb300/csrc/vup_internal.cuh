@@ -162,14 +162,14 @@ struct Orient {
     int64_t Q;          // number of rest points
     int64_t NC;         // Q * J
     int rest_axes[2];   // rest axes (up to 2), -1 if unused
+    int64_t rest_n[2];  // their sizes (1 if unused); q = a_rest0 * rest_n[1] + a_rest1
     int n_rest_axes;
-    int n_red_axes;     // 1, or 2 for the grouped 3-D orientation (axes 1 and 2)
 };
 
-// Orientation indices: 0 = reduce over the last axis, 1 = reduce over axis 0
-// (2-D, IPSA), 2 = 3-D grids reduce over axes 1 and 2 (tensor-core path; its
-// A operand is the product table w1 (x) w2).
-enum { kOrientLast = 0, kOrientFirst = 1, kOrientGrouped = 2, kNumOrient = 3 };
+// Orientation indices: 0 = reduce over the last axis (every contraction of
+// the forward moments, 2-D and 3-D), 1 = reduce over axis 0 (2-D, the IPSA
+// derivatives of axis 1).
+enum { kOrientLast = 0, kOrientFirst = 1, kNumOrient = 2 };
 
 struct vup_grid_s {
     int device = 0;
@@ -334,8 +334,9 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
                             cudaStream_t s);
 
 int vup_num_sms();
-// Orientation of the forward tensor-core contraction: grouped on 3-D grids.
-inline int vup_tc_orient(const vup_grid_s *g) { return g->ndim == 3 ? kOrientGrouped : kOrientLast; }
+// Orientation of the forward tensor-core contraction: the last axis is the
+// reduction (3-D grids apply both rest axes' factors in the epilogue).
+inline int vup_tc_orient(const vup_grid_s *) { return kOrientLast; }
 bool vup_profiling();
 vup_status vup_check_dens(vup_grid g, const vup_densities *d);
 vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa, bool tf32 = false);

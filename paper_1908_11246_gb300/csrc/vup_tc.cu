@@ -171,25 +171,41 @@ struct TcTile {
     int32_t inst, m, n, pad;
 };
 
-// kBatched == false: one instance, tensor maps as kernel parameters, tiles
-// t -> (m, n) = (t / n_n, t % n_n).  kBatched == true: tiles come from a work
-// list over many instances and each tile's maps and epilogue parameters from
-// its instance descriptor.  KIND 0: BF16 operands (kind::f16, 64 per
+// Work schedule of one (non-batched) contraction.  The tiles of a row tile
+// (128 densities) and reduction split are grouped into items that one CTA
+// processes in a row, summing their epilogue results in registers and
+// writing one partial column per item.  Plain items are single column tiles.
+// "Row-block" items (3-D grids whose second rest axis has a multiple of 64
+// points): a 256-column tile covers 64 consecutive points of that axis for
+// one index of the first, so an item takes L consecutive first-axis indices
+// at one second-axis block; its epilogue loads the block's 64 factors of the
+// second axis once and one factor of the first axis per tile.
+struct TcSched {
+    int n_m, n_n, n_split;  // row tiles, column tiles, reduction splits
+    int per_row;            // items per (row tile, split) = partial columns per split
+    int fast;               // row-block items
+    int T1, L, n0;          // row-block: column tiles per first-axis index, indices per item, first-axis size
+};
+constexpr int kItemRows = 16;  // first-axis indices per row-block item
+
+// kBatched == false: one instance, tensor maps as kernel parameters, items
+// of the schedule S.  kBatched == true: items are single tiles from a work
+// list over many instances and each tile's maps and epilogue parameters come
+// from its instance descriptor.  KIND 0: BF16 operands (kind::f16, 64 per
 // 128-byte row); KIND 1: TF32 operands (kind::tf32, 32 per row).  terms = 3:
 // hi*hi + hi*lo + lo*hi; terms = 1: hi*hi only (the lo planes are not read).
 template <int NOUT, bool kBatched, int KIND = 0>
 __global__ void __launch_bounds__(kThreads, 1)
 k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-             const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int n_m, int n_n,
+             const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, TcSched S,
              int n_kb, int64_t K_pad, TcEpi ep, float *__restrict__ part, const TcInst *__restrict__ insts,
-             const TcTile *__restrict__ tiles, int n_tiles_batched, int *__restrict__ dstatus, int terms = 3,
-             int n_split = 1) {
+             const TcTile *__restrict__ tiles, int n_tiles_batched, int *__restrict__ dstatus, int terms = 3) {
     pdl_trigger();
     pdl_wait();
     constexpr int BKE = KIND ? BK_TF32 : BK;  // operand elements per 128-byte row
     // split reduction: n_split accumulators of at most kSplitTerms terms each
     // (the tensor cores' FP32 accumulation error grows with the reduction
-    // length); every split writes its own partial column, summed in FP64
+    // length); every split writes its own partial columns, summed in FP64
     constexpr int kSplitKb = kSplitTerms / BKE;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -202,29 +218,40 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = kBatched ? n_tiles_batched : n_m * n_split * n_n;
-    // tile t -> (instance, row tile, column tile, k-block range [kb0, kb1),
-    // partial column, tile width)
-    auto tile_at = [&](int t, int &m, int &n, int &kb0, int &kb1, int &col, int &bn, const TcInst *&in) {
+    const int n_items = kBatched ? n_tiles_batched : S.n_m * S.n_split * S.per_row;
+    // item -> (instance, row tile, split, item column, tile count)
+    auto item_at = [&](int it, int &m, int &sp, int &ic, int &cnt, const TcInst *&in) {
         if (kBatched) {
-            const TcTile tt = tiles[t];
+            const TcTile tt = tiles[it];
             in = insts + tt.inst;
             m = tt.m;
-            n = tt.n;
+            sp = 0;
+            ic = tt.n;
+            cnt = 1;
+            return;
+        }
+        in = nullptr;
+        const int per = S.n_split * S.per_row;
+        m = it / per;
+        const int r = it - m * per;
+        sp = r / S.per_row;
+        ic = r - sp * S.per_row;
+        cnt = S.fast ? min(S.L, S.n0 - (ic / S.T1) * S.L) : 1;
+    };
+    // column tile of the i-th tile of item column ic
+    auto tile_n = [&](int ic, int i) -> int {
+        if (!kBatched && S.fast) return ((ic / S.T1) * S.L + i) * S.T1 + ic % S.T1;
+        return ic;
+    };
+    // k-block range and tile width of a split
+    auto kb_range = [&](int sp, const TcInst *in, int &kb0, int &kb1, int &bn) {
+        if (kBatched) {
             kb0 = 0;
             kb1 = in->n_kb;
-            col = n;
             bn = in->bn;
         } else {
-            in = nullptr;
-            const int per_m = n_split * n_n;
-            m = t / per_m;
-            const int r = t - m * per_m;
-            const int sp = r / n_n;
-            n = r - sp * n_n;
             kb0 = sp * kSplitKb;
             kb1 = min(n_kb, kb0 + kSplitKb);
-            col = sp * n_n + n;
             bn = BN;
         }
     };
@@ -256,32 +283,39 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            uint32_t it = 0;
+            uint32_t it_s = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                int m, n, kb0, kb1, col, bn;
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+                int m, sp, ic, cnt, kb0, kb1, bn;
                 const TcInst *in;
-                tile_at(t, m, n, kb0, kb1, col, bn, in);
+                item_at(it, m, sp, ic, cnt, in);
+                kb_range(sp, in, kb0, kb1, bn);
                 const CUtensorMap *mAh = kBatched ? &in->maps[0] : &tmAh;
                 const CUtensorMap *mAl = kBatched ? &in->maps[1] : &tmAl;
                 const CUtensorMap *mBh = kBatched ? &in->maps[2] : &tmBh;
                 const CUtensorMap *mBl = kBatched ? &in->maps[3] : &tmBl;
-                for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, dstatus)) { ok = false; break; }
-                    uint8_t *st = smem + s * STAGE_BYTES;
-                    mbar_expect_tx(&full[s], (terms == 3 ? 2 : 1) * (A_BYTES + 128 * bn));
-                    tma_load_2d(st, mAh, &full[s], kb * BKE, m * BM);
-                    tma_load_2d(st + 2 * A_BYTES, mBh, &full[s], kb * BKE, n * bn);
-                    if (terms == 3) {
-                        tma_load_2d(st + A_BYTES, mAl, &full[s], kb * BKE, m * BM);
-                        tma_load_2d(st + 2 * A_BYTES + B_BYTES, mBl, &full[s], kb * BKE, n * bn);
+                for (int i = 0; i < cnt && ok; ++i) {
+                    const int n = tile_n(ic, i);
+                    for (int kb = kb0; kb < kb1; ++kb, ++it_s) {
+                        const int s = it_s % STAGES;
+                        if (!mbar_wait(&empty[s], ((it_s / STAGES) & 1) ^ 1, abort_flag, dstatus)) {
+                            ok = false;
+                            break;
+                        }
+                        uint8_t *st = smem + s * STAGE_BYTES;
+                        mbar_expect_tx(&full[s], (terms == 3 ? 2 : 1) * (A_BYTES + 128 * bn));
+                        tma_load_2d(st, mAh, &full[s], kb * BKE, m * BM);
+                        tma_load_2d(st + 2 * A_BYTES, mBh, &full[s], kb * BKE, n * bn);
+                        if (terms == 3) {
+                            tma_load_2d(st + A_BYTES, mAl, &full[s], kb * BKE, m * BM);
+                            tma_load_2d(st + 2 * A_BYTES + B_BYTES, mBl, &full[s], kb * BKE, n * bn);
+                        }
                     }
                 }
             }
             // drain: every issued stage must land before shared memory is released
             if (!ok) {
-                for (uint32_t j = (it > (uint32_t)STAGES ? it - STAGES : 0); j < it; ++j) {
+                for (uint32_t j = (it_s > (uint32_t)STAGES ? it_s - STAGES : 0); j < it_s; ++j) {
                     for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(&full[j % STAGES], (j / STAGES) & 1); ++i) {
                     }
                 }
@@ -290,42 +324,51 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            uint32_t it = 0, tile_it = 0;
+            uint32_t it_s = 0, tile_it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tile_it) {
-                int m_, n_, kb0, kb1, col_, bn;
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+                int m_, sp, ic, cnt, kb0, kb1, bn;
                 const TcInst *in_;
-                tile_at(t, m_, n_, kb0, kb1, col_, bn, in_);
+                item_at(it, m_, sp, ic, cnt, in_);
+                kb_range(sp, in_, kb0, kb1, bn);
                 const uint32_t idesc = idesc_for<KIND>(bn);
-                const int b = tile_it & 1;
-                if (!mbar_wait(&tempty[b], ((tile_it >> 1) & 1) ^ 1, abort_flag, dstatus)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t dcol = tmem_base + (uint32_t)(b * BN);
-                for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, dstatus)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
-                    const uint32_t a_lo = a_hi + A_BYTES;
-                    const uint32_t b_hi = a_hi + 2 * A_BYTES;
-                    const uint32_t b_lo = b_hi + B_BYTES;
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        // 32 bytes along K inside the swizzle atom: 16 BF16 or 8 TF32
-                        const uint32_t off = kk * 32;
-                        const uint32_t acc0 = (kb > kb0 || kk > 0) ? 1u : 0u;
-                        if (terms == 3) {
-                            umma<KIND>(dcol, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, acc0);
-                            umma<KIND>(dcol, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
-                            umma<KIND>(dcol, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, 1u);
-                        } else {
-                            umma<KIND>(dcol, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, acc0);
-                        }
+                for (int i = 0; i < cnt; ++i, ++tile_it) {
+                    const int b = tile_it & 1;
+                    if (!mbar_wait(&tempty[b], ((tile_it >> 1) & 1) ^ 1, abort_flag, dstatus)) {
+                        ok = false;
+                        break;
                     }
-                    umma_commit(&empty[s]);
+                    tc_fence_after();
+                    const uint32_t dcol = tmem_base + (uint32_t)(b * BN);
+                    for (int kb = kb0; kb < kb1; ++kb, ++it_s) {
+                        const int s = it_s % STAGES;
+                        if (!mbar_wait(&full[s], (it_s / STAGES) & 1, abort_flag, dstatus)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
+                        const uint32_t a_lo = a_hi + A_BYTES;
+                        const uint32_t b_hi = a_hi + 2 * A_BYTES;
+                        const uint32_t b_lo = b_hi + B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            // 32 bytes along K inside the swizzle atom: 16 BF16 or 8 TF32
+                            const uint32_t off = kk * 32;
+                            const uint32_t acc0 = (kb > kb0 || kk > 0) ? 1u : 0u;
+                            if (terms == 3) {
+                                umma<KIND>(dcol, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, acc0);
+                                umma<KIND>(dcol, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+                                umma<KIND>(dcol, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, 1u);
+                            } else {
+                                umma<KIND>(dcol, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, acc0);
+                            }
+                        }
+                        umma_commit(&empty[s]);
+                    }
+                    if (!ok) break;
+                    umma_commit(&tfull[b]);
                 }
-                if (!ok) break;
-                umma_commit(&tfull[b]);
             }
             // all MMAs issued by this thread complete before TMEM is released
             umma_commit(drain);
@@ -337,17 +380,17 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
         uint32_t tile_it = 0;
-        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tile_it) {
-            int m, n, kb0, kb1, col, bn;
+        bool ok = true;
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            int m, sp, ic, cnt, kb0, kb1, bn;
             const TcInst *in;
-            tile_at(t, m, n, kb0, kb1, col, bn, in);
+            item_at(it, m, sp, ic, cnt, in);
+            kb_range(sp, in, kb0, kb1, bn);
             const TcEpi &E = kBatched ? in->ep : ep;
             const int64_t Kp = kBatched ? in->K_pad : K_pad;
-            const int nn = kBatched ? in->n_n : n_split * n_n;  // partial columns
+            const int ncols = kBatched ? in->n_n : S.n_split * S.per_row;  // partial columns
+            const int col = kBatched ? ic : sp * S.per_row + ic;
             float *const P = kBatched ? in->part : part;
-            const int b = tile_it & 1;
-            if (!mbar_wait(&tfull[b], (tile_it >> 1) & 1, abort_flag, dstatus)) break;
-            tc_fence_after();
             const int64_t k = (int64_t)m * BM + row;
             float out[NOUT][4];
 #pragma unroll
@@ -356,49 +399,83 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
                 for (int j = 0; j < 4; ++j) out[o][j] = 0.f;
             DensConst dc{};
             if (NOUT == 3) dc = E.dconst[k * E.ndim + E.rest_axis];
-            const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN);
-#pragma unroll 1
-            for (int ch = 0; ch < bn / 32; ++ch) {
-                float v[32];
-                tmem_ld32(tbase + ch * 32, v);
-                const int64_t q0 = (int64_t)n * (bn / 4) + ch * 8;
-                float e[8];
+            const bool rows_fast = NOUT == 1 && !kBatched && S.fast;
+            // row-block item: the 64 second-axis factors of its block, loaded once
+            float g1v[64];
+            if (rows_fast) {
+                const float *g1 = E.g_rest1 + (int64_t)(ic % S.T1) * 64 * Kp + k;
 #pragma unroll
-                for (int qq = 0; qq < 8; ++qq) {
-                    const int64_t q = q0 + qq;
-                    float w = 0.f;
-                    if (q < E.Q) {
-                        if (E.g_rest1) {
-                            const int64_t qa = q / E.n_rest1, qb = q - qa * E.n_rest1;
-                            w = E.g_rest0[qa * Kp + k] * E.g_rest1[qb * Kp + k];
-                        } else {
-                            w = E.g_rest0[q * Kp + k];
+                for (int e = 0; e < 64; ++e) g1v[e] = g1[e * Kp];
+            }
+            for (int i = 0; i < cnt; ++i, ++tile_it) {
+                const int n = tile_n(ic, i);
+                float g0 = 0.f;
+                if (rows_fast) g0 = E.g_rest0[(int64_t)((ic / S.T1) * S.L + i) * Kp + k];
+                const int b = tile_it & 1;
+                if (!mbar_wait(&tfull[b], (tile_it >> 1) & 1, abort_flag, dstatus)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN);
+                if (rows_fast) {
+#pragma unroll
+                    for (int ch = 0; ch < BN / 32; ++ch) {
+                        float v[32];
+                        tmem_ld32(tbase + ch * 32, v);
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq) {
+                            const float w = g0 * g1v[ch * 8 + qq];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) out[0][j] = fmaf(w, v[qq * 4 + j], out[0][j]);
                         }
                     }
-                    e[qq] = w;
-                }
+                } else {
+#pragma unroll 1
+                    for (int ch = 0; ch < bn / 32; ++ch) {
+                        float v[32];
+                        tmem_ld32(tbase + ch * 32, v);
+                        const int64_t q0 = (int64_t)n * (bn / 4) + ch * 8;
+                        float e[8];
 #pragma unroll
-                for (int qq = 0; qq < 8; ++qq) {
-                    float w[NOUT];
-                    w[0] = e[qq];
-                    if (NOUT == 3) {
-                        const float tt = (float)(q0 + qq - dc.n) - dc.f;
-                        const float u = tt * dc.r;
-                        w[NOUT == 3 ? 1 : 0] = e[qq] * u;
-                        w[NOUT == 3 ? 2 : 0] = e[qq] * u * u;
+                        for (int qq = 0; qq < 8; ++qq) {
+                            const int64_t q = q0 + qq;
+                            float w = 0.f;
+                            if (q < E.Q) {
+                                if (E.g_rest1) {
+                                    const int64_t qa = q / E.n_rest1, qb = q - qa * E.n_rest1;
+                                    w = E.g_rest0[qa * Kp + k] * E.g_rest1[qb * Kp + k];
+                                } else {
+                                    w = E.g_rest0[q * Kp + k];
+                                }
+                            }
+                            e[qq] = w;
+                        }
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq) {
+                            float w[NOUT];
+                            w[0] = e[qq];
+                            if (NOUT == 3) {
+                                const float tt = (float)(q0 + qq - dc.n) - dc.f;
+                                const float u = tt * dc.r;
+                                w[NOUT == 3 ? 1 : 0] = e[qq] * u;
+                                w[NOUT == 3 ? 2 : 0] = e[qq] * u * u;
+                            }
+#pragma unroll
+                            for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) out[o][j] = fmaf(w[o], v[qq * 4 + j], out[o][j]);
+                        }
                     }
-#pragma unroll
-                    for (int o = 0; o < NOUT; ++o)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) out[o][j] = fmaf(w[o], v[qq * 4 + j], out[o][j]);
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
+            if (!ok) break;
 #pragma unroll
             for (int o = 0; o < NOUT; ++o)
-                *reinterpret_cast<float4 *>(P + (((int64_t)o * nn + col) * Kp + k) * 4) =
+                *reinterpret_cast<float4 *>(P + (((int64_t)o * ncols + col) * Kp + k) * 4) =
                     make_float4(out[o][0], out[o][1], out[o][2], out[o][3]);
         }
     }
@@ -447,16 +524,37 @@ bool make_map(CUtensorMap *m, const void *base, int64_t ld, int64_t rows, int bo
 
 }  // namespace
 
-// Partial columns of the contraction: column tiles x reduction splits.
+// Schedule of a contraction over K_pad rows (see TcSched); its partial
+// columns per row are n_split * per_row.
 static int tc_splits(const Orient &o) { return (int)ceil_div64(o.R_pad, kSplitTerms); }
-int64_t vup_tc_col_tiles(const Orient &o) { return ceil_div64(o.NC, BN) * tc_splits(o); }
+static TcSched tc_sched(const Orient &o, int64_t K_pad) {
+    TcSched S{};
+    S.n_m = (int)(K_pad / BM);
+    S.n_n = (int)ceil_div64(o.NC, BN);
+    S.n_split = tc_splits(o);
+    S.fast = o.n_rest_axes == 2 && o.rest_n[1] % (BN / 4) == 0;
+    if (S.fast) {
+        S.T1 = (int)(o.rest_n[1] / (BN / 4));
+        S.n0 = (int)o.rest_n[0];
+        S.L = kItemRows;
+        S.per_row = S.T1 * (int)ceil_div64(S.n0, S.L);
+    } else {
+        S.T1 = 1;
+        S.L = 1;
+        S.n0 = S.n_n;
+        S.per_row = S.n_n;
+    }
+    return S;
+}
+int64_t vup_tc_col_tiles(const Orient &o) {
+    const TcSched S = tc_sched(o, BM);
+    return (int64_t)S.n_split * S.per_row;
+}
 
 vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s, int kind,
                           int terms) {
     const Orient &o = g->orient[orient];
     const int64_t K_pad = ceil_div64(K, 128) * 128;
-    const int64_t nn = ceil_div64(o.NC, BN);
-    const int n_split = tc_splits(o);
     const int64_t rows_b = ceil_div64(o.NC, 256) * 256;
     const bool f32 = kind == 1;
     const size_t esz = f32 ? 4 : 2;
@@ -486,30 +584,31 @@ vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *p
     ep.dconst = (const DensConst *)g->dconst.p;
     ep.ndim = g->ndim;
     ep.rest_axis = o.rest_axes[0];
-    const int n_m = (int)(K_pad / BM), n_n = (int)nn, n_kb = (int)(o.R_pad / (f32 ? BK_TF32 : BK));
-    const int n_tiles = n_m * n_split * n_n;
-    const int grid = std::min(n_tiles, vup_num_sms());
+    const TcSched S = tc_sched(o, K_pad);
+    const int n_kb = (int)(o.R_pad / (f32 ? BK_TF32 : BK));
+    const int n_items = S.n_m * S.n_split * S.per_row;
+    const int grid = std::min(n_items, vup_num_sms());
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
     if (f32) {
         if (n_out != 1) return VUP_ERR_UNSUPPORTED;
         VUP_PROF(terms == 3 ? "moments_tf32x3_tc" : "moments_tf32_tc", s, 1);
         VUP_CHECK_CUDA(
             cudaFuncSetAttribute(k_moments_tc<1, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_moments_tc<1, false, 1><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part,
-                                                               nullptr, nullptr, 0, g->dstatus, terms, n_split);
+        k_moments_tc<1, false, 1><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, S, n_kb, K_pad, ep, part,
+                                                               nullptr, nullptr, 0, g->dstatus, terms);
         VUP_CHECK_LAUNCH();
         return VUP_OK;
     }
     VUP_PROF(n_out == 1 ? "moments_bf16x3_tc" : "ipsa_bf16x3_tc", s, 1);
     if (n_out == 1) {
         VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        VUP_CHECK_CUDA(launch_pdl(k_moments_tc<1, false>, dim3(grid), dim3(kThreads), smem, s, mAh, mAl, mBh, mBl, n_m,
-                                  n_n, n_kb, K_pad, ep, part, (const TcInst *)nullptr, (const TcTile *)nullptr, 0,
-                                  g->dstatus, 3, n_split));
+        VUP_CHECK_CUDA(launch_pdl(k_moments_tc<1, false>, dim3(grid), dim3(kThreads), smem, s, mAh, mAl, mBh, mBl, S,
+                                  n_kb, K_pad, ep, part, (const TcInst *)nullptr, (const TcTile *)nullptr, 0,
+                                  g->dstatus, 3));
     } else {
         VUP_CHECK_CUDA(cudaFuncSetAttribute(k_moments_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_moments_tc<3, false><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, n_m, n_n, n_kb, K_pad, ep, part, nullptr,
-                                                            nullptr, 0, g->dstatus, 3, n_split);
+        k_moments_tc<3, false><<<grid, kThreads, smem, s>>>(mAh, mAl, mBh, mBl, S, n_kb, K_pad, ep, part, nullptr,
+                                                            nullptr, 0, g->dstatus, 3);
     }
     VUP_CHECK_LAUNCH();
     return VUP_OK;
@@ -611,7 +710,7 @@ vup_status vup_tc_batched(void *plan, int *dstatus, cudaStream_t s) {
     CUtensorMap dummy;
     memset(&dummy, 0, sizeof(dummy));
     TcEpi ep{};
-    k_moments_tc<1, true><<<grid, kThreads, smem, s>>>(dummy, dummy, dummy, dummy, 0, 0, 0, 0, ep, nullptr,
+    k_moments_tc<1, true><<<grid, kThreads, smem, s>>>(dummy, dummy, dummy, dummy, TcSched{}, 0, 0, ep, nullptr,
                                                        (const TcInst *)P->insts.p, (const TcTile *)P->tiles.p,
                                                        P->n_tiles, dstatus);
     VUP_CHECK_LAUNCH();

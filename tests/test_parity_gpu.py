@@ -121,6 +121,22 @@ def test_propagate_small_configs_bf16x3(name):
     _parity(I.config(name, "small"), "bf16x3")
 
 
+def _rowblock_3d():
+    """A 3-D grid whose middle axis has a multiple of 64 points (the
+    tensor-core epilogue's row-block items), first axis not a multiple of the
+    16 indices an item takes, a ragged density count, every density kind."""
+    rng = np.random.default_rng(77)
+    lo, hi = (-3.0, -2.5, -3.1), (3.0, 2.0, 2.9)
+    return I.Problem("rowblock3d", (37, 128, 72), lo, hi, I.MODEL_MIXED_3D, (5.0, 0.08),
+                     I.random_densities(rng, 300, lo, hi, kinds=(I.GAUSS, I.UNIFORM, I.TRUNCNORM),
+                                        sig=(0.3, 0.9), width=(0.5, 1.5)), 300)
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3", "fp32"])
+def test_propagate_3d_row_block_items(precision):
+    _parity(_rowblock_3d(), precision)
+
+
 @pytest.mark.parametrize("seed", [211, 212, 213, 214])
 def test_propagate_random_ragged_shapes_bf16x3(seed):
     prob = I.random_problem(seed, ndim=2 + seed % 2)
