@@ -633,6 +633,10 @@ def main():
         # histogram: one working launch per pass (the other stream's launch exits at once)
         if k.startswith("hist_seg"):
             return args.steps * getattr(work, "hist_passes", 1)
+        # the supplied-weights group is one pass per step over several launches
+        # (power table, the W stream, the finish): its bytes are per pass
+        if k.startswith("weights"):
+            return args.steps
         return launches
 
     def roof_of(k, v):

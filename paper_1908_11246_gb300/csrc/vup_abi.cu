@@ -283,6 +283,9 @@ static void free_grid(vup_grid g) {
     devbuf_free(g->ipsa_part);
     devbuf_free(g->atf_hi);
     devbuf_free(g->atf_lo);
+    devbuf_free(g->wsort_pt);
+    devbuf_free(g->wsort_z);
+    devbuf_free(g->wsort_split);
     delete g;
 }
 

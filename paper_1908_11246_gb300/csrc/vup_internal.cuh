@@ -273,6 +273,13 @@ struct vup_grid_s {
     DevBuf hist_prefix;  // prefix-sum tiles of the gathered axis [P][K_pad / 128][rows + 1][128]
     DevBuf atf_hi, atf_lo;         // TF32 split of the A operand [K_pad][R_pad]
 
+    // supplied-weights path: the grid points in blocks of 256, each block's
+    // points sorted by bin (word: local index | bin << 8), their powers of
+    // z = y / s_abs in that order, and every block's split into eight warp
+    // slices at bin boundaries; built for model generation wsort_gen
+    DevBuf wsort_pt, wsort_z, wsort_split;
+    uint64_t wsort_gen = ~0ull;
+
     int *dstatus = nullptr;        // [1] device status word
 };
 

@@ -199,14 +199,222 @@ __global__ void __launch_bounds__(kThreads) k_weights_t(const float *__restrict_
     }
 }
 
+// Sorted-block walk (B <= 1024, rows of W 16-byte aligned).  The grid's
+// points are cut into blocks of kWBlock; within a block they are sorted by
+// bin once per model (wsort_*), and the block's sorted positions are cut at
+// bin boundaries into eight nearly equal warp slices.  A CTA owns 32 rows of
+// W (lane l: row k0 + l) and a range of blocks; each block's 32 x 256 tile of
+// W is staged in shared memory with cp.async (kWStages deep, rows padded to
+// 260 floats: a warp reading one column of 32 rows hits 32 banks) together
+// with the block's sorted words and powers.  Warp w walks its slice: a bin's
+// points are summed in a register and added once to the lane's histogram row
+// in shared memory -- every (row, bin) entry of a block has one writer, so no
+// atomics -- and the moments are summed per block in FP32 and across blocks
+// in FP64.  The histogram rows hold at most ~64 blocks' contributions per bin
+// (column splits are sized for that), the partial rows are summed in FP64.
+constexpr int kWBlock = 256;
+constexpr int kWLd = kWBlock + 4;       // padded tile row (floats)
+constexpr int kWRows = 32;
+constexpr int kWMaxBlocksPerCta = 64;   // bounds each FP32 histogram sum
+constexpr int kWWarps = 8;              // warp slices per block
+constexpr int kWThreads = kWWarps * 32;
+constexpr int kWSplit = 32;             // split entries per block (kWWarps + 1, padded)
+// sorted word: column byte offset in the tile row (bits 0-9), bin (10-22),
+// first position of its bin (31)
+constexpr uint32_t kWColMask = 0x3ffu, kWBinShift = 10, kWBinMask = 0x1fffu, kWBinStart = 1u << 31;
+struct WStage {
+    float tile[kWRows][kWLd];
+    uint32_t pt[kWBlock];
+    float4 z[kWBlock];
+    uint16_t split[kWSplit];
+};
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+template <int STAGES, int MINB>
+__global__ void __launch_bounds__(kWThreads, MINB)
+k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32_t *__restrict__ wpt,
+                 const float4 *__restrict__ wz, const uint16_t *__restrict__ wsplit, int B, int64_t n_split,
+                 double *__restrict__ mpart, float *__restrict__ hpart) {
+    extern __shared__ __align__(16) uint8_t wsm[];
+    WStage *st = reinterpret_cast<WStage *>(wsm);
+    float *H = reinterpret_cast<float *>(wsm + sizeof(WStage) * STAGES);  // [kWRows][B + 1]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ld = B + 1;
+    const int64_t k0 = (int64_t)blockIdx.y * kWRows;
+    const int64_t n_blk = (N + kWBlock - 1) / kWBlock;
+    const int64_t split = blockIdx.x;
+    const int64_t c_lo = split * n_blk / n_split, c_hi = (split + 1) * n_blk / n_split;
+    for (int e = threadIdx.x; e < kWRows * ld; e += blockDim.x) H[e] = 0.f;
+
+    // stage block c into buffer b: 32 rows x 64 chunks of W (rows past K
+    // re-read row K - 1, never stored), 64 chunks of sorted words, 256 of powers
+    auto stage = [&](int64_t c, int b) {
+        WStage &S = st[b];
+        const int64_t col0 = c * kWBlock;
+        const int64_t ncol = min((int64_t)kWBlock, N - col0);
+        for (int e = threadIdx.x; e < kWRows * (kWBlock / 4); e += blockDim.x) {
+            const int r = e >> 6, c4 = e & 63;
+            if (c4 * 4 < ncol) cp_async16(&S.tile[r][c4 * 4], W + min(k0 + r, K - 1) * N + col0 + c4 * 4);
+        }
+        if (threadIdx.x < kWBlock / 4) cp_async16(&S.pt[threadIdx.x * 4], wpt + col0 + threadIdx.x * 4);
+        for (int e = threadIdx.x; e < kWBlock; e += blockDim.x) cp_async16(&S.z[e], wz + col0 + e);
+        if (threadIdx.x >= kWThreads - kWSplit / 8)
+            cp_async16(&S.split[(threadIdx.x - (kWThreads - kWSplit / 8)) * 8],
+                       wsplit + c * kWSplit + (threadIdx.x - (kWThreads - kWSplit / 8)) * 8);
+    };
+    for (int q = 0; q < STAGES - 1; ++q) {
+        if (c_lo + q < c_hi) stage(c_lo + q, q);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    double mom[4] = {0.0, 0.0, 0.0, 0.0};
+    float *hrow = H + lane * ld;
+    for (int64_t c = c_lo; c < c_hi; ++c) {
+        const int b = (int)((c - c_lo) % STAGES);
+        // keep STAGES - 1 blocks in flight: issue block c + STAGES - 1 (its
+        // buffer was last read in iteration c - 1, before that iteration's
+        // closing barrier), then wait for block c
+        if (c + STAGES - 1 < c_hi) stage(c + STAGES - 1, (int)((c + STAGES - 1 - c_lo) % STAGES));
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(STAGES - 1) : "memory");
+        __syncthreads();
+        const WStage &S = st[b];
+        const int t0 = S.split[warp], t1 = S.split[warp + 1];
+        const char *trow = reinterpret_cast<const char *>(&S.tile[lane][0]);
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, acc = 0.f;
+        uint32_t cur = t0 < t1 ? (S.pt[t0] >> kWBinShift) & kWBinMask : 0u;
+        // batches of eight positions: every load of a batch before its
+        // histogram updates, so the loads are in flight together; a word
+        // carries its column's byte offset, its bin and whether it starts one
+        for (int t = t0; t < t1; t += 8) {
+            uint32_t wd[8];
+            float4 zz[8];
+            float wv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int tt = min(t + u, t1 - 1);
+                wd[u] = S.pt[tt];
+                zz[u] = S.z[tt];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                wv[u] = t + u < t1 ? *reinterpret_cast<const float *>(trow + (wd[u] & kWColMask)) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                m0 = fmaf(wv[u], zz[u].x, m0);
+                m1 = fmaf(wv[u], zz[u].y, m1);
+                m2 = fmaf(wv[u], zz[u].z, m2);
+                m3 = fmaf(wv[u], zz[u].w, m3);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (t + u < t1 && (wd[u] & kWBinStart)) {  // uniform: every lane walks the same positions
+                    hrow[cur] += acc;
+                    acc = 0.f;
+                    cur = (wd[u] >> kWBinShift) & kWBinMask;
+                }
+                acc += wv[u];
+            }
+        }
+        if (t0 < t1) hrow[cur] += acc;
+        mom[0] += m0;
+        mom[1] += m1;
+        mom[2] += m2;
+        mom[3] += m3;
+        __syncthreads();  // buffer b and the histogram rows are free again
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    // the warps' moment sums of each row, reduced through the idle stage buffers
+    double *red = reinterpret_cast<double *>(wsm);  // [warps][kWRows][4]
+#pragma unroll
+    for (int j = 0; j < 4; ++j) red[(warp * kWRows + lane) * 4 + j] = mom[j];
+    __syncthreads();
+    if (threadIdx.x < kWRows * 4) {
+        const int r = threadIdx.x >> 2, j = threadIdx.x & 3;
+        double v = 0.0;
+        for (int q = 0; q < kWWarps; ++q) v += red[(q * kWRows + r) * 4 + j];
+        if (k0 + r < K) mpart[(split * K + k0 + r) * 4 + j] = v;
+    }
+    for (int e = threadIdx.x; e < kWRows * B; e += blockDim.x) {
+        const int r = e / B, bb = e - r * B;
+        if (k0 + r < K) hpart[(split * K + k0 + r) * B + bb] = H[r * ld + bb];
+    }
+}
+
+// Block sort of the grid points by bin (once per model): one CTA of 256
+// threads per block sorts the keys bin << 8 | local index (bitonic, in
+// shared memory), writes the sorted words (kWColMask etc.) and the powers z^j of z = y / s_abs
+// (FP32, as the other supplied-weights kernels form them) in sorted order,
+// and cuts the sorted positions into kWWarps slices at bin boundaries, each
+// boundary the one nearest an equal share.  Positions past the grid's end
+// sort last and are never walked.
+__global__ void __launch_bounds__(kWBlock) k_wsort_blocks(const int32_t *__restrict__ bins,
+                                                          const double *__restrict__ y, int64_t N,
+                                                          const double *__restrict__ scale,
+                                                          uint32_t *__restrict__ wpt, float4 *__restrict__ wz,
+                                                          uint16_t *__restrict__ wsplit) {
+    __shared__ uint32_t key[kWBlock];
+    const int t = threadIdx.x;
+    const int64_t c = blockIdx.x, col0 = c * kWBlock;
+    const int nv = (int)min((int64_t)kWBlock, N - col0);
+    key[t] = t < nv ? ((uint32_t)bins[col0 + t] << 8) | (uint32_t)t : 0xffffffffu;
+    __syncthreads();
+    for (int size = 2; size <= kWBlock; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const int o = t ^ stride;
+            if (o > t) {
+                const bool up = (t & size) == 0;
+                const uint32_t a = key[t], bb = key[o];
+                if ((a > bb) == up) {
+                    key[t] = bb;
+                    key[o] = a;
+                }
+            }
+            __syncthreads();
+        }
+    const uint32_t kw = key[t];
+    const bool starts = t < nv && (t == 0 || (key[t - 1] >> 8) != (kw >> 8));
+    wpt[col0 + t] = t < nv ? ((kw & 0xffu) << 2) | ((kw >> 8) << kWBinShift) | (starts ? kWBinStart : 0u) : 0u;
+    float4 zp = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t < nv) {
+        const float p = (float)(y[col0 + (kw & 0xffu)] / scale[kScaleAbs]);
+        zp.x = p;
+        zp.y = zp.x * p;
+        zp.z = zp.y * p;
+        zp.w = zp.z * p;
+    }
+    wz[col0 + t] = zp;
+    if (t == 0) {
+        uint16_t *sp = wsplit + c * kWSplit;
+        sp[0] = 0;
+        int prev = 0;
+        for (int w = 1; w < kWWarps; ++w) {
+            const int target = w * nv / kWWarps;
+            int lo = target, hi = target;  // nearest bin starts at or below / above the target
+            while (lo > prev && (key[lo] >> 8) == (key[lo - 1] >> 8)) --lo;
+            while (hi < nv && hi > 0 && (key[hi] >> 8) == (key[hi - 1] >> 8)) ++hi;
+            int pick = (target - lo <= hi - target) ? lo : hi;
+            if (pick < prev) pick = prev;
+            sp[w] = (uint16_t)pick;
+            prev = pick;
+        }
+        for (int w = kWWarps; w < kWSplit; ++w) sp[w] = (uint16_t)nv;
+    }
+}
+
 __global__ void k_weights_finish(const double *__restrict__ mpart, const float *__restrict__ hpart,
                                  int64_t n_split, int64_t K, int B, int J, const double *__restrict__ scale,
                                  double *__restrict__ raw, float *__restrict__ hist) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (hist && e < K * B) {
-        float s = 0.f;
+        double s = 0.0;
         for (int64_t q = 0; q < n_split; ++q) s += hpart[q * K * B + e];
-        hist[e] = s;
+        hist[e] = (float)s;
     }
     if (raw && e < K * J) {
         const int64_t k = e / J;
@@ -238,6 +446,55 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
     k_z32<<<(unsigned)std::min<int64_t>(ceil_div64(N, 256), 4096), 256, 0, s>>>(g->y, N, g->ydev_scale,
                                                                                 (float *)g_wz32.p);
     VUP_CHECK_LAUNCH();
+    const bool aligned = N % 4 == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+    if (B <= 1024 && aligned && ceil_div64(K, kWRows) <= 65535) {
+        const int64_t n_blk = ceil_div64(N, kWBlock);
+        if (g->wsort_gen != g->model_gen) {
+            if ((st = devbuf_reserve(g->wsort_pt, sizeof(uint32_t) * n_blk * kWBlock)) != VUP_OK ||
+                (st = devbuf_reserve(g->wsort_z, sizeof(float4) * n_blk * kWBlock)) != VUP_OK ||
+                (st = devbuf_reserve(g->wsort_split, sizeof(uint16_t) * kWSplit * n_blk)) != VUP_OK)
+                return st;
+            k_wsort_blocks<<<(unsigned)n_blk, kWBlock, 0, s>>>(g->bins, g->y, N, g->ydev_scale,
+                                                                (uint32_t *)g->wsort_pt.p, (float4 *)g->wsort_z.p,
+                                                                (uint16_t *)g->wsort_split.p);
+            VUP_CHECK_LAUNCH();
+            g->wsort_gen = g->model_gen;
+        }
+        const int64_t rows = ceil_div64(K, kWRows);
+        // column splits: enough CTAs to fill the GPU, each over at most
+        // kWMaxBlocksPerCta blocks
+        int64_t n_split = std::max<int64_t>(ceil_div64(n_blk, kWMaxBlocksPerCta),
+                                            ceil_div64((int64_t)vup_num_sms() * 2, rows));
+        n_split = std::min<int64_t>(n_split, n_blk);
+        if ((st = devbuf_reserve(g_wmpart, sizeof(double) * 4 * K * n_split)) != VUP_OK) return st;
+        if ((st = devbuf_reserve(g_whpart, sizeof(float) * (size_t)B * K * n_split)) != VUP_OK) return st;
+        // two stages of blocks in flight per CTA; up to 256 bins two CTAs per SM
+        const size_t smem = sizeof(WStage) * 2 + sizeof(float) * (size_t)kWRows * (B + 1);
+        VUP_PROF("weights_stream", s, 2);
+        dim3 grd((unsigned)n_split, (unsigned)rows);
+        if (B <= 256) {
+            VUP_CHECK_CUDA(cudaFuncSetAttribute(k_weights_sorted<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem));
+            k_weights_sorted<2, 2><<<grd, kWThreads, smem, s>>>(W, K, N, (const uint32_t *)g->wsort_pt.p,
+                                                                (const float4 *)g->wsort_z.p,
+                                                                (const uint16_t *)g->wsort_split.p, B, n_split,
+                                                                (double *)g_wmpart.p, (float *)g_whpart.p);
+        } else {
+            VUP_CHECK_CUDA(cudaFuncSetAttribute(k_weights_sorted<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem));
+            k_weights_sorted<2, 1><<<grd, kWThreads, smem, s>>>(W, K, N, (const uint32_t *)g->wsort_pt.p,
+                                                                (const float4 *)g->wsort_z.p,
+                                                                (const uint16_t *)g->wsort_split.p, B, n_split,
+                                                                (double *)g_wmpart.p, (float *)g_whpart.p);
+        }
+        VUP_CHECK_LAUNCH();
+        const int64_t tot = std::max<int64_t>(K * B, K * g->J);
+        k_weights_finish<<<(unsigned)ceil_div64(tot, 256), 256, 0, s>>>((const double *)g_wmpart.p,
+                                                                        (const float *)g_whpart.p, n_split, K, B,
+                                                                        g->J, g->ydev_scale, raw, hist);
+        VUP_CHECK_LAUNCH();
+        return VUP_OK;
+    }
     if (B <= 1024) {
         const int64_t rows = ceil_div64(K, kRowsT);
         int64_t n_split = std::max<int64_t>(1, (int64_t)vup_num_sms() * 4 / std::max<int64_t>(rows, 1));

@@ -281,6 +281,32 @@ def test_weights_path_matches_oracle():
     Hp.check_hist(hist.cpu().numpy(), res["hist"])
 
 
+def test_weights_path_full_grid_matches_oracle():
+    """The supplied-W path on the full c2 grid (1024^2 points, 4096 sorted
+    blocks, every CTA over 64 of them) for 48 densities, against the oracle at
+    the FP32 gates; a second call reuses the grid's block sort."""
+    vup = vupmod()
+    import torch
+    prob = I.config("c2")
+    rows = Hp.tile_rows(prob.K, 48, seed=71)
+    Wd = np.stack([O.weights(prob.n, prob.lo, prob.hi, prob.dens, int(k))[0] for k in rows])
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.eval_model(prob.model_id, prob.theta, prob.n_bins, 4)
+    W = torch.as_tensor(Wd.astype(np.float32), device="cuda")
+    del Wd
+    res = O.solve(prob, rows=rows, threads=Hp.oracle_threads())
+    scale = Hp.abs_moment_scale(prob, res["y"], rows)
+    amb = Hp.ambiguous_points(res["y"], res["bins"], prob.n_bins)
+    for _ in range(2):
+        raw = torch.empty((rows.size, 4), dtype=torch.float64, device="cuda")
+        hist = torch.empty((rows.size, prob.n_bins), dtype=torch.float32, device="cuda")
+        vup.vup_propagate_weights(g.h, W, raw, hist)
+        g.sync()
+        Hp.check_moments(raw.cpu().numpy(), res["raw"], scale, Hp.TOL["fp32"])
+        Hp.check_hist(hist.cpu().numpy(), res["hist"], Hp.ambiguous_mass(prob, amb, rows))
+    g.close()
+
+
 # ------------------------------------------------------------ IPSA adjoint
 # Gradients are gated at tol x their condition scale (oracle ipsa_scale: the
 # sum of the absolute values of the products that make up dM_j/dp), the same
