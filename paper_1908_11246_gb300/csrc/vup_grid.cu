@@ -859,13 +859,14 @@ __device__ __forceinline__ uint32_t rest_code(int32_t rest, int ndim, int64_t n1
 __global__ void k_layout_encode(const int32_t *__restrict__ run_start, const int32_t *__restrict__ run_rest,
                                 const int32_t *__restrict__ n_runs_p, const int32_t *__restrict__ iv_rest,
                                 const int32_t *__restrict__ n_iv_p, int ndim, int64_t n1, int shift,
-                                uint32_t *__restrict__ hpt, uint2 *__restrict__ ipt, const int32_t *gate) {
+                                uint32_t *__restrict__ hpt, uint2 *__restrict__ ipt, int run_ahead,
+                                const int32_t *gate) {
     if (gated_off(gate)) return;
     const int32_t n_runs = n_runs_p[0], n_iv = n_iv_p[0];
     const int32_t n = n_runs > n_iv ? n_runs : n_iv;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t xa = x + kRunAhead;
-        if (x < n_runs && xa < n_runs) hpt[run_start[x + 1] - 1] |= rest_code(run_rest[xa], ndim, n1, shift);
+        const int64_t xr = x + run_ahead, xa = x + kRunAhead;
+        if (x < n_runs && xr < n_runs) hpt[run_start[x + 1] - 1] |= rest_code(run_rest[xr], ndim, n1, shift);
         if (x < n_iv && xa < n_iv) reinterpret_cast<uint32_t *>(ipt + x)[1] |= rest_code(iv_rest[xa], ndim, n1, shift);
     }
 }
@@ -1746,8 +1747,12 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed, cuda
         k_layout_build<<<rb, 256, 0, s>>>(HL.perm, HL.keys, N, L, kRowShift, flags, excl, HL.run_start, HL.run_rest,
                                           HL.run_bin, HL.hpt, HL.n_runs, HL.ipt, HL.iv_rest, HL.n_iv, gate);
         VUP_CHECK_LAUNCH();
+        // run-end words carry the rest code of the run kRunAhead places later
+        // (their factors come from L2, loaded that far ahead), or of the next
+        // run when the 3-D point stream stages the rest factors in shared memory
+        const int run_ahead = vup_hist_rest_staged(g) ? 1 : kRunAhead;
         k_layout_encode<<<rb, 256, 0, s>>>(HL.run_start, HL.run_rest, HL.n_runs, HL.iv_rest, HL.n_iv, g->ndim,
-                                           g->ndim == 3 ? g->n[1] : 1, kRowShift, HL.hpt, HL.ipt, gate);
+                                           g->ndim == 3 ? g->n[1] : 1, kRowShift, HL.hpt, HL.ipt, run_ahead, gate);
         VUP_CHECK_LAUNCH();
         // chunks of every part
         const int PC = g->hist_P * C;

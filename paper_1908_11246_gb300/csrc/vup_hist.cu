@@ -74,6 +74,8 @@ struct HistArgs {
     int C_rec;            // record chunks per part
     int GB;               // record groups per part: ceil(B / kRecBins)
     int points_only;      // 1: point stream whatever the layout choice says
+    int rest_smem;        // 3-D point stream: both rest-axis factor tiles staged in shared memory
+    int64_t rest_n0;      // rows of the first rest axis (3-D)
     float *hist;          // [K][B]
     float *part;          // [P * C][2][K_pad]
     float *direct;        // [P][K][B] (P > 1)
@@ -128,10 +130,12 @@ __host__ __device__ inline size_t hist_warp_bytes() { return (size_t)2 * kWin * 
 // record stream with 16 warps of up to 128 registers (more of its five
 // gathers and four accumulators in flight per warp; measured faster when the
 // rest-factor table stays in L2, slower when its rows come from HBM and more
-// warps hide the latency).  The others run 20 warps of 96 registers.  Each
-// fills the register file of the one CTA per SM that the tile allows.
-__host__ __device__ constexpr int hist_warps(int mode) { return mode >= 2 ? 16 : kHistWarps; }
-__host__ __device__ constexpr int hist_stream_of(int mode) { return mode == 3 ? 2 : mode; }
+// warps hide the latency), 4 point stream of a 3-D grid with both rest-axis
+// factor tables staged in shared memory.  The others run 20 warps of 96
+// registers.  Each fills the register file of the one CTA per SM that the
+// tile allows.
+__host__ __device__ constexpr int hist_warps(int mode) { return (mode == 2 || mode == 3) ? 16 : kHistWarps; }
+__host__ __device__ constexpr int hist_stream_of(int mode) { return mode == 3 ? 2 : (mode == 4 ? 0 : mode); }
 __host__ __device__ inline size_t hist_smem_bytes(int64_t rows, int warps = kHistWarps) {
     return hist_tile_bytes(rows) + warps * hist_warp_bytes() + warps * 2 * sizeof(uint64_t);
 }
@@ -168,21 +172,48 @@ __device__ __forceinline__ float4 load_inv_z(const HistArgs &A, int64_t k) {
     return make_float4(inv_z(A, k), inv_z(A, k + 1), inv_z(A, k + 2), inv_z(A, k + 3));
 }
 
+// Four densities' values per lane, handled as two packed FP32 pairs: the
+// .f32x2 forms round each half exactly as the scalar operation does, so the
+// sums are bit-identical to four scalar FMAs / subtractions, in half the
+// instructions.
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 up2(uint64_t r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float4 from_pairs(uint64_t lo, uint64_t hi) {
+    const float2 l = up2(lo), h = up2(hi);
+    return make_float4(l.x, l.y, h.x, h.y);
+}
 __device__ __forceinline__ float4 ld4(const float *q) { return *reinterpret_cast<const float4 *>(q); }
 __device__ __forceinline__ float4 mul4(float4 a, float4 b) {
-    return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+    uint64_t lo, hi;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(lo) : "l"(pk2(a.x, a.y)), "l"(pk2(b.x, b.y)));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(hi) : "l"(pk2(a.z, a.w)), "l"(pk2(b.z, b.w)));
+    return from_pairs(lo, hi);
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) {
+    uint64_t lo, hi;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(lo) : "l"(pk2(a.x, a.y)), "l"(pk2(b.x, b.y)));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(hi) : "l"(pk2(a.z, a.w)), "l"(pk2(b.z, b.w)));
+    return from_pairs(lo, hi);
 }
 __device__ __forceinline__ void add4(float4 &a, float4 b) {
-    a.x += b.x;
-    a.y += b.y;
-    a.z += b.z;
-    a.w += b.w;
+    uint64_t lo = pk2(a.x, a.y), hi = pk2(a.z, a.w);
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(lo) : "l"(pk2(b.x, b.y)));
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(hi) : "l"(pk2(b.z, b.w)));
+    a = from_pairs(lo, hi);
 }
 __device__ __forceinline__ void fma4(float4 &a, float4 w, float4 b) {
-    a.x = fmaf(w.x, b.x, a.x);
-    a.y = fmaf(w.y, b.y, a.y);
-    a.z = fmaf(w.z, b.z, a.z);
-    a.w = fmaf(w.w, b.w, a.w);
+    uint64_t lo = pk2(a.x, a.y), hi = pk2(a.z, a.w);
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(lo) : "l"(pk2(w.x, w.y)), "l"(pk2(b.x, b.y)));
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(hi) : "l"(pk2(w.z, w.w)), "l"(pk2(b.z, b.w)));
+    a = from_pairs(lo, hi);
 }
 
 // Per-item context, kept in shared memory: the chosen layout, the output
@@ -195,6 +226,8 @@ struct ItemCtx {
     int64_t K, K_pad;
     int B, C, group_chunks, rec_sets, C_rec, GB;
     int mode;      // 0: point stream, tile holds factors; 1: interval stream, tile holds prefix sums
+    int rest_smem;  // (3-D point stream) rest-axis factors [n0][kKT], [n1][kKT] after the staging buffers
+    int64_t rest_n0;
     const float *prefix;
     int64_t pre_rows;
     int *dstatus;
@@ -287,8 +320,7 @@ __device__ __forceinline__ bool iv_chunk(const ItemCtx &X, int c, int p, int64_t
     };
     auto step = [&](uint32_t x, uint32_t y, float4 &f) {
         const float4 pa = gather(wsl + x), pb = gather(wsl + (y & kOffMask));
-        const float4 d = make_float4(pb.x - pa.x, pb.y - pa.y, pb.z - pa.z, pb.w - pa.w);
-        fma4(bacc, f, d);
+        fma4(bacc, f, sub4(pb, pa));
         f = coded_factor(y);
         if (y & kBinEnd) {
             flush(cur_key, bacc);
@@ -436,7 +468,6 @@ __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, i
                      : "r"(addr));
         return v;
     };
-    auto sub4 = [](float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); };
     auto step = [&](const uint4 u, const uint4 v, float4 &f) {
         // boundary rows B_0..B_8 (16 bits each); bins with B_j+1 == B_j are absent
         const uint32_t rw[kRecBinsH + 1] = {u.x & 0xffffu, u.x >> 16, u.y & 0xffffu, u.y >> 16, u.z & 0xffffu,
@@ -546,6 +577,8 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         X.prefix = A.prefix;
         X.pre_rows = A.pre_rows;
         X.dstatus = A.dstatus;
+        X.rest_smem = MODE == 4 ? 1 : 0;
+        X.rest_n0 = A.rest_n0;
     }
     if (threadIdx.x < kKT) s_invz[threadIdx.x] = inv_z(*Ap, k0 + threadIdx.x);
     __syncthreads();
@@ -556,7 +589,8 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     // normaliser 1 / prod_d Z_d
     const int64_t row0 = (int64_t)p * H.part_rows;
     const int64_t nrows = min(H.part_rows, H.n_last - row0);
-    const bool pre = MODE && X.prefix != nullptr;  // the prefix sums come ready-made
+    constexpr bool kPrefixTile = hist_stream_of(MODE) != 0;  // interval / record streams: prefix sums
+    const bool pre = kPrefixTile && X.prefix != nullptr;     // the prefix sums come ready-made
     if (pre) {
         const float *src = X.prefix + ((int64_t)p * (X.K_pad / kKT) + k0 / kKT) * X.pre_rows * kKT;
         for (int64_t e = threadIdx.x; e < (nrows + 1) * (kKT / 4); e += blockDim.x) cp_async16(ws + e * 4, src + e * 4);
@@ -568,6 +602,16 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
             cp_async16(ws + a * kKT + cc * 4, src + a * K_pad + cc * 4);
         }
     }
+    if (MODE == 4) {
+        // the k-tile's rows of both rest-axis factor tables (unnormalised)
+        float *rs = reinterpret_cast<float *>(sm + hist_smem_bytes(tile_rows, kWarps));
+        const int64_t n0 = X.rest_n0, n1 = H.n1, K_pad = X.K_pad;
+        for (int64_t e = threadIdx.x; e < (n0 + n1) * (kKT / 4); e += blockDim.x) {
+            const int64_t a = e / (kKT / 4), cc = e % (kKT / 4);
+            const float *src = a < n0 ? H.g0 + a * K_pad : H.g1 + (a - n0) * K_pad;
+            cp_async16(rs + a * kKT + cc * 4, src + k0 + cc * 4);
+        }
+    }
     cp_async_commit();
     if (!pre && threadIdx.x < kKT) ws[nrows * kKT + threadIdx.x] = 0.f;
     cp_async_wait_all();
@@ -575,7 +619,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
     if (pre) {
         // the staging buffers are next written by bulk copies (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    } else if (MODE) {
+    } else if (kPrefixTile) {
         // interval stream: every column becomes the exclusive prefix sums
         // P[0..nrows] of its scaled factors (compensated sums, each P rounded
         // once to FP32), so that rows a .. b - 1 sum to P[b] - P[a].  The
@@ -653,24 +697,46 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         const float *g0k = H.g0 + k;
         const float *g1k = NF == 2 ? H.g1 + k : nullptr;
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        // 3-D: the product of the two rest axes' rows; with the rows staged in
+        // shared memory (MODE 4) the first axis' row is kept in registers while
+        // consecutive runs share it (95% of them on the 3-D workload: runs of
+        // a bin are ordered by line)
+        constexpr bool rs = NF == 2 && MODE == 4;
+        const float *w0s = reinterpret_cast<const float *>(sm + hist_smem_bytes(tile_rows, kWarps)) + 4 * lane;
+        const float *w1s = w0s + X.rest_n0 * kKT;
+        uint32_t a0c = 0xffffffffu;
+        float4 w0c = zero4;
+        auto rest_rows = [&](uint32_t a0, uint32_t a1) -> float4 {
+            if (rs) {
+                if (a0 != a0c) {  // uniform: every lane follows the same run
+                    w0c = ld4(w0s + a0 * kKT);
+                    a0c = a0;
+                }
+                return mul4(w0c, ld4(w1s + a1 * kKT));
+            }
+            return mul4(ld4(g0k + (int64_t)a0 * K_pad), ld4(g1k + (int64_t)a1 * K_pad));
+        };
         auto rest_factor = [&](int32_t r) -> float4 {
             if (r >= r1) return zero4;
             const int32_t rest = H.run_rest[r];
             if (NF == 2) {
                 const int32_t a0 = rest / (int32_t)H.n1, a1 = rest - a0 * (int32_t)H.n1;
-                return mul4(ld4(g0k + a0 * K_pad), ld4(g1k + a1 * K_pad));
+                return rest_rows((uint32_t)a0, (uint32_t)a1);
             }
             return ld4(g0k + rest * K_pad);
         };
         // fc = factor of the current run, f1..f3 those of the next three runs
-        float4 fc = rest_factor(r0), f1 = rest_factor(r0 + 1), f2 = rest_factor(r0 + 2), f3 = rest_factor(r0 + 3);
-        // factor of run r + 4, decoded from run r's end word: 9 low bits below the
-        // row field and 12 bits above it
+        // (MODE 4: shared-memory factors, no look-ahead: fc only)
+        float4 fc = rest_factor(r0), f1 = zero4, f2 = zero4, f3 = zero4;
+        if (!rs) {
+            f1 = rest_factor(r0 + 1);
+            f2 = rest_factor(r0 + 2);
+            f3 = rest_factor(r0 + 3);
+        }
+        // factor of run r + 4 (MODE 4: r + 1), decoded from run r's end word: 9
+        // low bits below the row field and 12 bits above it
         auto coded_factor = [&](uint32_t u) -> float4 {
-            if (NF == 2) {
-                const uint32_t a0 = u & 0x1ffu, a1 = (u >> 18) & 0xfffu;
-                return mul4(ld4(g0k + (int64_t)a0 * K_pad), ld4(g1k + (int64_t)a1 * K_pad));
-            }
+            if (NF == 2) return rest_rows(u & 0x1ffu, (u >> 18) & 0xfffu);
             const uint32_t idx = (u & 0x1ffu) | (((u >> 18) & 0xfffu) << 9);
             return ld4(g0k + (int64_t)idx * K_pad);
         };
@@ -689,10 +755,14 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
                 bacc = zero4;
                 cur_key = r + 1 < r1 ? H.run_bin[r + 1] : -1;
             }
-            fc = f1;
-            f1 = f2;
-            f2 = f3;
-            f3 = coded_factor(u);
+            if (rs) {
+                fc = r + 1 < r1 ? coded_factor(u) : zero4;
+            } else {
+                fc = f1;
+                f1 = f2;
+                f2 = f3;
+                f3 = coded_factor(u);
+            }
             ++r;
         };
         auto gather = [&](uint32_t addr) -> float4 {
@@ -762,7 +832,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         if (cur_key >= 0) flush(cur_key, bacc);
         return true;
     };
-    if constexpr (MODE >= 2) {
+    if constexpr (hist_stream_of(MODE) == 2) {
         // this item's range of the part's record chunks, handed out one at a time
         const int c_lo = (int)((int64_t)cg * X.C_rec / X.rec_sets), c_hi = (int)((int64_t)(cg + 1) * X.C_rec / X.rec_sets);
         for (;;) {
@@ -1176,6 +1246,12 @@ bool vup_hist_prefix(vup_grid g, int64_t K, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess;
 }
 
+bool vup_hist_rest_staged(const vup_grid_s *g) {
+    if (g->ndim != 3 || g->hl[0].last_axis != 2 || g->n[0] > 512 || g->n[1] > 4096) return false;
+    const size_t rest_bytes = (size_t)(g->n[0] + g->n[1]) * kKT * sizeof(float);
+    return hist_smem_bytes(g->hl[0].part_rows, hist_warps(4)) + rest_bytes <= 220 * 1024;
+}
+
 vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, const float *ftab,
                           bool points_only, cudaEvent_t keys_ready, bool prefix_ready) {
     const int nd = g->ndim;
@@ -1186,6 +1262,10 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
     // run-end words encode the rest index in 21 bits (3-D: a0 < 512, a1 < 4096)
     const bool coded = nd == 2 || (g->n[0] <= 512 && g->n[1] <= 4096);
     const bool in_smem = smem <= 220 * 1024 && coded;
+    // 3-D point stream: both rest-axis factor tiles in shared memory when they fit beside the tile
+    const size_t rest_bytes = nd == 3 ? (size_t)(g->n[0] + g->n[1]) * kKT * sizeof(float) : 0;
+    A.rest_n0 = nd == 3 ? g->n[0] : 0;
+    A.rest_smem = in_smem && vup_hist_rest_staged(g);
     // the global-memory fallback walks points whatever the device chose
     points_only = points_only || !in_smem;
     A.points_only = points_only ? 1 : 0;
@@ -1236,7 +1316,7 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
         VUP_PROF("hist_segmented", s, in_smem && !points_only ? 3 : 1);
         if (in_smem) {
             auto launch = [&](auto kern, int gg, int items, int mode) -> vup_status {
-                const size_t sm_bytes = hist_smem_bytes(rows, hist_warps(mode));
+                const size_t sm_bytes = hist_smem_bytes(rows, hist_warps(mode)) + (mode == 4 ? rest_bytes : 0);
                 VUP_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes));
                 VUP_CHECK_CUDA(launch_pdl(kern, dim3(items), dim3(hist_warps(mode) * 32), sm_bytes, s, A, rows,
                                           P_max, gg, items));
@@ -1258,7 +1338,9 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
                 if (st != VUP_OK) return st;
             }
             if (keys_ready) VUP_CHECK_CUDA(cudaStreamWaitEvent(s, keys_ready, 0));
-            st = nd == 3 ? launch(k_hist_smem<2, 0>, G, n_items, 0) : launch(k_hist_smem<1, 0>, G, n_items, 0);
+            st = nd == 3 ? (A.rest_smem ? launch(k_hist_smem<2, 4>, G, n_items, 4)
+                                        : launch(k_hist_smem<2, 0>, G, n_items, 0))
+                         : launch(k_hist_smem<1, 0>, G, n_items, 0);
             if (st != VUP_OK) return st;
             if (!points_only) {
                 st = nd == 3 ? launch(k_hist_smem<2, 1>, G, n_items, 1) : launch(k_hist_smem<1, 1>, G, n_items, 1);

@@ -300,6 +300,9 @@ vup_status vup_build_layout(vup_grid g, cudaStream_t s, bool points_needed = fal
 vup_status vup_ensure_layout(vup_grid g, cudaStream_t s, bool points_needed = false);
 // every layout's part tile fits the shared-memory histogram kernels
 bool vup_hist_tile_fits(vup_grid g);
+// the 3-D point stream stages both rest-axis factor tables in shared memory
+// (and its run-end words then carry the next run's rest code)
+bool vup_hist_rest_staged(const vup_grid_s *g);
 vup_status vup_build_tables(vup_grid g, int orient, int bf16, cudaStream_t s);
 vup_status vup_natural_sort(vup_grid g, cudaStream_t s);
 
