@@ -574,14 +574,7 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
             VUP_CHECK_CUDA(cudaEventCreateWithFlags(&g->ev_lay, cudaEventDisableTiming));
         }
         VUP_CHECK_CUDA(cudaEventRecord(g->ev_fork, s));
-        VUP_CHECK_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
-        vup_status lst = vup_build_layout(g, g->side, false, g->ev_rec, g->ev_lay);
-        VUP_CHECK_CUDA(cudaEventRecord(g->ev_join, g->side));
         forked = true;
-        if (lst != VUP_OK) {
-            cudaStreamWaitEvent(s, g->ev_join, 0);
-            return lst;
-        }
     }
     // every return below joins the second stream back into the caller's
     struct Join {
@@ -597,6 +590,14 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
                       VUP_OK)
         return st;
     if ((st = vup_density_prep(g, d, ((bf16 || tf32) && want_m) ? (1 << to) : 0, s, tf32)) != VUP_OK) return st;
+    if (forked) {
+        // the layout's launches are enqueued after the density preparation's, so
+        // that the main stream's work is not held behind their host-side cost
+        VUP_CHECK_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+        vup_status lst = vup_build_layout(g, g->side, false, g->ev_rec, g->ev_lay);
+        VUP_CHECK_CUDA(cudaEventRecord(g->ev_join, g->side));
+        if (lst != VUP_OK) return lst;
+    }
     // the histogram's prefix-sum tiles on a third stream, beside the
     // contraction (they need the densities and the layout choice only)
     bool prefix_ready = false;

@@ -218,14 +218,18 @@ constexpr int kWRows = 32;
 constexpr int kWMaxBlocksPerCta = 64;   // bounds each FP32 histogram sum
 constexpr int kWWarps = 8;              // warp slices per block
 constexpr int kWThreads = kWWarps * 32;
-constexpr int kWSplit = 32;             // split entries per block (kWWarps + 1, padded)
-// sorted word: column byte offset in the tile row (bits 0-9), bin (10-22),
-// first position of its bin (31)
-constexpr uint32_t kWColMask = 0x3ffu, kWBinShift = 10, kWBinMask = 0x1fffu, kWBinStart = 1u << 31;
+constexpr int kWSplit = 16;             // split entries per block (kWWarps + 1, padded)
+// each warp slice padded to a multiple of 8 positions (at most 7 fillers per
+// slice): a block's sorted list takes at most kWBlock + 7 kWWarps entries
+constexpr int kWPad = kWBlock + 64;
+// sorted word: column byte offset in the tile row (bits 0-10), bin (11-23),
+// first position of its bin (31); fillers point at the zero column, no flag
+constexpr uint32_t kWColMask = 0x7ffu, kWBinShift = 11, kWBinMask = 0x1fffu, kWBinStart = 1u << 31;
+constexpr uint32_t kWFiller = (uint32_t)kWBlock * 4u;
 struct WStage {
-    float tile[kWRows][kWLd];
-    uint32_t pt[kWBlock];
-    float4 z[kWBlock];
+    float tile[kWRows][kWLd];  // column kWBlock is zero (the fillers' column)
+    uint32_t pt[kWPad];
+    float4 z[kWPad];
     uint16_t split[kWSplit];
 };
 
@@ -250,6 +254,7 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
     const int64_t split = blockIdx.x;
     const int64_t c_lo = split * n_blk / n_split, c_hi = (split + 1) * n_blk / n_split;
     for (int e = threadIdx.x; e < kWRows * ld; e += blockDim.x) H[e] = 0.f;
+    for (int e = threadIdx.x; e < STAGES * kWRows; e += blockDim.x) st[e / kWRows].tile[e % kWRows][kWBlock] = 0.f;
 
     // stage block c into buffer b: 32 rows x 64 chunks of W (rows past K
     // re-read row K - 1, never stored), 64 chunks of sorted words, 256 of powers
@@ -261,8 +266,8 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
             const int r = e >> 6, c4 = e & 63;
             if (c4 * 4 < ncol) cp_async16(&S.tile[r][c4 * 4], W + min(k0 + r, K - 1) * N + col0 + c4 * 4);
         }
-        if (threadIdx.x < kWBlock / 4) cp_async16(&S.pt[threadIdx.x * 4], wpt + col0 + threadIdx.x * 4);
-        for (int e = threadIdx.x; e < kWBlock; e += blockDim.x) cp_async16(&S.z[e], wz + col0 + e);
+        if (threadIdx.x < kWPad / 4) cp_async16(&S.pt[threadIdx.x * 4], wpt + c * kWPad + threadIdx.x * 4);
+        for (int e = threadIdx.x; e < kWPad; e += blockDim.x) cp_async16(&S.z[e], wz + c * kWPad + e);
         if (threadIdx.x >= kWThreads - kWSplit / 8)
             cp_async16(&S.split[(threadIdx.x - (kWThreads - kWSplit / 8)) * 8],
                        wsplit + c * kWSplit + (threadIdx.x - (kWThreads - kWSplit / 8)) * 8);
@@ -290,29 +295,25 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         // batches of eight positions: every load of a batch before its
         // histogram updates, so the loads are in flight together; a word
         // carries its column's byte offset, its bin and whether it starts one
+        // the slice is a whole number of batches (fillers read the zero column)
         for (int t = t0; t < t1; t += 8) {
-            uint32_t wd[8];
-            float4 zz[8];
+            const uint4 wa = *reinterpret_cast<const uint4 *>(&S.pt[t]);
+            const uint4 wb = *reinterpret_cast<const uint4 *>(&S.pt[t + 4]);
+            const uint32_t wd[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
             float wv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int tt = min(t + u, t1 - 1);
-                wd[u] = S.pt[tt];
-                zz[u] = S.z[tt];
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                wv[u] = t + u < t1 ? *reinterpret_cast<const float *>(trow + (wd[u] & kWColMask)) : 0.f;
+            for (int u = 0; u < 8; ++u) wv[u] = *reinterpret_cast<const float *>(trow + (wd[u] & kWColMask));
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                m0 = fmaf(wv[u], zz[u].x, m0);
-                m1 = fmaf(wv[u], zz[u].y, m1);
-                m2 = fmaf(wv[u], zz[u].z, m2);
-                m3 = fmaf(wv[u], zz[u].w, m3);
+                const float4 z = S.z[t + u];
+                m0 = fmaf(wv[u], z.x, m0);
+                m1 = fmaf(wv[u], z.y, m1);
+                m2 = fmaf(wv[u], z.z, m2);
+                m3 = fmaf(wv[u], z.w, m3);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                if (t + u < t1 && (wd[u] & kWBinStart)) {  // uniform: every lane walks the same positions
+                if (wd[u] & kWBinStart) {  // uniform: every lane walks the same positions
                     hrow[cur] += acc;
                     acc = 0.f;
                     cur = (wd[u] >> kWBinShift) & kWBinMask;
@@ -377,20 +378,9 @@ __global__ void __launch_bounds__(kWBlock) k_wsort_blocks(const int32_t *__restr
             }
             __syncthreads();
         }
-    const uint32_t kw = key[t];
-    const bool starts = t < nv && (t == 0 || (key[t - 1] >> 8) != (kw >> 8));
-    wpt[col0 + t] = t < nv ? ((kw & 0xffu) << 2) | ((kw >> 8) << kWBinShift) | (starts ? kWBinStart : 0u) : 0u;
-    float4 zp = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (t < nv) {
-        const float p = (float)(y[col0 + (kw & 0xffu)] / scale[kScaleAbs]);
-        zp.x = p;
-        zp.y = zp.x * p;
-        zp.z = zp.y * p;
-        zp.w = zp.z * p;
-    }
-    wz[col0 + t] = zp;
+    // slice boundaries (unpadded positions), then each slice's padded start
+    __shared__ int sp[kWWarps + 1], pp[kWWarps + 1];
     if (t == 0) {
-        uint16_t *sp = wsplit + c * kWSplit;
         sp[0] = 0;
         int prev = 0;
         for (int w = 1; w < kWWarps; ++w) {
@@ -400,10 +390,35 @@ __global__ void __launch_bounds__(kWBlock) k_wsort_blocks(const int32_t *__restr
             while (hi < nv && hi > 0 && (key[hi] >> 8) == (key[hi - 1] >> 8)) ++hi;
             int pick = (target - lo <= hi - target) ? lo : hi;
             if (pick < prev) pick = prev;
-            sp[w] = (uint16_t)pick;
+            sp[w] = pick;
             prev = pick;
         }
-        for (int w = kWWarps; w < kWSplit; ++w) sp[w] = (uint16_t)nv;
+        sp[kWWarps] = nv;
+        pp[0] = 0;
+        for (int w = 0; w < kWWarps; ++w) pp[w + 1] = pp[w] + ((sp[w + 1] - sp[w] + 7) & ~7);
+        uint16_t *o = wsplit + c * kWSplit;
+        for (int w = 0; w < kWSplit; ++w) o[w] = (uint16_t)pp[w <= kWWarps ? w : kWWarps];
+    }
+    __syncthreads();
+    // every padded position: a point of some slice, or a filler
+    for (int q = t; q < kWPad; q += blockDim.x) {
+        int w = 0;
+        while (w < kWWarps - 1 && q >= pp[w + 1]) ++w;
+        const int u = sp[w] + (q - pp[w]);  // unpadded position, if q is not a filler
+        uint32_t word = kWFiller;
+        float4 zp = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < pp[kWWarps] && u < sp[w + 1]) {
+            const uint32_t kw = key[u];
+            const bool starts = u == 0 || (key[u - 1] >> 8) != (kw >> 8);
+            word = ((kw & 0xffu) << 2) | ((kw >> 8) << kWBinShift) | (starts ? kWBinStart : 0u);
+            const float p = (float)(y[col0 + (kw & 0xffu)] / scale[kScaleAbs]);
+            zp.x = p;
+            zp.y = zp.x * p;
+            zp.z = zp.y * p;
+            zp.w = zp.z * p;
+        }
+        wpt[c * kWPad + q] = word;
+        wz[c * kWPad + q] = zp;
     }
 }
 
@@ -450,8 +465,8 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
     if (B <= 1024 && aligned && ceil_div64(K, kWRows) <= 65535) {
         const int64_t n_blk = ceil_div64(N, kWBlock);
         if (g->wsort_gen != g->model_gen) {
-            if ((st = devbuf_reserve(g->wsort_pt, sizeof(uint32_t) * n_blk * kWBlock)) != VUP_OK ||
-                (st = devbuf_reserve(g->wsort_z, sizeof(float4) * n_blk * kWBlock)) != VUP_OK ||
+            if ((st = devbuf_reserve(g->wsort_pt, sizeof(uint32_t) * n_blk * kWPad)) != VUP_OK ||
+                (st = devbuf_reserve(g->wsort_z, sizeof(float4) * n_blk * kWPad)) != VUP_OK ||
                 (st = devbuf_reserve(g->wsort_split, sizeof(uint16_t) * kWSplit * n_blk)) != VUP_OK)
                 return st;
             k_wsort_blocks<<<(unsigned)n_blk, kWBlock, 0, s>>>(g->bins, g->y, N, g->ydev_scale,
