@@ -277,7 +277,8 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
     double mom[4] = {0.0, 0.0, 0.0, 0.0};
-    float *hrow = H + lane * ld;
+    const float *hrow = H + lane * ld;
+    const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(hrow);
     for (int64_t c = c_lo; c < c_hi; ++c) {
         const int b = (int)((c - c_lo) % STAGES);
         // keep STAGES - 1 blocks in flight: issue block c + STAGES - 1 (its
@@ -291,18 +292,34 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         const int t0 = S.split[warp], t1 = S.split[warp + 1];
         const char *trow = reinterpret_cast<const char *>(&S.tile[lane][0]);
         float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, acc = 0.f;
-        uint32_t cur = t0 < t1 ? (S.pt[t0] >> kWBinShift) & kWBinMask : 0u;
-        // batches of eight positions: every load of a batch before its
-        // histogram updates, so the loads are in flight together; a word
-        // carries its column's byte offset, its bin and whether it starts one
-        // the slice is a whole number of batches (fillers read the zero column)
+        // the open run: the shared address of its histogram entry and its
+        // sum so far, which starts from the entry's old value; every bin of a
+        // block is one run of one slice, so the entries a batch reads at its
+        // start are ones no earlier run of the block wrote.  Before the first
+        // run the open entry is the spare column B.
+        uint32_t cur = hbase + (uint32_t)B * 4u;
+        // batches of eight positions: every load of a batch (tile values,
+        // powers, the histogram entries of the runs it starts) is issued
+        // before its arithmetic, and a run's close is a predicated store, not
+        // a branch; a word carries its column's byte offset, its bin and
+        // whether it starts one; the slice is a whole number of batches
+        // (fillers read the zero column and start no run)
         for (int t = t0; t < t1; t += 8) {
             const uint4 wa = *reinterpret_cast<const uint4 *>(&S.pt[t]);
             const uint4 wb = *reinterpret_cast<const uint4 *>(&S.pt[t + 4]);
             const uint32_t wd[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-            float wv[8];
+            float wv[8], hv[8];
+            uint32_t ha[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) wv[u] = *reinterpret_cast<const float *>(trow + (wd[u] & kWColMask));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                hv[u] = 0.f;
+                ha[u] = hbase + (((wd[u] >> kWBinShift) & kWBinMask) << 2);
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p ld.shared.f32 %0, [%1];\n\t}"
+                             : "+f"(hv[u])
+                             : "r"(ha[u]), "r"(wd[u] & kWBinStart));
+            }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const float4 z = S.z[t + u];
@@ -313,15 +330,15 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                if (wd[u] & kWBinStart) {  // uniform: every lane walks the same positions
-                    hrow[cur] += acc;
-                    acc = 0.f;
-                    cur = (wd[u] >> kWBinShift) & kWBinMask;
-                }
-                acc += wv[u];
+                const uint32_t st_u = wd[u] & kWBinStart;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.shared.f32 [%0], %1;\n\t}"
+                             ::"r"(cur), "f"(acc), "r"(st_u)
+                             : "memory");
+                acc = (st_u ? hv[u] : acc) + wv[u];
+                cur = st_u ? ha[u] : cur;
             }
         }
-        if (t0 < t1) hrow[cur] += acc;
+        if (t0 < t1) asm volatile("st.shared.f32 [%0], %1;" ::"r"(cur), "f"(acc) : "memory");
         mom[0] += m0;
         mom[1] += m1;
         mom[2] += m2;
@@ -476,32 +493,49 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
             g->wsort_gen = g->model_gen;
         }
         const int64_t rows = ceil_div64(K, kWRows);
-        // column splits: enough CTAs to fill the GPU, each over at most
-        // kWMaxBlocksPerCta blocks
-        int64_t n_split = std::max<int64_t>(ceil_div64(n_blk, kWMaxBlocksPerCta),
-                                            ceil_div64((int64_t)vup_num_sms() * 2, rows));
-        n_split = std::min<int64_t>(n_split, n_blk);
+        // two CTAs of two stages per SM when their histogram rows fit (the
+        // walks of two CTAs overlap each other's barriers; measured faster
+        // than one CTA of four stages), else one CTA with as many stages as
+        // shared memory holds, up to four
+        const size_t hbytes = sizeof(float) * (size_t)kWRows * (B + 1);
+        const size_t cap = 227 * 1024;
+        const bool two_ctas = 2 * (sizeof(WStage) * 2 + hbytes) <= cap;
+        int stages = two_ctas ? 2 : 4;
+        while (stages > 2 && sizeof(WStage) * stages + hbytes > cap) --stages;
+        const size_t smem = sizeof(WStage) * stages + hbytes;
+        // column splits: each CTA over at most kWMaxBlocksPerCta blocks; among
+        // the counts that allows, the one with the shortest schedule of
+        // (waves of CTAs) x (blocks per CTA), searched up to 16 waves (past
+        // that the last wave's tail costs little and the partial histograms
+        // grow with the count)
+        const int64_t slots = (int64_t)vup_num_sms() * (two_ctas ? 2 : 1);
+        const int64_t lo_split = std::min<int64_t>(ceil_div64(n_blk, kWMaxBlocksPerCta), n_blk);
+        const int64_t hi_split = std::max<int64_t>(lo_split, std::min<int64_t>(n_blk, 16 * slots / rows));
+        int64_t n_split = lo_split, best = -1;
+        for (int64_t q = lo_split; q <= hi_split; ++q) {
+            const int64_t cost = ceil_div64(q * rows, slots) * ceil_div64(n_blk, q);
+            if (best < 0 || cost < best) best = cost, n_split = q;
+        }
         if ((st = devbuf_reserve(g_wmpart, sizeof(double) * 4 * K * n_split)) != VUP_OK) return st;
         if ((st = devbuf_reserve(g_whpart, sizeof(float) * (size_t)B * K * n_split)) != VUP_OK) return st;
-        // two stages of blocks in flight per CTA; up to 256 bins two CTAs per SM
-        const size_t smem = sizeof(WStage) * 2 + sizeof(float) * (size_t)kWRows * (B + 1);
         VUP_PROF("weights_stream", s, 2);
         dim3 grd((unsigned)n_split, (unsigned)rows);
-        if (B <= 256) {
-            VUP_CHECK_CUDA(cudaFuncSetAttribute(k_weights_sorted<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)smem));
-            k_weights_sorted<2, 2><<<grd, kWThreads, smem, s>>>(W, K, N, (const uint32_t *)g->wsort_pt.p,
-                                                                (const float4 *)g->wsort_z.p,
-                                                                (const uint16_t *)g->wsort_split.p, B, n_split,
-                                                                (double *)g_wmpart.p, (float *)g_whpart.p);
-        } else {
-            VUP_CHECK_CUDA(cudaFuncSetAttribute(k_weights_sorted<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)smem));
-            k_weights_sorted<2, 1><<<grd, kWThreads, smem, s>>>(W, K, N, (const uint32_t *)g->wsort_pt.p,
-                                                                (const float4 *)g->wsort_z.p,
-                                                                (const uint16_t *)g->wsort_split.p, B, n_split,
-                                                                (double *)g_wmpart.p, (float *)g_whpart.p);
-        }
+        auto launch = [&](auto kern) -> vup_status {
+            VUP_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<grd, kWThreads, smem, s>>>(W, K, N, (const uint32_t *)g->wsort_pt.p, (const float4 *)g->wsort_z.p,
+                                             (const uint16_t *)g->wsort_split.p, B, n_split, (double *)g_wmpart.p,
+                                             (float *)g_whpart.p);
+            return VUP_OK;
+        };
+        if (two_ctas)
+            st = launch(k_weights_sorted<2, 2>);
+        else if (stages == 4)
+            st = launch(k_weights_sorted<4, 1>);
+        else if (stages == 3)
+            st = launch(k_weights_sorted<3, 1>);
+        else
+            st = launch(k_weights_sorted<2, 1>);
+        if (st != VUP_OK) return st;
         VUP_CHECK_LAUNCH();
         const int64_t tot = std::max<int64_t>(K * B, K * g->J);
         k_weights_finish<<<(unsigned)ceil_div64(tot, 256), 256, 0, s>>>((const double *)g_wmpart.p,
