@@ -5,6 +5,7 @@
 // Eq. MUP applied to each column).  The kernel is bound by the W read:
 // 4 bytes per distribution-point.
 #include "vup_internal.cuh"
+#include "vup_async.cuh"
 
 #include <algorithm>
 
@@ -204,9 +205,12 @@ __global__ void __launch_bounds__(kThreads) k_weights_t(const float *__restrict_
 // bin once per model (wsort_*), and the block's sorted positions are cut at
 // bin boundaries into eight nearly equal warp slices.  A CTA owns 32 rows of
 // W (lane l: row k0 + l) and a range of blocks; each block's 32 x 256 tile of
-// W is staged in shared memory with cp.async (kWStages deep, rows padded to
-// 260 floats: a warp reading one column of 32 rows hits 32 banks) together
-// with the block's sorted words and powers.  Warp w walks its slice: a bin's
+// W is staged in shared memory by bulk copies (cp.async.bulk, one per row,
+// issued by warp 0 and completing on the stage's mbarrier; STAGES deep)
+// together with the block's sorted words and powers.  Rows are padded to 260
+// floats: a warp reading one column of 32 rows touches 8 banks (a 4-way
+// conflict; rows copied in 16-byte units cannot spread one column over more
+// than 8).  Warp w walks its slice: a bin's
 // points are summed in a register and added once to the lane's histogram row
 // in shared memory -- every (row, bin) entry of a block has one writer, so no
 // atomics -- and the moments are summed per block in FP32 and across blocks
@@ -233,18 +237,16 @@ struct WStage {
     uint16_t split[kWSplit];
 };
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
+using namespace vup_async;
 
 template <int STAGES, int MINB>
 __global__ void __launch_bounds__(kWThreads, MINB)
 k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32_t *__restrict__ wpt,
                  const float4 *__restrict__ wz, const uint16_t *__restrict__ wsplit, int B, int64_t n_split,
-                 double *__restrict__ mpart, float *__restrict__ hpart) {
+                 double *__restrict__ mpart, float *__restrict__ hpart, int *dstatus) {
     extern __shared__ __align__(16) uint8_t wsm[];
+    __shared__ uint64_t full[STAGES];
+    __shared__ int abort_flag;
     WStage *st = reinterpret_cast<WStage *>(wsm);
     float *H = reinterpret_cast<float *>(wsm + sizeof(WStage) * STAGES);  // [kWRows][B + 1]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -255,27 +257,34 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
     const int64_t c_lo = split * n_blk / n_split, c_hi = (split + 1) * n_blk / n_split;
     for (int e = threadIdx.x; e < kWRows * ld; e += blockDim.x) H[e] = 0.f;
     for (int e = threadIdx.x; e < STAGES * kWRows; e += blockDim.x) st[e / kWRows].tile[e % kWRows][kWBlock] = 0.f;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < STAGES; ++q) mbar_init(&full[q], 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
-    // stage block c into buffer b: 32 rows x 64 chunks of W (rows past K
-    // re-read row K - 1, never stored), 64 chunks of sorted words, 256 of powers
+    // stage block c into buffer b (warp 0): one bulk copy per row of W (lane
+    // l: row k0 + l; rows past K re-read row K - 1, never stored), one each
+    // for the block's sorted words, powers and slice starts, all completing
+    // on full[b]
     auto stage = [&](int64_t c, int b) {
         WStage &S = st[b];
         const int64_t col0 = c * kWBlock;
-        const int64_t ncol = min((int64_t)kWBlock, N - col0);
-        for (int e = threadIdx.x; e < kWRows * (kWBlock / 4); e += blockDim.x) {
-            const int r = e >> 6, c4 = e & 63;
-            if (c4 * 4 < ncol) cp_async16(&S.tile[r][c4 * 4], W + min(k0 + r, K - 1) * N + col0 + c4 * 4);
+        const uint32_t row_bytes = (uint32_t)min((int64_t)kWBlock, N - col0) * 4u;
+        if (lane == 0)
+            mbar_expect_tx(&full[b], kWRows * row_bytes + (uint32_t)(sizeof(S.pt) + sizeof(S.z) + sizeof(S.split)));
+        __syncwarp();
+        bulk_g2s(&S.tile[lane][0], W + min(k0 + lane, K - 1) * N + col0, row_bytes, &full[b]);
+        if (lane == 0) {
+            bulk_g2s(S.pt, wpt + c * kWPad, (uint32_t)sizeof(S.pt), &full[b]);
+            bulk_g2s(S.z, wz + c * kWPad, (uint32_t)sizeof(S.z), &full[b]);
+            bulk_g2s(S.split, wsplit + c * kWSplit, (uint32_t)sizeof(S.split), &full[b]);
         }
-        if (threadIdx.x < kWPad / 4) cp_async16(&S.pt[threadIdx.x * 4], wpt + c * kWPad + threadIdx.x * 4);
-        for (int e = threadIdx.x; e < kWPad; e += blockDim.x) cp_async16(&S.z[e], wz + c * kWPad + e);
-        if (threadIdx.x >= kWThreads - kWSplit / 8)
-            cp_async16(&S.split[(threadIdx.x - (kWThreads - kWSplit / 8)) * 8],
-                       wsplit + c * kWSplit + (threadIdx.x - (kWThreads - kWSplit / 8)) * 8);
     };
-    for (int q = 0; q < STAGES - 1; ++q) {
-        if (c_lo + q < c_hi) stage(c_lo + q, q);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
+    int64_t issued = 0;  // blocks staged so far (warp 0's count)
+    if (warp == 0)
+        for (int q = 0; q < STAGES - 1 && c_lo + q < c_hi; ++q, ++issued) stage(c_lo + q, q);
     double mom[4] = {0.0, 0.0, 0.0, 0.0};
     const float *hrow = H + lane * ld;
     const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(hrow);
@@ -283,13 +292,16 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         const int b = (int)((c - c_lo) % STAGES);
         // keep STAGES - 1 blocks in flight: issue block c + STAGES - 1 (its
         // buffer was last read in iteration c - 1, before that iteration's
-        // closing barrier), then wait for block c
-        if (c + STAGES - 1 < c_hi) stage(c + STAGES - 1, (int)((c + STAGES - 1 - c_lo) % STAGES));
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group %0;" ::"n"(STAGES - 1) : "memory");
-        __syncthreads();
+        // closing barrier), then wait for block c.  After an expired wait
+        // nothing more is issued or walked; every thread still meets the
+        // closing barriers, and the copies in flight are drained below.
+        if (warp == 0 && !abort_flag && c + STAGES - 1 < c_hi) {
+            stage(c + STAGES - 1, (int)((c + STAGES - 1 - c_lo) % STAGES));
+            ++issued;
+        }
+        const bool ready = mbar_wait(&full[b], (uint32_t)(((c - c_lo) / STAGES) & 1), &abort_flag, dstatus);
         const WStage &S = st[b];
-        const int t0 = S.split[warp], t1 = S.split[warp + 1];
+        const int t0 = ready ? S.split[warp] : 0, t1 = ready ? S.split[warp + 1] : 0;
         const char *trow = reinterpret_cast<const char *>(&S.tile[lane][0]);
         float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, acc = 0.f;
         // the open run: the shared address of its histogram entry and its
@@ -345,8 +357,14 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         mom[3] += m3;
         __syncthreads();  // buffer b and the histogram rows are free again
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
+    if (abort_flag) {
+        // drain: wait (bounded) for the last phase staged into each buffer,
+        // then leave without writing partial results
+        if (threadIdx.x == 0)
+            for (int64_t i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i)
+                mbar_drain(&full[i % STAGES], (uint32_t)((i / STAGES) & 1));
+        return;
+    }
     // the warps' moment sums of each row, reduced through the idle stage buffers
     double *red = reinterpret_cast<double *>(wsm);  // [warps][kWRows][4]
 #pragma unroll
@@ -524,7 +542,7 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
             VUP_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<grd, kWThreads, smem, s>>>(W, K, N, (const uint32_t *)g->wsort_pt.p, (const float4 *)g->wsort_z.p,
                                              (const uint16_t *)g->wsort_split.p, B, n_split, (double *)g_wmpart.p,
-                                             (float *)g_whpart.p);
+                                             (float *)g_whpart.p, g->dstatus);
             return VUP_OK;
         };
         if (two_ctas)
