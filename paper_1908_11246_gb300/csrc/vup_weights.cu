@@ -239,6 +239,14 @@ struct WStage {
 
 using namespace vup_async;
 
+// hi + lo += x: TwoSum (Knuth) of hi and x, the rounding error kept in lo
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+
 template <int STAGES, int MINB>
 __global__ void __launch_bounds__(kWThreads, MINB)
 k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32_t *__restrict__ wpt,
@@ -285,7 +293,10 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
     int64_t issued = 0;  // blocks staged so far (warp 0's count)
     if (warp == 0)
         for (int q = 0; q < STAGES - 1 && c_lo + q < c_hi; ++q, ++issued) stage(c_lo + q, q);
-    double mom[4] = {0.0, 0.0, 0.0, 0.0};
+    // per-row moment sums across blocks: FP32 pairs (sum, compensation)
+    // updated by TwoSum (Knuth), exact to about FP32 squared; one FP64
+    // conversion per CTA at the end
+    float mhi[4] = {0.f, 0.f, 0.f, 0.f}, mlo[4] = {0.f, 0.f, 0.f, 0.f};
     const float *hrow = H + lane * ld;
     const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(hrow);
     for (int64_t c = c_lo; c < c_hi; ++c) {
@@ -351,10 +362,10 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
             }
         }
         if (t0 < t1) asm volatile("st.shared.f32 [%0], %1;" ::"r"(cur), "f"(acc) : "memory");
-        mom[0] += m0;
-        mom[1] += m1;
-        mom[2] += m2;
-        mom[3] += m3;
+        two_sum_acc(mhi[0], mlo[0], m0);
+        two_sum_acc(mhi[1], mlo[1], m1);
+        two_sum_acc(mhi[2], mlo[2], m2);
+        two_sum_acc(mhi[3], mlo[3], m3);
         __syncthreads();  // buffer b and the histogram rows are free again
     }
     if (abort_flag) {
@@ -368,7 +379,7 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
     // the warps' moment sums of each row, reduced through the idle stage buffers
     double *red = reinterpret_cast<double *>(wsm);  // [warps][kWRows][4]
 #pragma unroll
-    for (int j = 0; j < 4; ++j) red[(warp * kWRows + lane) * 4 + j] = mom[j];
+    for (int j = 0; j < 4; ++j) red[(warp * kWRows + lane) * 4 + j] = (double)mhi[j] + (double)mlo[j];
     __syncthreads();
     if (threadIdx.x < kWRows * 4) {
         const int r = threadIdx.x >> 2, j = threadIdx.x & 3;
