@@ -226,13 +226,14 @@ constexpr int kWSplit = 16;             // split entries per block (kWWarps + 1,
 // each warp slice padded to a multiple of 8 positions (at most 7 fillers per
 // slice): a block's sorted list takes at most kWBlock + 7 kWWarps entries
 constexpr int kWPad = kWBlock + 64;
-// sorted word: column byte offset in the tile row (bits 0-10), bin (11-23),
-// first position of its bin (31); fillers point at the zero column, no flag
-constexpr uint32_t kWColMask = 0x7ffu, kWBinShift = 11, kWBinMask = 0x1fffu, kWBinStart = 1u << 31;
-constexpr uint32_t kWFiller = (uint32_t)kWBlock * 4u;
+// two words per sorted position: the byte offset of its column in a tile
+// row (pt[t]), and the byte offset of its bin in a histogram row plus 1 if
+// it is the first position of its bin (pt[kWPad + t]); fillers: the zero
+// column, bin word 0
+constexpr uint32_t kWFillerCol = (uint32_t)kWBlock * 4u;
 struct WStage {
     float tile[kWRows][kWLd];  // column kWBlock is zero (the fillers' column)
-    uint32_t pt[kWPad];
+    uint32_t pt[2 * kWPad];
     float4 z[kWPad];
     uint16_t split[kWSplit];
 };
@@ -285,7 +286,7 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         __syncwarp();
         bulk_g2s(&S.tile[lane][0], W + min(k0 + lane, K - 1) * N + col0, row_bytes, &full[b]);
         if (lane == 0) {
-            bulk_g2s(S.pt, wpt + c * kWPad, (uint32_t)sizeof(S.pt), &full[b]);
+            bulk_g2s(S.pt, wpt + c * 2 * kWPad, (uint32_t)sizeof(S.pt), &full[b]);
             bulk_g2s(S.z, wz + c * kWPad, (uint32_t)sizeof(S.z), &full[b]);
             bulk_g2s(S.split, wsplit + c * kWSplit, (uint32_t)sizeof(S.split), &full[b]);
         }
@@ -298,7 +299,7 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
     // conversion per CTA at the end
     float mhi[4] = {0.f, 0.f, 0.f, 0.f}, mlo[4] = {0.f, 0.f, 0.f, 0.f};
     const float *hrow = H + lane * ld;
-    const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(hrow);
+    const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(hrow), hbase_m1 = hbase - 1u;
     for (int64_t c = c_lo; c < c_hi; ++c) {
         const int b = (int)((c - c_lo) % STAGES);
         // keep STAGES - 1 blocks in flight: issue block c + STAGES - 1 (its
@@ -328,20 +329,24 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         // whether it starts one; the slice is a whole number of batches
         // (fillers read the zero column and start no run)
         for (int t = t0; t < t1; t += 8) {
-            const uint4 wa = *reinterpret_cast<const uint4 *>(&S.pt[t]);
-            const uint4 wb = *reinterpret_cast<const uint4 *>(&S.pt[t + 4]);
-            const uint32_t wd[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+            const uint4 ca = *reinterpret_cast<const uint4 *>(&S.pt[t]);
+            const uint4 cb = *reinterpret_cast<const uint4 *>(&S.pt[t + 4]);
+            const uint4 ba = *reinterpret_cast<const uint4 *>(&S.pt[kWPad + t]);
+            const uint4 bb = *reinterpret_cast<const uint4 *>(&S.pt[kWPad + t + 4]);
+            const uint32_t cw[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+            const uint32_t bw[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
             float wv[8], hv[8];
             uint32_t ha[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) wv[u] = *reinterpret_cast<const float *>(trow + (wd[u] & kWColMask));
+            for (int u = 0; u < 8; ++u) wv[u] = *reinterpret_cast<const float *>(trow + cw[u]);
+            // a run's first position: its entry's address is hbase + (bw - 1);
+            // elsewhere ha and hv are not used
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                hv[u] = 0.f;
-                ha[u] = hbase + (((wd[u] >> kWBinShift) & kWBinMask) << 2);
+                ha[u] = hbase_m1 + bw[u];
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p ld.shared.f32 %0, [%1];\n\t}"
-                             : "+f"(hv[u])
-                             : "r"(ha[u]), "r"(wd[u] & kWBinStart));
+                             : "=f"(hv[u])
+                             : "r"(ha[u]), "r"(bw[u] & 1u));
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -353,7 +358,7 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const uint32_t st_u = wd[u] & kWBinStart;
+                const uint32_t st_u = bw[u] & 1u;
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.shared.f32 [%0], %1;\n\t}"
                              ::"r"(cur), "f"(acc), "r"(st_u)
                              : "memory");
@@ -395,7 +400,7 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
 
 // Block sort of the grid points by bin (once per model): one CTA of 256
 // threads per block sorts the keys bin << 8 | local index (bitonic, in
-// shared memory), writes the sorted words (kWColMask etc.) and the powers z^j of z = y / s_abs
+// shared memory), writes the sorted words (column and bin offsets) and the powers z^j of z = y / s_abs
 // (FP32, as the other supplied-weights kernels form them) in sorted order,
 // and cuts the sorted positions into kWWarps slices at bin boundaries, each
 // boundary the one nearest an equal share.  Positions past the grid's end
@@ -451,19 +456,21 @@ __global__ void __launch_bounds__(kWBlock) k_wsort_blocks(const int32_t *__restr
         int w = 0;
         while (w < kWWarps - 1 && q >= pp[w + 1]) ++w;
         const int u = sp[w] + (q - pp[w]);  // unpadded position, if q is not a filler
-        uint32_t word = kWFiller;
+        uint32_t cword = kWFillerCol, bword = 0u;
         float4 zp = make_float4(0.f, 0.f, 0.f, 0.f);
         if (q < pp[kWWarps] && u < sp[w + 1]) {
             const uint32_t kw = key[u];
             const bool starts = u == 0 || (key[u - 1] >> 8) != (kw >> 8);
-            word = ((kw & 0xffu) << 2) | ((kw >> 8) << kWBinShift) | (starts ? kWBinStart : 0u);
+            cword = (kw & 0xffu) << 2;
+            bword = ((kw >> 8) << 2) | (starts ? 1u : 0u);
             const float p = (float)(y[col0 + (kw & 0xffu)] / scale[kScaleAbs]);
             zp.x = p;
             zp.y = zp.x * p;
             zp.z = zp.y * p;
             zp.w = zp.z * p;
         }
-        wpt[c * kWPad + q] = word;
+        wpt[c * 2 * kWPad + q] = cword;
+        wpt[c * 2 * kWPad + kWPad + q] = bword;
         wz[c * kWPad + q] = zp;
     }
 }
@@ -511,7 +518,7 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
     if (B <= 1024 && aligned && ceil_div64(K, kWRows) <= 65535) {
         const int64_t n_blk = ceil_div64(N, kWBlock);
         if (g->wsort_gen != g->model_gen) {
-            if ((st = devbuf_reserve(g->wsort_pt, sizeof(uint32_t) * n_blk * kWPad)) != VUP_OK ||
+            if ((st = devbuf_reserve(g->wsort_pt, sizeof(uint32_t) * n_blk * 2 * kWPad)) != VUP_OK ||
                 (st = devbuf_reserve(g->wsort_z, sizeof(float4) * n_blk * kWPad)) != VUP_OK ||
                 (st = devbuf_reserve(g->wsort_split, sizeof(uint16_t) * kWSplit * n_blk)) != VUP_OK)
                 return st;
