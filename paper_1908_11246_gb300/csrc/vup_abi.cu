@@ -285,7 +285,7 @@ static void free_grid(vup_grid g) {
     devbuf_free(g->atf_lo);
     devbuf_free(g->wsort_pt);
     devbuf_free(g->wsort_z);
-    devbuf_free(g->wsort_split);
+    devbuf_free(g->wsort_fix);
     delete g;
 }
 

@@ -277,7 +277,7 @@ struct vup_grid_s {
     // points sorted by bin (word: local index | bin << 8), their powers of
     // z = y / s_abs in that order, and every block's split into eight warp
     // slices at bin boundaries; built for model generation wsort_gen
-    DevBuf wsort_pt, wsort_z, wsort_split;
+    DevBuf wsort_pt, wsort_z, wsort_fix;
     uint64_t wsort_gen = ~0ull;
 
     int *dstatus = nullptr;        // [1] device status word

@@ -202,40 +202,51 @@ __global__ void __launch_bounds__(kThreads) k_weights_t(const float *__restrict_
 
 // Sorted-block walk (B <= 1024, rows of W 16-byte aligned).  The grid's
 // points are cut into blocks of kWBlock; within a block they are sorted by
-// bin once per model (wsort_*), and the block's sorted positions are cut at
-// bin boundaries into eight nearly equal warp slices.  A CTA owns 32 rows of
-// W (lane l: row k0 + l) and a range of blocks; each block's 32 x 256 tile of
-// W is staged in shared memory by bulk copies (cp.async.bulk, one per row,
-// issued by warp 0 and completing on the stage's mbarrier; STAGES deep)
-// together with the block's sorted words and powers.  Rows are padded to 260
-// floats: a warp reading one column of 32 rows touches 8 banks (a 4-way
-// conflict; rows copied in 16-byte units cannot spread one column over more
-// than 8).  Warp w walks its slice: a bin's
-// points are summed in a register and added once to the lane's histogram row
-// in shared memory -- every (row, bin) entry of a block has one writer, so no
-// atomics -- and the moments are summed per block in FP32 and across blocks
-// in FP64.  The histogram rows hold at most ~64 blocks' contributions per bin
-// (column splits are sized for that), the partial rows are summed in FP64.
+// bin once per model (wsort_*), and warp w walks sorted positions
+// [32 w, 32 w + 32) of every block.  A CTA owns 32 rows of W (lane l: row
+// k0 + l) and a range of blocks; each block's 32 x 256 tile of W is staged in
+// shared memory by bulk copies (cp.async.bulk, one per row, issued by warp 0
+// and completing on the stage's mbarrier; two stages) together with the
+// block's sorted words and powers.  Rows are padded to 260 floats: a warp
+// reading one column of 32 rows touches 8 banks (a 4-way conflict; rows
+// copied in 16-byte units cannot spread one column over more than 8).  A
+// bin's points (a run) are summed in a register and added once to the lane's
+// histogram row in shared memory.  A run inside one slice has one writer and
+// is added by a plain read-modify-write; a run that crosses a slice edge is
+// summed per slice into the warp's own scratch columns of the row and added
+// to its bin with a shared-memory atomic after the walk.  The moments are
+// summed per block in FP32 and across blocks as TwoSum pairs.  The histogram
+// rows hold at most ~64 blocks' contributions per bin (column splits are
+// sized for that), the partial rows are summed in FP64.
 constexpr int kWBlock = 256;
 constexpr int kWLd = kWBlock + 4;       // padded tile row (floats)
 constexpr int kWRows = 32;
 constexpr int kWMaxBlocksPerCta = 64;   // bounds each FP32 histogram sum
 constexpr int kWWarps = 8;              // warp slices per block
 constexpr int kWThreads = kWWarps * 32;
-constexpr int kWSplit = 16;             // split entries per block (kWWarps + 1, padded)
-// each warp slice padded to a multiple of 8 positions (at most 7 fillers per
-// slice): a block's sorted list takes at most kWBlock + 7 kWWarps entries
-constexpr int kWPad = kWBlock + 64;
+constexpr int kWSlice = kWBlock / kWWarps;
+// Histogram row of a lane: bins 0..B-1, then a spare column B (the flush
+// before a slice's first run lands there), the warps' head columns B+1+w (a
+// run continued from the previous slice) and tail columns B+1+kWWarps+w (a
+// run continuing into the next slice); odd row length, so that the 32 rows'
+// entries of one column fall in 32 banks.
+constexpr int kWExtraCols = 1 + 2 * kWWarps;
+__host__ __device__ constexpr int w_hist_ld(int B) { return (B + kWExtraCols) | 1; }
 // two words per sorted position: the byte offset of its column in a tile
-// row (pt[t]), and the byte offset of its bin in a histogram row plus 1 if
-// it is the first position of its bin (pt[kWPad + t]); fillers: the zero
-// column, bin word 0
+// row (pt[t]), and the byte offset of its histogram entry plus 1 if it is the
+// first position of its run (pt[kWBlock + t]); a run that continues into the
+// next slice names the warp's tail column.  Positions past the grid's end:
+// the zero column, word 0.  fix[w] / fix[kWWarps + w]: the bin of slice w's
+// head / tail run with bit 15 set when that run crosses the slice's start /
+// end.
 constexpr uint32_t kWFillerCol = (uint32_t)kWBlock * 4u;
+constexpr int kWFix = 2 * kWWarps;
+constexpr uint16_t kWCross = 0x8000u;
 struct WStage {
     float tile[kWRows][kWLd];  // column kWBlock is zero (the fillers' column)
-    uint32_t pt[2 * kWPad];
-    float4 z[kWPad];
-    uint16_t split[kWSplit];
+    uint32_t pt[2 * kWBlock];
+    float4 z[kWBlock];
+    uint16_t fix[kWFix];
 };
 
 using namespace vup_async;
@@ -251,15 +262,15 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
 template <int STAGES, int MINB>
 __global__ void __launch_bounds__(kWThreads, MINB)
 k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32_t *__restrict__ wpt,
-                 const float4 *__restrict__ wz, const uint16_t *__restrict__ wsplit, int B, int64_t n_split,
+                 const float4 *__restrict__ wz, const uint16_t *__restrict__ wfix, int B, int64_t n_split,
                  double *__restrict__ mpart, float *__restrict__ hpart, int *dstatus) {
     extern __shared__ __align__(16) uint8_t wsm[];
     __shared__ uint64_t full[STAGES];
     __shared__ int abort_flag;
     WStage *st = reinterpret_cast<WStage *>(wsm);
-    float *H = reinterpret_cast<float *>(wsm + sizeof(WStage) * STAGES);  // [kWRows][B + 1]
+    float *H = reinterpret_cast<float *>(wsm + sizeof(WStage) * STAGES);  // [kWRows][ld]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ld = B + 1;
+    const int ld = w_hist_ld(B);
     const int64_t k0 = (int64_t)blockIdx.y * kWRows;
     const int64_t n_blk = (N + kWBlock - 1) / kWBlock;
     const int64_t split = blockIdx.x;
@@ -275,20 +286,20 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
 
     // stage block c into buffer b (warp 0): one bulk copy per row of W (lane
     // l: row k0 + l; rows past K re-read row K - 1, never stored), one each
-    // for the block's sorted words, powers and slice starts, all completing
+    // for the block's sorted words, powers and crossing runs, all completing
     // on full[b]
     auto stage = [&](int64_t c, int b) {
         WStage &S = st[b];
         const int64_t col0 = c * kWBlock;
         const uint32_t row_bytes = (uint32_t)min((int64_t)kWBlock, N - col0) * 4u;
         if (lane == 0)
-            mbar_expect_tx(&full[b], kWRows * row_bytes + (uint32_t)(sizeof(S.pt) + sizeof(S.z) + sizeof(S.split)));
+            mbar_expect_tx(&full[b], kWRows * row_bytes + (uint32_t)(sizeof(S.pt) + sizeof(S.z) + sizeof(S.fix)));
         __syncwarp();
         bulk_g2s(&S.tile[lane][0], W + min(k0 + lane, K - 1) * N + col0, row_bytes, &full[b]);
         if (lane == 0) {
-            bulk_g2s(S.pt, wpt + c * 2 * kWPad, (uint32_t)sizeof(S.pt), &full[b]);
-            bulk_g2s(S.z, wz + c * kWPad, (uint32_t)sizeof(S.z), &full[b]);
-            bulk_g2s(S.split, wsplit + c * kWSplit, (uint32_t)sizeof(S.split), &full[b]);
+            bulk_g2s(S.pt, wpt + c * 2 * kWBlock, (uint32_t)sizeof(S.pt), &full[b]);
+            bulk_g2s(S.z, wz + c * kWBlock, (uint32_t)sizeof(S.z), &full[b]);
+            bulk_g2s(S.fix, wfix + c * kWFix, (uint32_t)sizeof(S.fix), &full[b]);
         }
     };
     int64_t issued = 0;  // blocks staged so far (warp 0's count)
@@ -313,15 +324,19 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         }
         const bool ready = mbar_wait(&full[b], (uint32_t)(((c - c_lo) / STAGES) & 1), &abort_flag, dstatus);
         const WStage &S = st[b];
-        const int t0 = ready ? S.split[warp] : 0, t1 = ready ? S.split[warp + 1] : 0;
+        const int t0 = ready ? warp * kWSlice : 0, t1 = ready ? t0 + kWSlice : 0;
+        const uint32_t head = ready ? S.fix[warp] : 0u, tail = ready ? S.fix[kWWarps + warp] : 0u;
         const char *trow = reinterpret_cast<const char *>(&S.tile[lane][0]);
         float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, acc = 0.f;
         // the open run: the shared address of its histogram entry and its
-        // sum so far, which starts from the entry's old value; every bin of a
-        // block is one run of one slice, so the entries a batch reads at its
-        // start are ones no earlier run of the block wrote.  Before the first
-        // run the open entry is the spare column B.
-        uint32_t cur = hbase + (uint32_t)B * 4u;
+        // sum so far, which starts from the entry's old value (a run inside
+        // the slice: no other run of the block has its bin, so the entries a
+        // batch reads at its start are ones no earlier run wrote; a run
+        // crossing the slice's end: the warp's tail column, zero).  Before
+        // the slice's first run start the open entry is the warp's head
+        // column if the slice begins inside a run, else the spare column B.
+        const uint32_t head_col = hbase + (uint32_t)(B + 1 + warp) * 4u;
+        uint32_t cur = (head & kWCross) ? head_col : hbase + (uint32_t)B * 4u;
         // batches of eight positions: every load of a batch (tile values,
         // powers, the histogram entries of the runs it starts) is issued
         // before its arithmetic, and a run's close is a predicated store, not
@@ -331,8 +346,8 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         for (int t = t0; t < t1; t += 8) {
             const uint4 ca = *reinterpret_cast<const uint4 *>(&S.pt[t]);
             const uint4 cb = *reinterpret_cast<const uint4 *>(&S.pt[t + 4]);
-            const uint4 ba = *reinterpret_cast<const uint4 *>(&S.pt[kWPad + t]);
-            const uint4 bb = *reinterpret_cast<const uint4 *>(&S.pt[kWPad + t + 4]);
+            const uint4 ba = *reinterpret_cast<const uint4 *>(&S.pt[kWBlock + t]);
+            const uint4 bb = *reinterpret_cast<const uint4 *>(&S.pt[kWBlock + t + 4]);
             const uint32_t cw[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
             const uint32_t bw[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
             float wv[8], hv[8];
@@ -366,7 +381,17 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
                 cur = st_u ? ha[u] : cur;
             }
         }
-        if (t0 < t1) asm volatile("st.shared.f32 [%0], %1;" ::"r"(cur), "f"(acc) : "memory");
+        if (t0 < t1) {
+            asm volatile("st.shared.f32 [%0], %1;" ::"r"(cur), "f"(acc) : "memory");
+            // crossing runs: this slice's part, from the warp's own columns,
+            // added to the bin atomically (other slices add their parts)
+            float *hrow_w = H + lane * ld;
+            if (head & kWCross) atomicAdd(hrow_w + (head & 0x7fffu), hrow_w[B + 1 + warp]);
+            if (tail & kWCross) {
+                atomicAdd(hrow_w + (tail & 0x7fffu), hrow_w[B + 1 + kWWarps + warp]);
+                hrow_w[B + 1 + kWWarps + warp] = 0.f;
+            }
+        }
         two_sum_acc(mhi[0], mlo[0], m0);
         two_sum_acc(mhi[1], mlo[1], m1);
         two_sum_acc(mhi[2], mlo[2], m2);
@@ -400,16 +425,16 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
 
 // Block sort of the grid points by bin (once per model): one CTA of 256
 // threads per block sorts the keys bin << 8 | local index (bitonic, in
-// shared memory), writes the sorted words (column and bin offsets) and the powers z^j of z = y / s_abs
-// (FP32, as the other supplied-weights kernels form them) in sorted order,
-// and cuts the sorted positions into kWWarps slices at bin boundaries, each
-// boundary the one nearest an equal share.  Positions past the grid's end
-// sort last and are never walked.
+// shared memory) and writes, in sorted order, the column words, the
+// histogram words (see WStage) and the powers z^j of z = y / s_abs (FP32, as
+// the other supplied-weights kernels form them), and for each warp slice the
+// bins of the runs that cross its start and its end.  Positions past the
+// grid's end sort last.
 __global__ void __launch_bounds__(kWBlock) k_wsort_blocks(const int32_t *__restrict__ bins,
                                                           const double *__restrict__ y, int64_t N,
-                                                          const double *__restrict__ scale,
+                                                          const double *__restrict__ scale, int B,
                                                           uint32_t *__restrict__ wpt, float4 *__restrict__ wz,
-                                                          uint16_t *__restrict__ wsplit) {
+                                                          uint16_t *__restrict__ wfix) {
     __shared__ uint32_t key[kWBlock];
     const int t = threadIdx.x;
     const int64_t c = blockIdx.x, col0 = c * kWBlock;
@@ -429,49 +454,36 @@ __global__ void __launch_bounds__(kWBlock) k_wsort_blocks(const int32_t *__restr
             }
             __syncthreads();
         }
-    // slice boundaries (unpadded positions), then each slice's padded start
-    __shared__ int sp[kWWarps + 1], pp[kWWarps + 1];
-    if (t == 0) {
-        sp[0] = 0;
-        int prev = 0;
-        for (int w = 1; w < kWWarps; ++w) {
-            const int target = w * nv / kWWarps;
-            int lo = target, hi = target;  // nearest bin starts at or below / above the target
-            while (lo > prev && (key[lo] >> 8) == (key[lo - 1] >> 8)) --lo;
-            while (hi < nv && hi > 0 && (key[hi] >> 8) == (key[hi - 1] >> 8)) ++hi;
-            int pick = (target - lo <= hi - target) ? lo : hi;
-            if (pick < prev) pick = prev;
-            sp[w] = pick;
-            prev = pick;
+    auto bin_at = [&](int q) { return key[q] >> 8; };
+    // position q continues the run of q - 1 (q a real position)
+    auto cont = [&](int q) { return q > 0 && q < nv && bin_at(q) == bin_at(q - 1); };
+    uint32_t cword = kWFillerCol, bword = 0u;
+    float4 zp = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t < nv) {
+        const uint32_t kw = key[t];
+        const int w = t / kWSlice, next = (w + 1) * kWSlice;  // first position of the next slice
+        cword = (kw & 0xffu) << 2;
+        if (!cont(t)) {
+            const bool crosses = next < nv && bin_at(next) == (kw >> 8);
+            bword = ((crosses ? (uint32_t)(B + 1 + kWWarps + w) : (kw >> 8)) << 2) | 1u;
         }
-        sp[kWWarps] = nv;
-        pp[0] = 0;
-        for (int w = 0; w < kWWarps; ++w) pp[w + 1] = pp[w] + ((sp[w + 1] - sp[w] + 7) & ~7);
-        uint16_t *o = wsplit + c * kWSplit;
-        for (int w = 0; w < kWSplit; ++w) o[w] = (uint16_t)pp[w <= kWWarps ? w : kWWarps];
+        const float p = (float)(y[col0 + (kw & 0xffu)] / scale[kScaleAbs]);
+        zp.x = p;
+        zp.y = zp.x * p;
+        zp.z = zp.y * p;
+        zp.w = zp.z * p;
     }
-    __syncthreads();
-    // every padded position: a point of some slice, or a filler
-    for (int q = t; q < kWPad; q += blockDim.x) {
-        int w = 0;
-        while (w < kWWarps - 1 && q >= pp[w + 1]) ++w;
-        const int u = sp[w] + (q - pp[w]);  // unpadded position, if q is not a filler
-        uint32_t cword = kWFillerCol, bword = 0u;
-        float4 zp = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (q < pp[kWWarps] && u < sp[w + 1]) {
-            const uint32_t kw = key[u];
-            const bool starts = u == 0 || (key[u - 1] >> 8) != (kw >> 8);
-            cword = (kw & 0xffu) << 2;
-            bword = ((kw >> 8) << 2) | (starts ? 1u : 0u);
-            const float p = (float)(y[col0 + (kw & 0xffu)] / scale[kScaleAbs]);
-            zp.x = p;
-            zp.y = zp.x * p;
-            zp.z = zp.y * p;
-            zp.w = zp.z * p;
-        }
-        wpt[c * 2 * kWPad + q] = cword;
-        wpt[c * 2 * kWPad + kWPad + q] = bword;
-        wz[c * kWPad + q] = zp;
+    wpt[c * 2 * kWBlock + t] = cword;
+    wpt[c * 2 * kWBlock + kWBlock + t] = bword;
+    wz[c * kWBlock + t] = zp;
+    if (t < kWWarps) {
+        const int p0 = t * kWSlice, p1 = p0 + kWSlice;
+        // head: the slice begins inside a run; tail: a run that starts in the
+        // slice continues into the next one
+        const bool head = cont(p0);
+        const bool tail = cont(p1) && !(head && bin_at(p0) == bin_at(p1));
+        wfix[c * kWFix + t] = head ? (uint16_t)(bin_at(p0) | kWCross) : 0;
+        wfix[c * kWFix + kWWarps + t] = tail ? (uint16_t)(bin_at(p1) | kWCross) : 0;
     }
 }
 
@@ -518,13 +530,13 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
     if (B <= 1024 && aligned && ceil_div64(K, kWRows) <= 65535) {
         const int64_t n_blk = ceil_div64(N, kWBlock);
         if (g->wsort_gen != g->model_gen) {
-            if ((st = devbuf_reserve(g->wsort_pt, sizeof(uint32_t) * n_blk * 2 * kWPad)) != VUP_OK ||
-                (st = devbuf_reserve(g->wsort_z, sizeof(float4) * n_blk * kWPad)) != VUP_OK ||
-                (st = devbuf_reserve(g->wsort_split, sizeof(uint16_t) * kWSplit * n_blk)) != VUP_OK)
+            if ((st = devbuf_reserve(g->wsort_pt, sizeof(uint32_t) * n_blk * 2 * kWBlock)) != VUP_OK ||
+                (st = devbuf_reserve(g->wsort_z, sizeof(float4) * n_blk * kWBlock)) != VUP_OK ||
+                (st = devbuf_reserve(g->wsort_fix, sizeof(uint16_t) * kWFix * n_blk)) != VUP_OK)
                 return st;
-            k_wsort_blocks<<<(unsigned)n_blk, kWBlock, 0, s>>>(g->bins, g->y, N, g->ydev_scale,
+            k_wsort_blocks<<<(unsigned)n_blk, kWBlock, 0, s>>>(g->bins, g->y, N, g->ydev_scale, B,
                                                                 (uint32_t *)g->wsort_pt.p, (float4 *)g->wsort_z.p,
-                                                                (uint16_t *)g->wsort_split.p);
+                                                                (uint16_t *)g->wsort_fix.p);
             VUP_CHECK_LAUNCH();
             g->wsort_gen = g->model_gen;
         }
@@ -533,7 +545,7 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
         // walks of two CTAs overlap each other's barriers; measured faster
         // than one CTA of four stages), else one CTA with as many stages as
         // shared memory holds, up to four
-        const size_t hbytes = sizeof(float) * (size_t)kWRows * (B + 1);
+        const size_t hbytes = sizeof(float) * (size_t)kWRows * w_hist_ld(B);
         const size_t cap = 227 * 1024;
         const bool two_ctas = 2 * (sizeof(WStage) * 2 + hbytes) <= cap;
         int stages = two_ctas ? 2 : 4;
@@ -559,7 +571,7 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
         auto launch = [&](auto kern) -> vup_status {
             VUP_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<grd, kWThreads, smem, s>>>(W, K, N, (const uint32_t *)g->wsort_pt.p, (const float4 *)g->wsort_z.p,
-                                             (const uint16_t *)g->wsort_split.p, B, n_split, (double *)g_wmpart.p,
+                                             (const uint16_t *)g->wsort_fix.p, B, n_split, (double *)g_wmpart.p,
                                              (float *)g_whpart.p, g->dstatus);
             return VUP_OK;
         };
