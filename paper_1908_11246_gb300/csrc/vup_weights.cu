@@ -278,33 +278,37 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
     for (int e = threadIdx.x; e < kWRows * ld; e += blockDim.x) H[e] = 0.f;
     for (int e = threadIdx.x; e < STAGES * kWRows; e += blockDim.x) st[e / kWRows].tile[e % kWRows][kWBlock] = 0.f;
     if (threadIdx.x == 0) {
-        for (int q = 0; q < STAGES; ++q) mbar_init(&full[q], 1);
+        for (int q = 0; q < STAGES; ++q) mbar_init(&full[q], kWWarps);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    // stage block c into buffer b (warp 0): one bulk copy per row of W (lane
-    // l: row k0 + l; rows past K re-read row K - 1, never stored), one each
-    // for the block's sorted words, powers and crossing runs, all completing
-    // on full[b]
+    // stage block c into buffer b (every warp: lanes 0-3 of warp w copy rows
+    // 4 w .. 4 w + 3 of W, rows past K re-reading row K - 1, never stored;
+    // warp 0 also the block's sorted words, powers and crossing runs); each
+    // warp adds its bytes to full[b] and arrives once
     auto stage = [&](int64_t c, int b) {
         WStage &S = st[b];
         const int64_t col0 = c * kWBlock;
         const uint32_t row_bytes = (uint32_t)min((int64_t)kWBlock, N - col0) * 4u;
-        if (lane == 0)
-            mbar_expect_tx(&full[b], kWRows * row_bytes + (uint32_t)(sizeof(S.pt) + sizeof(S.z) + sizeof(S.fix)));
+        constexpr uint32_t meta = (uint32_t)(sizeof(WStage::pt) + sizeof(WStage::z) + sizeof(WStage::fix));
+        constexpr int rows_per_warp = kWRows / kWWarps;
+        if (lane == 0) mbar_expect_tx(&full[b], rows_per_warp * row_bytes + (warp == 0 ? meta : 0u));
         __syncwarp();
-        bulk_g2s(&S.tile[lane][0], W + min(k0 + lane, K - 1) * N + col0, row_bytes, &full[b]);
-        if (lane == 0) {
+        if (lane < rows_per_warp) {
+            const int r = warp * rows_per_warp + lane;
+            bulk_g2s(&S.tile[r][0], W + min(k0 + r, K - 1) * N + col0, row_bytes, &full[b]);
+        }
+        if (warp == 0 && lane == 0) {
             bulk_g2s(S.pt, wpt + c * 2 * kWBlock, (uint32_t)sizeof(S.pt), &full[b]);
             bulk_g2s(S.z, wz + c * kWBlock, (uint32_t)sizeof(S.z), &full[b]);
             bulk_g2s(S.fix, wfix + c * kWFix, (uint32_t)sizeof(S.fix), &full[b]);
         }
     };
-    int64_t issued = 0;  // blocks staged so far (warp 0's count)
-    if (warp == 0)
-        for (int q = 0; q < STAGES - 1 && c_lo + q < c_hi; ++q, ++issued) stage(c_lo + q, q);
+    int64_t issued = 0;  // blocks staged so far
+    bool stop = false;   // a wait expired (the same value in every thread)
+    for (int q = 0; q < STAGES - 1 && c_lo + q < c_hi; ++q, ++issued) stage(c_lo + q, q);
     // per-row moment sums across blocks: FP32 pairs (sum, compensation)
     // updated by TwoSum (Knuth), exact to about FP32 squared; one FP64
     // conversion per CTA at the end
@@ -318,7 +322,7 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         // closing barrier), then wait for block c.  After an expired wait
         // nothing more is issued or walked; every thread still meets the
         // closing barriers, and the copies in flight are drained below.
-        if (warp == 0 && !abort_flag && c + STAGES - 1 < c_hi) {
+        if (!stop && c + STAGES - 1 < c_hi) {
             stage(c + STAGES - 1, (int)((c + STAGES - 1 - c_lo) % STAGES));
             ++issued;
         }
@@ -396,9 +400,12 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
         two_sum_acc(mhi[1], mlo[1], m1);
         two_sum_acc(mhi[2], mlo[2], m2);
         two_sum_acc(mhi[3], mlo[3], m3);
-        __syncthreads();  // buffer b and the histogram rows are free again
+        // buffer b and the histogram rows are free again; every thread learns
+        // at once whether any wait expired (so all warps stop issuing
+        // together and every issued phase gets all its arrivals)
+        stop = __syncthreads_or(ready ? 0 : 1) != 0 || stop;
     }
-    if (abort_flag) {
+    if (stop) {
         // drain: wait (bounded) for the last phase staged into each buffer,
         // then leave without writing partial results
         if (threadIdx.x == 0)
