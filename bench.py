@@ -657,8 +657,10 @@ def main():
             stage["ipsa"] += v["ms_per_step"]
         else:
             stage["other"] += v["ms_per_step"]
+    # the supplied-weights path computes in FP32 (FP64 finish) whatever --precision says
+    precision = "fp32" if args.config == "weights" else args.precision
     cfg = {"workload": WORKLOADS[args.config], "dist_points_per_step": work.units, "K": work.K,
-           "precision": args.precision, "parallelism": f"replicas x{world} (no collective)",
+           "precision": precision, "parallelism": f"replicas x{world} (no collective)",
            "l2": "flushed before every timed step (256 MB write, outside the step events)"}
     if args.k:
         cfg["k_subset"] = work.K
@@ -669,7 +671,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"bf16x3": "bf16", "tf32x3": "tf32", "tf32": "tf32"}.get(args.precision, "f32"),
+        "vs_baseline": None, "dtype": {"bf16x3": "bf16", "tf32x3": "tf32", "tf32": "tf32"}.get(precision, "f32"),
         "data": "synthetic",
         "config": cfg,
         "roofline": roof,
