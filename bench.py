@@ -14,6 +14,7 @@ Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import statistics
@@ -117,6 +118,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.steps is None:
+        args.steps = 20
     from oracle import oracle as O
     threads = os.cpu_count() or 1
     rows_per_step = threads
@@ -451,7 +454,8 @@ class Weights:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: enough for a timed region of about 1.5 s, 20 to 2000)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "tf32x3", "tf32"])
@@ -500,6 +504,18 @@ def main():
         work.step(stream)
     work.sync()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    if args.steps is None:
+        # default step count: a timed region long enough for several clock
+        # samples (one more untimed step sizes it)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        work.step(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        est = torch.tensor([max(e0.elapsed_time(e1), 1e-3)], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(est, op=dist.ReduceOp.MAX)
+        args.steps = int(min(2000, max(20, math.ceil(1500.0 / float(est.item())))))
 
     clocks = Clocks(local)
     if world > 1:
