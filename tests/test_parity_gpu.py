@@ -200,7 +200,8 @@ def test_propagate_c1_full_fp64_all_rows():
 def test_full_size_bins_bit_exact(name):
     """Per-point bin ids of the full-size grids (the cooperative model-and-
     bins kernel with its FP32 screen) against the oracle's exact FP64 rule;
-    a point may differ only where the two libms' values straddle an edge."""
+    a point may differ only where the two libms' values straddle an edge.
+    The stable sort by bin and the bin offsets are bit-exact."""
     prob = I.config(name)
     vup = vupmod()
     g = vup.Grid(prob.n, prob.lo, prob.hi)
@@ -219,6 +220,13 @@ def test_full_size_bins_bit_exact(name):
     assert not (mism & ~amb).any(), f"{int((mism & ~amb).sum())} bins differ away from edges"
     info = g.info()
     assert info.ymin == y_g.min() and info.ymax == y_g.max()
+    # the model matrix in sorted form (Eq. MUP): the stable sort by bin and
+    # the bin offsets, against numpy's stable argsort of the same bins
+    p_g = g.array("perm").cpu().numpy()
+    off_g = g.array("offsets").cpu().numpy()
+    np.testing.assert_array_equal(p_g, np.argsort(b_g, kind="stable"))
+    np.testing.assert_array_equal(off_g[:-1], np.searchsorted(np.sort(b_g), np.arange(prob.n_bins)))
+    assert off_g[-1] == prob.N
     g.close()
 
 
