@@ -114,6 +114,24 @@ def cpu_baseline(prob, budget_s=12.0, threads=None):
             "sample": f"{n_rows} of {prob.K} distributions x all {prob.N} grid points ({dt:.1f} s)"}
 
 
+def ranks_max(value, world, dist, device):
+    """The largest of the ranks' values (all_reduce MAX); the value itself
+    when one rank runs.  Step times are reduced this way: the job is as slow
+    as its slowest replica."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds_per_step):
+    """Whole-job throughput of `world` replicas that each process
+    `units_per_rank` units per step (weak scaling), paced by the slowest."""
+    return world * units_per_rank / seconds_per_step
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -512,10 +530,8 @@ def main():
         work.step(stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        est = torch.tensor([max(e0.elapsed_time(e1), 1e-3)], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(est, op=dist.ReduceOp.MAX)
-        args.steps = int(min(2000, max(20, math.ceil(1500.0 / float(est.item())))))
+        est = ranks_max(max(e0.elapsed_time(e1), 1e-3), world, dist, "cuda")
+        args.steps = int(min(2000, max(20, math.ceil(1500.0 / est))))
 
     clocks = Clocks(local)
     if world > 1:
@@ -546,13 +562,9 @@ def main():
     vup.vup_profile(False)
     prof = vup.vup_profile_read()
     work.sync()
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_ms = float(t.item())
+    t_ms = ranks_max(sum(a.elapsed_time(b) for a, b in ev), world, dist, "cuda")
     ms_step = t_ms / args.steps
-    value = world * work.units / (ms_step * 1e-3)
+    value = job_rate(work.units, world, ms_step * 1e-3)
 
     # end-to-end through the public API with host buffers (pinned)
     e2e = None
@@ -570,7 +582,8 @@ def main():
             torch.cuda.synchronize()
             tot += time.perf_counter() - t0
         work.sync()
-        e2e = {"value": world * work.units / (tot / n_e2e), "unit": UNIT, "h2d_bytes_per_step": bi,
+        tot = ranks_max(tot, world, dist, "cuda")
+        e2e = {"value": job_rate(work.units, world, tot / n_e2e), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": 1e3 * tot / n_e2e}
 
     # the plain FP32 GPU path on the same workload (the metric's comparator):
@@ -602,12 +615,8 @@ def main():
         prof32 = vup.vup_profile_read()
         work.sync()
         work.prec = prec
-        ms32 = sum(a.elapsed_time(b) for a, b in e32) / n32
-        t = torch.tensor([ms32], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms32 = float(t.item())
-        v32 = world * work.units / (ms32 * 1e-3)
+        ms32 = ranks_max(sum(a.elapsed_time(b) for a, b in e32) / n32, world, dist, "cuda")
+        v32 = job_rate(work.units, world, ms32 * 1e-3)
 
         def contraction_ms(pr, n):
             return sum(v[1] for k, v in pr.items() if k.startswith("moments_") and "finish" not in k) / n
