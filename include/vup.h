@@ -34,9 +34,14 @@
  * - Every call returns a vup_status.  Argument errors are detected on the
  *   host before any work is queued and leave all outputs untouched.
  *   Conditions detected on the device (a density with no grid point in its
- *   support, a bounded device-side wait that expired) are recorded in the
- *   grid's device status word and returned by vup_sync().  No call exits,
- *   aborts or traps.
+ *   support, a bounded device-side wait that expired, and in the debug build
+ *   a failed bounds check) are recorded in the grid's device status word and
+ *   returned by vup_sync().  No call exits, aborts or traps.
+ * - Debug build: libvup_debug.so exports the same ABI, compiled with
+ *   VUP_DEBUG: the histogram walks and the supplied-weights walk check every
+ *   row, column and histogram index they read from a layout or a sorted word
+ *   against the array it addresses, record VUP_ERR_BOUNDS and skip the access
+ *   (no trap).  The Python binding loads it when VUP_DEBUG=1.
  * - Stream-ordered calls enqueue work on `stream` and return without
  *   synchronising.  A grid must not be used from two streams concurrently.
  */
@@ -62,7 +67,10 @@ typedef enum {
     VUP_ERR_STATE = 4,         /* grid has no model outputs yet (call vup_eval_model first) */
     VUP_ERR_EMPTY_SUPPORT = 5, /* some density holds no grid point in its support */
     VUP_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired; results are invalid */
-    VUP_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+    VUP_ERR_UNSUPPORTED = 7,   /* valid request this build does not implement */
+    VUP_ERR_BOUNDS = 8         /* debug build (libvup_debug.so, compiled with VUP_DEBUG) only: a device
+                                  bounds check on an index read from a layout or a sorted word failed;
+                                  the access was skipped and the results are invalid */
 } vup_status;
 
 typedef enum { VUP_GAUSS = 0, VUP_UNIFORM = 1, VUP_TRUNCNORM = 2 } vup_density_kind;

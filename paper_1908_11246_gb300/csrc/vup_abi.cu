@@ -204,6 +204,7 @@ extern "C" const char *vup_status_string(vup_status s) {
     case VUP_ERR_STATE: return "VUP_ERR_STATE: grid has no model outputs (call vup_eval_model)";
     case VUP_ERR_EMPTY_SUPPORT: return "VUP_ERR_EMPTY_SUPPORT: a density holds no grid point";
     case VUP_ERR_TIMEOUT: return "VUP_ERR_TIMEOUT: a bounded device wait expired";
+    case VUP_ERR_BOUNDS: return "VUP_ERR_BOUNDS: a device bounds check of the debug build failed";
     case VUP_ERR_UNSUPPORTED: return "VUP_ERR_UNSUPPORTED: not implemented for these arguments";
     }
     return "unknown vup_status";
@@ -709,6 +710,7 @@ extern "C" vup_status vup_sync(vup_grid g, vup_stream_t stream) {
     case 0: return VUP_OK;
     case VUP_DSTAT_EMPTY: return VUP_ERR_EMPTY_SUPPORT;
     case VUP_DSTAT_TIMEOUT: return VUP_ERR_TIMEOUT;
+    case VUP_DSTAT_BOUNDS: return VUP_ERR_BOUNDS;
     default: return VUP_ERR_INVALID_ARG;
     }
 }

@@ -59,6 +59,7 @@ struct LayoutArgs {
     const float *g0, *g1;  // rest-axis factor tables (g1 only for 3-D)
     int64_t n_last, part_rows;
     int64_t n1;            // size of the second rest axis (3-D)
+    int64_t n0;            // rows of g0 (the first rest axis)
     int P;
 };
 
@@ -274,18 +275,28 @@ __device__ __forceinline__ bool iv_chunk(const ItemCtx &X, int c, int p, int64_t
     };
     // factor of interval i + 4 from interval i's code: 9 low bits below the row
     // field and 12 bits above it (2-D: the rest index; 3-D: a0 low, a1 high)
+    // (debug build: rows outside the factor tables are recorded and read as row 0)
+    auto rest2 = [&](uint32_t a0, uint32_t a1) -> float4 {
+        if (!VUP_DBG_IN(a0, H.n0, X.dstatus)) a0 = 0;
+        if (!VUP_DBG_IN(a1, H.n1, X.dstatus)) a1 = 0;
+        return mul4(row4(g0b, a0), row4(g1b, a1));
+    };
+    auto rest1 = [&](uint32_t a0) -> float4 {
+        if (!VUP_DBG_IN(a0, H.n0, X.dstatus)) a0 = 0;
+        return row4(g0b, a0);
+    };
     auto coded_factor = [&](uint32_t u) -> float4 {
-        if (NF == 2) return mul4(row4(g0b, u & 0x1ffu), row4(g1b, (u >> 18) & 0xfffu));
-        return row4(g0b, (u & 0x1ffu) | ((u >> 9) & (0xfffu << 9)));
+        if (NF == 2) return rest2(u & 0x1ffu, (u >> 18) & 0xfffu);
+        return rest1((u & 0x1ffu) | ((u >> 9) & (0xfffu << 9)));
     };
     auto first_factor = [&](int32_t i) -> float4 {
         if (i < i0 || i >= i1) return zero4;
         const int32_t rest = H.iv_rest[i];
         if (NF == 2) {
             const int32_t a0 = rest / (int32_t)H.n1;
-            return mul4(row4(g0b, (uint32_t)a0), row4(g1b, (uint32_t)(rest - a0 * (int32_t)H.n1)));
+            return rest2((uint32_t)a0, (uint32_t)(rest - a0 * (int32_t)H.n1));
         }
-        return row4(g0b, (uint32_t)rest);
+        return rest1((uint32_t)rest);
     };
     float4 f0 = first_factor(ib), f1 = first_factor(ib + 1), f2 = first_factor(ib + 2), f3 = first_factor(ib + 3);
 
@@ -303,11 +314,14 @@ __device__ __forceinline__ bool iv_chunk(const ItemCtx &X, int c, int p, int64_t
         flush_key(&X, c, p, k, key, v, first ? sh_first : (key == last_key && sh_last), first);
     };
     auto step = [&](uint32_t x, uint32_t y, float4 &f) {
-        const float4 pa = gather(wsl + x), pb = gather(wsl + (y & kOffMask));
+        uint32_t xo = x, yo = y & kOffMask;  // (debug build: rows past the tile are recorded, read as row 0)
+        if (!VUP_DBG_IN(xo >> kRowShift, X.pre_rows, X.dstatus)) xo = 0;
+        if (!VUP_DBG_IN(yo >> kRowShift, X.pre_rows, X.dstatus)) yo = 0;
+        const float4 pa = gather(wsl + xo), pb = gather(wsl + yo);
         fma4(bacc, f, sub4(pb, pa));
         f = coded_factor(y);
         if (y & kBinEnd) {
-            flush(cur_key, bacc);
+            if (VUP_DBG_IN(cur_key, (int64_t)H.P * X.B, X.dstatus)) flush(cur_key, bacc);
             bacc = zero4;
             cur_key = r + 1 < r1 ? H.run_bin[r + 1] : -1;
         }
@@ -419,18 +433,28 @@ __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, i
         return *reinterpret_cast<const float4 *>(base + (uint64_t)row * stride);
     };
     // rest factor from a record's code (2-D: the rest index; 3-D: a0 | a1 << 15)
+    // (debug build: rows outside the factor tables are recorded and read as row 0)
+    auto rest2 = [&](uint32_t a0, uint32_t a1) -> float4 {
+        if (!VUP_DBG_IN(a0, H.n0, X.dstatus)) a0 = 0;
+        if (!VUP_DBG_IN(a1, H.n1, X.dstatus)) a1 = 0;
+        return mul4(row4(g0b, a0), row4(g1b, a1));
+    };
+    auto rest1 = [&](uint32_t a0) -> float4 {
+        if (!VUP_DBG_IN(a0, H.n0, X.dstatus)) a0 = 0;
+        return row4(g0b, a0);
+    };
     auto coded_factor = [&](uint32_t u) -> float4 {
-        if (NF == 2) return mul4(row4(g0b, u & 0x7fffu), row4(g1b, u >> 15));
-        return row4(g0b, u);
+        if (NF == 2) return rest2(u & 0x7fffu, u >> 15);
+        return rest1(u);
     };
     auto first_factor = [&](int32_t t) -> float4 {
         if (t < r0 || t >= r1) return zero4;
         const int32_t rest = H.rec_rest[t];
         if (NF == 2) {
             const int32_t a0 = rest / (int32_t)H.n1;
-            return mul4(row4(g0b, (uint32_t)a0), row4(g1b, (uint32_t)(rest - a0 * (int32_t)H.n1)));
+            return rest2((uint32_t)a0, (uint32_t)(rest - a0 * (int32_t)H.n1));
         }
-        return row4(g0b, (uint32_t)rest);
+        return rest1((uint32_t)rest);
     };
     float4 f0 = first_factor(rb), f1 = first_factor(rb + 1), f2 = first_factor(rb + 2), f3 = first_factor(rb + 3);
 
@@ -440,7 +464,8 @@ __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, i
     // a group's eight sums: whole groups to their direct rows, cut ones to the chunk's partials
     auto flush = [&](int32_t gr) {
         const bool first = gr == first_grp;
-        flush_group(&X, c, p, k, gr, first ? sh_first : (gr == last_grp && sh_last), first, acc[0], acc[1], acc[2],
+        if (VUP_DBG_IN(gr - p * X.GB, X.GB, X.dstatus))  // (debug build: a group outside the part is skipped)
+            flush_group(&X, c, p, k, gr, first ? sh_first : (gr == last_grp && sh_last), first, acc[0], acc[1], acc[2],
                     acc[3], acc[4], acc[5], acc[6], acc[7]);
 #pragma unroll
         for (int j = 0; j < kRecBinsH; ++j) acc[j] = zero4;
@@ -454,8 +479,17 @@ __device__ __forceinline__ bool rec_chunk_walk(const ItemCtx &X, int c, int p, i
     };
     auto step = [&](const uint4 u, const uint4 v, float4 &f) {
         // boundary rows B_0..B_8 (16 bits each); bins with B_j+1 == B_j are absent
-        const uint32_t rw[kRecBinsH + 1] = {u.x & 0xffffu, u.x >> 16, u.y & 0xffffu, u.y >> 16, u.z & 0xffffu,
-                                            u.z >> 16,     u.w & 0xffffu, u.w >> 16, v.x & 0xffffu};
+        uint32_t rw[kRecBinsH + 1] = {u.x & 0xffffu, u.x >> 16, u.y & 0xffffu, u.y >> 16, u.z & 0xffffu,
+                                      u.z >> 16,     u.w & 0xffffu, u.w >> 16, v.x & 0xffffu};
+#ifdef VUP_DEBUG
+        // (debug build: a boundary row past the tile makes the record empty)
+        bool rows_ok = true;
+#pragma unroll
+        for (int j = 0; j <= kRecBinsH; ++j) rows_ok = rows_ok && VUP_DBG_IN(rw[j], X.pre_rows, X.dstatus);
+        if (!rows_ok)
+#pragma unroll
+            for (int j = 0; j <= kRecBinsH; ++j) rw[j] = 0;
+#endif
         const float4 fs = (v.x & kRecNegFlag) ? make_float4(-f.x, -f.y, -f.z, -f.w) : f;
         // each half of the group is skipped when it holds no bin (its
         // boundaries then all equal its first)
@@ -691,6 +725,9 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         uint32_t a0c = 0xffffffffu;
         float4 w0c = zero4;
         auto rest_rows = [&](uint32_t a0, uint32_t a1) -> float4 {
+            // (debug build: rows outside the factor tables are recorded and read as row 0)
+            if (!VUP_DBG_IN(a0, H.n0, X.dstatus)) a0 = 0;
+            if (!VUP_DBG_IN(a1, H.n1, X.dstatus)) a1 = 0;
             if (rs) {
                 if (a0 != a0c) {  // uniform: every lane follows the same run
                     w0c = ld4(w0s + a0 * kKT);
@@ -707,7 +744,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
                 const int32_t a0 = rest / (int32_t)H.n1, a1 = rest - a0 * (int32_t)H.n1;
                 return rest_rows((uint32_t)a0, (uint32_t)a1);
             }
-            return ld4(g0k + rest * K_pad);
+            return ld4(g0k + (VUP_DBG_IN(rest, H.n0, X.dstatus) ? rest : 0) * K_pad);
         };
         // fc = factor of the current run, f1..f3 those of the next three runs
         // (MODE 4: shared-memory factors, no look-ahead: fc only)
@@ -722,7 +759,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         auto coded_factor = [&](uint32_t u) -> float4 {
             if (NF == 2) return rest_rows(u & 0x1ffu, (u >> 18) & 0xfffu);
             const uint32_t idx = (u & 0x1ffu) | (((u >> 18) & 0xfffu) << 9);
-            return ld4(g0k + (int64_t)idx * K_pad);
+            return ld4(g0k + (int64_t)(VUP_DBG_IN(idx, H.n0, X.dstatus) ? idx : 0u) * K_pad);
         };
 
         // every point's factor is multiplied by its run's rest-axis factor fc as it
@@ -735,7 +772,7 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
 
         auto run_end = [&](uint32_t u) {
             if (u & kBinEnd) {
-                flush(cur_key, bacc);
+                if (VUP_DBG_IN(cur_key, (int64_t)H.P * X.B, X.dstatus)) flush(cur_key, bacc);
                 bacc = zero4;
                 cur_key = r + 1 < r1 ? H.run_bin[r + 1] : -1;
             }
@@ -757,7 +794,18 @@ __device__ __forceinline__ void hist_item(const HistArgs *Ap, int p, int cg, int
         };
         // words without flags carry nothing but the row byte offset (run codes sit
         // on run-end words only), so the common path needs no masking
-        auto group = [&](const uint4 v) {
+#ifdef VUP_DEBUG
+        // (debug build: a row offset past the tile is recorded and read as the zero row 0)
+        auto dbg_word = [&](uint32_t w) -> uint32_t {
+            if ((w & kFlags) == 0)
+                return VUP_DBG_IN(w >> kRowShift, nrows + 1, X.dstatus) && (w & ~kOffMask) == 0 ? w : 0u;
+            return VUP_DBG_IN((w & kOffMask) >> kRowShift, nrows + 1, X.dstatus) ? w : (w & ~kOffMask);
+        };
+#endif
+        auto group = [&](uint4 v) {
+#ifdef VUP_DEBUG
+            v = make_uint4(dbg_word(v.x), dbg_word(v.y), dbg_word(v.z), dbg_word(v.w));
+#endif
             if (((v.x | v.y | v.z | v.w) & kFlags) == 0) {
                 const float4 a0 = gather(wsl + v.x), a1 = gather(wsl + v.y), a2 = gather(wsl + v.z),
                              a3 = gather(wsl + v.w);
@@ -1191,10 +1239,12 @@ static HistArgs hist_args_for(vup_grid g, int64_t K, float *hist, int64_t &rows,
             La.g0 = tab(0);
             La.g1 = tab(1);
             La.n1 = g->n[1];
+            La.n0 = g->n[0];
         } else {
             La.g0 = tab(HL.last_axis == 1 ? 0 : 1);
             La.g1 = nullptr;
             La.n1 = 1;
+            La.n0 = g->n[HL.last_axis == 1 ? 0 : 1];
         }
         La.n_last = HL.n_last;
         La.part_rows = HL.part_rows;

@@ -56,7 +56,23 @@ inline cudaError_t vup_dev_malloc(T **p, size_t bytes) {
 }
 
 // Device status word codes (grid->dstatus[0]); the first non-zero code wins.
-enum { VUP_DSTAT_OK = 0, VUP_DSTAT_EMPTY = 5, VUP_DSTAT_TIMEOUT = 6 };
+enum { VUP_DSTAT_OK = 0, VUP_DSTAT_EMPTY = 5, VUP_DSTAT_TIMEOUT = 6, VUP_DSTAT_BOUNDS = 7 };
+
+// Device bounds checks of the debug build (-DVUP_DEBUG, libvup_debug.so):
+// VUP_DBG_IN(i, n, dstatus) is true when 0 <= i < n; otherwise it records
+// VUP_DSTAT_BOUNDS (returned by vup_sync as VUP_ERR_BOUNDS) and is false, and
+// the caller skips or clamps the access instead of trapping.  In the release
+// build it is the constant true and its arguments are not evaluated.
+#ifdef VUP_DEBUG
+__device__ __forceinline__ bool vup_dbg_in(uint64_t i, uint64_t n, int *dstatus) {
+    if (i < n) return true;
+    atomicCAS(dstatus, 0, VUP_DSTAT_BOUNDS);
+    return false;
+}
+#define VUP_DBG_IN(i, n, dstatus) vup_dbg_in((uint64_t)(i), (uint64_t)(n), (dstatus))
+#else
+#define VUP_DBG_IN(i, n, dstatus) true
+#endif
 
 // Per-(k, axis) density constants written by the density-prep kernel.
 //   Gaussian / truncated normal, index space: the midpoint index of mu is

@@ -352,8 +352,17 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
             const uint4 cb = *reinterpret_cast<const uint4 *>(&S.pt[t + 4]);
             const uint4 ba = *reinterpret_cast<const uint4 *>(&S.pt[kWBlock + t]);
             const uint4 bb = *reinterpret_cast<const uint4 *>(&S.pt[kWBlock + t + 4]);
-            const uint32_t cw[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
-            const uint32_t bw[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+            uint32_t cw[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+            uint32_t bw[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+#ifdef VUP_DEBUG
+            // (debug build: a column past the tile reads the zero column; a
+            // histogram entry past the row lands in the spare column)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (!VUP_DBG_IN(cw[u] >> 2, kWBlock + 1, dstatus) || (cw[u] & 3u)) cw[u] = kWFillerCol;
+                if ((bw[u] & 1u) && !VUP_DBG_IN((bw[u] - 1u) >> 2, ld, dstatus)) bw[u] = (uint32_t)B * 4u + 1u;
+            }
+#endif
             float wv[8], hv[8];
             uint32_t ha[8];
 #pragma unroll
@@ -390,9 +399,11 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
             // crossing runs: this slice's part, from the warp's own columns,
             // added to the bin atomically (other slices add their parts)
             float *hrow_w = H + lane * ld;
-            if (head & kWCross) atomicAdd(hrow_w + (head & 0x7fffu), hrow_w[B + 1 + warp]);
+            if ((head & kWCross) && VUP_DBG_IN(head & 0x7fffu, B, dstatus))
+                atomicAdd(hrow_w + (head & 0x7fffu), hrow_w[B + 1 + warp]);
             if (tail & kWCross) {
-                atomicAdd(hrow_w + (tail & 0x7fffu), hrow_w[B + 1 + kWWarps + warp]);
+                if (VUP_DBG_IN(tail & 0x7fffu, B, dstatus))
+                    atomicAdd(hrow_w + (tail & 0x7fffu), hrow_w[B + 1 + kWWarps + warp]);
                 hrow_w[B + 1 + kWWarps + warp] = 0.f;
             }
         }

@@ -14,10 +14,12 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "libvup.so")
+# VUP_DEBUG=1 selects the debug build (device bounds checks that record
+# VUP_ERR_BOUNDS instead of trapping; built by build(debug=True))
+LIB_PATH = os.path.join(_PKG, "_lib", "libvup_debug.so" if os.environ.get("VUP_DEBUG") == "1" else "libvup.so")
 
 VUP_OK, VUP_ERR_INVALID_ARG, VUP_ERR_CUDA, VUP_ERR_OOM, VUP_ERR_STATE = 0, 1, 2, 3, 4
-VUP_ERR_EMPTY_SUPPORT, VUP_ERR_TIMEOUT, VUP_ERR_UNSUPPORTED = 5, 6, 7
+VUP_ERR_EMPTY_SUPPORT, VUP_ERR_TIMEOUT, VUP_ERR_UNSUPPORTED, VUP_ERR_BOUNDS = 5, 6, 7, 8
 VUP_GAUSS, VUP_UNIFORM, VUP_TRUNCNORM = 0, 1, 2
 VUP_FP64, VUP_FP32, VUP_BF16X3, VUP_TF32, VUP_TF32X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": VUP_FP64, "fp32": VUP_FP32, "bf16x3": VUP_BF16X3, "tf32": VUP_TF32, "tf32x3": VUP_TF32X3}

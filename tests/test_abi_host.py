@@ -42,8 +42,9 @@ def test_binding_names_match_header():
 
 
 def test_status_strings(L):
-    for code in range(8):
+    for code in range(9):
         assert vup.vup_status_string(code).startswith("VUP_")
+    assert vup.vup_status_string(vup.VUP_ERR_BOUNDS).startswith("VUP_ERR_BOUNDS")
     assert "sm_103a" in vup.vup_version()
 
 
