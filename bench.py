@@ -236,7 +236,7 @@ def roofline_for(name, ms, n_work, units, pk, workload, hist_units=None):
                         f"peak = burst {'TF32 (bf16 x 1.1/2.25)' if tf32 else 'bf16'} (the kernel runs well "
                         f"under a second), sustained beside it, of {pk['source']}"}
     if name.startswith("moments_fp32") or name.startswith("ipsa_fp32"):
-        fl = 8.0 if name.startswith("moments") else 24.0
+        fl = 8.0  # each FP32 launch is one weighted contraction (the IPSA takes three per orientation)
         peak = pk["ffma_tflops"]
         a = fl * units / per / 1e12
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
@@ -330,9 +330,12 @@ class SingleGrid:
         if self.bayes:
             v.vup_posterior_means(self.g.h, self.ds, self.hist, self.post, stream)
             return
-        v.vup_propagate(self.g.h, self.ds, self.prec, self.raw, self.cen, self.hist, stream)
         if self.ipsa:
-            v.vup_ipsa_sensitivity(self.g.h, self.ds, self.prec, self.dmu, self.dsg, self.grad, stream)
+            # forward pass and sensitivities in one call (one density preparation)
+            v.vup_propagate_ipsa(self.g.h, self.ds, self.prec, self.raw, self.cen, self.hist, self.dmu, self.dsg,
+                                 self.grad, stream)
+        else:
+            v.vup_propagate(self.g.h, self.ds, self.prec, self.raw, self.cen, self.hist, stream)
         if self.sa:
             v.vup_model_at(self.g.h, self.centres, self.yref, stream)
             v.vup_deviation_moments(self.g.h, self.raw, self.yref, self.dev_m, stream)
@@ -619,7 +622,8 @@ def main():
         v32 = job_rate(work.units, world, ms32 * 1e-3)
 
         def contraction_ms(pr, n):
-            return sum(v[1] for k, v in pr.items() if k.startswith("moments_") and "finish" not in k) / n
+            return sum(v[1] for k, v in pr.items() if k.startswith(("moments_", "ipsa_")) and
+                       k.endswith(("_tc", "_simt"))) / n
         c_main, c_32 = contraction_ms(prof, args.steps), contraction_ms(prof32, n32)
         fp32_arm = {"value": v32, "unit": UNIT, "ms_per_step": ms32, "steps": n32,
                     "factor_step": value / v32, "contraction_ms": {args.precision: c_main, "fp32": c_32},

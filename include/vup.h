@@ -238,6 +238,21 @@ vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, vup_precisio
                                 vup_stream_t stream);
 
 /*
+ * Forward pass and IPSA sensitivities in one call: the outputs of
+ * vup_propagate (moments_raw, moments_central, hist; each may be NULL) and of
+ * vup_ipsa_sensitivity (grad_moments, dmu, dsigma as there) for the same
+ * densities.  On a 2-D grid with VUP_FP32 or VUP_BF16X3 the densities are
+ * prepared once and the moments are read off the sensitivity contraction of
+ * the forward orientation (its first output plane is the moment contraction
+ * itself), so no separate moment contraction runs; the results equal the two
+ * separate calls'.  Other grids and precisions run the two calls in turn.
+ * Errors as the two calls.
+ */
+vup_status vup_propagate_ipsa(vup_grid g, const vup_densities *d, vup_precision precision,
+                              double *moments_raw, double *moments_central, float *hist,
+                              const double *grad_moments, float *dmu, float *dsigma, vup_stream_t stream);
+
+/*
  * Batched uneven propagation: n_inst independent instances (grid g[i] with
  * densities d[i]), the many-small-problems form of the Sec. 4 pipeline.  Every
  * stage runs as one launch over the work items of all instances, longest

@@ -540,25 +540,24 @@ vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa, bool tf32)
     return VUP_OK;
 }
 
-extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_precision precision,
-                                    double *moments_raw, double *moments_central, float *hist,
-                                    vup_stream_t stream) {
-    if (!g) return VUP_ERR_INVALID_ARG;
-    vup_status st = vup_check_dens(g, d);
-    if (st != VUP_OK) return st;
-    if (precision < VUP_FP64 || precision > VUP_TF32X3) return VUP_ERR_INVALID_ARG;
-    if (!g->have_model) return VUP_ERR_STATE;
-    cudaStream_t s = (cudaStream_t)stream;
+// Sensitivity outputs of a fused forward + IPSA call (vup_propagate_ipsa).
+struct IpsaOut {
+    const double *grad;
+    float *dmu, *dsg;
+};
+
+// The forward pass of a 2-D / 3-D grid; with `ip` (2-D, FP32 or BF16x3) also
+// the IPSA sensitivities, from one density preparation, the moments read off
+// the first output plane of the forward orientation's sensitivity contraction.
+static vup_status propagate_nd(vup_grid g, const vup_densities *d, vup_precision precision, double *moments_raw,
+                               double *moments_central, float *hist, cudaStream_t s, const IpsaOut *ip) {
+    vup_status st;
     const int64_t K = d->K;
-    if (g->ndim == 1) {
-        if (precision != VUP_FP64 && precision != VUP_FP32) return VUP_ERR_UNSUPPORTED;
-        return vup_propagate_1d(g, d, moments_raw, moments_central, hist, s);
-    }
-    if (precision == VUP_FP64) return VUP_ERR_UNSUPPORTED;
     const bool bf16 = precision == VUP_BF16X3;
     const bool tf32 = precision == VUP_TF32 || precision == VUP_TF32X3;
     const bool want_m = moments_raw || moments_central;
-    if ((st = vup_reserve_k(g, K, bf16, false, tf32)) != VUP_OK) return st;
+    const bool fuse = ip != nullptr;
+    if ((st = vup_reserve_k(g, K, bf16, fuse, tf32)) != VUP_OK) return st;
     // the histogram layout (when not built for this model yet) on the second
     // stream, beside the density preparation and the contraction
     bool forked = false;
@@ -587,10 +586,18 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
         }
     } join{forked, s, g->ev_join}, join_fin{false, s, g->ev_mfin};
     const int to = vup_tc_orient(g);
-    if (want_m && (st = vup_build_tables(g, (bf16 || tf32) ? to : kOrientLast, tf32 ? 2 : (bf16 ? 1 : 0), s)) !=
-                      VUP_OK)
-        return st;
-    if ((st = vup_density_prep(g, d, ((bf16 || tf32) && want_m) ? (1 << to) : 0, s, tf32)) != VUP_OK) return st;
+    if (fuse) {
+        // both orientations' tables and split factors, and the statistics the
+        // sensitivities need
+        for (int o = 0; o < 2; ++o)
+            if ((st = vup_build_tables(g, o, bf16 ? 1 : 0, s)) != VUP_OK) return st;
+        if ((st = vup_density_prep(g, d, bf16 ? 3 : 0, s, false, true)) != VUP_OK) return st;
+    } else {
+        if (want_m && (st = vup_build_tables(g, (bf16 || tf32) ? to : kOrientLast, tf32 ? 2 : (bf16 ? 1 : 0), s)) !=
+                          VUP_OK)
+            return st;
+        if ((st = vup_density_prep(g, d, ((bf16 || tf32) && want_m) ? (1 << to) : 0, s, tf32)) != VUP_OK) return st;
+    }
     if (forked) {
         // the layout's launches are enqueued after the density preparation's, so
         // that the main stream's work is not held behind their host-side cost
@@ -617,9 +624,28 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
         prefix_ready = vup_hist_prefix(g, K, g->side2);
         VUP_CHECK_CUDA(cudaEventRecord(g->ev_pre, g->side2));
     }
-    if (want_m) {
+    // fused: the sensitivity partials of both orientations ([3][tiles][K_pad][4]
+    // each, orientation 1 after orientation 0), the forward orientation first
+    const int fo = bf16 ? to : 0;
+    float *ipart[2] = {nullptr, nullptr};
+    int64_t inct[2] = {0, 0};
+    if (fuse) {
+        const int64_t K_pad = ceil_div64(K, 128) * 128;
+        for (int o = 0; o < 2; ++o)
+            inct[o] = bf16 ? vup_tc_col_tiles(g->orient[o]) : vup_simt_col_tiles(g->orient[o]);
+        ipart[0] = (float *)g->ipsa_part.p;
+        ipart[1] = ipart[0] + (size_t)3 * inct[0] * K_pad * 4;
+    }
+    if (want_m || fuse) {
         int64_t nct;
-        if (bf16 || tf32) {
+        const float *mpart = nullptr;
+        if (fuse) {
+            // w, w u, w u^2 of the forward orientation: plane 0 is the moment contraction
+            st = bf16 ? vup_moments_tc(g, K, fo, 3, ipart[fo], s) : vup_moments_simt(g, K, fo, 3, ipart[fo], s);
+            if (st != VUP_OK) return st;
+            nct = inct[fo];
+            mpart = ipart[fo];
+        } else if (bf16 || tf32) {
             if ((st = vup_moments_tc(g, K, to, 1, (float *)g->partials.p, s, tf32 ? 1 : 0,
                                      precision == VUP_TF32 ? 1 : 3)) != VUP_OK)
                 return st;
@@ -628,15 +654,16 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
             if ((st = vup_moments_simt(g, K, 0, 1, (float *)g->partials.p, s)) != VUP_OK) return st;
             nct = vup_simt_col_tiles(g->orient[0]);
         }
-        if (prefix_ready) {
+        if (!want_m) {
+        } else if (prefix_ready) {
             // the FP64 finish on the third stream: the histogram does not need it
             VUP_CHECK_CUDA(cudaEventRecord(g->ev_mom, s));
             VUP_CHECK_CUDA(cudaStreamWaitEvent(g->side2, g->ev_mom, 0));
             join_fin.on = true;
-            st = vup_moments_finish(g, K, (int)nct, moments_raw, moments_central, g->side2);
+            st = vup_moments_finish(g, K, (int)nct, moments_raw, moments_central, g->side2, mpart);
             VUP_CHECK_CUDA(cudaEventRecord(g->ev_mfin, g->side2));
             if (st != VUP_OK) return st;
-        } else if ((st = vup_moments_finish(g, K, (int)nct, moments_raw, moments_central, s)) != VUP_OK) {
+        } else if ((st = vup_moments_finish(g, K, (int)nct, moments_raw, moments_central, s, mpart)) != VUP_OK) {
             return st;
         }
     }
@@ -650,7 +677,32 @@ extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_prec
             return st;
         join.on = false;
     }
+    if (fuse) {
+        // the other orientation's sensitivity contraction, then the combine
+        const int oo = 1 - fo;
+        st = bf16 ? vup_moments_tc(g, K, oo, 3, ipart[oo], s) : vup_moments_simt(g, K, oo, 3, ipart[oo], s);
+        if (st != VUP_OK) return st;
+        if ((st = vup_ipsa_finish(g, K, (int)inct[0], (int)inct[1], ip->grad, ip->dmu, ip->dsg, s)) != VUP_OK)
+            return st;
+    }
     return VUP_OK;
+}
+
+extern "C" vup_status vup_propagate(vup_grid g, const vup_densities *d, vup_precision precision,
+                                    double *moments_raw, double *moments_central, float *hist,
+                                    vup_stream_t stream) {
+    if (!g) return VUP_ERR_INVALID_ARG;
+    vup_status st = vup_check_dens(g, d);
+    if (st != VUP_OK) return st;
+    if (precision < VUP_FP64 || precision > VUP_TF32X3) return VUP_ERR_INVALID_ARG;
+    if (!g->have_model) return VUP_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->ndim == 1) {
+        if (precision != VUP_FP64 && precision != VUP_FP32) return VUP_ERR_UNSUPPORTED;
+        return vup_propagate_1d(g, d, moments_raw, moments_central, hist, s);
+    }
+    if (precision == VUP_FP64) return VUP_ERR_UNSUPPORTED;
+    return propagate_nd(g, d, precision, moments_raw, moments_central, hist, s, nullptr);
 }
 
 extern "C" vup_status vup_propagate_weights(vup_grid g, int64_t K, const float *W, double *moments_raw,
@@ -698,6 +750,23 @@ extern "C" vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, v
         if (st != VUP_OK) return st;
     }
     return vup_ipsa_finish(g, K, (int)n0, (int)n1, grad_moments, dmu, dsigma, s);
+}
+
+extern "C" vup_status vup_propagate_ipsa(vup_grid g, const vup_densities *d, vup_precision precision,
+                                         double *moments_raw, double *moments_central, float *hist,
+                                         const double *grad_moments, float *dmu, float *dsigma,
+                                         vup_stream_t stream) {
+    if (!g || !dmu || !dsigma) return VUP_ERR_INVALID_ARG;
+    vup_status st = vup_check_dens(g, d);
+    if (st != VUP_OK) return st;
+    if (precision < VUP_FP64 || precision > VUP_TF32X3) return VUP_ERR_INVALID_ARG;
+    if (!g->have_model) return VUP_ERR_STATE;
+    if (g->ndim == 2 && (precision == VUP_FP32 || precision == VUP_BF16X3)) {
+        const IpsaOut ip{grad_moments, dmu, dsigma};
+        return propagate_nd(g, d, precision, moments_raw, moments_central, hist, (cudaStream_t)stream, &ip);
+    }
+    if ((st = vup_propagate(g, d, precision, moments_raw, moments_central, hist, stream)) != VUP_OK) return st;
+    return vup_ipsa_sensitivity(g, d, precision, grad_moments, dmu, dsigma, stream);
 }
 
 extern "C" vup_status vup_sync(vup_grid g, vup_stream_t stream) {

@@ -332,8 +332,10 @@ vup_status vup_moments_simt(vup_grid g, int64_t K, int orient, int n_out, float 
 // terms = 3 split products or 1 (hi only).
 vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s,
                           int kind = 0, int terms = 3);
+// FP64 finish of the contraction partials [n_col_tiles][K_pad][4] at `part`
+// (NULL: the grid's moment partials)
 vup_status vup_moments_finish(vup_grid g, int64_t K, int n_col_tiles, double *raw,
-                              double *central, cudaStream_t s);
+                              double *central, cudaStream_t s, const float *part = nullptr);
 // Segmented histogram of the K densities; `ftab` replaces the grid's factor
 // tables when not null (same layout), e.g. tables weighted by a coordinate.
 // points_only: walk the point stream even where the interval stream was

@@ -382,11 +382,11 @@ vup_status vup_moments_simt(vup_grid g, int64_t K, int orient, int n_out, float 
 }
 
 vup_status vup_moments_finish(vup_grid g, int64_t K, int n_col_tiles, double *raw, double *central,
-                              cudaStream_t s) {
+                              cudaStream_t s, const float *part) {
     const int64_t K_pad = ceil_div64(K, 128) * 128;
     VUP_PROF("moments_finish_fp64", s, 1);
     VUP_CHECK_CUDA(launch_pdl(k_moments_finish, dim3((unsigned)ceil_div64(K, 128)), dim3(128), 0, s,
-                              (const float *)g->partials.p, (int64_t)n_col_tiles, K, K_pad, g->J,
+                              part ? part : (const float *)g->partials.p, (int64_t)n_col_tiles, K, K_pad, g->J,
                               (const DensStats *)g->dstats.p, g->ndim, (const double *)g->ydev_scale, raw, central));
     return VUP_OK;
 }

@@ -540,10 +540,6 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
     const int64_t N = g->N;
     const int B = g->B;
     vup_status st;
-    if ((st = devbuf_reserve(g_wz32, sizeof(float) * (N + 4))) != VUP_OK) return st;
-    k_z32<<<(unsigned)std::min<int64_t>(ceil_div64(N, 256), 4096), 256, 0, s>>>(g->y, N, g->ydev_scale,
-                                                                                (float *)g_wz32.p);
-    VUP_CHECK_LAUNCH();
     const bool aligned = N % 4 == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0;
     if (B <= 1024 && aligned && ceil_div64(K, kWRows) <= 65535) {
         const int64_t n_blk = ceil_div64(N, kWBlock);
@@ -610,6 +606,11 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
         VUP_CHECK_LAUNCH();
         return VUP_OK;
     }
+    // the other forms read the FP32 powers z = y / s_abs in grid order
+    if ((st = devbuf_reserve(g_wz32, sizeof(float) * (N + 4))) != VUP_OK) return st;
+    k_z32<<<(unsigned)std::min<int64_t>(ceil_div64(N, 256), 4096), 256, 0, s>>>(g->y, N, g->ydev_scale,
+                                                                                (float *)g_wz32.p);
+    VUP_CHECK_LAUNCH();
     if (B <= 1024) {
         const int64_t rows = ceil_div64(K, kRowsT);
         int64_t n_split = std::max<int64_t>(1, (int64_t)vup_num_sms() * 4 / std::max<int64_t>(rows, 1));

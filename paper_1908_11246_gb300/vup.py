@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": VUP_FP64, "fp32": VUP_FP32, "bf16x3": VUP_BF16X3, "tf32": 
 # exported symbols declared in include/vup.h
 ABI_SYMBOLS = [
     "vup_grid_create", "vup_grid_destroy", "vup_eval_model", "vup_set_outputs", "vup_propagate",
-    "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_batched", "vup_batched_report", "vup_sync", "vup_selftest_wait", "vup_model_at",
+    "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_ipsa", "vup_propagate_batched", "vup_batched_report", "vup_sync", "vup_selftest_wait", "vup_model_at",
     "vup_deviation_moments", "vup_ipsa_matrix", "vup_sa_fields", "vup_posterior_means",
     "vup_grid_info", "vup_set_hist_stream", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
     "vup_profile_read", "vup_profile_timeline", "vup_last_error_detail", "vup_debug_fail_alloc",
@@ -73,6 +73,7 @@ def lib():
         l.vup_propagate_weights.argtypes = [vp, i64, vp, vp, vp, vp]
         l.vup_propagate_weights_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
         l.vup_ipsa_sensitivity.argtypes = [vp, C.POINTER(vup_densities), C.c_int, vp, vp, vp, vp]
+        l.vup_propagate_ipsa.argtypes = [vp, C.POINTER(vup_densities), C.c_int, vp, vp, vp, vp, vp, vp, vp]
         l.vup_propagate_batched.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vup_densities), C.c_int,
                                             C.POINTER(vp), C.POINTER(vp), vp]
         l.vup_batched_report.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -200,6 +201,14 @@ def vup_propagate_weights_noalloc(h, W, moments_raw=None, hist=None, stream=None
 def vup_ipsa_sensitivity(h, dens, precision, dmu, dsigma, grad_moments=None, stream=None):
     _check(lib().vup_ipsa_sensitivity(h, C.byref(dens), int(precision), _ptr(grad_moments), _ptr(dmu),
                                       _ptr(dsigma), _stream(stream)), "vup_ipsa_sensitivity")
+
+
+def vup_propagate_ipsa(h, dens, precision, moments_raw, moments_central, hist, dmu, dsigma, grad_moments=None,
+                       stream=None):
+    """vup_propagate and vup_ipsa_sensitivity of the same densities in one call."""
+    _check(lib().vup_propagate_ipsa(h, C.byref(dens), int(precision), _ptr(moments_raw), _ptr(moments_central),
+                                    _ptr(hist), _ptr(grad_moments), _ptr(dmu), _ptr(dsigma), _stream(stream)),
+           "vup_propagate_ipsa")
 
 
 class BatchedArgs:

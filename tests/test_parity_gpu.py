@@ -404,6 +404,55 @@ def test_ipsa_c4_full_size_256_rows(precision):
     g.close()
 
 
+def _fused_vs_separate(prob, precision, grad_seed=None):
+    """vup_propagate_ipsa against vup_propagate + vup_ipsa_sensitivity on the
+    same grid and densities: moments, histograms and sensitivities equal."""
+    vup = vupmod()
+    import torch
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.eval_model(prob.model_id, prob.theta, prob.n_bins, prob.n_moments)
+    dd = vup.densities_to_device(prob.dens)  # kept alive: the struct holds its pointers
+    ds = vup.make_densities(dd)
+    K, J, B, nd = prob.K, prob.n_moments, prob.n_bins, prob.ndim
+    pr = vup.PRECISIONS[precision]
+    grad = None
+    if grad_seed is not None:
+        grad = torch.as_tensor(np.random.default_rng(grad_seed).standard_normal((K, J)), device="cuda")
+    shape = (K, nd) if grad is not None else (K, nd, J)
+
+    def outs():
+        return (torch.full((K, J), np.nan, dtype=torch.float64, device="cuda"),
+                torch.full((K, J), np.nan, dtype=torch.float64, device="cuda"),
+                torch.full((K, B), np.nan, dtype=torch.float32, device="cuda"),
+                torch.full(shape, np.nan, dtype=torch.float32, device="cuda"),
+                torch.full(shape, np.nan, dtype=torch.float32, device="cuda"))
+    a, b = outs(), outs()
+    vup.vup_propagate(g.h, ds, pr, a[0], a[1], a[2])
+    vup.vup_ipsa_sensitivity(g.h, ds, pr, a[3], a[4], grad)
+    g.sync()
+    vup.vup_propagate_ipsa(g.h, ds, pr, b[0], b[1], b[2], b[3], b[4], grad)
+    g.sync()
+    for name, x, y in zip(("raw", "central", "hist", "dmu", "dsigma"), a, b):
+        x, y = x.cpu().numpy(), y.cpu().numpy()
+        assert np.isfinite(y).all(), name
+        np.testing.assert_allclose(y, x, rtol=1e-12, atol=1e-300, err_msg=name)
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("name", ["c2", "c4"])
+@pytest.mark.parametrize("vjp", [False, True])
+def test_propagate_ipsa_matches_separate_calls(name, precision, vjp):
+    _fused_vs_separate(I.config(name, "small"), precision, grad_seed=7 if vjp else None)
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+def test_propagate_ipsa_c4_full_size(precision):
+    """The fused call bench.py times for c4 (2048^2, K = 65536) against the two
+    separate calls, whose full-size parity with the oracle is tested above."""
+    _fused_vs_separate(I.config("c4"), precision, grad_seed=11)
+
+
 def test_ipsa_1d_fp64_matches_oracle():
     vup = vupmod()
     prob = I.config("c1", "small")
