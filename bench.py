@@ -280,6 +280,19 @@ WORKLOADS = {
 }
 
 
+def packed(torch, specs, device="cuda"):
+    """Tensors of the given (shape, dtype) as views of one contiguous byte
+    buffer (each view 256-byte aligned); returns (buffer, views)."""
+    offs, o = [], 0
+    for shape, dt in specs:
+        n = int(np.prod(shape)) * torch.empty((), dtype=dt).element_size()
+        offs.append((o, n))
+        o += -(-n // 256) * 256
+    buf = torch.empty(max(o, 1), dtype=torch.uint8, device=device)
+    views = [buf[a:a + n].view(dt).view(shape) for (a, n), (shape, dt) in zip(offs, specs)]
+    return buf, views
+
+
 class SingleGrid:
     """c2 / c3 / c4: one grid; a step evaluates the model (values, range, bins,
     sort, power tables) and propagates all K densities (plus the adjoint for c4)."""
@@ -296,31 +309,38 @@ class SingleGrid:
         self.hist_passes = 1 + prob.ndim if self.bayes else 1  # posterior means: H, then one pass per axis
         self.prec = prec
         self.g = vup.Grid(prob.n, prob.lo, prob.hi)
-        self.dev = vup.densities_to_device(prob.dens)
+        K, J, B, nd_ = prob.K, prob.n_moments, prob.n_bins, prob.ndim
+        f64, f32, i32 = torch.float64, torch.float32, torch.int32
+        # the densities and every per-step output as views of one input and one
+        # output buffer (one host copy each way end to end)
+        dd = vup.densities_to_device(prob.dens)
+        names = ("kind", "mu", "sigma", "lo", "hi")
+        self.in_buf, views = packed(torch, [(tuple(dd[n].shape), dd[n].dtype) for n in names])
+        self.dev = dict(zip(names, views))
+        for n in names:
+            self.dev[n].copy_(dd[n])
+        del dd
         self.ds = vup.make_densities(self.dev)
-        K, J, B = prob.K, prob.n_moments, prob.n_bins
-        dv = "cuda"
-        self.raw = torch.empty((K, J), dtype=torch.float64, device=dv)
-        self.cen = torch.empty((K, J), dtype=torch.float64, device=dv)
-        self.hist = torch.empty((K, B), dtype=torch.float32, device=dv)
+        self.nd = 1000
+        specs = {"hist": ((K, B), f32)} if self.bayes else \
+            {"raw": ((K, J), f64), "cen": ((K, J), f64), "hist": ((K, B), f32)}
         if self.ipsa:
-            self.grad = torch.ones((K, J), dtype=torch.float64, device=dv)
-            self.dmu = torch.empty((K, 2), dtype=torch.float32, device=dv)
-            self.dsg = torch.empty((K, 2), dtype=torch.float32, device=dv)
+            specs.update(dmu=((K, 2), f32), dsg=((K, 2), f32))
         if self.bayes:
-            self.post = torch.empty((K, B, prob.ndim), dtype=torch.float32, device=dv)
+            specs.update(post=((K, B, nd_), f32))
+        if self.sa:
+            specs.update(yref=((K,), f64), dev_m=((K, J), f64), mat=((K, self.nd), f32), am=((K,), i32),
+                         ci=((K, 2), i32), glob=((self.nd,), f64))
+        self.out_buf, outs = packed(torch, list(specs.values()))
+        for name, v in zip(specs, outs):
+            setattr(self, name, v)
+        if self.ipsa:
+            self.grad = torch.ones((K, J), dtype=f64, device="cuda")
         if self.sa:
             self.g.eval_model(prob.model_id, prob.theta, B, J)
             info = self.g.info()
             self.span = info.ymax - info.ymin
-            self.nd = 1000
             self.centres = self.dev["mu"].contiguous()
-            self.yref = torch.empty(K, dtype=torch.float64, device=dv)
-            self.dev_m = torch.empty((K, J), dtype=torch.float64, device=dv)
-            self.mat = torch.empty((K, self.nd), dtype=torch.float32, device=dv)
-            self.am = torch.empty(K, dtype=torch.int32, device=dv)
-            self.ci = torch.empty((K, 2), dtype=torch.int32, device=dv)
-            self.glob = torch.empty(self.nd, dtype=torch.float64, device=dv)
         self.units = K * prob.N
         self.K = K
 
@@ -349,23 +369,17 @@ class SingleGrid:
         return [(self.g, self.K)]
 
     def e2e(self):
-        """Host buffers: inputs copied in, every output copied back, each step."""
+        """Host buffers: the densities copied in and every output of the step
+        copied back, each step (one copy each way: the packed buffers)."""
         torch = self.torch
-        host = {k: v.cpu().pin_memory() for k, v in self.dev.items()}
-        outs = ([self.hist] if self.bayes else [self.raw, self.cen, self.hist]) + \
-            ([self.dmu, self.dsg] if self.ipsa else []) + \
-            ([self.yref, self.dev_m, self.mat, self.am, self.ci, self.glob] if self.sa else []) + \
-            ([self.post] if self.bayes else [])
-        outs_h = [torch.empty_like(x, device="cpu").pin_memory() for x in outs]
-        bi = sum(v.numel() * v.element_size() for v in host.values())
-        bo = sum(x.numel() * x.element_size() for x in outs_h)
+        in_h = self.in_buf.cpu().pin_memory()
+        out_h = torch.empty_like(self.out_buf, device="cpu").pin_memory()
+        bi, bo = in_h.numel(), out_h.numel()
 
         def run(stream):
-            for k, v in host.items():
-                self.dev[k].copy_(v, non_blocking=True)
+            self.in_buf.copy_(in_h, non_blocking=True)
             self.step(stream)
-            for h, d in zip(outs_h, outs):
-                h.copy_(d, non_blocking=True)
+            out_h.copy_(self.out_buf, non_blocking=True)
         return run, bi, bo
 
 
