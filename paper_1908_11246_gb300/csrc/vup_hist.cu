@@ -1121,22 +1121,34 @@ __device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0
                         add4(total, v[q]);
                         continue;
                     }
+                    // the partials of the chunks holding the key, four chunks' loads
+                    // in flight together, added in chunk order
                     float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (recs) {
-                        const int32_t gr = p * A.GB + b / kRecBinsH;
-                        for (int c = cc.x; c <= cc.y; ++c) {
-                            if (H.rec_chunk[c] >= H.rec_chunk[c + 1]) continue;
-                            const int side = H.rec_chunk_grp[2 * c] == gr ? 0 : 1;
-                            add4(sum, *reinterpret_cast<const float4 *>(
-                                          A.part + (((int64_t)c * 2 + side) * kRecBinsH + b % kRecBinsH) * A.K_pad + k));
+                    const int32_t gr = p * A.GB + b / kRecBinsH, key = p * A.B + b;
+                    for (int c0 = cc.x; c0 <= cc.y; c0 += 4) {
+                        float4 pv[4];
+                        bool use[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int c = c0 + q;
+                            use[q] = false;
+                            pv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (c > cc.y) continue;
+                            if (recs) {
+                                if (H.rec_chunk[c] >= H.rec_chunk[c + 1]) continue;
+                                const int side = H.rec_chunk_grp[2 * c] == gr ? 0 : 1;
+                                pv[q] = *reinterpret_cast<const float4 *>(
+                                    A.part + (((int64_t)c * 2 + side) * kRecBinsH + b % kRecBinsH) * A.K_pad + k);
+                            } else {
+                                if (H.chunk_pt[c] >= H.chunk_pt[c + 1]) continue;
+                                const int side = H.chunk_bin[2 * c] == key ? 0 : 1;
+                                pv[q] = *reinterpret_cast<const float4 *>(A.part + ((int64_t)c * 2 + side) * A.K_pad + k);
+                            }
+                            use[q] = true;
                         }
-                    } else {
-                        const int32_t key = p * A.B + b;
-                        for (int c = cc.x; c <= cc.y; ++c) {
-                            if (H.chunk_pt[c] >= H.chunk_pt[c + 1]) continue;
-                            const int side = H.chunk_bin[2 * c] == key ? 0 : 1;
-                            add4(sum, *reinterpret_cast<const float4 *>(A.part + ((int64_t)c * 2 + side) * A.K_pad + k));
-                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (use[q]) add4(sum, pv[q]);
                     }
                     add4(total, sum);
                 }
@@ -1158,14 +1170,14 @@ __device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0
     }
 }
 
-__global__ void __launch_bounds__(256, 5) k_hist_finish(const __grid_constant__ HistArgs A) {
+__global__ void __launch_bounds__(256, 4) k_hist_finish(const __grid_constant__ HistArgs A) {
     pdl_trigger();
     pdl_wait();
     hist_finish_tiles(A, blockIdx.x, 1, blockIdx.y);
 }
 
 // Batched finish: items[i] = (instance, density tile, bin tile).
-__global__ void __launch_bounds__(256, 5) k_hist_finish_batched(const HistArgs *__restrict__ insts, const int4 *__restrict__ items) {
+__global__ void __launch_bounds__(256, 4) k_hist_finish_batched(const HistArgs *__restrict__ insts, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
     hist_finish_tiles(insts[it.x], it.y, 1, it.z);
 }
