@@ -251,8 +251,8 @@ __device__ __forceinline__ void density_finish_body(const DensJob &J, int64_t kb
 }
 
 // A-operand table of the tensor-core contraction: rows k, reduction index a
-// contiguous (K-major), each FP32 factor split into BF16 hi + lo.  Block
-// (bx, by) transposes the 32 x 32 tile at a = 32 bx, k = 32 by.
+// contiguous (K-major), each FP32 factor split into BF16 hi + lo (see
+// split_transpose_body for the tiling).
 // Split of one FP32 value into hi + lo: BF16 pair (tensor kind::f16) or
 // TF32 pair stored in floats (kind::tf32).
 __device__ __forceinline__ float to_tf32(float x) {
@@ -275,23 +275,36 @@ __device__ __forceinline__ void split_store2(float *hi, float *lo, int64_t i, fl
     *reinterpret_cast<float2 *>(lo + i) = make_float2(to_tf32(v0 - h0), to_tf32(v1 - h1));
 }
 
-// Block (bx, by) transposes the 64 (a) x 32 (k) tile at a = 64 bx, k = 32 by;
-// each lane writes two consecutive a of one density row.  R_pad is a
-// multiple of 64.
+// Block (bx, by) transposes the 64 (a) x 128 (k) tile at a = 64 bx,
+// k = 128 by: the 64 rows are read with 16-byte loads (eight per thread, in
+// flight together), then each lane writes two consecutive a of one density
+// row.  R_pad is a multiple of 64, K_pad of 128.
+constexpr int kSplitK = 128;
 template <typename T>
 __device__ __forceinline__ void split_transpose_body(const float *__restrict__ tab, int64_t nd, int64_t K_pad,
                                                      int64_t R_pad, T *__restrict__ hi, T *__restrict__ lo,
                                                      int64_t bx, int64_t by) {
-    __shared__ float t[64][33];
-    const int64_t a0 = bx * 64, k0 = by * 32;
-    for (int y = threadIdx.y; y < 64; y += blockDim.y) {
-        int64_t a = a0 + y, k = k0 + threadIdx.x;
-        t[y][threadIdx.x] = (a < nd && k < K_pad) ? tab[a * K_pad + k] : 0.f;
+    __shared__ float t[64][kSplitK + 1];
+    const int64_t a0 = bx * 64, k0 = by * kSplitK;
+    float4 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t a = a0 + threadIdx.y + 8 * i;
+        v[i] = a < nd ? *reinterpret_cast<const float4 *>(tab + a * K_pad + k0 + 4 * threadIdx.x)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float *r = &t[threadIdx.y + 8 * i][4 * threadIdx.x];
+        r[0] = v[i].x;
+        r[1] = v[i].y;
+        r[2] = v[i].z;
+        r[3] = v[i].w;
     }
     __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    for (int y = threadIdx.y; y < kSplitK; y += blockDim.y) {
         const int64_t k = k0 + y, a = a0 + 2 * threadIdx.x;
-        if (k < K_pad && a < R_pad) split_store2(hi, lo, k * R_pad + a, t[2 * threadIdx.x][y], t[2 * threadIdx.x + 1][y]);
+        split_store2(hi, lo, k * R_pad + a, t[2 * threadIdx.x][y], t[2 * threadIdx.x + 1][y]);
     }
     __syncthreads();
 }
@@ -308,7 +321,7 @@ __global__ void k_density_finish(DensJob J) {
     pdl_wait();
     density_finish_body(J, blockIdx.x, blockIdx.y);
 }
-// grid: x = density tiles of 32 (K_pad / 32 may exceed the 65535 limit of y), y = axis tiles
+// grid: x = density tiles of 128 (more than the 65535 limit of y for large K), y = axis tiles
 template <typename T>
 __global__ void k_split_transpose(const float *__restrict__ tab, int64_t nd, int64_t K_pad, int64_t R_pad,
                                   T *__restrict__ hi, T *__restrict__ lo) {
@@ -420,7 +433,7 @@ static vup_status split_tables(vup_grid g, int mask, int64_t K_pad, T *hi0, T *l
             hi += o0;
             lo += o0;
         }
-        dim3 tg((unsigned)ceil_div64(K_pad, 32), (unsigned)ceil_div64(ori.R_pad, 64));
+        dim3 tg((unsigned)ceil_div64(K_pad, kSplitK), (unsigned)ceil_div64(ori.R_pad, 64));
         VUP_CHECK_CUDA(launch_pdl(k_split_transpose<T>, tg, dim3(32, 8), 0, s, (const float *)g->ftab.p + off,
                                   (int64_t)g->n[dred], K_pad, ori.R_pad, hi, lo));
     }
@@ -450,7 +463,7 @@ vup_status vup_density_plan(int n, const vup_grid *gs, const vup_densities *ds, 
         for (int d = 0; d < J.ndim; ++d)
             for (int64_t kb = 0; kb < nkb; ++kb) fin.push_back(make_int4(i, (int)kb, d, 0));
         if (bf16)
-            for (int64_t by = 0; by < ceil_div64(J.K_pad, 32); ++by)
+            for (int64_t by = 0; by < ceil_div64(J.K_pad, kSplitK); ++by)
                 for (int64_t bx = 0; bx < ceil_div64(J.R_pad, 64); ++bx)
                     split.push_back(make_int4(i, (int)bx, (int)by, 0));
     }
