@@ -2,8 +2,12 @@
 // (N x K in the paper's Eq. VUP, stored here row-major as W[K][N]) and is
 // streamed once from HBM.  Every grid point's weight is multiplied into the
 // moment sums and added into its output bin (the one-hot model matrix of
-// Eq. MUP applied to each column).  The kernel is bound by the W read:
-// 4 bytes per distribution-point.
+// Eq. MUP applied to each column).  The roofline is the W read: 4 bytes per
+// distribution-point.  Forms: the bin-sorted block walk k_weights_sorted
+// (B <= 1024, rows of W 16-byte aligned; the blocks sorted once per model by
+// k_wsort_blocks), else k_weights_t (a row per lane, shared-memory atomics;
+// B <= 1024) or k_weights<RB> (larger B), each finished by
+// k_weights_finish.
 #include "vup_internal.cuh"
 #include "vup_async.cuh"
 
