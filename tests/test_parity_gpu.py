@@ -453,6 +453,47 @@ def test_propagate_ipsa_c4_full_size(precision):
     _fused_vs_separate(I.config("c4"), precision, grad_seed=11)
 
 
+def test_propagate_ipsa_other_grids_run_the_two_calls():
+    """Where the fused path does not apply the call runs the two calls in
+    turn: a 1-D grid in FP64 gives their results; a 3-D grid reports the
+    sensitivities unsupported (as vup_ipsa_sensitivity does) and the TF32
+    kinds likewise."""
+    vup = vupmod()
+    import torch
+    prob = I.config("c1", "small")
+    _fused_vs_separate(prob, "fp64")
+    p3 = I.config("c3", "small")
+    g = vup.Grid(p3.n, p3.lo, p3.hi)
+    g.eval_model(p3.model_id, p3.theta, p3.n_bins, p3.n_moments)
+    dd = vup.densities_to_device(p3.dens)
+    ds = vup.make_densities(dd)
+    K, J, B = p3.K, p3.n_moments, p3.n_bins
+    raw = torch.empty((K, J), dtype=torch.float64, device="cuda")
+    cen = torch.empty((K, J), dtype=torch.float64, device="cuda")
+    hist = torch.empty((K, B), dtype=torch.float32, device="cuda")
+    dmu = torch.empty((K, 3, J), dtype=torch.float32, device="cuda")
+    dsg = torch.empty((K, 3, J), dtype=torch.float32, device="cuda")
+    with pytest.raises(vup.VUPError) as e:
+        vup.vup_propagate_ipsa(g.h, ds, vup.VUP_BF16X3, raw, cen, hist, dmu, dsg)
+    assert e.value.status == vup.VUP_ERR_UNSUPPORTED
+    g.sync()
+    g.close()
+    p2 = I.config("c2", "small")
+    g = vup.Grid(p2.n, p2.lo, p2.hi)
+    g.eval_model(p2.model_id, p2.theta, p2.n_bins, p2.n_moments)
+    dd = vup.densities_to_device(p2.dens)
+    ds = vup.make_densities(dd)
+    K, J, B = p2.K, p2.n_moments, p2.n_bins
+    outs = [torch.empty((K, J), dtype=torch.float64, device="cuda") for _ in range(2)] + \
+        [torch.empty((K, B), dtype=torch.float32, device="cuda")] + \
+        [torch.empty((K, 2, J), dtype=torch.float32, device="cuda") for _ in range(2)]
+    with pytest.raises(vup.VUPError) as e:
+        vup.vup_propagate_ipsa(g.h, ds, vup.VUP_TF32X3, *outs)
+    assert e.value.status == vup.VUP_ERR_UNSUPPORTED
+    g.sync()
+    g.close()
+
+
 def test_ipsa_1d_fp64_matches_oracle():
     vup = vupmod()
     prob = I.config("c1", "small")
