@@ -55,6 +55,16 @@ inline cudaError_t vup_dev_malloc(T **p, size_t bytes) {
     return vup_dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
 }
 
+// hi + lo += x: TwoSum (Knuth) of hi and x, the rounding error kept in lo.
+// FP32 sums of many terms are taken in short runs folded into such pairs,
+// which keeps about FP32-squared accuracy over a long range.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+
 // Device status word codes (grid->dstatus[0]); the first non-zero code wins.
 enum { VUP_DSTAT_OK = 0, VUP_DSTAT_EMPTY = 5, VUP_DSTAT_TIMEOUT = 6, VUP_DSTAT_BOUNDS = 7 };
 

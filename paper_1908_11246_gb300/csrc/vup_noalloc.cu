@@ -40,11 +40,11 @@ __global__ void __launch_bounds__(kThreads) k_weights_static(const float *__rest
     const double s = scale[kScaleAbs];
     const int64_t per = (N + n_split - 1) / n_split;
     const int64_t i0 = split * per, i1 = min(N, i0 + per);
-    float m[RB][4];
+    float m[RB][4], ml[RB][4];  // TwoSum pairs (two_sum_acc)
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) m[r][j] = 0.f;
+        for (int j = 0; j < 4; ++j) m[r][j] = ml[r][j] = 0.f;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const float p = (float)(y[i] / s);
         const int bq = bins[i];
@@ -53,13 +53,13 @@ __global__ void __launch_bounds__(kThreads) k_weights_static(const float *__rest
             if (k0 + r >= K) break;
             const float w = W[(k0 + r) * N + i];
             float t = w * p;
-            m[r][0] += t;
+            two_sum_acc(m[r][0], ml[r][0], t);
             t *= p;
-            m[r][1] += t;
+            two_sum_acc(m[r][1], ml[r][1], t);
             t *= p;
-            m[r][2] += t;
+            two_sum_acc(m[r][2], ml[r][2], t);
             t *= p;
-            m[r][3] += t;
+            two_sum_acc(m[r][3], ml[r][3], t);
             atomicAdd(&sh[r * B + bq], w);
         }
     }
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_weights_static(const float *__rest
     for (int r = 0; r < RB; ++r)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            double v = m[r][j];
+            double v = (double)m[r][j] + (double)ml[r][j];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) red[r][j][warp] = v;
         }

@@ -17,6 +17,10 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Every form below sums each thread's moment terms in short FP32 runs folded
+// into TwoSum pairs (two_sum_acc), so that a long point range keeps about
+// FP32-squared accuracy.
+
 template <int RB>
 __global__ void __launch_bounds__(kThreads) k_weights(const float *__restrict__ W, int64_t K, int64_t N,
                                                       const float *__restrict__ z32,
@@ -39,11 +43,11 @@ __global__ void __launch_bounds__(kThreads) k_weights(const float *__restrict__ 
     const int64_t n4 = (N % 4 == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0) ? N / 4 : 0;
     const int64_t per = (n4 + n_split - 1) / n_split;
     const int64_t c0 = split * per, c1 = min(n4, c0 + per);
-    float m[RB][4];
+    float m[RB][4], ml[RB][4];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) m[r][j] = 0.f;
+        for (int j = 0; j < 4; ++j) m[r][j] = ml[r][j] = 0.f;
 #pragma unroll 2
     for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         float4 w[RB];
@@ -56,16 +60,19 @@ __global__ void __launch_bounds__(kThreads) k_weights(const float *__restrict__ 
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
             const float ww[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
+            float s4[4] = {0.f, 0.f, 0.f, 0.f};  // the column's four points, then folded
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float p = zz[q];
                 float t = ww[q] * p;
-                m[r][0] += t;
-                t *= p; m[r][1] += t;
-                t *= p; m[r][2] += t;
-                t *= p; m[r][3] += t;
+                s4[0] += t;
+                t *= p; s4[1] += t;
+                t *= p; s4[2] += t;
+                t *= p; s4[3] += t;
                 atomicAdd(&sh[r * B + bb[q]], ww[q]);
             }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) two_sum_acc(m[r][j], ml[r][j], s4[j]);
         }
     }
     // columns not covered by the float4 loop, split evenly
@@ -79,10 +86,10 @@ __global__ void __launch_bounds__(kThreads) k_weights(const float *__restrict__ 
             for (int r = 0; r < RB; ++r) {
                 const float w = wrow[r][i];
                 float t = w * p;
-                m[r][0] += t;
-                t *= p; m[r][1] += t;
-                t *= p; m[r][2] += t;
-                t *= p; m[r][3] += t;
+                two_sum_acc(m[r][0], ml[r][0], t);
+                t *= p; two_sum_acc(m[r][1], ml[r][1], t);
+                t *= p; two_sum_acc(m[r][2], ml[r][2], t);
+                t *= p; two_sum_acc(m[r][3], ml[r][3], t);
                 atomicAdd(&sh[r * B + bq], w);
             }
         }
@@ -92,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_weights(const float *__restrict__ 
     for (int r = 0; r < RB; ++r)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            double v = m[r][j];
+            double v = (double)m[r][j] + (double)ml[r][j];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) red[r][j][warp] = v;
         }
@@ -122,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) k_weights_t(const float *__restrict_
                                                         const int32_t *__restrict__ bins, int B, int64_t n_split,
                                                         double *__restrict__ mpart, float *__restrict__ hpart) {
     extern __shared__ float sh[];  // [kRowsT][B + 1]
-    __shared__ float red[kThreads / 32][kRowsT][4];
+    __shared__ double red[kThreads / 32][kRowsT][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t split = blockIdx.x;
     const int64_t k0 = (int64_t)blockIdx.y * kRowsT;
@@ -131,10 +138,9 @@ __global__ void __launch_bounds__(kThreads) k_weights_t(const float *__restrict_
     __syncthreads();
     const float *wrow = W + min(k0 + lane, K - 1) * N;  // rows past K are never stored
     float *hrow = sh + lane * ld;
-    // moments: a step's 16 points are summed on their own, then added to the
-    // running sums (two-level FP32 summation keeps the rounding error of a
-    // lane's long point range small)
-    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+    // moments: a step's 16 points are summed on their own, then folded into
+    // the running TwoSum pairs
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f, l3 = 0.f;
     float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
     auto point = [&](float w, float p, int b) {
         float t = w * p;
@@ -148,10 +154,10 @@ __global__ void __launch_bounds__(kThreads) k_weights_t(const float *__restrict_
         atomicAdd(hrow + b, w);
     };
     auto fold = [&]() {
-        m0 += t0;
-        m1 += t1;
-        m2 += t2;
-        m3 += t3;
+        two_sum_acc(m0, l0, t0);
+        two_sum_acc(m1, l1, t1);
+        two_sum_acc(m2, l2, t2);
+        two_sum_acc(m3, l3, t3);
         t0 = t1 = t2 = t3 = 0.f;
     };
     // vector steps of kPtsT points (rows 16-byte aligned only when N % 4 == 0)
@@ -184,13 +190,20 @@ __global__ void __launch_bounds__(kThreads) k_weights_t(const float *__restrict_
         const int64_t rem = N - n_steps * kPtsT;
         const int64_t per1 = (rem + n_split - 1) / n_split;
         const int64_t i0 = n_steps * kPtsT + split * per1, i1 = min(N, i0 + per1);
-        for (int64_t i = i0 + warp; i < i1; i += kThreads / 32) point(wrow[i], z32[i], bins[i]);
+        int64_t n_pt = 0;
+        for (int64_t i = i0 + warp; i < i1; i += kThreads / 32) {
+            point(wrow[i], z32[i], bins[i]);
+            if (++n_pt == kPtsT) {
+                fold();
+                n_pt = 0;
+            }
+        }
         fold();
     }
-    red[warp][lane][0] = m0;
-    red[warp][lane][1] = m1;
-    red[warp][lane][2] = m2;
-    red[warp][lane][3] = m3;
+    red[warp][lane][0] = (double)m0 + (double)l0;
+    red[warp][lane][1] = (double)m1 + (double)l1;
+    red[warp][lane][2] = (double)m2 + (double)l2;
+    red[warp][lane][3] = (double)m3 + (double)l3;
     __syncthreads();
     if (threadIdx.x < kRowsT * 4) {
         const int r = threadIdx.x >> 2, j = threadIdx.x & 3;
@@ -255,13 +268,6 @@ struct WStage {
 
 using namespace vup_async;
 
-// hi + lo += x: TwoSum (Knuth) of hi and x, the rounding error kept in lo
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
-    const float s = hi + x;
-    const float bp = s - hi;
-    lo += (hi - (s - bp)) + (x - bp);
-    hi = s;
-}
 
 template <int STAGES, int MINB>
 __global__ void __launch_bounds__(kWThreads, MINB)

@@ -289,6 +289,31 @@ def test_weights_path_matches_oracle():
     Hp.check_hist(hist.cpu().numpy(), res["hist"])
 
 
+def test_weights_path_rows_not_16_byte_aligned():
+    """A grid whose N is not a multiple of 4 (rows of W not 16-byte aligned):
+    the row-per-lane form of the supplied-weights path, against the oracle."""
+    vup = vupmod()
+    import torch
+    prob = I.Problem("ragged_w", (101, 57), (-2.0, -1.0), (2.5, 1.5), I.MODEL_SIN_SIN2_2D, (1.0, 3.0),
+                     I.random_densities(np.random.default_rng(12), 45, (-2.0, -1.0), (2.5, 1.5),
+                                        sig=(0.1, 0.8), width=(0.3, 1.0)), 100)
+    assert prob.N % 4 != 0
+    K = prob.K
+    Wd = np.stack([O.weights(prob.n, prob.lo, prob.hi, prob.dens, k)[0] for k in range(K)])
+    g = vup.Grid(prob.n, prob.lo, prob.hi)
+    g.eval_model(prob.model_id, prob.theta, prob.n_bins, 4)
+    W = torch.as_tensor(Wd.astype(np.float32), device="cuda")
+    raw = torch.empty((K, 4), dtype=torch.float64, device="cuda")
+    hist = torch.empty((K, prob.n_bins), dtype=torch.float32, device="cuda")
+    vup.vup_propagate_weights(g.h, W, raw, hist)
+    g.sync()
+    res = O.solve(prob, rows=np.arange(K))
+    scale = Hp.abs_moment_scale(prob, res["y"], np.arange(K))
+    Hp.check_moments(raw.cpu().numpy(), res["raw"], scale, Hp.TOL["fp32"])
+    Hp.check_hist(hist.cpu().numpy(), res["hist"])
+    g.close()
+
+
 def test_weights_path_full_grid_matches_oracle():
     """The supplied-W path on the full c2 grid (1024^2 points, 4096 sorted
     blocks, every CTA over 64 of them) for 48 densities, against the oracle at
