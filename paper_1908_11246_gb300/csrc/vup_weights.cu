@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_weights_t(const float *__restrict_
 // k0 + l) and a range of blocks; each block's 32 x 256 tile of W is staged in
 // shared memory by bulk copies (cp.async.bulk, one per row, issued by warp 0
 // and completing on the stage's mbarrier; two stages) together with the
-// block's sorted words and powers.  Rows are padded to 260 floats: a warp
+// block's sorted words and z values.  Rows are padded to 260 floats: a warp
 // reading one column of 32 rows touches 8 banks (a 4-way conflict; rows
 // copied in 16-byte units cannot spread one column over more than 8).  A
 // bin's points (a run) are summed in a register and added once to the lane's
@@ -262,7 +262,7 @@ constexpr uint16_t kWCross = 0x8000u;
 struct WStage {
     float tile[kWRows][kWLd];  // column kWBlock is zero (the fillers' column)
     uint32_t pt[2 * kWBlock];
-    float4 z[kWBlock];
+    float z[kWBlock];  // z = y / s_abs; the walk forms z^2..z^4 (as the sort kernel would)
     uint16_t fix[kWFix];
 };
 
@@ -272,7 +272,7 @@ using namespace vup_async;
 template <int STAGES, int MINB>
 __global__ void __launch_bounds__(kWThreads, MINB)
 k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32_t *__restrict__ wpt,
-                 const float4 *__restrict__ wz, const uint16_t *__restrict__ wfix, int B, int64_t n_split,
+                 const float *__restrict__ wz, const uint16_t *__restrict__ wfix, int B, int64_t n_split,
                  double *__restrict__ mpart, float *__restrict__ hpart, int *dstatus) {
     extern __shared__ __align__(16) uint8_t wsm[];
     __shared__ uint64_t full[STAGES];
@@ -296,7 +296,7 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
 
     // stage block c into buffer b (every warp: lanes 0-3 of warp w copy rows
     // 4 w .. 4 w + 3 of W, rows past K re-reading row K - 1, never stored;
-    // warp 0 also the block's sorted words, powers and crossing runs); each
+    // warp 0 also the block's sorted words, z values and crossing runs); each
     // warp adds its bytes to full[b] and arrives once
     auto stage = [&](int64_t c, int b) {
         WStage &S = st[b];
@@ -386,13 +386,18 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
                              : "=f"(hv[u])
                              : "r"(ha[u]), "r"(bw[u] & 1u));
             }
+            // the batch's eight z in two broadcast loads; powers by repeated
+            // multiplication in FP32, as the other forms take them
+            const float4 za = *reinterpret_cast<const float4 *>(&S.z[t]);
+            const float4 zb = *reinterpret_cast<const float4 *>(&S.z[t + 4]);
+            const float zv[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const float4 z = S.z[t + u];
-                m0 = fmaf(wv[u], z.x, m0);
-                m1 = fmaf(wv[u], z.y, m1);
-                m2 = fmaf(wv[u], z.z, m2);
-                m3 = fmaf(wv[u], z.w, m3);
+                const float p1 = zv[u], p2 = p1 * p1, p3 = p2 * p1, p4 = p3 * p1;
+                m0 = fmaf(wv[u], p1, m0);
+                m1 = fmaf(wv[u], p2, m1);
+                m2 = fmaf(wv[u], p3, m2);
+                m3 = fmaf(wv[u], p4, m3);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -454,14 +459,14 @@ k_weights_sorted(const float *__restrict__ W, int64_t K, int64_t N, const uint32
 // Block sort of the grid points by bin (once per model): one CTA of 256
 // threads per block sorts the keys bin << 8 | local index (bitonic, in
 // shared memory) and writes, in sorted order, the column words, the
-// histogram words (see WStage) and the powers z^j of z = y / s_abs (FP32, as
-// the other supplied-weights kernels form them), and for each warp slice the
+// histogram words (see WStage) and z = y / s_abs (FP32, as the other
+// supplied-weights kernels form it), and for each warp slice the
 // bins of the runs that cross its start and its end.  Positions past the
 // grid's end sort last.
 __global__ void __launch_bounds__(kWBlock) k_wsort_blocks(const int32_t *__restrict__ bins,
                                                           const double *__restrict__ y, int64_t N,
                                                           const double *__restrict__ scale, int B,
-                                                          uint32_t *__restrict__ wpt, float4 *__restrict__ wz,
+                                                          uint32_t *__restrict__ wpt, float *__restrict__ wz,
                                                           uint16_t *__restrict__ wfix) {
     __shared__ uint32_t key[kWBlock];
     const int t = threadIdx.x;
@@ -486,7 +491,7 @@ __global__ void __launch_bounds__(kWBlock) k_wsort_blocks(const int32_t *__restr
     // position q continues the run of q - 1 (q a real position)
     auto cont = [&](int q) { return q > 0 && q < nv && bin_at(q) == bin_at(q - 1); };
     uint32_t cword = kWFillerCol, bword = 0u;
-    float4 zp = make_float4(0.f, 0.f, 0.f, 0.f);
+    float zp = 0.f;
     if (t < nv) {
         const uint32_t kw = key[t];
         const int w = t / kWSlice, next = (w + 1) * kWSlice;  // first position of the next slice
@@ -496,10 +501,7 @@ __global__ void __launch_bounds__(kWBlock) k_wsort_blocks(const int32_t *__restr
             bword = ((crosses ? (uint32_t)(B + 1 + kWWarps + w) : (kw >> 8)) << 2) | 1u;
         }
         const float p = (float)(y[col0 + (kw & 0xffu)] / scale[kScaleAbs]);
-        zp.x = p;
-        zp.y = zp.x * p;
-        zp.z = zp.y * p;
-        zp.w = zp.z * p;
+        zp = p;
     }
     wpt[c * 2 * kWBlock + t] = cword;
     wpt[c * 2 * kWBlock + kWBlock + t] = bword;
@@ -555,11 +557,11 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
         const int64_t n_blk = ceil_div64(N, kWBlock);
         if (g->wsort_gen != g->model_gen) {
             if ((st = devbuf_reserve(g->wsort_pt, sizeof(uint32_t) * n_blk * 2 * kWBlock)) != VUP_OK ||
-                (st = devbuf_reserve(g->wsort_z, sizeof(float4) * n_blk * kWBlock)) != VUP_OK ||
+                (st = devbuf_reserve(g->wsort_z, sizeof(float) * n_blk * kWBlock)) != VUP_OK ||
                 (st = devbuf_reserve(g->wsort_fix, sizeof(uint16_t) * kWFix * n_blk)) != VUP_OK)
                 return st;
             k_wsort_blocks<<<(unsigned)n_blk, kWBlock, 0, s>>>(g->bins, g->y, N, g->ydev_scale, B,
-                                                                (uint32_t *)g->wsort_pt.p, (float4 *)g->wsort_z.p,
+                                                                (uint32_t *)g->wsort_pt.p, (float *)g->wsort_z.p,
                                                                 (uint16_t *)g->wsort_fix.p);
             VUP_CHECK_LAUNCH();
             g->wsort_gen = g->model_gen;
@@ -594,7 +596,7 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
         dim3 grd((unsigned)n_split, (unsigned)rows);
         auto launch = [&](auto kern) -> vup_status {
             VUP_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<grd, kWThreads, smem, s>>>(W, K, N, (const uint32_t *)g->wsort_pt.p, (const float4 *)g->wsort_z.p,
+            kern<<<grd, kWThreads, smem, s>>>(W, K, N, (const uint32_t *)g->wsort_pt.p, (const float *)g->wsort_z.p,
                                              (const uint16_t *)g->wsort_fix.p, B, n_split, (double *)g_wmpart.p,
                                              (float *)g_whpart.p, g->dstatus);
             return VUP_OK;
