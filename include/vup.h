@@ -422,6 +422,15 @@ vup_status vup_grid_info(vup_grid g, vup_grid_info_t *info);
  */
 vup_status vup_set_hist_stream(vup_grid g, int32_t stream_kind, vup_stream_t stream);
 
+/* Form of vup_propagate_weights (_noalloc has its own): -1 (default) lets
+ * the library choose; 0 the bin-sorted block walk (B <= 1024, N a multiple
+ * of 4, W 16-byte aligned, ceil(K / 32) <= 65535); 1 a row of W per lane with shared-memory histogram rows
+ * (B <= 1024); 2 the general form (any B).  A forced form that does not
+ * apply to a call's B or K gives way to the next that does.  All give the
+ * moments and H[k, b] of Eq. 4 from the same FP32 products (summed in a
+ * different order).  VUP_ERR_INVALID_ARG for another value. */
+vup_status vup_set_weights_form(vup_grid g, int32_t form);
+
 /* Copy one of the grid's arrays into a caller device buffer (for checks).
  * which: 0 = y (double[N]), 1 = bin ids (int32[N]), 2 = sorted order
  * (int32[N], flat index of the t-th point in bin order), 3 = bin offsets

@@ -840,6 +840,12 @@ extern "C" vup_status vup_set_hist_stream(vup_grid g, int32_t stream_kind, vup_s
     return VUP_OK;
 }
 
+extern "C" vup_status vup_set_weights_form(vup_grid g, int32_t form) {
+    if (!g || form < -1 || form > 2) return VUP_ERR_INVALID_ARG;
+    g->weights_form = form;
+    return VUP_OK;
+}
+
 extern "C" vup_status vup_grid_copy(vup_grid g, int which, void *dst_dev, size_t nbytes, vup_stream_t stream) {
     if (!g || !dst_dev) return VUP_ERR_INVALID_ARG;
     if (!g->have_model) return VUP_ERR_STATE;

@@ -305,6 +305,7 @@ struct vup_grid_s {
     // slices at bin boundaries; built for model generation wsort_gen
     DevBuf wsort_pt, wsort_z, wsort_fix;
     uint64_t wsort_gen = ~0ull;
+    int weights_form = -1;         // supplied-W form: -1 auto, 0 sorted walk, 1 row per lane, 2 general
 
     int *dstatus = nullptr;        // [1] device status word
 };

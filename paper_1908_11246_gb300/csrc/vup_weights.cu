@@ -553,7 +553,10 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
     const int B = g->B;
     vup_status st;
     const bool aligned = N % 4 == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0;
-    if (B <= 1024 && aligned && ceil_div64(K, kWRows) <= 65535) {
+    // a forced form (vup_set_weights_form) where it applies, else the first
+    // that does: the sorted walk, the row-per-lane form, the general one
+    const int form = g->weights_form;
+    if ((form == -1 || form == 0) && B <= 1024 && aligned && ceil_div64(K, kWRows) <= 65535) {
         const int64_t n_blk = ceil_div64(N, kWBlock);
         if (g->wsort_gen != g->model_gen) {
             if ((st = devbuf_reserve(g->wsort_pt, sizeof(uint32_t) * n_blk * 2 * kWBlock)) != VUP_OK ||
@@ -623,7 +626,7 @@ vup_status vup_weights_path(vup_grid g, int64_t K, const float *W, double *raw, 
     k_z32<<<(unsigned)std::min<int64_t>(ceil_div64(N, 256), 4096), 256, 0, s>>>(g->y, N, g->ydev_scale,
                                                                                 (float *)g_wz32.p);
     VUP_CHECK_LAUNCH();
-    if (B <= 1024) {
+    if (B <= 1024 && form != 2) {
         const int64_t rows = ceil_div64(K, kRowsT);
         int64_t n_split = std::max<int64_t>(1, (int64_t)vup_num_sms() * 4 / std::max<int64_t>(rows, 1));
         n_split = std::min<int64_t>(n_split, std::max<int64_t>(1, N / 8192));

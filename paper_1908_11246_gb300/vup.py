@@ -29,7 +29,7 @@ ABI_SYMBOLS = [
     "vup_grid_create", "vup_grid_destroy", "vup_eval_model", "vup_set_outputs", "vup_propagate",
     "vup_propagate_weights", "vup_propagate_weights_noalloc", "vup_ipsa_sensitivity", "vup_propagate_ipsa", "vup_propagate_batched", "vup_batched_report", "vup_sync", "vup_selftest_wait", "vup_model_at",
     "vup_deviation_moments", "vup_ipsa_matrix", "vup_sa_fields", "vup_posterior_means",
-    "vup_grid_info", "vup_set_hist_stream", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
+    "vup_grid_info", "vup_set_hist_stream", "vup_set_weights_form", "vup_grid_copy", "vup_status_string", "vup_version", "vup_profile",
     "vup_profile_read", "vup_profile_timeline", "vup_last_error_detail", "vup_debug_fail_alloc",
     "vup_measure_peak",
 ]
@@ -86,6 +86,7 @@ def lib():
         l.vup_posterior_means.argtypes = [vp, C.POINTER(vup_densities), vp, vp, vp]
         l.vup_grid_info.argtypes = [vp, C.POINTER(vup_grid_info_t)]
         l.vup_set_hist_stream.argtypes = [vp, C.c_int32, vp]
+        l.vup_set_weights_form.argtypes = [vp, C.c_int32]
         l.vup_grid_copy.argtypes = [vp, C.c_int, vp, C.c_size_t, vp]
         l.vup_profile.argtypes = [C.c_int]
         l.vup_profile_read.argtypes = [C.c_char_p, C.c_size_t]
@@ -308,6 +309,11 @@ def vup_set_hist_stream(h, kind: int, stream=None):
     _check(lib().vup_set_hist_stream(h, int(kind), _stream(stream)), "vup_set_hist_stream")
 
 
+def vup_set_weights_form(h, form: int):
+    """Supplied-W form: -1 auto, 0 sorted block walk, 1 row per lane, 2 general."""
+    _check(lib().vup_set_weights_form(h, int(form)), "vup_set_weights_form")
+
+
 def vup_grid_copy(h, which, out, stream=None):
     _check(lib().vup_grid_copy(h, int(which), _ptr(out), out.numel() * out.element_size(), _stream(stream)),
            "vup_grid_copy")
@@ -407,6 +413,10 @@ class Grid:
     def set_hist_stream(self, kind: int, stream=None):
         """-1: automatic choice; 0: sorted points; 1: sorted intervals; 2: records."""
         vup_set_hist_stream(self.h, kind, stream)
+
+    def set_weights_form(self, form: int):
+        """-1: automatic choice; 0: sorted block walk; 1: row per lane; 2: general form."""
+        vup_set_weights_form(self.h, form)
 
     def array(self, which):
         import torch

@@ -270,7 +270,10 @@ def test_large_output_offset_keeps_central_moments():
     g.close()
 
 
-def test_weights_path_matches_oracle():
+@pytest.mark.parametrize("form", [-1, 1, 2])
+def test_weights_path_matches_oracle(form):
+    """The supplied-W path on c2's small grid, each form (automatic choice:
+    the sorted block walk; row per lane; general), against the oracle."""
     vup = vupmod()
     import torch
     prob = I.config("c2", "small")
@@ -278,6 +281,7 @@ def test_weights_path_matches_oracle():
     Wd = np.stack([O.weights(prob.n, prob.lo, prob.hi, prob.dens, k)[0] for k in range(K)])
     g = vup.Grid(prob.n, prob.lo, prob.hi)
     g.eval_model(prob.model_id, prob.theta, prob.n_bins, 4)
+    g.set_weights_form(form)
     W = torch.as_tensor(Wd.astype(np.float32), device="cuda")
     raw = torch.empty((K, 4), dtype=torch.float64, device="cuda")
     hist = torch.empty((K, prob.n_bins), dtype=torch.float32, device="cuda")
@@ -289,9 +293,12 @@ def test_weights_path_matches_oracle():
     Hp.check_hist(hist.cpu().numpy(), res["hist"])
 
 
-def test_weights_path_rows_not_16_byte_aligned():
+@pytest.mark.parametrize("form", [-1, 2])
+def test_weights_path_rows_not_16_byte_aligned(form):
     """A grid whose N is not a multiple of 4 (rows of W not 16-byte aligned):
-    the row-per-lane form of the supplied-weights path, against the oracle."""
+    the automatic choice (the row-per-lane form; the sorted walk's bulk row
+    copies need 16-byte rows) and the general form of the supplied-weights
+    path, against the oracle."""
     vup = vupmod()
     import torch
     prob = I.Problem("ragged_w", (101, 57), (-2.0, -1.0), (2.5, 1.5), I.MODEL_SIN_SIN2_2D, (1.0, 3.0),
@@ -302,6 +309,7 @@ def test_weights_path_rows_not_16_byte_aligned():
     Wd = np.stack([O.weights(prob.n, prob.lo, prob.hi, prob.dens, k)[0] for k in range(K)])
     g = vup.Grid(prob.n, prob.lo, prob.hi)
     g.eval_model(prob.model_id, prob.theta, prob.n_bins, 4)
+    g.set_weights_form(form)
     W = torch.as_tensor(Wd.astype(np.float32), device="cuda")
     raw = torch.empty((K, 4), dtype=torch.float64, device="cuda")
     hist = torch.empty((K, prob.n_bins), dtype=torch.float32, device="cuda")
@@ -311,6 +319,8 @@ def test_weights_path_rows_not_16_byte_aligned():
     scale = Hp.abs_moment_scale(prob, res["y"], np.arange(K))
     Hp.check_moments(raw.cpu().numpy(), res["raw"], scale, Hp.TOL["fp32"])
     Hp.check_hist(hist.cpu().numpy(), res["hist"])
+    with pytest.raises(vup.VUPError):
+        g.set_weights_form(3)
     g.close()
 
 
