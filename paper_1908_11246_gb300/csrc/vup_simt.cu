@@ -228,11 +228,21 @@ __device__ __forceinline__ void moments_finish_body(const float *__restrict__ pa
                                                     int64_t kb) {
     const int64_t k = kb * (int64_t)blockDim.x + threadIdx.x;
     if (k >= K) return;
-    double mz[4] = {0, 0, 0, 0};
+    // the column tiles' partials summed as FP32 TwoSum pairs (about 2^-44
+    // relative to the sum of magnitudes, far below the partials' own FP32
+    // rounding) on the FP32 pipes, one FP64 conversion per sum: FP64
+    // arithmetic runs at a small fraction of the FP32 rate here
+    float mh[4] = {0.f, 0.f, 0.f, 0.f}, ml[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
     for (int64_t t = 0; t < n_ct; ++t) {
         const float4 v = *reinterpret_cast<const float4 *>(part + (t * K_pad + k) * 4);
-        mz[0] += v.x; mz[1] += v.y; mz[2] += v.z; mz[3] += v.w;
+        two_sum_acc(mh[0], ml[0], v.x);
+        two_sum_acc(mh[1], ml[1], v.y);
+        two_sum_acc(mh[2], ml[2], v.z);
+        two_sum_acc(mh[3], ml[3], v.w);
     }
+    double mz[4];
+    for (int j = 0; j < 4; ++j) mz[j] = (double)mh[j] + (double)ml[j];
     double invZ = 1.0;
     for (int d = 0; d < ndim; ++d) invZ *= ds[k * ndim + d].invZ;
     invZ /= scale[kScaleP];  // the tables' power-of-two factor
@@ -270,30 +280,49 @@ __global__ void k_moments_finish_batched(const FinishJob *__restrict__ jobs, con
 //   dMz_m/dsigma_d = (sum_i W u_d^2 z^m - E_d[u^2] Mz_m) / sigma_d
 // and dM_j/dp = sum_{m=1..j} C(j, m) c^(j-m) s^m dMz_m/dp (Mz_0 = 1 is constant).
 // part0 holds orientation 0 (rest = axis 0): [w, w u_0, w u_0^2] partials,
-// part1 orientation 1 (rest = axis 1, 2-D only).
-__global__ void k_ipsa_finish(const float *__restrict__ part0, int64_t nct0, const float *__restrict__ part1,
-                              int64_t nct1, int64_t K, int64_t K_pad, int J, const DensStats *__restrict__ ds,
-                              const DensConst *__restrict__ dc, int ndim, const double *__restrict__ scale,
-                              const double *__restrict__ grad, float *__restrict__ dmu,
-                              float *__restrict__ dsg) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= K) return;
+// part1 orientation 1 (rest = axis 1, 2-D only).  A CTA serves 128
+// densities with 128 threads per plane q = 3 o + w (orientation o, weight w):
+// each sums its plane's column tiles for its density as FP32 TwoSum pairs
+// (see moments_finish_body), and the threads of plane 0 combine the six
+// sums of their density in FP64.
+constexpr int kIpsaFinK = 128;
+__global__ void __launch_bounds__(6 * kIpsaFinK) k_ipsa_finish(const float *__restrict__ part0, int64_t nct0,
+                                                               const float *__restrict__ part1, int64_t nct1,
+                                                               int64_t K, int64_t K_pad, int J,
+                                                               const DensStats *__restrict__ ds,
+                                                               const DensConst *__restrict__ dc, int ndim,
+                                                               const double *__restrict__ scale,
+                                                               const double *__restrict__ grad,
+                                                               float *__restrict__ dmu, float *__restrict__ dsg) {
+    __shared__ double sS[6][kIpsaFinK][4];
+    const int kk = threadIdx.x % kIpsaFinK, q = threadIdx.x / kIpsaFinK;
+    const int64_t k = blockIdx.x * (int64_t)kIpsaFinK + kk;
+    {
+        const int o = q / 3, w = q % 3;
+        float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+        if (k < K && o < ndim) {
+            const float *part = o == 0 ? part0 : part1;
+            const int64_t nct = o == 0 ? nct0 : nct1;
+#pragma unroll 4
+            for (int64_t t = 0; t < nct; ++t) {
+                const float4 v = *reinterpret_cast<const float4 *>(part + ((w * nct + t) * K_pad + k) * 4);
+                two_sum_acc(sh[0], sl[0], v.x);
+                two_sum_acc(sh[1], sl[1], v.y);
+                two_sum_acc(sh[2], sl[2], v.z);
+                two_sum_acc(sh[3], sl[3], v.w);
+            }
+        }
+        for (int j = 0; j < 4; ++j) sS[q][kk][j] = (double)sh[j] + (double)sl[j];
+    }
+    __syncthreads();
+    if (q != 0 || k >= K) return;
     double invZ = 1.0 / scale[kScaleP];  // the tables' power-of-two factor
     for (int d = 0; d < ndim; ++d) invZ *= ds[k * ndim + d].invZ;
     const double s = scale[kScaleS], c = scale[kScaleC];
     double S[2][3][4];
     for (int o = 0; o < 2; ++o)
         for (int w = 0; w < 3; ++w)
-            for (int j = 0; j < 4; ++j) S[o][w][j] = 0.0;
-    for (int o = 0; o < ndim; ++o) {
-        const float *part = o == 0 ? part0 : part1;
-        const int64_t nct = o == 0 ? nct0 : nct1;
-        for (int w = 0; w < 3; ++w)
-            for (int64_t t = 0; t < nct; ++t) {
-                const float4 v = *reinterpret_cast<const float4 *>(part + ((w * nct + t) * K_pad + k) * 4);
-                S[o][w][0] += v.x; S[o][w][1] += v.y; S[o][w][2] += v.z; S[o][w][3] += v.w;
-            }
-    }
+            for (int j = 0; j < 4; ++j) S[o][w][j] = sS[3 * o + w][kk][j];
     for (int d = 0; d < ndim; ++d) {
         const DensStats st = ds[k * ndim + d];
         const bool diff = dc[k * ndim + d].kind != VUP_UNIFORM;
@@ -397,7 +426,7 @@ vup_status vup_ipsa_finish(vup_grid g, int64_t K, int n_tiles0, int n_tiles1, co
     const float *p0 = (const float *)g->ipsa_part.p;
     const float *p1 = p0 + (size_t)3 * n_tiles0 * K_pad * 4;
     VUP_PROF("ipsa_finish_fp64", s, 1);
-    k_ipsa_finish<<<(unsigned)ceil_div64(K, 128), 128, 0, s>>>(
+    k_ipsa_finish<<<(unsigned)ceil_div64(K, kIpsaFinK), 6 * kIpsaFinK, 0, s>>>(
         p0, n_tiles0, p1, n_tiles1, K, K_pad, g->J, (const DensStats *)g->dstats.p,
         (const DensConst *)g->dconst.p, g->ndim, g->ydev_scale, grad, dmu, dsg);
     VUP_CHECK_LAUNCH();
