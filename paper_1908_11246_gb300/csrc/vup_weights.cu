@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kThreads) k_weights_t(const float *__restrict_
 // to its bin with a shared-memory atomic after the walk.  The moments are
 // summed per block in FP32 and across blocks as TwoSum pairs.  The histogram
 // rows hold at most ~64 blocks' contributions per bin (column splits are
-// sized for that), the partial rows are summed in FP64.
+// sized for that), the partial rows are summed as FP32 TwoSum pairs.
 constexpr int kWBlock = 256;
 constexpr int kWLd = kWBlock + 4;       // padded tile row (floats)
 constexpr int kWRows = 32;
@@ -522,9 +522,13 @@ __global__ void k_weights_finish(const double *__restrict__ mpart, const float *
                                  double *__restrict__ raw, float *__restrict__ hist) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (hist && e < K * B) {
-        double s = 0.0;
-        for (int64_t q = 0; q < n_split; ++q) s += hpart[q * K * B + e];
-        hist[e] = (float)s;
+        // the splits' partial rows as an FP32 TwoSum pair (about 2^-44
+        // relative to the sum of magnitudes) on the FP32 pipes: FP64 adds
+        // run at a small fraction of the FP32 rate here
+        float sh = 0.f, sl = 0.f;
+#pragma unroll 4
+        for (int64_t q = 0; q < n_split; ++q) two_sum_acc(sh, sl, hpart[q * K * B + e]);
+        hist[e] = (float)((double)sh + (double)sl);
     }
     if (raw && e < K * J) {
         const int64_t k = e / J;
