@@ -1069,15 +1069,17 @@ __global__ void __launch_bounds__(128) k_prefix_tiles(const __grid_constant__ Hi
 // Finish H[k, b]: for every part, the key (part, b) is either empty, summed
 // whole by the single chunk that holds it (direct row), or cut by chunk
 // boundaries and summed from the partials of the chunks overlapping it (in
-// chunk order); parts are added in order.  A tile of 128 densities x 8 bins
-// per 256 threads: warp w takes bin w, each lane four consecutive densities,
-// so the direct rows and partials are read as coalesced 512-byte rows; the
-// tile goes to the [K][B] output through shared memory (8 consecutive bins,
-// one 32-byte sector, per row).
+// chunk order); parts are added in order.  Two tiles of 128 densities x 8
+// bins per 256 threads: warp w takes bin w, each lane four consecutive
+// densities of each tile (the two tiles' loads in flight together), so the
+// direct rows and partials are read as coalesced 512-byte rows; the tiles go
+// to the [K][B] output through shared memory (8 consecutive bins, one
+// 32-byte sector, per row).
 constexpr int kFinK = 128, kFinB = 8;
+constexpr int kFinNK = 2;     // density tiles per CTA: their loads are in flight together
 constexpr int kFinMaxP = 96;  // >= parts of any axis: ceil(32767 / kMaxPartRows) = 84
-__device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0, int nkt, int bt) {
-    __shared__ float tile[kFinB][kFinK + 1];
+__device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0, int bt) {
+    __shared__ float tile[kFinNK][kFinB][kFinK + 1];
     __shared__ int2 s_cc[kFinMaxP][kFinB];
     const LayoutArgs &H = A.sel[0] ? A.L1 : A.L0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1093,93 +1095,114 @@ __device__ __forceinline__ void hist_finish_tiles(const HistArgs &A, int64_t kt0
     }
     __syncthreads();
     const int b = bt * kFinB + warp;
-    for (int64_t kt = kt0; kt < kt0 + nkt; ++kt) {
-        const int64_t k = kt * kFinK + 4 * lane;
-        float4 total = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (b < A.B) {
-            // four parts at a time: their direct rows in flight together, then
-            // added in part order (cut keys from their chunks' partials)
-            for (int p0 = 0; p0 < P; p0 += 4) {
-                float4 v[4];
+    int64_t kq[kFinNK];  // this lane's first density in each tile
+    bool live[kFinNK];   // the tile holds densities
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int p = p0 + q;
-                    v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (p < P) {
-                        const int2 cc = s_cc[p][warp];
-                        if (cc.x >= 0 && cc.x == cc.y)
-                            v[q] = *reinterpret_cast<const float4 *>(A.direct + ((int64_t)p * A.B + b) * A.K_pad + k);
-                    }
+    for (int t = 0; t < kFinNK; ++t) {
+        live[t] = (kt0 + t) * kFinK < A.K;
+        kq[t] = (kt0 + t) * kFinK + 4 * lane;
+    }
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 total[kFinNK];
+#pragma unroll
+    for (int t = 0; t < kFinNK; ++t) total[t] = zero;
+    if (b < A.B) {
+        // four parts at a time: their direct rows (of every tile) in flight
+        // together, then added in part order (cut keys from their chunks'
+        // partials)
+        for (int p0 = 0; p0 < P; p0 += 4) {
+            float4 v[4][kFinNK];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int p = p0 + q;
+                const int2 cc = p < P ? s_cc[p][warp] : make_int2(-1, -1);
+                const float *row = A.direct + ((int64_t)p * A.B + b) * A.K_pad;
+#pragma unroll
+                for (int t = 0; t < kFinNK; ++t)
+                    v[q][t] = (cc.x >= 0 && cc.x == cc.y && live[t]) ? *reinterpret_cast<const float4 *>(row + kq[t])
+                                                                     : zero;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int p = p0 + q;
+                if (p >= P) break;
+                const int2 cc = s_cc[p][warp];
+                if (cc.x < 0) continue;
+                if (cc.x == cc.y) {
+#pragma unroll
+                    for (int t = 0; t < kFinNK; ++t) add4(total[t], v[q][t]);
+                    continue;
                 }
+                // the partials of the chunks holding the key, two chunks'
+                // loads (of every tile) in flight together, added in chunk order
+                float4 sum[kFinNK];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int p = p0 + q;
-                    if (p >= P) break;
-                    const int2 cc = s_cc[p][warp];
-                    if (cc.x < 0) continue;
-                    if (cc.x == cc.y) {
-                        add4(total, v[q]);
-                        continue;
-                    }
-                    // the partials of the chunks holding the key, four chunks' loads
-                    // in flight together, added in chunk order
-                    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-                    const int32_t gr = p * A.GB + b / kRecBinsH, key = p * A.B + b;
-                    for (int c0 = cc.x; c0 <= cc.y; c0 += 4) {
-                        float4 pv[4];
-                        bool use[4];
+                for (int t = 0; t < kFinNK; ++t) sum[t] = zero;
+                const int32_t gr = p * A.GB + b / kRecBinsH, key = p * A.B + b;
+                for (int c0 = cc.x; c0 <= cc.y; c0 += 2) {
+                    float4 pv[2][kFinNK];
+                    bool use[2];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int c = c0 + q;
-                            use[q] = false;
-                            pv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (c > cc.y) continue;
-                            if (recs) {
-                                if (H.rec_chunk[c] >= H.rec_chunk[c + 1]) continue;
-                                const int side = H.rec_chunk_grp[2 * c] == gr ? 0 : 1;
-                                pv[q] = *reinterpret_cast<const float4 *>(
-                                    A.part + (((int64_t)c * 2 + side) * kRecBinsH + b % kRecBinsH) * A.K_pad + k);
-                            } else {
-                                if (H.chunk_pt[c] >= H.chunk_pt[c + 1]) continue;
-                                const int side = H.chunk_bin[2 * c] == key ? 0 : 1;
-                                pv[q] = *reinterpret_cast<const float4 *>(A.part + ((int64_t)c * 2 + side) * A.K_pad + k);
-                            }
-                            use[q] = true;
+                    for (int q2 = 0; q2 < 2; ++q2) {
+                        const int c = c0 + q2;
+                        use[q2] = false;
+#pragma unroll
+                        for (int t = 0; t < kFinNK; ++t) pv[q2][t] = zero;
+                        if (c > cc.y) continue;
+                        const float *row;
+                        if (recs) {
+                            if (H.rec_chunk[c] >= H.rec_chunk[c + 1]) continue;
+                            const int side = H.rec_chunk_grp[2 * c] == gr ? 0 : 1;
+                            row = A.part + (((int64_t)c * 2 + side) * kRecBinsH + b % kRecBinsH) * A.K_pad;
+                        } else {
+                            if (H.chunk_pt[c] >= H.chunk_pt[c + 1]) continue;
+                            const int side = H.chunk_bin[2 * c] == key ? 0 : 1;
+                            row = A.part + ((int64_t)c * 2 + side) * A.K_pad;
                         }
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (use[q]) add4(sum, pv[q]);
+                        for (int t = 0; t < kFinNK; ++t)
+                            if (live[t]) pv[q2][t] = *reinterpret_cast<const float4 *>(row + kq[t]);
+                        use[q2] = true;
                     }
-                    add4(total, sum);
+#pragma unroll
+                    for (int q2 = 0; q2 < 2; ++q2)
+                        if (use[q2])
+#pragma unroll
+                            for (int t = 0; t < kFinNK; ++t) add4(sum[t], pv[q2][t]);
                 }
+#pragma unroll
+                for (int t = 0; t < kFinNK; ++t) add4(total[t], sum[t]);
             }
         }
-        float *row = tile[warp] + 4 * lane;
-        row[0] = total.x;
-        row[1] = total.y;
-        row[2] = total.z;
-        row[3] = total.w;
-        __syncthreads();
-        for (int e = threadIdx.x; e < kFinK * kFinB; e += blockDim.x) {
-            const int kk = e / kFinB, bb = e - kk * kFinB;
-            const int64_t kr = kt * kFinK + kk;
-            const int bo = bt * kFinB + bb;
-            if (kr < A.K && bo < A.B) A.hist[kr * A.B + bo] = tile[bb][kk];
-        }
-        __syncthreads();  // the tile is reused by the next density tile
+    }
+#pragma unroll
+    for (int t = 0; t < kFinNK; ++t) {
+        float *row = tile[t][warp] + 4 * lane;
+        row[0] = total[t].x;
+        row[1] = total[t].y;
+        row[2] = total[t].z;
+        row[3] = total[t].w;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kFinNK * kFinK * kFinB; e += blockDim.x) {
+        const int t = e / (kFinK * kFinB), r = e - t * (kFinK * kFinB);
+        const int kk = r / kFinB, bb = r - kk * kFinB;
+        const int64_t kr = (kt0 + t) * kFinK + kk;
+        const int bo = bt * kFinB + bb;
+        if (kr < A.K && bo < A.B) A.hist[kr * A.B + bo] = tile[t][bb][kk];
     }
 }
 
-__global__ void __launch_bounds__(256, 4) k_hist_finish(const __grid_constant__ HistArgs A) {
+__global__ void __launch_bounds__(256, 3) k_hist_finish(const __grid_constant__ HistArgs A) {
     pdl_trigger();
     pdl_wait();
-    hist_finish_tiles(A, blockIdx.x, 1, blockIdx.y);
+    hist_finish_tiles(A, (int64_t)blockIdx.x * kFinNK, blockIdx.y);
 }
 
 // Batched finish: items[i] = (instance, density tile, bin tile).
-__global__ void __launch_bounds__(256, 4) k_hist_finish_batched(const HistArgs *__restrict__ insts, const int4 *__restrict__ items) {
+__global__ void __launch_bounds__(256, 3) k_hist_finish_batched(const HistArgs *__restrict__ insts, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
-    hist_finish_tiles(insts[it.x], it.y, 1, it.z);
+    hist_finish_tiles(insts[it.x], (int64_t)it.y * kFinNK, it.z);
 }
 
 }  // namespace
@@ -1400,7 +1423,7 @@ vup_status vup_hist_fused(vup_grid g, int64_t K, float *hist, cudaStream_t s, co
         }
     }
     VUP_PROF("hist_fixup", s, 1);
-    dim3 fg((unsigned)ceil_div64(K, kFinK), (unsigned)ceil_div64(g->B, kFinB));
+    dim3 fg((unsigned)ceil_div64(K, kFinK * kFinNK), (unsigned)ceil_div64(g->B, kFinB));
     VUP_CHECK_CUDA(launch_pdl(k_hist_finish, fg, dim3(32 * kFinB), 0, s, A));
     return VUP_OK;
 }
@@ -1449,7 +1472,7 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
         for (int p = 0; p < P_max; ++p)
             for (int cg = 0; cg < G; ++cg)
                 for (int64_t kt = 0; kt < nkt; ++kt) work.push_back({cost, HistItem{i, p, cg, (int32_t)kt}});
-        for (int64_t kb = 0; kb < ceil_div64(Ks[i], kFinK); ++kb)
+        for (int64_t kb = 0; kb < ceil_div64(Ks[i], kFinK * kFinNK); ++kb)
             for (int bt = 0; bt < (int)ceil_div64(gs[i]->B, kFinB); ++bt) fin.push_back(make_int4(i, (int)kb, bt, 0));
     }
     std::stable_sort(work.begin(), work.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
