@@ -94,9 +94,11 @@ typedef enum {
 } vup_model_id;
 
 /*
- * Densities, structure of arrays with element [k * ndim + d].  All pointers
- * are device pointers owned by the caller and must stay valid until the
- * queued work has run.
+ * Densities, structure of arrays with element [k * ndim + d], for
+ * 1 <= K <= VUP_MAX_DENSITIES (else the calls taking them return
+ * VUP_ERR_INVALID_ARG; so does K < 1 in vup_propagate_weights).  All
+ * pointers are device pointers owned by the caller and must stay valid until
+ * the queued work has run.
  *   kind  : uint8 vup_density_kind per (k, d)
  *   mu    : Gaussian / truncated-normal mean; uniform centre
  *   sigma : Gaussian / truncated-normal standard deviation (> 0);

@@ -632,6 +632,13 @@ def test_state_and_argument_errors():
     with pytest.raises(vup.VUPError) as e:
         g.propagate(dd3, "fp32")                              # ndim mismatch
     assert e.value.status == vup.VUP_ERR_INVALID_ARG
+    d0 = vup.densities_to_device(prob.dens.take([]))         # no densities
+    with pytest.raises(vup.VUPError) as e:
+        g.propagate(d0, "bf16x3")
+    assert e.value.status == vup.VUP_ERR_INVALID_ARG
+    with pytest.raises(vup.VUPError) as e:
+        vup.vup_propagate_weights(g.h, torch.empty((0, prob.N), dtype=torch.float32, device="cuda"))
+    assert e.value.status == vup.VUP_ERR_INVALID_ARG
 
 
 def test_set_outputs_user_model_matches_builtin():
