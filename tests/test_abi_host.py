@@ -100,3 +100,52 @@ def test_allocation_failure_hook_on_host(L):
         assert "cudaErrorMemoryAllocation" in vup.vup_last_error_detail()
     finally:
         vup.vup_debug_fail_alloc(-1)
+
+
+C_PROGRAM = r"""
+#include "vup.h"
+#include <stdio.h>
+#include <string.h>
+
+/* A C99 caller of the boundary: the header alone, linked against libvup.so;
+   only calls that need no device. */
+int main(void) {
+    int fails = 0;
+    vup_grid g = NULL;
+    const int64_t n[2] = {10, 10};
+    const double lo[2] = {0.0, 0.0}, hi[2] = {1.0, 1.0};
+    vup_densities d;
+    int s;
+    memset(&d, 0, sizeof d);
+    if (strstr(vup_version(), "sm_103a") == NULL) ++fails;
+    for (s = 0; s <= VUP_ERR_BOUNDS; ++s)
+        if (strncmp(vup_status_string((vup_status)s), "VUP_", 4) != 0) ++fails;
+    if (vup_grid_create(0, n, lo, hi, &g) != VUP_ERR_INVALID_ARG || g != NULL) ++fails;
+    if (vup_propagate(NULL, &d, VUP_BF16X3, NULL, NULL, NULL, NULL) != VUP_ERR_INVALID_ARG) ++fails;
+    if (vup_propagate_weights(NULL, 0, NULL, NULL, NULL, NULL) != VUP_ERR_INVALID_ARG) ++fails;
+    if (vup_set_weights_form(NULL, 0) != VUP_ERR_INVALID_ARG) ++fails;
+    if (vup_set_hist_stream(NULL, 0, NULL) != VUP_ERR_INVALID_ARG) ++fails;
+    if (vup_sync(NULL, NULL) != VUP_ERR_INVALID_ARG) ++fails;
+    printf("%s %d\n", fails ? "FAIL" : "OK", fails);
+    return fails != 0;
+}
+"""
+
+
+def test_header_compiles_as_c99_and_links(L, tmp_path):
+    """include/vup.h compiles as strict C99 without warnings and a C program
+    links against libvup.so and calls it (host-only calls)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "caller.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(vup.LIB_PATH)
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           str(src), "-o", str(exe), "-L", libdir, "-l:" + os.path.basename(vup.LIB_PATH), "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
