@@ -504,7 +504,7 @@ vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa, bool tf32)
     if ((st = devbuf_reserve(g->dstats, sizeof(DensStats) * K_pad * nd)) != VUP_OK) return st;
     if ((st = devbuf_reserve(g->ftab, sizeof(float) * K_pad * vup_ftab_floats(g))) != VUP_OK) return st;
     if (nd >= 2) {
-        const int64_t nct = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles(g->orient[vup_tc_orient(g)]));
+        const int64_t nct = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles_max(g->orient[vup_tc_orient(g)]));
         if ((st = devbuf_reserve(g->partials, sizeof(float) * 4 * K_pad * nct)) != VUP_OK) return st;
         // partial rows of cut keys (2 per chunk) or cut record groups (2 x 8 bins per record chunk)
         const size_t part_rows = std::max<size_t>(2 * (size_t)g->n_chunks, 16 * (size_t)g->n_chunks_rec);
@@ -530,8 +530,8 @@ vup_status vup_reserve_k(vup_grid g, int64_t K, bool bf16, bool ipsa, bool tf32)
             if ((st = devbuf_reserve(g->atab_lo, sizeof(__nv_bfloat16) * a)) != VUP_OK) return st;
         }
         if (ipsa) {
-            int64_t n0 = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles(g->orient[0]));
-            int64_t n1 = std::max(vup_simt_col_tiles(g->orient[1]), vup_tc_col_tiles(g->orient[1]));
+            int64_t n0 = std::max(vup_simt_col_tiles(g->orient[0]), vup_tc_col_tiles_max(g->orient[0]));
+            int64_t n1 = std::max(vup_simt_col_tiles(g->orient[1]), vup_tc_col_tiles_max(g->orient[1]));
             if ((st = devbuf_reserve(g->ipsa_part, sizeof(float) * 4 * 3 * K_pad * (n0 + n1))) != VUP_OK)
                 return st;
         }
@@ -632,7 +632,7 @@ static vup_status propagate_nd(vup_grid g, const vup_densities *d, vup_precision
     if (fuse) {
         const int64_t K_pad = ceil_div64(K, 128) * 128;
         for (int o = 0; o < 2; ++o)
-            inct[o] = bf16 ? vup_tc_col_tiles(g->orient[o]) : vup_simt_col_tiles(g->orient[o]);
+            inct[o] = bf16 ? vup_tc_col_tiles(g->orient[o], K) : vup_simt_col_tiles(g->orient[o]);
         ipart[0] = (float *)g->ipsa_part.p;
         ipart[1] = ipart[0] + (size_t)3 * inct[0] * K_pad * 4;
     }
@@ -649,7 +649,7 @@ static vup_status propagate_nd(vup_grid g, const vup_densities *d, vup_precision
             if ((st = vup_moments_tc(g, K, to, 1, (float *)g->partials.p, s, tf32 ? 1 : 0,
                                      precision == VUP_TF32 ? 1 : 3)) != VUP_OK)
                 return st;
-            nct = vup_tc_col_tiles(g->orient[to]);
+            nct = vup_tc_col_tiles(g->orient[to], K);
         } else {
             if ((st = vup_moments_simt(g, K, 0, 1, (float *)g->partials.p, s)) != VUP_OK) return st;
             nct = vup_simt_col_tiles(g->orient[0]);
@@ -737,8 +737,8 @@ extern "C" vup_status vup_ipsa_sensitivity(vup_grid g, const vup_densities *d, v
     float *p0 = (float *)g->ipsa_part.p;
     int64_t n0, n1;
     if (bf16) {
-        n0 = vup_tc_col_tiles(g->orient[0]);
-        n1 = vup_tc_col_tiles(g->orient[1]);
+        n0 = vup_tc_col_tiles(g->orient[0], K);
+        n1 = vup_tc_col_tiles(g->orient[1], K);
     } else {
         n0 = vup_simt_col_tiles(g->orient[0]);
         n1 = vup_simt_col_tiles(g->orient[1]);

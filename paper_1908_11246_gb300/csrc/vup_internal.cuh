@@ -422,7 +422,9 @@ struct ProfScope {
 
 // Column-tile counts used by the contraction kernels (for the finish step).
 int64_t vup_simt_col_tiles(const Orient &o);
-int64_t vup_tc_col_tiles(const Orient &o);
+// partial columns of a contraction of K densities, and the most any K can need
+int64_t vup_tc_col_tiles(const Orient &o, int64_t K);
+int64_t vup_tc_col_tiles_max(const Orient &o);
 
 // Scratch sizes per K row.
 size_t vup_ftab_floats(const vup_grid g);   // sum_d n[d] floats per k

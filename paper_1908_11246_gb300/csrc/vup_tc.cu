@@ -145,6 +145,7 @@ struct TcTile {
 // second axis once and one factor of the first axis per tile.
 struct TcSched {
     int n_m, n_n, n_split;  // row tiles, column tiles, reduction splits
+    int split_terms;        // reduction terms per split (a multiple of 64)
     int per_row;            // items per (row tile, split) = partial columns per split
     int fast;               // row-block items
     int T1, L, n0;          // row-block: column tiles per first-axis index, indices per item, first-axis size
@@ -168,8 +169,8 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
     constexpr int BKE = KIND ? BK_TF32 : BK;  // operand elements per 128-byte row
     // split reduction: n_split accumulators of at most kSplitTerms terms each
     // (the tensor cores' FP32 accumulation error grows with the reduction
-    // length); every split writes its own partial columns, summed in FP64
-    constexpr int kSplitKb = kSplitTerms / BKE;
+    // length); every split writes its own partial columns, summed by the
+    // finish
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
@@ -213,8 +214,9 @@ k_moments_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ C
             kb1 = in->n_kb;
             bn = in->bn;
         } else {
-            kb0 = sp * kSplitKb;
-            kb1 = min(n_kb, kb0 + kSplitKb);
+            const int split_kb = S.split_terms / BKE;
+            kb0 = sp * split_kb;
+            kb1 = min(n_kb, kb0 + split_kb);
             bn = BN;
         }
     };
@@ -488,13 +490,20 @@ bool make_map(CUtensorMap *m, const void *base, int64_t ld, int64_t rows, int bo
 }  // namespace
 
 // Schedule of a contraction over K_pad rows (see TcSched); its partial
-// columns per row are n_split * per_row.
+// columns per row are n_split * per_row.  Splits of at most kSplitTerms
+// terms; a reduction of one split of at least 2 * kMinSplitTerms terms is
+// cut in two when that fills the persistent grid's last wave better (c2:
+// 2048 items are 13.5 waves of 152 CTAs, 4096 half items 26.9), the
+// epilogue of a half item being far shorter than its MMAs.
+constexpr int kMinSplitTerms = 512;
 static int tc_splits(const Orient &o) { return (int)ceil_div64(o.R_pad, kSplitTerms); }
+static bool tc_can_halve(const Orient &o) { return tc_splits(o) == 1 && o.R_pad >= 2 * kMinSplitTerms; }
 static TcSched tc_sched(const Orient &o, int64_t K_pad) {
     TcSched S{};
     S.n_m = (int)(K_pad / BM);
     S.n_n = (int)ceil_div64(o.NC, BN);
     S.n_split = tc_splits(o);
+    S.split_terms = kSplitTerms;
     S.fast = o.n_rest_axes == 2 && o.rest_n[1] % (BN / 4) == 0;
     if (S.fast) {
         S.T1 = (int)(o.rest_n[1] / (BN / 4));
@@ -507,11 +516,23 @@ static TcSched tc_sched(const Orient &o, int64_t K_pad) {
         S.n0 = S.n_n;
         S.per_row = S.n_n;
     }
+    if (tc_can_halve(o)) {
+        const int64_t sms = vup_num_sms(), items = (int64_t)S.n_m * S.per_row;
+        auto fill = [&](int64_t it) { return (double)it / (double)(ceil_div64(it, sms) * sms); };
+        if (fill(2 * items) > fill(items) + 0.02) {
+            S.n_split = 2;
+            S.split_terms = (int)(ceil_div64(o.R_pad, 2 * 64) * 64);
+        }
+    }
     return S;
 }
-int64_t vup_tc_col_tiles(const Orient &o) {
-    const TcSched S = tc_sched(o, BM);
+int64_t vup_tc_col_tiles(const Orient &o, int64_t K) {
+    const TcSched S = tc_sched(o, ceil_div64(K, 128) * 128);
     return (int64_t)S.n_split * S.per_row;
+}
+int64_t vup_tc_col_tiles_max(const Orient &o) {
+    const TcSched S = tc_sched(o, BM);
+    return (int64_t)S.n_split * S.per_row * (tc_can_halve(o) ? 2 : 1);
 }
 
 vup_status vup_moments_tc(vup_grid g, int64_t K, int orient, int n_out, float *part, cudaStream_t s, int kind,
