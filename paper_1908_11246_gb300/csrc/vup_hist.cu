@@ -941,10 +941,61 @@ struct HistItem {
     int32_t inst, p, cg, kt;
 };
 
+// Per-stream item lists of a batch: the items of the instances whose
+// device-chosen stream s is served by launch s, in the plan's (longest
+// first) order, so that no launch walks past the other streams' items.  One
+// CTA: the instances' streams to shared memory (global reads past
+// kSplitStaged instances), then the items in blocks of kSplitThreads, each
+// block compacted in order by warp ballots and per-warp counts.
+constexpr int kSplitThreads = 1024;
+constexpr int kSplitStaged = 32768;
+__global__ void __launch_bounds__(kSplitThreads) k_hist_split_items(const HistArgs *__restrict__ insts, int n_inst,
+                                                                    const HistItem *__restrict__ items, int n_items,
+                                                                    int32_t *__restrict__ lists,
+                                                                    int32_t *__restrict__ counts) {
+    extern __shared__ uint8_t s_stream[];  // [n_inst] when staged
+    __shared__ int s_warp[3][kSplitThreads / 32];
+    __shared__ int s_base[3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool staged = n_inst <= kSplitStaged;
+    if (staged)
+        for (int i = tid; i < n_inst; i += blockDim.x) s_stream[i] = (uint8_t)min(hist_stream(insts[i]), 3);
+    if (tid < 3) s_base[tid] = 0;
+    __syncthreads();
+    for (int base = 0; base < n_items; base += kSplitThreads) {
+        const int it = base + tid;
+        int st = 3;  // 3: no launch serves it
+        if (it < n_items) {
+            const int inst = items[it].inst;
+            st = staged ? (int)s_stream[inst] : min(hist_stream(insts[inst]), 3);
+        }
+        unsigned m[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) m[q] = __ballot_sync(0xffffffffu, st == q);
+        if (lane < 3) s_warp[lane][warp] = __popc(m[lane]);
+        __syncthreads();
+        if (st < 3) {
+            int off = s_base[st] + __popc(m[st] & ((1u << lane) - 1u));
+            for (int w = 0; w < warp; ++w) off += s_warp[st][w];
+            lists[(int64_t)st * n_items + off] = it;
+        }
+        __syncthreads();
+        if (tid < 3) {
+            int t = 0;
+            for (int w = 0; w < kSplitThreads / 32; ++w) t += s_warp[tid][w];
+            s_base[tid] += t;
+        }
+        __syncthreads();
+    }
+    if (tid < 3) counts[tid] = s_base[tid];
+}
+
 template <int NF, int MODE>
 __global__ void __launch_bounds__(hist_warps(MODE) * 32, 1) k_hist_batched(const HistArgs *__restrict__ insts,
                                                                      const HistItem *__restrict__ items,
-                                                                     int n_items, int64_t tile_rows,
+                                                                     const int32_t *__restrict__ list,
+                                                                     const int32_t *__restrict__ count,
+                                                                     int64_t tile_rows,
                                                                      int *__restrict__ next_item) {
     extern __shared__ __align__(128) uint8_t sm[];
     __shared__ ItemCtx X;
@@ -953,15 +1004,16 @@ __global__ void __launch_bounds__(hist_warps(MODE) * 32, 1) k_hist_batched(const
     if (threadIdx.x == 0) abort = 0;
     hist_init_mbar(sm, tile_rows, hist_warps(MODE));
     uint32_t wseq = 0;
-    // items are handed out one at a time in their (longest first) order
+    // this stream's items are handed out one at a time in their (longest
+    // first) order
+    const int n_items = *count;
     for (;;) {
         __syncthreads();  // every thread has read the previous s_it
         if (threadIdx.x == 0) s_it = atomicAdd(next_item, 1);
         __syncthreads();
         const int it = s_it;
         if (it >= n_items) break;
-        const HistItem w = items[it];
-        if (hist_stream(insts[w.inst]) != hist_stream_of(MODE)) continue;  // uniform
+        const HistItem w = items[list[it]];
         hist_item<NF, MODE>(insts + w.inst, w.p, w.cg, (int64_t)w.kt * kKT, sm, tile_rows, wseq, &abort, X, s_invz,
                             &next_chunk);
     }
@@ -1447,8 +1499,9 @@ bool vup_hist_batchable(vup_grid g) {
 // instance's (part, chunk group, density tile) items, longest first, and one
 // finishing launch.
 struct HistPlan {
-    DevBuf args, items, fitems, ctr;  // ctr: next item of each stream's launch
-    int n_items = 0, n_fitems = 0;
+    DevBuf args, items, fitems, ctr;  // ctr: next item of each stream's launch, then each stream's item count
+    DevBuf lists;                     // [3][n_items] each stream's items (k_hist_split_items)
+    int n_inst = 0, n_items = 0, n_fitems = 0;
     int64_t rows = 0;
 };
 
@@ -1479,6 +1532,7 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
     std::vector<HistItem> items(work.size());
     for (size_t q = 0; q < work.size(); ++q) items[q] = work[q].second;
     HistPlan *P = new HistPlan();
+    P->n_inst = n;
     P->n_items = (int)items.size();
     P->n_fitems = (int)fin.size();
     P->rows = rows_max;
@@ -1486,11 +1540,13 @@ vup_status vup_hist_plan(int n, const vup_grid *gs, const int64_t *Ks, float *co
     if ((st = devbuf_reserve(P->args, sizeof(HistArgs) * n)) != VUP_OK ||
         (st = devbuf_reserve(P->items, sizeof(HistItem) * std::max<size_t>(1, items.size()))) != VUP_OK ||
         (st = devbuf_reserve(P->fitems, sizeof(int4) * std::max<size_t>(1, fin.size()))) != VUP_OK ||
-        (st = devbuf_reserve(P->ctr, sizeof(int) * 3)) != VUP_OK) {
+        (st = devbuf_reserve(P->ctr, sizeof(int) * 6)) != VUP_OK ||
+        (st = devbuf_reserve(P->lists, sizeof(int32_t) * 3 * std::max<size_t>(1, items.size()))) != VUP_OK) {
         devbuf_free(P->args);
         devbuf_free(P->items);
         devbuf_free(P->fitems);
         devbuf_free(P->ctr);
+        devbuf_free(P->lists);
         delete P;
         return st;
     }
@@ -1515,6 +1571,7 @@ void vup_hist_plan_free(void *plan) {
     devbuf_free(P->items);
     devbuf_free(P->fitems);
     devbuf_free(P->ctr);
+    devbuf_free(P->lists);
     delete P;
 }
 
@@ -1524,22 +1581,24 @@ vup_status vup_hist_batched(void *plan, cudaStream_t s) {
     const size_t smem = hist_smem_bytes(P->rows);
     if (smem > 220 * 1024) return VUP_ERR_UNSUPPORTED;
     {
-        VUP_PROF("hist_segmented_batched", s, 3);
+        VUP_PROF("hist_segmented_batched", s, 4);
         const int grid = std::max(1, std::min(P->n_items, vup_num_sms()));
-        int *ctr = (int *)P->ctr.p;
+        int *ctr = (int *)P->ctr.p, *counts = ctr + 3;
+        const int32_t *lists = (const int32_t *)P->lists.p;
+        const HistArgs *args = (const HistArgs *)P->args.p;
+        const HistItem *items = (const HistItem *)P->items.p;
         VUP_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(int), s));
-        k_hist_batched<1, 0><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
-                                                                 (const HistItem *)P->items.p, P->n_items, P->rows,
-                                                                 ctr);
+        const size_t split_smem = P->n_inst <= kSplitStaged ? (size_t)P->n_inst : 0;
+        k_hist_split_items<<<1, kSplitThreads, split_smem, s>>>(args, P->n_inst, items, P->n_items,
+                                                                (int32_t *)P->lists.p, counts);
         VUP_CHECK_LAUNCH();
-        k_hist_batched<1, 1><<<grid, kHistWarps * 32, smem, s>>>((const HistArgs *)P->args.p,
-                                                                 (const HistItem *)P->items.p, P->n_items, P->rows,
-                                                                 ctr + 1);
+        k_hist_batched<1, 0><<<grid, kHistWarps * 32, smem, s>>>(args, items, lists, counts, P->rows, ctr);
+        VUP_CHECK_LAUNCH();
+        k_hist_batched<1, 1><<<grid, kHistWarps * 32, smem, s>>>(args, items, lists + P->n_items, counts + 1,
+                                                                 P->rows, ctr + 1);
         VUP_CHECK_LAUNCH();
         k_hist_batched<1, 2><<<grid, hist_warps(2) * 32, hist_smem_bytes(P->rows, hist_warps(2)), s>>>(
-            (const HistArgs *)P->args.p,
-                                                                 (const HistItem *)P->items.p, P->n_items, P->rows,
-                                                                 ctr + 2);
+            args, items, lists + 2 * (size_t)P->n_items, counts + 2, P->rows, ctr + 2);
         VUP_CHECK_LAUNCH();
     }
     VUP_PROF("hist_fixup_batched", s, 1);
